@@ -1,0 +1,35 @@
+"""Plain FP64 CPU oracle for the particle-mesh (PM) hot path of arXiv:2404.02783.
+
+TEST INFRASTRUCTURE ONLY.  Nothing in the product path may import this package:
+only ``tests/``, ``__graft_entry__.smoke()`` and the ``cpu_baseline`` /
+``--impl reference`` legs of ``bench.py`` use it.  It shares no code, tables or
+constants with the CUDA library in ``paper_2404_02783_gb300/``; the two meet only
+through the seeded input generators in ``inputs/``.
+
+Everything here is written for a reader checking it against the paper by eye:
+numpy FP64 arrays, ``numpy.fft`` / ``scipy.integrate`` as library primitives, no
+blocking, fusion or reordering beyond what each definition states.
+
+Modules (each function cites the passage it follows):
+
+* ``cosmology``  -- background E(a), growth D(a), f(a), kick/drift integrals,
+  Eisenstein-Hu no-wiggle linear P(k) normalised to sigma_8 (Sec. 3 "Simulation setup").
+* ``philox``     -- Philox4x32-10 counter-based generator (Salmon et al. 2011) and
+  the per-wavevector Gaussian draw used for the initial phases ("same initial
+  random perturbation phases", Sec. 2).
+* ``ic``         -- Zel'dovich (1LPT) initial conditions (Sec. 2, nLPT with n=1).
+* ``cic``        -- cloud-in-cell deposit / interpolation, cell keys and sort order
+  (counting density, Sec. 4).
+* ``gravity``    -- Newtonian Poisson solve, spectral gradient, linearised
+  Poisson-gauge scalar constraint (Sec. 2; Eq. physical_density).
+* ``pm``         -- kick-drift-kick leapfrog in the scale factor.
+* ``combine``    -- GR displacement field and combination (Eqs. xiGR and combined).
+* ``stats``      -- power spectrum (Eq. powerspectrum), bispectrum (Eq. bispectre),
+  halo-proxy linear-bias fit (Eq. b1).
+
+Parity status: every function is pinned by a ``-m "not gpu"`` test against a
+closed form, an invariant, a brute-force evaluation or a textbook special case,
+except the amplitude of the horizon-scale GR displacement, for which the paper
+prints no values (parity unpinned beyond the k >> H limit and the matter-era
+identity tested in ``tests/test_oracle_gravity.py``).
+"""

@@ -1,0 +1,98 @@
+"""Zel'dovich (first-order LPT) initial conditions on a particle lattice.
+
+Oracle (test infrastructure only).
+
+Sec. 2 combines Newtonian and relativistic runs that start from the same random
+phases; Sec. 2 also names first-order LPT ("1LPT") as a way to produce particle
+positions.  Sec. 3 starts the runs at z = 50.  Reading used here:
+
+* delta_n = N^3 g_n sqrt(P(k_n)/V) on the N_p^3 lattice, with g_n the unit complex
+  Gaussian of ``philox.hermitian_noise_half`` or g = FFT(w)/N^{3/2} for a caller's
+  real white-noise field w; P is the z = 0 linear spectrum (D(1) = 1).
+* Psi_n = i k delta_n / k^2 (the zero mode and Nyquist components are zero).
+* x = q + D(a) Psi(q),  p = a^2 E(a) f(a) D(a) Psi(q), with q the lattice node
+  i L / N_p and p = a^2 dx/dt / H0 (Mpc/h in H0 = 1 units).
+* Positions are returned in units of the box side: as uint32 ticks
+  (2^32 per side, exact periodic wrap) or as FP64 fractions in [0, 1).
+"""
+import numpy as np
+
+from . import philox
+
+
+def linear_delta_k(cosmo, n, box, seed=None, white_noise=None, paired=False):
+    """delta_n at a = 1 on the rfftn half grid (n, n, n/2+1)."""
+    if white_noise is not None:
+        w = np.asarray(white_noise, dtype=np.float64).reshape(n, n, n)
+        g = np.fft.rfftn(w) / n**1.5
+        f = philox.signed_freqs(n)
+        fz = np.arange(n // 2 + 1)
+        NX, NY, NZ = np.meshgrid(f, f, fz, indexing="ij")
+        nyq = (np.abs(NX) == n // 2) | (np.abs(NY) == n // 2) | (NZ == n // 2)
+        g = np.where(nyq, 0.0, g)
+        g[0, 0, 0] = 0.0
+    else:
+        g = philox.hermitian_noise_half(seed, n)
+    if paired:
+        g = -g
+    kf = 2.0 * np.pi / box
+    n2 = mode_n2(n)
+    k = kf * np.sqrt(n2.astype(np.float64))
+    pk = np.zeros_like(k)
+    nz = n2 > 0
+    pk[nz] = cosmo.power_linear(k[nz])
+    return n**3 * g * np.sqrt(pk / box**3)
+
+
+def mode_n2(n):
+    """|n|^2 on the rfftn half grid, with signed integer wavenumbers."""
+    f = philox.signed_freqs(n)
+    fz = np.arange(n // 2 + 1, dtype=np.int64)
+    NX, NY, NZ = np.meshgrid(f, f, fz, indexing="ij")
+    return NX * NX + NY * NY + NZ * NZ
+
+
+def za_displacement(delta_k, n, box):
+    """Psi_j(q) = IFFT[i k_j delta_k / k^2] on the lattice, shape (3, n, n, n) in Mpc/h."""
+    kf = 2.0 * np.pi / box
+    f = philox.signed_freqs(n).astype(np.float64)
+    fz = np.arange(n // 2 + 1, dtype=np.float64)
+    f_nyq0 = np.where(np.abs(f) == n // 2, 0.0, f)
+    fz_nyq0 = np.where(fz == n // 2, 0.0, fz)
+    NX, NY, NZ = np.meshgrid(f_nyq0, f_nyq0, fz_nyq0, indexing="ij")
+    n2 = mode_n2(n).astype(np.float64)
+    inv_k2 = np.zeros_like(n2)
+    inv_k2[n2 > 0] = 1.0 / (kf * kf * n2[n2 > 0])
+    psi = np.empty((3, n, n, n))
+    for j, Nj in enumerate((NX, NY, NZ)):
+        psi[j] = np.fft.irfftn(1j * kf * Nj * delta_k * inv_k2, s=(n, n, n), axes=(0, 1, 2))
+    return psi
+
+
+def lattice_ticks(n):
+    """Lattice node coordinates in ticks, particle id = (ix n + iy) n + iz."""
+    step = 2**32 // n
+    i = np.arange(n, dtype=np.uint64) * np.uint64(step)
+    X, Y, Z = np.meshgrid(i, i, i, indexing="ij")
+    return np.stack([X.ravel(), Y.ravel(), Z.ravel()]).astype(np.uint32)
+
+
+def zeldovich(cosmo, n, box, a_init, seed=None, white_noise=None, paired=False, fixed=True):
+    """ZA particles at a_init: returns (x, p) with x (3, n^3) ticks or fractions, p (3, n^3)."""
+    dk = linear_delta_k(cosmo, n, box, seed=seed, white_noise=white_noise, paired=paired)
+    psi = za_displacement(dk, n, box).reshape(3, -1)
+    D = cosmo.growth_D(a_init)
+    f = cosmo.growth_f(a_init)
+    E = float(cosmo.E(a_init))
+    p = a_init**2 * E * f * D * psi
+    if fixed:
+        q = lattice_ticks(n).astype(np.int64)
+        disp = np.rint(D * psi * (2.0**32 / box)).astype(np.int64)
+        x = ((q + disp) % 2**32).astype(np.uint32)
+    else:
+        i = np.arange(n, dtype=np.float64) / n
+        X, Y, Z = np.meshgrid(i, i, i, indexing="ij")
+        q = np.stack([X.ravel(), Y.ravel(), Z.ravel()])
+        x = q + D * psi / box
+        x = x - np.floor(x)
+    return x, p

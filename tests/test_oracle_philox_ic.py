@@ -1,0 +1,100 @@
+"""Pins of the Philox phases and the Zel'dovich initial conditions."""
+import os
+
+import numpy as np
+import pytest
+
+from oracle import ic, philox
+from oracle.cosmology import Cosmology
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def test_philox_known_answers():
+    rows = [l.split() for l in open(os.path.join(GOLDEN, "philox4x32_10_kat.txt")) if l.strip() and not l.startswith("#")]
+    assert len(rows) == 3
+    for r in rows:
+        v = [int(t, 16) for t in r]
+        out = philox.philox4x32_10(*[np.uint64(t) for t in v[:6]])
+        assert [int(o) for o in out] == v[6:]
+
+
+def test_gaussian_moments():
+    n = np.arange(200_000)
+    g = philox.unit_gaussian_modes(7, n % 97, n // 97, np.ones_like(n))
+    se = 1.0 / np.sqrt(n.size)
+    assert abs(g.real.mean()) < 5 * se and abs(g.imag.mean()) < 5 * se
+    assert np.mean(np.abs(g)**2) == pytest.approx(1.0, abs=5 * se)
+    assert np.var(g.real) == pytest.approx(0.5, abs=5 * se)
+    # Box-Muller: |g|^2 is exponential with unit mean -> P(|g|^2 > 1) = e^-1
+    assert np.mean(np.abs(g)**2 > 1.0) == pytest.approx(np.exp(-1.0), abs=5 * se)
+
+
+@pytest.mark.parametrize("n", [8, 16])
+def test_noise_is_hermitian(n):
+    # A half-grid spectrum is the rfft of a real field iff it is Hermitian on the nz=0 plane:
+    # the round trip irfftn -> rfftn must reproduce it exactly.
+    g = philox.hermitian_noise_half(3, n)
+    back = np.fft.rfftn(np.fft.irfftn(g, s=(n, n, n), axes=(0, 1, 2)))
+    assert np.max(np.abs(back - g)) < 1e-12
+
+
+def test_noise_shared_across_resolutions():
+    g16 = philox.hermitian_noise_half(11, 16)
+    g32 = philox.hermitian_noise_half(11, 32)
+    f16 = philox.signed_freqs(16)
+    for ix in range(16):
+        for iy in range(16):
+            nx, ny = f16[ix], f16[iy]
+            if abs(nx) == 8 or abs(ny) == 8:
+                continue
+            np.testing.assert_array_equal(g16[ix, iy, :8], g32[nx % 32, ny % 32, :8])
+
+
+def test_za_single_mode_displacement():
+    # A single cosine in the white noise gives an analytic Zel'dovich displacement:
+    # delta = eps cos(k x) -> Psi_x = -(eps/k) sin(k x), Psi_y = Psi_z = 0.
+    n, box = 16, 100.0
+    x = np.arange(n) / n
+    eps = 0.01
+    delta = eps * np.cos(2 * np.pi * 2 * x)[:, None, None] * np.ones((n, n, n))
+    psi = ic.za_displacement(np.fft.rfftn(delta), n, box)
+    k = 2 * np.pi * 2 / box
+    expect = -(eps / k) * np.sin(2 * np.pi * 2 * x)[:, None, None] * np.ones((n, n, n))
+    assert np.max(np.abs(psi[0] - expect)) < 1e-14 * box
+    assert np.max(np.abs(psi[1])) < 1e-15 * box and np.max(np.abs(psi[2])) < 1e-15 * box
+
+
+def test_za_divergence_is_minus_delta():
+    # Linear continuity: div Psi = -delta (every non-Nyquist mode).
+    n, box = 16, 500.0
+    dk = ic.linear_delta_k(Cosmology(), n, box, seed=5)
+    psi = ic.za_displacement(dk, n, box)
+    kf = 2 * np.pi / box
+    f = philox.signed_freqs(n)
+    div = np.zeros_like(dk)
+    for j, axis_f in enumerate((f[:, None, None], f[None, :, None], np.arange(n // 2 + 1)[None, None, :])):
+        div = div + 1j * kf * axis_f * np.fft.rfftn(psi[j])
+    assert np.max(np.abs(div + dk)) < 1e-10 * np.max(np.abs(dk))
+
+
+def test_ic_spectrum_amplitude_exact():
+    # |delta_n|^2 = N^6 |g_n|^2 P(k_n) / V mode by mode (Eq. powerspectrum normalisation).
+    n, box, c = 16, 1000.0, Cosmology()
+    dk = ic.linear_delta_k(c, n, box, seed=9)
+    g = philox.hermitian_noise_half(9, n)
+    n2 = ic.mode_n2(n)
+    m = (n2 > 0) & (np.abs(g) > 0)
+    P = c.power_linear(2 * np.pi / box * np.sqrt(n2[m]))
+    np.testing.assert_allclose(np.abs(dk[m])**2, n**6 * np.abs(g[m])**2 * P / box**3, rtol=1e-12)
+
+
+def test_zeldovich_particles_fixed_and_float_agree():
+    c = Cosmology()
+    xt, pt = ic.zeldovich(c, 8, 1000.0, 1 / 51, seed=2, fixed=True)
+    xf, pf = ic.zeldovich(c, 8, 1000.0, 1 / 51, seed=2, fixed=False)
+    np.testing.assert_array_equal(pt, pf)
+    d = xt.astype(np.float64) / 2**32 - xf
+    d -= np.rint(d)
+    assert np.max(np.abs(d)) <= 2**-32
+    assert abs(pt.mean()) < 1e-12 * np.abs(pt).max()

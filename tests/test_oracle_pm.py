@@ -1,0 +1,122 @@
+"""Pins of the kick-drift-kick PM oracle: Zel'dovich plane wave, growth, conservation."""
+import numpy as np
+import pytest
+
+import inputs
+from oracle import cic, gravity, ic, pm, stats
+from oracle.cosmology import Cosmology
+
+
+def _plane_wave_run(n_steps, n=32, box=100.0, a_i=0.05, a_f=0.5, fixed=False, nmode=1):
+    # delta_L(q, a=1) = A cos(k q_x): ZA is exact for planar symmetry before shell crossing.
+    c = Cosmology()
+    k = 2 * np.pi * nmode / box
+    A = 0.5 / c.growth_D(a_f)  # D(a_f) A k |Psi|/... -> 1 - D A cos(kq) > 0.5 everywhere
+    q = np.arange(n) / n
+    X, Y, Z = np.meshgrid(q, q, q, indexing="ij")
+    qx = X.ravel()
+    psi = np.zeros((3, n**3))
+    psi[0] = -(A / k) * np.sin(k * qx * box)
+
+    def za(a):
+        D, f, E = c.growth_D(a), c.growth_f(a), float(c.E(a))
+        xx = np.stack([X.ravel(), Y.ravel(), Z.ravel()]) + D * psi / box
+        return xx - np.floor(xx), a * a * E * f * D * psi
+
+    x0, p0 = za(a_i)
+    if fixed:
+        x0 = (np.floor(x0 * 2.0**32).astype(np.uint64) % np.uint64(2**32)).astype(np.uint32)
+    run = pm.PMRun(c, n, box, a_i, a_f, n_steps, x0, p0)
+    run.step(n_steps)
+    x_end, p_end = za(a_f)
+    return run, x_end, p_end
+
+
+def _disp_err(run, x_end):
+    x = run.x.astype(np.float64) / 2**32 if run.fixed else run.x
+    d = x[0] - x_end[0]
+    d -= np.rint(d)
+    return d
+
+
+def test_zeldovich_plane_wave_and_second_order_convergence():
+    errs = {}
+    for ns in (8, 16, 32):
+        run, x_end, p_end = _plane_wave_run(ns)
+        errs[ns] = _disp_err(run, x_end)
+    amp = 0.5 / (2 * np.pi)  # D(a_f) A / k in box units
+    # A 32-cell plane wave tracks the exact (Zel'dovich) solution to a few per cent of its
+    # amplitude; the remaining error is the mesh's and halves when the mesh is refined.
+    assert np.max(np.abs(errs[32])) < 0.04 * amp
+    np.testing.assert_allclose(run.p[0], p_end[0], rtol=0, atol=0.045 * np.max(np.abs(p_end[0])))
+    run16, x16, _ = _plane_wave_run(32, n=16)
+    rm = np.max(np.abs(_disp_err(run16, x16))) / np.max(np.abs(errs[32]))
+    assert 1.7 < rm < 2.8, rm
+    # KDK is second order in the step: successive differences shrink ~4x per halving
+    # (measured from a = 0.2, where the uniform a-grid is in its asymptotic regime)
+    e = {ns: _disp_err(*_plane_wave_run(ns, a_i=0.2)[:2]) for ns in (8, 16, 32)}
+    r = np.max(np.abs(e[8] - e[16])) / np.max(np.abs(e[16] - e[32]))
+    assert 2.8 < r < 5.5, r
+    # y and z stay on the lattice
+    assert np.max(np.abs(run.p[1])) < 1e-12 and np.max(np.abs(run.p[2])) < 1e-12
+
+
+def test_fixed_point_and_fp64_positions_agree():
+    run_f, x_end, _ = _plane_wave_run(16, fixed=True)
+    run_d, _, _ = _plane_wave_run(16, fixed=False)
+    d = run_f.x.astype(np.float64) / 2**32 - run_d.x
+    d -= np.rint(d)
+    assert np.max(np.abs(d)) < 1e-7
+
+
+def test_linear_growth_of_low_k_power():
+    c = Cosmology()
+    n, box, a_i, a_f = 32, 2000.0, 0.02, 0.04
+    x, p = ic.zeldovich(c, n, box, a_i, seed=1, fixed=False)
+    run = pm.PMRun(c, n, box, a_i, a_f, 20, x, p)
+    edges = np.array([1.0, 2.0, 3.0, 4.0])
+    _, p0, _ = stats.power_spectrum(cic.density_contrast(x, n), box, edges)
+    run.step(20)
+    _, p1, _ = stats.power_spectrum(cic.density_contrast(run.x, n), box, edges)
+    want = (c.growth_D(a_f) / c.growth_D(a_i))**2
+    ratio = p1 / p0 / want
+    # the lowest bin grows as D^2 to 1%; the CIC-smoothed force slows growth as k^2 above it
+    assert abs(ratio[0] - 1) < 0.01
+    assert np.all(np.diff(ratio) < 0) and ratio[-1] > 0.95
+
+
+def test_momentum_conservation():
+    c = Cosmology()
+    n = 16
+    x = inputs.ticks_to_fractions(inputs.lattice_order_ticks(12, 16, 2.0))
+    p = inputs.momenta(13, x.shape[1], 50.0)
+    run = pm.PMRun(c, n, 500.0, 0.3, 1.0, 5, x, p)
+    p_sum0 = run.p.sum(axis=1)
+    run.step(5)
+    assert np.max(np.abs(run.p.sum(axis=1) - p_sum0)) < 1e-10 * np.abs(run.p).sum()
+
+
+def test_pair_forces_antisymmetric():
+    c = Cosmology()
+    x = inputs.ticks_to_fractions(inputs.uniform_ticks(14, 2))
+    run = pm.PMRun(c, 16, 100.0, 0.5, 1.0, 1, x, np.zeros((3, 2)))
+    g = run.accel(0.5)
+    np.testing.assert_allclose(g[:, 0], -g[:, 1], rtol=1e-10, atol=1e-14 * np.abs(g).max())
+    assert np.abs(g).max() > 0
+
+
+def test_gr_mode_matches_newton_for_small_box_and_differs_on_horizon_scales():
+    c = Cosmology()
+    n = 16
+    for box, close in ((50.0, True), (20000.0, False)):
+        x, p = ic.zeldovich(c, n, box, 0.1, seed=3, fixed=False)
+        rn = pm.PMRun(c, n, box, 0.1, 0.3, 4, x, p, mode=pm.NEWTON)
+        rg = pm.PMRun(c, n, box, 0.1, 0.3, 4, x, p, mode=pm.GR_POISSON)
+        rn.step(4)
+        rg.step(4)
+        d = rg.x - rn.x
+        d -= np.rint(d)
+        disp = rn.x - x
+        disp -= np.rint(disp)
+        rel = np.max(np.abs(d)) / np.max(np.abs(disp))
+        assert (rel < 1e-3) if close else (rel > 1e-3), (box, rel)
