@@ -16,7 +16,8 @@ W(n) = prod_j sinc^2(pi n_j / N) is the CIC window (deconvolution on by default,
 as in Pylians3, Sec. 4).  Bins are given by edges e_0 < ... < e_B in units of the
 fundamental mode k_f = 2 pi / L; a mode belongs to bin b when
 e_b^2 <= |n|^2 < e_{b+1}^2 (the last bin is closed), which both sides decide on
-the exact integer |n|^2.  The zero mode and modes with |n| > N/2 are excluded.
+the exact integer |n|^2.  The zero mode and modes with |n| > N/2 are excluded;
+the bispectrum also leaves out modes with a Nyquist component (reading).
 """
 import math
 
@@ -107,7 +108,10 @@ def bispectrum(delta, box, edges, M=None, deconvolve=True):
         dk = dk / W
     n2 = NX * NX + NY * NY + NZ * NZ
     b = assign_bins(n2, edges)
-    b = np.where((n2 > 0) & (n2 <= (n // 2)**2), b, -1)
+    # modes with a Nyquist component have no distinct partner at -n; they are left
+    # out of every triangle so that each I_b stays a real field
+    nyq = (np.abs(NX) == n // 2) | (np.abs(NY) == n // 2) | (np.abs(NZ) == n // 2)
+    b = np.where((n2 > 0) & (n2 <= (n // 2)**2) & ~nyq, b, -1)
     nb = len(edges) - 1
     inbin = b >= 0
     nmax = int(max(np.abs(NX[inbin]).max(), np.abs(NY[inbin]).max(), np.abs(NZ[inbin]).max()))

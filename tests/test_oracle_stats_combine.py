@@ -56,7 +56,8 @@ def _brute_bispectrum(delta, box, edges):
     NX, NY, NZ = np.meshgrid(f, f, f, indexing="ij")
     n2 = NX**2 + NY**2 + NZ**2
     b = stats.assign_bins(n2, edges)
-    b = np.where((n2 > 0) & (n2 <= (n // 2)**2), b, -1)
+    nyq = (np.abs(NX) == n // 2) | (np.abs(NY) == n // 2) | (np.abs(NZ) == n // 2)
+    b = np.where((n2 > 0) & (n2 <= (n // 2)**2) & ~nyq, b, -1)
     modes = [(int(NX[i]), int(NY[i]), int(NZ[i]), int(b[i]), dk[i]) for i in zip(*np.nonzero(b >= 0))]
     lookup = {(m[0], m[1], m[2]): (m[3], m[4]) for m in modes}
     nb = len(edges) - 1
