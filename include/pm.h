@@ -1,0 +1,215 @@
+/*
+ * pm.h -- C ABI of the GB300 (sm_103a) particle-mesh library for arXiv:2404.02783,
+ * "Simulating the Universe from the cosmological horizon to halo scales".
+ *
+ * The paper (Sec. 2) obtains a relativistic displacement field by running a
+ * particle-mesh (PM) code twice from the same initial phases, once in the
+ * Poisson gauge (general relativity, GR) and once in the Newtonian N-body gauge,
+ * subtracting the particle positions (Eq. xiGR) and adding the difference to a
+ * Newtonian run (Eq. combined); it then measures the matter power spectrum
+ * (Eq. powerspectrum) and bispectrum (Eq. bispectre) of the counting density
+ * (Sec. 4).  This library implements that data path on one GPU:
+ *
+ *   pm_ic_zeldovich            Zel'dovich initial conditions (Sec. 2 nLPT, n = 1; Sec. 3 IC at z = 50)
+ *   pm_step                    CIC deposit, r2c FFT, Green's function (Newtonian, or the
+ *                              linearised Poisson-gauge constraint), spectral gradient,
+ *                              c2r FFT, CIC interpolation + kick + drift (KDK in a)
+ *   pm_displacement_correction Eqs. xiGR and combined
+ *   pm_power / pm_bispectrum   Eqs. powerspectrum / bispectre on the CIC counting density
+ *
+ * Conventions shared by every entry point
+ * --------------------------------------
+ * Units: lengths in Mpc/h, wavenumbers in h/Mpc, H0 = 1 (velocities in 100 km/s).
+ * Positions are stored in units of the box side: PM_FP32_FIXED keeps uint32 ticks
+ * (2^32 ticks per side, periodic wrap is integer overflow), PM_FP64 keeps double
+ * fractions in [0, 1).  Momenta p = a^2 dx/dt / H0 are in Mpc/h (float or double).
+ * Particle arrays are structure-of-arrays: x[3][count], p[3][count], axis-major.
+ * Particle id = (ix np + iy) np + iz on the Lagrangian lattice q = (ix, iy, iz) L / np.
+ * Meshes are C-ordered real arrays [x][y][z] of side n (z fastest), float or double.
+ * Mesh nodes sit at cell centres (j + 1/2) L / n.
+ * Spectra use the library's transposed half-complex layout [kz][kx][ky] of shape
+ * (n/2 + 1, n, n), complex float2 / double2, unnormalised forward DFT
+ * F_n = sum_x f(x) exp(-2 pi i n.x / n); it is numpy's rfftn output permuted (2, 0, 1).
+ * Bin edges are given in units of the fundamental mode k_f = 2 pi / L; a mode with
+ * integer wavevector n is in bin b when e_b^2 <= |n|^2 < e_{b+1}^2 (last bin closed).
+ *
+ * Memory ownership: the library never allocates device memory.  Every device
+ * buffer (the context workspace, outputs, scratch) is owned by the caller, who
+ * sizes it with the *_size queries.  Host output arrays are caller-owned too.
+ * Streams: calls are asynchronous on the stream given at pm_init (or per call for
+ * the stateless operators) except pm_power and pm_bispectrum, which synchronise
+ * that stream before returning host results.
+ * Errors: every call returns a pm_status; pm_last_error() gives a static,
+ * thread-local message for the last failure.  A CUDA error inside a call is
+ * returned as PM_ERR_CUDA and leaves the context unusable (pm_destroy it).
+ * There is no CPU fallback: without an sm_100-family device the calls that launch
+ * kernels return PM_ERR_UNSUPPORTED.
+ */
+#ifndef PM_H
+#define PM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    PM_OK = 0,
+    PM_ERR_INVALID_ARG = 1,   /* bad size, null pointer, unsupported combination */
+    PM_ERR_CUDA = 2,          /* a CUDA runtime call or kernel launch failed */
+    PM_ERR_WORKSPACE = 3,     /* caller buffer too small or misaligned (256 B) */
+    PM_ERR_TIMEOUT = 4,       /* a bounded device wait gave up (reserved) */
+    PM_ERR_BOUNDS = 5,        /* a device-side index check failed */
+    PM_ERR_UNSUPPORTED = 6,   /* no suitable GPU */
+    PM_ERR_STATE = 7          /* call out of order (e.g. stepping past a_final) */
+} pm_status;
+
+enum { PM_NEWTON = 0, PM_GR_POISSON = 1 };
+enum { PM_FP32_FIXED = 0, PM_FP64 = 1 };
+
+/* Run configuration (Sec. 3 "Simulation setup"; sizes are powers of two). */
+typedef struct {
+    int np;            /* particle lattice side, 16..1024 */
+    int nmesh;         /* PM mesh side, 16..1024, a multiple of np */
+    double box;        /* comoving box side L in Mpc/h */
+    double omega_m;    /* Omega_m; Omega_Lambda = 1 - Omega_m (no radiation, Sec. 3) */
+    double omega_b;
+    double h;
+    double n_s;
+    double sigma8;     /* normalisation of the Eisenstein-Hu no-wiggle linear P(k) at z = 0 */
+    double a_init;     /* start of the uniform a-grid */
+    double a_final;    /* end of the uniform a-grid */
+    int n_steps;       /* number of KDK steps on the a-grid */
+    int mode;          /* PM_NEWTON or PM_GR_POISSON */
+    int precision;     /* PM_FP32_FIXED or PM_FP64 */
+    int n_lo;          /* GR only: modes with |n|^2 <= n_lo^2 are solved and stored in FP64 */
+} pm_config;
+
+typedef struct pm_ctx pm_ctx;   /* opaque host object owned by the library */
+
+/* ------------------------------------------------------------------ context */
+
+/* Bytes of device workspace a context needs for cfg (particles, meshes, spectra,
+ * GR history, tables).  Returns PM_ERR_INVALID_ARG for an unsupported cfg. */
+pm_status pm_workspace_size(const pm_config* cfg, size_t* bytes);
+
+/* Create a context on caller-owned device memory `workspace` (>= pm_workspace_size,
+ * 256-byte aligned, kept alive until pm_destroy).  `stream` is a cudaStream_t
+ * (NULL = legacy default).  Host-side FP64 tables (a-grid, kick/drift integrals,
+ * growth, Eisenstein-Hu amplitudes, FFT twiddles) are built here and copied into
+ * the workspace.  Particles are undefined until pm_ic_zeldovich or pm_set_particles. */
+pm_status pm_init(const pm_config* cfg, void* workspace, size_t bytes, void* stream, pm_ctx** out);
+
+/* Release the host object; the workspace stays the caller's.  NULL is accepted. */
+pm_status pm_destroy(pm_ctx* ctx);
+
+/* Zel'dovich initial conditions at a_init (Sec. 2: same random phases for every run;
+ * first-order LPT).  Phases: white_noise == NULL draws one unit complex Gaussian per
+ * wavevector from Philox4x32-10 (key = seed, counter = (nx, ny, nz, 0)) with a
+ * Box-Muller transform, so every resolution shares its common modes; otherwise
+ * white_noise is a device real field w[np][np][np] (ctx precision) of unit variance
+ * and the phases are FFT(w) / np^{3/2}.  paired != 0 flips the sign of every phase
+ * (the pairing of Sec. 4.2).  Modes with a Nyquist component and the zero mode are 0.
+ * Resets the step counter to 0 and the GR potential history. */
+pm_status pm_ic_zeldovich(pm_ctx* ctx, uint64_t seed, const void* white_noise, int paired);
+
+/* Advance n_steps KDK steps along the a-grid (one force evaluation per step; after
+ * the last step of the grid a closing half kick synchronises the momenta).
+ * PM_ERR_STATE when the grid would be overrun. */
+pm_status pm_step(pm_ctx* ctx, int n_steps);
+
+/* Device pointers to the context's particle arrays x[3][np^3], p[3][np^3]. */
+pm_status pm_particles(pm_ctx* ctx, void** x, void** p);
+
+/* Copy particles in (device-to-device, caller layout = context layout) and reset
+ * the step counter to 0 with synchronised momenta at a_init. */
+pm_status pm_set_particles(pm_ctx* ctx, const void* x, const void* p);
+
+/* Host view of the integrator (no device work): current step index, scale factor
+ * and whether the momenta are synchronised with the positions (1) or half a step
+ * behind (0). */
+pm_status pm_state(pm_ctx* ctx, int* step, double* a, int* synchronised);
+
+/* CIC counting density contrast delta = rho / rho_bar - 1 of the current particles
+ * on the context mesh (Sec. 4), written to the device mesh delta[n][n][n]. */
+pm_status pm_density(pm_ctx* ctx, void* delta);
+
+/* Code potential phi (Mpc/h)^2 of the current particles on the mesh, Newtonian:
+ * phi_k = -(3/2) Omega_m delta_k / k^2 (phi_0 = 0), written to phi[n][n][n].
+ * (The Poisson-gauge potential depends on the step history; see pm_step.) */
+pm_status pm_potential(pm_ctx* ctx, void* phi);
+
+/* Eqs. xiGR and combined: xi = x_GR - x_Newton per particle id (minimum image),
+ * interpolated trilinearly in Lagrangian coordinates when the target lattice is
+ * finer (target->np = r gr->np, r a power of two; integer weights over r^3 with
+ * round-half-even on ticks), then x_target += xi.  gr and newton must share np and
+ * precision with each other and precision with target.  xi_out (device, target
+ * layout: int32[3][np^3] ticks or double[3][np^3] fractions) may be NULL. */
+pm_status pm_displacement_correction(pm_ctx* target, const pm_ctx* gr, const pm_ctx* newton,
+                                     void* xi_out);
+
+/* Eq. powerspectrum: binned P(k) = (V/n^6) <|delta_k / W(k)|^2> over the full sphere
+ * of modes, W = prod_j sinc^2(pi n_j / n) when deconvolve != 0 (CIC window), the zero
+ * mode and |n| > n/2 excluded.  field == NULL: the CIC counting density of the
+ * context's particles; otherwise a device real mesh field[n][n][n] (ctx precision).
+ * field2 != NULL gives the cross spectrum Re<delta1 delta2*>.  k_out (mean |k| of the
+ * modes, h/Mpc), p_out ((Mpc/h)^3) and nmodes_out are host arrays of nbins
+ * (NaN where a bin holds no mode).  Synchronises.  nbins in 1..256. */
+pm_status pm_power(pm_ctx* ctx, const void* field, const void* field2, int nbins,
+                   const double* edges, int deconvolve,
+                   double* k_out, double* p_out, double* nmodes_out);
+
+/* Device scratch bytes pm_bispectrum needs for grid m and nbins bins. */
+pm_status pm_bispectrum_scratch_size(const pm_ctx* ctx, int m, int nbins, size_t* bytes);
+
+/* Eq. bispectre: B_ijl = (V^2/n^9) sum_{n1+n2+n3=0, n_a in bins i,j,l} delta_1 delta_2
+ * delta_3 / N_ijl for every triangle i <= j <= l (lexicographic order,
+ * nbins (nbins+1)(nbins+2)/6 entries), by the FFT identity on an m^3 grid:
+ * sum_x I_i I_j I_l with I_b = IFFT_m[delta 1_b].  Exact (no aliasing) when every
+ * mode of every bin has |n_i| < m/3; PM_ERR_INVALID_ARG otherwise.  field as in
+ * pm_power.  b_out and ntri_out are host arrays (NaN where N_ijl = 0).
+ * scratch is caller device memory of pm_bispectrum_scratch_size bytes.  Synchronises. */
+pm_status pm_bispectrum(pm_ctx* ctx, const void* field, int nbins, const double* edges,
+                        int m, int deconvolve, void* scratch, size_t scratch_bytes,
+                        double* b_out, double* ntri_out);
+
+/* ------------------------------------------------ stateless device operators
+ * Building blocks of pm_step exposed for testing and reuse; every pointer is a
+ * device pointer, sizes are element counts, `stream` is a cudaStream_t. */
+
+/* CIC deposit (Sec. 4 counting density): rho[n][n][n] += mass * CIC weights of
+ * count particles x[3][count] (ticks or fractions, per precision).  rho is NOT
+ * cleared first.  n a power of two in 8..1024. */
+pm_status pm_cic_deposit(const void* x, int64_t count, int precision, int n, double mass,
+                         void* rho, void* stream);
+
+/* CIC interpolation of a scalar mesh field[n][n][n] to count particles: out[count]. */
+pm_status pm_cic_interp(const void* field, int n, const void* x, int64_t count, int precision,
+                        void* out, void* stream);
+
+/* Base cell (ix n + iy) n + iz of each particle (keys_out, uint32[count]) and the
+ * stable counting-sort order of the particles by that key (order_out,
+ * uint32[count]; NULL to skip).  scratch: pm_cell_sort_scratch_size bytes. */
+pm_status pm_cell_sort_scratch_size(int64_t count, int n, size_t* bytes);
+pm_status pm_cell_sort(const void* x, int64_t count, int precision, int n,
+                       uint32_t* keys_out, uint32_t* order_out,
+                       void* scratch, size_t scratch_bytes, void* stream);
+
+/* 3D real-to-complex FFT of real[n][n][n] into spec (layout above), unnormalised. */
+pm_status pm_fft_r2c(const void* real, void* spec, int n, int precision, void* stream);
+
+/* Inverse: complex-to-real of spec (overwritten) into real[n][n][n], unnormalised
+ * (sum over modes of F_n exp(+2 pi i n.x / n)). */
+pm_status pm_fft_c2r(void* spec, void* real, int n, int precision, void* stream);
+
+/* Library version string and last error message. */
+const char* pm_version(void);
+const char* pm_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PM_H */

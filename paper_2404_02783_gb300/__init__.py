@@ -1,0 +1,321 @@
+"""Python binding of libpm.so, the sm_103a particle-mesh library of arXiv:2404.02783.
+
+Argument marshalling only: every step of the path runs in the CUDA kernels behind
+``include/pm.h``.  PyTorch supplies device memory (workspaces, outputs) and the
+current CUDA stream.  The functions keep the C names (``pm_init``, ``pm_step``, ...)
+and raise :class:`PMError` on a non-zero status.  There is no CPU fallback: if
+``libpm.so`` is missing, :func:`lib` raises instead of computing anything.
+
+:class:`PMRun` bundles a configuration, its torch-allocated workspace and the
+context handle for the common case of one simulation.
+"""
+import ctypes
+import math
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libpm.so")
+
+PM_OK = 0
+PM_NEWTON, PM_GR_POISSON = 0, 1
+PM_FP32_FIXED, PM_FP64 = 0, 1
+_STATUS = {0: "PM_OK", 1: "PM_ERR_INVALID_ARG", 2: "PM_ERR_CUDA", 3: "PM_ERR_WORKSPACE", 4: "PM_ERR_TIMEOUT",
+           5: "PM_ERR_BOUNDS", 6: "PM_ERR_UNSUPPORTED", 7: "PM_ERR_STATE"}
+
+# every entry point declared in include/pm.h
+EXPORTS = ("pm_workspace_size", "pm_init", "pm_destroy", "pm_ic_zeldovich", "pm_step", "pm_particles",
+           "pm_set_particles", "pm_state", "pm_density", "pm_potential", "pm_displacement_correction", "pm_power",
+           "pm_bispectrum_scratch_size", "pm_bispectrum", "pm_cic_deposit", "pm_cic_interp",
+           "pm_cell_sort_scratch_size", "pm_cell_sort", "pm_fft_r2c", "pm_fft_c2r", "pm_version", "pm_last_error")
+
+
+class PMError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__(f"{_STATUS.get(status, status)}: {message}")
+        self.status = status
+
+
+class PMConfig(ctypes.Structure):
+    """Mirror of ``pm_config`` (include/pm.h)."""
+    _fields_ = [("np", ctypes.c_int), ("nmesh", ctypes.c_int), ("box", ctypes.c_double),
+                ("omega_m", ctypes.c_double), ("omega_b", ctypes.c_double), ("h", ctypes.c_double),
+                ("n_s", ctypes.c_double), ("sigma8", ctypes.c_double), ("a_init", ctypes.c_double),
+                ("a_final", ctypes.c_double), ("n_steps", ctypes.c_int), ("mode", ctypes.c_int),
+                ("precision", ctypes.c_int), ("n_lo", ctypes.c_int)]
+
+
+def make_config(np_side, nmesh, box, a_init, a_final, n_steps, mode=PM_NEWTON, precision=PM_FP32_FIXED,
+                omega_m=0.31, omega_b=0.049, h=0.67, n_s=0.965, sigma8=0.81, n_lo=0):
+    return PMConfig(np_side, nmesh, box, omega_m, omega_b, h, n_s, sigma8, a_init, a_final, n_steps, mode,
+                    precision, n_lo)
+
+
+_lib = None
+
+
+def lib():
+    """Load libpm.so from the package directory (built by ``build.py``)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: build it with __graft_entry__.build() "
+                           "(nvcc, sm_103a); there is no CPU fallback")
+    L = ctypes.CDLL(LIB_PATH)
+    vp, sz, i, d, i64, u64 = (ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int, ctypes.c_double, ctypes.c_int64,
+                              ctypes.c_uint64)
+    pd = ctypes.POINTER(ctypes.c_double)
+    cfgp = ctypes.POINTER(PMConfig)
+    sig = {
+        "pm_workspace_size": (cfgp, ctypes.POINTER(sz)),
+        "pm_init": (cfgp, vp, sz, vp, ctypes.POINTER(vp)),
+        "pm_destroy": (vp,),
+        "pm_ic_zeldovich": (vp, u64, vp, i),
+        "pm_step": (vp, i),
+        "pm_particles": (vp, ctypes.POINTER(vp), ctypes.POINTER(vp)),
+        "pm_set_particles": (vp, vp, vp),
+        "pm_state": (vp, ctypes.POINTER(i), pd, ctypes.POINTER(i)),
+        "pm_density": (vp, vp),
+        "pm_potential": (vp, vp),
+        "pm_displacement_correction": (vp, vp, vp, vp),
+        "pm_power": (vp, vp, vp, i, pd, i, pd, pd, pd),
+        "pm_bispectrum_scratch_size": (vp, i, i, ctypes.POINTER(sz)),
+        "pm_bispectrum": (vp, vp, i, pd, i, i, vp, sz, pd, pd),
+        "pm_cic_deposit": (vp, i64, i, i, d, vp, vp),
+        "pm_cic_interp": (vp, i, vp, i64, i, vp, vp),
+        "pm_cell_sort_scratch_size": (i64, i, ctypes.POINTER(sz)),
+        "pm_cell_sort": (vp, i64, i, i, vp, vp, vp, sz, vp),
+        "pm_fft_r2c": (vp, vp, i, i, vp),
+        "pm_fft_c2r": (vp, vp, i, i, vp),
+    }
+    for name, args in sig.items():
+        fn = getattr(L, name)
+        fn.argtypes = list(args)
+        fn.restype = ctypes.c_int
+    for name in ("pm_version", "pm_last_error"):
+        getattr(L, name).restype = ctypes.c_char_p
+        getattr(L, name).argtypes = []
+    _lib = L
+    return L
+
+
+def _check(status):
+    if status != PM_OK:
+        raise PMError(status, lib().pm_last_error().decode())
+
+
+def _ptr(t):
+    """Device (or host) address of a tensor/array, or None."""
+    if t is None:
+        return None
+    if hasattr(t, "data_ptr"):
+        return ctypes.c_void_p(t.data_ptr())
+    if isinstance(t, np.ndarray):
+        return ctypes.c_void_p(t.ctypes.data)
+    return ctypes.c_void_p(int(t))
+
+
+def _dptr(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _stream(stream=None):
+    import torch
+    s = torch.cuda.current_stream() if stream is None else stream
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+# --------------------------------------------------------------------------- C names
+def pm_version():
+    return lib().pm_version().decode()
+
+
+def pm_workspace_size(cfg):
+    out = ctypes.c_size_t()
+    _check(lib().pm_workspace_size(ctypes.byref(cfg), ctypes.byref(out)))
+    return out.value
+
+
+def pm_init(cfg, workspace, stream=None):
+    h = ctypes.c_void_p()
+    _check(lib().pm_init(ctypes.byref(cfg), _ptr(workspace), workspace.numel() * workspace.element_size(),
+                         _stream(stream), ctypes.byref(h)))
+    return h
+
+
+def pm_destroy(ctx):
+    _check(lib().pm_destroy(ctx))
+
+
+def pm_ic_zeldovich(ctx, seed, white_noise=None, paired=False):
+    _check(lib().pm_ic_zeldovich(ctx, ctypes.c_uint64(seed), _ptr(white_noise), int(bool(paired))))
+
+
+def pm_step(ctx, n_steps=1):
+    _check(lib().pm_step(ctx, int(n_steps)))
+
+
+def pm_particles(ctx):
+    x, p = ctypes.c_void_p(), ctypes.c_void_p()
+    _check(lib().pm_particles(ctx, ctypes.byref(x), ctypes.byref(p)))
+    return x.value, p.value
+
+
+def pm_set_particles(ctx, x, p):
+    _check(lib().pm_set_particles(ctx, _ptr(x), _ptr(p)))
+
+
+def pm_state(ctx):
+    s, a, y = ctypes.c_int(), ctypes.c_double(), ctypes.c_int()
+    _check(lib().pm_state(ctx, ctypes.byref(s), ctypes.byref(a), ctypes.byref(y)))
+    return s.value, a.value, bool(y.value)
+
+
+def pm_density(ctx, out):
+    _check(lib().pm_density(ctx, _ptr(out)))
+
+
+def pm_potential(ctx, out):
+    _check(lib().pm_potential(ctx, _ptr(out)))
+
+
+def pm_displacement_correction(target, gr, newton, xi_out=None):
+    _check(lib().pm_displacement_correction(target, gr, newton, _ptr(xi_out)))
+
+
+def pm_power(ctx, edges, field=None, field2=None, deconvolve=True):
+    edges = np.ascontiguousarray(edges, dtype=np.float64)
+    nb = len(edges) - 1
+    k, p, nm = np.empty(nb), np.empty(nb), np.empty(nb)
+    _check(lib().pm_power(ctx, _ptr(field), _ptr(field2), nb, _dptr(edges), int(bool(deconvolve)), _dptr(k),
+                          _dptr(p), _dptr(nm)))
+    return k, p, nm
+
+
+def pm_bispectrum_scratch_size(ctx, m, nbins):
+    out = ctypes.c_size_t()
+    _check(lib().pm_bispectrum_scratch_size(ctx, int(m), int(nbins), ctypes.byref(out)))
+    return out.value
+
+
+def pm_bispectrum(ctx, edges, m, scratch, field=None, deconvolve=True):
+    edges = np.ascontiguousarray(edges, dtype=np.float64)
+    nb = len(edges) - 1
+    nt = nb * (nb + 1) * (nb + 2) // 6
+    b, c = np.empty(nt), np.empty(nt)
+    _check(lib().pm_bispectrum(ctx, _ptr(field), nb, _dptr(edges), int(m), int(bool(deconvolve)), _ptr(scratch),
+                               scratch.numel() * scratch.element_size(), _dptr(b), _dptr(c)))
+    return b, c
+
+
+def pm_cic_deposit(x, count, precision, n, mass, rho, stream=None):
+    _check(lib().pm_cic_deposit(_ptr(x), int(count), precision, int(n), float(mass), _ptr(rho), _stream(stream)))
+
+
+def pm_cic_interp(field, n, x, count, precision, out, stream=None):
+    _check(lib().pm_cic_interp(_ptr(field), int(n), _ptr(x), int(count), precision, _ptr(out), _stream(stream)))
+
+
+def pm_cell_sort_scratch_size(count, n):
+    out = ctypes.c_size_t()
+    _check(lib().pm_cell_sort_scratch_size(int(count), int(n), ctypes.byref(out)))
+    return out.value
+
+
+def pm_cell_sort(x, count, precision, n, keys, order, scratch, stream=None):
+    nbytes = 0 if scratch is None else scratch.numel() * scratch.element_size()
+    _check(lib().pm_cell_sort(_ptr(x), int(count), precision, int(n), _ptr(keys), _ptr(order), _ptr(scratch), nbytes,
+                              _stream(stream)))
+
+
+def pm_fft_r2c(real, spec, n, precision, stream=None):
+    _check(lib().pm_fft_r2c(_ptr(real), _ptr(spec), int(n), precision, _stream(stream)))
+
+
+def pm_fft_c2r(spec, real, n, precision, stream=None):
+    _check(lib().pm_fft_c2r(_ptr(spec), _ptr(real), int(n), precision, _stream(stream)))
+
+
+# --------------------------------------------------------------------------- convenience
+def log_edges(nbins, lo, hi):
+    """Logarithmic bin edges (any unit; pass them in units of k_f to the estimators)."""
+    return lo * (hi / lo)**(np.arange(nbins + 1) / nbins)
+
+
+class PMRun:
+    """One simulation: configuration + torch workspace on the current device + context."""
+
+    def __init__(self, cfg, device="cuda", stream=None):
+        import torch
+        self.cfg = cfg
+        self.device = torch.device(device)
+        nbytes = pm_workspace_size(cfg)
+        self.workspace = torch.empty(nbytes + 256, dtype=torch.uint8, device=self.device)
+        off = (-self.workspace.data_ptr()) % 256
+        self._ws = self.workspace[off:off + nbytes]
+        self.stream = stream
+        self.ctx = pm_init(cfg, self._ws, stream)
+        self.fp64 = cfg.precision == PM_FP64
+        self.rdtype = torch.float64 if self.fp64 else torch.float32
+        self.count = cfg.np**3
+
+    def __del__(self):
+        ctx = getattr(self, "ctx", None)
+        if ctx is not None and _lib is not None:
+            _lib.pm_destroy(ctx)
+            self.ctx = None
+
+    def ic(self, seed=0, white_noise=None, paired=False):
+        pm_ic_zeldovich(self.ctx, seed, white_noise, paired)
+
+    def step(self, n=1):
+        pm_step(self.ctx, n)
+
+    def particles(self):
+        """(x, p) torch views of the context's particle arrays, shape (3, np^3)."""
+        import torch
+        xp, pp = pm_particles(self.ctx)
+        nbytes = 3 * self.count * (8 if self.fp64 else 4)
+        xdt = torch.float64 if self.fp64 else torch.int32
+        x = _view(self._ws, xp, nbytes).view(xdt).view(3, self.count)
+        p = _view(self._ws, pp, nbytes).view(self.rdtype).view(3, self.count)
+        return x, p
+
+    def density(self):
+        import torch
+        n = self.cfg.nmesh
+        out = torch.empty((n, n, n), dtype=self.rdtype, device=self.device)
+        pm_density(self.ctx, out)
+        return out
+
+    def potential(self):
+        import torch
+        n = self.cfg.nmesh
+        out = torch.empty((n, n, n), dtype=self.rdtype, device=self.device)
+        pm_potential(self.ctx, out)
+        return out
+
+    def power(self, edges, field=None, field2=None, deconvolve=True):
+        return pm_power(self.ctx, edges, field, field2, deconvolve)
+
+    def bispectrum(self, edges, m, field=None, deconvolve=True):
+        import torch
+        nb = len(edges) - 1
+        scratch = torch.empty(pm_bispectrum_scratch_size(self.ctx, m, nb) + 256, dtype=torch.uint8,
+                              device=self.device)
+        off = (-scratch.data_ptr()) % 256
+        return pm_bispectrum(self.ctx, edges, m, scratch[off:], field, deconvolve)
+
+    def state(self):
+        return pm_state(self.ctx)
+
+    @property
+    def kf(self):
+        return 2 * math.pi / self.cfg.box
+
+
+def _view(ws, ptr, nbytes):
+    off = ptr - ws.data_ptr()
+    return ws[off:off + nbytes]

@@ -1,0 +1,689 @@
+// C ABI of the particle-mesh library (include/pm.h): argument checks, workspace
+// carving, host FP64 tables and the orchestration of the device passes.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "host_cosmo.h"
+#include "internal.h"
+#include "particles.h"
+
+using namespace pm;
+
+namespace {
+
+thread_local std::string g_err;
+
+pm_status fail(pm_status s, const std::string& msg) {
+    g_err = msg;
+    return s;
+}
+
+#define PM_CK(expr)                                                                             \
+    do {                                                                                        \
+        cudaError_t e_ = (expr);                                                                \
+        if (e_ != cudaSuccess) return fail(PM_ERR_CUDA, std::string(#expr) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+#define PM_TRY(expr)                      \
+    do {                                  \
+        pm_status s_ = (expr);            \
+        if (s_ != PM_OK) return s_;       \
+    } while (0)
+
+bool pow2(int64_t n) { return n > 0 && (n & (n - 1)) == 0; }
+size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
+
+pm_status check_device() {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(PM_ERR_UNSUPPORTED, "no CUDA device");
+    }
+    int major = 0;
+    if (cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev) != cudaSuccess || major != 10) {
+        cudaGetLastError();
+        return fail(PM_ERR_UNSUPPORTED, "needs a Blackwell (sm_10x) GPU; this library is built for sm_103a");
+    }
+    PM_CK(ensure_device_tables());
+    return PM_OK;
+}
+
+struct Layout {
+    size_t x = 0, p = 0, rho = 0, spec[3] = {0, 0, 0}, force[3] = {0, 0, 0};
+    size_t phi_old = 0, island = 0, amp = 0, bin_of = 0, wtab = 0, acc = 0, total = 0;
+    bool gr = false, has_island = false;
+};
+
+constexpr int kMaxBins = 256;
+
+pm_status validate(const pm_config* c) {
+    if (!c) return fail(PM_ERR_INVALID_ARG, "null config");
+    if (!pow2(c->np) || c->np < 16 || c->np > 1024) return fail(PM_ERR_INVALID_ARG, "np must be a power of two in 16..1024");
+    if (!pow2(c->nmesh) || c->nmesh < 16 || c->nmesh > 1024)
+        return fail(PM_ERR_INVALID_ARG, "nmesh must be a power of two in 16..1024");
+    if (c->nmesh % c->np) return fail(PM_ERR_INVALID_ARG, "nmesh must be a multiple of np");
+    if (!(c->box > 0)) return fail(PM_ERR_INVALID_ARG, "box must be positive");
+    if (!(c->omega_m > 0 && c->omega_m <= 1 && c->h > 0 && c->sigma8 > 0 && c->omega_b >= 0 && c->omega_b < c->omega_m))
+        return fail(PM_ERR_INVALID_ARG, "bad cosmological parameters");
+    if (!(c->a_init > 0 && c->a_final > c->a_init)) return fail(PM_ERR_INVALID_ARG, "need 0 < a_init < a_final");
+    if (c->n_steps < 1) return fail(PM_ERR_INVALID_ARG, "n_steps must be >= 1");
+    if (c->mode != PM_NEWTON && c->mode != PM_GR_POISSON) return fail(PM_ERR_INVALID_ARG, "bad mode");
+    if (c->precision != PM_FP32_FIXED && c->precision != PM_FP64) return fail(PM_ERR_INVALID_ARG, "bad precision");
+    if (c->n_lo < 0 || 2 * c->n_lo >= c->nmesh) return fail(PM_ERR_INVALID_ARG, "n_lo must be in [0, nmesh/2)");
+    return PM_OK;
+}
+
+Layout plan(const pm_config& c) {
+    Layout L;
+    const size_t sT = c.precision == PM_FP64 ? 8 : 4, sC = 2 * sT;
+    const size_t np3 = (size_t)c.np * c.np * c.np;
+    const size_t n = c.nmesh, n3 = n * n * n, nspec = (n / 2 + 1) * n * n;
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        const size_t o = off;
+        off = align256(off + bytes);
+        return o;
+    };
+    L.x = take(3 * np3 * sT);
+    L.p = take(3 * np3 * sT);
+    L.rho = take(n3 * sT);
+    for (int j = 0; j < 3; ++j) L.spec[j] = take(nspec * sC);
+    for (int j = 0; j < 3; ++j) L.force[j] = take(n3 * sT);
+    L.gr = c.mode == PM_GR_POISSON;
+    if (L.gr) L.phi_old = take(nspec * sC);
+    L.has_island = L.gr && c.n_lo > 0;
+    if (L.has_island) L.island = take((size_t)(c.n_lo + 1) * (2 * c.n_lo + 1) * (2 * c.n_lo + 1) * 16);
+    L.amp = take((3 * (size_t)(c.np / 2) * (c.np / 2) + 1) * 8);
+    L.bin_of = take((3 * (n / 2) * (n / 2) + 1) * 2);
+    L.wtab = take((n / 2 + 1) * 8);
+    L.acc = take(3 * kMaxBins * 8);
+    L.total = off;
+    return L;
+}
+
+}  // namespace
+
+struct pm_ctx {
+    pm_config cfg;
+    Layout L;
+    unsigned char* ws = nullptr;
+    cudaStream_t st = nullptr;
+    pmhost::Cosmo cosmo;
+    int n = 0, np = 0;
+    int64_t np3 = 0;
+    double kf = 0.0;
+    int step = 0;
+    bool synced = true;
+    bool have_phi = false;
+    double a_last = 0.0;
+    void* at(size_t off) const { return ws + off; }
+    double a_grid(int i) const { return cfg.a_init + ((cfg.a_final - cfg.a_init) * i) / cfg.n_steps; }
+    bool fp64() const { return cfg.precision == PM_FP64; }
+    size_t sT() const { return fp64() ? 8 : 4; }
+};
+
+namespace {
+
+template <typename T>
+pm_status forward_to_y(pm_ctx* c, const void* real, void* spec, int n) {
+    PM_CK(z_r2c<T>((const T*)real, (cplx<T>*)spec, n, 1, c->st));
+    PM_CK((y_rows<T, false>((cplx<T>*)spec, (int64_t)(n / 2 + 1) * n, n, c->st)));
+    return PM_OK;
+}
+
+// Counting density of the context's particles (mass (n/np)^3 per particle) on rho.
+pm_status deposit_particles(pm_ctx* c, void* rho) {
+    PM_CK(cudaMemsetAsync(rho, 0, c->sT() * (size_t)c->n * c->n * c->n, c->st));
+    const double mass = std::pow((double)c->n / c->np, 3);
+    PM_CK(deposit(c->at(c->L.x), c->np3, c->cfg.precision, c->n, mass, rho, c->st));
+    return PM_OK;
+}
+
+// Force meshes g = -grad phi of the current particles at scale factor a.
+template <typename T>
+pm_status compute_forces_t(pm_ctx* c, double a) {
+    const int n = c->n;
+    void* rho = c->at(c->L.rho);
+    PM_TRY(deposit_particles(c, rho));
+    cplx<T>* s0 = (cplx<T>*)c->at(c->L.spec[0]);
+    cplx<T>* s1 = (cplx<T>*)c->at(c->L.spec[1]);
+    cplx<T>* s2 = (cplx<T>*)c->at(c->L.spec[2]);
+    PM_TRY(forward_to_y<T>(c, rho, s0, n));
+    SpecOp op;
+    op.kf = c->kf;
+    op.fwd = 1;
+    const double n3 = (double)n * n * n;
+    if (c->cfg.mode == PM_NEWTON) {
+        op.kind = OP_NEWTON;
+        op.coef = -1.5 * c->cfg.omega_m / (c->kf * c->kf * n3);
+    } else {
+        op.kind = OP_GR;
+        op.calH = pmhost::conformal_hubble(c->cosmo, a);
+        op.omm_a = pmhost::omega_m_a(c->cosmo, a);
+        op.first = c->have_phi ? 0 : 1;
+        op.inv_dtau = c->have_phi ? 1.0 / (pmhost::kCLight * pmhost::kick_integral(c->cosmo, c->a_last, a)) : 0.0;
+        op.ac2_over_n3 = a * pmhost::kCLight * pmhost::kCLight / n3;
+        op.n_lo = c->L.has_island ? c->cfg.n_lo : 0;
+        op.phi_old = c->at(c->L.phi_old);
+        op.island = c->L.has_island ? (double2*)c->at(c->L.island) : nullptr;
+    }
+    PM_CK(x_cols<T>(s0, s1, n / 2 + 1, n, op, c->st));
+    PM_CK(y_rows_grad3<T>(s0, s1, s2, (int64_t)(n / 2 + 1) * n, n, c->kf, c->st));
+    const cplx<T>* in[3] = {s1, s2, s0};
+    T* out[3] = {(T*)c->at(c->L.force[0]), (T*)c->at(c->L.force[1]), (T*)c->at(c->L.force[2])};
+    PM_CK(z_c2r<T>(in, out, 3, n, 1, 4u, c->kf, c->st));
+    if (c->cfg.mode == PM_GR_POISSON) {
+        c->have_phi = true;
+        c->a_last = a;
+    }
+    return PM_OK;
+}
+
+pm_status compute_forces(pm_ctx* c, double a) {
+    return c->fp64() ? compute_forces_t<double>(c, a) : compute_forces_t<float>(c, a);
+}
+
+pm_status kick_drift(pm_ctx* c, double kick, double drift) {
+    void* g[3] = {c->at(c->L.force[0]), c->at(c->L.force[1]), c->at(c->L.force[2])};
+    PM_CK(interp_kick_drift(c->at(c->L.x), c->at(c->L.p), c->np3, c->cfg.precision, c->n, g, kick, drift,
+                            c->cfg.box, c->st));
+    return PM_OK;
+}
+
+void build_bin_table(int n, int nbins, const double* edges, std::vector<int16_t>& tab) {
+    const int64_t nmax = 3 * (int64_t)(n / 2) * (n / 2);
+    tab.assign(nmax + 1, (int16_t)-1);
+    std::vector<double> e2(nbins + 1);
+    for (int b = 0; b <= nbins; ++b) e2[b] = edges[b] * edges[b];
+    for (int64_t n2 = 0; n2 <= nmax; ++n2) {
+        const double v = (double)n2;
+        int b = -1;
+        for (int q = nbins; q >= 0; --q)
+            if (e2[q] <= v) {
+                b = q;
+                break;
+            }
+        if (v == e2[nbins]) b = nbins - 1;
+        tab[n2] = (b >= 0 && b < nbins) ? (int16_t)b : (int16_t)-1;
+    }
+}
+
+pm_status check_edges(int nbins, const double* edges) {
+    if (nbins < 1 || nbins > kMaxBins || !edges) return fail(PM_ERR_INVALID_ARG, "need 1..256 bins and edges");
+    for (int b = 0; b < nbins; ++b)
+        if (!(edges[b] >= 0 && edges[b + 1] > edges[b])) return fail(PM_ERR_INVALID_ARG, "edges must increase");
+    return PM_OK;
+}
+
+template <typename T>
+pm_status power_t(pm_ctx* c, const void* field, const void* field2, int nbins, const double* edges, int deconv,
+                  double* k_out, double* p_out, double* nmodes_out) {
+    const int n = c->n;
+    const void* f1 = field;
+    if (!f1) {
+        PM_TRY(deposit_particles(c, c->at(c->L.rho)));
+        f1 = c->at(c->L.rho);
+    }
+    void* s0 = c->at(c->L.spec[0]);
+    void* s1 = c->at(c->L.spec[1]);
+    PM_TRY(forward_to_y<T>(c, f1, s0, n));
+    if (field2) PM_TRY(forward_to_y<T>(c, field2, s1, n));
+    std::vector<int16_t> tab;
+    build_bin_table(n, nbins, edges, tab);
+    PM_CK(cudaMemcpyAsync(c->at(c->L.bin_of), tab.data(), tab.size() * 2, cudaMemcpyHostToDevice, c->st));
+    double* acc = (double*)c->at(c->L.acc);
+    PM_CK(cudaMemsetAsync(acc, 0, sizeof(double) * 3 * nbins, c->st));
+    SpecOp op;
+    op.kind = OP_BIN;
+    op.fwd = 1;
+    op.kf = c->kf;
+    op.bin_of = (const int16_t*)c->at(c->L.bin_of);
+    op.wtab = (const double*)c->at(c->L.wtab);
+    op.acc = acc;
+    op.nbins = nbins;
+    op.deconv = deconv ? 1 : 0;
+    op.in2 = field2 ? s1 : nullptr;
+    PM_CK(x_cols<T>((cplx<T>*)s0, nullptr, n / 2 + 1, n, op, c->st));
+    std::vector<double> h(3 * nbins);
+    PM_CK(cudaMemcpyAsync(h.data(), acc, sizeof(double) * 3 * nbins, cudaMemcpyDeviceToHost, c->st));
+    PM_CK(cudaStreamSynchronize(c->st));
+    const double V = c->cfg.box * c->cfg.box * c->cfg.box;
+    const double n6 = std::pow((double)n, 6);
+    for (int b = 0; b < nbins; ++b) {
+        const double w = h[b];
+        if (nmodes_out) nmodes_out[b] = w;
+        if (w > 0) {
+            if (p_out) p_out[b] = V / n6 * h[nbins + b] / w;
+            if (k_out) k_out[b] = h[2 * nbins + b] / w;
+        } else {
+            if (p_out) p_out[b] = NAN;
+            if (k_out) k_out[b] = NAN;
+        }
+    }
+    return PM_OK;
+}
+
+struct BkLayout {
+    size_t specs, fields, tri, accS, accC, total;
+    int ntri;
+};
+BkLayout bk_plan(int sT, int m, int nbins) {
+    BkLayout B;
+    const size_t per_spec = (size_t)(m / 2 + 1) * m * m * 2 * sT;
+    const size_t per_field = (size_t)m * m * m * sT;
+    B.ntri = nbins * (nbins + 1) * (nbins + 2) / 6;
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        const size_t o = off;
+        off = align256(off + bytes);
+        return o;
+    };
+    B.specs = take(2 * (size_t)nbins * per_spec);
+    B.fields = take(2 * (size_t)nbins * per_field);
+    B.tri = take(sizeof(int4) * (size_t)B.ntri);
+    B.accS = take(sizeof(double) * (size_t)B.ntri);
+    B.accC = take(sizeof(double) * (size_t)B.ntri);
+    B.total = off;
+    return B;
+}
+
+template <typename T>
+pm_status bispectrum_t(pm_ctx* c, const void* field, int nbins, const double* edges, int m, int deconv,
+                       unsigned char* scratch, const BkLayout& B, double* b_out, double* ntri_out) {
+    const int n = c->n;
+    const void* f1 = field;
+    if (!f1) {
+        PM_TRY(deposit_particles(c, c->at(c->L.rho)));
+        f1 = c->at(c->L.rho);
+    }
+    cplx<T>* s0 = (cplx<T>*)c->at(c->L.spec[0]);
+    PM_TRY(forward_to_y<T>(c, f1, s0, n));
+    SpecOp fw;
+    fw.kind = OP_FWD_STORE;
+    fw.fwd = 1;
+    PM_CK(x_cols<T>(s0, nullptr, n / 2 + 1, n, fw, c->st));
+    std::vector<int16_t> tab;
+    build_bin_table(n, nbins, edges, tab);
+    PM_CK(cudaMemcpyAsync(c->at(c->L.bin_of), tab.data(), tab.size() * 2, cudaMemcpyHostToDevice, c->st));
+    cplx<T>* specs = (cplx<T>*)(scratch + B.specs);
+    T* fields = (T*)(scratch + B.fields);
+    PM_CK(bk_masks<T>(s0, n, specs, m, nbins, (const int16_t*)c->at(c->L.bin_of), (const double*)c->at(c->L.wtab),
+                      deconv ? 1 : 0, c->st));
+    const int nspec = 2 * nbins;
+    SpecOp inv;
+    inv.kind = OP_INV;
+    inv.fwd = 0;
+    PM_CK(x_cols<T>(specs, nullptr, nspec * (m / 2 + 1), m, inv, c->st));
+    PM_CK((y_rows<T, true>(specs, (int64_t)nspec * (m / 2 + 1) * m, m, c->st)));
+    const cplx<T>* in[1] = {specs};
+    T* out[1] = {fields};
+    PM_CK(z_c2r<T>(in, out, 1, m, nspec, 0u, 0.0, c->st));
+    std::vector<int4> tri;
+    tri.reserve(B.ntri);
+    for (int i = 0; i < nbins; ++i)
+        for (int j = i; j < nbins; ++j)
+            for (int l = j; l < nbins; ++l) tri.push_back(make_int4(i, j, l, 0));
+    int4* dtri = (int4*)(scratch + B.tri);
+    double* accS = (double*)(scratch + B.accS);
+    double* accC = (double*)(scratch + B.accC);
+    PM_CK(cudaMemcpyAsync(dtri, tri.data(), sizeof(int4) * tri.size(), cudaMemcpyHostToDevice, c->st));
+    PM_CK(cudaMemsetAsync(accS, 0, sizeof(double) * B.ntri, c->st));
+    PM_CK(cudaMemsetAsync(accC, 0, sizeof(double) * B.ntri, c->st));
+    PM_CK(bk_triangles<T>(fields, m, nbins, dtri, B.ntri, accS, accC, c->st));
+    std::vector<double> hs(B.ntri), hc(B.ntri);
+    PM_CK(cudaMemcpyAsync(hs.data(), accS, sizeof(double) * B.ntri, cudaMemcpyDeviceToHost, c->st));
+    PM_CK(cudaMemcpyAsync(hc.data(), accC, sizeof(double) * B.ntri, cudaMemcpyDeviceToHost, c->st));
+    PM_CK(cudaStreamSynchronize(c->st));
+    const double V = c->cfg.box * c->cfg.box * c->cfg.box;
+    const double n9 = std::pow((double)n, 9);
+    const double m3 = (double)m * m * m;
+    for (int t = 0; t < B.ntri; ++t) {
+        const double cnt = hc[t] / m3;
+        if (ntri_out) ntri_out[t] = cnt;
+        if (b_out) b_out[t] = (cnt > 0.5) ? V * V / n9 * hs[t] / hc[t] : NAN;
+    }
+    return PM_OK;
+}
+
+}  // namespace
+
+// ====================================================================== C ABI
+extern "C" {
+
+const char* pm_version(void) { return "pm-gb300 0.1 (sm_103a)"; }
+
+const char* pm_last_error(void) { return g_err.c_str(); }
+
+pm_status pm_workspace_size(const pm_config* cfg, size_t* bytes) {
+    PM_TRY(validate(cfg));
+    if (!bytes) return fail(PM_ERR_INVALID_ARG, "null bytes");
+    *bytes = plan(*cfg).total;
+    return PM_OK;
+}
+
+pm_status pm_init(const pm_config* cfg, void* workspace, size_t bytes, void* stream, pm_ctx** out) {
+    PM_TRY(validate(cfg));
+    if (!out) return fail(PM_ERR_INVALID_ARG, "null out");
+    *out = nullptr;
+    const Layout L = plan(*cfg);
+    if (!workspace || bytes < L.total) return fail(PM_ERR_WORKSPACE, "workspace smaller than pm_workspace_size");
+    if ((uintptr_t)workspace % 256) return fail(PM_ERR_WORKSPACE, "workspace must be 256-byte aligned");
+    PM_TRY(check_device());
+    pm_ctx* c = new pm_ctx();
+    c->cfg = *cfg;
+    c->L = L;
+    c->ws = (unsigned char*)workspace;
+    c->st = (cudaStream_t)stream;
+    c->n = cfg->nmesh;
+    c->np = cfg->np;
+    c->np3 = (int64_t)cfg->np * cfg->np * cfg->np;
+    c->kf = 2.0 * M_PI / cfg->box;
+    c->cosmo.omega_m = cfg->omega_m;
+    c->cosmo.omega_b = cfg->omega_b;
+    c->cosmo.h = cfg->h;
+    c->cosmo.n_s = cfg->n_s;
+    c->cosmo.sigma8 = cfg->sigma8;
+    pmhost::normalise_sigma8(c->cosmo);
+    // sqrt(P(k)/V) per integer |n|^2 on the particle lattice, and the CIC window per |n_j|
+    const int hp = cfg->np / 2;
+    std::vector<double> amp(3 * (size_t)hp * hp + 1, 0.0);
+    const double V = cfg->box * cfg->box * cfg->box;
+    for (size_t n2 = 1; n2 < amp.size(); ++n2)
+        amp[n2] = std::sqrt(pmhost::power_linear(c->cosmo, c->kf * std::sqrt((double)n2)) / V);
+    std::vector<double> wtab(c->n / 2 + 1);
+    for (int mq = 0; mq <= c->n / 2; ++mq) {
+        const double x = M_PI * mq / c->n;
+        const double s = (mq == 0) ? 1.0 : std::sin(x) / x;
+        wtab[mq] = s * s;
+    }
+    cudaError_t e = cudaMemcpyAsync(c->at(L.amp), amp.data(), amp.size() * 8, cudaMemcpyHostToDevice, c->st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(c->at(L.wtab), wtab.data(), wtab.size() * 8, cudaMemcpyHostToDevice, c->st);
+    if (e == cudaSuccess && L.has_island)
+        e = cudaMemsetAsync(c->at(L.island), 0, (size_t)(cfg->n_lo + 1) * (2 * cfg->n_lo + 1) * (2 * cfg->n_lo + 1) * 16,
+                            c->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
+    if (e != cudaSuccess) {
+        delete c;
+        return fail(PM_ERR_CUDA, std::string("pm_init: ") + cudaGetErrorString(e));
+    }
+    *out = c;
+    return PM_OK;
+}
+
+pm_status pm_destroy(pm_ctx* ctx) {
+    delete ctx;
+    return PM_OK;
+}
+
+pm_status pm_particles(pm_ctx* c, void** x, void** p) {
+    if (!c) return fail(PM_ERR_INVALID_ARG, "null context");
+    if (x) *x = c->at(c->L.x);
+    if (p) *p = c->at(c->L.p);
+    return PM_OK;
+}
+
+pm_status pm_set_particles(pm_ctx* c, const void* x, const void* p) {
+    if (!c || !x || !p) return fail(PM_ERR_INVALID_ARG, "null argument");
+    const size_t bytes = 3 * (size_t)c->np3 * c->sT();
+    PM_CK(cudaMemcpyAsync(c->at(c->L.x), x, bytes, cudaMemcpyDeviceToDevice, c->st));
+    PM_CK(cudaMemcpyAsync(c->at(c->L.p), p, bytes, cudaMemcpyDeviceToDevice, c->st));
+    c->step = 0;
+    c->synced = true;
+    c->have_phi = false;
+    return PM_OK;
+}
+
+pm_status pm_state(pm_ctx* c, int* step, double* a, int* synchronised) {
+    if (!c) return fail(PM_ERR_INVALID_ARG, "null context");
+    if (step) *step = c->step;
+    if (a) *a = c->a_grid(c->step);
+    if (synchronised) *synchronised = c->synced ? 1 : 0;
+    return PM_OK;
+}
+
+pm_status pm_ic_zeldovich(pm_ctx* c, uint64_t seed, const void* white_noise, int paired) {
+    if (!c) return fail(PM_ERR_INVALID_ARG, "null context");
+    const int np = c->np;
+    const double a = c->cfg.a_init;
+    const double D = pmhost::growth_D(c->cosmo, a);
+    const double f = pmhost::growth_f(c->cosmo, a);
+    const double E = pmhost::E(c->cosmo, a);
+    void* s0 = c->at(c->L.spec[0]);
+    void* s1 = c->at(c->L.spec[1]);
+    void* s2 = c->at(c->L.spec[2]);
+    SpecOp op;
+    op.kind = OP_ZA;
+    op.kf = c->kf;
+    op.amp = (const double*)c->at(c->L.amp);
+    const double sign = paired ? -1.0 : 1.0;
+    double scale = 1.0;
+    if (white_noise) {
+        if (c->fp64()) PM_TRY(forward_to_y<double>(c, white_noise, s0, np));
+        else PM_TRY(forward_to_y<float>(c, white_noise, s0, np));
+        op.fwd = 1;
+        scale = std::pow((double)np, -1.5);
+    } else {
+        if (c->fp64()) PM_CK(noise<double>((double2*)s0, np, seed, c->st));
+        else PM_CK(noise<float>((float2*)s0, np, seed, c->st));
+        op.fwd = 0;
+    }
+    op.coef = -sign * scale / (c->kf * c->kf);
+    void* psi[3] = {c->at(c->L.force[0]), c->at(c->L.force[1]), c->at(c->L.force[2])};
+    if (c->fp64()) {
+        PM_CK(x_cols<double>((double2*)s0, (double2*)s1, np / 2 + 1, np, op, c->st));
+        PM_CK(y_rows_grad3<double>((double2*)s0, (double2*)s1, (double2*)s2, (int64_t)(np / 2 + 1) * np, np, c->kf,
+                                   c->st));
+        const double2* in[3] = {(double2*)s1, (double2*)s2, (double2*)s0};
+        double* out[3] = {(double*)psi[0], (double*)psi[1], (double*)psi[2]};
+        PM_CK(z_c2r<double>(in, out, 3, np, 1, 4u, c->kf, c->st));
+    } else {
+        PM_CK(x_cols<float>((float2*)s0, (float2*)s1, np / 2 + 1, np, op, c->st));
+        PM_CK(y_rows_grad3<float>((float2*)s0, (float2*)s1, (float2*)s2, (int64_t)(np / 2 + 1) * np, np, c->kf,
+                                  c->st));
+        const float2* in[3] = {(float2*)s1, (float2*)s2, (float2*)s0};
+        float* out[3] = {(float*)psi[0], (float*)psi[1], (float*)psi[2]};
+        PM_CK(z_c2r<float>(in, out, 3, np, 1, 4u, c->kf, c->st));
+    }
+    PM_CK(ic_place(c->at(c->L.x), c->at(c->L.p), psi, np, c->cfg.precision, D, a * a * E * f * D, c->cfg.box, c->st));
+    c->step = 0;
+    c->synced = true;
+    c->have_phi = false;
+    return PM_OK;
+}
+
+pm_status pm_step(pm_ctx* c, int n_steps) {
+    if (!c) return fail(PM_ERR_INVALID_ARG, "null context");
+    if (n_steps < 0) return fail(PM_ERR_INVALID_ARG, "negative step count");
+    if (c->step + n_steps > c->cfg.n_steps) return fail(PM_ERR_STATE, "stepping past a_final");
+    for (int k = 0; k < n_steps; ++k) {
+        const double a0 = c->a_grid(c->step), a1 = c->a_grid(c->step + 1);
+        const double ah = 0.5 * (a0 + a1);
+        PM_TRY(compute_forces(c, a0));
+        const double a_from = c->synced ? a0 : 0.5 * (c->a_grid(c->step - 1) + a0);
+        PM_TRY(kick_drift(c, pmhost::kick_integral(c->cosmo, a_from, ah), pmhost::drift_integral(c->cosmo, a0, a1)));
+        c->step += 1;
+        c->synced = false;
+        if (c->step == c->cfg.n_steps) {
+            PM_TRY(compute_forces(c, a1));
+            PM_TRY(kick_drift(c, pmhost::kick_integral(c->cosmo, ah, a1), 0.0));
+            c->synced = true;
+        }
+    }
+    return PM_OK;
+}
+
+pm_status pm_density(pm_ctx* c, void* delta) {
+    if (!c || !delta) return fail(PM_ERR_INVALID_ARG, "null argument");
+    const int64_t n3 = (int64_t)c->n * c->n * c->n;
+    PM_CK(fill(delta, n3, c->cfg.precision, -1.0, c->st));
+    PM_CK(deposit(c->at(c->L.x), c->np3, c->cfg.precision, c->n, std::pow((double)c->n / c->np, 3), delta, c->st));
+    return PM_OK;
+}
+
+pm_status pm_potential(pm_ctx* c, void* phi) {
+    if (!c || !phi) return fail(PM_ERR_INVALID_ARG, "null argument");
+    const int n = c->n;
+    PM_TRY(deposit_particles(c, c->at(c->L.rho)));
+    SpecOp op;
+    op.kind = OP_POTENTIAL;
+    op.fwd = 1;
+    op.kf = c->kf;
+    op.coef = -1.5 * c->cfg.omega_m / (c->kf * c->kf * (double)n * n * n);
+    if (c->fp64()) {
+        double2* s0 = (double2*)c->at(c->L.spec[0]);
+        PM_TRY(forward_to_y<double>(c, c->at(c->L.rho), s0, n));
+        PM_CK(x_cols<double>(s0, nullptr, n / 2 + 1, n, op, c->st));
+        PM_CK((y_rows<double, true>(s0, (int64_t)(n / 2 + 1) * n, n, c->st)));
+        const double2* in[1] = {s0};
+        double* out[1] = {(double*)phi};
+        PM_CK(z_c2r<double>(in, out, 1, n, 1, 0u, 0.0, c->st));
+    } else {
+        float2* s0 = (float2*)c->at(c->L.spec[0]);
+        PM_TRY(forward_to_y<float>(c, c->at(c->L.rho), s0, n));
+        PM_CK(x_cols<float>(s0, nullptr, n / 2 + 1, n, op, c->st));
+        PM_CK((y_rows<float, true>(s0, (int64_t)(n / 2 + 1) * n, n, c->st)));
+        const float2* in[1] = {s0};
+        float* out[1] = {(float*)phi};
+        PM_CK(z_c2r<float>(in, out, 1, n, 1, 0u, 0.0, c->st));
+    }
+    return PM_OK;
+}
+
+pm_status pm_displacement_correction(pm_ctx* target, const pm_ctx* gr, const pm_ctx* newton, void* xi_out) {
+    if (!target || !gr || !newton) return fail(PM_ERR_INVALID_ARG, "null context");
+    if (gr->np != newton->np || gr->cfg.precision != newton->cfg.precision ||
+        target->cfg.precision != gr->cfg.precision)
+        return fail(PM_ERR_INVALID_ARG, "gr and newton must share np; all three must share precision");
+    if (target->np < gr->np || target->np % gr->np)
+        return fail(PM_ERR_INVALID_ARG, "target lattice must be a power-of-two multiple of the gr/newton lattice");
+    if (gr->st != target->st) PM_CK(cudaStreamSynchronize(gr->st));
+    if (newton->st != target->st) PM_CK(cudaStreamSynchronize(newton->st));
+    PM_CK(combine(target->at(target->L.x), gr->at(gr->L.x), newton->at(newton->L.x), xi_out, target->np, gr->np,
+                  target->cfg.precision, target->st));
+    return PM_OK;
+}
+
+pm_status pm_power(pm_ctx* c, const void* field, const void* field2, int nbins, const double* edges, int deconvolve,
+                   double* k_out, double* p_out, double* nmodes_out) {
+    if (!c) return fail(PM_ERR_INVALID_ARG, "null context");
+    PM_TRY(check_edges(nbins, edges));
+    return c->fp64() ? power_t<double>(c, field, field2, nbins, edges, deconvolve, k_out, p_out, nmodes_out)
+                     : power_t<float>(c, field, field2, nbins, edges, deconvolve, k_out, p_out, nmodes_out);
+}
+
+pm_status pm_bispectrum_scratch_size(const pm_ctx* c, int m, int nbins, size_t* bytes) {
+    if (!c || !bytes) return fail(PM_ERR_INVALID_ARG, "null argument");
+    if (!pow2(m) || m < 16 || m > 1024) return fail(PM_ERR_INVALID_ARG, "m must be a power of two in 16..1024");
+    if (nbins < 1 || nbins > 64) return fail(PM_ERR_INVALID_ARG, "bispectrum needs 1..64 bins");
+    *bytes = bk_plan((int)c->sT(), m, nbins).total;
+    return PM_OK;
+}
+
+pm_status pm_bispectrum(pm_ctx* c, const void* field, int nbins, const double* edges, int m, int deconvolve,
+                        void* scratch, size_t scratch_bytes, double* b_out, double* ntri_out) {
+    if (!c) return fail(PM_ERR_INVALID_ARG, "null context");
+    PM_TRY(check_edges(nbins, edges));
+    size_t need = 0;
+    PM_TRY(pm_bispectrum_scratch_size(c, m, nbins, &need));
+    if (!scratch || scratch_bytes < need || (uintptr_t)scratch % 256)
+        return fail(PM_ERR_WORKSPACE, "bispectrum scratch too small or not 256-byte aligned");
+    const int nmax = std::min((int)std::floor(edges[nbins]), c->n / 2 - 1);
+    if (3 * nmax >= m) return fail(PM_ERR_INVALID_ARG, "grid m too small for an alias-free triangle sum");
+    const BkLayout B = bk_plan((int)c->sT(), m, nbins);
+    return c->fp64() ? bispectrum_t<double>(c, field, nbins, edges, m, deconvolve, (unsigned char*)scratch, B, b_out,
+                                            ntri_out)
+                     : bispectrum_t<float>(c, field, nbins, edges, m, deconvolve, (unsigned char*)scratch, B, b_out,
+                                           ntri_out);
+}
+
+// ------------------------------------------------------------------ stateless operators
+pm_status pm_cic_deposit(const void* x, int64_t count, int precision, int n, double mass, void* rho, void* stream) {
+    if ((!x && count > 0) || !rho || count < 0) return fail(PM_ERR_INVALID_ARG, "null pointer or negative count");
+    if (!pow2(n) || n < 2 || n > 1024) return fail(PM_ERR_INVALID_ARG, "n must be a power of two in 2..1024");
+    if (precision != PM_FP32_FIXED && precision != PM_FP64) return fail(PM_ERR_INVALID_ARG, "bad precision");
+    PM_TRY(check_device());
+    PM_CK(deposit(x, count, precision, n, mass, rho, (cudaStream_t)stream));
+    return PM_OK;
+}
+
+pm_status pm_cic_interp(const void* field, int n, const void* x, int64_t count, int precision, void* out,
+                        void* stream) {
+    if (!field || (!x && count > 0) || (!out && count > 0) || count < 0)
+        return fail(PM_ERR_INVALID_ARG, "null pointer or negative count");
+    if (!pow2(n) || n < 2 || n > 1024) return fail(PM_ERR_INVALID_ARG, "n must be a power of two in 2..1024");
+    if (precision != PM_FP32_FIXED && precision != PM_FP64) return fail(PM_ERR_INVALID_ARG, "bad precision");
+    PM_TRY(check_device());
+    PM_CK(interp(field, n, x, count, precision, out, (cudaStream_t)stream));
+    return PM_OK;
+}
+
+pm_status pm_cell_sort_scratch_size(int64_t count, int n, size_t* bytes) {
+    if (!bytes || count < 0 || !pow2(n) || n < 2 || n > 1024) return fail(PM_ERR_INVALID_ARG, "bad arguments");
+    if (count > 0xFFFFFFFFll) return fail(PM_ERR_INVALID_ARG, "count must fit in 32 bits");
+    *bytes = cell_sort_scratch_bytes(count, n);
+    return PM_OK;
+}
+
+pm_status pm_cell_sort(const void* x, int64_t count, int precision, int n, uint32_t* keys_out, uint32_t* order_out,
+                       void* scratch, size_t scratch_bytes, void* stream) {
+    size_t need = 0;
+    PM_TRY(pm_cell_sort_scratch_size(count, n, &need));
+    if ((!x && count > 0) || (!keys_out && count > 0)) return fail(PM_ERR_INVALID_ARG, "null pointer");
+    if (order_out && (!scratch || scratch_bytes < need)) return fail(PM_ERR_WORKSPACE, "cell sort scratch too small");
+    if (precision != PM_FP32_FIXED && precision != PM_FP64) return fail(PM_ERR_INVALID_ARG, "bad precision");
+    PM_TRY(check_device());
+    PM_CK(cell_sort(x, count, precision, n, keys_out, order_out, scratch, (cudaStream_t)stream));
+    return PM_OK;
+}
+
+pm_status pm_fft_r2c(const void* real, void* spec, int n, int precision, void* stream) {
+    if (!real || !spec) return fail(PM_ERR_INVALID_ARG, "null pointer");
+    if (!pow2(n) || n < 16 || n > 1024) return fail(PM_ERR_INVALID_ARG, "n must be a power of two in 16..1024");
+    if (precision != PM_FP32_FIXED && precision != PM_FP64) return fail(PM_ERR_INVALID_ARG, "bad precision");
+    PM_TRY(check_device());
+    cudaStream_t st = (cudaStream_t)stream;
+    SpecOp fw;
+    fw.kind = OP_FWD_STORE;
+    fw.fwd = 1;
+    if (precision == PM_FP64) {
+        PM_CK(z_r2c<double>((const double*)real, (double2*)spec, n, 1, st));
+        PM_CK((y_rows<double, false>((double2*)spec, (int64_t)(n / 2 + 1) * n, n, st)));
+        PM_CK(x_cols<double>((double2*)spec, nullptr, n / 2 + 1, n, fw, st));
+    } else {
+        PM_CK(z_r2c<float>((const float*)real, (float2*)spec, n, 1, st));
+        PM_CK((y_rows<float, false>((float2*)spec, (int64_t)(n / 2 + 1) * n, n, st)));
+        PM_CK(x_cols<float>((float2*)spec, nullptr, n / 2 + 1, n, fw, st));
+    }
+    return PM_OK;
+}
+
+pm_status pm_fft_c2r(void* spec, void* real, int n, int precision, void* stream) {
+    if (!real || !spec) return fail(PM_ERR_INVALID_ARG, "null pointer");
+    if (!pow2(n) || n < 16 || n > 1024) return fail(PM_ERR_INVALID_ARG, "n must be a power of two in 16..1024");
+    if (precision != PM_FP32_FIXED && precision != PM_FP64) return fail(PM_ERR_INVALID_ARG, "bad precision");
+    PM_TRY(check_device());
+    cudaStream_t st = (cudaStream_t)stream;
+    SpecOp inv;
+    inv.kind = OP_INV;
+    inv.fwd = 0;
+    if (precision == PM_FP64) {
+        PM_CK(x_cols<double>((double2*)spec, nullptr, n / 2 + 1, n, inv, st));
+        PM_CK((y_rows<double, true>((double2*)spec, (int64_t)(n / 2 + 1) * n, n, st)));
+        const double2* in[1] = {(double2*)spec};
+        double* out[1] = {(double*)real};
+        PM_CK(z_c2r<double>(in, out, 1, n, 1, 0u, 0.0, st));
+    } else {
+        PM_CK(x_cols<float>((float2*)spec, nullptr, n / 2 + 1, n, inv, st));
+        PM_CK((y_rows<float, true>((float2*)spec, (int64_t)(n / 2 + 1) * n, n, st)));
+        const float2* in[1] = {(float2*)spec};
+        float* out[1] = {(float*)real};
+        PM_CK(z_c2r<float>(in, out, 1, n, 1, 0u, 0.0, st));
+    }
+    return PM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,68 @@
+// Internal launcher interfaces shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "pm_common.cuh"
+
+namespace pm {
+
+// Per-mode operator applied by the strided (x-axis) FFT pass between its forward
+// and inverse transforms.
+enum OpKind {
+    OP_FWD_STORE = 0,  // forward x-FFT, store the spectrum
+    OP_INV = 1,        // inverse x-FFT
+    OP_NEWTON = 2,     // Newtonian Green's function, outputs IFFT_x(phi) and IFFT_x(-i kx phi)
+    OP_GR = 3,         // linearised Poisson-gauge constraint, same outputs, updates Phi_old
+    OP_ZA = 4,         // Zel'dovich displacement potential from unit phases, same outputs
+    OP_BIN = 5,        // power-spectrum binning (auto or cross), no output
+    OP_POTENTIAL = 6   // Newtonian potential only: IFFT_x(phi)
+};
+
+struct SpecOp {
+    int kind = OP_FWD_STORE;
+    int fwd = 1;              // forward x-FFT of the input first
+    double coef = 0.0;        // NEWTON/POTENTIAL: -3/2 Om / (kf^2 n^3); ZA: -sign * scale / kf^2
+    double kf = 0.0;          // fundamental mode, h/Mpc
+    // linearised Poisson gauge
+    double calH = 0.0, omm_a = 0.0, inv_dtau = 0.0, ac2_over_n3 = 0.0;
+    int first = 1;            // Phi' = 0 at the first force evaluation
+    int n_lo = 0;             // |n|^2 <= n_lo^2 handled in FP64
+    void* phi_old = nullptr;  // cplx<T> [kz][kx][ky]
+    double2* island = nullptr;  // double2 [(n_lo+1)(2 n_lo+1)^2]
+    // Zel'dovich
+    const double* amp = nullptr;  // sqrt(P(k)/V) per integer |n|^2
+    // power spectrum
+    const int16_t* bin_of = nullptr;  // bin per integer |n|^2 (-1 = none)
+    const double* wtab = nullptr;     // CIC sinc^2(pi m / n) for m = 0..n/2
+    double* acc = nullptr;            // [3][nbins]: sum w, sum w P, sum w k
+    int nbins = 0;
+    int deconv = 0;
+    const void* in2 = nullptr;        // second (y-transformed) field for the cross spectrum
+};
+
+// Twiddle table exp(-2 pi i k / 1024), k < 1024, resident on the current device.
+const float2* twiddles_f32();
+const double2* twiddles_f64();
+template <typename T> const cplx<T>* twiddles();
+cudaError_t ensure_device_tables();
+
+// FFT passes.  n is the transform length (power of two, 16..1024); batch counts
+// independent 3D fields stored back to back.
+template <typename T>
+cudaError_t z_r2c(const T* in, cplx<T>* out, int n, int batch, cudaStream_t st);
+// out_j = c2r(in_j [* -i kf kz when gradz_mask bit j is set]) for the ncomp fields
+template <typename T>
+cudaError_t z_c2r(const cplx<T>* const* in, T* const* out, int ncomp, int n, int batch,
+                  unsigned gradz_mask, double kf, cudaStream_t st);
+template <typename T, bool INV>
+cudaError_t y_rows(cplx<T>* data, int64_t nrows, int n, cudaStream_t st);
+// A <- IFFT_y(A), B <- IFFT_y(B), C <- IFFT_y(-i ky A)
+template <typename T>
+cudaError_t y_rows_grad3(cplx<T>* A, cplx<T>* B, cplx<T>* C, int64_t nrows, int n, double kf,
+                         cudaStream_t st);
+template <typename T>
+cudaError_t x_cols(cplx<T>* data, cplx<T>* out2, int nplanes, int n, const SpecOp& op, cudaStream_t st);
+
+}  // namespace pm

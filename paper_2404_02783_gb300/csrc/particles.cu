@@ -1,0 +1,630 @@
+// Particle-side kernels of the PM step: CIC deposit (counting density, Sec. 4),
+// fused CIC interpolation + kick + drift (KDK in a), Zel'dovich placement, the
+// per-wavevector Philox phases, the GR displacement combination (Eqs. xiGR and
+// combined) and the cell keys / stable cell order of the particles.
+//
+// Position encodings (units of the box side):
+//   FP32 path: uint32 ticks, 2^32 per side; the periodic wrap is integer overflow.
+//   FP64 path: double fraction in [0, 1).
+// Mesh nodes sit at cell centres, so mesh coordinate s = x n - 1/2; on ticks that
+// is (u - 2^(31 - log2 n)) >> (32 - log2 n) for the base node and the low bits
+// for the fraction, both exact.
+#include <math.h>
+
+#include "internal.h"
+#include "particles.h"
+
+namespace pm {
+
+// ---------------------------------------------------------------- CIC decode
+struct CicF {
+    int i0, i1;
+    float w1;
+};
+__device__ __forceinline__ CicF cic_ticks(uint32_t u, int logn, float inv_cell_ticks) {
+    const int sh = 32 - logn;
+    const uint32_t t = u - (1u << (sh - 1));
+    CicF c;
+    c.i0 = (int)(t >> sh);
+    c.i1 = (c.i0 + 1) & ((1 << logn) - 1);
+    c.w1 = __uint2float_rn(t & ((1u << sh) - 1u)) * inv_cell_ticks;
+    return c;
+}
+struct CicD {
+    int i0, i1;
+    double w1;
+};
+__device__ __forceinline__ CicD cic_frac(double x, int n) {
+    const double s = x * (double)n - 0.5;
+    const double fl = floor(s);
+    CicD c;
+    c.w1 = s - fl;
+    c.i0 = ((int)fl) & (n - 1);
+    c.i1 = (c.i0 + 1) & (n - 1);
+    return c;
+}
+
+// ---------------------------------------------------------------- deposit
+__global__ void k_deposit_ticks(const uint32_t* __restrict__ x, int64_t count, int logn, float inv_cell_ticks,
+                                float mass, float* __restrict__ rho) {
+    const size_t n = (size_t)1 << logn;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const CicF cx = cic_ticks(x[i], logn, inv_cell_ticks);
+        const CicF cy = cic_ticks(x[count + i], logn, inv_cell_ticks);
+        const CicF cz = cic_ticks(x[2 * count + i], logn, inv_cell_ticks);
+        const float wx[2] = {1.0f - cx.w1, cx.w1}, wy[2] = {1.0f - cy.w1, cy.w1}, wz[2] = {1.0f - cz.w1, cz.w1};
+        const int ix[2] = {cx.i0, cx.i1}, iy[2] = {cy.i0, cy.i1}, iz[2] = {cz.i0, cz.i1};
+#pragma unroll
+        for (int a = 0; a < 2; ++a)
+#pragma unroll
+            for (int b = 0; b < 2; ++b) {
+                const float wab = mass * wx[a] * wy[b];
+                float* row = rho + ((size_t)ix[a] * n + iy[b]) * n;
+                atomicAdd(row + iz[0], wab * wz[0]);
+                atomicAdd(row + iz[1], wab * wz[1]);
+            }
+    }
+}
+
+__global__ void k_deposit_frac(const double* __restrict__ x, int64_t count, int n, double mass,
+                               double* __restrict__ rho) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const CicD cx = cic_frac(x[i], n), cy = cic_frac(x[count + i], n), cz = cic_frac(x[2 * count + i], n);
+        const double wx[2] = {1.0 - cx.w1, cx.w1}, wy[2] = {1.0 - cy.w1, cy.w1}, wz[2] = {1.0 - cz.w1, cz.w1};
+        const int ix[2] = {cx.i0, cx.i1}, iy[2] = {cy.i0, cy.i1}, iz[2] = {cz.i0, cz.i1};
+#pragma unroll
+        for (int a = 0; a < 2; ++a)
+#pragma unroll
+            for (int b = 0; b < 2; ++b) {
+                const double wab = mass * wx[a] * wy[b];
+                double* row = rho + ((size_t)ix[a] * n + iy[b]) * n;
+                atomicAdd(row + iz[0], wab * wz[0]);
+                atomicAdd(row + iz[1], wab * wz[1]);
+            }
+    }
+}
+
+static unsigned grid_for(int64_t count, int threads) {
+    int64_t b = (count + threads - 1) / threads;
+    const int64_t cap = 152 * 32;
+    if (b > cap) b = cap;
+    if (b < 1) b = 1;
+    return (unsigned)b;
+}
+
+cudaError_t deposit(const void* x, int64_t count, int precision, int n, double mass, void* rho,
+                    cudaStream_t st) {
+    if (count == 0) return cudaSuccess;
+    const int logn = ilog2(n);
+    if (precision == PM_FP32_FIXED) {
+        const float inv = (float)ldexp(1.0, -(32 - logn));
+        k_deposit_ticks<<<grid_for(count, 256), 256, 0, st>>>((const uint32_t*)x, count, logn, inv, (float)mass,
+                                                              (float*)rho);
+    } else {
+        k_deposit_frac<<<grid_for(count, 256), 256, 0, st>>>((const double*)x, count, n, mass, (double*)rho);
+    }
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- interpolation
+template <typename T, typename X>
+__device__ __forceinline__ T gather8(const T* __restrict__ f, size_t n, const int* ix, const int* iy,
+                                     const int* iz, const T* wx, const T* wy, const T* wz) {
+    T acc = T(0);
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int b = 0; b < 2; ++b) {
+            const T* row = f + ((size_t)ix[a] * n + iy[b]) * n;
+            acc += wx[a] * wy[b] * (wz[0] * __ldg(row + iz[0]) + wz[1] * __ldg(row + iz[1]));
+        }
+    return acc;
+}
+
+__global__ void k_interp_ticks(const float* __restrict__ f, int logn, const uint32_t* __restrict__ x,
+                               int64_t count, float inv_cell_ticks, float* __restrict__ out) {
+    const size_t n = (size_t)1 << logn;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const CicF cx = cic_ticks(x[i], logn, inv_cell_ticks);
+        const CicF cy = cic_ticks(x[count + i], logn, inv_cell_ticks);
+        const CicF cz = cic_ticks(x[2 * count + i], logn, inv_cell_ticks);
+        const float wx[2] = {1.0f - cx.w1, cx.w1}, wy[2] = {1.0f - cy.w1, cy.w1}, wz[2] = {1.0f - cz.w1, cz.w1};
+        const int ix[2] = {cx.i0, cx.i1}, iy[2] = {cy.i0, cy.i1}, iz[2] = {cz.i0, cz.i1};
+        out[i] = gather8<float, uint32_t>(f, n, ix, iy, iz, wx, wy, wz);
+    }
+}
+
+__global__ void k_interp_frac(const double* __restrict__ f, int n, const double* __restrict__ x, int64_t count,
+                              double* __restrict__ out) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const CicD cx = cic_frac(x[i], n), cy = cic_frac(x[count + i], n), cz = cic_frac(x[2 * count + i], n);
+        const double wx[2] = {1.0 - cx.w1, cx.w1}, wy[2] = {1.0 - cy.w1, cy.w1}, wz[2] = {1.0 - cz.w1, cz.w1};
+        const int ix[2] = {cx.i0, cx.i1}, iy[2] = {cy.i0, cy.i1}, iz[2] = {cz.i0, cz.i1};
+        out[i] = gather8<double, double>(f, (size_t)n, ix, iy, iz, wx, wy, wz);
+    }
+}
+
+cudaError_t interp(const void* field, int n, const void* x, int64_t count, int precision, void* out,
+                   cudaStream_t st) {
+    if (count == 0) return cudaSuccess;
+    const int logn = ilog2(n);
+    if (precision == PM_FP32_FIXED) {
+        const float inv = (float)ldexp(1.0, -(32 - logn));
+        k_interp_ticks<<<grid_for(count, 256), 256, 0, st>>>((const float*)field, logn, (const uint32_t*)x, count,
+                                                             inv, (float*)out);
+    } else {
+        k_interp_frac<<<grid_for(count, 256), 256, 0, st>>>((const double*)field, n, (const double*)x, count,
+                                                            (double*)out);
+    }
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- interp + kick + drift
+// p += kick * g(x);  x += drift * p   (g = -grad phi gathered with the deposit's weights)
+__global__ void __launch_bounds__(256) k_ikd_ticks(uint32_t* __restrict__ x, float* __restrict__ p, int64_t count,
+                                                   int logn, float inv_cell_ticks, const float* __restrict__ gx,
+                                                   const float* __restrict__ gy, const float* __restrict__ gz,
+                                                   float kick, float drift_ticks) {
+    const size_t n = (size_t)1 << logn;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t ux = x[i], uy = x[count + i], uz = x[2 * count + i];
+        const CicF cx = cic_ticks(ux, logn, inv_cell_ticks);
+        const CicF cy = cic_ticks(uy, logn, inv_cell_ticks);
+        const CicF cz = cic_ticks(uz, logn, inv_cell_ticks);
+        const float wx[2] = {1.0f - cx.w1, cx.w1}, wy[2] = {1.0f - cy.w1, cy.w1}, wz[2] = {1.0f - cz.w1, cz.w1};
+        const int ix[2] = {cx.i0, cx.i1}, iy[2] = {cy.i0, cy.i1}, iz[2] = {cz.i0, cz.i1};
+        const float fx = gather8<float, uint32_t>(gx, n, ix, iy, iz, wx, wy, wz);
+        const float fy = gather8<float, uint32_t>(gy, n, ix, iy, iz, wx, wy, wz);
+        const float fz = gather8<float, uint32_t>(gz, n, ix, iy, iz, wx, wy, wz);
+        const float px = p[i] + kick * fx;
+        const float py = p[count + i] + kick * fy;
+        const float pz = p[2 * count + i] + kick * fz;
+        p[i] = px;
+        p[count + i] = py;
+        p[2 * count + i] = pz;
+        x[i] = ux + (uint32_t)__float2ll_rn(px * drift_ticks);
+        x[count + i] = uy + (uint32_t)__float2ll_rn(py * drift_ticks);
+        x[2 * count + i] = uz + (uint32_t)__float2ll_rn(pz * drift_ticks);
+    }
+}
+
+__global__ void __launch_bounds__(256) k_ikd_frac(double* __restrict__ x, double* __restrict__ p, int64_t count,
+                                                  int n, const double* __restrict__ gx, const double* __restrict__ gy,
+                                                  const double* __restrict__ gz, double kick, double drift_box) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        double xs[3] = {x[i], x[count + i], x[2 * count + i]};
+        const CicD cx = cic_frac(xs[0], n), cy = cic_frac(xs[1], n), cz = cic_frac(xs[2], n);
+        const double wx[2] = {1.0 - cx.w1, cx.w1}, wy[2] = {1.0 - cy.w1, cy.w1}, wz[2] = {1.0 - cz.w1, cz.w1};
+        const int ix[2] = {cx.i0, cx.i1}, iy[2] = {cy.i0, cy.i1}, iz[2] = {cz.i0, cz.i1};
+        const double f[3] = {gather8<double, double>(gx, (size_t)n, ix, iy, iz, wx, wy, wz),
+                             gather8<double, double>(gy, (size_t)n, ix, iy, iz, wx, wy, wz),
+                             gather8<double, double>(gz, (size_t)n, ix, iy, iz, wx, wy, wz)};
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            const double pj = p[j * count + i] + kick * f[j];
+            p[j * count + i] = pj;
+            double xj = xs[j] + drift_box * pj;
+            xj -= floor(xj);
+            x[j * count + i] = xj;
+        }
+    }
+}
+
+cudaError_t interp_kick_drift(void* x, void* p, int64_t count, int precision, int n, void* const* g,
+                              double kick, double drift, double box, cudaStream_t st) {
+    if (count == 0) return cudaSuccess;
+    const int logn = ilog2(n);
+    if (precision == PM_FP32_FIXED) {
+        const float inv = (float)ldexp(1.0, -(32 - logn));
+        const float dt = (float)(drift * 4294967296.0 / box);
+        k_ikd_ticks<<<grid_for(count, 256), 256, 0, st>>>((uint32_t*)x, (float*)p, count, logn, inv,
+                                                          (const float*)g[0], (const float*)g[1], (const float*)g[2],
+                                                          (float)kick, dt);
+    } else {
+        k_ikd_frac<<<grid_for(count, 256), 256, 0, st>>>((double*)x, (double*)p, count, n, (const double*)g[0],
+                                                         (const double*)g[1], (const double*)g[2], kick, drift / box);
+    }
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- Zel'dovich placement
+// x = q + D Psi(q), p = a^2 E f D Psi(q); q the lattice node of particle id i.
+__global__ void k_ic_ticks(uint32_t* __restrict__ x, float* __restrict__ p, const float* __restrict__ psx,
+                           const float* __restrict__ psy, const float* __restrict__ psz, int lognp,
+                           double disp_ticks, double pfac) {
+    const int64_t count = (int64_t)1 << (3 * lognp);
+    const int sh = 32 - lognp;
+    const int mask = (1 << lognp) - 1;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t q[3] = {(uint32_t)((i >> (2 * lognp)) & mask) << sh, (uint32_t)((i >> lognp) & mask) << sh,
+                               (uint32_t)(i & mask) << sh};
+        const float ps[3] = {psx[i], psy[i], psz[i]};
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            x[j * count + i] = q[j] + (uint32_t)__double2ll_rn((double)ps[j] * disp_ticks);
+            p[j * count + i] = (float)(pfac * (double)ps[j]);
+        }
+    }
+}
+
+__global__ void k_ic_frac(double* __restrict__ x, double* __restrict__ p, const double* __restrict__ psx,
+                          const double* __restrict__ psy, const double* __restrict__ psz, int lognp, double disp_box,
+                          double pfac) {
+    const int64_t count = (int64_t)1 << (3 * lognp);
+    const int mask = (1 << lognp) - 1;
+    const double inv_np = ldexp(1.0, -lognp);
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const double q[3] = {(double)((i >> (2 * lognp)) & mask) * inv_np, (double)((i >> lognp) & mask) * inv_np,
+                             (double)(i & mask) * inv_np};
+        const double ps[3] = {psx[i], psy[i], psz[i]};
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            double xj = q[j] + disp_box * ps[j];
+            xj -= floor(xj);
+            x[j * count + i] = xj;
+            p[j * count + i] = pfac * ps[j];
+        }
+    }
+}
+
+cudaError_t ic_place(void* x, void* p, void* const* psi, int np, int precision, double D, double pfac, double box,
+                     cudaStream_t st) {
+    const int lognp = ilog2(np);
+    const int64_t count = (int64_t)np * np * np;
+    if (precision == PM_FP32_FIXED) {
+        k_ic_ticks<<<grid_for(count, 256), 256, 0, st>>>((uint32_t*)x, (float*)p, (const float*)psi[0],
+                                                         (const float*)psi[1], (const float*)psi[2], lognp,
+                                                         D * 4294967296.0 / box, pfac);
+    } else {
+        k_ic_frac<<<grid_for(count, 256), 256, 0, st>>>((double*)x, (double*)p, (const double*)psi[0],
+                                                        (const double*)psi[1], (const double*)psi[2], lognp, D / box,
+                                                        pfac);
+    }
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- Philox phases
+// Philox4x32-10 (Salmon, Moraes, Dror & Shaw, SC'11): ten rounds of two 32x32->64
+// multiplies with the Philox multipliers, xor with the key, word permutation, and
+// a Weyl-sequence key bump between rounds.
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1) {
+    const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u;
+    const uint32_t W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r > 0) {
+            k0 += W0;
+            k1 += W1;
+        }
+        const uint32_t hi0 = __umulhi(M0, c.x), lo0 = M0 * c.x;
+        const uint32_t hi1 = __umulhi(M1, c.z), lo1 = M1 * c.z;
+        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+    }
+    return c;
+}
+
+// Unit complex Gaussian per wavevector on the [kz][kx][ky] half grid; Hermitian
+// partners on kz = 0 are conjugates of the canonical draw; Nyquist and zero modes 0.
+template <typename T>
+__global__ void k_noise(cplx<T>* __restrict__ spec, int n, uint32_t seed_lo, uint32_t seed_hi) {
+    const int M = n >> 1;
+    const int64_t total = (int64_t)(M + 1) * n * n;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int kz = (int)(e / ((int64_t)n * n));
+        const int rem = (int)(e - (int64_t)kz * n * n);
+        const int nx = signed_k(rem / n, n), ny = signed_k(rem % n, n), nz = kz;
+        cplx<T> g;
+        g.x = T(0);
+        g.y = T(0);
+        const bool nyq = (2 * nx == -n) || (2 * ny == -n) || (nz == M);
+        if (!nyq && (nx | ny | nz) != 0) {
+            const bool canonical = nz > 0 || ny > 0 || (ny == 0 && nx > 0);
+            const int cx = canonical ? nx : -nx, cy = canonical ? ny : -ny;
+            const uint4 r = philox4x32_10(make_uint4((uint32_t)cx, (uint32_t)cy, (uint32_t)nz, 0u), seed_lo, seed_hi);
+            const double u1 = ((double)r.x + 0.5) * 2.3283064365386963e-10;  // 2^-32
+            const double u2 = ((double)r.y + 0.5) * 2.3283064365386963e-10;
+            const double amp = sqrt(-log(u1));
+            double s, c;
+            sincospi(2.0 * u2, &s, &c);
+            g.x = T(amp * c);
+            g.y = T(canonical ? amp * s : -amp * s);
+        }
+        spec[e] = g;
+    }
+}
+
+template <typename T>
+cudaError_t noise(cplx<T>* spec, int n, uint64_t seed, cudaStream_t st) {
+    const int64_t total = (int64_t)(n / 2 + 1) * n * n;
+    k_noise<T><<<grid_for(total, 256), 256, 0, st>>>(spec, n, (uint32_t)(seed & 0xFFFFFFFFu), (uint32_t)(seed >> 32));
+    return cudaGetLastError();
+}
+template cudaError_t noise<float>(float2*, int, uint64_t, cudaStream_t);
+template cudaError_t noise<double>(double2*, int, uint64_t, cudaStream_t);
+
+// ---------------------------------------------------------------- GR displacement combination
+// xi = x_GR - x_N on the coarse lattice (exact minimum image on ticks), trilinear in
+// the Lagrangian lattice index to the target lattice (r = npt / npc), x_t += xi.
+__global__ void k_combine_ticks(uint32_t* __restrict__ xt, const uint32_t* __restrict__ xg,
+                                const uint32_t* __restrict__ xn, int32_t* __restrict__ xi_out, int lognt,
+                                int lognc) {
+    const int64_t countt = (int64_t)1 << (3 * lognt);
+    const int64_t countc = (int64_t)1 << (3 * lognc);
+    const int logr = lognt - lognc;
+    const int r = 1 << logr;
+    const int maskt = (1 << lognt) - 1, maskc = (1 << lognc) - 1;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < countt;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int it[3] = {(int)((i >> (2 * lognt)) & maskt), (int)((i >> lognt) & maskt), (int)(i & maskt)};
+        int base[3], off[3];
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            base[j] = it[j] >> logr;
+            off[j] = it[j] & (r - 1);
+        }
+        int64_t S[3] = {0, 0, 0};
+#pragma unroll
+        for (int dx = 0; dx < 2; ++dx)
+#pragma unroll
+            for (int dy = 0; dy < 2; ++dy)
+#pragma unroll
+                for (int dz = 0; dz < 2; ++dz) {
+                    const int64_t W = (int64_t)(dx ? off[0] : r - off[0]) * (dy ? off[1] : r - off[1]) *
+                                      (dz ? off[2] : r - off[2]);
+                    if (W == 0) continue;
+                    const int64_t c = (((int64_t)((base[0] + dx) & maskc) << (2 * lognc)) |
+                                       ((int64_t)((base[1] + dy) & maskc) << lognc) | ((base[2] + dz) & maskc));
+#pragma unroll
+                    for (int j = 0; j < 3; ++j) {
+                        const int32_t d = (int32_t)(xg[j * countc + c] - xn[j * countc + c]);
+                        S[j] += W * (int64_t)d;
+                    }
+                }
+        const int s = 3 * logr;
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            int64_t q = S[j];
+            if (s > 0) {  // round-half-even of S / 2^s
+                const int64_t fl = S[j] >> s;
+                const int64_t rem = S[j] - (fl << s);
+                const int64_t half = (int64_t)1 << (s - 1);
+                q = fl + ((rem > half || (rem == half && (fl & 1))) ? 1 : 0);
+            }
+            xt[j * countt + i] += (uint32_t)q;
+            if (xi_out) xi_out[j * countt + i] = (int32_t)q;
+        }
+    }
+}
+
+__global__ void k_combine_frac(double* __restrict__ xt, const double* __restrict__ xg, const double* __restrict__ xn,
+                               double* __restrict__ xi_out, int lognt, int lognc) {
+    const int64_t countt = (int64_t)1 << (3 * lognt);
+    const int64_t countc = (int64_t)1 << (3 * lognc);
+    const int logr = lognt - lognc;
+    const int r = 1 << logr;
+    const double inv_r3 = ldexp(1.0, -3 * logr);
+    const int maskt = (1 << lognt) - 1, maskc = (1 << lognc) - 1;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < countt;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int it[3] = {(int)((i >> (2 * lognt)) & maskt), (int)((i >> lognt) & maskt), (int)(i & maskt)};
+        int base[3], off[3];
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            base[j] = it[j] >> logr;
+            off[j] = it[j] & (r - 1);
+        }
+        double S[3] = {0, 0, 0};
+        for (int dx = 0; dx < 2; ++dx)
+            for (int dy = 0; dy < 2; ++dy)
+                for (int dz = 0; dz < 2; ++dz) {
+                    const int W = (dx ? off[0] : r - off[0]) * (dy ? off[1] : r - off[1]) * (dz ? off[2] : r - off[2]);
+                    if (W == 0) continue;
+                    const int64_t c = (((int64_t)((base[0] + dx) & maskc) << (2 * lognc)) |
+                                       ((int64_t)((base[1] + dy) & maskc) << lognc) | ((base[2] + dz) & maskc));
+                    for (int j = 0; j < 3; ++j) {
+                        double d = xg[j * countc + c] - xn[j * countc + c];
+                        d -= rint(d);
+                        S[j] += (double)W * d;
+                    }
+                }
+        for (int j = 0; j < 3; ++j) {
+            const double xi = S[j] * inv_r3;
+            double xj = xt[j * countt + i] + xi;
+            xj -= floor(xj);
+            xt[j * countt + i] = xj;
+            if (xi_out) xi_out[j * countt + i] = xi;
+        }
+    }
+}
+
+cudaError_t combine(void* xt, const void* xg, const void* xn, void* xi_out, int npt, int npc, int precision,
+                    cudaStream_t st) {
+    const int lognt = ilog2(npt), lognc = ilog2(npc);
+    const int64_t count = (int64_t)npt * npt * npt;
+    if (precision == PM_FP32_FIXED)
+        k_combine_ticks<<<grid_for(count, 256), 256, 0, st>>>((uint32_t*)xt, (const uint32_t*)xg,
+                                                              (const uint32_t*)xn, (int32_t*)xi_out, lognt, lognc);
+    else
+        k_combine_frac<<<grid_for(count, 256), 256, 0, st>>>((double*)xt, (const double*)xg, (const double*)xn,
+                                                             (double*)xi_out, lognt, lognc);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- fill
+template <typename T>
+__global__ void k_fill(T* __restrict__ a, int64_t count, T v) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x)
+        a[i] = v;
+}
+cudaError_t fill(void* a, int64_t count, int precision, double v, cudaStream_t st) {
+    if (precision == PM_FP32_FIXED)
+        k_fill<float><<<grid_for(count, 256), 256, 0, st>>>((float*)a, count, (float)v);
+    else
+        k_fill<double><<<grid_for(count, 256), 256, 0, st>>>((double*)a, count, v);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- cell keys and stable order
+__global__ void k_cell_keys(const void* __restrict__ xv, int64_t count, int precision, int logn, float inv_cell_ticks,
+                            uint32_t* __restrict__ keys, uint32_t* __restrict__ counts) {
+    const int n = 1 << logn;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        int b[3];
+        if (precision == PM_FP32_FIXED) {
+            const uint32_t* x = (const uint32_t*)xv;
+            for (int j = 0; j < 3; ++j) b[j] = cic_ticks(x[j * count + i], logn, inv_cell_ticks).i0;
+        } else {
+            const double* x = (const double*)xv;
+            for (int j = 0; j < 3; ++j) b[j] = cic_frac(x[j * count + i], n).i0;
+        }
+        const uint32_t key = ((uint32_t)b[0] << (2 * logn)) | ((uint32_t)b[1] << logn) | (uint32_t)b[2];
+        keys[i] = key;
+        if (counts) atomicAdd(&counts[key], 1u);
+    }
+}
+
+// Exclusive scan, 4 elements per thread, 1024 threads per block.
+__global__ void __launch_bounds__(1024) k_scan_block(const uint32_t* __restrict__ in, uint32_t* __restrict__ out,
+                                                     int64_t count, uint32_t* __restrict__ block_sums) {
+    __shared__ uint32_t warp_tot[32];
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const int64_t base = (int64_t)blockIdx.x * 4096 + 4 * tid;
+    uint32_t v[4];
+    uint32_t local = 0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        v[k] = (base + k < count) ? in[base + k] : 0u;
+        const uint32_t t = v[k];
+        v[k] = local;
+        local += t;
+    }
+    uint32_t incl = local;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, incl, d);
+        if (lane >= d) incl += y;
+    }
+    if (lane == 31) warp_tot[wid] = incl;
+    __syncthreads();
+    if (wid == 0) {
+        uint32_t w = warp_tot[lane];
+        uint32_t wi = w;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, wi, d);
+            if (lane >= d) wi += y;
+        }
+        warp_tot[lane] = wi - w;  // exclusive warp offsets
+        if (lane == 31 && block_sums) block_sums[blockIdx.x] = wi;
+    }
+    __syncthreads();
+    const uint32_t off = warp_tot[wid] + (incl - local);
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+        if (base + k < count) out[base + k] = v[k] + off;
+}
+
+__global__ void k_scan_add(uint32_t* __restrict__ out, int64_t count, const uint32_t* __restrict__ sums) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < count) out[i] += sums[i / 4096];
+}
+
+// Exclusive scan of count uint32 values; scratch: scan_scratch_words(count) words.
+static int64_t scan_scratch_words(int64_t count) {
+    int64_t words = 0;
+    while (count > 4096) {
+        count = (count + 4095) / 4096;
+        words += count + 1;
+    }
+    return words + 1;
+}
+static cudaError_t scan_u32(const uint32_t* in, uint32_t* out, int64_t count, uint32_t* scratch, cudaStream_t st) {
+    const int64_t nblk = (count + 4095) / 4096;
+    if (nblk <= 1) {
+        k_scan_block<<<1, 1024, 0, st>>>(in, out, count, nullptr);
+        return cudaGetLastError();
+    }
+    uint32_t* sums = scratch;
+    k_scan_block<<<(unsigned)nblk, 1024, 0, st>>>(in, out, count, sums);
+    cudaError_t e = scan_u32(sums, sums, nblk, scratch + nblk + 1, st);
+    if (e != cudaSuccess) return e;
+    k_scan_add<<<(unsigned)((count + 255) / 256), 256, 0, st>>>(out, count, sums);
+    return cudaGetLastError();
+}
+
+__global__ void k_scatter_unstable(const uint32_t* __restrict__ keys, int64_t count, uint32_t* __restrict__ cursor,
+                                   uint32_t* __restrict__ order) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count;
+         i += (int64_t)gridDim.x * blockDim.x)
+        order[atomicAdd(&cursor[keys[i]], 1u)] = (uint32_t)i;
+}
+
+// Within each cell the ids were placed in arbitrary order; sort them ascending
+// (Shell sort with gaps 1, 4, 13, ...), which makes the whole order stable in id.
+__global__ void k_sort_buckets(const uint32_t* __restrict__ start, const uint32_t* __restrict__ cursor, int64_t ncell,
+                               uint32_t* __restrict__ order) {
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < ncell; c += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t s = start[c], e = cursor[c];
+        const uint32_t len = e - s;
+        if (len < 2) continue;
+        uint32_t* a = order + s;
+        uint32_t gap = 1;
+        while (gap < len / 3) gap = 3 * gap + 1;
+        for (; gap > 0; gap /= 3)
+            for (uint32_t i = gap; i < len; ++i) {
+                const uint32_t v = a[i];
+                uint32_t j = i;
+                while (j >= gap && a[j - gap] > v) {
+                    a[j] = a[j - gap];
+                    j -= gap;
+                }
+                a[j] = v;
+            }
+    }
+}
+
+size_t cell_sort_scratch_bytes(int64_t count, int n) {
+    const int64_t ncell = (int64_t)n * n * n;
+    (void)count;
+    return sizeof(uint32_t) * (size_t)(3 * ncell + scan_scratch_words(ncell) + 64);
+}
+
+cudaError_t cell_sort(const void* x, int64_t count, int precision, int n, uint32_t* keys, uint32_t* order,
+                      void* scratch, cudaStream_t st) {
+    const int logn = ilog2(n);
+    const int64_t ncell = (int64_t)n * n * n;
+    uint32_t* counts = (uint32_t*)scratch;
+    uint32_t* start = counts + ncell;
+    uint32_t* cursor = start + ncell;
+    uint32_t* sc = cursor + ncell;
+    const float inv = (float)ldexp(1.0, -(32 - logn));
+    cudaError_t e;
+    if (order) {
+        e = cudaMemsetAsync(counts, 0, sizeof(uint32_t) * ncell, st);
+        if (e != cudaSuccess) return e;
+    }
+    if (count > 0)
+        k_cell_keys<<<grid_for(count, 256), 256, 0, st>>>(x, count, precision, logn, inv, keys,
+                                                          order ? counts : nullptr);
+    e = cudaGetLastError();
+    if (e != cudaSuccess || !order) return e;
+    e = scan_u32(counts, start, ncell, sc, st);
+    if (e != cudaSuccess) return e;
+    e = cudaMemcpyAsync(cursor, start, sizeof(uint32_t) * ncell, cudaMemcpyDeviceToDevice, st);
+    if (e != cudaSuccess) return e;
+    if (count > 0) k_scatter_unstable<<<grid_for(count, 256), 256, 0, st>>>(keys, count, cursor, order);
+    k_sort_buckets<<<grid_for(ncell, 256), 256, 0, st>>>(start, cursor, ncell, order);
+    return cudaGetLastError();
+}
+
+}  // namespace pm

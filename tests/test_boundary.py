@@ -1,0 +1,87 @@
+"""The C-ABI library loads, exports every symbol include/pm.h declares, and checks
+its arguments on the host (no GPU needed)."""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "pm.h")
+
+
+@pytest.fixture(scope="session")
+def pm():
+    import paper_2404_02783_gb300 as pm
+    if not os.path.exists(pm.LIB_PATH):
+        from paper_2404_02783_gb300 import build
+        build.build()
+    pm.lib()
+    return pm
+
+
+def declared_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:pm_status|const char\*)\s+(pm_\w+)\s*\(", src, flags=re.M)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for core in ("pm_init", "pm_ic_zeldovich", "pm_step", "pm_displacement_correction", "pm_power",
+                 "pm_bispectrum"):
+        assert core in names
+
+
+def test_library_exports_every_declared_symbol(pm):
+    names = declared_functions()
+    L = pm.lib()
+    for name in names:
+        assert hasattr(L, name), name
+    assert set(names) == set(pm.EXPORTS)
+    out = subprocess.run(["nm", "-D", "--defined-only", pm.LIB_PATH], capture_output=True, text=True).stdout
+    exported = set(re.findall(r" T (pm_\w+)$", out, flags=re.M))
+    assert set(names) <= exported
+
+
+def test_workspace_size_and_validation(pm):
+    cfg = pm.make_config(32, 64, 1000.0, 0.02, 1.0, 10)
+    n = pm.pm_workspace_size(cfg)
+    # particles (24 B) + 4 meshes (16 B) + 3 half spectra (24 B per cell-ish) at least
+    assert n >= 24 * 32**3 + 16 * 64**3 + 3 * 8 * 33 * 64 * 64
+    gr = pm.make_config(32, 64, 1000.0, 0.02, 1.0, 10, mode=pm.PM_GR_POISSON, n_lo=8)
+    assert pm.pm_workspace_size(gr) > n
+    f64 = pm.make_config(32, 64, 1000.0, 0.02, 1.0, 10, precision=pm.PM_FP64)
+    assert pm.pm_workspace_size(f64) > 1.9 * n
+    for bad in (pm.make_config(24, 64, 1000.0, 0.02, 1.0, 10),      # not a power of two
+                pm.make_config(64, 32, 1000.0, 0.02, 1.0, 10),      # mesh coarser than lattice
+                pm.make_config(32, 64, -1.0, 0.02, 1.0, 10),        # box
+                pm.make_config(32, 64, 1000.0, 1.0, 0.5, 10),       # a-grid
+                pm.make_config(32, 64, 1000.0, 0.02, 1.0, 0),       # steps
+                pm.make_config(32, 64, 1000.0, 0.02, 1.0, 10, mode=5),
+                pm.make_config(32, 64, 1000.0, 0.02, 1.0, 10, n_lo=40)):
+        with pytest.raises(pm.PMError) as e:
+            pm.pm_workspace_size(bad)
+        assert e.value.status == 1
+
+
+def test_stateless_calls_check_arguments_before_the_device(pm):
+    L = pm.lib()
+    assert L.pm_cic_deposit(None, 10, 0, 16, 1.0, None, None) == 1
+    assert L.pm_fft_r2c(None, None, 16, 0, None) == 1
+    assert L.pm_fft_r2c(ctypes.c_void_p(256), ctypes.c_void_p(256), 12, 0, None) == 1
+    sz = ctypes.c_size_t()
+    assert L.pm_cell_sort_scratch_size(1000, 16, ctypes.byref(sz)) == 0 and sz.value >= 3 * 16**3 * 4
+    assert "pm-gb300" in pm.pm_version()
+
+
+def test_no_cpu_fallback_without_a_device(pm):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    L = pm.lib()
+    # valid arguments but no GPU: the library refuses instead of computing on the host
+    st = L.pm_cic_deposit(ctypes.c_void_p(4096), 1, 0, 16, 1.0, ctypes.c_void_p(4096), None)
+    assert st == 6
+    assert "device" in L.pm_last_error().decode().lower()

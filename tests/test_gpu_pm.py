@@ -1,0 +1,151 @@
+"""GPU parity of the PM run: Zel'dovich ICs, density and potential, single steps,
+a full Newtonian run (32^3 particles, 20 steps to z = 0) and the Poisson-gauge mode.
+
+The oracle builds its own ICs from the same seed (Philox phases) or the same seeded
+white noise; nothing it uses comes from the GPU.
+"""
+import numpy as np
+import pytest
+
+import inputs
+from oracle import cic, gravity, ic, pm as opm, stats
+from oracle.cosmology import Cosmology
+from tests.gpu_util import lib, min_image, positions_box_units, rel_l2, ticks_to_host, to_dev, to_host, torch
+
+pytestmark = pytest.mark.gpu
+FP32, FP64 = 0, 1
+
+
+def _run(pm, np_side, nmesh, box, a_i, a_f, steps, prec, mode=0, n_lo=0):
+    cfg = pm.make_config(np_side, nmesh, box, a_i, a_f, steps, mode=mode, precision=prec, n_lo=n_lo)
+    return pm.PMRun(cfg)
+
+
+def _host_particles(run):
+    x, p = run.particles()
+    torch.cuda.synchronize()
+    xh = ticks_to_host(x) if not run.fp64 else to_host(x)
+    return xh.copy(), to_host(p).astype(np.float64).copy()
+
+
+def _disp(x, np_side):
+    """Displacement from the lattice node in box units (minimum image)."""
+    q = ic.lattice_ticks(np_side).astype(np.float64) * 2.0**-32
+    return min_image(positions_box_units(x) - q)
+
+
+@pytest.mark.parametrize("prec", [FP32, FP64])
+@pytest.mark.parametrize("source", ["philox", "white_noise", "paired"])
+def test_zeldovich_ic_matches_oracle(prec, source):
+    pm = lib()
+    np_side, nmesh, box, a_i = 32, 64, 1000.0, 1.0 / 51.0
+    run = _run(pm, np_side, nmesh, box, a_i, 1.0, 10, prec)
+    c = Cosmology()
+    kw = {}
+    if source == "white_noise":
+        w = inputs.gaussian_field(41, np_side)
+        run.ic(white_noise=to_dev(w if prec == FP64 else w.astype(np.float32)))
+        kw["white_noise"] = w if prec == FP64 else w.astype(np.float32).astype(np.float64)
+    else:
+        run.ic(seed=12345, paired=(source == "paired"))
+        kw["seed"] = 12345
+        kw["paired"] = source == "paired"
+    xg, pg = _host_particles(run)
+    xo, po = ic.zeldovich(c, np_side, box, a_i, fixed=(prec == FP32), **kw)
+    tol = 2e-6 if prec == FP32 else 1e-11
+    assert rel_l2(_disp(xg, np_side), _disp(xo, np_side)) < tol
+    assert rel_l2(pg, po) < tol
+    assert run.state() == (0, a_i, True)
+
+
+@pytest.mark.parametrize("prec", [FP32, FP64])
+def test_density_and_potential_after_one_step(prec):
+    pm = lib()
+    np_side, nmesh, box, a_i, a_f, steps = 32, 64, 500.0, 0.1, 1.0, 10
+    run = _run(pm, np_side, nmesh, box, a_i, a_f, steps, prec)
+    run.ic(seed=5)
+    run.step(1)
+    delta_g = to_host(run.density()).astype(np.float64)
+    phi_g = to_host(run.potential()).astype(np.float64)
+    c = Cosmology()
+    x0, p0 = ic.zeldovich(c, np_side, box, a_i, seed=5, fixed=(prec == FP32))
+    ref = opm.PMRun(c, nmesh, box, a_i, a_f, steps, x0, p0)
+    ref.step(1)
+    delta_o = cic.density_contrast(ref.x, nmesh)
+    phi_o = gravity.potential_mesh(gravity.newton_potential_k(np.fft.rfftn(delta_o), nmesh, box, c.omega_m), nmesh)
+    tol = 1e-5 if prec == FP32 else 1e-11
+    assert rel_l2(delta_g, delta_o) < tol
+    assert rel_l2(phi_g, phi_o) < tol
+    xg, pg = _host_particles(run)
+    assert rel_l2(min_image(positions_box_units(xg) - positions_box_units(x0)),
+                  min_image(positions_box_units(ref.x) - positions_box_units(x0))) < tol
+    assert rel_l2(pg, ref.p) < tol
+
+
+@pytest.mark.parametrize("prec", [FP32, FP64])
+def test_full_run_power_spectrum(prec):
+    # 32^3 particles on a 32^3 mesh, L = 2000 Mpc/h, ZA at z = 50, 20 KDK steps to z = 0,
+    # P(k) in 16 log bins on [k_f, k_Ny].
+    pm = lib()
+    np_side = nmesh = 32
+    box, a_i, a_f, steps = 2000.0, 1.0 / 51.0, 1.0, 20
+    run = _run(pm, np_side, nmesh, box, a_i, a_f, steps, prec)
+    run.ic(seed=1)
+    run.step(steps)
+    assert run.state() == (steps, a_f, True)
+    edges = stats.log_edges(16, 1.0, nmesh / 2.0)
+    kg, pg, ng = run.power(edges)
+    c = Cosmology()
+    x0, p0 = ic.zeldovich(c, np_side, box, a_i, seed=1, fixed=(prec == FP32))
+    ref = opm.PMRun(c, nmesh, box, a_i, a_f, steps, x0, p0)
+    ref.step(steps)
+    ko, po, no = stats.power_spectrum(cic.density_contrast(ref.x, nmesh), box, edges)
+    np.testing.assert_array_equal(ng, no)
+    ok = no > 0
+    assert np.max(np.abs(pg[ok] / po[ok] - 1)) < (1e-3 if prec == FP32 else 1e-9)
+    assert np.max(np.abs(kg[ok] / ko[ok] - 1)) < 1e-12
+    xg, pgm = _host_particles(run)
+    assert np.max(np.abs(min_image(positions_box_units(xg) - positions_box_units(ref.x)))) * box < \
+        (0.05 if prec == FP32 else 1e-8)
+    # momentum is conserved by the CIC + symmetric Green's function + odd gradient
+    assert np.max(np.abs(pgm.sum(axis=1) - p0.sum(axis=1))) < (1e-4 if prec == FP32 else 1e-9) * np.abs(pgm).sum()
+
+
+def test_stepping_past_the_grid_is_refused():
+    pm = lib()
+    run = _run(pm, 16, 16, 100.0, 0.5, 1.0, 2, FP32)
+    run.ic(seed=3)
+    run.step(2)
+    with pytest.raises(pm.PMError) as e:
+        run.step(1)
+    assert e.value.status == 7
+
+
+@pytest.mark.parametrize("prec", [FP32, FP64])
+def test_poisson_gauge_run_matches_oracle(prec):
+    # horizon-scale box (L = 20 Gpc/h, 16^3 particles on a 32^3 mesh, z = 100 -> 1): the GR run
+    # departs from the Newtonian one; both sides solve the lagged linear constraint.
+    pm = lib()
+    np_side, nmesh, box, a_i, a_f, steps = 16, 32, 20000.0, 1.0 / 101.0, 1.0, 12
+    c = Cosmology()
+    x0, p0 = ic.zeldovich(c, np_side, box, a_i, seed=21, fixed=(prec == FP32))
+    ref_gr = opm.PMRun(c, nmesh, box, a_i, a_f, steps, x0, p0, mode=opm.GR_POISSON)
+    ref_gr.step(steps)
+    ref_n = opm.PMRun(c, nmesh, box, a_i, a_f, steps, x0, p0, mode=opm.NEWTON)
+    ref_n.step(steps)
+    out = {}
+    for mode, n_lo in ((1, 4), (1, 0), (0, 0)):
+        run = _run(pm, np_side, nmesh, box, a_i, a_f, steps, prec, mode=mode, n_lo=n_lo)
+        run.ic(seed=21)
+        run.step(steps)
+        out[(mode, n_lo)] = _host_particles(run)
+    xi_o = min_image(positions_box_units(ref_gr.x) - positions_box_units(ref_n.x))
+    assert np.max(np.abs(xi_o)) * box > 1e-3  # the GR displacement is not negligible here
+    for key in ((1, 4), (1, 0)):
+        xg, pg = out[key]
+        xn, _ = out[(0, 0)]
+        xi_g = min_image(positions_box_units(xg) - positions_box_units(xn))
+        assert rel_l2(xi_g, xi_o) < (2e-3 if prec == FP32 else 1e-9)
+        d_g = min_image(positions_box_units(xg) - positions_box_units(x0))
+        d_o = min_image(positions_box_units(ref_gr.x) - positions_box_units(x0))
+        assert rel_l2(d_g, d_o) < (1e-5 if prec == FP32 else 1e-11)
