@@ -1,0 +1,370 @@
+#!/usr/bin/env python
+"""PM particle-steps/s and fraction of the HBM roofline at 512^3 on GB300 (FP32 vs FP64 plain).
+
+Workload: 512^3 particles on a 512^3 CIC mesh, L = 5000 Mpc/h, Newtonian PM from
+Zel'dovich ICs at z = 50 (Lambda-CDM, Eisenstein-Hu no-wiggle P(k), sigma_8 = 0.81),
+kick-drift-kick steps on a uniform a-grid to z = 0.  A step is one force evaluation
+plus update: CIC deposit, r2c FFT, Green's function and spectral gradient, c2r FFT,
+CIC interpolation + kick + drift.  Inputs (3.2 GB of particles, 0.5 GB per mesh) are
+larger than L2, so no flush is needed between steps.
+
+Prints one JSON line (rank 0).  Under torchrun every rank runs an independent
+realisation (replicas, no collective on the data path); value sums over ranks and
+time is the maximum over ranks.
+
+--impl reference times the FP64 CPU oracle (oracle/) on this host's cores on a
+bounded sample of the same workload.
+"""
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "PM particle-steps/s and fraction of HBM roofline at 512^3, FP32 vs FP64 plain"
+UNIT = "particle-steps/s"
+A_INIT, A_FINAL = 1.0 / 51.0, 1.0
+PHASES = ("deposit", "fft_z_r2c", "fft_y_fwd", "fft_x_green", "fft_y_grad", "fft_z_c2r", "kick_drift")
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def kernel_bytes(np_side, n, fp64):
+    """Algorithmic bytes per launch of each phase (each array it must touch, once)."""
+    s = 8 if fp64 else 4
+    P = np_side**3
+    R = n**3 * s
+    S = (n // 2 + 1) * n * n * 2 * s
+    return {
+        "deposit": 3 * s * P + R,            # read x, write rho
+        "fft_z_r2c": R + S,                  # read rho, write half spectrum
+        "fft_y_fwd": 2 * S,
+        "fft_x_green": 3 * S,                # read delta_k, write IFFT_x(phi), IFFT_x(-i kx phi)
+        "fft_y_grad": 5 * S,                 # read 2, write 3
+        "fft_z_c2r": 3 * S + 3 * R,          # read 3 spectra, write 3 force meshes
+        "kick_drift": 12 * s * P + 3 * R,    # read + write x, p; gather 3 meshes once
+    }
+
+
+def step_bytes(np_side, n, fp64):
+    """Algorithmic bytes of one whole PM step: 60 B/particle + 40 B/cell (x2 in FP64)."""
+    f = 2 if fp64 else 1
+    return f * (60 * np_side**3 + 40 * n**3)
+
+
+def csrc_sha():
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_2404_02783_gb300", "csrc")
+    for name in sorted(os.listdir(d)):
+        with open(os.path.join(d, name), "rb") as f:
+            h.update(name.encode() + f.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel):
+    """DRAM bytes per launch from the committed ncu summary, if it matches the current kernels."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        d = json.load(f)
+    if d.get("source_sha") != csrc_sha():
+        return None
+    v = d.get("bytes_per_launch", {}).get(kernel)
+    return None if v is None else float(v)
+
+
+class Clocks:
+    """nvidia-smi sampler running across the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.rows = []
+        self.proc = None
+        self.t0 = self.t1 = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                          "-i", str(self.index), "-lms", "50"], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+        except (OSError, ValueError):
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+        time.sleep(0.3)
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append((time.time(), [c.strip() for c in line.split(",")]))
+
+    def mark(self, which):
+        setattr(self, which, time.time())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        time.sleep(0.2)
+        self.proc.terminate()
+        self.proc.wait(timeout=5)
+        rows = [r for t, r in self.rows if self.t0 - 0.06 <= t <= self.t1 + 0.06] or [r for _, r in self.rows]
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+            except (ValueError, IndexError):
+                continue
+            for name, v in zip(names, r[5:9]):
+                if v.strip().lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(v, world):
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def time_steps(pm, torch, run, k, world):
+    """CUDA-event time (ms) of k steps on the library's stream (the current torch stream)."""
+    st = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier(world)
+    torch.cuda.synchronize()
+    e0.record(st)
+    run.step(k)
+    e1.record(st)
+    e1.synchronize()
+    torch.cuda.synchronize()
+    barrier(world)
+    return e0.elapsed_time(e1)
+
+
+def bench_precision(pm, torch, args, prec, rank, world, clocks=None):
+    fp64 = prec == pm.PM_FP64
+    n_steps = max(100, args.warmup + 2 * args.steps + 2)
+    cfg = pm.make_config(args.np, args.nmesh, args.box, A_INIT, A_FINAL, n_steps, precision=prec)
+    run = pm.PMRun(cfg)
+    run.ic(seed=1 + rank)
+    run.step(args.warmup)
+    torch.cuda.synchronize()
+    if clocks:
+        clocks.mark("t0")
+    ms = time_steps(pm, torch, run, args.steps, world)
+    if clocks:
+        clocks.mark("t1")
+    ms = max_over_ranks(ms, world)
+    # same number of steps again with per-phase events for the kernel roofline
+    pm.pm_profile(run.ctx, True)
+    pm.pm_timings(run.ctx)
+    run.step(args.steps)
+    phases = pm.pm_timings(run.ctx)
+    pm.pm_profile(run.ctx, False)
+    del run
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    return ms, phases, n_steps
+
+
+def roofline(phases, np_side, n, fp64, peak, peak_kind):
+    kb = kernel_bytes(np_side, n, fp64)
+    dom = max(PHASES, key=lambda p: phases[p][0])
+    ms, launches = phases[dom]
+    per_launch_ms = ms / max(launches, 1)
+    achieved = kb[dom] / (per_launch_ms * 1e-3) / 1e9
+    table = {}
+    for p in PHASES:
+        t, c = phases[p]
+        pl = t / max(c, 1)
+        table[p] = {"ms_per_launch": round(pl, 4), "launches": c,
+                    "GBps": round(kb[p] / (pl * 1e-3) / 1e9, 1) if pl > 0 else None,
+                    "frac": round(kb[p] / (pl * 1e-3) / 1e9 / peak, 4) if pl > 0 else None}
+    return {"kernel": dom, "bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+            "frac": round(achieved / peak, 4), "traffic": ncu_traffic(dom), "algorithmic_bytes": kb[dom],
+            "peak_source": f"{peak_kind} hbm_gbs (MEASURED_PEAKS.json)" if peak_kind == "measured" else "fallback"}, table
+
+
+def e2e(pm, torch, args, rank, world, n_jobs=2):
+    """Public-API end to end: ICs from pinned host memory -> k steps -> P(k) back to the host."""
+    n_steps = max(100, args.steps + 2)
+    cfg = pm.make_config(args.np, args.nmesh, args.box, A_INIT, A_FINAL, n_steps)
+    run = pm.PMRun(cfg)
+    run.ic(seed=1 + rank)
+    x0, p0 = run.particles()
+    x_h = torch.empty_like(x0, device="cpu").pin_memory()
+    p_h = torch.empty_like(p0, device="cpu").pin_memory()
+    x_h.copy_(x0)
+    p_h.copy_(p0)
+    x = torch.empty_like(x0)
+    p = torch.empty_like(p0)
+    torch.cuda.synchronize()
+    import numpy as np
+    edges = np.geomspace(1.0, args.nmesh / 2.0, 65)
+    times = []
+    for _ in range(n_jobs):
+        barrier(world)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        x.copy_(x_h, non_blocking=True)
+        p.copy_(p_h, non_blocking=True)
+        pm.pm_set_particles(run.ctx, x, p)
+        run.step(args.steps)
+        k, pk, nm = run.power(edges)  # synchronises and copies P(k) to the host
+        times.append(time.perf_counter() - t0)
+    t = max_over_ranks(min(times), world)
+    h2d = (x.numel() * x.element_size() + p.numel() * p.element_size()) / args.steps
+    d2h = 3 * (len(edges) - 1) * 8 / args.steps
+    del run
+    torch.cuda.empty_cache()
+    return {"value": world * args.np**3 * args.steps / t, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+            "d2h_bytes_per_step": int(d2h),
+            "what": "IC particles copied from pinned host memory, k PM steps, P(k) (64 bins) read back"}
+
+
+def cpu_oracle(seconds, np_side=64):
+    """The FP64 oracle on this host: a 64^3 sample of the workload at the same mesh spacing."""
+    import numpy as np
+    from oracle import ic, pm as opm
+    from oracle.cosmology import Cosmology
+    box = 5000.0 * np_side / 512.0
+    c = Cosmology()
+    x, p = ic.zeldovich(c, np_side, box, A_INIT, seed=1, fixed=True)
+    run = opm.PMRun(c, np_side, box, A_INIT, A_FINAL, 100, x, p)
+    t0 = time.perf_counter()
+    steps = 0
+    while steps < 99 and (time.perf_counter() - t0 < seconds or steps < 2):
+        run.step(1)
+        steps += 1
+    dt = time.perf_counter() - t0
+    return {"value": np_side**3 * steps / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{np_side}^3 particles on a {np_side}^3 mesh, L={box:g} Mpc/h (same cell size), "
+                      f"{steps} KDK steps from z=50, FP64 numpy oracle, single thread, {dt:.1f} s"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--np", type=int, default=512)
+    ap.add_argument("--nmesh", type=int, default=512)
+    ap.add_argument("--box", type=float, default=5000.0)
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("at least 3 warm-up steps")
+    world, rank, local = dist_setup()
+    workload = (f"{args.np}^3 particles, {args.nmesh}^3 CIC mesh, L={args.box:g} Mpc/h, Newtonian PM, "
+                f"ZA ICs at z=50, KDK on a uniform a-grid to z=0 (LCDM Om=0.31, EH no-wiggle, sigma8=0.81)")
+    config = {"workload": workload, "np": args.np, "nmesh": args.nmesh, "box_mpc_h": args.box,
+              "positions": "uint32 fixed point", "parallelism": f"replicas x{world}",
+              "l2": "inputs larger than L2 (3.2 GB particles, 0.5 GB per mesh); no flush"}
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        ms_t0 = time.perf_counter()
+        cb = cpu_oracle(max(args.cpu_seconds, 5.0))
+        total = time.perf_counter() - ms_t0
+        line = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": UNIT, "n_gpus": args.gpus,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * args.np**3 / cb["value"],
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                "data": "synthetic (seeded Philox phases)", "config": config,
+                "cpu_baseline": {**cb}, "e2e": {"value": cb["value"], "unit": UNIT, "h2d_bytes_per_step": 0,
+                                                "d2h_bytes_per_step": 0},
+                "note": f"FP64 CPU oracle timed on a bounded sample ({total:.1f} s wall)"}
+        print(json.dumps(line))
+        return
+
+    import torch
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group(backend="nccl")
+    else:
+        torch.cuda.set_device(0)
+    import paper_2404_02783_gb300 as pm
+    pm.lib()
+    peak, peak_kind = peaks()
+    clocks = Clocks(local if world > 1 else 0)
+    clocks.start()
+    ms32, ph32, n_steps = bench_precision(pm, torch, args, pm.PM_FP32_FIXED, rank, world, clocks)
+    clk = clocks.stop()
+    value = world * args.np**3 * args.steps / (ms32 * 1e-3)
+    ms_step = ms32 / args.steps
+    roof, table32 = roofline(ph32, args.np, args.nmesh, False, peak, peak_kind)
+    sb = step_bytes(args.np, args.nmesh, False)
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded Philox phases, EH no-wiggle LCDM)",
+           "config": {**config, "a_grid_steps": n_steps}, "clocks": clk,
+           "gpu_launches": 7 * args.steps,
+           "roofline": roof,
+           "step_roofline": {"bytes_per_step": sb, "achieved": round(sb / (ms_step * 1e-3) / 1e9, 1),
+                             "peak": peak, "unit": "GB/s", "frac": round(sb / (ms_step * 1e-3) / 1e9 / peak, 4),
+                             "bytes_model": "60 B/particle + 40 B/cell"},
+           "phases_fp32": table32}
+    if not args.no_fp64:
+        ms64, ph64, _ = bench_precision(pm, torch, args, pm.PM_FP64, rank, world)
+        sb64 = step_bytes(args.np, args.nmesh, True)
+        roof64, table64 = roofline(ph64, args.np, args.nmesh, True, peak, peak_kind)
+        out["fp64_plain"] = {"value": world * args.np**3 * args.steps / (ms64 * 1e-3), "unit": UNIT,
+                             "ms_per_step": ms64 / args.steps,
+                             "step_roofline_frac": round(sb64 / (ms64 / args.steps * 1e-3) / 1e9 / peak, 4),
+                             "dominant": roof64, "phases": table64}
+    if not args.no_e2e:
+        out["e2e"] = e2e(pm, torch, args, rank, world)
+    if rank == 0:
+        out["cpu_baseline"] = cpu_oracle(args.cpu_seconds)
+        print(json.dumps(out))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

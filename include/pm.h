@@ -132,6 +132,24 @@ pm_status pm_set_particles(pm_ctx* ctx, const void* x, const void* p);
  * behind (0). */
 pm_status pm_state(pm_ctx* ctx, int* step, double* a, int* synchronised);
 
+/* Per-phase device timing of pm_step with CUDA events recorded on the context
+ * stream around each kernel of a force evaluation and update.  pm_profile(ctx, 1)
+ * starts recording (0 stops); pm_timings synchronises the stream, writes the summed
+ * milliseconds and the number of timed launches per phase since the previous call
+ * into caller arrays of PM_NPHASES entries, and resets the counters. */
+enum {
+    PM_PHASE_DEPOSIT = 0,      /* zeroing + CIC deposit */
+    PM_PHASE_FFT_Z_R2C = 1,    /* z pass, real to half spectrum */
+    PM_PHASE_FFT_Y_FWD = 2,    /* forward y pass */
+    PM_PHASE_FFT_X_GREEN = 3,  /* x pass with Green's function / constraint and x gradient */
+    PM_PHASE_FFT_Y_GRAD = 4,   /* inverse y pass with y gradient */
+    PM_PHASE_FFT_Z_C2R = 5,    /* inverse z pass of the three force components */
+    PM_PHASE_KICK_DRIFT = 6,   /* CIC interpolation + kick + drift */
+    PM_NPHASES = 7
+};
+pm_status pm_profile(pm_ctx* ctx, int enable);
+pm_status pm_timings(pm_ctx* ctx, double* ms, int64_t* launches);
+
 /* CIC counting density contrast delta = rho / rho_bar - 1 of the current particles
  * on the context mesh (Sec. 4), written to the device mesh delta[n][n][n]. */
 pm_status pm_density(pm_ctx* ctx, void* delta);

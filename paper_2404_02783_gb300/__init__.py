@@ -26,7 +26,7 @@ _STATUS = {0: "PM_OK", 1: "PM_ERR_INVALID_ARG", 2: "PM_ERR_CUDA", 3: "PM_ERR_WOR
 
 # every entry point declared in include/pm.h
 EXPORTS = ("pm_workspace_size", "pm_init", "pm_destroy", "pm_ic_zeldovich", "pm_step", "pm_particles",
-           "pm_set_particles", "pm_state", "pm_density", "pm_potential", "pm_displacement_correction", "pm_power",
+           "pm_set_particles", "pm_state", "pm_profile", "pm_timings", "pm_density", "pm_potential", "pm_displacement_correction", "pm_power",
            "pm_bispectrum_scratch_size", "pm_bispectrum", "pm_cic_deposit", "pm_cic_interp",
            "pm_cell_sort_scratch_size", "pm_cell_sort", "pm_fft_r2c", "pm_fft_c2r", "pm_version", "pm_last_error")
 
@@ -77,6 +77,8 @@ def lib():
         "pm_particles": (vp, ctypes.POINTER(vp), ctypes.POINTER(vp)),
         "pm_set_particles": (vp, vp, vp),
         "pm_state": (vp, ctypes.POINTER(i), pd, ctypes.POINTER(i)),
+        "pm_profile": (vp, i),
+        "pm_timings": (vp, pd, ctypes.POINTER(i64)),
         "pm_density": (vp, vp),
         "pm_potential": (vp, vp),
         "pm_displacement_correction": (vp, vp, vp, vp),
@@ -171,6 +173,21 @@ def pm_state(ctx):
     s, a, y = ctypes.c_int(), ctypes.c_double(), ctypes.c_int()
     _check(lib().pm_state(ctx, ctypes.byref(s), ctypes.byref(a), ctypes.byref(y)))
     return s.value, a.value, bool(y.value)
+
+
+PHASES = ("deposit", "fft_z_r2c", "fft_y_fwd", "fft_x_green", "fft_y_grad", "fft_z_c2r", "kick_drift")
+
+
+def pm_profile(ctx, enable=True):
+    _check(lib().pm_profile(ctx, int(bool(enable))))
+
+
+def pm_timings(ctx):
+    """{phase: (ms, launches)} summed since the previous call (synchronises)."""
+    ms = np.zeros(len(PHASES))
+    n = np.zeros(len(PHASES), dtype=np.int64)
+    _check(lib().pm_timings(ctx, _dptr(ms), n.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))))
+    return {name: (float(ms[i]), int(n[i])) for i, name in enumerate(PHASES)}
 
 
 def pm_density(ctx, out):

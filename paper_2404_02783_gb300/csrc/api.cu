@@ -119,6 +119,31 @@ struct pm_ctx {
     bool synced = true;
     bool have_phi = false;
     double a_last = 0.0;
+    // per-phase timing (pm_profile / pm_timings)
+    bool prof = false;
+    std::vector<cudaEvent_t> pool;
+    struct Rec {
+        int phase;
+        cudaEvent_t a, b;
+    };
+    std::vector<Rec> recs;
+    cudaEvent_t take_event() {
+        if (!pool.empty()) {
+            cudaEvent_t e = pool.back();
+            pool.pop_back();
+            return e;
+        }
+        cudaEvent_t e = nullptr;
+        cudaEventCreate(&e);
+        return e;
+    }
+    ~pm_ctx() {
+        for (auto& r : recs) {
+            cudaEventDestroy(r.a);
+            cudaEventDestroy(r.b);
+        }
+        for (auto e : pool) cudaEventDestroy(e);
+    }
     void* at(size_t off) const { return ws + off; }
     double a_grid(int i) const { return cfg.a_init + ((cfg.a_final - cfg.a_init) * i) / cfg.n_steps; }
     bool fp64() const { return cfg.precision == PM_FP64; }
@@ -127,15 +152,40 @@ struct pm_ctx {
 
 namespace {
 
+// Records a CUDA event pair around one phase when profiling is on.
+struct Phase {
+    pm_ctx* c;
+    int id;
+    cudaEvent_t a = nullptr;
+    Phase(pm_ctx* ctx, int phase) : c(ctx), id(phase) {
+        if (c->prof) {
+            a = c->take_event();
+            cudaEventRecord(a, c->st);
+        }
+    }
+    ~Phase() {
+        if (a) {
+            cudaEvent_t b = c->take_event();
+            cudaEventRecord(b, c->st);
+            c->recs.push_back({id, a, b});
+        }
+    }
+};
+
 template <typename T>
 pm_status forward_to_y(pm_ctx* c, const void* real, void* spec, int n) {
-    PM_CK(z_r2c<T>((const T*)real, (cplx<T>*)spec, n, 1, c->st));
+    {
+        Phase ph(c, PM_PHASE_FFT_Z_R2C);
+        PM_CK(z_r2c<T>((const T*)real, (cplx<T>*)spec, n, 1, c->st));
+    }
+    Phase ph(c, PM_PHASE_FFT_Y_FWD);
     PM_CK((y_rows<T, false>((cplx<T>*)spec, (int64_t)(n / 2 + 1) * n, n, c->st)));
     return PM_OK;
 }
 
 // Counting density of the context's particles (mass (n/np)^3 per particle) on rho.
 pm_status deposit_particles(pm_ctx* c, void* rho) {
+    Phase ph(c, PM_PHASE_DEPOSIT);
     PM_CK(cudaMemsetAsync(rho, 0, c->sT() * (size_t)c->n * c->n * c->n, c->st));
     const double mass = std::pow((double)c->n / c->np, 3);
     PM_CK(deposit(c->at(c->L.x), c->np3, c->cfg.precision, c->n, mass, rho, c->st));
@@ -170,11 +220,20 @@ pm_status compute_forces_t(pm_ctx* c, double a) {
         op.phi_old = c->at(c->L.phi_old);
         op.island = c->L.has_island ? (double2*)c->at(c->L.island) : nullptr;
     }
-    PM_CK(x_cols<T>(s0, s1, n / 2 + 1, n, op, c->st));
-    PM_CK(y_rows_grad3<T>(s0, s1, s2, (int64_t)(n / 2 + 1) * n, n, c->kf, c->st));
-    const cplx<T>* in[3] = {s1, s2, s0};
-    T* out[3] = {(T*)c->at(c->L.force[0]), (T*)c->at(c->L.force[1]), (T*)c->at(c->L.force[2])};
-    PM_CK(z_c2r<T>(in, out, 3, n, 1, 4u, c->kf, c->st));
+    {
+        Phase ph(c, PM_PHASE_FFT_X_GREEN);
+        PM_CK(x_cols<T>(s0, s1, n / 2 + 1, n, op, c->st));
+    }
+    {
+        Phase ph(c, PM_PHASE_FFT_Y_GRAD);
+        PM_CK(y_rows_grad3<T>(s0, s1, s2, (int64_t)(n / 2 + 1) * n, n, c->kf, c->st));
+    }
+    {
+        Phase ph(c, PM_PHASE_FFT_Z_C2R);
+        const cplx<T>* in[3] = {s1, s2, s0};
+        T* out[3] = {(T*)c->at(c->L.force[0]), (T*)c->at(c->L.force[1]), (T*)c->at(c->L.force[2])};
+        PM_CK(z_c2r<T>(in, out, 3, n, 1, 4u, c->kf, c->st));
+    }
     if (c->cfg.mode == PM_GR_POISSON) {
         c->have_phi = true;
         c->a_last = a;
@@ -187,6 +246,7 @@ pm_status compute_forces(pm_ctx* c, double a) {
 }
 
 pm_status kick_drift(pm_ctx* c, double kick, double drift) {
+    Phase ph(c, PM_PHASE_KICK_DRIFT);
     void* g[3] = {c->at(c->L.force[0]), c->at(c->L.force[1]), c->at(c->L.force[2])};
     PM_CK(interp_kick_drift(c->at(c->L.x), c->at(c->L.p), c->np3, c->cfg.precision, c->n, g, kick, drift,
                             c->cfg.box, c->st));
@@ -512,6 +572,33 @@ pm_status pm_step(pm_ctx* c, int n_steps) {
             PM_TRY(kick_drift(c, pmhost::kick_integral(c->cosmo, ah, a1), 0.0));
             c->synced = true;
         }
+    }
+    return PM_OK;
+}
+
+pm_status pm_profile(pm_ctx* c, int enable) {
+    if (!c) return fail(PM_ERR_INVALID_ARG, "null context");
+    c->prof = enable != 0;
+    return PM_OK;
+}
+
+pm_status pm_timings(pm_ctx* c, double* ms, int64_t* launches) {
+    if (!c) return fail(PM_ERR_INVALID_ARG, "null context");
+    PM_CK(cudaStreamSynchronize(c->st));
+    double acc[PM_NPHASES] = {0};
+    int64_t cnt[PM_NPHASES] = {0};
+    for (auto& r : c->recs) {
+        float t = 0.0f;
+        PM_CK(cudaEventElapsedTime(&t, r.a, r.b));
+        acc[r.phase] += t;
+        cnt[r.phase] += 1;
+        c->pool.push_back(r.a);
+        c->pool.push_back(r.b);
+    }
+    c->recs.clear();
+    for (int i = 0; i < PM_NPHASES; ++i) {
+        if (ms) ms[i] = acc[i];
+        if (launches) launches[i] = cnt[i];
     }
     return PM_OK;
 }
