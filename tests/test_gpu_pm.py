@@ -151,4 +151,6 @@ def test_poisson_gauge_run_matches_oracle(prec):
         assert rel_l2(xi_g, xi_o) < (2e-2 if prec == FP32 else 1e-9)
         d_g = min_image(positions_box_units(xg) - positions_box_units(x0))
         d_o = min_image(positions_box_units(ref_gr.x) - positions_box_units(x0))
-        assert rel_l2(d_g, d_o) < (1e-5 if prec == FP32 else 1e-11)
+        # FP32 stores rho ~ 1 + delta and resolves delta to ~6e-8; with delta ~ 1e-4 on these
+        # Gpc-sized cells at z = 100 the FP32 forces, hence displacements, carry ~1e-3 errors
+        assert rel_l2(d_g, d_o) < (3e-3 if prec == FP32 else 1e-11)
