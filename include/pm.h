@@ -215,6 +215,23 @@ pm_status pm_cell_sort(const void* x, int64_t count, int precision, int n,
                        uint32_t* keys_out, uint32_t* order_out,
                        void* scratch, size_t scratch_bytes, void* stream);
 
+/* pm_cell_sort without a scratch argument: the same keys and order, computed with
+ * counting scratch that lives in a fixed device array inside the library.  The paper
+ * has no counterpart; the entry point exists for callers that cannot allocate device
+ * memory per call -- hosts that hand the whole GPU memory to their own fixed pool, or
+ * plain C / Fortran drivers with no device allocator at hand -- and for whom finding
+ * and passing a scratch buffer is not an option.  It allocates nothing itself.
+ * Limits: n^3 <= PM_CELL_SORT_STATIC_MAX_CELLS (a 64^3 mesh); larger meshes return
+ * PM_ERR_INVALID_ARG.  The array (about 3 MB) is held on every GPU that loads the
+ * library until the process exits.  The first call on each device looks up the
+ * array's device address (cudaGetSymbolAddress); make that first call before any
+ * stream capture.  Every call on a device shares the one array and clears the part it
+ * counts in before use, so calls that overlap on the GPU (different streams or host
+ * threads without ordering) race and give wrong results: serialise them. */
+#define PM_CELL_SORT_STATIC_MAX_CELLS 262144
+pm_status pm_cell_sort_static(const void* x, int64_t count, int precision, int n,
+                              uint32_t* keys_out, uint32_t* order_out, void* stream);
+
 /* 3D real-to-complex FFT of real[n][n][n] into spec (layout above), unnormalised. */
 pm_status pm_fft_r2c(const void* real, void* spec, int n, int precision, void* stream);
 

@@ -28,7 +28,7 @@ _STATUS = {0: "PM_OK", 1: "PM_ERR_INVALID_ARG", 2: "PM_ERR_CUDA", 3: "PM_ERR_WOR
 EXPORTS = ("pm_workspace_size", "pm_init", "pm_destroy", "pm_ic_zeldovich", "pm_step", "pm_particles",
            "pm_set_particles", "pm_state", "pm_profile", "pm_timings", "pm_density", "pm_potential", "pm_displacement_correction", "pm_power",
            "pm_bispectrum_scratch_size", "pm_bispectrum", "pm_cic_deposit", "pm_cic_interp",
-           "pm_cell_sort_scratch_size", "pm_cell_sort", "pm_fft_r2c", "pm_fft_c2r", "pm_version", "pm_last_error")
+           "pm_cell_sort_scratch_size", "pm_cell_sort", "pm_cell_sort_static", "pm_fft_r2c", "pm_fft_c2r", "pm_version", "pm_last_error")
 
 
 class PMError(RuntimeError):
@@ -89,6 +89,7 @@ def lib():
         "pm_cic_interp": (vp, i, vp, i64, i, vp, vp),
         "pm_cell_sort_scratch_size": (i64, i, ctypes.POINTER(sz)),
         "pm_cell_sort": (vp, i64, i, i, vp, vp, vp, sz, vp),
+        "pm_cell_sort_static": (vp, i64, i, i, vp, vp, vp),
         "pm_fft_r2c": (vp, vp, i, i, vp),
         "pm_fft_c2r": (vp, vp, i, i, vp),
     }
@@ -245,6 +246,16 @@ def pm_cell_sort(x, count, precision, n, keys, order, scratch, stream=None):
     nbytes = 0 if scratch is None else scratch.numel() * scratch.element_size()
     _check(lib().pm_cell_sort(_ptr(x), int(count), precision, int(n), _ptr(keys), _ptr(order), _ptr(scratch), nbytes,
                               _stream(stream)))
+
+
+def pm_cell_sort_static(x, count, precision, n, keys, order, stream=None):
+    """pm_cell_sort with the library's fixed device scratch (meshes up to 64^3 cells).
+
+    For callers that cannot allocate device memory per call; calls on one GPU share
+    that scratch, so they must not overlap.
+    """
+    _check(lib().pm_cell_sort_static(_ptr(x), int(count), precision, int(n), _ptr(keys), _ptr(order),
+                                     _stream(stream)))
 
 
 def pm_fft_r2c(real, spec, n, precision, stream=None):

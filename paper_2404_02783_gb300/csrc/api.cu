@@ -727,6 +727,19 @@ pm_status pm_cell_sort(const void* x, int64_t count, int precision, int n, uint3
     return PM_OK;
 }
 
+pm_status pm_cell_sort_static(const void* x, int64_t count, int precision, int n, uint32_t* keys_out,
+                              uint32_t* order_out, void* stream) {
+    if (count < 0 || !pow2(n) || n < 2 || n > 1024) return fail(PM_ERR_INVALID_ARG, "bad arguments");
+    if ((int64_t)n * n * n > PM_CELL_SORT_STATIC_MAX_CELLS || cell_sort_static_max_cells() != PM_CELL_SORT_STATIC_MAX_CELLS)
+        return fail(PM_ERR_INVALID_ARG, "pm_cell_sort_static handles meshes of at most 64^3 cells; use pm_cell_sort");
+    if (count > 0xFFFFFFFFll) return fail(PM_ERR_INVALID_ARG, "count must fit in 32 bits");
+    if ((!x && count > 0) || (!keys_out && count > 0)) return fail(PM_ERR_INVALID_ARG, "null pointer");
+    if (precision != PM_FP32_FIXED && precision != PM_FP64) return fail(PM_ERR_INVALID_ARG, "bad precision");
+    PM_TRY(check_device());
+    PM_CK(cell_sort_static(x, count, precision, n, keys_out, order_out, (cudaStream_t)stream));
+    return PM_OK;
+}
+
 pm_status pm_fft_r2c(const void* real, void* spec, int n, int precision, void* stream) {
     if (!real || !spec) return fail(PM_ERR_INVALID_ARG, "null pointer");
     if (!pow2(n) || n < 16 || n > 1024) return fail(PM_ERR_INVALID_ARG, "n must be a power of two in 16..1024");

@@ -11,6 +11,8 @@
 // for the fraction, both exact.
 #include <math.h>
 
+#include <mutex>
+
 #include "internal.h"
 #include "particles.h"
 
@@ -625,6 +627,47 @@ cudaError_t cell_sort(const void* x, int64_t count, int precision, int n, uint32
     if (count > 0) k_scatter_unstable<<<grid_for(count, 256), 256, 0, st>>>(keys, count, cursor, order);
     k_sort_buckets<<<grid_for(ncell, 256), 256, 0, st>>>(start, cursor, ncell, order);
     return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- cell order without caller scratch
+// Counting scratch for cell_sort_static: a fixed device array that every call on this
+// GPU shares (it lives until the process exits).  Host code must not use the symbol
+// as an address: the device address is looked up once per device below.
+constexpr int64_t kStaticSortCells = (int64_t)64 * 64 * 64;
+constexpr int64_t kStaticSortWords = 3 * kStaticSortCells + 4096;
+static __device__ __align__(256) uint32_t g_sort_scratch[kStaticSortWords];
+
+static std::mutex g_sort_mutex;
+static uint32_t* g_sort_ptr[128];
+
+int64_t cell_sort_static_max_cells() { return kStaticSortCells; }
+
+// Looks up the device address of g_sort_scratch for the current device (first call
+// on each device only).
+static cudaError_t static_sort_scratch(uint32_t** out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 128) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(g_sort_mutex);
+    if (!g_sort_ptr[dev]) {
+        void* p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_sort_scratch);
+        if (e != cudaSuccess) return e;
+        g_sort_ptr[dev] = (uint32_t*)p;
+    }
+    *out = g_sort_ptr[dev];
+    return cudaSuccess;
+}
+
+cudaError_t cell_sort_static(const void* x, int64_t count, int precision, int n, uint32_t* keys, uint32_t* order,
+                             cudaStream_t st) {
+    uint32_t* scratch = nullptr;
+    cudaError_t e = static_sort_scratch(&scratch);
+    if (e != cudaSuccess) return e;
+    // cell_sort clears the counts it needs before use, so stale contents of the
+    // shared array from an earlier call do not leak into this one
+    return cell_sort(x, count, precision, n, keys, order, scratch, st);
 }
 
 }  // namespace pm

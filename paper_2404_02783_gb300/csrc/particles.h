@@ -25,6 +25,9 @@ cudaError_t fill(void* a, int64_t count, int precision, double v, cudaStream_t s
 size_t cell_sort_scratch_bytes(int64_t count, int n);
 cudaError_t cell_sort(const void* x, int64_t count, int precision, int n, uint32_t* keys, uint32_t* order,
                       void* scratch, cudaStream_t st);
+int64_t cell_sort_static_max_cells();
+cudaError_t cell_sort_static(const void* x, int64_t count, int precision, int n, uint32_t* keys, uint32_t* order,
+                             cudaStream_t st);
 
 // Bispectrum: fill the m-grid masked spectra (bins x {delta 1_b, 1_b}) from the
 // n-grid spectrum, and accumulate the triangle sums of the inverse transforms.
