@@ -188,7 +188,7 @@ pm_status deposit_particles(pm_ctx* c, void* rho) {
     Phase ph(c, PM_PHASE_DEPOSIT);
     PM_CK(cudaMemsetAsync(rho, 0, c->sT() * (size_t)c->n * c->n * c->n, c->st));
     const double mass = std::pow((double)c->n / c->np, 3);
-    PM_CK(deposit(c->at(c->L.x), c->np3, c->cfg.precision, c->n, mass, rho, c->st));
+    PM_CK(deposit_lattice(c->at(c->L.x), c->np, c->cfg.precision, c->n, mass, rho, c->st));
     return PM_OK;
 }
 
@@ -607,7 +607,8 @@ pm_status pm_density(pm_ctx* c, void* delta) {
     if (!c || !delta) return fail(PM_ERR_INVALID_ARG, "null argument");
     const int64_t n3 = (int64_t)c->n * c->n * c->n;
     PM_CK(fill(delta, n3, c->cfg.precision, -1.0, c->st));
-    PM_CK(deposit(c->at(c->L.x), c->np3, c->cfg.precision, c->n, std::pow((double)c->n / c->np, 3), delta, c->st));
+    PM_CK(deposit_lattice(c->at(c->L.x), c->np, c->cfg.precision, c->n, std::pow((double)c->n / c->np, 3), delta,
+                          c->st));
     return PM_OK;
 }
 

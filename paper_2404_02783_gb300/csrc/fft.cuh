@@ -1,16 +1,18 @@
-// In-shared-memory FFT building blocks (Stockham autosort, radix 8/4/2).
+// Register-resident FFT engine (Stockham autosort, radix 8 with one radix-4 or
+// radix-2 closing stage), compile-time length.
 //
-// A CTA transforms a tile of independent length-L sequences held in shared
-// memory.  Each sequence ("row" b) is served by L/8 threads; thread t of row b
-// performs 8/R radix-R butterflies per stage, so every stage is one
-// load -> twiddle -> register DFT -> barrier -> store -> barrier round, in
-// place.  Stockham ordering reads element j + r L/R and writes element
-// (j / Ns) Ns R + (j mod Ns) + r Ns, leaving the result in natural order
-// after the last stage without a bit-reversal pass.
+// A length-L sequence is owned by Q = L/8 threads; thread t holds the eight
+// elements t + m Q (m = 0..7) in registers.  A stage of radix R performs 8/R
+// butterflies per thread: butterfly j = t + q Q reads elements j + r L/R,
+// multiplies by exp(-+2 pi i (j mod Ns) r / (Ns R)) and runs a register DFT of
+// size R; the result element (j / Ns) Ns R + (j mod Ns) + r Ns goes through
+// shared memory to whichever thread reads it in the next stage.  Loads of stage
+// one and stores after the last stage touch elements t + m Q, i.e. consecutive
+// threads touch consecutive elements, so callers stream them to and from global
+// memory directly.  Only the exchanges between stages use shared memory.
 //
-// Twiddles come from a shared table tw[k] = exp(-2 pi i k / Ltab) built on the
-// host in FP64; a length-L transform uses stride Ltab / L.  INV selects the
-// conjugate (inverse, unnormalised) transform.
+// Twiddles come from a shared table tw[k] = exp(-2 pi i k / L) (host FP64,
+// rounded once); INV conjugates them (unnormalised inverse).
 #pragma once
 
 #include "pm_common.cuh"
@@ -51,93 +53,130 @@ __device__ __forceinline__ C mul_w8_3(C a) {
 
 template <bool INV, typename C>
 __device__ __forceinline__ void dft8(C* v) {
-    // even / odd split: E = DFT4(v0 v2 v4 v6), O = DFT4(v1 v3 v5 v7)
+    // even / odd split: E = DFT4(v0 v2 v4 v6), O = DFT4(v1 v3 v5 v7); X_k = E_k + w^k O_k
     dft4<INV>(v[0], v[2], v[4], v[6]);
     dft4<INV>(v[1], v[3], v[5], v[7]);
-    C o1 = mul_w8_1<INV>(v[3]);
-    C o2 = cmul_mi<INV>(v[5]);
-    C o3 = mul_w8_3<INV>(v[7]);
-    C e0 = v[0], e1 = v[2], e2 = v[4], e3 = v[6], o0 = v[1];
+    const C o1 = mul_w8_1<INV>(v[3]);
+    const C o2 = cmul_mi<INV>(v[5]);
+    const C o3 = mul_w8_3<INV>(v[7]);
+    const C e0 = v[0], e1 = v[2], e2 = v[4], e3 = v[6], o0 = v[1];
     v[0] = cadd(e0, o0); v[4] = csub(e0, o0);
     v[1] = cadd(e1, o1); v[5] = csub(e1, o1);
     v[2] = cadd(e2, o2); v[6] = csub(e2, o2);
     v[3] = cadd(e3, o3); v[7] = csub(e3, o3);
 }
 
-// ---------------------------------------------------------------- addressing
-// Row tile: row b occupies [b * stride, b * stride + spad(L)).
-struct RowAddr {
-    int stride;
-    __device__ __forceinline__ int operator()(int b, int i) const { return b * stride + spad(i); }
-};
-// Column tile: element i of column b sits at i * stride + b (columns interleaved).
-struct ColAddr {
-    int stride;
-    __device__ __forceinline__ int operator()(int b, int i) const { return i * stride + b; }
-};
+template <int R, bool INV, typename C>
+__device__ __forceinline__ void dftR(C* v) {
+    if constexpr (R == 8) dft8<INV>(v);
+    else if constexpr (R == 4) dft4<INV>(v[0], v[1], v[2], v[3]);
+    else if constexpr (R == 2) dft2<INV>(v[0], v[1]);
+}
 
 template <bool INV, typename C>
-__device__ __forceinline__ C twiddle(const C* tw, int e) {
+__device__ __forceinline__ C twid(const C* tw, int e) {
     C w = tw[e];
     if (INV) w.y = -w.y;
     return w;
 }
 
-// One Stockham stage of radix R for the thread's butterflies.
-template <int R, bool INV, typename C, class Addr>
-__device__ __forceinline__ void stockham_stage(C* s, int L, int Ns, int t, int b, bool active,
-                                               const C* tw, int tw_stride, Addr addr) {
-    constexpr int NB = 8 / R;  // butterflies per thread
-    C v[8];
-    const int quarter = L >> 3;  // threads per row
-    const int LR = L / R;
-    if (active) {
+__host__ __device__ constexpr int radix_at(int L, int Ns) { return (L / Ns) >= 8 ? 8 : (L / Ns); }
+__host__ __device__ constexpr int last_radix(int L, int Ns = 1) { return (Ns * radix_at(L, Ns) >= L) ? radix_at(L, Ns) : last_radix(L, Ns * radix_at(L, Ns)); }
+
+// ---------------------------------------------------------------- exchangers
+// Rows: sequence s of row b at base[((p NSEQ + s) RB + b) RS + spad(i)]; two
+// buffers alternate (p) when PP, so one barrier per exchange suffices.
+template <typename C, int NSEQ, bool PP>
+struct RowEx {
+    C* base;
+    int RB, RS, b, p;
+    __device__ __forceinline__ C& at(int s, int i) {
+        return base[((size_t)((PP ? p : 0) * NSEQ + s) * RB + b) * RS + spad(i)];
+    }
+    __device__ __forceinline__ void begin() {
+        if (!PP) __syncthreads();
+    }
+    __device__ __forceinline__ void end() {
+        if (PP) p ^= 1;
+    }
+};
+
+// Columns: element i of column b of sequence s at base[(s L + i) CS + b] (columns
+// interleaved so that lanes of consecutive columns hit consecutive banks).
+template <typename C, int L>
+struct ColEx {
+    C* base;
+    int CS, b;
+    __device__ __forceinline__ C& at(int s, int i) { return base[((size_t)s * L + i) * CS + b]; }
+    __device__ __forceinline__ void begin() { __syncthreads(); }
+    __device__ __forceinline__ void end() {}
+};
+
+// ---------------------------------------------------------------- stages
+template <int L, int Ns, int NSEQ, bool INV, typename C, class X>
+__device__ __forceinline__ void fft_stages(C (*v)[8], int t, const C* __restrict__ tw, X& ex) {
+    constexpr int R = radix_at(L, Ns);
+    constexpr int NB = 8 / R;
+    constexpr int Q = L / 8;
+    constexpr int TWS = L / (Ns * R);
+#pragma unroll
+    for (int s = 0; s < NSEQ; ++s)
 #pragma unroll
         for (int q = 0; q < NB; ++q) {
-            const int j = t + q * quarter;
-            const int jm = j % Ns;
-            const int tstep = jm * (L / (Ns * R)) * tw_stride;
+            if constexpr (Ns > 1) {
+                const int jm = (t + q * Q) & (Ns - 1);
 #pragma unroll
-            for (int r = 0; r < R; ++r) {
-                C a = s[addr(b, j + r * LR)];
-                if (r > 0) a = cmul(a, twiddle<INV>(tw, r * tstep));
-                v[q * R + r] = a;
+                for (int r = 1; r < R; ++r) v[s][q * R + r] = cmul(v[s][q * R + r], twid<INV>(tw, jm * r * TWS));
             }
-            if (R == 8) dft8<INV>(v);
-            if (R == 4) dft4<INV>(v[q * 4 + 0], v[q * 4 + 1], v[q * 4 + 2], v[q * 4 + 3]);
-            if (R == 2) dft2<INV>(v[q * 2 + 0], v[q * 2 + 1]);
+            dftR<R, INV>(&v[s][q * R]);
         }
-    }
-    __syncthreads();
-    if (active) {
+    if constexpr (Ns * R < L) {
+        constexpr int Ns2 = Ns * R;
+        constexpr int R2 = radix_at(L, Ns2);
+        constexpr int NB2 = 8 / R2;
+        ex.begin();
 #pragma unroll
-        for (int q = 0; q < NB; ++q) {
-            const int j = t + q * quarter;
-            const int jm = j % Ns;
-            const int base = (j / Ns) * Ns * R + jm;
+        for (int s = 0; s < NSEQ; ++s)
 #pragma unroll
-            for (int r = 0; r < R; ++r) s[addr(b, base + r * Ns)] = v[q * R + r];
-        }
+            for (int q = 0; q < NB; ++q) {
+                const int j = t + q * Q;
+                const int base = (j / Ns) * Ns2 + (j & (Ns - 1));
+#pragma unroll
+                for (int r = 0; r < R; ++r) ex.at(s, base + r * Ns) = v[s][q * R + r];
+            }
+        __syncthreads();
+#pragma unroll
+        for (int s = 0; s < NSEQ; ++s)
+#pragma unroll
+            for (int q = 0; q < NB2; ++q) {
+                const int j = t + q * Q;
+#pragma unroll
+                for (int r = 0; r < R2; ++r) v[s][q * R2 + r] = ex.at(s, j + r * (L / R2));
+            }
+        ex.end();
+        fft_stages<L, Ns2, NSEQ, INV>(v, t, tw, ex);
     }
-    __syncthreads();
 }
 
-// Full length-L transform (L a power of two, 8 <= L <= 4096) of every row in the
-// tile; all threads of the CTA must call it (it contains barriers).
-template <bool INV, typename C, class Addr>
-__device__ void fft_tile(C* s, int L, int t, int b, bool active, const C* tw, int tw_stride, Addr addr) {
-    int Ns = 1;
-    while (Ns < L) {
-        const int rem = L / Ns;
-        if (rem >= 8) {
-            stockham_stage<8, INV>(s, L, Ns, t, b, active, tw, tw_stride, addr);
-            Ns *= 8;
-        } else if (rem == 4) {
-            stockham_stage<4, INV>(s, L, Ns, t, b, active, tw, tw_stride, addr);
-            Ns *= 4;
-        } else {
-            stockham_stage<2, INV>(s, L, Ns, t, b, active, tw, tw_stride, addr);
-            Ns *= 2;
+// Transform NSEQ sequences of length L (8 <= L <= 1024, a power of two).  On entry
+// v[s][m] is element t + m L/8 of sequence s; on exit v[s][m] is transform element
+// t + m L/8.  Contains barriers: every thread of the CTA must call it.
+template <int L, int NSEQ, bool INV, typename C, class X>
+__device__ __forceinline__ void fft_regs(C (*v)[8], int t, const C* __restrict__ tw, X& ex) {
+    fft_stages<L, 1, NSEQ, INV>(v, t, tw, ex);
+    constexpr int RL = last_radix(L);
+    if constexpr (RL < 8) {
+        // after a closing radix-RL stage, slot q RL + r holds element t + (q + r 8/RL) L/8
+        constexpr int NB = 8 / RL;
+#pragma unroll
+        for (int s = 0; s < NSEQ; ++s) {
+            C w[8];
+#pragma unroll
+            for (int q = 0; q < NB; ++q)
+#pragma unroll
+                for (int r = 0; r < RL; ++r) w[q + r * NB] = v[s][q * RL + r];
+#pragma unroll
+            for (int m = 0; m < 8; ++m) v[s][m] = w[m];
         }
     }
 }

@@ -1,0 +1,529 @@
+// 3D real FFT passes and the fused spectral operators of the PM step, templated on
+// precision and transform size (included by fft_f32.cu and fft_f64.cu).
+//
+// Data flow of a 3D r2c transform of a real mesh R[x][y][z] (side n):
+//   z_r2c : rows along z -> half spectrum T[kz][x][y]  (kz = 0..n/2; transposing store)
+//   y_rows: rows along y (contiguous)                  -> T[kz][x][ky]
+//   x_cols: columns along x (stride n)                 -> S[kz][kx][ky]
+// and the inverse runs x_cols -> y_rows -> z_c2r.  Every pass reads and writes each
+// element once: loads go straight from global memory into registers, the butterflies
+// run in registers, shared memory carries only the exchanges between stages.  The
+// Green's function, the Poisson-gauge constraint, the Zel'dovich filter, the x part
+// of the spectral gradient and the power-spectrum binning act on registers inside
+// the x-column pass, the y part of the gradient inside the inverse y pass and the z
+// part inside the c2r pass.
+#pragma once
+
+#include <math.h>
+
+#include "fft.cuh"
+#include "internal.h"
+
+namespace pm {
+
+template <typename T> __device__ __forceinline__ cplx<T> tw_global(int k);
+
+template <typename T>
+__device__ __forceinline__ void load_twiddles(cplx<T>* tw, int L) {
+    const int stride = 1024 / L;
+    for (int k = threadIdx.x; k < L; k += blockDim.x) tw[k] = tw_global<T>(k * stride);
+}
+
+// First `count` entries of the length-L table.
+template <typename T>
+__device__ __forceinline__ void load_twiddles_head(cplx<T>* tw, int L, int count) {
+    const int stride = 1024 / L;
+    for (int k = threadIdx.x; k < count; k += blockDim.x) tw[k] = tw_global<T>(k * stride);
+}
+
+// Padded row stride (complex elements) holding `len` elements; odd so lanes walking
+// across rows hit different banks.
+__host__ __device__ constexpr int row_stride(int len) { return (len + (len >> 3) + 1) | 1; }
+
+static inline cudaError_t set_smem(const void* fn, size_t bytes) {
+    if (bytes <= 48 * 1024) return cudaSuccess;
+    return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+// Launch shapes (compile time): sequences per CTA for each pass.
+template <typename T, int LOGN> struct Shape {
+    static constexpr int N = 1 << LOGN;
+    static constexpr int M = N / 2;
+    static constexpr int QN = N / 8;            // threads per length-N sequence
+    static constexpr int QM = (M >= 8) ? M / 8 : 1;
+    static constexpr int YB = (512 / QM < N) ? 512 / QM : N;     // z passes: rows per CTA
+    static constexpr int RB = (256 / QN > 0) ? 256 / QN : 1;     // y pass
+    static constexpr int RB3 = (sizeof(T) == 8) ? ((128 / QN > 0) ? 128 / QN : 1) : RB;  // y grad3
+    static constexpr int CB0 = (512 / QN < N) ? 512 / QN : N;
+    static constexpr int CB = (sizeof(T) == 8 && N >= 512) ? CB0 / 2 : CB0;  // x pass columns
+};
+
+// =============================================================== z: r2c
+template <typename T, int LOGN>
+__global__ void __launch_bounds__(512) k_z_r2c(const T* __restrict__ in, cplx<T>* __restrict__ out) {
+    typedef cplx<T> C;
+    typedef Shape<T, LOGN> S;
+    constexpr int N = S::N, M = S::M, Q = S::QM, YB = S::YB;
+    constexpr int RS = row_stride(M + 1);
+    constexpr int TWN = (M + 2) & ~1;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* twM = reinterpret_cast<C*>(smem_raw);
+    C* twN = twM + M;
+    C* buf = twN + TWN;
+    const int tid = threadIdx.x;
+    const int y0 = blockIdx.x * YB;
+    const int x = blockIdx.y % N;
+    const size_t f = blockIdx.y / N;
+    load_twiddles<T>(twM, M);
+    load_twiddles_head<T>(twN, N, M + 1);
+    const int b = tid / Q, t = tid % Q;
+    const C* row = reinterpret_cast<const C*>(in + ((f * N + x) * (size_t)N + y0 + b) * N);
+    C v[1][8];
+#pragma unroll
+    for (int m = 0; m < 8; ++m) v[0][m] = row[t + m * Q];
+    __syncthreads();
+    RowEx<C, 1, false> ex{buf, YB, RS, b, 0};
+    fft_regs<M, 1, false>(v, t, twM, ex);
+    C* z = buf;
+    __syncthreads();  // every thread has read its last exchange before the buffer is reused
+#pragma unroll
+    for (int m = 0; m < 8; ++m) z[b * RS + spad(t + m * Q)] = v[0][m];
+    __syncthreads();
+    C* outp = out + f * (size_t)(M + 1) * N * N;
+    constexpr int NT = YB * Q, ITERS = ((M + 1) * YB + NT - 1) / NT;
+#pragma unroll
+    for (int it = 0; it < ITERS; ++it) {
+        const int e = tid + it * NT;
+        if (e >= (M + 1) * YB) break;
+        const int k = e / YB, bb = e % YB;
+        const C z1 = z[bb * RS + spad(k == M ? 0 : k)];
+        const C z2 = cconj(z[bb * RS + spad(k == 0 ? 0 : M - k)]);
+        const C E = cscale(cadd(z1, z2), T(0.5));
+        const C O = cscale(cmul_mi<false>(csub(z1, z2)), T(0.5));
+        outp[((size_t)k * N + x) * N + y0 + bb] = cadd(E, cmul(twN[k], O));
+    }
+}
+
+// =============================================================== z: c2r
+template <typename T> struct Ptr3 {
+    const cplx<T>* in[3];
+    T* out[3];
+};
+
+template <typename T, int LOGN>
+__global__ void __launch_bounds__(512) k_z_c2r(Ptr3<T> P, unsigned gradz_mask, T kf) {
+    typedef cplx<T> C;
+    typedef Shape<T, LOGN> S;
+    constexpr int N = S::N, M = S::M, Q = S::QM, YB = S::YB;
+    constexpr int RS = row_stride(M + 1);
+    constexpr int TWN = (M + 2) & ~1;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* twM = reinterpret_cast<C*>(smem_raw);
+    C* twN = twM + M;
+    C* buf = twN + TWN;
+    const int tid = threadIdx.x;
+    const int comp = blockIdx.z;
+    const bool grad = (gradz_mask >> comp) & 1u;
+    const int y0 = blockIdx.x * YB;
+    const int x = blockIdx.y % N;
+    const size_t f = blockIdx.y / N;
+    load_twiddles<T>(twM, M);
+    load_twiddles_head<T>(twN, N, M + 1);
+    const C* pin = comp == 0 ? P.in[0] : (comp == 1 ? P.in[1] : P.in[2]);
+    T* pout = comp == 0 ? P.out[0] : (comp == 1 ? P.out[1] : P.out[2]);
+    const C* inp = pin + f * (size_t)(M + 1) * N * N;
+    C* xb = buf;  // gathered half spectrum; the FFT exchanges reuse the buffer afterwards
+    constexpr int NT = YB * Q, ITERS = ((M + 1) * YB + NT - 1) / NT;
+#pragma unroll
+    for (int it = 0; it < ITERS; ++it) {
+        const int e = tid + it * NT;
+        if (e >= (M + 1) * YB) break;
+        const int k = e / YB, bb = e % YB;
+        C X = inp[((size_t)k * N + x) * N + y0 + bb];
+        if (grad) {  // (-i kz) X, Nyquist kz -> 0
+            const T kz = (k == M) ? T(0) : kf * T(k);
+            X = cmake<C>(X.y * kz, -X.x * kz);
+        }
+        xb[bb * RS + spad(k)] = X;
+    }
+    __syncthreads();
+    // Y_k = (X_k + X*_{M-k}) + i (X_k - X*_{M-k}) exp(+2 pi i k / N), pairs (k, M-k) per thread
+    for (int e = tid; e < (M / 2 + 1) * YB; e += YB * Q) {
+        const int k = e / YB, bb = e % YB;
+        C* r = xb + bb * RS;
+        C a = r[spad(k)];
+        C c = r[spad(M - k)];
+        if (k == 0) {
+            a.y = T(0);
+            c.y = T(0);
+        }
+        const C bconj = cconj(c);
+        const C d = cmul(csub(a, bconj), cconj(twN[k]));
+        const C y = cadd(cadd(a, bconj), cmake<C>(-d.y, d.x));
+        if (k > 0 && k < M - k) {
+            const C aconj = cconj(a);
+            const C d2 = cmul(csub(c, aconj), cconj(twN[M - k]));
+            r[spad(M - k)] = cadd(cadd(c, aconj), cmake<C>(-d2.y, d2.x));
+        }
+        r[spad(k)] = y;
+    }
+    __syncthreads();
+    const int b = tid / Q, t = tid % Q;
+    C v[1][8];
+#pragma unroll
+    for (int m = 0; m < 8; ++m) v[0][m] = xb[b * RS + spad(t + m * Q)];
+    RowEx<C, 1, false> ex{buf, YB, RS, b, 0};
+    fft_regs<M, 1, true>(v, t, twM, ex);
+    C* orow = reinterpret_cast<C*>(pout + ((f * N + x) * (size_t)N + y0 + b) * N);
+#pragma unroll
+    for (int m = 0; m < 8; ++m) orow[t + m * Q] = v[0][m];
+}
+
+// =============================================================== y: contiguous rows
+template <typename T, int LOGN, bool INV>
+__global__ void __launch_bounds__(512) k_y_rows(cplx<T>* __restrict__ data, int64_t nrows) {
+    typedef cplx<T> C;
+    typedef Shape<T, LOGN> S;
+    constexpr int N = S::N, Q = S::QN, RB = S::RB;
+    constexpr int RS = row_stride(N);
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* tw = reinterpret_cast<C*>(smem_raw);
+    C* buf = tw + N;
+    const int tid = threadIdx.x;
+    const int b = tid / Q, t = tid % Q;
+    const int64_t r = (int64_t)blockIdx.x * RB + b;
+    const bool ok = r < nrows;
+    load_twiddles<T>(tw, N);
+    C v[1][8];
+    C* row = data + r * N;
+    if (ok) {
+#pragma unroll
+        for (int m = 0; m < 8; ++m) v[0][m] = row[t + m * Q];
+    }
+    __syncthreads();
+    RowEx<C, 1, true> ex{buf, RB, RS, b, 0};
+    fft_regs<N, 1, INV>(v, t, tw, ex);
+    if (ok) {
+#pragma unroll
+        for (int m = 0; m < 8; ++m) row[t + m * Q] = v[0][m];
+    }
+}
+
+// A <- IFFT_y(A), B <- IFFT_y(B), C <- IFFT_y(-i ky A)
+template <typename T, int LOGN>
+__global__ void __launch_bounds__(512) k_y_grad3(cplx<T>* __restrict__ A, cplx<T>* __restrict__ B,
+                                                 cplx<T>* __restrict__ Cout, int64_t nrows, T kf) {
+    typedef cplx<T> C;
+    typedef Shape<T, LOGN> S;
+    constexpr int N = S::N, Q = S::QN, RB = S::RB3;
+    constexpr int RS = row_stride(N);
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* tw = reinterpret_cast<C*>(smem_raw);
+    C* buf = tw + N;
+    const int tid = threadIdx.x;
+    const int b = tid / Q, t = tid % Q;
+    const int64_t r = (int64_t)blockIdx.x * RB + b;
+    const bool ok = r < nrows;
+    load_twiddles<T>(tw, N);
+    C v[3][8];
+    if (ok) {
+#pragma unroll
+        for (int m = 0; m < 8; ++m) {
+            const int i = t + m * Q;
+            const C a = A[r * N + i];
+            v[0][m] = a;
+            v[1][m] = B[r * N + i];
+            const int ny = (i < N / 2) ? i : i - N;
+            const T ky = (2 * ny == -N) ? T(0) : kf * T(ny);
+            v[2][m] = cmake<C>(a.y * ky, -a.x * ky);
+        }
+    }
+    __syncthreads();
+    RowEx<C, 3, false> ex{buf, RB, RS, b, 0};
+    fft_regs<N, 3, true>(v, t, tw, ex);
+    if (ok) {
+#pragma unroll
+        for (int m = 0; m < 8; ++m) {
+            const int i = t + m * Q;
+            A[r * N + i] = v[0][m];
+            B[r * N + i] = v[1][m];
+            Cout[r * N + i] = v[2][m];
+        }
+    }
+}
+
+// =============================================================== x: strided columns + spectral operators
+template <typename T, int LOGN, int KIND>
+__global__ void __launch_bounds__(512) k_x_cols(cplx<T>* __restrict__ data, cplx<T>* __restrict__ out2, SpecOp op) {
+    typedef cplx<T> C;
+    typedef Shape<T, LOGN> S;
+    constexpr int N = S::N, M = S::M, Q = S::QN, CB = S::CB;
+    constexpr int CS = CB + 1;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* tw = reinterpret_cast<C*>(smem_raw);
+    C* buf = tw + N;
+    double* acc = reinterpret_cast<double*>(buf + (size_t)2 * N * CS);
+    const int tid = threadIdx.x;
+    const int b = tid % CB, t = tid / CB;
+    const int plane = blockIdx.y;
+    const int kz = plane % (M + 1);
+    const int c = blockIdx.x * CB + b;
+    const size_t pbase = (size_t)plane * N * N;
+    C* base = data + pbase;
+    const bool cross = (KIND == OP_BIN) && op.in2 != nullptr;
+    load_twiddles<T>(tw, N);
+    if (KIND == OP_BIN)
+        for (int e = tid; e < 3 * op.nbins; e += blockDim.x) acc[e] = 0.0;
+    C v[2][8];
+#pragma unroll
+    for (int m = 0; m < 8; ++m) v[0][m] = base[(size_t)(t + m * Q) * N + c];
+    if (cross) {
+        const C* b2 = reinterpret_cast<const C*>(op.in2) + pbase;
+#pragma unroll
+        for (int m = 0; m < 8; ++m) v[1][m] = b2[(size_t)(t + m * Q) * N + c];
+    }
+    __syncthreads();
+    ColEx<C, N> ex{buf, CS, b};
+    if (op.fwd) {
+        if (cross) fft_regs<N, 2, false>(v, t, tw, ex);
+        else fft_regs<N, 1, false>(v, t, tw, ex);
+    }
+    if constexpr (KIND == OP_FWD_STORE) {
+#pragma unroll
+        for (int m = 0; m < 8; ++m) base[(size_t)(t + m * Q) * N + c] = v[0][m];
+        return;
+    }
+    if constexpr (KIND == OP_INV) {
+        fft_regs<N, 1, true>(v, t, tw, ex);
+#pragma unroll
+        for (int m = 0; m < 8; ++m) base[(size_t)(t + m * Q) * N + c] = v[0][m];
+        return;
+    }
+    // ---- per-mode operator on modes (kx = t + m Q, ky = c, kz)
+    const int ny = (c < M) ? c : c - N;
+    const int nz = kz;
+#pragma unroll
+    for (int m = 0; m < 8; ++m) {
+        const int i = t + m * Q;
+        const int nx = (i < M) ? i : i - N;
+        const int n2 = nx * nx + ny * ny + nz * nz;
+        const C vv = v[0][m];
+        if constexpr (KIND == OP_BIN) {
+            if (n2 == 0 || n2 > M * M) continue;
+            const int bin = op.bin_of[n2];
+            if (bin < 0) continue;
+            const double w = (nz == 0 || nz == M) ? 1.0 : 2.0;
+            double val;
+            if (cross) {
+                const C u = v[1][m];
+                val = (double)vv.x * (double)u.x + (double)vv.y * (double)u.y;
+            } else {
+                val = (double)vv.x * (double)vv.x + (double)vv.y * (double)vv.y;
+            }
+            if (op.deconv) {
+                const double W = op.wtab[nx < 0 ? -nx : nx] * op.wtab[ny < 0 ? -ny : ny] * op.wtab[nz];
+                val /= W * W;
+            }
+            atomicAdd(&acc[bin], w);
+            atomicAdd(&acc[op.nbins + bin], w * val);
+            atomicAdd(&acc[2 * op.nbins + bin], w * op.kf * sqrt((double)n2));
+        } else {
+            C phi;
+            if constexpr (KIND == OP_NEWTON || KIND == OP_POTENTIAL) {
+                phi = (n2 == 0) ? cmake<C>(T(0), T(0)) : cscale(vv, T(op.coef) / T(n2));
+            } else if constexpr (KIND == OP_ZA) {
+                const bool nyq = (2 * nx == -N) || (2 * ny == -N) || (nz == M);
+                phi = (n2 == 0 || nyq) ? cmake<C>(T(0), T(0)) : cscale(vv, T(op.coef * op.amp[n2] / (double)n2));
+            } else {  // OP_GR
+                if (n2 == 0) {
+                    phi = cmake<C>(T(0), T(0));
+                    if (op.n_lo > 0) {
+                        const int L = op.n_lo, W2 = 2 * L + 1;
+                        op.island[((size_t)nz * W2 + L) * W2 + L] = make_double2(0.0, 0.0);
+                    }
+                } else if (n2 <= op.n_lo * op.n_lo) {
+                    const int L = op.n_lo, W2 = 2 * L + 1;
+                    const size_t id = ((size_t)nz * W2 + (nx + L)) * W2 + (ny + L);
+                    const double k2 = op.kf * op.kf * (double)n2;
+                    const double H = op.calH;
+                    const double num_s = -1.5 * H * H * op.omm_a;
+                    double den = k2 + 3.0 * H * H + 4.5 * H * H * op.omm_a;
+                    double2 P = make_double2(num_s * (double)vv.x, num_s * (double)vv.y);
+                    if (!op.first) {
+                        const double2 old = op.island[id];
+                        const double cc = 3.0 * H * op.inv_dtau;
+                        P.x += cc * old.x;
+                        P.y += cc * old.y;
+                        den += cc;
+                    }
+                    P.x /= den;
+                    P.y /= den;
+                    op.island[id] = P;
+                    phi = cmake<C>(T(P.x * op.ac2_over_n3), T(P.y * op.ac2_over_n3));
+                } else {
+                    C* old = reinterpret_cast<C*>(op.phi_old) + pbase + (size_t)i * N + c;
+                    const T k2 = T(op.kf * op.kf) * T(n2);
+                    const T H = T(op.calH), om = T(op.omm_a);
+                    const T num_s = T(-1.5) * H * H * om;
+                    T den = k2 + T(3) * H * H + T(4.5) * H * H * om;
+                    C Pc = cscale(vv, num_s);
+                    if (!op.first) {
+                        const T cc = T(3) * H * T(op.inv_dtau);
+                        const C o = *old;
+                        Pc.x += cc * o.x;
+                        Pc.y += cc * o.y;
+                        den += cc;
+                    }
+                    Pc = cscale(Pc, T(1) / den);
+                    *old = Pc;
+                    phi = cscale(Pc, T(op.ac2_over_n3));
+                }
+            }
+            v[0][m] = phi;
+            if constexpr (KIND != OP_POTENTIAL) {
+                const T kx = (2 * nx == -N) ? T(0) : T(op.kf) * T(nx);
+                v[1][m] = cmake<C>(phi.y * kx, -phi.x * kx);  // -i kx phi
+            }
+        }
+    }
+    if constexpr (KIND == OP_BIN) {
+        __syncthreads();
+        for (int e = tid; e < 3 * op.nbins; e += blockDim.x)
+            if (acc[e] != 0.0) atomicAdd(&op.acc[e], acc[e]);
+        return;
+    }
+    if constexpr (KIND == OP_POTENTIAL) {
+        fft_regs<N, 1, true>(v, t, tw, ex);
+#pragma unroll
+        for (int m = 0; m < 8; ++m) base[(size_t)(t + m * Q) * N + c] = v[0][m];
+    } else {
+        fft_regs<N, 2, true>(v, t, tw, ex);
+#pragma unroll
+        for (int m = 0; m < 8; ++m) {
+            base[(size_t)(t + m * Q) * N + c] = v[0][m];
+            out2[pbase + (size_t)(t + m * Q) * N + c] = v[1][m];
+        }
+    }
+}
+
+// =============================================================== launchers
+template <typename T, int LOGN>
+cudaError_t z_r2c_n(const T* in, cplx<T>* out, int batch, cudaStream_t st) {
+    typedef Shape<T, LOGN> S;
+    const size_t smem = sizeof(cplx<T>) * (S::M + ((S::M + 2) & ~1) + (size_t)S::YB * row_stride(S::M + 1));
+    cudaError_t e = set_smem((const void*)k_z_r2c<T, LOGN>, smem);
+    if (e != cudaSuccess) return e;
+    k_z_r2c<T, LOGN><<<dim3(S::N / S::YB, S::N * batch), S::YB * S::QM, smem, st>>>(in, out);
+    return cudaGetLastError();
+}
+
+template <typename T, int LOGN>
+cudaError_t z_c2r_n(const Ptr3<T>& P, int ncomp, int batch, unsigned mask, double kf, cudaStream_t st) {
+    typedef Shape<T, LOGN> S;
+    const size_t smem = sizeof(cplx<T>) * (S::M + ((S::M + 2) & ~1) + (size_t)S::YB * row_stride(S::M + 1));
+    cudaError_t e = set_smem((const void*)k_z_c2r<T, LOGN>, smem);
+    if (e != cudaSuccess) return e;
+    k_z_c2r<T, LOGN><<<dim3(S::N / S::YB, S::N * batch, ncomp), S::YB * S::QM, smem, st>>>(P, mask, (T)kf);
+    return cudaGetLastError();
+}
+
+template <typename T, int LOGN, bool INV>
+cudaError_t y_rows_n(cplx<T>* data, int64_t nrows, cudaStream_t st) {
+    typedef Shape<T, LOGN> S;
+    const size_t smem = sizeof(cplx<T>) * (S::N + 2 * (size_t)S::RB * row_stride(S::N));
+    cudaError_t e = set_smem((const void*)k_y_rows<T, LOGN, INV>, smem);
+    if (e != cudaSuccess) return e;
+    const int64_t nblk = (nrows + S::RB - 1) / S::RB;
+    k_y_rows<T, LOGN, INV><<<(unsigned)nblk, S::RB * S::QN, smem, st>>>(data, nrows);
+    return cudaGetLastError();
+}
+
+template <typename T, int LOGN>
+cudaError_t y_grad3_n(cplx<T>* A, cplx<T>* B, cplx<T>* Cc, int64_t nrows, double kf, cudaStream_t st) {
+    typedef Shape<T, LOGN> S;
+    const size_t smem = sizeof(cplx<T>) * (S::N + 3 * (size_t)S::RB3 * row_stride(S::N));
+    cudaError_t e = set_smem((const void*)k_y_grad3<T, LOGN>, smem);
+    if (e != cudaSuccess) return e;
+    const int64_t nblk = (nrows + S::RB3 - 1) / S::RB3;
+    k_y_grad3<T, LOGN><<<(unsigned)nblk, S::RB3 * S::QN, smem, st>>>(A, B, Cc, nrows, (T)kf);
+    return cudaGetLastError();
+}
+
+template <typename T, int LOGN, int KIND>
+cudaError_t x_cols_n(cplx<T>* data, cplx<T>* out2, int nplanes, const SpecOp& op, cudaStream_t st) {
+    typedef Shape<T, LOGN> S;
+    const size_t smem = sizeof(cplx<T>) * (S::N + 2 * (size_t)S::N * (S::CB + 1)) + sizeof(double) * 3 * op.nbins;
+    cudaError_t e = set_smem((const void*)k_x_cols<T, LOGN, KIND>, smem);
+    if (e != cudaSuccess) return e;
+    k_x_cols<T, LOGN, KIND><<<dim3(S::N / S::CB, nplanes), S::CB * S::QN, smem, st>>>(data, out2, op);
+    return cudaGetLastError();
+}
+
+template <typename T, int LOGN>
+cudaError_t x_cols_kind(cplx<T>* data, cplx<T>* out2, int nplanes, const SpecOp& op, cudaStream_t st) {
+    switch (op.kind) {
+        case OP_FWD_STORE: return x_cols_n<T, LOGN, OP_FWD_STORE>(data, out2, nplanes, op, st);
+        case OP_INV: return x_cols_n<T, LOGN, OP_INV>(data, out2, nplanes, op, st);
+        case OP_NEWTON: return x_cols_n<T, LOGN, OP_NEWTON>(data, out2, nplanes, op, st);
+        case OP_GR: return x_cols_n<T, LOGN, OP_GR>(data, out2, nplanes, op, st);
+        case OP_ZA: return x_cols_n<T, LOGN, OP_ZA>(data, out2, nplanes, op, st);
+        case OP_BIN: return x_cols_n<T, LOGN, OP_BIN>(data, out2, nplanes, op, st);
+        case OP_POTENTIAL: return x_cols_n<T, LOGN, OP_POTENTIAL>(data, out2, nplanes, op, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+#define PM_DISPATCH_LOGN(n, CALL)      \
+    switch (ilog2(n)) {                \
+        case 4: { constexpr int LG = 4; return CALL; } \
+        case 5: { constexpr int LG = 5; return CALL; } \
+        case 6: { constexpr int LG = 6; return CALL; } \
+        case 7: { constexpr int LG = 7; return CALL; } \
+        case 8: { constexpr int LG = 8; return CALL; } \
+        case 9: { constexpr int LG = 9; return CALL; } \
+        case 10: { constexpr int LG = 10; return CALL; } \
+        default: return cudaErrorInvalidValue; \
+    }
+
+template <typename T>
+cudaError_t z_r2c(const T* in, cplx<T>* out, int n, int batch, cudaStream_t st) {
+    PM_DISPATCH_LOGN(n, (z_r2c_n<T, LG>(in, out, batch, st)))
+}
+
+template <typename T>
+cudaError_t z_c2r(const cplx<T>* const* in, T* const* out, int ncomp, int n, int batch, unsigned gradz_mask,
+                  double kf, cudaStream_t st) {
+    Ptr3<T> P;
+    for (int j = 0; j < 3; ++j) {
+        P.in[j] = in[j < ncomp ? j : 0];
+        P.out[j] = out[j < ncomp ? j : 0];
+    }
+    PM_DISPATCH_LOGN(n, (z_c2r_n<T, LG>(P, ncomp, batch, gradz_mask, kf, st)))
+}
+
+template <typename T, bool INV>
+cudaError_t y_rows(cplx<T>* data, int64_t nrows, int n, cudaStream_t st) {
+    PM_DISPATCH_LOGN(n, (y_rows_n<T, LG, INV>(data, nrows, st)))
+}
+
+template <typename T>
+cudaError_t y_rows_grad3(cplx<T>* A, cplx<T>* B, cplx<T>* Cc, int64_t nrows, int n, double kf, cudaStream_t st) {
+    PM_DISPATCH_LOGN(n, (y_grad3_n<T, LG>(A, B, Cc, nrows, kf, st)))
+}
+
+template <typename T>
+cudaError_t x_cols(cplx<T>* data, cplx<T>* out2, int nplanes, int n, const SpecOp& op, cudaStream_t st) {
+    PM_DISPATCH_LOGN(n, (x_cols_kind<T, LG>(data, out2, nplanes, op, st)))
+}
+
+#define PM_INST(T)                                                                                     \
+    template cudaError_t z_r2c<T>(const T*, cplx<T>*, int, int, cudaStream_t);                         \
+    template cudaError_t z_c2r<T>(const cplx<T>* const*, T* const*, int, int, int, unsigned, double,  \
+                                  cudaStream_t);                                                       \
+    template cudaError_t y_rows<T, false>(cplx<T>*, int64_t, int, cudaStream_t);                      \
+    template cudaError_t y_rows<T, true>(cplx<T>*, int64_t, int, cudaStream_t);                       \
+    template cudaError_t y_rows_grad3<T>(cplx<T>*, cplx<T>*, cplx<T>*, int64_t, int, double,           \
+                                         cudaStream_t);                                                \
+    template cudaError_t x_cols<T>(cplx<T>*, cplx<T>*, int, int, const SpecOp&, cudaStream_t);
+
+}  // namespace pm

@@ -42,10 +42,8 @@ struct SpecOp {
     const void* in2 = nullptr;        // second (y-transformed) field for the cross spectrum
 };
 
-// Twiddle table exp(-2 pi i k / 1024), k < 1024, resident on the current device.
-const float2* twiddles_f32();
-const double2* twiddles_f64();
-template <typename T> const cplx<T>* twiddles();
+// Uploads the twiddle tables exp(-2 pi i k / 1024) of both precisions to the current
+// device (once per device).
 cudaError_t ensure_device_tables();
 
 // FFT passes.  n is the transform length (power of two, 16..1024); batch counts

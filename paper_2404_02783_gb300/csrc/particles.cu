@@ -47,8 +47,8 @@ __device__ __forceinline__ CicD cic_frac(double x, int n) {
 }
 
 // ---------------------------------------------------------------- deposit
-__global__ void k_deposit_ticks(const uint32_t* __restrict__ x, int64_t count, int logn, float inv_cell_ticks,
-                                float mass, float* __restrict__ rho) {
+__global__ void __launch_bounds__(256) k_deposit_ticks(const uint32_t* __restrict__ x, int64_t count, int logn,
+                                                       float inv_cell_ticks, float mass, float* __restrict__ rho) {
     const size_t n = (size_t)1 << logn;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count;
          i += (int64_t)gridDim.x * blockDim.x) {
@@ -66,6 +66,75 @@ __global__ void k_deposit_ticks(const uint32_t* __restrict__ x, int64_t count, i
                 atomicAdd(row + iz[0], wab * wz[0]);
                 atomicAdd(row + iz[1], wab * wz[1]);
             }
+    }
+}
+
+// Deposit of lattice-ordered particles (count = np^3, id = (ix np + iy) np + iz) by
+// Lagrangian tiles.  A CTA owns a TX x TY x TZ block of lattice sites (16 x 16 x 32
+// mesh cells' worth, R = n / np cells per lattice step); particles that have not
+// travelled far land in that mesh box widened by H cells on every side, which the CTA
+// accumulates with shared-memory atomics and then adds to the global mesh once per
+// cell.  A particle whose CIC stencil leaves the box adds its weights to global memory
+// directly, so the result is the same CIC density for any displacement.
+template <int R>
+struct DepTile {
+    static constexpr int TX = 16 / R, TY = 16 / R, TZ = 32 / R, H = 2;
+    static constexpr int DX = TX * R + 2 * H, DY = TY * R + 2 * H, DZ = TZ * R + 2 * H;
+    static constexpr int CELLS = DX * DY * DZ;
+    static constexpr int PER = TX * TY * TZ;
+};
+
+template <int R>
+__global__ void __launch_bounds__(512) k_deposit_tiled(const uint32_t* __restrict__ x, int lognp, int logn,
+                                                       float inv_cell_ticks, float mass, float* __restrict__ rho) {
+    typedef DepTile<R> D;
+    extern __shared__ __align__(16) float tile[];  // D::CELLS floats
+    const int np = 1 << lognp, n = 1 << logn, nm = n - 1;
+    const int ntz = np / D::TZ, nty = np / D::TY;
+    const int bz = blockIdx.x % ntz, by = (blockIdx.x / ntz) % nty, bx = blockIdx.x / (ntz * nty);
+    const int ox = bx * D::TX * R - D::H, oy = by * D::TY * R - D::H, oz = bz * D::TZ * R - D::H;
+    const int64_t count = (int64_t)1 << (3 * lognp);
+    for (int c = threadIdx.x; c < D::CELLS / 4; c += 512) reinterpret_cast<float4*>(tile)[c] = make_float4(0, 0, 0, 0);
+    __syncthreads();
+#pragma unroll 2
+    for (int e = threadIdx.x; e < D::PER; e += 512) {
+        const int lz = e % D::TZ, ly = (e / D::TZ) % D::TY, lx = e / (D::TZ * D::TY);
+        const int64_t id = (((int64_t)(bx * D::TX + lx) << lognp) + by * D::TY + ly) * np + bz * D::TZ + lz;
+        const CicF cx = cic_ticks(x[id], logn, inv_cell_ticks);
+        const CicF cy = cic_ticks(x[count + id], logn, inv_cell_ticks);
+        const CicF cz = cic_ticks(x[2 * count + id], logn, inv_cell_ticks);
+        const float wx[2] = {1.0f - cx.w1, cx.w1}, wy[2] = {1.0f - cy.w1, cy.w1}, wz[2] = {1.0f - cz.w1, cz.w1};
+        const int dx = (cx.i0 - ox) & nm, dy = (cy.i0 - oy) & nm, dz = (cz.i0 - oz) & nm;
+        if (dx < D::DX - 1 && dy < D::DY - 1 && dz < D::DZ - 1) {
+#pragma unroll
+            for (int a = 0; a < 2; ++a)
+#pragma unroll
+                for (int b = 0; b < 2; ++b) {
+                    const float wab = mass * wx[a] * wy[b];
+                    float* row = tile + ((dx + a) * D::DY + dy + b) * D::DZ + dz;
+                    atomicAdd(row, wab * wz[0]);
+                    atomicAdd(row + 1, wab * wz[1]);
+                }
+        } else {
+            const int ix[2] = {cx.i0, cx.i1}, iy[2] = {cy.i0, cy.i1}, iz[2] = {cz.i0, cz.i1};
+#pragma unroll
+            for (int a = 0; a < 2; ++a)
+#pragma unroll
+                for (int b = 0; b < 2; ++b) {
+                    const float wab = mass * wx[a] * wy[b];
+                    float* row = rho + ((size_t)ix[a] * n + iy[b]) * n;
+                    atomicAdd(row + iz[0], wab * wz[0]);
+                    atomicAdd(row + iz[1], wab * wz[1]);
+                }
+        }
+    }
+    __syncthreads();
+    for (int c = threadIdx.x; c < D::CELLS; c += 512) {
+        const float v = tile[c];
+        if (v != 0.0f) {
+            const int lz = c % D::DZ, ly = (c / D::DZ) % D::DY, lx = c / (D::DZ * D::DY);
+            atomicAdd(rho + (((size_t)((ox + lx) & nm) * n + ((oy + ly) & nm)) * n + ((oz + lz) & nm)), v);
+        }
     }
 }
 
@@ -94,6 +163,30 @@ static unsigned grid_for(int64_t count, int threads) {
     if (b > cap) b = cap;
     if (b < 1) b = 1;
     return (unsigned)b;
+}
+
+template <int R>
+static cudaError_t deposit_tiled_r(const void* x, int np, int n, double mass, void* rho, cudaStream_t st) {
+    typedef DepTile<R> D;
+    const int lognp = ilog2(np), logn = ilog2(n);
+    const unsigned blocks = (unsigned)((np / D::TX) * (np / D::TY) * (np / D::TZ));
+    const float inv = (float)ldexp(1.0, -(32 - logn));
+    const size_t smem = sizeof(float) * D::CELLS;
+    cudaError_t e = cudaFuncSetAttribute((const void*)k_deposit_tiled<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    k_deposit_tiled<R><<<blocks, 512, smem, st>>>((const uint32_t*)x, lognp, logn, inv, (float)mass, (float*)rho);
+    return cudaGetLastError();
+}
+
+cudaError_t deposit_lattice(const void* x, int np, int precision, int n, double mass, void* rho, cudaStream_t st) {
+    const int R = n / np;
+    // the tile box (16 + 4) x (16 + 4) x (32 + 4) cells must fit in the mesh without overlapping itself
+    const bool tiled = precision == PM_FP32_FIXED && n >= 64 && (R == 1 || R == 2 || R == 4) && np >= 32 / R;
+    if (!tiled) return deposit(x, (int64_t)np * np * np, precision, n, mass, rho, st);
+    if (R == 1) return deposit_tiled_r<1>(x, np, n, mass, rho, st);
+    if (R == 2) return deposit_tiled_r<2>(x, np, n, mass, rho, st);
+    return deposit_tiled_r<4>(x, np, n, mass, rho, st);
 }
 
 cudaError_t deposit(const void* x, int64_t count, int precision, int n, double mass, void* rho,
@@ -166,32 +259,69 @@ cudaError_t interp(const void* field, int n, const void* x, int64_t count, int p
 }
 
 // ---------------------------------------------------------------- interp + kick + drift
-// p += kick * g(x);  x += drift * p   (g = -grad phi gathered with the deposit's weights)
+// p += kick * g(x);  x += drift * p   (g = -grad phi gathered with the deposit's weights).
+__device__ __forceinline__ void ikd_particle(uint32_t& u0, uint32_t& u1, uint32_t& u2, float& p0, float& p1,
+                                             float& p2, int logn, float inv_cell_ticks, const float* __restrict__ gx,
+                                             const float* __restrict__ gy, const float* __restrict__ gz, float kick,
+                                             float drift_ticks) {
+    const size_t n = (size_t)1 << logn;
+    const CicF cx = cic_ticks(u0, logn, inv_cell_ticks);
+    const CicF cy = cic_ticks(u1, logn, inv_cell_ticks);
+    const CicF cz = cic_ticks(u2, logn, inv_cell_ticks);
+    const float wx[2] = {1.0f - cx.w1, cx.w1}, wy[2] = {1.0f - cy.w1, cy.w1}, wz[2] = {1.0f - cz.w1, cz.w1};
+    const int ix[2] = {cx.i0, cx.i1}, iy[2] = {cy.i0, cy.i1}, iz[2] = {cz.i0, cz.i1};
+    p0 += kick * gather8<float, uint32_t>(gx, n, ix, iy, iz, wx, wy, wz);
+    p1 += kick * gather8<float, uint32_t>(gy, n, ix, iy, iz, wx, wy, wz);
+    p2 += kick * gather8<float, uint32_t>(gz, n, ix, iy, iz, wx, wy, wz);
+    u0 += (uint32_t)__float2ll_rn(p0 * drift_ticks);
+    u1 += (uint32_t)__float2ll_rn(p1 * drift_ticks);
+    u2 += (uint32_t)__float2ll_rn(p2 * drift_ticks);
+}
+
 __global__ void __launch_bounds__(256) k_ikd_ticks(uint32_t* __restrict__ x, float* __restrict__ p, int64_t count,
                                                    int logn, float inv_cell_ticks, const float* __restrict__ gx,
                                                    const float* __restrict__ gy, const float* __restrict__ gz,
                                                    float kick, float drift_ticks) {
-    const size_t n = (size_t)1 << logn;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count;
          i += (int64_t)gridDim.x * blockDim.x) {
-        const uint32_t ux = x[i], uy = x[count + i], uz = x[2 * count + i];
-        const CicF cx = cic_ticks(ux, logn, inv_cell_ticks);
-        const CicF cy = cic_ticks(uy, logn, inv_cell_ticks);
-        const CicF cz = cic_ticks(uz, logn, inv_cell_ticks);
-        const float wx[2] = {1.0f - cx.w1, cx.w1}, wy[2] = {1.0f - cy.w1, cy.w1}, wz[2] = {1.0f - cz.w1, cz.w1};
-        const int ix[2] = {cx.i0, cx.i1}, iy[2] = {cy.i0, cy.i1}, iz[2] = {cz.i0, cz.i1};
-        const float fx = gather8<float, uint32_t>(gx, n, ix, iy, iz, wx, wy, wz);
-        const float fy = gather8<float, uint32_t>(gy, n, ix, iy, iz, wx, wy, wz);
-        const float fz = gather8<float, uint32_t>(gz, n, ix, iy, iz, wx, wy, wz);
-        const float px = p[i] + kick * fx;
-        const float py = p[count + i] + kick * fy;
-        const float pz = p[2 * count + i] + kick * fz;
-        p[i] = px;
-        p[count + i] = py;
-        p[2 * count + i] = pz;
-        x[i] = ux + (uint32_t)__float2ll_rn(px * drift_ticks);
-        x[count + i] = uy + (uint32_t)__float2ll_rn(py * drift_ticks);
-        x[2 * count + i] = uz + (uint32_t)__float2ll_rn(pz * drift_ticks);
+        uint32_t u0 = x[i], u1 = x[count + i], u2 = x[2 * count + i];
+        float p0 = p[i], p1 = p[count + i], p2 = p[2 * count + i];
+        ikd_particle(u0, u1, u2, p0, p1, p2, logn, inv_cell_ticks, gx, gy, gz, kick, drift_ticks);
+        p[i] = p0;
+        p[count + i] = p1;
+        p[2 * count + i] = p2;
+        x[i] = u0;
+        x[count + i] = u1;
+        x[2 * count + i] = u2;
+    }
+}
+
+// Same update, two neighbouring particles per thread through 8-byte loads and stores
+// (count even, arrays 8-byte aligned): neighbours share most CIC corners, so the
+// second particle's gathers mostly hit L1.
+__global__ void __launch_bounds__(256) k_ikd_ticks2(uint32_t* __restrict__ x, float* __restrict__ p, int64_t count,
+                                                    int logn, float inv_cell_ticks, const float* __restrict__ gx,
+                                                    const float* __restrict__ gy, const float* __restrict__ gz,
+                                                    float kick, float drift_ticks) {
+    const int64_t pairs = count >> 1;
+    uint2* x0 = reinterpret_cast<uint2*>(x);
+    uint2* x1 = reinterpret_cast<uint2*>(x + count);
+    uint2* x2 = reinterpret_cast<uint2*>(x + 2 * count);
+    float2* p0 = reinterpret_cast<float2*>(p);
+    float2* p1 = reinterpret_cast<float2*>(p + count);
+    float2* p2 = reinterpret_cast<float2*>(p + 2 * count);
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < pairs;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        uint2 a = x0[i], b = x1[i], c = x2[i];
+        float2 pa = p0[i], pb = p1[i], pc = p2[i];
+        ikd_particle(a.x, b.x, c.x, pa.x, pb.x, pc.x, logn, inv_cell_ticks, gx, gy, gz, kick, drift_ticks);
+        ikd_particle(a.y, b.y, c.y, pa.y, pb.y, pc.y, logn, inv_cell_ticks, gx, gy, gz, kick, drift_ticks);
+        p0[i] = pa;
+        p1[i] = pb;
+        p2[i] = pc;
+        x0[i] = a;
+        x1[i] = b;
+        x2[i] = c;
     }
 }
 
@@ -225,9 +355,15 @@ cudaError_t interp_kick_drift(void* x, void* p, int64_t count, int precision, in
     if (precision == PM_FP32_FIXED) {
         const float inv = (float)ldexp(1.0, -(32 - logn));
         const float dt = (float)(drift * 4294967296.0 / box);
-        k_ikd_ticks<<<grid_for(count, 256), 256, 0, st>>>((uint32_t*)x, (float*)p, count, logn, inv,
-                                                          (const float*)g[0], (const float*)g[1], (const float*)g[2],
-                                                          (float)kick, dt);
+        const bool pairs = (count % 2 == 0) && ((uintptr_t)x % 8 == 0) && ((uintptr_t)p % 8 == 0);
+        if (pairs)
+            k_ikd_ticks2<<<grid_for(count / 2, 256), 256, 0, st>>>((uint32_t*)x, (float*)p, count, logn, inv,
+                                                                   (const float*)g[0], (const float*)g[1],
+                                                                   (const float*)g[2], (float)kick, dt);
+        else
+            k_ikd_ticks<<<grid_for(count, 256), 256, 0, st>>>((uint32_t*)x, (float*)p, count, logn, inv,
+                                                              (const float*)g[0], (const float*)g[1],
+                                                              (const float*)g[2], (float)kick, dt);
     } else {
         k_ikd_frac<<<grid_for(count, 256), 256, 0, st>>>((double*)x, (double*)p, count, n, (const double*)g[0],
                                                          (const double*)g[1], (const double*)g[2], kick, drift / box);

@@ -10,6 +10,8 @@
 namespace pm {
 
 cudaError_t deposit(const void* x, int64_t count, int precision, int n, double mass, void* rho, cudaStream_t st);
+// Deposit of the np^3 lattice-ordered particles of a context (Lagrangian tiles when possible).
+cudaError_t deposit_lattice(const void* x, int np, int precision, int n, double mass, void* rho, cudaStream_t st);
 cudaError_t interp(const void* field, int n, const void* x, int64_t count, int precision, void* out,
                    cudaStream_t st);
 // g: three force meshes; kick = K(a, b); drift = D(a, b) in Mpc/h per unit p

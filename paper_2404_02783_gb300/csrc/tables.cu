@@ -1,0 +1,47 @@
+// Once-per-device constant tables: exp(-2 pi i k / 1024), k < 1024, in FP64 and
+// rounded to FP32, for the FFT passes of both precisions.
+#include <math.h>
+
+#include <mutex>
+
+#include "internal.h"
+
+namespace pm {
+
+cudaError_t upload_twiddles_f32(const float2* host);
+cudaError_t upload_twiddles_f64(const double2* host);
+
+static std::mutex g_tab_mutex;
+static bool g_tab_ready[128];
+
+cudaError_t ensure_device_tables() {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lock(g_tab_mutex);
+    if (dev >= 0 && dev < 128 && g_tab_ready[dev]) return cudaSuccess;
+    static float2 h32[1024];
+    static double2 h64[1024];
+    for (int k = 0; k < 1024; ++k) {
+        double c, s;
+        if (k % 256 == 0) {  // exact quarter turns
+            const int q = k / 256;
+            c = (q == 0) ? 1.0 : (q == 2 ? -1.0 : 0.0);
+            s = (q == 1) ? -1.0 : (q == 3 ? 1.0 : 0.0);
+        } else {
+            const double ang = -2.0 * M_PI * (double)k / 1024.0;
+            c = cos(ang);
+            s = sin(ang);
+        }
+        h64[k] = make_double2(c, s);
+        h32[k] = make_float2((float)c, (float)s);
+    }
+    e = upload_twiddles_f32(h32);
+    if (e != cudaSuccess) return e;
+    e = upload_twiddles_f64(h64);
+    if (e != cudaSuccess) return e;
+    if (dev >= 0 && dev < 128) g_tab_ready[dev] = true;
+    return cudaSuccess;
+}
+
+}  // namespace pm
