@@ -1,0 +1,169 @@
+"""Reverse-mode gradient of a field-level loss through the particle-mesh run.
+
+Oracle (test infrastructure only), FP64, positions as box fractions.
+
+The differentiable workload fits the initial white noise w of a run at field level
+(the paper's GR displacement and bias are field-level quantities, Secs. 2 and 5):
+
+    L(w) = (1/N^3) sum_c (delta(c) - delta_t(c))^2,
+
+with delta the CIC counting density contrast of the final particles and delta_t a
+target mesh.  The forward map is the Zel'dovich IC of ``ic`` (white-noise path)
+followed by the kick-drift-kick steps of ``pm``, written out here as a list of kick
+and drift operations so that the reverse sweep can walk it backwards:
+
+    drift  u <- u + D p / L          reverse: lambda_p += (D / L) lambda_u
+    kick   p <- p + K g(u)           reverse: lambda_u += K J(u)^T lambda_p
+
+with J(u)^T v = sum_j v_j grad(interp(G_j)) + m grad(interp(rho_bar)), where G_j are
+the force meshes at u, rho_bar = sum_j T_j^T V_j, V_j the CIC deposit of v_j and
+T_j the (real, antisymmetric) Fourier operator rho -> G_j, so T_j^T = -T_j.  The CIC
+weights are piecewise linear in u; their derivative is taken on the same side as the
+forward floor() (the right derivative at a cell boundary).
+"""
+import numpy as np
+
+from . import cic, gravity, ic, philox
+
+
+def _grad_gather(field, u, n):
+    """sum_c F(c) dW(u_p, c)/du_i for i = x, y, z: shape (3, Np)."""
+    base, frac = cic.mesh_coords(u, n)
+    flat = field.ravel()
+    out = np.zeros((3, base.shape[1]))
+    for dx in (0, 1):
+        for dy in (0, 1):
+            for dz in (0, 1):
+                d = (dx, dy, dz)
+                idx = (((base[0] + dx) % n) * n + (base[1] + dy) % n) * n + (base[2] + dz) % n
+                f = flat[idx]
+                w = [frac[a] if d[a] else 1.0 - frac[a] for a in range(3)]
+                dw = [n * (1.0 if d[a] else -1.0) for a in range(3)]
+                out[0] += dw[0] * w[1] * w[2] * f
+                out[1] += w[0] * dw[1] * w[2] * f
+                out[2] += w[0] * w[1] * dw[2] * f
+    return out
+
+
+def _weighted_deposit(u, weights, n):
+    """V(c) = sum_p weights_p W(u_p, c)."""
+    base, frac = cic.mesh_coords(u, n)
+    V = np.zeros(n**3)
+    for dx in (0, 1):
+        wx = frac[0] if dx else 1.0 - frac[0]
+        for dy in (0, 1):
+            wy = frac[1] if dy else 1.0 - frac[1]
+            for dz in (0, 1):
+                wz = frac[2] if dz else 1.0 - frac[2]
+                idx = (((base[0] + dx) % n) * n + (base[1] + dy) % n) * n + (base[2] + dz) % n
+                V += np.bincount(idx, weights=weights * wx * wy * wz, minlength=n**3)
+    return V.reshape(n, n, n)
+
+
+def _k_components(n, box):
+    kf = 2.0 * np.pi / box
+    f = philox.signed_freqs(n).astype(np.float64)
+    fz = np.arange(n // 2 + 1, dtype=np.float64)
+    NX, NY, NZ = np.meshgrid(f, f, fz, indexing="ij")
+    return [kf * np.where(np.abs(Nj) == n // 2, 0.0, Nj) for Nj in (NX, NY, NZ)]
+
+
+def _force_meshes(u, n, box, omega_m):
+    delta = cic.density_contrast(u, n)
+    phik = gravity.newton_potential_k(np.fft.rfftn(delta), n, box, omega_m)
+    return gravity.gradient_force(phik, n, box)
+
+
+def _rho_bar(V, n, box, omega_m):
+    """sum_j T_j^T V_j with T_j rho = IFFT[-i k_j C(k) FFT(rho)], C = -(3/2) Om / k^2: T_j^T = -T_j."""
+    k = _k_components(n, box)
+    _, _, k2 = gravity._wavenumbers(n, box)
+    C = np.zeros_like(k2)
+    C[k2 > 0] = -1.5 * omega_m / k2[k2 > 0]
+    acc = np.zeros((n, n, n // 2 + 1), dtype=np.complex128)
+    for j in range(3):
+        acc += 1j * k[j] * C * np.fft.rfftn(V[j])
+    return np.fft.irfftn(acc, s=(n, n, n), axes=(0, 1, 2))
+
+
+def _za_operator(w_or_s, n_p, box, cosmo, j):
+    """Psi_j = A_j w: the white-noise Zel'dovich displacement along axis j (Mpc/h)."""
+    dk = ic.linear_delta_k(cosmo, n_p, box, white_noise=w_or_s)
+    kf = 2.0 * np.pi / box
+    f = philox.signed_freqs(n_p).astype(np.float64)
+    fz = np.arange(n_p // 2 + 1, dtype=np.float64)
+    axes = np.meshgrid(f, f, fz, indexing="ij")
+    Nj = np.where(np.abs(axes[j]) == n_p // 2, 0.0, axes[j])
+    n2 = ic.mode_n2(n_p).astype(np.float64)
+    inv_k2 = np.zeros_like(n2)
+    inv_k2[n2 > 0] = 1.0 / (kf * kf * n2[n2 > 0])
+    return np.fft.irfftn(1j * kf * Nj * dk * inv_k2, s=(n_p,) * 3, axes=(0, 1, 2))
+
+
+def forward(cosmo, n_p, n_mesh, box, a_i, a_f, n_steps, w):
+    """ZA ICs from w and the KDK run; returns (u_final, p_final, ops)."""
+    psi = ic.za_displacement(ic.linear_delta_k(cosmo, n_p, box, white_noise=w), n_p, box).reshape(3, -1)
+    D, f, E = cosmo.growth_D(a_i), cosmo.growth_f(a_i), float(cosmo.E(a_i))
+    i = np.arange(n_p, dtype=np.float64) / n_p
+    X, Y, Z = np.meshgrid(i, i, i, indexing="ij")
+    u = np.stack([X.ravel(), Y.ravel(), Z.ravel()]) + D * psi / box
+    u = u - np.floor(u)
+    p = a_i**2 * E * f * D * psi
+    grid = a_i + (a_f - a_i) * np.arange(n_steps + 1) / n_steps
+    ops = []
+    mass = (n_mesh / n_p)**3
+
+    def accel(uu):
+        G = _force_meshes(uu, n_mesh, box, cosmo.omega_m)
+        return np.stack([cic.interpolate(G[j], uu) for j in range(3)])
+
+    synced = True
+    for s in range(n_steps):
+        a0, a1 = grid[s], grid[s + 1]
+        ah = 0.5 * (a0 + a1)
+        a_from = a0 if synced else 0.5 * (grid[s - 1] + a0)
+        K = cosmo.kick_factor(a_from, ah)
+        ops.append(("kick", K, u.copy()))
+        p = p + K * accel(u)
+        Dd = cosmo.drift_factor(a0, a1)
+        ops.append(("drift", Dd))
+        u = u + Dd * p / box
+        u = u - np.floor(u)
+        synced = False
+        if s == n_steps - 1:
+            K = cosmo.kick_factor(ah, a1)
+            ops.append(("kick", K, u.copy()))
+            p = p + K * accel(u)
+    return u, p, ops, mass
+
+
+def loss(cosmo, n_p, n_mesh, box, a_i, a_f, n_steps, w, delta_t):
+    u, _, _, _ = forward(cosmo, n_p, n_mesh, box, a_i, a_f, n_steps, w)
+    return float(np.mean((cic.density_contrast(u, n_mesh) - delta_t)**2))
+
+
+def loss_and_grad(cosmo, n_p, n_mesh, box, a_i, a_f, n_steps, w, delta_t):
+    """(L, dL/dw) with dL/dw of shape (n_p, n_p, n_p)."""
+    u, p, ops, mass = forward(cosmo, n_p, n_mesh, box, a_i, a_f, n_steps, w)
+    delta = cic.density_contrast(u, n_mesh)
+    L = float(np.mean((delta - delta_t)**2))
+    lam_rho = 2.0 * (delta - delta_t) / n_mesh**3
+    lam_u = mass * _grad_gather(lam_rho, u, n_mesh)
+    lam_p = np.zeros_like(lam_u)
+    for op in reversed(ops):
+        if op[0] == "drift":
+            lam_p += op[1] / box * lam_u
+        else:
+            K, uk = op[1], op[2]
+            G = _force_meshes(uk, n_mesh, box, cosmo.omega_m)
+            direct = sum(lam_p[j] * _grad_gather(G[j], uk, n_mesh) for j in range(3))
+            V = np.stack([_weighted_deposit(uk, lam_p[j], n_mesh) for j in range(3)])
+            rho_bar = _rho_bar(V, n_mesh, box, cosmo.omega_m)
+            lam_u = lam_u + K * (direct + mass * _grad_gather(rho_bar, uk, n_mesh))
+    D, f, E = cosmo.growth_D(a_i), cosmo.growth_f(a_i), float(cosmo.E(a_i))
+    s = (D / box) * lam_u + a_i**2 * E * f * D * lam_p
+    # lambda_w = sum_j A_j^T s_j and A_j^T = -A_j (odd, real Fourier multiplier)
+    grad = np.zeros((n_p, n_p, n_p))
+    for j in range(3):
+        grad -= _za_operator(s[j].reshape(n_p, n_p, n_p), n_p, box, cosmo, j)
+    return L, grad
