@@ -179,6 +179,26 @@ pm_status pm_power(pm_ctx* ctx, const void* field, const void* field2, int nbins
                    const double* edges, int deconvolve,
                    double* k_out, double* p_out, double* nmodes_out);
 
+/* Halo proxy of the linear-bias measurement (Sec. 5.2): the K = ceil(fraction n^3)
+ * densest cells of field (device mesh[n][n][n], ctx precision) -- or, field == NULL, of
+ * the CIC counting density of the context's particles -- ties broken by the lower linear
+ * index (x slowest), written as the tracer contrast delta_h = n_h / mean(n_h) - 1 into the
+ * device mesh delta_h (n_h = 1 on selected cells, 0 elsewhere).  *selected = K.  The
+ * selection is exact (radix select on the IEEE bit patterns).  Uses the context's
+ * spectrum buffers as scratch, so it must not run concurrently with pm_step. */
+pm_status pm_halo_proxy(pm_ctx* ctx, const void* field, double fraction, void* delta_h, int64_t* selected);
+
+/* Linear halo bias, Eq. b1: fits P_hm / P_mm = b1 [+ b1^GR calH^2 / k^2] [+ c k^2] by least
+ * squares weighted with the bins' mode counts, over the bins (edges as in pm_power) whose
+ * mean k is below k_max.  terms = 1: b1; 2: b1, b1^GR; 3: b1, b1^GR, c.  calH = a E(a)/c at
+ * the context's current scale factor.  P_hm is the cross spectrum of delta_h and delta_m
+ * (device meshes), both CIC-deconvolved.  coef[terms] receives the fit; k_out, ratio_out
+ * and nmodes_out (host arrays of nbins, may be NULL) the binned k, P_hm/P_mm and mode
+ * counts.  Synchronises. */
+pm_status pm_linear_bias(pm_ctx* ctx, const void* delta_h, const void* delta_m, int nbins, const double* edges,
+                         double k_max, int terms, double* coef, double* k_out, double* ratio_out,
+                         double* nmodes_out);
+
 /* Device scratch bytes pm_bispectrum needs for grid m and nbins bins. */
 pm_status pm_bispectrum_scratch_size(const pm_ctx* ctx, int m, int nbins, size_t* bytes);
 
@@ -192,6 +212,58 @@ pm_status pm_bispectrum_scratch_size(const pm_ctx* ctx, int m, int nbins, size_t
 pm_status pm_bispectrum(pm_ctx* ctx, const void* field, int nbins, const double* edges,
                         int m, int deconvolve, void* scratch, size_t scratch_bytes,
                         double* b_out, double* ntri_out);
+
+/* ------------------------------------------------------- gradient of a field loss
+ * Field-level fits (the paper's GR displacement and bias are field-level quantities,
+ * Secs. 2 and 5) need the gradient of a loss on the final density with respect to the
+ * initial phases.  L(w) = mean_c (delta(c) - delta_t(c))^2, with delta the CIC counting
+ * density contrast of the particles after the full a-grid (cfg.n_steps steps) started
+ * from the Zel'dovich ICs of the white-noise field w (device, np^3, as pm_ic_zeldovich
+ * with white_noise) and delta_t a device target mesh n^3.  pm_loss_grad returns L and
+ * writes dL/dw (device, np^3) by a reverse sweep: (x, p) checkpoints every
+ * checkpoint_every steps; each segment is re-run forward keeping its positions and
+ * force meshes; then the transposed drift, kick (direct CIC-gradient term plus the
+ * transposed deposit -> Green -> gradient chain) and Zel'dovich map are applied.  CIC
+ * weight derivatives are taken on the side of the forward floor().  FP32 Newtonian
+ * contexts only; scratch: pm_adjoint_scratch_size bytes (256-byte aligned).  Leaves the
+ * context's particles at an intermediate step (run pm_ic_zeldovich before stepping
+ * again).  Synchronises. */
+pm_status pm_adjoint_scratch_size(const pm_ctx* ctx, int checkpoint_every, size_t* bytes);
+pm_status pm_loss_grad(pm_ctx* ctx, const void* white_noise, const void* delta_target, int checkpoint_every,
+                       void* scratch, size_t scratch_bytes, double* loss, void* grad_w);
+
+/* ------------------------------------------------------- batch of realisations
+ * Many independent realisations (seeds, box sizes) of the same FP32 Newtonian run,
+ * advanced together: every pass of a step is one launch over all of them, and a
+ * multi-step run can be recorded once and replayed as a single CUDA graph launch.
+ * This serves the paper's ensembles of runs from shared phases (Secs. 2-3) and the
+ * variance of b1 across realisations (Sec. 5.2).  Requirements: precision
+ * PM_FP32_FIXED, mode PM_NEWTON, nmesh >= 64 and nmesh / np in {1, 2, 4}; cfg->box is
+ * the default box, boxes[r] (may be NULL) the box of realisation r.  Memory: one
+ * caller workspace of pm_batch_workspace_size bytes, particles [r][3][np^3], meshes
+ * [r][n^3].  The batch owns one extra CUDA stream and two events for graph replay. */
+typedef struct pm_batch pm_batch;
+pm_status pm_batch_workspace_size(const pm_config* cfg, int nreal, size_t* bytes);
+pm_status pm_batch_init(const pm_config* cfg, int nreal, const double* boxes, void* workspace, size_t bytes,
+                        void* stream, pm_batch** out);
+pm_status pm_batch_destroy(pm_batch* batch);
+/* Context view of realisation r (particles, density, estimators); valid while the batch
+ * lives.  Must not be stepped or destroyed by the caller. */
+pm_status pm_batch_context(pm_batch* batch, int r, pm_ctx** view);
+/* Zel'dovich ICs of every realisation from seeds[r] (as pm_ic_zeldovich). */
+pm_status pm_batch_ic(pm_batch* batch, const uint64_t* seeds, int paired);
+/* n_steps KDK steps of every realisation; use_graph != 0 records the run once (cached for
+ * the same start step and length) and replays it as one graph launch ordered after the
+ * batch stream's prior work.  PM_ERR_STATE when the a-grid would be overrun. */
+pm_status pm_batch_step(pm_batch* batch, int n_steps, int use_graph);
+pm_status pm_batch_state(pm_batch* batch, int* step, double* a, int* synchronised);
+/* Per-realisation P(k) of the particles: host arrays [nreal][nbins].  Synchronises. */
+pm_status pm_batch_power(pm_batch* batch, int nbins, const double* edges, int deconvolve, double* k_out,
+                         double* p_out, double* nmodes_out);
+/* Per-realisation halo-proxy linear bias (pm_halo_proxy + pm_linear_bias on the CIC
+ * density): coef_out [nreal][terms].  Synchronises. */
+pm_status pm_batch_bias(pm_batch* batch, double fraction, int nbins, const double* edges, double k_max, int terms,
+                        double* coef_out);
 
 /* ------------------------------------------------ stateless device operators
  * Building blocks of pm_step exposed for testing and reuse; every pointer is a

@@ -26,8 +26,10 @@ _STATUS = {0: "PM_OK", 1: "PM_ERR_INVALID_ARG", 2: "PM_ERR_CUDA", 3: "PM_ERR_WOR
 
 # every entry point declared in include/pm.h
 EXPORTS = ("pm_workspace_size", "pm_init", "pm_destroy", "pm_ic_zeldovich", "pm_step", "pm_particles",
-           "pm_set_particles", "pm_state", "pm_profile", "pm_timings", "pm_density", "pm_potential", "pm_displacement_correction", "pm_power",
+           "pm_set_particles", "pm_state", "pm_profile", "pm_timings", "pm_density", "pm_potential", "pm_displacement_correction", "pm_power", "pm_halo_proxy", "pm_linear_bias",
            "pm_bispectrum_scratch_size", "pm_bispectrum", "pm_cic_deposit", "pm_cic_interp",
+           "pm_adjoint_scratch_size", "pm_loss_grad", "pm_batch_workspace_size", "pm_batch_init", "pm_batch_destroy", "pm_batch_context", "pm_batch_ic",
+           "pm_batch_step", "pm_batch_state", "pm_batch_power", "pm_batch_bias",
            "pm_cell_sort_scratch_size", "pm_cell_sort", "pm_cell_sort_static", "pm_fft_r2c", "pm_fft_c2r", "pm_version", "pm_last_error")
 
 
@@ -83,8 +85,21 @@ def lib():
         "pm_potential": (vp, vp),
         "pm_displacement_correction": (vp, vp, vp, vp),
         "pm_power": (vp, vp, vp, i, pd, i, pd, pd, pd),
+        "pm_halo_proxy": (vp, vp, d, vp, ctypes.POINTER(i64)),
+        "pm_linear_bias": (vp, vp, vp, i, pd, d, i, pd, pd, pd, pd),
         "pm_bispectrum_scratch_size": (vp, i, i, ctypes.POINTER(sz)),
         "pm_bispectrum": (vp, vp, i, pd, i, i, vp, sz, pd, pd),
+        "pm_adjoint_scratch_size": (vp, i, ctypes.POINTER(sz)),
+        "pm_loss_grad": (vp, vp, vp, i, vp, sz, pd, vp),
+        "pm_batch_workspace_size": (cfgp, i, ctypes.POINTER(sz)),
+        "pm_batch_init": (cfgp, i, pd, vp, sz, vp, ctypes.POINTER(vp)),
+        "pm_batch_destroy": (vp,),
+        "pm_batch_context": (vp, i, ctypes.POINTER(vp)),
+        "pm_batch_ic": (vp, ctypes.POINTER(u64), i),
+        "pm_batch_step": (vp, i, i),
+        "pm_batch_state": (vp, ctypes.POINTER(i), pd, ctypes.POINTER(i)),
+        "pm_batch_power": (vp, i, pd, i, pd, pd, pd),
+        "pm_batch_bias": (vp, d, i, pd, d, i, pd),
         "pm_cic_deposit": (vp, i64, i, i, d, vp, vp),
         "pm_cic_interp": (vp, i, vp, i64, i, vp, vp),
         "pm_cell_sort_scratch_size": (i64, i, ctypes.POINTER(sz)),
@@ -210,6 +225,24 @@ def pm_power(ctx, edges, field=None, field2=None, deconvolve=True):
     _check(lib().pm_power(ctx, _ptr(field), _ptr(field2), nb, _dptr(edges), int(bool(deconvolve)), _dptr(k),
                           _dptr(p), _dptr(nm)))
     return k, p, nm
+
+
+def pm_halo_proxy(ctx, out, field=None, fraction=0.05):
+    """delta_h of the ceil(fraction n^3) densest cells (ties by lower index); returns K."""
+    k = ctypes.c_int64()
+    _check(lib().pm_halo_proxy(ctx, _ptr(field), float(fraction), _ptr(out), ctypes.byref(k)))
+    return k.value
+
+
+def pm_linear_bias(ctx, delta_h, delta_m, edges, k_max, terms=1):
+    """Eq. b1 fit: returns (coef, k, ratio, nmodes)."""
+    edges = np.ascontiguousarray(edges, dtype=np.float64)
+    nb = len(edges) - 1
+    coef = np.zeros(3)
+    k, r, nm = np.empty(nb), np.empty(nb), np.empty(nb)
+    _check(lib().pm_linear_bias(ctx, _ptr(delta_h), _ptr(delta_m), nb, _dptr(edges), float(k_max), int(terms),
+                                _dptr(coef), _dptr(k), _dptr(r), _dptr(nm)))
+    return coef[:terms], k, r, nm
 
 
 def pm_bispectrum_scratch_size(ctx, m, nbins):
@@ -339,9 +372,111 @@ class PMRun:
     def state(self):
         return pm_state(self.ctx)
 
+    def loss_grad(self, white_noise, target, checkpoint_every=10):
+        """(L, dL/dw) of L = mean((delta_final - target)^2) for ICs from white_noise (pm_loss_grad)."""
+        import torch
+        out = ctypes.c_size_t()
+        _check(lib().pm_adjoint_scratch_size(self.ctx, int(checkpoint_every), ctypes.byref(out)))
+        scratch = torch.empty(out.value + 256, dtype=torch.uint8, device=self.device)
+        off = (-scratch.data_ptr()) % 256
+        grad = torch.empty_like(white_noise)
+        loss = ctypes.c_double()
+        _check(lib().pm_loss_grad(self.ctx, _ptr(white_noise), _ptr(target), int(checkpoint_every),
+                                  _ptr(scratch[off:]), out.value, ctypes.byref(loss), _ptr(grad)))
+        return loss.value, grad
+
     @property
     def kf(self):
         return 2 * math.pi / self.cfg.box
+
+
+def field_loss(run, white_noise, target, checkpoint_every=10):
+    """Differentiable L(w) = mean((delta_final(w) - target)^2) through the whole PM run.
+
+    A torch.autograd.Function: the forward pass runs pm_loss_grad (loss and gradient
+    in one reverse sweep on the GPU) and the backward pass scales the stored gradient.
+    """
+    import torch
+
+    class _FieldLoss(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, w):
+            loss, grad = run.loss_grad(w.detach().contiguous(), target, checkpoint_every)
+            ctx.save_for_backward(grad)
+            return torch.tensor(loss, dtype=torch.float64, device=w.device)
+
+        @staticmethod
+        def backward(ctx, gout):
+            (grad,) = ctx.saved_tensors
+            return (gout.to(grad.dtype) * grad,)
+
+    return _FieldLoss.apply(white_noise)
+
+
+class PMBatch:
+    """Independent realisations advanced together (pm_batch_*), on a torch workspace."""
+
+    def __init__(self, cfg, boxes=None, device="cuda", stream=None):
+        import torch
+        self.cfg = cfg
+        self.B = len(boxes)
+        self.boxes = np.ascontiguousarray(boxes, dtype=np.float64)
+        out = ctypes.c_size_t()
+        _check(lib().pm_batch_workspace_size(ctypes.byref(cfg), self.B, ctypes.byref(out)))
+        nbytes = out.value
+        self.workspace = torch.empty(nbytes + 256, dtype=torch.uint8, device=device)
+        off = (-self.workspace.data_ptr()) % 256
+        self._ws = self.workspace[off:off + nbytes]
+        h = ctypes.c_void_p()
+        _check(lib().pm_batch_init(ctypes.byref(cfg), self.B, _dptr(self.boxes), _ptr(self._ws), nbytes,
+                                   _stream(stream), ctypes.byref(h)))
+        self.h = h
+        self.count = cfg.np**3
+
+    def __del__(self):
+        h = getattr(self, "h", None)
+        if h is not None and _lib is not None:
+            _lib.pm_batch_destroy(h)
+            self.h = None
+
+    def ic(self, seeds, paired=False):
+        s = np.ascontiguousarray(seeds, dtype=np.uint64)
+        _check(lib().pm_batch_ic(self.h, s.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)), int(bool(paired))))
+
+    def step(self, n=1, graph=True):
+        _check(lib().pm_batch_step(self.h, int(n), int(bool(graph))))
+
+    def state(self):
+        s, a, y = ctypes.c_int(), ctypes.c_double(), ctypes.c_int()
+        _check(lib().pm_batch_state(self.h, ctypes.byref(s), ctypes.byref(a), ctypes.byref(y)))
+        return s.value, a.value, bool(y.value)
+
+    def context(self, r):
+        v = ctypes.c_void_p()
+        _check(lib().pm_batch_context(self.h, int(r), ctypes.byref(v)))
+        return v
+
+    def particles(self, r):
+        import torch
+        xp, pp = pm_particles(self.context(r))
+        nbytes = 3 * self.count * 4
+        x = _view(self._ws, xp, nbytes).view(torch.int32).view(3, self.count)
+        p = _view(self._ws, pp, nbytes).view(torch.float32).view(3, self.count)
+        return x, p
+
+    def power(self, edges, deconvolve=True):
+        edges = np.ascontiguousarray(edges, dtype=np.float64)
+        nb = len(edges) - 1
+        k, p, nm = (np.empty((self.B, nb)) for _ in range(3))
+        _check(lib().pm_batch_power(self.h, nb, _dptr(edges), int(bool(deconvolve)), _dptr(k), _dptr(p), _dptr(nm)))
+        return k, p, nm
+
+    def bias(self, edges, k_max, fraction=0.05, terms=1):
+        edges = np.ascontiguousarray(edges, dtype=np.float64)
+        coef = np.empty((self.B, terms))
+        _check(lib().pm_batch_bias(self.h, float(fraction), len(edges) - 1, _dptr(edges), float(k_max), int(terms),
+                                   _dptr(coef)))
+        return coef
 
 
 def _view(ws, ptr, nbytes):

@@ -1,0 +1,211 @@
+// Kernels of the reverse sweep (gradient of a field-level loss with respect to the
+// initial white noise) through the FP32 particle-mesh step.
+//
+// Positions enter as uint32 ticks and derivatives are taken with respect to the box
+// fraction u = ticks / 2^32.  With mesh coordinate s = u n - 1/2 the CIC weights of a
+// particle along one axis are (1 - d, d), d = s - floor(s), so dW/du = n (-1, +1) on
+// the same side of a cell boundary as the forward floor().
+#include "internal.h"
+#include "particles.h"
+
+namespace pm {
+
+namespace {
+
+struct Cic1 {
+    int i0, i1;
+    float w1;
+};
+__device__ __forceinline__ Cic1 decode(uint32_t u, int logn, float inv_cell_ticks) {
+    const int sh = 32 - logn;
+    const uint32_t t = u - (1u << (sh - 1));
+    Cic1 c;
+    c.i0 = (int)(t >> sh);
+    c.i1 = (c.i0 + 1) & ((1 << logn) - 1);
+    c.w1 = __uint2float_rn(t & ((1u << sh) - 1u)) * inv_cell_ticks;
+    return c;
+}
+
+// grad_u of sum_c F(c) W(u, c) for the three axes.
+__device__ __forceinline__ void grad_gather(const float* __restrict__ F, size_t n, const Cic1& cx, const Cic1& cy,
+                                            const Cic1& cz, float out[3]) {
+    const float nf = (float)n;
+    const int ix[2] = {cx.i0, cx.i1}, iy[2] = {cy.i0, cy.i1}, iz[2] = {cz.i0, cz.i1};
+    const float wx[2] = {1.0f - cx.w1, cx.w1}, wy[2] = {1.0f - cy.w1, cy.w1}, wz[2] = {1.0f - cz.w1, cz.w1};
+    const float dw[2] = {-nf, nf};
+    out[0] = out[1] = out[2] = 0.0f;
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int b = 0; b < 2; ++b)
+#pragma unroll
+            for (int c = 0; c < 2; ++c) {
+                const float f = __ldg(F + ((size_t)ix[a] * n + iy[b]) * n + iz[c]);
+                out[0] += dw[a] * wy[b] * wz[c] * f;
+                out[1] += wx[a] * dw[b] * wz[c] * f;
+                out[2] += wx[a] * wy[b] * dw[c] * f;
+            }
+}
+
+}  // namespace
+
+// lam_u (+)= scale grad_u interp(F)
+__global__ void k_adj_gather(const uint32_t* __restrict__ x, int64_t count, int logn, float inv_cell_ticks,
+                             const float* __restrict__ F, float scale, int accumulate, float* __restrict__ lam_u) {
+    const size_t n = (size_t)1 << logn;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x) {
+        const Cic1 cx = decode(x[i], logn, inv_cell_ticks), cy = decode(x[count + i], logn, inv_cell_ticks),
+                   cz = decode(x[2 * count + i], logn, inv_cell_ticks);
+        float g[3];
+        grad_gather(F, n, cx, cy, cz, g);
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            const float v = scale * g[j];
+            lam_u[j * count + i] = accumulate ? lam_u[j * count + i] + v : v;
+        }
+    }
+}
+
+// lam_u += K sum_j v_j grad_u interp(G_j)  (the direct part of the transposed kick)
+__global__ void k_adj_direct(const uint32_t* __restrict__ x, int64_t count, int logn, float inv_cell_ticks,
+                             const float* __restrict__ v, const float* __restrict__ G0, const float* __restrict__ G1,
+                             const float* __restrict__ G2, float K, float* __restrict__ lam_u) {
+    const size_t n = (size_t)1 << logn;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x) {
+        const Cic1 cx = decode(x[i], logn, inv_cell_ticks), cy = decode(x[count + i], logn, inv_cell_ticks),
+                   cz = decode(x[2 * count + i], logn, inv_cell_ticks);
+        const float v0 = v[i], v1 = v[count + i], v2 = v[2 * count + i];
+        float g0[3], g1[3], g2[3];
+        grad_gather(G0, n, cx, cy, cz, g0);
+        grad_gather(G1, n, cx, cy, cz, g1);
+        grad_gather(G2, n, cx, cy, cz, g2);
+#pragma unroll
+        for (int j = 0; j < 3; ++j) lam_u[j * count + i] += K * (v0 * g0[j] + v1 * g1[j] + v2 * g2[j]);
+    }
+}
+
+// V_j(c) += sum_p v_j W(u_p, c) for the three components
+__global__ void k_deposit_vec(const uint32_t* __restrict__ x, int64_t count, int logn, float inv_cell_ticks,
+                              const float* __restrict__ v, float* __restrict__ V0, float* __restrict__ V1,
+                              float* __restrict__ V2) {
+    const size_t n = (size_t)1 << logn;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x) {
+        const Cic1 cx = decode(x[i], logn, inv_cell_ticks), cy = decode(x[count + i], logn, inv_cell_ticks),
+                   cz = decode(x[2 * count + i], logn, inv_cell_ticks);
+        const float vv[3] = {v[i], v[count + i], v[2 * count + i]};
+        const int ix[2] = {cx.i0, cx.i1}, iy[2] = {cy.i0, cy.i1}, iz[2] = {cz.i0, cz.i1};
+        const float wx[2] = {1.0f - cx.w1, cx.w1}, wy[2] = {1.0f - cy.w1, cy.w1}, wz[2] = {1.0f - cz.w1, cz.w1};
+#pragma unroll
+        for (int a = 0; a < 2; ++a)
+#pragma unroll
+            for (int b = 0; b < 2; ++b)
+#pragma unroll
+                for (int c = 0; c < 2; ++c) {
+                    const float w = wx[a] * wy[b] * wz[c];
+                    const size_t id = ((size_t)ix[a] * n + iy[b]) * n + iz[c];
+                    atomicAdd(V0 + id, w * vv[0]);
+                    atomicAdd(V1 + id, w * vv[1]);
+                    atomicAdd(V2 + id, w * vv[2]);
+                }
+    }
+}
+
+// out = sum_j i k_j c(k) in_j on the [kz][kx][ky] half spectrum, with
+//   mode 0 (transposed force): c = -(3/2) Om / (k^2 n^3), k_j = 0 at the Nyquist index;
+//   mode 1 (transposed Zel'dovich map): c = -amp(|n|^2) np^{-3/2} / k^2, zero on every
+//   mode with a Nyquist component.  The zero mode is zero.
+__global__ void k_adj_combine(const float2* __restrict__ in0, const float2* __restrict__ in1,
+                              const float2* __restrict__ in2, float2* __restrict__ out, int n, double kf, double coef,
+                              const double* __restrict__ amp, int mode) {
+    const int M = n / 2;
+    const int64_t total = (int64_t)(M + 1) * n * n;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int kz = (int)(e / ((int64_t)n * n));
+        const int rem = (int)(e - (int64_t)kz * n * n);
+        const int nx = signed_k(rem / n, n), ny = signed_k(rem % n, n), nz = kz;
+        const int n2 = nx * nx + ny * ny + nz * nz;
+        float2 r = make_float2(0.f, 0.f);
+        const bool nyq_any = (2 * nx == -n) || (2 * ny == -n) || (nz == M);
+        if (n2 > 0 && !(mode == 1 && nyq_any)) {
+            double c = coef / (kf * kf * (double)n2);
+            if (mode == 1) c *= amp[n2];
+            const float kx = (2 * nx == -n) ? 0.f : (float)(kf * nx);
+            const float ky = (2 * ny == -n) ? 0.f : (float)(kf * ny);
+            const float kzz = (nz == M) ? 0.f : (float)(kf * nz);
+            const float2 a = in0[e], b = in1[e], d = in2[e];
+            // i k_j c z = c k_j (-z.y, z.x)
+            const float sx = kx * a.x + ky * b.x + kzz * d.x;
+            const float sy = kx * a.y + ky * b.y + kzz * d.y;
+            r = make_float2((float)(-c * sy), (float)(c * sx));
+        }
+        out[e] = r;
+    }
+}
+
+// lambda_rho = 2 (delta - target) / n^3 (in place over delta) and sum (delta - target)^2
+__global__ void k_loss(float* __restrict__ delta, const float* __restrict__ target, int64_t n3, double inv_n3,
+                       double* __restrict__ acc) {
+    double s = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n3; i += (int64_t)gridDim.x * blockDim.x) {
+        const float d = delta[i] - target[i];
+        s += (double)d * (double)d;
+        delta[i] = (float)(2.0 * inv_n3 * (double)d);
+    }
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) atomicAdd(acc, s);
+}
+
+// y = alpha a + beta b (three components, count each); b may be null
+__global__ void k_axpby(float* __restrict__ y, const float* __restrict__ a, const float* __restrict__ b, int64_t m,
+                        float alpha, float beta) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x)
+        y[i] = alpha * a[i] + (b ? beta * b[i] : 0.0f);
+}
+
+static unsigned blocks_for(int64_t count) {
+    int64_t b = (count + 255) / 256;
+    if (b > 152 * 16) b = 152 * 16;
+    return (unsigned)(b < 1 ? 1 : b);
+}
+
+cudaError_t adj_gather(const uint32_t* x, int64_t count, int n, const float* F, float scale, int accumulate,
+                       float* lam_u, cudaStream_t st) {
+    const int logn = ilog2(n);
+    k_adj_gather<<<blocks_for(count), 256, 0, st>>>(x, count, logn, (float)ldexp(1.0, -(32 - logn)), F, scale,
+                                                    accumulate, lam_u);
+    return cudaGetLastError();
+}
+
+cudaError_t adj_direct(const uint32_t* x, int64_t count, int n, const float* v, const float* const* G, float K,
+                       float* lam_u, cudaStream_t st) {
+    const int logn = ilog2(n);
+    k_adj_direct<<<blocks_for(count), 256, 0, st>>>(x, count, logn, (float)ldexp(1.0, -(32 - logn)), v, G[0], G[1],
+                                                    G[2], K, lam_u);
+    return cudaGetLastError();
+}
+
+cudaError_t deposit_vec(const uint32_t* x, int64_t count, int n, const float* v, float* const* V, cudaStream_t st) {
+    const int logn = ilog2(n);
+    k_deposit_vec<<<blocks_for(count), 256, 0, st>>>(x, count, logn, (float)ldexp(1.0, -(32 - logn)), v, V[0], V[1],
+                                                     V[2]);
+    return cudaGetLastError();
+}
+
+cudaError_t adj_combine(const float2* const* in, float2* out, int n, double kf, double coef, const double* amp,
+                        int mode, cudaStream_t st) {
+    const int64_t total = (int64_t)(n / 2 + 1) * n * n;
+    k_adj_combine<<<blocks_for(total), 256, 0, st>>>(in[0], in[1], in[2], out, n, kf, coef, amp, mode);
+    return cudaGetLastError();
+}
+
+cudaError_t loss_mse(float* delta, const float* target, int64_t n3, double* acc, cudaStream_t st) {
+    k_loss<<<blocks_for(n3), 256, 0, st>>>(delta, target, n3, 1.0 / (double)n3, acc);
+    return cudaGetLastError();
+}
+
+cudaError_t axpby(float* y, const float* a, const float* b, int64_t m, float alpha, float beta, cudaStream_t st) {
+    k_axpby<<<blocks_for(m), 256, 0, st>>>(y, a, b, m, alpha, beta);
+    return cudaGetLastError();
+}
+
+}  // namespace pm

@@ -119,6 +119,11 @@ struct pm_ctx {
     bool synced = true;
     bool have_phi = false;
     double a_last = 0.0;
+    // device scratch of the halo-proxy selection (spectrum buffers by default)
+    size_t scratch_off = 0, scratch_bytes = 0;
+    // rho holds the counting density of the current positions (left by the fused
+    // kick-drift-deposit pass of the previous step)
+    bool rho_valid = false;
     // per-phase timing (pm_profile / pm_timings)
     bool prof = false;
     std::vector<cudaEvent_t> pool;
@@ -193,22 +198,37 @@ pm_status deposit_particles(pm_ctx* c, void* rho) {
 }
 
 // Force meshes g = -grad phi of the current particles at scale factor a.
+bool fused_update(const pm_ctx* c) { return ikd_deposit_supported(c->np, c->cfg.precision, c->n); }
+
 template <typename T>
 pm_status compute_forces_t(pm_ctx* c, double a) {
     const int n = c->n;
     void* rho = c->at(c->L.rho);
-    PM_TRY(deposit_particles(c, rho));
+    if (!c->rho_valid) PM_TRY(deposit_particles(c, rho));
     cplx<T>* s0 = (cplx<T>*)c->at(c->L.spec[0]);
     cplx<T>* s1 = (cplx<T>*)c->at(c->L.spec[1]);
     cplx<T>* s2 = (cplx<T>*)c->at(c->L.spec[2]);
-    PM_TRY(forward_to_y<T>(c, rho, s0, n));
+    {
+        Phase ph(c, PM_PHASE_FFT_Z_R2C);
+        PM_CK(z_r2c<T>((const T*)rho, s0, n, 1, c->st));
+    }
+    if (fused_update(c)) {
+        // the forward z pass has consumed rho: clear it for the fused deposit of the update
+        Phase ph(c, PM_PHASE_DEPOSIT);
+        PM_CK(cudaMemsetAsync(rho, 0, sizeof(T) * (size_t)n * n * n, c->st));
+    }
+    c->rho_valid = false;
+    {
+        Phase ph(c, PM_PHASE_FFT_Y_FWD);
+        PM_CK((y_rows<T, false>(s0, (int64_t)(n / 2 + 1) * n, n, c->st)));
+    }
     SpecOp op;
     op.kf = c->kf;
     op.fwd = 1;
     const double n3 = (double)n * n * n;
     if (c->cfg.mode == PM_NEWTON) {
         op.kind = OP_NEWTON;
-        op.coef = -1.5 * c->cfg.omega_m / (c->kf * c->kf * n3);
+        op.coef = -1.5 * c->cfg.omega_m / n3;
     } else {
         op.kind = OP_GR;
         op.calH = pmhost::conformal_hubble(c->cosmo, a);
@@ -248,6 +268,12 @@ pm_status compute_forces(pm_ctx* c, double a) {
 pm_status kick_drift(pm_ctx* c, double kick, double drift) {
     Phase ph(c, PM_PHASE_KICK_DRIFT);
     void* g[3] = {c->at(c->L.force[0]), c->at(c->L.force[1]), c->at(c->L.force[2])};
+    if (fused_update(c)) {
+        PM_CK(interp_kick_drift_deposit(c->at(c->L.x), c->at(c->L.p), c->np, c->cfg.precision, c->n, g, kick, drift,
+                                        c->cfg.box, std::pow((double)c->n / c->np, 3), c->at(c->L.rho), c->st));
+        c->rho_valid = true;
+        return PM_OK;
+    }
     PM_CK(interp_kick_drift(c->at(c->L.x), c->at(c->L.p), c->np3, c->cfg.precision, c->n, g, kick, drift,
                             c->cfg.box, c->st));
     return PM_OK;
@@ -441,6 +467,8 @@ pm_status pm_init(const pm_config* cfg, void* workspace, size_t bytes, void* str
     c->np = cfg->np;
     c->np3 = (int64_t)cfg->np * cfg->np * cfg->np;
     c->kf = 2.0 * M_PI / cfg->box;
+    c->scratch_off = L.spec[0];
+    c->scratch_bytes = L.force[0] - L.spec[0];
     c->cosmo.omega_m = cfg->omega_m;
     c->cosmo.omega_b = cfg->omega_b;
     c->cosmo.h = cfg->h;
@@ -494,6 +522,7 @@ pm_status pm_set_particles(pm_ctx* c, const void* x, const void* p) {
     c->step = 0;
     c->synced = true;
     c->have_phi = false;
+    c->rho_valid = false;
     return PM_OK;
 }
 
@@ -531,7 +560,7 @@ pm_status pm_ic_zeldovich(pm_ctx* c, uint64_t seed, const void* white_noise, int
         else PM_CK(noise<float>((float2*)s0, np, seed, c->st));
         op.fwd = 0;
     }
-    op.coef = -sign * scale / (c->kf * c->kf);
+    op.coef = -sign * scale;
     void* psi[3] = {c->at(c->L.force[0]), c->at(c->L.force[1]), c->at(c->L.force[2])};
     if (c->fp64()) {
         PM_CK(x_cols<double>((double2*)s0, (double2*)s1, np / 2 + 1, np, op, c->st));
@@ -552,6 +581,7 @@ pm_status pm_ic_zeldovich(pm_ctx* c, uint64_t seed, const void* white_noise, int
     c->step = 0;
     c->synced = true;
     c->have_phi = false;
+    c->rho_valid = false;
     return PM_OK;
 }
 
@@ -620,7 +650,7 @@ pm_status pm_potential(pm_ctx* c, void* phi) {
     op.kind = OP_POTENTIAL;
     op.fwd = 1;
     op.kf = c->kf;
-    op.coef = -1.5 * c->cfg.omega_m / (c->kf * c->kf * (double)n * n * n);
+    op.coef = -1.5 * c->cfg.omega_m / ((double)n * n * n);
     if (c->fp64()) {
         double2* s0 = (double2*)c->at(c->L.spec[0]);
         PM_TRY(forward_to_y<double>(c, c->at(c->L.rho), s0, n));
@@ -652,6 +682,7 @@ pm_status pm_displacement_correction(pm_ctx* target, const pm_ctx* gr, const pm_
     if (newton->st != target->st) PM_CK(cudaStreamSynchronize(newton->st));
     PM_CK(combine(target->at(target->L.x), gr->at(gr->L.x), newton->at(newton->L.x), xi_out, target->np, gr->np,
                   target->cfg.precision, target->st));
+    target->rho_valid = false;
     return PM_OK;
 }
 
@@ -661,6 +692,81 @@ pm_status pm_power(pm_ctx* c, const void* field, const void* field2, int nbins, 
     PM_TRY(check_edges(nbins, edges));
     return c->fp64() ? power_t<double>(c, field, field2, nbins, edges, deconvolve, k_out, p_out, nmodes_out)
                      : power_t<float>(c, field, field2, nbins, edges, deconvolve, k_out, p_out, nmodes_out);
+}
+
+pm_status pm_halo_proxy(pm_ctx* c, const void* field, double fraction, void* delta_h, int64_t* selected) {
+    if (!c || !delta_h) return fail(PM_ERR_INVALID_ARG, "null argument");
+    if (!(fraction > 0.0 && fraction <= 1.0)) return fail(PM_ERR_INVALID_ARG, "fraction must be in (0, 1]");
+    const int64_t n3 = (int64_t)c->n * c->n * c->n;
+    if (n3 > 0xFFFFFFFFll) return fail(PM_ERR_INVALID_ARG, "mesh too large for 32-bit ranks");
+    const int64_t K = (int64_t)std::ceil(fraction * (double)n3);
+    const void* f = field;
+    if (!f) {
+        c->rho_valid = false;  // rho is about to hold delta = rho - 1
+        PM_CK(fill(c->at(c->L.rho), n3, c->cfg.precision, -1.0, c->st));
+        PM_CK(deposit_lattice(c->at(c->L.x), c->np, c->cfg.precision, c->n, std::pow((double)c->n / c->np, 3),
+                              c->at(c->L.rho), c->st));
+        f = c->at(c->L.rho);
+    }
+    // spectrum buffers are free outside a step and serve as scratch
+    if (halo_proxy_scratch_bytes(n3) > c->scratch_bytes)
+        return fail(PM_ERR_WORKSPACE, "workspace too small for the selection");
+    void* scratch = c->at(c->scratch_off);
+    if (c->fp64())
+        PM_CK(halo_proxy<double>((const double*)f, n3, K, (double*)delta_h, scratch, c->st));
+    else
+        PM_CK(halo_proxy<float>((const float*)f, n3, K, (float*)delta_h, scratch, c->st));
+    if (selected) *selected = K;
+    return PM_OK;
+}
+
+pm_status pm_linear_bias(pm_ctx* c, const void* delta_h, const void* delta_m, int nbins, const double* edges,
+                         double k_max, int terms, double* coef, double* k_out, double* ratio_out, double* nmodes_out) {
+    if (!c || !delta_h || !delta_m || !coef) return fail(PM_ERR_INVALID_ARG, "null argument");
+    if (terms < 1 || terms > 3) return fail(PM_ERR_INVALID_ARG, "terms must be 1 (b1), 2 (+ b1GR) or 3 (+ k^2)");
+    PM_TRY(check_edges(nbins, edges));
+    std::vector<double> k(nbins), phm(nbins), pmm(nbins), nm(nbins);
+    PM_TRY(pm_power(c, delta_h, delta_m, nbins, edges, 1, k.data(), phm.data(), nm.data()));
+    PM_TRY(pm_power(c, delta_m, nullptr, nbins, edges, 1, nullptr, pmm.data(), nullptr));
+    const double a = c->a_grid(c->step);
+    const double H = pmhost::conformal_hubble(c->cosmo, a);
+    // weighted least squares (weights = mode counts) of P_hm/P_mm = b1 [+ b1GR H^2/k^2] [+ c k^2] on k < k_max
+    double AtA[3][3] = {{0}}, Atb[3] = {0};
+    int used = 0;
+    for (int b = 0; b < nbins; ++b) {
+        const double r = phm[b] / pmm[b];
+        if (ratio_out) ratio_out[b] = r;
+        if (k_out) k_out[b] = k[b];
+        if (nmodes_out) nmodes_out[b] = nm[b];
+        if (!(nm[b] > 0) || !std::isfinite(r) || !(k[b] < k_max)) continue;
+        const double row[3] = {1.0, H * H / (k[b] * k[b]), k[b] * k[b]};
+        for (int i = 0; i < terms; ++i) {
+            Atb[i] += nm[b] * row[i] * r;
+            for (int j = 0; j < terms; ++j) AtA[i][j] += nm[b] * row[i] * row[j];
+        }
+        ++used;
+    }
+    if (used < terms) return fail(PM_ERR_INVALID_ARG, "fewer usable bins than fit parameters");
+    // Gaussian elimination with partial pivoting
+    for (int i = 0; i < terms; ++i) {
+        int piv = i;
+        for (int r = i + 1; r < terms; ++r)
+            if (std::fabs(AtA[r][i]) > std::fabs(AtA[piv][i])) piv = r;
+        for (int j = 0; j < terms; ++j) std::swap(AtA[i][j], AtA[piv][j]);
+        std::swap(Atb[i], Atb[piv]);
+        if (AtA[i][i] == 0.0) return fail(PM_ERR_INVALID_ARG, "singular bias fit");
+        for (int r = i + 1; r < terms; ++r) {
+            const double fct = AtA[r][i] / AtA[i][i];
+            for (int j = i; j < terms; ++j) AtA[r][j] -= fct * AtA[i][j];
+            Atb[r] -= fct * Atb[i];
+        }
+    }
+    for (int i = terms - 1; i >= 0; --i) {
+        double s = Atb[i];
+        for (int j = i + 1; j < terms; ++j) s -= AtA[i][j] * coef[j];
+        coef[i] = s / AtA[i][i];
+    }
+    return PM_OK;
 }
 
 pm_status pm_bispectrum_scratch_size(const pm_ctx* c, int m, int nbins, size_t* bytes) {
@@ -687,6 +793,534 @@ pm_status pm_bispectrum(pm_ctx* c, const void* field, int nbins, const double* e
                      : bispectrum_t<float>(c, field, nbins, edges, m, deconvolve, (unsigned char*)scratch, B, b_out,
                                            ntri_out);
 }
+
+}  // extern "C"
+
+
+// ====================================================================== gradient of a field loss
+namespace {
+
+struct AdjLayout {
+    size_t ckpt = 0, seg_x = 0, seg_g = 0, lam_u = 0, lam_p = 0, acc = 0, total = 0;
+    int nseg = 0, C = 0;
+};
+
+AdjLayout adj_plan(const pm_ctx* c, int C) {
+    AdjLayout A;
+    const int S = c->cfg.n_steps;
+    A.C = C;
+    A.nseg = (S + C - 1) / C;
+    const size_t P = 3 * (size_t)c->np3 * 4, G = 3 * (size_t)c->n * c->n * c->n * 4;
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        const size_t o = off;
+        off = align256(off + bytes);
+        return o;
+    };
+    A.ckpt = take((size_t)A.nseg * 2 * P);
+    A.seg_x = take((size_t)(C + 1) * P);
+    A.seg_g = take((size_t)(C + 1) * G);
+    A.lam_u = take(P);
+    A.lam_p = take(P);
+    A.acc = take(8);
+    A.total = off;
+    return A;
+}
+
+// Forward transform of a real mesh of side n into spec ([kz][kx][ky]).
+pm_status fft_forward_f32(pm_ctx* c, const float* real, float2* spec, int n) {
+    PM_CK(z_r2c<float>(real, spec, n, 1, c->st));
+    PM_CK((y_rows<float, false>(spec, (int64_t)(n / 2 + 1) * n, n, c->st)));
+    SpecOp fw;
+    fw.kind = OP_FWD_STORE;
+    fw.fwd = 1;
+    PM_CK(x_cols<float>(spec, nullptr, n / 2 + 1, n, fw, c->st));
+    return PM_OK;
+}
+
+pm_status fft_inverse_f32(pm_ctx* c, float2* spec, float* real, int n) {
+    SpecOp inv;
+    inv.kind = OP_INV;
+    inv.fwd = 0;
+    PM_CK(x_cols<float>(spec, nullptr, n / 2 + 1, n, inv, c->st));
+    PM_CK((y_rows<float, true>(spec, (int64_t)(n / 2 + 1) * n, n, c->st)));
+    const float2* in[1] = {spec};
+    float* out[1] = {real};
+    PM_CK(z_c2r<float>(in, out, 1, n, 1, 0u, 0.0, c->st));
+    return PM_OK;
+}
+
+// lambda_u += K J(u)^T lambda_p at positions xs with force meshes gs (three n^3 meshes).
+pm_status adj_kick(pm_ctx* c, const uint32_t* xs, const float* gs, double K, float* lam_u, const float* lam_p) {
+    const int n = c->n;
+    const size_t n3 = (size_t)n * n * n;
+    const float* G[3] = {gs, gs + n3, gs + 2 * n3};
+    PM_CK(adj_direct(xs, c->np3, n, lam_p, G, (float)K, lam_u, c->st));
+    float* V[3] = {(float*)c->at(c->L.force[0]), (float*)c->at(c->L.force[1]), (float*)c->at(c->L.force[2])};
+    for (int j = 0; j < 3; ++j) PM_CK(cudaMemsetAsync(V[j], 0, n3 * 4, c->st));
+    PM_CK(deposit_vec(xs, c->np3, n, lam_p, V, c->st));
+    float2* sp[3] = {(float2*)c->at(c->L.spec[0]), (float2*)c->at(c->L.spec[1]), (float2*)c->at(c->L.spec[2])};
+    for (int j = 0; j < 3; ++j) PM_TRY(fft_forward_f32(c, V[j], sp[j], n));
+    const float2* in[3] = {sp[0], sp[1], sp[2]};
+    PM_CK(adj_combine(in, sp[0], n, c->kf, -1.5 * c->cfg.omega_m / ((double)n * n * n), nullptr, 0, c->st));
+    float* rho_bar = (float*)c->at(c->L.rho);
+    PM_TRY(fft_inverse_f32(c, sp[0], rho_bar, n));
+    const double mass = std::pow((double)n / c->np, 3);
+    PM_CK(adj_gather(xs, c->np3, n, rho_bar, (float)(K * mass), 1, lam_u, c->st));
+    return PM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+pm_status pm_adjoint_scratch_size(const pm_ctx* c, int checkpoint_every, size_t* bytes) {
+    if (!c || !bytes || checkpoint_every < 1) return fail(PM_ERR_INVALID_ARG, "bad arguments");
+    *bytes = adj_plan(c, std::min(checkpoint_every, c->cfg.n_steps)).total;
+    return PM_OK;
+}
+
+pm_status pm_loss_grad(pm_ctx* c, const void* white_noise, const void* target, int checkpoint_every, void* scratch,
+                       size_t scratch_bytes, double* loss_out, void* grad_out) {
+    if (!c || !white_noise || !target || !loss_out || !grad_out || checkpoint_every < 1)
+        return fail(PM_ERR_INVALID_ARG, "null argument or bad checkpoint interval");
+    if (c->cfg.precision != PM_FP32_FIXED || c->cfg.mode != PM_NEWTON)
+        return fail(PM_ERR_UNSUPPORTED, "the gradient is implemented for the FP32 Newtonian step");
+    const int S = c->cfg.n_steps, C = std::min(checkpoint_every, S);
+    const AdjLayout A = adj_plan(c, C);
+    if (!scratch || scratch_bytes < A.total || (uintptr_t)scratch % 256)
+        return fail(PM_ERR_WORKSPACE, "adjoint scratch too small or not 256-byte aligned");
+    unsigned char* sc = (unsigned char*)scratch;
+    const int n = c->n, np = c->np;
+    const size_t n3 = (size_t)n * n * n, P = 3 * (size_t)c->np3 * 4;
+    const double box = c->cfg.box, mass = std::pow((double)n / np, 3);
+    auto at = [&](size_t off) { return (void*)(sc + off); };
+    float* lam_u = (float*)at(A.lam_u);
+    float* lam_p = (float*)at(A.lam_p);
+    void* x = c->at(c->L.x);
+    void* p = c->at(c->L.p);
+    // ---- forward with checkpoints
+    PM_TRY(pm_ic_zeldovich(c, 0, white_noise, 0));
+    for (int k = 0; k < A.nseg; ++k) {
+        PM_CK(cudaMemcpyAsync(at(A.ckpt + (size_t)k * 2 * P), x, P, cudaMemcpyDeviceToDevice, c->st));
+        PM_CK(cudaMemcpyAsync(at(A.ckpt + (size_t)k * 2 * P + P), p, P, cudaMemcpyDeviceToDevice, c->st));
+        PM_TRY(pm_step(c, std::min(C, S - k * C)));
+    }
+    // ---- loss and its mesh adjoint
+    float* rho = (float*)c->at(c->L.rho);
+    PM_CK(fill(rho, (int64_t)n3, PM_FP32_FIXED, -1.0, c->st));
+    PM_CK(deposit_lattice(x, np, PM_FP32_FIXED, n, mass, rho, c->st));
+    c->rho_valid = false;
+    double* acc = (double*)at(A.acc);
+    PM_CK(cudaMemsetAsync(acc, 0, 8, c->st));
+    PM_CK(loss_mse(rho, (const float*)target, (int64_t)n3, acc, c->st));
+    double hsum = 0.0;
+    PM_CK(cudaMemcpyAsync(&hsum, acc, 8, cudaMemcpyDeviceToHost, c->st));
+    PM_CK(cudaStreamSynchronize(c->st));
+    *loss_out = hsum / (double)n3;
+    PM_CK(adj_gather((const uint32_t*)x, c->np3, n, rho, (float)mass, 0, lam_u, c->st));
+    PM_CK(cudaMemsetAsync(lam_p, 0, P, c->st));
+    // ---- reverse sweep, segment by segment
+    auto kick_of = [&](int s) {
+        const double a0 = c->a_grid(s), a1 = c->a_grid(s + 1);
+        const double a_from = (s == 0) ? a0 : 0.5 * (c->a_grid(s - 1) + a0);
+        return pmhost::kick_integral(c->cosmo, a_from, 0.5 * (a0 + a1));
+    };
+    const size_t Gb = 3 * n3 * 4;
+    for (int k = A.nseg - 1; k >= 0; --k) {
+        const int s0 = k * C, s1 = std::min(S, s0 + C);
+        PM_CK(cudaMemcpyAsync(x, at(A.ckpt + (size_t)k * 2 * P), P, cudaMemcpyDeviceToDevice, c->st));
+        PM_CK(cudaMemcpyAsync(p, at(A.ckpt + (size_t)k * 2 * P + P), P, cudaMemcpyDeviceToDevice, c->st));
+        c->step = s0;
+        c->synced = (s0 == 0);
+        c->rho_valid = false;
+        for (int s = s0; s < s1; ++s) {
+            PM_CK(cudaMemcpyAsync(at(A.seg_x + (size_t)(s - s0) * P), x, P, cudaMemcpyDeviceToDevice, c->st));
+            PM_TRY(compute_forces(c, c->a_grid(s)));
+            for (int j = 0; j < 3; ++j)
+                PM_CK(cudaMemcpyAsync((char*)at(A.seg_g + (size_t)(s - s0) * Gb) + j * n3 * 4, c->at(c->L.force[j]),
+                                      n3 * 4, cudaMemcpyDeviceToDevice, c->st));
+            PM_TRY(kick_drift(c, kick_of(s), pmhost::drift_integral(c->cosmo, c->a_grid(s), c->a_grid(s + 1))));
+            c->step = s + 1;
+            c->synced = false;
+        }
+        if (s1 == S) {  // positions and forces of the closing half kick
+            const int q = s1 - s0;
+            PM_CK(cudaMemcpyAsync(at(A.seg_x + (size_t)q * P), x, P, cudaMemcpyDeviceToDevice, c->st));
+            PM_TRY(compute_forces(c, c->a_grid(S)));
+            for (int j = 0; j < 3; ++j)
+                PM_CK(cudaMemcpyAsync((char*)at(A.seg_g + (size_t)q * Gb) + j * n3 * 4, c->at(c->L.force[j]), n3 * 4,
+                                      cudaMemcpyDeviceToDevice, c->st));
+            const double Kc = pmhost::kick_integral(c->cosmo, 0.5 * (c->a_grid(S - 1) + c->a_grid(S)), c->a_grid(S));
+            PM_TRY(adj_kick(c, (const uint32_t*)at(A.seg_x + (size_t)q * P), (const float*)at(A.seg_g + (size_t)q * Gb),
+                            Kc, lam_u, lam_p));
+        }
+        for (int s = s1 - 1; s >= s0; --s) {
+            const double Dd = pmhost::drift_integral(c->cosmo, c->a_grid(s), c->a_grid(s + 1));
+            PM_CK(axpby(lam_p, lam_u, lam_p, 3 * c->np3, (float)(Dd / box), 1.0f, c->st));
+            PM_TRY(adj_kick(c, (const uint32_t*)at(A.seg_x + (size_t)(s - s0) * P),
+                            (const float*)at(A.seg_g + (size_t)(s - s0) * Gb), kick_of(s), lam_u, lam_p));
+        }
+    }
+    // ---- transposed Zel'dovich map: grad = sum_j A_j^T (D/L lam_u_j + a^2 E f D lam_p_j)
+    const double a = c->cfg.a_init;
+    const double D = pmhost::growth_D(c->cosmo, a), f = pmhost::growth_f(c->cosmo, a), E = pmhost::E(c->cosmo, a);
+    const int64_t np3 = c->np3;
+    float* s_j[3] = {(float*)c->at(c->L.force[0]), (float*)c->at(c->L.force[1]), (float*)c->at(c->L.force[2])};
+    float2* sp[3] = {(float2*)c->at(c->L.spec[0]), (float2*)c->at(c->L.spec[1]), (float2*)c->at(c->L.spec[2])};
+    for (int j = 0; j < 3; ++j) {
+        PM_CK(axpby(s_j[j], lam_u + j * np3, lam_p + j * np3, np3, (float)(D / box), (float)(a * a * E * f * D),
+                    c->st));
+        PM_TRY(fft_forward_f32(c, s_j[j], sp[j], np));
+    }
+    const float2* in[3] = {sp[0], sp[1], sp[2]};
+    PM_CK(adj_combine(in, sp[0], np, c->kf, -std::pow((double)np, -1.5), (const double*)c->at(c->L.amp), 1, c->st));
+    PM_TRY(fft_inverse_f32(c, sp[0], (float*)grad_out, np));
+    c->rho_valid = false;
+    return PM_OK;
+}
+
+}  // extern "C"
+
+// ====================================================================== batch of realisations
+struct pm_batch {
+    pm_config cfg;
+    int B = 0;
+    unsigned char* ws = nullptr;
+    cudaStream_t st = nullptr;   // caller stream
+    cudaStream_t cap = nullptr;  // library stream on which runs are captured into a graph
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int exec_from = -1, exec_steps = 0;
+    std::vector<pm_ctx*> views;  // one context per realisation on slices of the workspace
+    size_t X = 0, P = 0, RHO = 0, SPEC[3] = {0, 0, 0}, FORCE[3] = {0, 0, 0}, AMP = 0, KF = 0, SCALE = 0;
+    size_t BIN = 0, WTAB = 0, ACC = 0, total = 0;
+    int64_t amp_len = 0;
+    int step = 0;
+    bool synced = true;
+    bool rho_valid = false;
+    pmhost::Cosmo cosmo;
+    void* at(size_t off) const { return ws + off; }
+    double a_grid(int i) const { return cfg.a_init + ((cfg.a_final - cfg.a_init) * i) / cfg.n_steps; }
+    ~pm_batch() {
+        for (auto* v : views) delete v;
+        if (exec) cudaGraphExecDestroy(exec);
+        if (ev_in) cudaEventDestroy(ev_in);
+        if (ev_out) cudaEventDestroy(ev_out);
+        if (cap) cudaStreamDestroy(cap);
+    }
+};
+
+namespace {
+
+void batch_plan(pm_batch& b) {
+    const pm_config& c = b.cfg;
+    const size_t np3 = (size_t)c.np * c.np * c.np, n = c.nmesh, n3 = n * n * n, nspec = (n / 2 + 1) * n * n;
+    const size_t B = b.B;
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        const size_t o = off;
+        off = align256(off + bytes);
+        return o;
+    };
+    b.X = take(B * 3 * np3 * 4);
+    b.P = take(B * 3 * np3 * 4);
+    b.RHO = take(B * n3 * 4);
+    for (int j = 0; j < 3; ++j) b.SPEC[j] = take(B * nspec * 8);
+    for (int j = 0; j < 3; ++j) b.FORCE[j] = take(B * n3 * 4);
+    b.amp_len = 3 * (int64_t)(c.np / 2) * (c.np / 2) + 1;
+    b.AMP = take(B * b.amp_len * 8);
+    b.KF = take(B * 8);
+    b.SCALE = take(B * 8);
+    b.BIN = take((3 * (n / 2) * (n / 2) + 1) * 2);
+    b.WTAB = take((n / 2 + 1) * 8);
+    b.ACC = take(3 * kMaxBins * 8);
+    b.total = off;
+}
+
+pm_status batch_validate(const pm_config* cfg, int B, const double* boxes) {
+    PM_TRY(validate(cfg));
+    if (B < 1 || B > 4096) return fail(PM_ERR_INVALID_ARG, "batch size must be in 1..4096");
+    if (cfg->precision != PM_FP32_FIXED || cfg->mode != PM_NEWTON)
+        return fail(PM_ERR_INVALID_ARG, "batches run the FP32 Newtonian step");
+    if (!ikd_deposit_supported(cfg->np, cfg->precision, cfg->nmesh))
+        return fail(PM_ERR_INVALID_ARG, "batches need nmesh >= 64 and nmesh / np in {1, 2, 4}");
+    if (boxes)
+        for (int r = 0; r < B; ++r)
+            if (!(boxes[r] > 0)) return fail(PM_ERR_INVALID_ARG, "box sizes must be positive");
+    return PM_OK;
+}
+
+// Force meshes of every realisation from rho (one launch per pass for the whole batch).
+pm_status batch_forces(pm_batch* b, cudaStream_t s) {
+    const int n = b->cfg.nmesh, B = b->B, M = n / 2;
+    float* rho = (float*)b->at(b->RHO);
+    float2* s0 = (float2*)b->at(b->SPEC[0]);
+    float2* s1 = (float2*)b->at(b->SPEC[1]);
+    float2* s2 = (float2*)b->at(b->SPEC[2]);
+    const double* kf = (const double*)b->at(b->KF);
+    PM_CK(z_r2c<float>(rho, s0, n, B, s));
+    PM_CK(cudaMemsetAsync(rho, 0, sizeof(float) * (size_t)B * n * n * n, s));
+    PM_CK((y_rows<float, false>(s0, (int64_t)B * (M + 1) * n, n, s)));
+    SpecOp op;
+    op.kind = OP_NEWTON;
+    op.fwd = 1;
+    op.coef = -1.5 * b->cfg.omega_m / ((double)n * n * n);
+    op.kf_arr = kf;
+    PM_CK(x_cols<float>(s0, s1, B * (M + 1), n, op, s));
+    PM_CK(y_rows_grad3<float>(s0, s1, s2, (int64_t)B * (M + 1) * n, n, 0.0, s, kf, (int64_t)(M + 1) * n));
+    const float2* in[3] = {s1, s2, s0};
+    float* out[3] = {(float*)b->at(b->FORCE[0]), (float*)b->at(b->FORCE[1]), (float*)b->at(b->FORCE[2])};
+    PM_CK(z_c2r<float>(in, out, 3, n, B, 4u, 0.0, s, kf));
+    return PM_OK;
+}
+
+pm_status batch_update(pm_batch* b, double kick, double drift, cudaStream_t s) {
+    void* g[3] = {b->at(b->FORCE[0]), b->at(b->FORCE[1]), b->at(b->FORCE[2])};
+    const double mass = std::pow((double)b->cfg.nmesh / b->cfg.np, 3);
+    PM_CK(interp_kick_drift_deposit(b->at(b->X), b->at(b->P), b->cfg.np, PM_FP32_FIXED, b->cfg.nmesh, g, kick, drift,
+                                    1.0, mass, b->at(b->RHO), s, b->B, (const double*)b->at(b->SCALE)));
+    return PM_OK;
+}
+
+// One KDK step of every realisation (the same a-grid for all), enqueued on s.
+pm_status batch_enqueue_step(pm_batch* b, cudaStream_t s) {
+    const double a0 = b->a_grid(b->step), a1 = b->a_grid(b->step + 1), ah = 0.5 * (a0 + a1);
+    PM_TRY(batch_forces(b, s));
+    const double a_from = b->synced ? a0 : 0.5 * (b->a_grid(b->step - 1) + a0);
+    PM_TRY(batch_update(b, pmhost::kick_integral(b->cosmo, a_from, ah), pmhost::drift_integral(b->cosmo, a0, a1), s));
+    b->step += 1;
+    b->synced = false;
+    if (b->step == b->cfg.n_steps) {
+        PM_TRY(batch_forces(b, s));
+        PM_TRY(batch_update(b, pmhost::kick_integral(b->cosmo, ah, a1), 0.0, s));
+        b->synced = true;
+    }
+    return PM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+pm_status pm_batch_workspace_size(const pm_config* cfg, int nreal, size_t* bytes) {
+    PM_TRY(batch_validate(cfg, nreal, nullptr));
+    if (!bytes) return fail(PM_ERR_INVALID_ARG, "null bytes");
+    pm_batch b;
+    b.cfg = *cfg;
+    b.B = nreal;
+    batch_plan(b);
+    *bytes = b.total;
+    return PM_OK;
+}
+
+pm_status pm_batch_init(const pm_config* cfg, int nreal, const double* boxes, void* workspace, size_t bytes,
+                        void* stream, pm_batch** out) {
+    if (!out) return fail(PM_ERR_INVALID_ARG, "null out");
+    *out = nullptr;
+    PM_TRY(batch_validate(cfg, nreal, boxes));
+    pm_batch* b = new pm_batch();
+    b->cfg = *cfg;
+    b->B = nreal;
+    batch_plan(*b);
+    if (!workspace || bytes < b->total || (uintptr_t)workspace % 256) {
+        delete b;
+        return fail(PM_ERR_WORKSPACE, "batch workspace too small or not 256-byte aligned");
+    }
+    pm_status ds = check_device();
+    if (ds != PM_OK) {
+        delete b;
+        return ds;
+    }
+    b->ws = (unsigned char*)workspace;
+    b->st = (cudaStream_t)stream;
+    b->cosmo.omega_m = cfg->omega_m;
+    b->cosmo.omega_b = cfg->omega_b;
+    b->cosmo.h = cfg->h;
+    b->cosmo.n_s = cfg->n_s;
+    b->cosmo.sigma8 = cfg->sigma8;
+    pmhost::normalise_sigma8(b->cosmo);
+    const int np = cfg->np, n = cfg->nmesh;
+    const size_t np3 = (size_t)np * np * np, n3 = (size_t)n * n * n, nspec = (size_t)(n / 2 + 1) * n * n;
+    std::vector<double> kf(nreal), scale(nreal), amp((size_t)nreal * b->amp_len, 0.0);
+    for (int r = 0; r < nreal; ++r) {
+        const double box = boxes ? boxes[r] : cfg->box;
+        kf[r] = 2.0 * M_PI / box;
+        scale[r] = 4294967296.0 / box;
+        const double V = box * box * box;
+        for (int64_t n2 = 1; n2 < b->amp_len; ++n2)
+            amp[(size_t)r * b->amp_len + n2] =
+                std::sqrt(pmhost::power_linear(b->cosmo, kf[r] * std::sqrt((double)n2)) / V);
+        pm_ctx* v = new pm_ctx();
+        v->cfg = *cfg;
+        v->cfg.box = box;
+        v->ws = b->ws;
+        v->st = b->st;
+        v->n = n;
+        v->np = np;
+        v->np3 = (int64_t)np3;
+        v->kf = kf[r];
+        v->cosmo = b->cosmo;
+        Layout& L = v->L;
+        L.x = b->X + (size_t)r * 3 * np3 * 4;
+        L.p = b->P + (size_t)r * 3 * np3 * 4;
+        L.rho = b->RHO + (size_t)r * n3 * 4;
+        for (int j = 0; j < 3; ++j) {
+            L.spec[j] = b->SPEC[j] + (size_t)r * nspec * 8;
+            L.force[j] = b->FORCE[j] + (size_t)r * n3 * 4;
+        }
+        L.amp = b->AMP + (size_t)r * b->amp_len * 8;
+        L.bin_of = b->BIN;
+        L.wtab = b->WTAB;
+        L.acc = b->ACC;
+        // the second and third spectrum arrays of the whole batch are the views' selection scratch
+        v->scratch_off = b->SPEC[1];
+        v->scratch_bytes = 2 * (size_t)nreal * nspec * 8;
+        b->views.push_back(v);
+    }
+    std::vector<double> wtab(n / 2 + 1);
+    for (int mq = 0; mq <= n / 2; ++mq) {
+        const double xq = M_PI * mq / n;
+        const double sq = (mq == 0) ? 1.0 : std::sin(xq) / xq;
+        wtab[mq] = sq * sq;
+    }
+    cudaError_t e = cudaMemcpyAsync(b->at(b->AMP), amp.data(), amp.size() * 8, cudaMemcpyHostToDevice, b->st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(b->at(b->KF), kf.data(), kf.size() * 8, cudaMemcpyHostToDevice, b->st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(b->at(b->SCALE), scale.data(), scale.size() * 8, cudaMemcpyHostToDevice, b->st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(b->at(b->WTAB), wtab.data(), wtab.size() * 8, cudaMemcpyHostToDevice, b->st);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_in, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_out, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->st);
+    if (e != cudaSuccess) {
+        delete b;
+        return fail(PM_ERR_CUDA, std::string("pm_batch_init: ") + cudaGetErrorString(e));
+    }
+    *out = b;
+    return PM_OK;
+}
+
+pm_status pm_batch_destroy(pm_batch* b) {
+    if (b && b->exec) cudaStreamSynchronize(b->cap);
+    delete b;
+    return PM_OK;
+}
+
+pm_status pm_batch_context(pm_batch* b, int r, pm_ctx** view) {
+    if (!b || !view || r < 0 || r >= b->B) return fail(PM_ERR_INVALID_ARG, "bad batch index");
+    b->views[r]->step = b->step;
+    b->views[r]->synced = b->synced;
+    b->views[r]->rho_valid = false;
+    // operations on a view may overwrite its slice of the batch density
+    b->rho_valid = false;
+    *view = b->views[r];
+    return PM_OK;
+}
+
+pm_status pm_batch_ic(pm_batch* b, const uint64_t* seeds, int paired) {
+    if (!b || !seeds) return fail(PM_ERR_INVALID_ARG, "null argument");
+    for (int r = 0; r < b->B; ++r) PM_TRY(pm_ic_zeldovich(b->views[r], seeds[r], nullptr, paired));
+    b->step = 0;
+    b->synced = true;
+    b->rho_valid = false;
+    return PM_OK;
+}
+
+pm_status pm_batch_step(pm_batch* b, int n_steps, int use_graph) {
+    if (!b) return fail(PM_ERR_INVALID_ARG, "null batch");
+    if (n_steps < 0) return fail(PM_ERR_INVALID_ARG, "negative step count");
+    if (b->step + n_steps > b->cfg.n_steps) return fail(PM_ERR_STATE, "stepping past a_final");
+    if (n_steps == 0) return PM_OK;
+    if (!b->rho_valid) {
+        for (int r = 0; r < b->B; ++r) PM_TRY(deposit_particles(b->views[r], b->at(b->views[r]->L.rho)));
+        b->rho_valid = true;
+    }
+    if (!use_graph) {
+        for (int k = 0; k < n_steps; ++k) PM_TRY(batch_enqueue_step(b, b->st));
+        return PM_OK;
+    }
+    // the whole run is recorded once on the capture stream and replayed as one graph launch
+    const int from = b->step;
+    if (!(b->exec && b->exec_from == from && b->exec_steps == n_steps)) {
+        if (b->exec) {
+            PM_CK(cudaStreamSynchronize(b->cap));
+            cudaGraphExecDestroy(b->exec);
+            b->exec = nullptr;
+        }
+        const bool synced0 = b->synced;
+        PM_CK(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeRelaxed));
+        pm_status s = PM_OK;
+        for (int k = 0; k < n_steps && s == PM_OK; ++k) s = batch_enqueue_step(b, b->cap);
+        cudaGraph_t g = nullptr;
+        const cudaError_t ce = cudaStreamEndCapture(b->cap, &g);
+        b->step = from;  // the recording only planned the steps; they run below
+        b->synced = synced0;
+        if (s != PM_OK) {
+            if (g) cudaGraphDestroy(g);
+            return s;
+        }
+        if (ce != cudaSuccess) return fail(PM_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(ce));
+        const cudaError_t ie = cudaGraphInstantiate(&b->exec, g, 0);
+        cudaGraphDestroy(g);
+        if (ie != cudaSuccess) return fail(PM_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(ie));
+        b->exec_from = from;
+        b->exec_steps = n_steps;
+    }
+    PM_CK(cudaEventRecord(b->ev_in, b->st));
+    PM_CK(cudaStreamWaitEvent(b->cap, b->ev_in, 0));
+    PM_CK(cudaGraphLaunch(b->exec, b->cap));
+    PM_CK(cudaEventRecord(b->ev_out, b->cap));
+    PM_CK(cudaStreamWaitEvent(b->st, b->ev_out, 0));
+    // advance the host-side integrator state exactly as the recorded steps did
+    for (int k = 0; k < n_steps; ++k) {
+        b->step += 1;
+        b->synced = (b->step == b->cfg.n_steps);
+    }
+    return PM_OK;
+}
+
+pm_status pm_batch_state(pm_batch* b, int* step, double* a, int* synchronised) {
+    if (!b) return fail(PM_ERR_INVALID_ARG, "null batch");
+    if (step) *step = b->step;
+    if (a) *a = b->a_grid(b->step);
+    if (synchronised) *synchronised = b->synced ? 1 : 0;
+    return PM_OK;
+}
+
+pm_status pm_batch_power(pm_batch* b, int nbins, const double* edges, int deconvolve, double* k_out, double* p_out,
+                         double* nmodes_out) {
+    if (!b) return fail(PM_ERR_INVALID_ARG, "null batch");
+    for (int r = 0; r < b->B; ++r) {
+        pm_ctx* v = nullptr;
+        PM_TRY(pm_batch_context(b, r, &v));
+        PM_TRY(pm_power(v, nullptr, nullptr, nbins, edges, deconvolve, k_out ? k_out + (size_t)r * nbins : nullptr,
+                        p_out ? p_out + (size_t)r * nbins : nullptr,
+                        nmodes_out ? nmodes_out + (size_t)r * nbins : nullptr));
+    }
+    return PM_OK;
+}
+
+pm_status pm_batch_bias(pm_batch* b, double fraction, int nbins, const double* edges, double k_max, int terms,
+                        double* coef_out) {
+    if (!b || !coef_out) return fail(PM_ERR_INVALID_ARG, "null argument");
+    for (int r = 0; r < b->B; ++r) {
+        pm_ctx* v = nullptr;
+        PM_TRY(pm_batch_context(b, r, &v));
+        void* dm = b->at(v->L.force[0]);
+        void* dh = b->at(v->L.force[1]);
+        PM_TRY(pm_density(v, dm));
+        PM_TRY(pm_halo_proxy(v, dm, fraction, dh, nullptr));
+        PM_TRY(pm_linear_bias(v, dh, dm, nbins, edges, k_max, terms, coef_out + (size_t)r * terms, nullptr, nullptr,
+                              nullptr));
+    }
+    return PM_OK;
+}
+
+}  // extern "C"
+
+extern "C" {
 
 // ------------------------------------------------------------------ stateless operators
 pm_status pm_cic_deposit(const void* x, int64_t count, int precision, int n, double mass, void* rho, void* stream) {

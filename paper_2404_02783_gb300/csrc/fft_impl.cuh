@@ -22,6 +22,7 @@
 namespace pm {
 
 template <typename T> __device__ __forceinline__ cplx<T> tw_global(int k);
+cudaError_t set_smem_once(const void* fn, size_t bytes);
 
 template <typename T>
 __device__ __forceinline__ void load_twiddles(cplx<T>* tw, int L) {
@@ -40,9 +41,11 @@ __device__ __forceinline__ void load_twiddles_head(cplx<T>* tw, int L, int count
 // across rows hit different banks.
 __host__ __device__ constexpr int row_stride(int len) { return (len + (len >> 3) + 1) | 1; }
 
+// Opts a kernel into more than 48 KB of dynamic shared memory once per device, so that
+// launches (including those recorded into a CUDA graph) make no further attribute calls.
 static inline cudaError_t set_smem(const void* fn, size_t bytes) {
     if (bytes <= 48 * 1024) return cudaSuccess;
-    return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    return set_smem_once(fn, bytes);
 }
 
 // Launch shapes (compile time): sequences per CTA for each pass.
@@ -111,7 +114,7 @@ template <typename T> struct Ptr3 {
 };
 
 template <typename T, int LOGN>
-__global__ void __launch_bounds__(512) k_z_c2r(Ptr3<T> P, unsigned gradz_mask, T kf) {
+__global__ void __launch_bounds__(512) k_z_c2r(Ptr3<T> P, unsigned gradz_mask, T kf0, const double* __restrict__ kf_arr) {
     typedef cplx<T> C;
     typedef Shape<T, LOGN> S;
     constexpr int N = S::N, M = S::M, Q = S::QM, YB = S::YB;
@@ -129,6 +132,7 @@ __global__ void __launch_bounds__(512) k_z_c2r(Ptr3<T> P, unsigned gradz_mask, T
     const size_t f = blockIdx.y / N;
     load_twiddles<T>(twM, M);
     load_twiddles_head<T>(twN, N, M + 1);
+    const T kf = kf_arr ? T(kf_arr[f]) : kf0;
     const C* pin = comp == 0 ? P.in[0] : (comp == 1 ? P.in[1] : P.in[2]);
     T* pout = comp == 0 ? P.out[0] : (comp == 1 ? P.out[1] : P.out[2]);
     const C* inp = pin + f * (size_t)(M + 1) * N * N;
@@ -212,7 +216,8 @@ __global__ void __launch_bounds__(512) k_y_rows(cplx<T>* __restrict__ data, int6
 // A <- IFFT_y(A), B <- IFFT_y(B), C <- IFFT_y(-i ky A)
 template <typename T, int LOGN>
 __global__ void __launch_bounds__(512) k_y_grad3(cplx<T>* __restrict__ A, cplx<T>* __restrict__ B,
-                                                 cplx<T>* __restrict__ Cout, int64_t nrows, T kf) {
+                                                 cplx<T>* __restrict__ Cout, int64_t nrows, T kf0,
+                                                 const double* __restrict__ kf_arr, int64_t rows_per_field) {
     typedef cplx<T> C;
     typedef Shape<T, LOGN> S;
     constexpr int N = S::N, Q = S::QN, RB = S::RB3;
@@ -224,6 +229,7 @@ __global__ void __launch_bounds__(512) k_y_grad3(cplx<T>* __restrict__ A, cplx<T
     const int b = tid / Q, t = tid % Q;
     const int64_t r = (int64_t)blockIdx.x * RB + b;
     const bool ok = r < nrows;
+    const T kf = (kf_arr && ok) ? T(kf_arr[r / rows_per_field]) : kf0;
     load_twiddles<T>(tw, N);
     C v[3][8];
     if (ok) {
@@ -267,6 +273,8 @@ __global__ void __launch_bounds__(512) k_x_cols(cplx<T>* __restrict__ data, cplx
     const int b = tid % CB, t = tid / CB;
     const int plane = blockIdx.y;
     const int kz = plane % (M + 1);
+    const int field = plane / (M + 1);
+    const double kf = op.kf_arr ? op.kf_arr[field] : op.kf;
     const int c = blockIdx.x * CB + b;
     const size_t pbase = (size_t)plane * N * N;
     C* base = data + pbase;
@@ -326,14 +334,17 @@ __global__ void __launch_bounds__(512) k_x_cols(cplx<T>* __restrict__ data, cplx
             }
             atomicAdd(&acc[bin], w);
             atomicAdd(&acc[op.nbins + bin], w * val);
-            atomicAdd(&acc[2 * op.nbins + bin], w * op.kf * sqrt((double)n2));
+            atomicAdd(&acc[2 * op.nbins + bin], w * kf * sqrt((double)n2));
         } else {
             C phi;
             if constexpr (KIND == OP_NEWTON || KIND == OP_POTENTIAL) {
-                phi = (n2 == 0) ? cmake<C>(T(0), T(0)) : cscale(vv, T(op.coef) / T(n2));
+                const T coef = T(op.coef / (kf * kf));
+                phi = (n2 == 0) ? cmake<C>(T(0), T(0)) : cscale(vv, coef / T(n2));
             } else if constexpr (KIND == OP_ZA) {
                 const bool nyq = (2 * nx == -N) || (2 * ny == -N) || (nz == M);
-                phi = (n2 == 0 || nyq) ? cmake<C>(T(0), T(0)) : cscale(vv, T(op.coef * op.amp[n2] / (double)n2));
+                const double* amp = op.amp + (int64_t)field * op.amp_stride;
+                phi = (n2 == 0 || nyq) ? cmake<C>(T(0), T(0))
+                                       : cscale(vv, T(op.coef / (kf * kf) * amp[n2] / (double)n2));
             } else {  // OP_GR
                 if (n2 == 0) {
                     phi = cmake<C>(T(0), T(0));
@@ -344,7 +355,7 @@ __global__ void __launch_bounds__(512) k_x_cols(cplx<T>* __restrict__ data, cplx
                 } else if (n2 <= op.n_lo * op.n_lo) {
                     const int L = op.n_lo, W2 = 2 * L + 1;
                     const size_t id = ((size_t)nz * W2 + (nx + L)) * W2 + (ny + L);
-                    const double k2 = op.kf * op.kf * (double)n2;
+                    const double k2 = kf * kf * (double)n2;
                     const double H = op.calH;
                     const double num_s = -1.5 * H * H * op.omm_a;
                     double den = k2 + 3.0 * H * H + 4.5 * H * H * op.omm_a;
@@ -362,7 +373,7 @@ __global__ void __launch_bounds__(512) k_x_cols(cplx<T>* __restrict__ data, cplx
                     phi = cmake<C>(T(P.x * op.ac2_over_n3), T(P.y * op.ac2_over_n3));
                 } else {
                     C* old = reinterpret_cast<C*>(op.phi_old) + pbase + (size_t)i * N + c;
-                    const T k2 = T(op.kf * op.kf) * T(n2);
+                    const T k2 = T(kf * kf) * T(n2);
                     const T H = T(op.calH), om = T(op.omm_a);
                     const T num_s = T(-1.5) * H * H * om;
                     T den = k2 + T(3) * H * H + T(4.5) * H * H * om;
@@ -381,7 +392,7 @@ __global__ void __launch_bounds__(512) k_x_cols(cplx<T>* __restrict__ data, cplx
             }
             v[0][m] = phi;
             if constexpr (KIND != OP_POTENTIAL) {
-                const T kx = (2 * nx == -N) ? T(0) : T(op.kf) * T(nx);
+                const T kx = (2 * nx == -N) ? T(0) : T(kf) * T(nx);
                 v[1][m] = cmake<C>(phi.y * kx, -phi.x * kx);  // -i kx phi
             }
         }
@@ -418,12 +429,13 @@ cudaError_t z_r2c_n(const T* in, cplx<T>* out, int batch, cudaStream_t st) {
 }
 
 template <typename T, int LOGN>
-cudaError_t z_c2r_n(const Ptr3<T>& P, int ncomp, int batch, unsigned mask, double kf, cudaStream_t st) {
+cudaError_t z_c2r_n(const Ptr3<T>& P, int ncomp, int batch, unsigned mask, double kf, cudaStream_t st,
+                    const double* kf_arr) {
     typedef Shape<T, LOGN> S;
     const size_t smem = sizeof(cplx<T>) * (S::M + ((S::M + 2) & ~1) + (size_t)S::YB * row_stride(S::M + 1));
     cudaError_t e = set_smem((const void*)k_z_c2r<T, LOGN>, smem);
     if (e != cudaSuccess) return e;
-    k_z_c2r<T, LOGN><<<dim3(S::N / S::YB, S::N * batch, ncomp), S::YB * S::QM, smem, st>>>(P, mask, (T)kf);
+    k_z_c2r<T, LOGN><<<dim3(S::N / S::YB, S::N * batch, ncomp), S::YB * S::QM, smem, st>>>(P, mask, (T)kf, kf_arr);
     return cudaGetLastError();
 }
 
@@ -439,13 +451,15 @@ cudaError_t y_rows_n(cplx<T>* data, int64_t nrows, cudaStream_t st) {
 }
 
 template <typename T, int LOGN>
-cudaError_t y_grad3_n(cplx<T>* A, cplx<T>* B, cplx<T>* Cc, int64_t nrows, double kf, cudaStream_t st) {
+cudaError_t y_grad3_n(cplx<T>* A, cplx<T>* B, cplx<T>* Cc, int64_t nrows, double kf, cudaStream_t st,
+                      const double* kf_arr, int64_t rows_per_field) {
     typedef Shape<T, LOGN> S;
     const size_t smem = sizeof(cplx<T>) * (S::N + 3 * (size_t)S::RB3 * row_stride(S::N));
     cudaError_t e = set_smem((const void*)k_y_grad3<T, LOGN>, smem);
     if (e != cudaSuccess) return e;
     const int64_t nblk = (nrows + S::RB3 - 1) / S::RB3;
-    k_y_grad3<T, LOGN><<<(unsigned)nblk, S::RB3 * S::QN, smem, st>>>(A, B, Cc, nrows, (T)kf);
+    k_y_grad3<T, LOGN><<<(unsigned)nblk, S::RB3 * S::QN, smem, st>>>(A, B, Cc, nrows, (T)kf, kf_arr,
+                                                                       rows_per_field);
     return cudaGetLastError();
 }
 
@@ -492,13 +506,13 @@ cudaError_t z_r2c(const T* in, cplx<T>* out, int n, int batch, cudaStream_t st) 
 
 template <typename T>
 cudaError_t z_c2r(const cplx<T>* const* in, T* const* out, int ncomp, int n, int batch, unsigned gradz_mask,
-                  double kf, cudaStream_t st) {
+                  double kf, cudaStream_t st, const double* kf_arr) {
     Ptr3<T> P;
     for (int j = 0; j < 3; ++j) {
         P.in[j] = in[j < ncomp ? j : 0];
         P.out[j] = out[j < ncomp ? j : 0];
     }
-    PM_DISPATCH_LOGN(n, (z_c2r_n<T, LG>(P, ncomp, batch, gradz_mask, kf, st)))
+    PM_DISPATCH_LOGN(n, (z_c2r_n<T, LG>(P, ncomp, batch, gradz_mask, kf, st, kf_arr)))
 }
 
 template <typename T, bool INV>
@@ -507,8 +521,9 @@ cudaError_t y_rows(cplx<T>* data, int64_t nrows, int n, cudaStream_t st) {
 }
 
 template <typename T>
-cudaError_t y_rows_grad3(cplx<T>* A, cplx<T>* B, cplx<T>* Cc, int64_t nrows, int n, double kf, cudaStream_t st) {
-    PM_DISPATCH_LOGN(n, (y_grad3_n<T, LG>(A, B, Cc, nrows, kf, st)))
+cudaError_t y_rows_grad3(cplx<T>* A, cplx<T>* B, cplx<T>* Cc, int64_t nrows, int n, double kf, cudaStream_t st,
+                         const double* kf_arr, int64_t rows_per_field) {
+    PM_DISPATCH_LOGN(n, (y_grad3_n<T, LG>(A, B, Cc, nrows, kf, st, kf_arr, rows_per_field)))
 }
 
 template <typename T>
@@ -519,11 +534,11 @@ cudaError_t x_cols(cplx<T>* data, cplx<T>* out2, int nplanes, int n, const SpecO
 #define PM_INST(T)                                                                                     \
     template cudaError_t z_r2c<T>(const T*, cplx<T>*, int, int, cudaStream_t);                         \
     template cudaError_t z_c2r<T>(const cplx<T>* const*, T* const*, int, int, int, unsigned, double,  \
-                                  cudaStream_t);                                                       \
+                                  cudaStream_t, const double*);                                        \
     template cudaError_t y_rows<T, false>(cplx<T>*, int64_t, int, cudaStream_t);                      \
     template cudaError_t y_rows<T, true>(cplx<T>*, int64_t, int, cudaStream_t);                       \
     template cudaError_t y_rows_grad3<T>(cplx<T>*, cplx<T>*, cplx<T>*, int64_t, int, double,           \
-                                         cudaStream_t);                                                \
+                                         cudaStream_t, const double*, int64_t);                        \
     template cudaError_t x_cols<T>(cplx<T>*, cplx<T>*, int, int, const SpecOp&, cudaStream_t);
 
 }  // namespace pm

@@ -23,8 +23,10 @@ enum OpKind {
 struct SpecOp {
     int kind = OP_FWD_STORE;
     int fwd = 1;              // forward x-FFT of the input first
-    double coef = 0.0;        // NEWTON/POTENTIAL: -3/2 Om / (kf^2 n^3); ZA: -sign * scale / kf^2
+    double coef = 0.0;        // NEWTON/POTENTIAL: -3/2 Om / n^3; ZA: -sign * scale (both divided by kf^2 per field)
     double kf = 0.0;          // fundamental mode, h/Mpc
+    const double* kf_arr = nullptr;  // per-field kf when several fields (boxes) share a launch
+    int64_t amp_stride = 0;          // elements between the amplitude tables of consecutive fields
     // linearised Poisson gauge
     double calH = 0.0, omm_a = 0.0, inv_dtau = 0.0, ac2_over_n3 = 0.0;
     int first = 1;            // Phi' = 0 at the first force evaluation
@@ -45,6 +47,8 @@ struct SpecOp {
 // Uploads the twiddle tables exp(-2 pi i k / 1024) of both precisions to the current
 // device (once per device).
 cudaError_t ensure_device_tables();
+// cudaFuncSetAttribute(MaxDynamicSharedMemorySize) once per (kernel, device, size).
+cudaError_t set_smem_once(const void* fn, size_t bytes);
 
 // FFT passes.  n is the transform length (power of two, 16..1024); batch counts
 // independent 3D fields stored back to back.
@@ -53,13 +57,14 @@ cudaError_t z_r2c(const T* in, cplx<T>* out, int n, int batch, cudaStream_t st);
 // out_j = c2r(in_j [* -i kf kz when gradz_mask bit j is set]) for the ncomp fields
 template <typename T>
 cudaError_t z_c2r(const cplx<T>* const* in, T* const* out, int ncomp, int n, int batch,
-                  unsigned gradz_mask, double kf, cudaStream_t st);
+                  unsigned gradz_mask, double kf, cudaStream_t st, const double* kf_arr = nullptr);
 template <typename T, bool INV>
 cudaError_t y_rows(cplx<T>* data, int64_t nrows, int n, cudaStream_t st);
-// A <- IFFT_y(A), B <- IFFT_y(B), C <- IFFT_y(-i ky A)
+// A <- IFFT_y(A), B <- IFFT_y(B), C <- IFFT_y(-i ky A); kf_arr (optional) gives the kf of
+// each consecutive group of rows_per_field rows.
 template <typename T>
 cudaError_t y_rows_grad3(cplx<T>* A, cplx<T>* B, cplx<T>* C, int64_t nrows, int n, double kf,
-                         cudaStream_t st);
+                         cudaStream_t st, const double* kf_arr = nullptr, int64_t rows_per_field = 0);
 template <typename T>
 cudaError_t x_cols(cplx<T>* data, cplx<T>* out2, int nplanes, int n, const SpecOp& op, cudaStream_t st);
 

@@ -172,8 +172,7 @@ static cudaError_t deposit_tiled_r(const void* x, int np, int n, double mass, vo
     const unsigned blocks = (unsigned)((np / D::TX) * (np / D::TY) * (np / D::TZ));
     const float inv = (float)ldexp(1.0, -(32 - logn));
     const size_t smem = sizeof(float) * D::CELLS;
-    cudaError_t e = cudaFuncSetAttribute((const void*)k_deposit_tiled<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
+    cudaError_t e = set_smem_once((const void*)k_deposit_tiled<R>, smem);
     if (e != cudaSuccess) return e;
     k_deposit_tiled<R><<<blocks, 512, smem, st>>>((const uint32_t*)x, lognp, logn, inv, (float)mass, (float*)rho);
     return cudaGetLastError();
@@ -354,7 +353,7 @@ cudaError_t interp_kick_drift(void* x, void* p, int64_t count, int precision, in
     const int logn = ilog2(n);
     if (precision == PM_FP32_FIXED) {
         const float inv = (float)ldexp(1.0, -(32 - logn));
-        const float dt = (float)(drift * 4294967296.0 / box);
+        const float dt = (float)(drift * (4294967296.0 / box));
         const bool pairs = (count % 2 == 0) && ((uintptr_t)x % 8 == 0) && ((uintptr_t)p % 8 == 0);
         if (pairs)
             k_ikd_ticks2<<<grid_for(count / 2, 256), 256, 0, st>>>((uint32_t*)x, (float*)p, count, logn, inv,
@@ -369,6 +368,125 @@ cudaError_t interp_kick_drift(void* x, void* p, int64_t count, int precision, in
                                                          (const double*)g[1], (const double*)g[2], kick, drift / box);
     }
     return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- kick + drift + next deposit
+// One pass per step over the lattice-ordered particles by Lagrangian tiles: gather the
+// force at x, kick, drift, and deposit the new position into the (zeroed) next
+// density mesh through the tile's shared-memory accumulator, exactly as
+// k_deposit_tiled would have done from the drifted positions.
+// blockIdx.y selects the field of a batch of independent runs stored back to back
+// (particles [field][3][np^3], meshes [field][n^3]); scale = 2^32 / L of that field.
+template <int R>
+__global__ void __launch_bounds__(512) k_ikd_deposit(uint32_t* __restrict__ x, float* __restrict__ p, int lognp,
+                                                     int logn, float inv_cell_ticks, const float* __restrict__ gx,
+                                                     const float* __restrict__ gy, const float* __restrict__ gz,
+                                                     float kick, double drift, double scale0,
+                                                     const double* __restrict__ scale_arr, float mass,
+                                                     float* __restrict__ rho) {
+    typedef DepTile<R> D;
+    extern __shared__ __align__(16) float tile[];  // D::CELLS floats
+    const int np = 1 << lognp, n = 1 << logn, nm = n - 1;
+    {
+        const int fb = blockIdx.y;
+        const int64_t cnt = (int64_t)1 << (3 * lognp);
+        const int64_t n3 = (int64_t)1 << (3 * logn);
+        x += fb * 3 * cnt;
+        p += fb * 3 * cnt;
+        gx += fb * n3;
+        gy += fb * n3;
+        gz += fb * n3;
+        rho += fb * n3;
+    }
+    const float drift_ticks = (float)(drift * (scale_arr ? scale_arr[blockIdx.y] : scale0));
+    const int ntz = np / D::TZ, nty = np / D::TY;
+    const int bz = blockIdx.x % ntz, by = (blockIdx.x / ntz) % nty, bx = blockIdx.x / (ntz * nty);
+    const int ox = bx * D::TX * R - D::H, oy = by * D::TY * R - D::H, oz = bz * D::TZ * R - D::H;
+    const int64_t count = (int64_t)1 << (3 * lognp);
+    for (int c = threadIdx.x; c < D::CELLS / 4; c += 512) reinterpret_cast<float4*>(tile)[c] = make_float4(0, 0, 0, 0);
+    __syncthreads();
+    for (int e = threadIdx.x; e < D::PER; e += 512) {
+        const int lz = e % D::TZ, ly = (e / D::TZ) % D::TY, lx = e / (D::TZ * D::TY);
+        const int64_t id = (((int64_t)(bx * D::TX + lx) << lognp) + by * D::TY + ly) * np + bz * D::TZ + lz;
+        uint32_t u0 = x[id], u1 = x[count + id], u2 = x[2 * count + id];
+        float p0 = p[id], p1 = p[count + id], p2 = p[2 * count + id];
+        ikd_particle(u0, u1, u2, p0, p1, p2, logn, inv_cell_ticks, gx, gy, gz, kick, drift_ticks);
+        p[id] = p0;
+        p[count + id] = p1;
+        p[2 * count + id] = p2;
+        x[id] = u0;
+        x[count + id] = u1;
+        x[2 * count + id] = u2;
+        const CicF cx = cic_ticks(u0, logn, inv_cell_ticks);
+        const CicF cy = cic_ticks(u1, logn, inv_cell_ticks);
+        const CicF cz = cic_ticks(u2, logn, inv_cell_ticks);
+        const float wx[2] = {1.0f - cx.w1, cx.w1}, wy[2] = {1.0f - cy.w1, cy.w1}, wz[2] = {1.0f - cz.w1, cz.w1};
+        const int dx = (cx.i0 - ox) & nm, dy = (cy.i0 - oy) & nm, dz = (cz.i0 - oz) & nm;
+        if (dx < D::DX - 1 && dy < D::DY - 1 && dz < D::DZ - 1) {
+#pragma unroll
+            for (int a = 0; a < 2; ++a)
+#pragma unroll
+                for (int b = 0; b < 2; ++b) {
+                    const float wab = mass * wx[a] * wy[b];
+                    float* row = tile + ((dx + a) * D::DY + dy + b) * D::DZ + dz;
+                    atomicAdd(row, wab * wz[0]);
+                    atomicAdd(row + 1, wab * wz[1]);
+                }
+        } else {
+            const int ix[2] = {cx.i0, cx.i1}, iy[2] = {cy.i0, cy.i1}, iz[2] = {cz.i0, cz.i1};
+#pragma unroll
+            for (int a = 0; a < 2; ++a)
+#pragma unroll
+                for (int b = 0; b < 2; ++b) {
+                    const float wab = mass * wx[a] * wy[b];
+                    float* row = rho + ((size_t)ix[a] * n + iy[b]) * n;
+                    atomicAdd(row + iz[0], wab * wz[0]);
+                    atomicAdd(row + iz[1], wab * wz[1]);
+                }
+        }
+    }
+    __syncthreads();
+    for (int c = threadIdx.x; c < D::CELLS; c += 512) {
+        const float v = tile[c];
+        if (v != 0.0f) {
+            const int lz = c % D::DZ, ly = (c / D::DZ) % D::DY, lx = c / (D::DZ * D::DY);
+            atomicAdd(rho + (((size_t)((ox + lx) & nm) * n + ((oy + ly) & nm)) * n + ((oz + lz) & nm)), v);
+        }
+    }
+}
+
+template <int R>
+static cudaError_t ikd_deposit_r(void* x, void* p, int np, int n, void* const* g, double kick, double drift,
+                                 double box, double mass, void* rho, cudaStream_t st, int nfields,
+                                 const double* scale_arr) {
+    typedef DepTile<R> D;
+    const int lognp = ilog2(np), logn = ilog2(n);
+    const unsigned blocks = (unsigned)((np / D::TX) * (np / D::TY) * (np / D::TZ));
+    const float inv = (float)ldexp(1.0, -(32 - logn));
+    const size_t smem = sizeof(float) * D::CELLS;
+    cudaError_t e = set_smem_once((const void*)k_ikd_deposit<R>, smem);
+    if (e != cudaSuccess) return e;
+    k_ikd_deposit<R><<<dim3(blocks, nfields), 512, smem, st>>>((uint32_t*)x, (float*)p, lognp, logn, inv,
+                                                              (const float*)g[0], (const float*)g[1],
+                                                              (const float*)g[2], (float)kick, drift,
+                                                              4294967296.0 / box, scale_arr, (float)mass,
+                                                              (float*)rho);
+    return cudaGetLastError();
+}
+
+bool ikd_deposit_supported(int np, int precision, int n) {
+    const int R = n / np;
+    return precision == PM_FP32_FIXED && n >= 64 && (R == 1 || R == 2 || R == 4) && np >= 32 / R;
+}
+
+cudaError_t interp_kick_drift_deposit(void* x, void* p, int np, int precision, int n, void* const* g, double kick,
+                                      double drift, double box, double mass, void* rho, cudaStream_t st, int nfields,
+                                      const double* scale_arr) {
+    if (!ikd_deposit_supported(np, precision, n) || nfields < 1) return cudaErrorInvalidValue;
+    const int R = n / np;
+    if (R == 1) return ikd_deposit_r<1>(x, p, np, n, g, kick, drift, box, mass, rho, st, nfields, scale_arr);
+    if (R == 2) return ikd_deposit_r<2>(x, p, np, n, g, kick, drift, box, mass, rho, st, nfields, scale_arr);
+    return ikd_deposit_r<4>(x, p, np, n, g, kick, drift, box, mass, rho, st, nfields, scale_arr);
 }
 
 // ---------------------------------------------------------------- Zel'dovich placement
@@ -699,6 +817,12 @@ static cudaError_t scan_u32(const uint32_t* in, uint32_t* out, int64_t count, ui
     k_scan_add<<<(unsigned)((count + 255) / 256), 256, 0, st>>>(out, count, sums);
     return cudaGetLastError();
 }
+
+cudaError_t scan_exclusive_u32(const uint32_t* in, uint32_t* out, int64_t count, void* scratch, cudaStream_t st) {
+    return scan_u32(in, out, count, (uint32_t*)scratch, st);
+}
+
+size_t scan_scratch_bytes(int64_t count) { return sizeof(uint32_t) * (size_t)(scan_scratch_words(count) + 64); }
 
 __global__ void k_scatter_unstable(const uint32_t* __restrict__ keys, int64_t count, uint32_t* __restrict__ cursor,
                                    uint32_t* __restrict__ order) {

@@ -17,6 +17,14 @@ cudaError_t interp(const void* field, int n, const void* x, int64_t count, int p
 // g: three force meshes; kick = K(a, b); drift = D(a, b) in Mpc/h per unit p
 cudaError_t interp_kick_drift(void* x, void* p, int64_t count, int precision, int n, void* const* g, double kick,
                               double drift, double box, cudaStream_t st);
+// Kick + drift of the np^3 lattice-ordered particles fused with the deposit of the
+// drifted positions into rho (which must be zero on entry); FP32 ticks, n / np in {1,2,4}.
+bool ikd_deposit_supported(int np, int precision, int n);
+// nfields > 1: a batch of runs stored back to back, box given per field as
+// scale_arr[f] = 2^32 / L_f (box is then ignored).
+cudaError_t interp_kick_drift_deposit(void* x, void* p, int np, int precision, int n, void* const* g, double kick,
+                                      double drift, double box, double mass, void* rho, cudaStream_t st,
+                                      int nfields = 1, const double* scale_arr = nullptr);
 cudaError_t ic_place(void* x, void* p, void* const* psi, int np, int precision, double D, double pfac, double box,
                      cudaStream_t st);
 template <typename T>
@@ -30,6 +38,26 @@ cudaError_t cell_sort(const void* x, int64_t count, int precision, int n, uint32
 int64_t cell_sort_static_max_cells();
 cudaError_t cell_sort_static(const void* x, int64_t count, int precision, int n, uint32_t* keys, uint32_t* order,
                              cudaStream_t st);
+
+// Exclusive prefix sum of count uint32 values (scratch: scan_scratch_bytes).
+cudaError_t scan_exclusive_u32(const uint32_t* in, uint32_t* out, int64_t count, void* scratch, cudaStream_t st);
+size_t scan_scratch_bytes(int64_t count);
+
+// Halo proxy: delta_h of the K densest cells (ties by lower index); scratch: halo_proxy_scratch_bytes.
+template <typename T>
+cudaError_t halo_proxy(const T* field, int64_t count, int64_t K, T* out, void* scratch, cudaStream_t st);
+size_t halo_proxy_scratch_bytes(int64_t count);
+
+// Reverse sweep of the FP32 step (adjoint.cu).
+cudaError_t adj_gather(const uint32_t* x, int64_t count, int n, const float* F, float scale, int accumulate,
+                       float* lam_u, cudaStream_t st);
+cudaError_t adj_direct(const uint32_t* x, int64_t count, int n, const float* v, const float* const* G, float K,
+                       float* lam_u, cudaStream_t st);
+cudaError_t deposit_vec(const uint32_t* x, int64_t count, int n, const float* v, float* const* V, cudaStream_t st);
+cudaError_t adj_combine(const float2* const* in, float2* out, int n, double kf, double coef, const double* amp,
+                        int mode, cudaStream_t st);
+cudaError_t loss_mse(float* delta, const float* target, int64_t n3, double* acc, cudaStream_t st);
+cudaError_t axpby(float* y, const float* a, const float* b, int64_t m, float alpha, float beta, cudaStream_t st);
 
 // Bispectrum: fill the m-grid masked spectra (bins x {delta 1_b, 1_b}) from the
 // n-grid spectrum, and accumulate the triangle sums of the inverse transforms.

@@ -114,8 +114,7 @@ cudaError_t bk_triangles(const T* fields, int m, int nbins, const int4* tri, int
     const int gy = (ntri + kTriPerThread * nthr - 1) / (kTriPerThread * nthr);
     const size_t smem = sizeof(T) * kTriPoints * 2 * nbins;
     if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute((const void*)k_bk_triangles<T>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaError_t e = set_smem_once((const void*)k_bk_triangles<T>, smem);
         if (e != cudaSuccess) return e;
     }
     dim3 grid((unsigned)gx, (unsigned)gy);

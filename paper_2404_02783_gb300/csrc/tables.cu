@@ -3,6 +3,8 @@
 #include <math.h>
 
 #include <mutex>
+#include <set>
+#include <utility>
 
 #include "internal.h"
 
@@ -42,6 +44,21 @@ cudaError_t ensure_device_tables() {
     if (e != cudaSuccess) return e;
     if (dev >= 0 && dev < 128) g_tab_ready[dev] = true;
     return cudaSuccess;
+}
+
+static std::mutex g_attr_mutex;
+static std::set<std::pair<std::pair<const void*, int>, size_t>> g_attr_done;
+
+cudaError_t set_smem_once(const void* fn, size_t bytes) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lock(g_attr_mutex);
+    const auto key = std::make_pair(std::make_pair(fn, dev), bytes);
+    if (g_attr_done.count(key)) return cudaSuccess;
+    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e == cudaSuccess) g_attr_done.insert(key);
+    return e;
 }
 
 }  // namespace pm
