@@ -192,8 +192,11 @@ def time_steps(pm, torch, run, k, world):
 
 
 def bench_precision(pm, torch, args, prec, rank, world, clocks=None):
+    """K timed steps after W warm-up steps of a run whose a-grid has exactly W + K steps, so the
+    timed steps end at z = 0; then the same W + K steps again from the same ICs with the
+    library's per-phase events on (the kernel rooflines cover the same steps as the headline)."""
     fp64 = prec == pm.PM_FP64
-    n_steps = max(100, args.warmup + 2 * args.steps + 2)
+    n_steps = args.warmup + args.steps
     cfg = pm.make_config(args.np, args.nmesh, args.box, A_INIT, A_FINAL, n_steps, precision=prec)
     run = pm.PMRun(cfg)
     run.ic(seed=1 + rank)
@@ -205,7 +208,8 @@ def bench_precision(pm, torch, args, prec, rank, world, clocks=None):
     if clocks:
         clocks.mark("t1")
     ms = max_over_ranks(ms, world)
-    # same number of steps again with per-phase events for the kernel roofline
+    run.ic(seed=1 + rank)
+    run.step(args.warmup)
     pm.pm_profile(run.ctx, True)
     pm.pm_timings(run.ctx)
     run.step(args.steps)
@@ -316,6 +320,48 @@ def batched(pm, torch, args):
             "speedup_vs_sequential": t_seq / t_batch, "steps": k}
 
 
+def adjoint(pm, torch, args):
+    """Gradient of the field-level loss against the plain forward run: 128^3 particles on a
+    128^3 mesh, L = 2000 Mpc/h, 50 FP32 steps, checkpoints every 10 steps."""
+    np_side = n = 128
+    steps, every = 50, 10
+    cfg = pm.make_config(np_side, n, 2000.0, A_INIT, A_FINAL, steps)
+    run = pm.PMRun(cfg)
+    run.ic(seed=2)
+    run.step(steps)
+    target = run.density().clone()
+    g = torch.Generator(device="cuda")
+    g.manual_seed(1)
+    w = torch.randn((np_side,) * 3, generator=g, device="cuda", dtype=torch.float32)
+    st = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def forward():
+        run.ic(white_noise=w)
+        run.step(steps)
+        return run.density()
+
+    def timed(fn, reps=3):
+        fn()
+        torch.cuda.synchronize()
+        best = float("inf")
+        for _ in range(reps):
+            e0.record(st)
+            fn()
+            e1.record(st)
+            e1.synchronize()
+            best = min(best, e0.elapsed_time(e1) * 1e-3)
+        return best
+
+    t_fwd = timed(forward)
+    t_grad = timed(lambda: run.loss_grad(w, target, checkpoint_every=every))
+    return {"workload": f"{np_side}^3 particles, {n}^3 mesh, L=2000 Mpc/h, {steps} FP32 steps, "
+                        f"checkpoints every {every} steps; gradient of the mean-square density loss "
+                        "with respect to the white-noise field",
+            "forward_ms": 1e3 * t_fwd, "loss_grad_ms": 1e3 * t_grad, "cost_ratio": t_grad / t_fwd,
+            "value": np_side**3 * steps / t_grad, "unit": "particle-steps/s (forward + reverse)"}
+
+
 def cpu_oracle(seconds, np_side=64):
     """The FP64 oracle on this host: a 64^3 sample of the workload at the same mesh spacing."""
     import numpy as np
@@ -350,6 +396,7 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--batch", type=int, default=64)
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-adjoint", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("at least 3 warm-up steps")
@@ -416,6 +463,8 @@ def main():
         out["e2e"] = e2e(pm, torch, args, rank, world)
     if not args.no_batch:
         out["batched"] = batched(pm, torch, args)
+    if not args.no_adjoint:
+        out["adjoint"] = adjoint(pm, torch, args)
     if rank == 0:
         out["cpu_baseline"] = cpu_oracle(args.cpu_seconds)
         print(json.dumps(out))

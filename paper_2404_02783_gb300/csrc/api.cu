@@ -827,14 +827,15 @@ AdjLayout adj_plan(const pm_ctx* c, int C) {
     return A;
 }
 
-// Forward transform of a real mesh of side n into spec ([kz][kx][ky]).
-pm_status fft_forward_f32(pm_ctx* c, const float* real, float2* spec, int n) {
-    PM_CK(z_r2c<float>(real, spec, n, 1, c->st));
-    PM_CK((y_rows<float, false>(spec, (int64_t)(n / 2 + 1) * n, n, c->st)));
+// Forward transforms of `batch` real meshes of side n stored back to back into as many
+// spectra ([kz][kx][ky]) stored back to back.
+pm_status fft_forward_f32(pm_ctx* c, const float* real, float2* spec, int n, int batch = 1) {
+    PM_CK(z_r2c<float>(real, spec, n, batch, c->st));
+    PM_CK((y_rows<float, false>(spec, (int64_t)batch * (n / 2 + 1) * n, n, c->st)));
     SpecOp fw;
     fw.kind = OP_FWD_STORE;
     fw.fwd = 1;
-    PM_CK(x_cols<float>(spec, nullptr, n / 2 + 1, n, fw, c->st));
+    PM_CK(x_cols<float>(spec, nullptr, batch * (n / 2 + 1), n, fw, c->st));
     return PM_OK;
 }
 
@@ -856,11 +857,12 @@ pm_status adj_kick(pm_ctx* c, const uint32_t* xs, const float* gs, double K, flo
     const size_t n3 = (size_t)n * n * n;
     const float* G[3] = {gs, gs + n3, gs + 2 * n3};
     PM_CK(adj_direct(xs, c->np3, n, lam_p, G, (float)K, lam_u, c->st));
+    // V_j and the spectra are three meshes back to back (256-byte multiples): one batched transform
     float* V[3] = {(float*)c->at(c->L.force[0]), (float*)c->at(c->L.force[1]), (float*)c->at(c->L.force[2])};
-    for (int j = 0; j < 3; ++j) PM_CK(cudaMemsetAsync(V[j], 0, n3 * 4, c->st));
+    PM_CK(cudaMemsetAsync(V[0], 0, 3 * n3 * 4, c->st));
     PM_CK(deposit_vec(xs, c->np3, n, lam_p, V, c->st));
     float2* sp[3] = {(float2*)c->at(c->L.spec[0]), (float2*)c->at(c->L.spec[1]), (float2*)c->at(c->L.spec[2])};
-    for (int j = 0; j < 3; ++j) PM_TRY(fft_forward_f32(c, V[j], sp[j], n));
+    PM_TRY(fft_forward_f32(c, V[0], sp[0], n, 3));
     const float2* in[3] = {sp[0], sp[1], sp[2]};
     PM_CK(adj_combine(in, sp[0], n, c->kf, -1.5 * c->cfg.omega_m / ((double)n * n * n), nullptr, 0, c->st));
     float* rho_bar = (float*)c->at(c->L.rho);

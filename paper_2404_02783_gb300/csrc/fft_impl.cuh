@@ -310,6 +310,10 @@ __global__ void __launch_bounds__(512) k_x_cols(cplx<T>* __restrict__ data, cplx
     // ---- per-mode operator on modes (kx = t + m Q, ky = c, kz)
     const int ny = (c < M) ? c : c - N;
     const int nz = kz;
+    // per-CTA constants, formed once in the working precision (no FP64 work per mode in FP32)
+    const T kfT = T(kf);
+    const T coefT = T(op.coef) / (kfT * kfT);
+    const T kf2T = T(kf * kf);
 #pragma unroll
     for (int m = 0; m < 8; ++m) {
         const int i = t + m * Q;
@@ -338,8 +342,7 @@ __global__ void __launch_bounds__(512) k_x_cols(cplx<T>* __restrict__ data, cplx
         } else {
             C phi;
             if constexpr (KIND == OP_NEWTON || KIND == OP_POTENTIAL) {
-                const T coef = T(op.coef / (kf * kf));
-                phi = (n2 == 0) ? cmake<C>(T(0), T(0)) : cscale(vv, coef / T(n2));
+                phi = (n2 == 0) ? cmake<C>(T(0), T(0)) : cscale(vv, coefT / T(n2));
             } else if constexpr (KIND == OP_ZA) {
                 const bool nyq = (2 * nx == -N) || (2 * ny == -N) || (nz == M);
                 const double* amp = op.amp + (int64_t)field * op.amp_stride;
@@ -373,7 +376,7 @@ __global__ void __launch_bounds__(512) k_x_cols(cplx<T>* __restrict__ data, cplx
                     phi = cmake<C>(T(P.x * op.ac2_over_n3), T(P.y * op.ac2_over_n3));
                 } else {
                     C* old = reinterpret_cast<C*>(op.phi_old) + pbase + (size_t)i * N + c;
-                    const T k2 = T(kf * kf) * T(n2);
+                    const T k2 = kf2T * T(n2);
                     const T H = T(op.calH), om = T(op.omm_a);
                     const T num_s = T(-1.5) * H * H * om;
                     T den = k2 + T(3) * H * H + T(4.5) * H * H * om;
@@ -392,7 +395,7 @@ __global__ void __launch_bounds__(512) k_x_cols(cplx<T>* __restrict__ data, cplx
             }
             v[0][m] = phi;
             if constexpr (KIND != OP_POTENTIAL) {
-                const T kx = (2 * nx == -N) ? T(0) : T(kf) * T(nx);
+                const T kx = (2 * nx == -N) ? T(0) : kfT * T(nx);
                 v[1][m] = cmake<C>(phi.y * kx, -phi.x * kx);  // -i kx phi
             }
         }

@@ -73,69 +73,131 @@ __global__ void __launch_bounds__(256) k_deposit_ticks(const uint32_t* __restric
 // Lagrangian tiles.  A CTA owns a TX x TY x TZ block of lattice sites (16 x 16 x 32
 // mesh cells' worth, R = n / np cells per lattice step); particles that have not
 // travelled far land in that mesh box widened by H cells on every side, which the CTA
-// accumulates with shared-memory atomics and then adds to the global mesh once per
-// cell.  A particle whose CIC stencil leaves the box adds its weights to global memory
-// directly, so the result is the same CIC density for any displacement.
+// accumulates in shared memory and then adds to the global mesh once per cell.  A
+// particle whose CIC stencil leaves the box adds its weights to global memory directly,
+// so the result is the same CIC density for any displacement.
+//
+// The tile accumulates in fixed point: each weight is rounded to a multiple of 2^-24
+// (half a quantum at most, 3e-8, below the FP32 rounding of a sum near 1) and added
+// with a native 32-bit integer atomic (shared-memory float atomics are a compare-and-
+// swap loop on this part).  A wrap of the 32-bit word is seen in the atomic's return
+// value and counted in an 8-bit carry per cell.  A tile holds at most 8192 mass units
+// (TX TY TZ R^3 = 8192 for every R), i.e. 2^37 quanta, so a cell's carry stays below 32
+// and the tile sum is exact and independent of the order of the additions.
+// The box starts HZ = 4 cells below the tile in z so that its rows are made of 16-byte
+// chunks aligned in the mesh: the flush adds four cells per vector reduction.
 template <int R>
 struct DepTile {
-    static constexpr int TX = 16 / R, TY = 16 / R, TZ = 32 / R, H = 2;
-    static constexpr int DX = TX * R + 2 * H, DY = TY * R + 2 * H, DZ = TZ * R + 2 * H;
-    static constexpr int CELLS = DX * DY * DZ;
+    static constexpr int TX = 16 / R, TY = 16 / R, TZ = 32 / R, H = 2, HZ = 4;
+    static constexpr int DX = TX * R + 2 * H, DY = TY * R + 2 * H, DZ = TZ * R + 2 * HZ;
+    static constexpr int CELLS = DX * DY * DZ, CHUNKS = CELLS / 4;
+    static constexpr int CARRY_WORDS = CHUNKS;  // one word of four 8-bit carries per chunk
+    static constexpr int WORDS = CELLS + CARRY_WORDS;  // shared memory: lo[CELLS], carry[CARRY_WORDS]
     static constexpr int PER = TX * TY * TZ;
+    static_assert(PER * R * R * R == 8192, "tile mass bound");
+    static_assert(DZ % 4 == 0 && (TZ * R) % 4 == 0 && HZ % 4 == 0, "z box made of aligned 16-byte chunks");
 };
+
+__device__ __forceinline__ void red_add_v4(float* dst, float4 v) {
+    asm volatile("red.relaxed.gpu.global.add.v4.f32 [%0], {%1, %2, %3, %4};\n" ::"l"(dst), "f"(v.x), "f"(v.y),
+                 "f"(v.z), "f"(v.w)
+                 : "memory");
+}
+
+constexpr float kTileQuanta = 16777216.0f;  // 2^24 quanta per unit mass
+constexpr float kTileQuantum = 5.9604644775390625e-08f;  // 2^-24
+
+__device__ __forceinline__ void tile_add(uint32_t* lo, uint32_t* carry, int c, float w) {
+    const uint32_t v = __float2uint_rn(w * kTileQuanta);
+    const uint32_t old = atomicAdd(lo + c, v);
+    if (old + v < old) atomicAdd(carry + (c >> 2), 1u << (8 * (c & 3)));
+}
+
+template <class D>
+__device__ __forceinline__ void tile_zero(uint32_t* words) {
+    for (int c = threadIdx.x; c < D::WORDS; c += blockDim.x) words[c] = 0u;
+}
+
+// One particle's CIC weights into the tile (box origin o*) or, outside it, into rho.
+template <class D>
+__device__ __forceinline__ void tile_deposit(uint32_t* lo, uint32_t* carry, float* __restrict__ rho, uint32_t u0,
+                                             uint32_t u1, uint32_t u2, int logn, float inv_cell_ticks, int ox,
+                                             int oy, int oz, float mass) {
+    const int nm = (1 << logn) - 1;
+    const CicF cx = cic_ticks(u0, logn, inv_cell_ticks);
+    const CicF cy = cic_ticks(u1, logn, inv_cell_ticks);
+    const CicF cz = cic_ticks(u2, logn, inv_cell_ticks);
+    const float wx[2] = {1.0f - cx.w1, cx.w1}, wy[2] = {1.0f - cy.w1, cy.w1}, wz[2] = {1.0f - cz.w1, cz.w1};
+    const int dx = (cx.i0 - ox) & nm, dy = (cy.i0 - oy) & nm, dz = (cz.i0 - oz) & nm;
+    if (dx < D::DX - 1 && dy < D::DY - 1 && dz < D::DZ - 1) {
+        const int c0 = (dx * D::DY + dy) * D::DZ + dz;
+#pragma unroll
+        for (int a = 0; a < 2; ++a)
+#pragma unroll
+            for (int b = 0; b < 2; ++b) {
+                const float wab = mass * wx[a] * wy[b];
+                const int c = c0 + (a * D::DY + b) * D::DZ;
+                tile_add(lo, carry, c, wab * wz[0]);
+                tile_add(lo, carry, c + 1, wab * wz[1]);
+            }
+    } else {
+        const uint32_t ix[2] = {(uint32_t)cx.i0, (uint32_t)cx.i1}, iy[2] = {(uint32_t)cy.i0, (uint32_t)cy.i1};
+#pragma unroll
+        for (int a = 0; a < 2; ++a)
+#pragma unroll
+            for (int b = 0; b < 2; ++b) {
+                const float wab = mass * wx[a] * wy[b];
+                float* row = rho + (((ix[a] << logn) + iy[b]) << logn);
+                atomicAdd(row + cz.i0, wab * wz[0]);
+                atomicAdd(row + cz.i1, wab * wz[1]);
+            }
+    }
+}
+
+// Adds the tile's cells (box origin o*, oz a multiple of 4, rho 16-byte aligned) to rho,
+// four z-cells per reduction.
+template <class D>
+__device__ __forceinline__ void tile_flush(const uint32_t* lo, const uint32_t* carry, float* __restrict__ rho, int ox,
+                                           int oy, int oz, int logn) {
+    const int nm = (1 << logn) - 1;
+    for (int c = threadIdx.x; c < D::CHUNKS; c += blockDim.x) {
+        const uint4 l = reinterpret_cast<const uint4*>(lo)[c];
+        const uint32_t h = carry[c];
+        if (l.x | l.y | l.z | l.w | h) {
+            const int lz4 = c % (D::DZ / 4), ly = (c / (D::DZ / 4)) % D::DY, lx = c / ((D::DZ / 4) * D::DY);
+            const float4 v = make_float4(__uint2float_rn(l.x) * kTileQuantum + (float)(h & 255u) * 256.0f,
+                                         __uint2float_rn(l.y) * kTileQuantum + (float)((h >> 8) & 255u) * 256.0f,
+                                         __uint2float_rn(l.z) * kTileQuantum + (float)((h >> 16) & 255u) * 256.0f,
+                                         __uint2float_rn(l.w) * kTileQuantum + (float)(h >> 24) * 256.0f);
+            red_add_v4(rho + ((((uint32_t)((ox + lx) & nm) << logn) + (uint32_t)((oy + ly) & nm)) << logn) +
+                           ((oz + 4 * lz4) & nm),
+                       v);
+        }
+    }
+}
 
 template <int R>
 __global__ void __launch_bounds__(512) k_deposit_tiled(const uint32_t* __restrict__ x, int lognp, int logn,
                                                        float inv_cell_ticks, float mass, float* __restrict__ rho) {
     typedef DepTile<R> D;
-    extern __shared__ __align__(16) float tile[];  // D::CELLS floats
-    const int np = 1 << lognp, n = 1 << logn, nm = n - 1;
-    const int ntz = np / D::TZ, nty = np / D::TY;
+    extern __shared__ __align__(16) uint32_t tile_words[];  // D::WORDS
+    uint32_t* lo = tile_words;
+    uint32_t* carry = tile_words + D::CELLS;
+    const int ntz = (1 << lognp) / D::TZ, nty = (1 << lognp) / D::TY;
     const int bz = blockIdx.x % ntz, by = (blockIdx.x / ntz) % nty, bx = blockIdx.x / (ntz * nty);
-    const int ox = bx * D::TX * R - D::H, oy = by * D::TY * R - D::H, oz = bz * D::TZ * R - D::H;
+    const int ox = bx * D::TX * R - D::H, oy = by * D::TY * R - D::H, oz = bz * D::TZ * R - D::HZ;
     const int64_t count = (int64_t)1 << (3 * lognp);
-    for (int c = threadIdx.x; c < D::CELLS / 4; c += 512) reinterpret_cast<float4*>(tile)[c] = make_float4(0, 0, 0, 0);
+    tile_zero<D>(tile_words);
     __syncthreads();
 #pragma unroll 2
     for (int e = threadIdx.x; e < D::PER; e += 512) {
         const int lz = e % D::TZ, ly = (e / D::TZ) % D::TY, lx = e / (D::TZ * D::TY);
-        const int64_t id = (((int64_t)(bx * D::TX + lx) << lognp) + by * D::TY + ly) * np + bz * D::TZ + lz;
-        const CicF cx = cic_ticks(x[id], logn, inv_cell_ticks);
-        const CicF cy = cic_ticks(x[count + id], logn, inv_cell_ticks);
-        const CicF cz = cic_ticks(x[2 * count + id], logn, inv_cell_ticks);
-        const float wx[2] = {1.0f - cx.w1, cx.w1}, wy[2] = {1.0f - cy.w1, cy.w1}, wz[2] = {1.0f - cz.w1, cz.w1};
-        const int dx = (cx.i0 - ox) & nm, dy = (cy.i0 - oy) & nm, dz = (cz.i0 - oz) & nm;
-        if (dx < D::DX - 1 && dy < D::DY - 1 && dz < D::DZ - 1) {
-#pragma unroll
-            for (int a = 0; a < 2; ++a)
-#pragma unroll
-                for (int b = 0; b < 2; ++b) {
-                    const float wab = mass * wx[a] * wy[b];
-                    float* row = tile + ((dx + a) * D::DY + dy + b) * D::DZ + dz;
-                    atomicAdd(row, wab * wz[0]);
-                    atomicAdd(row + 1, wab * wz[1]);
-                }
-        } else {
-            const int ix[2] = {cx.i0, cx.i1}, iy[2] = {cy.i0, cy.i1}, iz[2] = {cz.i0, cz.i1};
-#pragma unroll
-            for (int a = 0; a < 2; ++a)
-#pragma unroll
-                for (int b = 0; b < 2; ++b) {
-                    const float wab = mass * wx[a] * wy[b];
-                    float* row = rho + ((size_t)ix[a] * n + iy[b]) * n;
-                    atomicAdd(row + iz[0], wab * wz[0]);
-                    atomicAdd(row + iz[1], wab * wz[1]);
-                }
-        }
+        const int64_t id = ((((int64_t)(bx * D::TX + lx) << lognp) + by * D::TY + ly) << lognp) + bz * D::TZ + lz;
+        tile_deposit<D>(lo, carry, rho, x[id], x[count + id], x[2 * count + id], logn, inv_cell_ticks, ox, oy, oz,
+                        mass);
     }
     __syncthreads();
-    for (int c = threadIdx.x; c < D::CELLS; c += 512) {
-        const float v = tile[c];
-        if (v != 0.0f) {
-            const int lz = c % D::DZ, ly = (c / D::DZ) % D::DY, lx = c / (D::DZ * D::DY);
-            atomicAdd(rho + (((size_t)((ox + lx) & nm) * n + ((oy + ly) & nm)) * n + ((oz + lz) & nm)), v);
-        }
-    }
+    tile_flush<D>(lo, carry, rho, ox, oy, oz, logn);
 }
 
 __global__ void k_deposit_frac(const double* __restrict__ x, int64_t count, int n, double mass,
@@ -171,7 +233,7 @@ static cudaError_t deposit_tiled_r(const void* x, int np, int n, double mass, vo
     const int lognp = ilog2(np), logn = ilog2(n);
     const unsigned blocks = (unsigned)((np / D::TX) * (np / D::TY) * (np / D::TZ));
     const float inv = (float)ldexp(1.0, -(32 - logn));
-    const size_t smem = sizeof(float) * D::CELLS;
+    const size_t smem = sizeof(uint32_t) * D::WORDS;
     cudaError_t e = set_smem_once((const void*)k_deposit_tiled<R>, smem);
     if (e != cudaSuccess) return e;
     k_deposit_tiled<R><<<blocks, 512, smem, st>>>((const uint32_t*)x, lognp, logn, inv, (float)mass, (float*)rho);
@@ -180,7 +242,8 @@ static cudaError_t deposit_tiled_r(const void* x, int np, int n, double mass, vo
 
 cudaError_t deposit_lattice(const void* x, int np, int precision, int n, double mass, void* rho, cudaStream_t st) {
     const int R = n / np;
-    // the tile box (16 + 4) x (16 + 4) x (32 + 4) cells must fit in the mesh without overlapping itself
+    if ((uintptr_t)rho % 16 != 0) return deposit(x, (int64_t)np * np * np, precision, n, mass, rho, st);
+    // the tile box (16 + 4) x (16 + 4) x (32 + 8) cells must fit in the mesh without overlapping itself
     const bool tiled = precision == PM_FP32_FIXED && n >= 64 && (R == 1 || R == 2 || R == 4) && np >= 32 / R;
     if (!tiled) return deposit(x, (int64_t)np * np * np, precision, n, mass, rho, st);
     if (R == 1) return deposit_tiled_r<1>(x, np, n, mass, rho, st);
@@ -259,22 +322,37 @@ cudaError_t interp(const void* field, int n, const void* x, int64_t count, int p
 
 // ---------------------------------------------------------------- interp + kick + drift
 // p += kick * g(x);  x += drift * p   (g = -grad phi gathered with the deposit's weights).
+// The eight corner offsets are formed once in 32 bits (n^3 <= 2^30) and serve the
+// three force meshes.
 __device__ __forceinline__ void ikd_particle(uint32_t& u0, uint32_t& u1, uint32_t& u2, float& p0, float& p1,
                                              float& p2, int logn, float inv_cell_ticks, const float* __restrict__ gx,
                                              const float* __restrict__ gy, const float* __restrict__ gz, float kick,
                                              float drift_ticks) {
-    const size_t n = (size_t)1 << logn;
     const CicF cx = cic_ticks(u0, logn, inv_cell_ticks);
     const CicF cy = cic_ticks(u1, logn, inv_cell_ticks);
     const CicF cz = cic_ticks(u2, logn, inv_cell_ticks);
     const float wx[2] = {1.0f - cx.w1, cx.w1}, wy[2] = {1.0f - cy.w1, cy.w1}, wz[2] = {1.0f - cz.w1, cz.w1};
-    const int ix[2] = {cx.i0, cx.i1}, iy[2] = {cy.i0, cy.i1}, iz[2] = {cz.i0, cz.i1};
-    p0 += kick * gather8<float, uint32_t>(gx, n, ix, iy, iz, wx, wy, wz);
-    p1 += kick * gather8<float, uint32_t>(gy, n, ix, iy, iz, wx, wy, wz);
-    p2 += kick * gather8<float, uint32_t>(gz, n, ix, iy, iz, wx, wy, wz);
-    u0 += (uint32_t)__float2ll_rn(p0 * drift_ticks);
-    u1 += (uint32_t)__float2ll_rn(p1 * drift_ticks);
-    u2 += (uint32_t)__float2ll_rn(p2 * drift_ticks);
+    const uint32_t ix[2] = {(uint32_t)cx.i0, (uint32_t)cx.i1}, iy[2] = {(uint32_t)cy.i0, (uint32_t)cy.i1};
+    float f0 = 0.f, f1 = 0.f, f2 = 0.f;
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int b = 0; b < 2; ++b) {
+            const uint32_t row = ((ix[a] << logn) + iy[b]) << logn;
+            const uint32_t o0 = row + (uint32_t)cz.i0, o1 = row + (uint32_t)cz.i1;
+            const float w0 = wx[a] * wy[b] * wz[0], w1 = wx[a] * wy[b] * wz[1];
+            f0 = fmaf(w0, __ldg(gx + o0), fmaf(w1, __ldg(gx + o1), f0));
+            f1 = fmaf(w0, __ldg(gy + o0), fmaf(w1, __ldg(gy + o1), f1));
+            f2 = fmaf(w0, __ldg(gz + o0), fmaf(w1, __ldg(gz + o1), f2));
+        }
+    p0 = fmaf(kick, f0, p0);
+    p1 = fmaf(kick, f1, p1);
+    p2 = fmaf(kick, f2, p2);
+    // 32-bit conversion (the 64-bit one is several times slower here): exact for drifts under
+    // half the box per step, i.e. |p drift_ticks| < 2^31, the range of any meaningful step
+    u0 += (uint32_t)__float2int_rn(p0 * drift_ticks);
+    u1 += (uint32_t)__float2int_rn(p1 * drift_ticks);
+    u2 += (uint32_t)__float2int_rn(p2 * drift_ticks);
 }
 
 __global__ void __launch_bounds__(256) k_ikd_ticks(uint32_t* __restrict__ x, float* __restrict__ p, int64_t count,
@@ -378,21 +456,23 @@ cudaError_t interp_kick_drift(void* x, void* p, int64_t count, int precision, in
 // blockIdx.y selects the field of a batch of independent runs stored back to back
 // (particles [field][3][np^3], meshes [field][n^3]); scale = 2^32 / L of that field.
 template <int R>
-__global__ void __launch_bounds__(512) k_ikd_deposit(uint32_t* __restrict__ x, float* __restrict__ p, int lognp,
+__global__ void __launch_bounds__(512, 2) k_ikd_deposit(uint32_t* __restrict__ x, float* __restrict__ p, int lognp,
                                                      int logn, float inv_cell_ticks, const float* __restrict__ gx,
                                                      const float* __restrict__ gy, const float* __restrict__ gz,
                                                      float kick, double drift, double scale0,
                                                      const double* __restrict__ scale_arr, float mass,
                                                      float* __restrict__ rho) {
     typedef DepTile<R> D;
-    extern __shared__ __align__(16) float tile[];  // D::CELLS floats
-    const int np = 1 << lognp, n = 1 << logn, nm = n - 1;
+    extern __shared__ __align__(16) uint32_t tile_words[];  // D::WORDS
+    uint32_t* lo = tile_words;
+    uint32_t* carry = tile_words + D::CELLS;
+    const int np = 1 << lognp;
+    const int64_t count = (int64_t)1 << (3 * lognp);
     {
-        const int fb = blockIdx.y;
-        const int64_t cnt = (int64_t)1 << (3 * lognp);
+        const int64_t fb = blockIdx.y;
         const int64_t n3 = (int64_t)1 << (3 * logn);
-        x += fb * 3 * cnt;
-        p += fb * 3 * cnt;
+        x += fb * 3 * count;
+        p += fb * 3 * count;
         gx += fb * n3;
         gy += fb * n3;
         gz += fb * n3;
@@ -401,13 +481,12 @@ __global__ void __launch_bounds__(512) k_ikd_deposit(uint32_t* __restrict__ x, f
     const float drift_ticks = (float)(drift * (scale_arr ? scale_arr[blockIdx.y] : scale0));
     const int ntz = np / D::TZ, nty = np / D::TY;
     const int bz = blockIdx.x % ntz, by = (blockIdx.x / ntz) % nty, bx = blockIdx.x / (ntz * nty);
-    const int ox = bx * D::TX * R - D::H, oy = by * D::TY * R - D::H, oz = bz * D::TZ * R - D::H;
-    const int64_t count = (int64_t)1 << (3 * lognp);
-    for (int c = threadIdx.x; c < D::CELLS / 4; c += 512) reinterpret_cast<float4*>(tile)[c] = make_float4(0, 0, 0, 0);
+    const int ox = bx * D::TX * R - D::H, oy = by * D::TY * R - D::H, oz = bz * D::TZ * R - D::HZ;
+    tile_zero<D>(tile_words);
     __syncthreads();
     for (int e = threadIdx.x; e < D::PER; e += 512) {
         const int lz = e % D::TZ, ly = (e / D::TZ) % D::TY, lx = e / (D::TZ * D::TY);
-        const int64_t id = (((int64_t)(bx * D::TX + lx) << lognp) + by * D::TY + ly) * np + bz * D::TZ + lz;
+        const int64_t id = ((((int64_t)(bx * D::TX + lx) << lognp) + by * D::TY + ly) << lognp) + bz * D::TZ + lz;
         uint32_t u0 = x[id], u1 = x[count + id], u2 = x[2 * count + id];
         float p0 = p[id], p1 = p[count + id], p2 = p[2 * count + id];
         ikd_particle(u0, u1, u2, p0, p1, p2, logn, inv_cell_ticks, gx, gy, gz, kick, drift_ticks);
@@ -417,42 +496,10 @@ __global__ void __launch_bounds__(512) k_ikd_deposit(uint32_t* __restrict__ x, f
         x[id] = u0;
         x[count + id] = u1;
         x[2 * count + id] = u2;
-        const CicF cx = cic_ticks(u0, logn, inv_cell_ticks);
-        const CicF cy = cic_ticks(u1, logn, inv_cell_ticks);
-        const CicF cz = cic_ticks(u2, logn, inv_cell_ticks);
-        const float wx[2] = {1.0f - cx.w1, cx.w1}, wy[2] = {1.0f - cy.w1, cy.w1}, wz[2] = {1.0f - cz.w1, cz.w1};
-        const int dx = (cx.i0 - ox) & nm, dy = (cy.i0 - oy) & nm, dz = (cz.i0 - oz) & nm;
-        if (dx < D::DX - 1 && dy < D::DY - 1 && dz < D::DZ - 1) {
-#pragma unroll
-            for (int a = 0; a < 2; ++a)
-#pragma unroll
-                for (int b = 0; b < 2; ++b) {
-                    const float wab = mass * wx[a] * wy[b];
-                    float* row = tile + ((dx + a) * D::DY + dy + b) * D::DZ + dz;
-                    atomicAdd(row, wab * wz[0]);
-                    atomicAdd(row + 1, wab * wz[1]);
-                }
-        } else {
-            const int ix[2] = {cx.i0, cx.i1}, iy[2] = {cy.i0, cy.i1}, iz[2] = {cz.i0, cz.i1};
-#pragma unroll
-            for (int a = 0; a < 2; ++a)
-#pragma unroll
-                for (int b = 0; b < 2; ++b) {
-                    const float wab = mass * wx[a] * wy[b];
-                    float* row = rho + ((size_t)ix[a] * n + iy[b]) * n;
-                    atomicAdd(row + iz[0], wab * wz[0]);
-                    atomicAdd(row + iz[1], wab * wz[1]);
-                }
-        }
+        tile_deposit<D>(lo, carry, rho, u0, u1, u2, logn, inv_cell_ticks, ox, oy, oz, mass);
     }
     __syncthreads();
-    for (int c = threadIdx.x; c < D::CELLS; c += 512) {
-        const float v = tile[c];
-        if (v != 0.0f) {
-            const int lz = c % D::DZ, ly = (c / D::DZ) % D::DY, lx = c / (D::DZ * D::DY);
-            atomicAdd(rho + (((size_t)((ox + lx) & nm) * n + ((oy + ly) & nm)) * n + ((oz + lz) & nm)), v);
-        }
-    }
+    tile_flush<D>(lo, carry, rho, ox, oy, oz, logn);
 }
 
 template <int R>
@@ -463,7 +510,7 @@ static cudaError_t ikd_deposit_r(void* x, void* p, int np, int n, void* const* g
     const int lognp = ilog2(np), logn = ilog2(n);
     const unsigned blocks = (unsigned)((np / D::TX) * (np / D::TY) * (np / D::TZ));
     const float inv = (float)ldexp(1.0, -(32 - logn));
-    const size_t smem = sizeof(float) * D::CELLS;
+    const size_t smem = sizeof(uint32_t) * D::WORDS;
     cudaError_t e = set_smem_once((const void*)k_ikd_deposit<R>, smem);
     if (e != cudaSuccess) return e;
     k_ikd_deposit<R><<<dim3(blocks, nfields), 512, smem, st>>>((uint32_t*)x, (float*)p, lognp, logn, inv,
@@ -482,7 +529,8 @@ bool ikd_deposit_supported(int np, int precision, int n) {
 cudaError_t interp_kick_drift_deposit(void* x, void* p, int np, int precision, int n, void* const* g, double kick,
                                       double drift, double box, double mass, void* rho, cudaStream_t st, int nfields,
                                       const double* scale_arr) {
-    if (!ikd_deposit_supported(np, precision, n) || nfields < 1) return cudaErrorInvalidValue;
+    if (!ikd_deposit_supported(np, precision, n) || nfields < 1 || (uintptr_t)rho % 16 != 0)
+        return cudaErrorInvalidValue;
     const int R = n / np;
     if (R == 1) return ikd_deposit_r<1>(x, p, np, n, g, kick, drift, box, mass, rho, st, nfields, scale_arr);
     if (R == 2) return ikd_deposit_r<2>(x, p, np, n, g, kick, drift, box, mass, rho, st, nfields, scale_arr);
