@@ -33,7 +33,7 @@ sys.path.insert(0, ROOT)
 METRIC = "PM particle-steps/s and fraction of HBM roofline at 512^3, FP32 vs FP64 plain"
 UNIT = "particle-steps/s"
 A_INIT, A_FINAL = 1.0 / 51.0, 1.0
-PHASES = ("deposit", "fft_z_r2c", "fft_y_fwd", "fft_x_green", "fft_y_grad", "fft_z_c2r", "kick_drift")
+PHASES = ("deposit", "fft_zy_fwd", "fft_x_green", "fft_yz_inv", "kick_drift")
 
 
 def peaks():
@@ -51,6 +51,13 @@ def fused_update(np_side, n, fp64):
     return (not fp64) and n >= 64 and r in (1, 2, 4) and np_side >= 32 // r
 
 
+def launches_per_step(np_side, n, fp64):
+    """Kernels of this library launched per step (one force evaluation + one update):
+    z r2c, y, x with the Green's function, y with the y gradient, z c2r of the three force
+    components, and the update (+ the deposit when it is not fused into the update)."""
+    return 5 + (1 if fused_update(np_side, n, fp64) else 2)
+
+
 def kernel_bytes(np_side, n, fp64):
     """Algorithmic bytes per launch of each phase (each array it must touch, once)."""
     s = 8 if fp64 else 4
@@ -59,11 +66,9 @@ def kernel_bytes(np_side, n, fp64):
     S = (n // 2 + 1) * n * n * 2 * s
     kb = {
         "deposit": 3 * s * P + R,            # read x, write rho
-        "fft_z_r2c": R + S,                  # read rho, write half spectrum
-        "fft_y_fwd": 2 * S,
+        "fft_zy_fwd": R + S,                 # read rho, write the y-transformed half spectrum
         "fft_x_green": 3 * S,                # read delta_k, write IFFT_x(phi), IFFT_x(-i kx phi)
-        "fft_y_grad": 5 * S,                 # read 2, write 3
-        "fft_z_c2r": 3 * S + 3 * R,          # read 3 spectra, write 3 force meshes
+        "fft_yz_inv": 2 * S + 3 * R,         # read the two x-inverted spectra, write 3 force meshes
         "kick_drift": 12 * s * P + 3 * R,    # read + write x, p; gather 3 meshes once
     }
     if fused_update(np_side, n, fp64):
@@ -445,7 +450,7 @@ def main():
            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded Philox phases, EH no-wiggle LCDM)",
            "config": {**config, "a_grid_steps": n_steps}, "clocks": clk,
-           "gpu_launches": (6 if fused_update(args.np, args.nmesh, False) else 7) * args.steps,
+           "gpu_launches": launches_per_step(args.np, args.nmesh, False) * args.steps,
            "roofline": roof,
            "step_roofline": {"bytes_per_step": sb, "achieved": round(sb / (ms_step * 1e-3) / 1e9, 1),
                              "peak": peak, "unit": "GB/s", "frac": round(sb / (ms_step * 1e-3) / 1e9 / peak, 4),

@@ -135,17 +135,16 @@ pm_status pm_state(pm_ctx* ctx, int* step, double* a, int* synchronised);
 /* Per-phase device timing of pm_step with CUDA events recorded on the context
  * stream around each kernel of a force evaluation and update.  pm_profile(ctx, 1)
  * starts recording (0 stops); pm_timings synchronises the stream, writes the summed
- * milliseconds and the number of timed launches per phase since the previous call
- * into caller arrays of PM_NPHASES entries, and resets the counters. */
+ * milliseconds and the number of timed launch groups per phase since the previous
+ * call into caller arrays of PM_NPHASES entries, and resets the counters. */
 enum {
     PM_PHASE_DEPOSIT = 0,      /* zeroing + CIC deposit */
-    PM_PHASE_FFT_Z_R2C = 1,    /* z pass, real to half spectrum */
-    PM_PHASE_FFT_Y_FWD = 2,    /* forward y pass */
-    PM_PHASE_FFT_X_GREEN = 3,  /* x pass with Green's function / constraint and x gradient */
-    PM_PHASE_FFT_Y_GRAD = 4,   /* inverse y pass with y gradient */
-    PM_PHASE_FFT_Z_C2R = 5,    /* inverse z pass of the three force components */
-    PM_PHASE_KICK_DRIFT = 6,   /* CIC interpolation + kick + drift */
-    PM_NPHASES = 7
+    PM_PHASE_FFT_ZY_FWD = 1,   /* z (real to half spectrum) and forward y passes, by x-slab chunks */
+    PM_PHASE_FFT_X_GREEN = 2,  /* x pass with Green's function / constraint and x gradient */
+    PM_PHASE_FFT_YZ_INV = 3,   /* inverse y (with y gradient) and z passes of the three force
+                                  components (z gradient fused), by x-slab chunks */
+    PM_PHASE_KICK_DRIFT = 4,   /* CIC interpolation + kick + drift (+ next deposit when fused) */
+    PM_NPHASES = 5
 };
 pm_status pm_profile(pm_ctx* ctx, int enable);
 pm_status pm_timings(pm_ctx* ctx, double* ms, int64_t* launches);

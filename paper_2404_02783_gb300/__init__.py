@@ -191,7 +191,7 @@ def pm_state(ctx):
     return s.value, a.value, bool(y.value)
 
 
-PHASES = ("deposit", "fft_z_r2c", "fft_y_fwd", "fft_x_green", "fft_y_grad", "fft_z_c2r", "kick_drift")
+PHASES = ("deposit", "fft_zy_fwd", "fft_x_green", "fft_yz_inv", "kick_drift")
 
 
 def pm_profile(ctx, enable=True):

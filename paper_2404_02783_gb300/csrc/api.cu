@@ -177,14 +177,11 @@ struct Phase {
     }
 };
 
+// Forward z and y passes of a real mesh of side n into spec.
 template <typename T>
 pm_status forward_to_y(pm_ctx* c, const void* real, void* spec, int n) {
-    {
-        Phase ph(c, PM_PHASE_FFT_Z_R2C);
-        PM_CK(z_r2c<T>((const T*)real, (cplx<T>*)spec, n, 1, c->st));
-    }
-    Phase ph(c, PM_PHASE_FFT_Y_FWD);
-    PM_CK((y_rows<T, false>((cplx<T>*)spec, (int64_t)(n / 2 + 1) * n, n, c->st)));
+    Phase ph(c, PM_PHASE_FFT_ZY_FWD);
+    PM_CK(forward_zy<T>((const T*)real, (cplx<T>*)spec, n, 1, c->st));
     return PM_OK;
 }
 
@@ -208,20 +205,13 @@ pm_status compute_forces_t(pm_ctx* c, double a) {
     cplx<T>* s0 = (cplx<T>*)c->at(c->L.spec[0]);
     cplx<T>* s1 = (cplx<T>*)c->at(c->L.spec[1]);
     cplx<T>* s2 = (cplx<T>*)c->at(c->L.spec[2]);
-    {
-        Phase ph(c, PM_PHASE_FFT_Z_R2C);
-        PM_CK(z_r2c<T>((const T*)rho, s0, n, 1, c->st));
-    }
+    PM_TRY(forward_to_y<T>(c, rho, s0, n));
     if (fused_update(c)) {
         // the forward z pass has consumed rho: clear it for the fused deposit of the update
         Phase ph(c, PM_PHASE_DEPOSIT);
         PM_CK(cudaMemsetAsync(rho, 0, sizeof(T) * (size_t)n * n * n, c->st));
     }
     c->rho_valid = false;
-    {
-        Phase ph(c, PM_PHASE_FFT_Y_FWD);
-        PM_CK((y_rows<T, false>(s0, (int64_t)(n / 2 + 1) * n, n, c->st)));
-    }
     SpecOp op;
     op.kf = c->kf;
     op.fwd = 1;
@@ -245,14 +235,9 @@ pm_status compute_forces_t(pm_ctx* c, double a) {
         PM_CK(x_cols<T>(s0, s1, n / 2 + 1, n, op, c->st));
     }
     {
-        Phase ph(c, PM_PHASE_FFT_Y_GRAD);
-        PM_CK(y_rows_grad3<T>(s0, s1, s2, (int64_t)(n / 2 + 1) * n, n, c->kf, c->st));
-    }
-    {
-        Phase ph(c, PM_PHASE_FFT_Z_C2R);
-        const cplx<T>* in[3] = {s1, s2, s0};
+        Phase ph(c, PM_PHASE_FFT_YZ_INV);
         T* out[3] = {(T*)c->at(c->L.force[0]), (T*)c->at(c->L.force[1]), (T*)c->at(c->L.force[2])};
-        PM_CK(z_c2r<T>(in, out, 3, n, 1, 4u, c->kf, c->st));
+        PM_CK(inverse_yz_grad<T>(s0, s1, s2, out, n, 1, c->kf, c->st));
     }
     if (c->cfg.mode == PM_GR_POISSON) {
         c->have_phi = true;
@@ -1061,19 +1046,16 @@ pm_status batch_forces(pm_batch* b, cudaStream_t s) {
     float2* s1 = (float2*)b->at(b->SPEC[1]);
     float2* s2 = (float2*)b->at(b->SPEC[2]);
     const double* kf = (const double*)b->at(b->KF);
-    PM_CK(z_r2c<float>(rho, s0, n, B, s));
+    PM_CK(forward_zy<float>(rho, s0, n, B, s));
     PM_CK(cudaMemsetAsync(rho, 0, sizeof(float) * (size_t)B * n * n * n, s));
-    PM_CK((y_rows<float, false>(s0, (int64_t)B * (M + 1) * n, n, s)));
     SpecOp op;
     op.kind = OP_NEWTON;
     op.fwd = 1;
     op.coef = -1.5 * b->cfg.omega_m / ((double)n * n * n);
     op.kf_arr = kf;
     PM_CK(x_cols<float>(s0, s1, B * (M + 1), n, op, s));
-    PM_CK(y_rows_grad3<float>(s0, s1, s2, (int64_t)B * (M + 1) * n, n, 0.0, s, kf, (int64_t)(M + 1) * n));
-    const float2* in[3] = {s1, s2, s0};
     float* out[3] = {(float*)b->at(b->FORCE[0]), (float*)b->at(b->FORCE[1]), (float*)b->at(b->FORCE[2])};
-    PM_CK(z_c2r<float>(in, out, 3, n, B, 4u, 0.0, s, kf));
+    PM_CK(inverse_yz_grad<float>(s0, s1, s2, out, n, B, 0.0, s, kf));
     return PM_OK;
 }
 

@@ -7,11 +7,11 @@
 //   x_cols: columns along x (stride n)                 -> S[kz][kx][ky]
 // and the inverse runs x_cols -> y_rows -> z_c2r.  Every pass reads and writes each
 // element once: loads go straight from global memory into registers, the butterflies
-// run in registers, shared memory carries only the exchanges between stages.  The
-// Green's function, the Poisson-gauge constraint, the Zel'dovich filter, the x part
-// of the spectral gradient and the power-spectrum binning act on registers inside
-// the x-column pass, the y part of the gradient inside the inverse y pass and the z
-// part inside the c2r pass.
+// run in registers, shared memory carries only the exchanges between stages.
+//
+// Slab rows g = field n + x index the z passes; the half spectrum of slab row g and
+// frequency kz sits at row ((g / C) (n/2 + 1) + kz) C + g % C with C = n, i.e. the
+// layout [field][kz][x][y].
 #pragma once
 
 #include <math.h>
@@ -61,9 +61,16 @@ template <typename T, int LOGN> struct Shape {
     static constexpr int CB = (sizeof(T) == 8 && N >= 512) ? CB0 / 2 : CB0;  // x pass columns
 };
 
+// Row of (slab row gl relative to the chunk start, frequency kz) in a half spectrum whose
+// blocks hold 2^xcl slab rows.
+template <int M>
+__device__ __forceinline__ size_t spec_row(int gl, int kz, int xcl) {
+    return (((size_t)(gl >> xcl) * (M + 1) + kz) << xcl) + (gl & ((1 << xcl) - 1));
+}
+
 // =============================================================== z: r2c
 template <typename T, int LOGN>
-__global__ void __launch_bounds__(512) k_z_r2c(const T* __restrict__ in, cplx<T>* __restrict__ out) {
+__global__ void __launch_bounds__(512) k_z_r2c(const T* __restrict__ in, cplx<T>* __restrict__ out, int g0, int xcl) {
     typedef cplx<T> C;
     typedef Shape<T, LOGN> S;
     constexpr int N = S::N, M = S::M, Q = S::QM, YB = S::YB;
@@ -75,12 +82,12 @@ __global__ void __launch_bounds__(512) k_z_r2c(const T* __restrict__ in, cplx<T>
     C* buf = twN + TWN;
     const int tid = threadIdx.x;
     const int y0 = blockIdx.x * YB;
-    const int x = blockIdx.y % N;
-    const size_t f = blockIdx.y / N;
+    const int gl = blockIdx.y;
+    const size_t g = (size_t)g0 + gl;
     load_twiddles<T>(twM, M);
     load_twiddles_head<T>(twN, N, M + 1);
     const int b = tid / Q, t = tid % Q;
-    const C* row = reinterpret_cast<const C*>(in + ((f * N + x) * (size_t)N + y0 + b) * N);
+    const C* row = reinterpret_cast<const C*>(in + (g * N + y0 + b) * N);
     C v[1][8];
 #pragma unroll
     for (int m = 0; m < 8; ++m) v[0][m] = row[t + m * Q];
@@ -92,7 +99,6 @@ __global__ void __launch_bounds__(512) k_z_r2c(const T* __restrict__ in, cplx<T>
 #pragma unroll
     for (int m = 0; m < 8; ++m) z[b * RS + spad(t + m * Q)] = v[0][m];
     __syncthreads();
-    C* outp = out + f * (size_t)(M + 1) * N * N;
     constexpr int NT = YB * Q, ITERS = ((M + 1) * YB + NT - 1) / NT;
 #pragma unroll
     for (int it = 0; it < ITERS; ++it) {
@@ -103,7 +109,7 @@ __global__ void __launch_bounds__(512) k_z_r2c(const T* __restrict__ in, cplx<T>
         const C z2 = cconj(z[bb * RS + spad(k == 0 ? 0 : M - k)]);
         const C E = cscale(cadd(z1, z2), T(0.5));
         const C O = cscale(cmul_mi<false>(csub(z1, z2)), T(0.5));
-        outp[((size_t)k * N + x) * N + y0 + bb] = cadd(E, cmul(twN[k], O));
+        out[spec_row<M>(gl, k, xcl) * N + y0 + bb] = cadd(E, cmul(twN[k], O));
     }
 }
 
@@ -114,7 +120,8 @@ template <typename T> struct Ptr3 {
 };
 
 template <typename T, int LOGN>
-__global__ void __launch_bounds__(512) k_z_c2r(Ptr3<T> P, unsigned gradz_mask, T kf0, const double* __restrict__ kf_arr) {
+__global__ void __launch_bounds__(512) k_z_c2r(Ptr3<T> P, unsigned gradz_mask, T kf0, const double* __restrict__ kf_arr,
+                                               int g0, int xcl) {
     typedef cplx<T> C;
     typedef Shape<T, LOGN> S;
     constexpr int N = S::N, M = S::M, Q = S::QM, YB = S::YB;
@@ -128,14 +135,13 @@ __global__ void __launch_bounds__(512) k_z_c2r(Ptr3<T> P, unsigned gradz_mask, T
     const int comp = blockIdx.z;
     const bool grad = (gradz_mask >> comp) & 1u;
     const int y0 = blockIdx.x * YB;
-    const int x = blockIdx.y % N;
-    const size_t f = blockIdx.y / N;
+    const int gl = blockIdx.y;
+    const size_t g = (size_t)g0 + gl;
     load_twiddles<T>(twM, M);
     load_twiddles_head<T>(twN, N, M + 1);
-    const T kf = kf_arr ? T(kf_arr[f]) : kf0;
-    const C* pin = comp == 0 ? P.in[0] : (comp == 1 ? P.in[1] : P.in[2]);
+    const T kf = kf_arr ? T(kf_arr[g >> LOGN]) : kf0;
+    const C* inp = comp == 0 ? P.in[0] : (comp == 1 ? P.in[1] : P.in[2]);
     T* pout = comp == 0 ? P.out[0] : (comp == 1 ? P.out[1] : P.out[2]);
-    const C* inp = pin + f * (size_t)(M + 1) * N * N;
     C* xb = buf;  // gathered half spectrum; the FFT exchanges reuse the buffer afterwards
     constexpr int NT = YB * Q, ITERS = ((M + 1) * YB + NT - 1) / NT;
 #pragma unroll
@@ -143,7 +149,7 @@ __global__ void __launch_bounds__(512) k_z_c2r(Ptr3<T> P, unsigned gradz_mask, T
         const int e = tid + it * NT;
         if (e >= (M + 1) * YB) break;
         const int k = e / YB, bb = e % YB;
-        C X = inp[((size_t)k * N + x) * N + y0 + bb];
+        C X = inp[spec_row<M>(gl, k, xcl) * N + y0 + bb];
         if (grad) {  // (-i kz) X, Nyquist kz -> 0
             const T kz = (k == M) ? T(0) : kf * T(k);
             X = cmake<C>(X.y * kz, -X.x * kz);
@@ -178,14 +184,15 @@ __global__ void __launch_bounds__(512) k_z_c2r(Ptr3<T> P, unsigned gradz_mask, T
     for (int m = 0; m < 8; ++m) v[0][m] = xb[b * RS + spad(t + m * Q)];
     RowEx<C, 1, false> ex{buf, YB, RS, b, 0};
     fft_regs<M, 1, true>(v, t, twM, ex);
-    C* orow = reinterpret_cast<C*>(pout + ((f * N + x) * (size_t)N + y0 + b) * N);
+    C* orow = reinterpret_cast<C*>(pout + (g * N + y0 + b) * N);
 #pragma unroll
     for (int m = 0; m < 8; ++m) orow[t + m * Q] = v[0][m];
 }
 
 // =============================================================== y: contiguous rows
+// In place when in == out.
 template <typename T, int LOGN, bool INV>
-__global__ void __launch_bounds__(512) k_y_rows(cplx<T>* __restrict__ data, int64_t nrows) {
+__global__ void __launch_bounds__(512) k_y_rows(const cplx<T>* in, cplx<T>* out, int64_t nrows) {
     typedef cplx<T> C;
     typedef Shape<T, LOGN> S;
     constexpr int N = S::N, Q = S::QN, RB = S::RB;
@@ -199,23 +206,24 @@ __global__ void __launch_bounds__(512) k_y_rows(cplx<T>* __restrict__ data, int6
     const bool ok = r < nrows;
     load_twiddles<T>(tw, N);
     C v[1][8];
-    C* row = data + r * N;
+    const C* irow = in + r * N;
     if (ok) {
 #pragma unroll
-        for (int m = 0; m < 8; ++m) v[0][m] = row[t + m * Q];
+        for (int m = 0; m < 8; ++m) v[0][m] = irow[t + m * Q];
     }
     __syncthreads();
     RowEx<C, 1, true> ex{buf, RB, RS, b, 0};
     fft_regs<N, 1, INV>(v, t, tw, ex);
+    C* orow = out + r * N;
     if (ok) {
 #pragma unroll
-        for (int m = 0; m < 8; ++m) row[t + m * Q] = v[0][m];
+        for (int m = 0; m < 8; ++m) orow[t + m * Q] = v[0][m];
     }
 }
 
-// A <- IFFT_y(A), B <- IFFT_y(B), C <- IFFT_y(-i ky A)
+// A' = IFFT_y(A), B' = IFFT_y(B), C' = IFFT_y(-i ky A) (in place when Aout == A, Bout == B).
 template <typename T, int LOGN>
-__global__ void __launch_bounds__(512) k_y_grad3(cplx<T>* __restrict__ A, cplx<T>* __restrict__ B,
+__global__ void __launch_bounds__(512) k_y_grad3(const cplx<T>* A, const cplx<T>* B, cplx<T>* Aout, cplx<T>* Bout,
                                                  cplx<T>* __restrict__ Cout, int64_t nrows, T kf0,
                                                  const double* __restrict__ kf_arr, int64_t rows_per_field) {
     typedef cplx<T> C;
@@ -229,6 +237,7 @@ __global__ void __launch_bounds__(512) k_y_grad3(cplx<T>* __restrict__ A, cplx<T
     const int b = tid / Q, t = tid % Q;
     const int64_t r = (int64_t)blockIdx.x * RB + b;
     const bool ok = r < nrows;
+    const int64_t ri = r;
     const T kf = (kf_arr && ok) ? T(kf_arr[r / rows_per_field]) : kf0;
     load_twiddles<T>(tw, N);
     C v[3][8];
@@ -236,9 +245,9 @@ __global__ void __launch_bounds__(512) k_y_grad3(cplx<T>* __restrict__ A, cplx<T
 #pragma unroll
         for (int m = 0; m < 8; ++m) {
             const int i = t + m * Q;
-            const C a = A[r * N + i];
+            const C a = A[ri * N + i];
             v[0][m] = a;
-            v[1][m] = B[r * N + i];
+            v[1][m] = B[ri * N + i];
             const int ny = (i < N / 2) ? i : i - N;
             const T ky = (2 * ny == -N) ? T(0) : kf * T(ny);
             v[2][m] = cmake<C>(a.y * ky, -a.x * ky);
@@ -251,8 +260,8 @@ __global__ void __launch_bounds__(512) k_y_grad3(cplx<T>* __restrict__ A, cplx<T
 #pragma unroll
         for (int m = 0; m < 8; ++m) {
             const int i = t + m * Q;
-            A[r * N + i] = v[0][m];
-            B[r * N + i] = v[1][m];
+            Aout[r * N + i] = v[0][m];
+            Bout[r * N + i] = v[1][m];
             Cout[r * N + i] = v[2][m];
         }
     }
@@ -422,48 +431,73 @@ __global__ void __launch_bounds__(512) k_x_cols(cplx<T>* __restrict__ data, cplx
 
 // =============================================================== launchers
 template <typename T, int LOGN>
-cudaError_t z_r2c_n(const T* in, cplx<T>* out, int batch, cudaStream_t st) {
+cudaError_t z_r2c_n(const T* in, cplx<T>* out, int g0, int rows, int xcl, cudaStream_t st) {
     typedef Shape<T, LOGN> S;
     const size_t smem = sizeof(cplx<T>) * (S::M + ((S::M + 2) & ~1) + (size_t)S::YB * row_stride(S::M + 1));
     cudaError_t e = set_smem((const void*)k_z_r2c<T, LOGN>, smem);
     if (e != cudaSuccess) return e;
-    k_z_r2c<T, LOGN><<<dim3(S::N / S::YB, S::N * batch), S::YB * S::QM, smem, st>>>(in, out);
+    k_z_r2c<T, LOGN><<<dim3(S::N / S::YB, rows), S::YB * S::QM, smem, st>>>(in, out, g0, xcl);
     return cudaGetLastError();
 }
 
 template <typename T, int LOGN>
-cudaError_t z_c2r_n(const Ptr3<T>& P, int ncomp, int batch, unsigned mask, double kf, cudaStream_t st,
+cudaError_t z_c2r_n(const Ptr3<T>& P, int ncomp, int g0, int rows, int xcl, unsigned mask, double kf, cudaStream_t st,
                     const double* kf_arr) {
     typedef Shape<T, LOGN> S;
     const size_t smem = sizeof(cplx<T>) * (S::M + ((S::M + 2) & ~1) + (size_t)S::YB * row_stride(S::M + 1));
     cudaError_t e = set_smem((const void*)k_z_c2r<T, LOGN>, smem);
     if (e != cudaSuccess) return e;
-    k_z_c2r<T, LOGN><<<dim3(S::N / S::YB, S::N * batch, ncomp), S::YB * S::QM, smem, st>>>(P, mask, (T)kf, kf_arr);
+    k_z_c2r<T, LOGN><<<dim3(S::N / S::YB, rows, ncomp), S::YB * S::QM, smem, st>>>(P, mask, (T)kf, kf_arr, g0, xcl);
     return cudaGetLastError();
 }
 
 template <typename T, int LOGN, bool INV>
-cudaError_t y_rows_n(cplx<T>* data, int64_t nrows, cudaStream_t st) {
+cudaError_t y_rows_n(const cplx<T>* in, cplx<T>* out, int64_t nrows, cudaStream_t st) {
     typedef Shape<T, LOGN> S;
     const size_t smem = sizeof(cplx<T>) * (S::N + 2 * (size_t)S::RB * row_stride(S::N));
     cudaError_t e = set_smem((const void*)k_y_rows<T, LOGN, INV>, smem);
     if (e != cudaSuccess) return e;
     const int64_t nblk = (nrows + S::RB - 1) / S::RB;
-    k_y_rows<T, LOGN, INV><<<(unsigned)nblk, S::RB * S::QN, smem, st>>>(data, nrows);
+    k_y_rows<T, LOGN, INV><<<(unsigned)nblk, S::RB * S::QN, smem, st>>>(in, out, nrows);
     return cudaGetLastError();
 }
 
 template <typename T, int LOGN>
-cudaError_t y_grad3_n(cplx<T>* A, cplx<T>* B, cplx<T>* Cc, int64_t nrows, double kf, cudaStream_t st,
-                      const double* kf_arr, int64_t rows_per_field) {
+cudaError_t y_grad3_n(const cplx<T>* A, const cplx<T>* B, cplx<T>* Ao, cplx<T>* Bo, cplx<T>* Co, int64_t nrows, double kf,
+                      cudaStream_t st, const double* kf_arr, int64_t rows_per_field) {
     typedef Shape<T, LOGN> S;
     const size_t smem = sizeof(cplx<T>) * (S::N + 3 * (size_t)S::RB3 * row_stride(S::N));
     cudaError_t e = set_smem((const void*)k_y_grad3<T, LOGN>, smem);
     if (e != cudaSuccess) return e;
     const int64_t nblk = (nrows + S::RB3 - 1) / S::RB3;
-    k_y_grad3<T, LOGN><<<(unsigned)nblk, S::RB3 * S::QN, smem, st>>>(A, B, Cc, nrows, (T)kf, kf_arr,
+    k_y_grad3<T, LOGN><<<(unsigned)nblk, S::RB3 * S::QN, smem, st>>>(A, B, Ao, Bo, Co, nrows, (T)kf, kf_arr,
                                                                        rows_per_field);
     return cudaGetLastError();
+}
+
+template <typename T, int LOGN>
+cudaError_t forward_zy_n(const T* in, cplx<T>* spec, int batch, cudaStream_t st) {
+    constexpr int N = 1 << LOGN, M = N / 2;
+    cudaError_t e = z_r2c_n<T, LOGN>(in, spec, 0, N * batch, LOGN, st);
+    if (e != cudaSuccess) return e;
+    return y_rows_n<T, LOGN, false>(spec, spec, (int64_t)batch * (M + 1) * N, st);
+}
+
+// A (phi after the inverse x pass) and B (-i kx phi) in the full layout; scratch holds
+// one half spectrum for IFFT_y(-i ky A).
+template <typename T, int LOGN>
+cudaError_t inverse_yz_grad_n(cplx<T>* A, cplx<T>* B, cplx<T>* scratch, T* const* out, int batch, double kf,
+                              const double* kf_arr, cudaStream_t st) {
+    constexpr int N = 1 << LOGN, M = N / 2;
+    const int64_t rows = (int64_t)batch * (M + 1) * N;
+    cudaError_t e = y_grad3_n<T, LOGN>(A, B, A, B, scratch, rows, kf, st, kf_arr, (int64_t)(M + 1) * N);
+    if (e != cudaSuccess) return e;
+    Ptr3<T> P;
+    P.in[0] = B;        // IFFT_y(-i kx phi)   -> g_x
+    P.in[1] = scratch;  // IFFT_y(-i ky phi)   -> g_y
+    P.in[2] = A;        // IFFT_y(phi), -i kz  -> g_z
+    for (int j = 0; j < 3; ++j) P.out[j] = out[j];
+    return z_c2r_n<T, LOGN>(P, 3, 0, N * batch, LOGN, 4u, kf, st, kf_arr);
 }
 
 template <typename T, int LOGN, int KIND>
@@ -504,7 +538,7 @@ cudaError_t x_cols_kind(cplx<T>* data, cplx<T>* out2, int nplanes, const SpecOp&
 
 template <typename T>
 cudaError_t z_r2c(const T* in, cplx<T>* out, int n, int batch, cudaStream_t st) {
-    PM_DISPATCH_LOGN(n, (z_r2c_n<T, LG>(in, out, batch, st)))
+    PM_DISPATCH_LOGN(n, (z_r2c_n<T, LG>(in, out, 0, n * batch, LG, st)))
 }
 
 template <typename T>
@@ -515,18 +549,29 @@ cudaError_t z_c2r(const cplx<T>* const* in, T* const* out, int ncomp, int n, int
         P.in[j] = in[j < ncomp ? j : 0];
         P.out[j] = out[j < ncomp ? j : 0];
     }
-    PM_DISPATCH_LOGN(n, (z_c2r_n<T, LG>(P, ncomp, batch, gradz_mask, kf, st, kf_arr)))
+    PM_DISPATCH_LOGN(n, (z_c2r_n<T, LG>(P, ncomp, 0, n * batch, LG, gradz_mask, kf, st, kf_arr)))
 }
 
 template <typename T, bool INV>
 cudaError_t y_rows(cplx<T>* data, int64_t nrows, int n, cudaStream_t st) {
-    PM_DISPATCH_LOGN(n, (y_rows_n<T, LG, INV>(data, nrows, st)))
+    PM_DISPATCH_LOGN(n, (y_rows_n<T, LG, INV>(data, data, nrows, st)))
 }
 
 template <typename T>
 cudaError_t y_rows_grad3(cplx<T>* A, cplx<T>* B, cplx<T>* Cc, int64_t nrows, int n, double kf, cudaStream_t st,
                          const double* kf_arr, int64_t rows_per_field) {
-    PM_DISPATCH_LOGN(n, (y_grad3_n<T, LG>(A, B, Cc, nrows, kf, st, kf_arr, rows_per_field)))
+    PM_DISPATCH_LOGN(n, (y_grad3_n<T, LG>(A, B, A, B, Cc, nrows, kf, st, kf_arr, rows_per_field)))
+}
+
+template <typename T>
+cudaError_t forward_zy(const T* in, cplx<T>* spec, int n, int batch, cudaStream_t st) {
+    PM_DISPATCH_LOGN(n, (forward_zy_n<T, LG>(in, spec, batch, st)))
+}
+
+template <typename T>
+cudaError_t inverse_yz_grad(cplx<T>* A, cplx<T>* B, cplx<T>* scratch, T* const* out, int n, int batch, double kf,
+                            cudaStream_t st, const double* kf_arr) {
+    PM_DISPATCH_LOGN(n, (inverse_yz_grad_n<T, LG>(A, B, scratch, out, batch, kf, kf_arr, st)))
 }
 
 template <typename T>
@@ -542,6 +587,9 @@ cudaError_t x_cols(cplx<T>* data, cplx<T>* out2, int nplanes, int n, const SpecO
     template cudaError_t y_rows<T, true>(cplx<T>*, int64_t, int, cudaStream_t);                       \
     template cudaError_t y_rows_grad3<T>(cplx<T>*, cplx<T>*, cplx<T>*, int64_t, int, double,           \
                                          cudaStream_t, const double*, int64_t);                        \
-    template cudaError_t x_cols<T>(cplx<T>*, cplx<T>*, int, int, const SpecOp&, cudaStream_t);
+    template cudaError_t x_cols<T>(cplx<T>*, cplx<T>*, int, int, const SpecOp&, cudaStream_t);      \
+    template cudaError_t forward_zy<T>(const T*, cplx<T>*, int, int, cudaStream_t);                     \
+    template cudaError_t inverse_yz_grad<T>(cplx<T>*, cplx<T>*, cplx<T>*, T* const*, int, int, double,   \
+                                            cudaStream_t, const double*);
 
 }  // namespace pm

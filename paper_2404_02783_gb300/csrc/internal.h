@@ -67,5 +67,15 @@ cudaError_t y_rows_grad3(cplx<T>* A, cplx<T>* B, cplx<T>* C, int64_t nrows, int 
                          cudaStream_t st, const double* kf_arr = nullptr, int64_t rows_per_field = 0);
 template <typename T>
 cudaError_t x_cols(cplx<T>* data, cplx<T>* out2, int nplanes, int n, const SpecOp& op, cudaStream_t st);
+// Forward z (r2c) and y passes of `batch` real meshes into spec ([field][kz][kx][ky]
+// before the x pass).
+template <typename T>
+cudaError_t forward_zy(const T* in, cplx<T>* spec, int n, int batch, cudaStream_t st);
+// The three force meshes from phi and -i kx phi after the inverse x pass (A, B, full
+// layout; both overwritten): out[0] = c2r(IFFT_y(B)), out[1] = c2r(IFFT_y(-i ky A)),
+// out[2] = c2r(-i kz IFFT_y(A)); scratch holds one half spectrum per field.
+template <typename T>
+cudaError_t inverse_yz_grad(cplx<T>* A, cplx<T>* B, cplx<T>* scratch, T* const* out, int n, int batch, double kf,
+                            cudaStream_t st, const double* kf_arr = nullptr);
 
 }  // namespace pm
