@@ -16,6 +16,8 @@
 
 #include <math.h>
 
+#include <algorithm>
+
 #include "fft.cuh"
 #include "internal.h"
 
@@ -58,7 +60,9 @@ template <typename T, int LOGN> struct Shape {
     static constexpr int RB = (256 / QN > 0) ? 256 / QN : 1;     // y pass
     static constexpr int RB3 = (sizeof(T) == 8) ? ((128 / QN > 0) ? 128 / QN : 1) : RB;  // y grad3
     static constexpr int CB0 = (512 / QN < N) ? 512 / QN : N;
-    static constexpr int CB = (sizeof(T) == 8 && N >= 512) ? CB0 / 2 : CB0;  // x pass columns
+    // x pass columns (FP64 halves them from n = 64 so that the exchange buffers and the
+    // prefetch stage stay within 227 KB of shared memory)
+    static constexpr int CB = (sizeof(T) == 8 && N >= 64) ? CB0 / 2 : CB0;
 };
 
 // Row of (slab row gl relative to the chunk start, frequency kz) in a half spectrum whose
@@ -268,144 +272,194 @@ __global__ void __launch_bounds__(512) k_y_grad3(const cplx<T>* A, const cplx<T>
 }
 
 // =============================================================== x: strided columns + spectral operators
+// 16-byte asynchronous copy global -> shared (cp.async, completion by wait_group).
+__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gmem_src) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(gmem_src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+// Persistent: each CTA walks blocks blk = blockIdx.x, + gridDim.x, ... of CB columns of one
+// plane (plane = blk / (N / CB)).  The next block's columns are copied into a shared
+// stage with cp.async while the current block is transformed, so the loads of one block
+// overlap the butterflies and stores of the previous one.
 template <typename T, int LOGN, int KIND>
-__global__ void __launch_bounds__(512) k_x_cols(cplx<T>* __restrict__ data, cplx<T>* __restrict__ out2, SpecOp op) {
+__global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) k_x_cols(cplx<T>* __restrict__ data, cplx<T>* __restrict__ out2, SpecOp op,
+                                                int nplanes) {
     typedef cplx<T> C;
     typedef Shape<T, LOGN> S;
     constexpr int N = S::N, M = S::M, Q = S::QN, CB = S::CB;
     constexpr int CS = CB + 1;
+    constexpr int NCG = N / CB;                              // column groups per plane
+    constexpr int CHUNKS_ROW = CB * (int)sizeof(C) / 16;     // 16-byte chunks per row of a group
+    static_assert(CB * sizeof(C) % 16 == 0, "column groups of whole 16-byte chunks");
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* tw = reinterpret_cast<C*>(smem_raw);
     C* buf = tw + N;
-    double* acc = reinterpret_cast<double*>(buf + (size_t)2 * N * CS);
+    const bool cross = (KIND == OP_BIN) && op.in2 != nullptr;
+    C* stage = buf + (size_t)2 * N * CS;                     // [1 + cross][N][CB]: field (and in2)
+    double* acc = reinterpret_cast<double*>(stage + (size_t)(cross ? 2 : 1) * N * CB);
     const int tid = threadIdx.x;
     const int b = tid % CB, t = tid / CB;
-    const int plane = blockIdx.y;
-    const int kz = plane % (M + 1);
-    const int field = plane / (M + 1);
-    const double kf = op.kf_arr ? op.kf_arr[field] : op.kf;
-    const int c = blockIdx.x * CB + b;
-    const size_t pbase = (size_t)plane * N * N;
-    C* base = data + pbase;
-    const bool cross = (KIND == OP_BIN) && op.in2 != nullptr;
+    const int64_t nblk = (int64_t)nplanes * NCG;
     load_twiddles<T>(tw, N);
     if (KIND == OP_BIN)
         for (int e = tid; e < 3 * op.nbins; e += blockDim.x) acc[e] = 0.0;
-    C v[2][8];
+    auto issue = [&](int64_t blk) {
+        const size_t pb = (size_t)(blk / NCG) * N * N + (size_t)(blk % NCG) * CB;
+        for (int q = tid; q < N * CHUNKS_ROW; q += blockDim.x) {
+            const int r = q / CHUNKS_ROW, h = q % CHUNKS_ROW;
+            cp_async16(reinterpret_cast<char*>(stage + (size_t)r * CB) + 16 * h,
+                       reinterpret_cast<const char*>(data + pb + (size_t)r * N) + 16 * h);
+            if (cross)
+                cp_async16(reinterpret_cast<char*>(stage + (size_t)(N + r) * CB) + 16 * h,
+                           reinterpret_cast<const char*>(reinterpret_cast<const C*>(op.in2) + pb + (size_t)r * N) +
+                               16 * h);
+        }
+        cp_async_commit();
+    };
+    if ((int64_t)blockIdx.x < nblk) issue(blockIdx.x);
+#pragma unroll 1
+    for (int64_t blk = blockIdx.x; blk < nblk; blk += gridDim.x) {
+        const int plane = (int)(blk / NCG);
+        const int kz = plane % (M + 1);
+        const int field = plane / (M + 1);
+        const double kf = op.kf_arr ? op.kf_arr[field] : op.kf;
+        const int c = (int)(blk % NCG) * CB + b;
+        const size_t pbase = (size_t)plane * N * N;
+        C* base = data + pbase;
+        cp_async_wait_all();
+        __syncthreads();
+        C v[2][8];
 #pragma unroll
-    for (int m = 0; m < 8; ++m) v[0][m] = base[(size_t)(t + m * Q) * N + c];
-    if (cross) {
-        const C* b2 = reinterpret_cast<const C*>(op.in2) + pbase;
+        for (int m = 0; m < 8; ++m) v[0][m] = stage[(size_t)(t + m * Q) * CB + b];
+        if (cross) {
 #pragma unroll
-        for (int m = 0; m < 8; ++m) v[1][m] = b2[(size_t)(t + m * Q) * N + c];
-    }
-    __syncthreads();
-    ColEx<C, N> ex{buf, CS, b};
-    if (op.fwd) {
-        if (cross) fft_regs<N, 2, false>(v, t, tw, ex);
-        else fft_regs<N, 1, false>(v, t, tw, ex);
-    }
-    if constexpr (KIND == OP_FWD_STORE) {
+            for (int m = 0; m < 8; ++m) v[1][m] = stage[(size_t)(N + t + m * Q) * CB + b];
+        }
+        __syncthreads();  // the stage is free: fetch the next block while this one is transformed
+        if (blk + gridDim.x < nblk) issue(blk + gridDim.x);
+        ColEx<C, N> ex{buf, CS, b};
+        if (op.fwd) {
+            if (cross) fft_regs<N, 2, false>(v, t, tw, ex);
+            else fft_regs<N, 1, false>(v, t, tw, ex);
+        }
+        if constexpr (KIND == OP_FWD_STORE) {
 #pragma unroll
-        for (int m = 0; m < 8; ++m) base[(size_t)(t + m * Q) * N + c] = v[0][m];
-        return;
-    }
-    if constexpr (KIND == OP_INV) {
-        fft_regs<N, 1, true>(v, t, tw, ex);
+            for (int m = 0; m < 8; ++m) base[(size_t)(t + m * Q) * N + c] = v[0][m];
+            continue;
+        }
+        if constexpr (KIND == OP_INV) {
+            fft_regs<N, 1, true>(v, t, tw, ex);
 #pragma unroll
-        for (int m = 0; m < 8; ++m) base[(size_t)(t + m * Q) * N + c] = v[0][m];
-        return;
-    }
-    // ---- per-mode operator on modes (kx = t + m Q, ky = c, kz)
-    const int ny = (c < M) ? c : c - N;
-    const int nz = kz;
-    // per-CTA constants, formed once in the working precision (no FP64 work per mode in FP32)
-    const T kfT = T(kf);
-    const T coefT = T(op.coef) / (kfT * kfT);
-    const T kf2T = T(kf * kf);
-#pragma unroll
-    for (int m = 0; m < 8; ++m) {
-        const int i = t + m * Q;
-        const int nx = (i < M) ? i : i - N;
-        const int n2 = nx * nx + ny * ny + nz * nz;
-        const C vv = v[0][m];
-        if constexpr (KIND == OP_BIN) {
-            if (n2 == 0 || n2 > M * M) continue;
-            const int bin = op.bin_of[n2];
-            if (bin < 0) continue;
-            const double w = (nz == 0 || nz == M) ? 1.0 : 2.0;
-            double val;
-            if (cross) {
-                const C u = v[1][m];
-                val = (double)vv.x * (double)u.x + (double)vv.y * (double)u.y;
-            } else {
-                val = (double)vv.x * (double)vv.x + (double)vv.y * (double)vv.y;
-            }
-            if (op.deconv) {
-                const double W = op.wtab[nx < 0 ? -nx : nx] * op.wtab[ny < 0 ? -ny : ny] * op.wtab[nz];
-                val /= W * W;
-            }
-            atomicAdd(&acc[bin], w);
-            atomicAdd(&acc[op.nbins + bin], w * val);
-            atomicAdd(&acc[2 * op.nbins + bin], w * kf * sqrt((double)n2));
-        } else {
-            C phi;
-            if constexpr (KIND == OP_NEWTON || KIND == OP_POTENTIAL) {
-                phi = (n2 == 0) ? cmake<C>(T(0), T(0)) : cscale(vv, coefT / T(n2));
-            } else if constexpr (KIND == OP_ZA) {
-                const bool nyq = (2 * nx == -N) || (2 * ny == -N) || (nz == M);
-                const double* amp = op.amp + (int64_t)field * op.amp_stride;
-                phi = (n2 == 0 || nyq) ? cmake<C>(T(0), T(0))
-                                       : cscale(vv, T(op.coef / (kf * kf) * amp[n2] / (double)n2));
-            } else {  // OP_GR
-                if (n2 == 0) {
-                    phi = cmake<C>(T(0), T(0));
-                    if (op.n_lo > 0) {
-                        const int L = op.n_lo, W2 = 2 * L + 1;
-                        op.island[((size_t)nz * W2 + L) * W2 + L] = make_double2(0.0, 0.0);
-                    }
-                } else if (n2 <= op.n_lo * op.n_lo) {
-                    const int L = op.n_lo, W2 = 2 * L + 1;
-                    const size_t id = ((size_t)nz * W2 + (nx + L)) * W2 + (ny + L);
-                    const double k2 = kf * kf * (double)n2;
-                    const double H = op.calH;
-                    const double num_s = -1.5 * H * H * op.omm_a;
-                    double den = k2 + 3.0 * H * H + 4.5 * H * H * op.omm_a;
-                    double2 P = make_double2(num_s * (double)vv.x, num_s * (double)vv.y);
-                    if (!op.first) {
-                        const double2 old = op.island[id];
-                        const double cc = 3.0 * H * op.inv_dtau;
-                        P.x += cc * old.x;
-                        P.y += cc * old.y;
-                        den += cc;
-                    }
-                    P.x /= den;
-                    P.y /= den;
-                    op.island[id] = P;
-                    phi = cmake<C>(T(P.x * op.ac2_over_n3), T(P.y * op.ac2_over_n3));
+            for (int m = 0; m < 8; ++m) base[(size_t)(t + m * Q) * N + c] = v[0][m];
+            continue;
+        }
+        // ---- per-mode operator on modes (kx = t + m Q, ky = c, kz)
+        const int ny = (c < M) ? c : c - N;
+        const int nz = kz;
+        // per-CTA constants, formed once in the working precision (no FP64 work per mode in FP32)
+        const T kfT = T(kf);
+        const T coefT = T(op.coef) / (kfT * kfT);
+        const T kf2T = T(kf * kf);
+    #pragma unroll
+        for (int m = 0; m < 8; ++m) {
+            const int i = t + m * Q;
+            const int nx = (i < M) ? i : i - N;
+            const int n2 = nx * nx + ny * ny + nz * nz;
+            const C vv = v[0][m];
+            if constexpr (KIND == OP_BIN) {
+                if (n2 == 0 || n2 > M * M) continue;
+                const int bin = op.bin_of[n2];
+                if (bin < 0) continue;
+                const double w = (nz == 0 || nz == M) ? 1.0 : 2.0;
+                double val;
+                if (cross) {
+                    const C u = v[1][m];
+                    val = (double)vv.x * (double)u.x + (double)vv.y * (double)u.y;
                 } else {
-                    C* old = reinterpret_cast<C*>(op.phi_old) + pbase + (size_t)i * N + c;
-                    const T k2 = kf2T * T(n2);
-                    const T H = T(op.calH), om = T(op.omm_a);
-                    const T num_s = T(-1.5) * H * H * om;
-                    T den = k2 + T(3) * H * H + T(4.5) * H * H * om;
-                    C Pc = cscale(vv, num_s);
-                    if (!op.first) {
-                        const T cc = T(3) * H * T(op.inv_dtau);
-                        const C o = *old;
-                        Pc.x += cc * o.x;
-                        Pc.y += cc * o.y;
-                        den += cc;
+                    val = (double)vv.x * (double)vv.x + (double)vv.y * (double)vv.y;
+                }
+                if (op.deconv) {
+                    const double W = op.wtab[nx < 0 ? -nx : nx] * op.wtab[ny < 0 ? -ny : ny] * op.wtab[nz];
+                    val /= W * W;
+                }
+                atomicAdd(&acc[bin], w);
+                atomicAdd(&acc[op.nbins + bin], w * val);
+                atomicAdd(&acc[2 * op.nbins + bin], w * kf * sqrt((double)n2));
+            } else {
+                C phi;
+                if constexpr (KIND == OP_NEWTON || KIND == OP_POTENTIAL) {
+                    phi = (n2 == 0) ? cmake<C>(T(0), T(0)) : cscale(vv, coefT / T(n2));
+                } else if constexpr (KIND == OP_ZA) {
+                    const bool nyq = (2 * nx == -N) || (2 * ny == -N) || (nz == M);
+                    const double* amp = op.amp + (int64_t)field * op.amp_stride;
+                    phi = (n2 == 0 || nyq) ? cmake<C>(T(0), T(0))
+                                           : cscale(vv, T(op.coef / (kf * kf) * amp[n2] / (double)n2));
+                } else {  // OP_GR
+                    if (n2 == 0) {
+                        phi = cmake<C>(T(0), T(0));
+                        if (op.n_lo > 0) {
+                            const int L = op.n_lo, W2 = 2 * L + 1;
+                            op.island[((size_t)nz * W2 + L) * W2 + L] = make_double2(0.0, 0.0);
+                        }
+                    } else if (n2 <= op.n_lo * op.n_lo) {
+                        const int L = op.n_lo, W2 = 2 * L + 1;
+                        const size_t id = ((size_t)nz * W2 + (nx + L)) * W2 + (ny + L);
+                        const double k2 = kf * kf * (double)n2;
+                        const double H = op.calH;
+                        const double num_s = -1.5 * H * H * op.omm_a;
+                        double den = k2 + 3.0 * H * H + 4.5 * H * H * op.omm_a;
+                        double2 P = make_double2(num_s * (double)vv.x, num_s * (double)vv.y);
+                        if (!op.first) {
+                            const double2 old = op.island[id];
+                            const double cc = 3.0 * H * op.inv_dtau;
+                            P.x += cc * old.x;
+                            P.y += cc * old.y;
+                            den += cc;
+                        }
+                        P.x /= den;
+                        P.y /= den;
+                        op.island[id] = P;
+                        phi = cmake<C>(T(P.x * op.ac2_over_n3), T(P.y * op.ac2_over_n3));
+                    } else {
+                        C* old = reinterpret_cast<C*>(op.phi_old) + pbase + (size_t)i * N + c;
+                        const T k2 = kf2T * T(n2);
+                        const T H = T(op.calH), om = T(op.omm_a);
+                        const T num_s = T(-1.5) * H * H * om;
+                        T den = k2 + T(3) * H * H + T(4.5) * H * H * om;
+                        C Pc = cscale(vv, num_s);
+                        if (!op.first) {
+                            const T cc = T(3) * H * T(op.inv_dtau);
+                            const C o = *old;
+                            Pc.x += cc * o.x;
+                            Pc.y += cc * o.y;
+                            den += cc;
+                        }
+                        Pc = cscale(Pc, T(1) / den);
+                        *old = Pc;
+                        phi = cscale(Pc, T(op.ac2_over_n3));
                     }
-                    Pc = cscale(Pc, T(1) / den);
-                    *old = Pc;
-                    phi = cscale(Pc, T(op.ac2_over_n3));
+                }
+                v[0][m] = phi;
+                if constexpr (KIND != OP_POTENTIAL) {
+                    const T kx = (2 * nx == -N) ? T(0) : kfT * T(nx);
+                    v[1][m] = cmake<C>(phi.y * kx, -phi.x * kx);  // -i kx phi
                 }
             }
-            v[0][m] = phi;
-            if constexpr (KIND != OP_POTENTIAL) {
-                const T kx = (2 * nx == -N) ? T(0) : kfT * T(nx);
-                v[1][m] = cmake<C>(phi.y * kx, -phi.x * kx);  // -i kx phi
+        }
+        if constexpr (KIND == OP_BIN) continue;
+        if constexpr (KIND == OP_POTENTIAL) {
+            fft_regs<N, 1, true>(v, t, tw, ex);
+    #pragma unroll
+            for (int m = 0; m < 8; ++m) base[(size_t)(t + m * Q) * N + c] = v[0][m];
+        } else {
+            fft_regs<N, 2, true>(v, t, tw, ex);
+    #pragma unroll
+            for (int m = 0; m < 8; ++m) {
+                base[(size_t)(t + m * Q) * N + c] = v[0][m];
+                out2[pbase + (size_t)(t + m * Q) * N + c] = v[1][m];
             }
         }
     }
@@ -413,19 +467,6 @@ __global__ void __launch_bounds__(512) k_x_cols(cplx<T>* __restrict__ data, cplx
         __syncthreads();
         for (int e = tid; e < 3 * op.nbins; e += blockDim.x)
             if (acc[e] != 0.0) atomicAdd(&op.acc[e], acc[e]);
-        return;
-    }
-    if constexpr (KIND == OP_POTENTIAL) {
-        fft_regs<N, 1, true>(v, t, tw, ex);
-#pragma unroll
-        for (int m = 0; m < 8; ++m) base[(size_t)(t + m * Q) * N + c] = v[0][m];
-    } else {
-        fft_regs<N, 2, true>(v, t, tw, ex);
-#pragma unroll
-        for (int m = 0; m < 8; ++m) {
-            base[(size_t)(t + m * Q) * N + c] = v[0][m];
-            out2[pbase + (size_t)(t + m * Q) * N + c] = v[1][m];
-        }
     }
 }
 
@@ -503,10 +544,18 @@ cudaError_t inverse_yz_grad_n(cplx<T>* A, cplx<T>* B, cplx<T>* scratch, T* const
 template <typename T, int LOGN, int KIND>
 cudaError_t x_cols_n(cplx<T>* data, cplx<T>* out2, int nplanes, const SpecOp& op, cudaStream_t st) {
     typedef Shape<T, LOGN> S;
-    const size_t smem = sizeof(cplx<T>) * (S::N + 2 * (size_t)S::N * (S::CB + 1)) + sizeof(double) * 3 * op.nbins;
-    cudaError_t e = set_smem((const void*)k_x_cols<T, LOGN, KIND>, smem);
+    const int nstage = (KIND == OP_BIN && op.in2 != nullptr) ? 2 : 1;
+    const size_t smem = sizeof(cplx<T>) * (S::N + 2 * (size_t)S::N * (S::CB + 1) + nstage * (size_t)S::N * S::CB) +
+                        sizeof(double) * 3 * op.nbins;
+    const void* fn = (const void*)k_x_cols<T, LOGN, KIND>;
+    cudaError_t e = set_smem(fn, smem);
     if (e != cudaSuccess) return e;
-    k_x_cols<T, LOGN, KIND><<<dim3(S::N / S::CB, nplanes), S::CB * S::QN, smem, st>>>(data, out2, op);
+    int per_sm = 1;
+    e = resident_ctas(fn, S::CB * S::QN, smem, &per_sm);
+    if (e != cudaSuccess) return e;
+    const int64_t nblk = (int64_t)nplanes * (S::N / S::CB);
+    const int64_t grid = std::min<int64_t>(nblk, (int64_t)per_sm * num_sms());
+    k_x_cols<T, LOGN, KIND><<<(unsigned)grid, S::CB * S::QN, smem, st>>>(data, out2, op, nplanes);
     return cudaGetLastError();
 }
 

@@ -47,8 +47,13 @@ struct SpecOp {
 // Uploads the twiddle tables exp(-2 pi i k / 1024) of both precisions to the current
 // device (once per device).
 cudaError_t ensure_device_tables();
-// cudaFuncSetAttribute(MaxDynamicSharedMemorySize) once per (kernel, device, size).
+// Raises cudaFuncAttributeMaxDynamicSharedMemorySize of fn on the current device to at least
+// bytes (monotone per kernel and device; only calls the runtime when it must grow).
 cudaError_t set_smem_once(const void* fn, size_t bytes);
+// CTAs of fn resident per SM for the launch shape (occupancy query, cached per device),
+// and the device's SM count (cached): the grid of persistent kernels.
+cudaError_t resident_ctas(const void* fn, int threads, size_t smem, int* per_sm);
+int num_sms();
 
 // FFT passes.  n is the transform length (power of two, 16..1024); batch counts
 // independent 3D fields stored back to back.
