@@ -11,8 +11,9 @@
 // threads touch consecutive elements, so callers stream them to and from global
 // memory directly.  Only the exchanges between stages use shared memory.
 //
-// Twiddles come from a shared table tw[k] = exp(-2 pi i k / L) (host FP64,
-// rounded once); INV conjugates them (unnormalised inverse).
+// Twiddles come from a shared per-stage table (tw_stage_offset; values from the host
+// FP64 table exp(-2 pi i k / 1024), rounded once); INV conjugates them (unnormalised
+// inverse).
 #pragma once
 
 #include "pm_common.cuh"
@@ -83,6 +84,15 @@ __device__ __forceinline__ C twid(const C* tw, int e) {
 __host__ __device__ constexpr int radix_at(int L, int Ns) { return (L / Ns) >= 8 ? 8 : (L / Ns); }
 __host__ __device__ constexpr int last_radix(int L, int Ns = 1) { return (Ns * radix_at(L, Ns) >= L) ? radix_at(L, Ns) : last_radix(L, Ns * radix_at(L, Ns)); }
 
+// Per-stage twiddle table: the stage with span Ns > 1 and radix R keeps
+// w(r, jm) = exp(-2 pi i jm r / (Ns R)) at [offset(Ns) + (r - 1) Ns + jm], r = 1..R-1,
+// jm = 0..Ns-1, so the lanes of a warp (consecutive jm) read consecutive entries.  The
+// table of a length-L transform holds L - radix_at(L, 1) < L entries.
+__host__ __device__ constexpr int tw_stage_offset(int L, int Ns, int s = 1, int off = 0) {
+    return (s >= Ns) ? off : tw_stage_offset(L, Ns, s * radix_at(L, s), off + (s > 1 ? (radix_at(L, s) - 1) * s : 0));
+}
+__host__ __device__ constexpr int tw_stage_entries(int L) { return tw_stage_offset(L, L); }
+
 // ---------------------------------------------------------------- exchangers
 // Rows: sequence s of row b at base[((p NSEQ + s) RB + b) RS + spad(i)]; two
 // buffers alternate (p) when PP, so one barrier per exchange suffices.
@@ -118,15 +128,15 @@ __device__ __forceinline__ void fft_stages(C (*v)[8], int t, const C* __restrict
     constexpr int R = radix_at(L, Ns);
     constexpr int NB = 8 / R;
     constexpr int Q = L / 8;
-    constexpr int TWS = L / (Ns * R);
 #pragma unroll
     for (int s = 0; s < NSEQ; ++s)
 #pragma unroll
         for (int q = 0; q < NB; ++q) {
             if constexpr (Ns > 1) {
                 const int jm = (t + q * Q) & (Ns - 1);
+                const C* tws = tw + tw_stage_offset(L, Ns) + jm;
 #pragma unroll
-                for (int r = 1; r < R; ++r) v[s][q * R + r] = cmul(v[s][q * R + r], twid<INV>(tw, jm * r * TWS));
+                for (int r = 1; r < R; ++r) v[s][q * R + r] = cmul(v[s][q * R + r], twid<INV>(tws, (r - 1) * Ns));
             }
             dftR<R, INV>(&v[s][q * R]);
         }

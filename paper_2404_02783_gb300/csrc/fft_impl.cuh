@@ -26,10 +26,20 @@ namespace pm {
 template <typename T> __device__ __forceinline__ cplx<T> tw_global(int k);
 cudaError_t set_smem_once(const void* fn, size_t bytes);
 
-template <typename T>
-__device__ __forceinline__ void load_twiddles(cplx<T>* tw, int L) {
-    const int stride = 1024 / L;
-    for (int k = threadIdx.x; k < L; k += blockDim.x) tw[k] = tw_global<T>(k * stride);
+// The per-stage twiddle table of a length-L transform (layout: fft.cuh, tw_stage_offset).
+template <typename T, int L>
+__device__ __forceinline__ void load_stage_twiddles(cplx<T>* tw) {
+    constexpr int TE = tw_stage_entries(L);
+    for (int k = threadIdx.x; k < TE; k += blockDim.x) {
+        int Ns = radix_at(L, 1), off = 0;  // stages with span Ns > 1, in order
+        while (k >= off + (radix_at(L, Ns) - 1) * Ns) {
+            off += (radix_at(L, Ns) - 1) * Ns;
+            Ns *= radix_at(L, Ns);
+        }
+        const int R = radix_at(L, Ns);
+        const int r = (k - off) / Ns + 1, jm = (k - off) % Ns;
+        tw[k] = tw_global<T>(jm * r * (1024 / (Ns * R)));
+    }
 }
 
 // First `count` entries of the length-L table.
@@ -88,7 +98,7 @@ __global__ void __launch_bounds__(512) k_z_r2c(const T* __restrict__ in, cplx<T>
     const int y0 = blockIdx.x * YB;
     const int gl = blockIdx.y;
     const size_t g = (size_t)g0 + gl;
-    load_twiddles<T>(twM, M);
+    load_stage_twiddles<T, M>(twM);
     load_twiddles_head<T>(twN, N, M + 1);
     const int b = tid / Q, t = tid % Q;
     const C* row = reinterpret_cast<const C*>(in + (g * N + y0 + b) * N);
@@ -141,7 +151,7 @@ __global__ void __launch_bounds__(512) k_z_c2r(Ptr3<T> P, unsigned gradz_mask, T
     const int y0 = blockIdx.x * YB;
     const int gl = blockIdx.y;
     const size_t g = (size_t)g0 + gl;
-    load_twiddles<T>(twM, M);
+    load_stage_twiddles<T, M>(twM);
     load_twiddles_head<T>(twN, N, M + 1);
     const T kf = kf_arr ? T(kf_arr[g >> LOGN]) : kf0;
     const C* inp = comp == 0 ? P.in[0] : (comp == 1 ? P.in[1] : P.in[2]);
@@ -208,7 +218,7 @@ __global__ void __launch_bounds__(512) k_y_rows(const cplx<T>* in, cplx<T>* out,
     const int b = tid / Q, t = tid % Q;
     const int64_t r = (int64_t)blockIdx.x * RB + b;
     const bool ok = r < nrows;
-    load_twiddles<T>(tw, N);
+    load_stage_twiddles<T, N>(tw);
     C v[1][8];
     const C* irow = in + r * N;
     if (ok) {
@@ -243,7 +253,7 @@ __global__ void __launch_bounds__(512) k_y_grad3(const cplx<T>* A, const cplx<T>
     const bool ok = r < nrows;
     const int64_t ri = r;
     const T kf = (kf_arr && ok) ? T(kf_arr[r / rows_per_field]) : kf0;
-    load_twiddles<T>(tw, N);
+    load_stage_twiddles<T, N>(tw);
     C v[3][8];
     if (ok) {
 #pragma unroll
@@ -303,7 +313,7 @@ __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) k_x_cols(cplx<T>*
     const int tid = threadIdx.x;
     const int b = tid % CB, t = tid / CB;
     const int64_t nblk = (int64_t)nplanes * NCG;
-    load_twiddles<T>(tw, N);
+    load_stage_twiddles<T, N>(tw);
     if (KIND == OP_BIN)
         for (int e = tid; e < 3 * op.nbins; e += blockDim.x) acc[e] = 0.0;
     auto issue = [&](int64_t blk) {
