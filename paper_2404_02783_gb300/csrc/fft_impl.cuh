@@ -254,30 +254,38 @@ __global__ void __launch_bounds__(512) k_y_grad3(const cplx<T>* A, const cplx<T>
     const int64_t ri = r;
     const T kf = (kf_arr && ok) ? T(kf_arr[r / rows_per_field]) : kf0;
     load_stage_twiddles<T, N>(tw);
-    C v[3][8];
+    // two rounds keep two sequences live at a time: (A, -i ky A), then B
+    C v[2][8];
     if (ok) {
 #pragma unroll
         for (int m = 0; m < 8; ++m) {
             const int i = t + m * Q;
             const C a = A[ri * N + i];
             v[0][m] = a;
-            v[1][m] = B[ri * N + i];
             const int ny = (i < N / 2) ? i : i - N;
             const T ky = (2 * ny == -N) ? T(0) : kf * T(ny);
-            v[2][m] = cmake<C>(a.y * ky, -a.x * ky);
+            v[1][m] = cmake<C>(a.y * ky, -a.x * ky);
         }
     }
     __syncthreads();
-    RowEx<C, 3, false> ex{buf, RB, RS, b, 0};
-    fft_regs<N, 3, true>(v, t, tw, ex);
+    RowEx<C, 2, false> ex{buf, RB, RS, b, 0};
+    fft_regs<N, 2, true>(v, t, tw, ex);
     if (ok) {
 #pragma unroll
         for (int m = 0; m < 8; ++m) {
             const int i = t + m * Q;
             Aout[r * N + i] = v[0][m];
-            Bout[r * N + i] = v[1][m];
-            Cout[r * N + i] = v[2][m];
+            Cout[r * N + i] = v[1][m];
         }
+        // Bout may alias B, never A: the rows of A written above are not read again
+#pragma unroll
+        for (int m = 0; m < 8; ++m) v[0][m] = B[ri * N + t + m * Q];
+    }
+    RowEx<C, 1, false> ex1{buf, RB, RS, b, 0};
+    fft_regs<N, 1, true>(v, t, tw, ex1);
+    if (ok) {
+#pragma unroll
+        for (int m = 0; m < 8; ++m) Bout[r * N + t + m * Q] = v[0][m];
     }
 }
 
@@ -517,7 +525,7 @@ template <typename T, int LOGN>
 cudaError_t y_grad3_n(const cplx<T>* A, const cplx<T>* B, cplx<T>* Ao, cplx<T>* Bo, cplx<T>* Co, int64_t nrows, double kf,
                       cudaStream_t st, const double* kf_arr, int64_t rows_per_field) {
     typedef Shape<T, LOGN> S;
-    const size_t smem = sizeof(cplx<T>) * (S::N + 3 * (size_t)S::RB3 * row_stride(S::N));
+    const size_t smem = sizeof(cplx<T>) * (S::N + 2 * (size_t)S::RB3 * row_stride(S::N));
     cudaError_t e = set_smem((const void*)k_y_grad3<T, LOGN>, smem);
     if (e != cudaSuccess) return e;
     const int64_t nblk = (nrows + S::RB3 - 1) / S::RB3;
