@@ -84,29 +84,144 @@ __global__ void k_adj_direct(const uint32_t* __restrict__ x, int64_t count, int 
     }
 }
 
-// V_j(c) += sum_p v_j W(u_p, c) for the three components
-__global__ void k_deposit_vec(const uint32_t* __restrict__ x, int64_t count, int logn, float inv_cell_ticks,
-                              const float* __restrict__ v, float* __restrict__ V0, float* __restrict__ V1,
-                              float* __restrict__ V2) {
-    const size_t n = (size_t)1 << logn;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x) {
-        const Cic1 cx = decode(x[i], logn, inv_cell_ticks), cy = decode(x[count + i], logn, inv_cell_ticks),
-                   cz = decode(x[2 * count + i], logn, inv_cell_ticks);
-        const float vv[3] = {v[i], v[count + i], v[2 * count + i]};
-        const int ix[2] = {cx.i0, cx.i1}, iy[2] = {cy.i0, cy.i1}, iz[2] = {cz.i0, cz.i1};
+// The particle side of the transposed kick at positions x (one pass, the next particle's
+// inputs loaded one iteration ahead):
+//   lam_u += K sum_j v_j grad_u interp(G_j) + K mass grad_u interp(rho_bar)
+// followed, when drift_next != 0, by the transposed drift of the step before,
+//   v += drift_next lam_u   (v = lam_p, updated in place).
+__global__ void __launch_bounds__(256) k_adj_kick(const uint32_t* __restrict__ x, int64_t count, int logn,
+                                                  float inv_cell_ticks, float* __restrict__ v,
+                                                  const float* __restrict__ G0, const float* __restrict__ G1,
+                                                  const float* __restrict__ G2, const float* __restrict__ rho_bar,
+                                                  float K, float Km, float drift_next, float* __restrict__ lam_u) {
+    const float nf = (float)(1 << logn);
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    uint32_t nx0 = 0, nx1 = 0, nx2 = 0;
+    float nv0 = 0.f, nv1 = 0.f, nv2 = 0.f;
+    if (i < count) {
+        nx0 = x[i], nx1 = x[count + i], nx2 = x[2 * count + i];
+        nv0 = v[i], nv1 = v[count + i], nv2 = v[2 * count + i];
+    }
+    for (; i < count; i += stride) {
+        const uint32_t u0 = nx0, u1 = nx1, u2 = nx2;
+        const float v0 = nv0, v1 = nv1, v2 = nv2;
+        if (i + stride < count) {
+            const int64_t j = i + stride;
+            nx0 = x[j], nx1 = x[count + j], nx2 = x[2 * count + j];
+            nv0 = v[j], nv1 = v[count + j], nv2 = v[2 * count + j];
+        }
+        const Cic1 cx = decode(u0, logn, inv_cell_ticks), cy = decode(u1, logn, inv_cell_ticks),
+                   cz = decode(u2, logn, inv_cell_ticks);
+        const uint32_t ix[2] = {(uint32_t)cx.i0, (uint32_t)cx.i1}, iy[2] = {(uint32_t)cy.i0, (uint32_t)cy.i1},
+                       iz[2] = {(uint32_t)cz.i0, (uint32_t)cz.i1};
         const float wx[2] = {1.0f - cx.w1, cx.w1}, wy[2] = {1.0f - cy.w1, cy.w1}, wz[2] = {1.0f - cz.w1, cz.w1};
+        const float dw[2] = {-nf, nf};
+        float g0 = 0.f, g1 = 0.f, g2 = 0.f;
 #pragma unroll
         for (int a = 0; a < 2; ++a)
 #pragma unroll
             for (int b = 0; b < 2; ++b)
 #pragma unroll
                 for (int c = 0; c < 2; ++c) {
-                    const float w = wx[a] * wy[b] * wz[c];
-                    const size_t id = ((size_t)ix[a] * n + iy[b]) * n + iz[c];
-                    atomicAdd(V0 + id, w * vv[0]);
-                    atomicAdd(V1 + id, w * vv[1]);
-                    atomicAdd(V2 + id, w * vv[2]);
+                    const uint32_t o = (((ix[a] << logn) + iy[b]) << logn) + iz[c];
+                    // K sum_j v_j G_j + K mass rho_bar at the corner
+                    const float s = K * (v0 * __ldg(G0 + o) + v1 * __ldg(G1 + o) + v2 * __ldg(G2 + o)) +
+                                    Km * __ldg(rho_bar + o);
+                    g0 = fmaf(dw[a] * wy[b] * wz[c], s, g0);
+                    g1 = fmaf(wx[a] * dw[b] * wz[c], s, g1);
+                    g2 = fmaf(wx[a] * wy[b] * dw[c], s, g2);
                 }
+        const float l0 = lam_u[i] + g0, l1 = lam_u[count + i] + g1, l2 = lam_u[2 * count + i] + g2;
+        lam_u[i] = l0;
+        lam_u[count + i] = l1;
+        lam_u[2 * count + i] = l2;
+        if (drift_next != 0.f) {
+            v[i] = fmaf(drift_next, l0, v0);
+            v[count + i] = fmaf(drift_next, l1, v1);
+            v[2 * count + i] = fmaf(drift_next, l2, v2);
+        }
+    }
+}
+
+// V_j(c) += sum_p v_j W(u_p, c) for the three components, particles in lattice order
+// (id = (ix np + iy) np + iz) walked along x in runs of RUN (thread = (iz, iy, run); the
+// next particle is loaded one iteration ahead).  With MERGE (lattice as fine as the mesh)
+// the next particle along x usually starts one cell further in x, so its lower-x corners
+// are the current upper-x corners: those 12 weighted values are carried in registers and
+// added with the next particle's (12 atomics a particle instead of 24).
+template <bool MERGE>
+__global__ void __launch_bounds__(256) k_deposit_vec_rows(const uint32_t* __restrict__ x, int lognp, int logn,
+                                                          int run, float inv_cell_ticks, const float* __restrict__ v,
+                                                          float* __restrict__ V0, float* __restrict__ V1,
+                                                          float* __restrict__ V2) {
+    const int np = 1 << lognp;
+    const int64_t count = (int64_t)1 << (3 * lognp);
+    const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int lz = (int)(gid & (np - 1)), ly = (int)((gid >> lognp) & (np - 1));
+    const int lx0 = (int)(gid >> (2 * lognp)) * run;
+    if (lx0 >= np) return;
+    const int64_t xstride = (int64_t)1 << (2 * lognp);
+    const int64_t id0 = (((int64_t)lx0 << lognp) + ly) * np + lz;
+    uint32_t nu0 = x[id0], nu1 = x[count + id0], nu2 = x[2 * count + id0];
+    float nv0 = v[id0], nv1 = v[count + id0], nv2 = v[2 * count + id0];
+    uint32_t carry_cell = 0xffffffffu, carry_o[4] = {0u, 0u, 0u, 0u};
+    float carry[4][3];
+    auto add3 = [&](uint32_t o, float a, float b, float c) {
+        atomicAdd(V0 + o, a);
+        atomicAdd(V1 + o, b);
+        atomicAdd(V2 + o, c);
+    };
+#pragma unroll 1
+    for (int k = 0; k < run; ++k) {
+        const int64_t id = id0 + k * xstride;
+        const uint32_t u0 = nu0, u1 = nu1, u2 = nu2;
+        const float v0 = nv0, v1 = nv1, v2 = nv2;
+        if (k + 1 < run) {
+            const int64_t j = id + xstride;
+            nu0 = x[j], nu1 = x[count + j], nu2 = x[2 * count + j];
+            nv0 = v[j], nv1 = v[count + j], nv2 = v[2 * count + j];
+        }
+        const Cic1 cx = decode(u0, logn, inv_cell_ticks), cy = decode(u1, logn, inv_cell_ticks),
+                   cz = decode(u2, logn, inv_cell_ticks);
+        const uint32_t iy[2] = {(uint32_t)cy.i0, (uint32_t)cy.i1}, iz[2] = {(uint32_t)cz.i0, (uint32_t)cz.i1};
+        const float wx0 = 1.0f - cx.w1, wx1 = cx.w1;
+        const float wy[2] = {1.0f - cy.w1, cy.w1}, wz[2] = {1.0f - cz.w1, cz.w1};
+        const uint32_t cell = ((((uint32_t)cx.i0 << logn) | iy[0]) << logn) | iz[0];
+        const bool merge = MERGE && cell == carry_cell;
+        if (MERGE && !merge && carry_cell != 0xffffffffu) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) add3(carry_o[q], carry[q][0], carry[q][1], carry[q][2]);
+        }
+#pragma unroll
+        for (int b = 0; b < 2; ++b)
+#pragma unroll
+            for (int c = 0; c < 2; ++c) {
+                const int q = 2 * b + c;
+                const float w = wy[b] * wz[c];
+                const uint32_t o0 = ((((uint32_t)cx.i0 << logn) + iy[b]) << logn) + iz[c];
+                const uint32_t o1 = ((((uint32_t)cx.i1 << logn) + iy[b]) << logn) + iz[c];
+                float a0 = wx0 * w * v0, a1 = wx0 * w * v1, a2 = wx0 * w * v2;
+                if (merge) {
+                    a0 += carry[q][0];
+                    a1 += carry[q][1];
+                    a2 += carry[q][2];
+                }
+                add3(o0, a0, a1, a2);
+                if (MERGE) {
+                    carry[q][0] = wx1 * w * v0;
+                    carry[q][1] = wx1 * w * v1;
+                    carry[q][2] = wx1 * w * v2;
+                    carry_o[q] = o1;
+                } else {
+                    add3(o1, wx1 * w * v0, wx1 * w * v1, wx1 * w * v2);
+                }
+            }
+        if (MERGE) carry_cell = ((((uint32_t)cx.i1 << logn) | iy[0]) << logn) | iz[0];
+    }
+    if (MERGE && carry_cell != 0xffffffffu) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) add3(carry_o[q], carry[q][0], carry[q][1], carry[q][2]);
     }
 }
 
@@ -119,6 +234,7 @@ __global__ void k_adj_combine(const float2* __restrict__ in0, const float2* __re
                               const double* __restrict__ amp, int mode) {
     const int M = n / 2;
     const int64_t total = (int64_t)(M + 1) * n * n;
+    const float kff = (float)kf, kf2 = kff * kff, coef_f = (float)coef;
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
         const int kz = (int)(e / ((int64_t)n * n));
         const int rem = (int)(e - (int64_t)kz * n * n);
@@ -127,16 +243,17 @@ __global__ void k_adj_combine(const float2* __restrict__ in0, const float2* __re
         float2 r = make_float2(0.f, 0.f);
         const bool nyq_any = (2 * nx == -n) || (2 * ny == -n) || (nz == M);
         if (n2 > 0 && !(mode == 1 && nyq_any)) {
-            double c = coef / (kf * kf * (double)n2);
-            if (mode == 1) c *= amp[n2];
-            const float kx = (2 * nx == -n) ? 0.f : (float)(kf * nx);
-            const float ky = (2 * ny == -n) ? 0.f : (float)(kf * ny);
-            const float kzz = (nz == M) ? 0.f : (float)(kf * nz);
+            // FP32 arithmetic (no FP64 divide per mode): c = coef / (kf^2 n2) [* amp(n2)]
+            float c = coef_f / (kf2 * (float)n2);
+            if (mode == 1) c *= (float)amp[n2];
+            const float kx = (2 * nx == -n) ? 0.f : kff * (float)nx;
+            const float ky = (2 * ny == -n) ? 0.f : kff * (float)ny;
+            const float kzz = (nz == M) ? 0.f : kff * (float)nz;
             const float2 a = in0[e], b = in1[e], d = in2[e];
             // i k_j c z = c k_j (-z.y, z.x)
             const float sx = kx * a.x + ky * b.x + kzz * d.x;
             const float sy = kx * a.y + ky * b.y + kzz * d.y;
-            r = make_float2((float)(-c * sy), (float)(c * sx));
+            r = make_float2(-c * sy, c * sx);
         }
         out[e] = r;
     }
@@ -184,10 +301,25 @@ cudaError_t adj_direct(const uint32_t* x, int64_t count, int n, const float* v, 
     return cudaGetLastError();
 }
 
-cudaError_t deposit_vec(const uint32_t* x, int64_t count, int n, const float* v, float* const* V, cudaStream_t st) {
+cudaError_t adj_kick_particles(const uint32_t* x, int64_t count, int n, float* v, const float* const* G,
+                               const float* rho_bar, float K, float Km, float drift_next, float* lam_u,
+                               cudaStream_t st) {
     const int logn = ilog2(n);
-    k_deposit_vec<<<blocks_for(count), 256, 0, st>>>(x, count, logn, (float)ldexp(1.0, -(32 - logn)), v, V[0], V[1],
-                                                     V[2]);
+    k_adj_kick<<<blocks_for(count), 256, 0, st>>>(x, count, logn, (float)ldexp(1.0, -(32 - logn)), v, G[0], G[1], G[2],
+                                                  rho_bar, K, Km, drift_next, lam_u);
+    return cudaGetLastError();
+}
+
+cudaError_t deposit_vec(const uint32_t* x, int np, int n, const float* v, float* const* V, cudaStream_t st) {
+    const int lognp = ilog2(np), logn = ilog2(n);
+    const int run = np < 16 ? np : 16;
+    const int64_t threads = (int64_t)np * np * (np / run);
+    const unsigned blocks = (unsigned)((threads + 255) / 256);
+    const float inv = (float)ldexp(1.0, -(32 - logn));
+    if (n == np)
+        k_deposit_vec_rows<true><<<blocks, 256, 0, st>>>(x, lognp, logn, run, inv, v, V[0], V[1], V[2]);
+    else
+        k_deposit_vec_rows<false><<<blocks, 256, 0, st>>>(x, lognp, logn, run, inv, v, V[0], V[1], V[2]);
     return cudaGetLastError();
 }
 

@@ -124,6 +124,10 @@ struct pm_ctx {
     // rho holds the counting density of the current positions (left by the fused
     // kick-drift-deposit pass of the previous step)
     bool rho_valid = false;
+    // when set, the force meshes of the step (three n^3 meshes back to back) live here
+    // instead of L.force (the gradient's forward re-run writes them straight into its record)
+    void* force_at = nullptr;
+    void* force(int j) { return force_at ? (void*)((char*)force_at + (size_t)j * n * n * n * sT()) : at(L.force[j]); }
     // per-phase timing (pm_profile / pm_timings)
     bool prof = false;
     std::vector<cudaEvent_t> pool;
@@ -236,7 +240,7 @@ pm_status compute_forces_t(pm_ctx* c, double a) {
     }
     {
         Phase ph(c, PM_PHASE_FFT_YZ_INV);
-        T* out[3] = {(T*)c->at(c->L.force[0]), (T*)c->at(c->L.force[1]), (T*)c->at(c->L.force[2])};
+        T* out[3] = {(T*)c->force(0), (T*)c->force(1), (T*)c->force(2)};
         PM_CK(inverse_yz_grad<T>(s0, s1, s2, out, n, 1, c->kf, c->st));
     }
     if (c->cfg.mode == PM_GR_POISSON) {
@@ -252,7 +256,7 @@ pm_status compute_forces(pm_ctx* c, double a) {
 
 pm_status kick_drift(pm_ctx* c, double kick, double drift) {
     Phase ph(c, PM_PHASE_KICK_DRIFT);
-    void* g[3] = {c->at(c->L.force[0]), c->at(c->L.force[1]), c->at(c->L.force[2])};
+    void* g[3] = {c->force(0), c->force(1), c->force(2)};
     if (fused_update(c)) {
         PM_CK(interp_kick_drift_deposit(c->at(c->L.x), c->at(c->L.p), c->np, c->cfg.precision, c->n, g, kick, drift,
                                         c->cfg.box, std::pow((double)c->n / c->np, 3), c->at(c->L.rho), c->st));
@@ -803,8 +807,8 @@ AdjLayout adj_plan(const pm_ctx* c, int C) {
         return o;
     };
     A.ckpt = take((size_t)A.nseg * 2 * P);
-    A.seg_x = take((size_t)(C + 1) * P);
-    A.seg_g = take((size_t)(C + 1) * G);
+    A.seg_x = take((size_t)C * P);
+    A.seg_g = take((size_t)C * G);
     A.lam_u = take(P);
     A.lam_p = take(P);
     A.acc = take(8);
@@ -836,24 +840,31 @@ pm_status fft_inverse_f32(pm_ctx* c, float2* spec, float* real, int n) {
     return PM_OK;
 }
 
-// lambda_u += K J(u)^T lambda_p at positions xs with force meshes gs (three n^3 meshes).
-pm_status adj_kick(pm_ctx* c, const uint32_t* xs, const float* gs, double K, float* lam_u, const float* lam_p) {
+// lambda_u += K J(u)^T lambda_p at positions xs with force meshes gs (three n^3 meshes),
+// then lambda_p += drift_next lambda_u (the transposed drift of the step before; 0: none).
+pm_status adj_kick(pm_ctx* c, const uint32_t* xs, const float* gs, double K, float* lam_u, float* lam_p,
+                   double drift_next) {
     const int n = c->n;
     const size_t n3 = (size_t)n * n * n;
     const float* G[3] = {gs, gs + n3, gs + 2 * n3};
-    PM_CK(adj_direct(xs, c->np3, n, lam_p, G, (float)K, lam_u, c->st));
     // V_j and the spectra are three meshes back to back (256-byte multiples): one batched transform
     float* V[3] = {(float*)c->at(c->L.force[0]), (float*)c->at(c->L.force[1]), (float*)c->at(c->L.force[2])};
     PM_CK(cudaMemsetAsync(V[0], 0, 3 * n3 * 4, c->st));
-    PM_CK(deposit_vec(xs, c->np3, n, lam_p, V, c->st));
+    PM_CK(deposit_vec(xs, c->np, n, lam_p, V, c->st));
     float2* sp[3] = {(float2*)c->at(c->L.spec[0]), (float2*)c->at(c->L.spec[1]), (float2*)c->at(c->L.spec[2])};
-    PM_TRY(fft_forward_f32(c, V[0], sp[0], n, 3));
-    const float2* in[3] = {sp[0], sp[1], sp[2]};
-    PM_CK(adj_combine(in, sp[0], n, c->kf, -1.5 * c->cfg.omega_m / ((double)n * n * n), nullptr, 0, c->st));
+    // forward z and y passes of the three meshes, then the x pass that combines them
+    // (sum_j i k_j C V_j) and transforms back, then the inverse y and z passes
+    PM_CK(forward_zy<float>(V[0], sp[0], n, 3, c->st));
+    // in place over field 0: each CTA reads and writes only its own columns
+    PM_CK(x_adj<float>(sp[0], sp[0], n, c->kf, -1.5 * c->cfg.omega_m / ((double)n * n * n), c->st));
     float* rho_bar = (float*)c->at(c->L.rho);
-    PM_TRY(fft_inverse_f32(c, sp[0], rho_bar, n));
+    PM_CK((y_rows<float, true>(sp[0], (int64_t)(n / 2 + 1) * n, n, c->st)));
+    const float2* zin[1] = {sp[0]};
+    float* zout[1] = {rho_bar};
+    PM_CK(z_c2r<float>(zin, zout, 1, n, 1, 0u, 0.0, c->st));
     const double mass = std::pow((double)n / c->np, 3);
-    PM_CK(adj_gather(xs, c->np3, n, rho_bar, (float)(K * mass), 1, lam_u, c->st));
+    PM_CK(adj_kick_particles(xs, c->np3, n, lam_p, G, rho_bar, (float)K, (float)(K * mass), (float)drift_next, lam_u,
+                             c->st));
     return PM_OK;
 }
 
@@ -886,12 +897,37 @@ pm_status pm_loss_grad(pm_ctx* c, const void* white_noise, const void* target, i
     float* lam_p = (float*)at(A.lam_p);
     void* x = c->at(c->L.x);
     void* p = c->at(c->L.p);
-    // ---- forward with checkpoints
+    auto kick_of = [&](int s) {
+        const double a0 = c->a_grid(s), a1 = c->a_grid(s + 1);
+        const double a_from = (s == 0) ? a0 : 0.5 * (c->a_grid(s - 1) + a0);
+        return pmhost::kick_integral(c->cosmo, a_from, 0.5 * (a0 + a1));
+    };
+    auto drift_of = [&](int s) { return pmhost::drift_integral(c->cosmo, c->a_grid(s), c->a_grid(s + 1)); };
+    const size_t Gb = 3 * n3 * 4;
+    // steps s0..s1-1 from the current state, keeping each step's positions and force meshes
+    auto record = [&](int s0, int s1) -> pm_status {
+        for (int s = s0; s < s1; ++s) {
+            PM_CK(cudaMemcpyAsync(at(A.seg_x + (size_t)(s - s0) * P), x, P, cudaMemcpyDeviceToDevice, c->st));
+            c->force_at = at(A.seg_g + (size_t)(s - s0) * Gb);
+            pm_status st = compute_forces(c, c->a_grid(s));
+            if (st == PM_OK) st = kick_drift(c, kick_of(s), drift_of(s));
+            c->force_at = nullptr;
+            if (st != PM_OK) return st;
+            c->step = s + 1;
+            c->synced = false;
+        }
+        return PM_OK;
+    };
+    // ---- forward with checkpoints; the last segment is recorded as it runs.  The closing
+    // half kick after the last step changes only p, which the loss does not see, so it is
+    // neither run nor transposed.
     PM_TRY(pm_ic_zeldovich(c, 0, white_noise, 0));
     for (int k = 0; k < A.nseg; ++k) {
+        const int s0 = k * C, s1 = std::min(S, s0 + C);
         PM_CK(cudaMemcpyAsync(at(A.ckpt + (size_t)k * 2 * P), x, P, cudaMemcpyDeviceToDevice, c->st));
         PM_CK(cudaMemcpyAsync(at(A.ckpt + (size_t)k * 2 * P + P), p, P, cudaMemcpyDeviceToDevice, c->st));
-        PM_TRY(pm_step(c, std::min(C, S - k * C)));
+        if (k < A.nseg - 1) PM_TRY(pm_step(c, s1 - s0));
+        else PM_TRY(record(s0, s1));
     }
     // ---- loss and its mesh adjoint
     float* rho = (float*)c->at(c->L.rho);
@@ -906,48 +942,23 @@ pm_status pm_loss_grad(pm_ctx* c, const void* white_noise, const void* target, i
     PM_CK(cudaStreamSynchronize(c->st));
     *loss_out = hsum / (double)n3;
     PM_CK(adj_gather((const uint32_t*)x, c->np3, n, rho, (float)mass, 0, lam_u, c->st));
-    PM_CK(cudaMemsetAsync(lam_p, 0, P, c->st));
-    // ---- reverse sweep, segment by segment
-    auto kick_of = [&](int s) {
-        const double a0 = c->a_grid(s), a1 = c->a_grid(s + 1);
-        const double a_from = (s == 0) ? a0 : 0.5 * (c->a_grid(s - 1) + a0);
-        return pmhost::kick_integral(c->cosmo, a_from, 0.5 * (a0 + a1));
-    };
-    const size_t Gb = 3 * n3 * 4;
+    // lam_p = 0 after the closing kick; the transposed drift of the last step gives lam_p
+    PM_CK(axpby(lam_p, lam_u, nullptr, 3 * c->np3, (float)(drift_of(S - 1) / box), 0.0f, c->st));
+    // ---- reverse sweep, segment by segment: kick of step s, then the drift of step s - 1
     for (int k = A.nseg - 1; k >= 0; --k) {
         const int s0 = k * C, s1 = std::min(S, s0 + C);
-        PM_CK(cudaMemcpyAsync(x, at(A.ckpt + (size_t)k * 2 * P), P, cudaMemcpyDeviceToDevice, c->st));
-        PM_CK(cudaMemcpyAsync(p, at(A.ckpt + (size_t)k * 2 * P + P), P, cudaMemcpyDeviceToDevice, c->st));
-        c->step = s0;
-        c->synced = (s0 == 0);
-        c->rho_valid = false;
-        for (int s = s0; s < s1; ++s) {
-            PM_CK(cudaMemcpyAsync(at(A.seg_x + (size_t)(s - s0) * P), x, P, cudaMemcpyDeviceToDevice, c->st));
-            PM_TRY(compute_forces(c, c->a_grid(s)));
-            for (int j = 0; j < 3; ++j)
-                PM_CK(cudaMemcpyAsync((char*)at(A.seg_g + (size_t)(s - s0) * Gb) + j * n3 * 4, c->at(c->L.force[j]),
-                                      n3 * 4, cudaMemcpyDeviceToDevice, c->st));
-            PM_TRY(kick_drift(c, kick_of(s), pmhost::drift_integral(c->cosmo, c->a_grid(s), c->a_grid(s + 1))));
-            c->step = s + 1;
-            c->synced = false;
+        if (k < A.nseg - 1) {
+            PM_CK(cudaMemcpyAsync(x, at(A.ckpt + (size_t)k * 2 * P), P, cudaMemcpyDeviceToDevice, c->st));
+            PM_CK(cudaMemcpyAsync(p, at(A.ckpt + (size_t)k * 2 * P + P), P, cudaMemcpyDeviceToDevice, c->st));
+            c->step = s0;
+            c->synced = (s0 == 0);
+            c->rho_valid = false;
+            PM_TRY(record(s0, s1));
         }
-        if (s1 == S) {  // positions and forces of the closing half kick
-            const int q = s1 - s0;
-            PM_CK(cudaMemcpyAsync(at(A.seg_x + (size_t)q * P), x, P, cudaMemcpyDeviceToDevice, c->st));
-            PM_TRY(compute_forces(c, c->a_grid(S)));
-            for (int j = 0; j < 3; ++j)
-                PM_CK(cudaMemcpyAsync((char*)at(A.seg_g + (size_t)q * Gb) + j * n3 * 4, c->at(c->L.force[j]), n3 * 4,
-                                      cudaMemcpyDeviceToDevice, c->st));
-            const double Kc = pmhost::kick_integral(c->cosmo, 0.5 * (c->a_grid(S - 1) + c->a_grid(S)), c->a_grid(S));
-            PM_TRY(adj_kick(c, (const uint32_t*)at(A.seg_x + (size_t)q * P), (const float*)at(A.seg_g + (size_t)q * Gb),
-                            Kc, lam_u, lam_p));
-        }
-        for (int s = s1 - 1; s >= s0; --s) {
-            const double Dd = pmhost::drift_integral(c->cosmo, c->a_grid(s), c->a_grid(s + 1));
-            PM_CK(axpby(lam_p, lam_u, lam_p, 3 * c->np3, (float)(Dd / box), 1.0f, c->st));
+        for (int s = s1 - 1; s >= s0; --s)
             PM_TRY(adj_kick(c, (const uint32_t*)at(A.seg_x + (size_t)(s - s0) * P),
-                            (const float*)at(A.seg_g + (size_t)(s - s0) * Gb), kick_of(s), lam_u, lam_p));
-        }
+                            (const float*)at(A.seg_g + (size_t)(s - s0) * Gb), kick_of(s), lam_u, lam_p,
+                            s > 0 ? drift_of(s - 1) / box : 0.0));
     }
     // ---- transposed Zel'dovich map: grad = sum_j A_j^T (D/L lam_u_j + a^2 E f D lam_p_j)
     const double a = c->cfg.a_init;

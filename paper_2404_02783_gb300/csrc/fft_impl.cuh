@@ -488,6 +488,70 @@ __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) k_x_cols(cplx<T>*
     }
 }
 
+// =============================================================== x: adjoint combine
+// Transposed force chain on the x pass: the three y-transformed spectra of the deposited
+// adjoint momenta V_j (fields j = 0, 1, 2 back to back, [kz][x][ky]) are transformed
+// along x one after the other and accumulated as out = sum_j i k_j c(k) V_j,
+// c = coef / (kf^2 |n|^2) (zero mode 0, k_j = 0 at its Nyquist index), then transformed
+// back along x into out ([kz][x][ky], ready for the inverse y and z passes).
+template <typename T, int LOGN>
+__global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) k_x_adj(const cplx<T>* V,
+                                                                      cplx<T>* out, double kf,
+                                                                      double coef) {
+    typedef cplx<T> C;
+    typedef Shape<T, LOGN> S;
+    constexpr int N = S::N, M = S::M, Q = S::QN, CB = S::CB;
+    constexpr int CS = CB + 1;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* tw = reinterpret_cast<C*>(smem_raw);
+    C* buf = tw + N;
+    const int tid = threadIdx.x;
+    const int b = tid % CB, t = tid / CB;
+    const int kz = blockIdx.y;
+    const int c = blockIdx.x * CB + b;
+    const size_t pbase = (size_t)kz * N * N;
+    const size_t field = (size_t)(M + 1) * N * N;
+    load_stage_twiddles<T, N>(tw);
+    const T kfT = T(kf);
+    const T coefT = T(coef) / (kfT * kfT);
+    const int ny = (c < M) ? c : c - N;
+    const T kyT = (2 * ny == -N) ? T(0) : kfT * T(ny);
+    const T kzT = (kz == M) ? T(0) : kfT * T(kz);
+    C acc[8];
+#pragma unroll
+    for (int m = 0; m < 8; ++m) acc[m] = cmake<C>(T(0), T(0));
+    ColEx<C, N> ex{buf, CS, b};
+#pragma unroll 1
+    for (int j = 0; j < 3; ++j) {
+        C v[1][8];
+        const C* col = V + j * field + pbase + c;
+#pragma unroll
+        for (int m = 0; m < 8; ++m) v[0][m] = col[(size_t)(t + m * Q) * N];
+        if (j == 0) __syncthreads();  // twiddles loaded
+        fft_regs<N, 1, false>(v, t, tw, ex);
+#pragma unroll
+        for (int m = 0; m < 8; ++m) {
+            const int i = t + m * Q;
+            const int nx = (i < M) ? i : i - N;
+            const T kj = (j == 0) ? ((2 * nx == -N) ? T(0) : kfT * T(nx)) : (j == 1 ? kyT : kzT);
+            acc[m].x += kj * v[0][m].x;
+            acc[m].y += kj * v[0][m].y;
+        }
+    }
+    C w[1][8];
+#pragma unroll
+    for (int m = 0; m < 8; ++m) {
+        const int i = t + m * Q;
+        const int nx = (i < M) ? i : i - N;
+        const int n2 = nx * nx + ny * ny + kz * kz;
+        const T cc = (n2 == 0) ? T(0) : coefT / T(n2);
+        w[0][m] = cmake<C>(-cc * acc[m].y, cc * acc[m].x);  // i c sum_j k_j V_j
+    }
+    fft_regs<N, 1, true>(w, t, tw, ex);
+#pragma unroll
+    for (int m = 0; m < 8; ++m) out[pbase + (size_t)(t + m * Q) * N + c] = w[0][m];
+}
+
 // =============================================================== launchers
 template <typename T, int LOGN>
 cudaError_t z_r2c_n(const T* in, cplx<T>* out, int g0, int rows, int xcl, cudaStream_t st) {
@@ -578,6 +642,16 @@ cudaError_t x_cols_n(cplx<T>* data, cplx<T>* out2, int nplanes, const SpecOp& op
 }
 
 template <typename T, int LOGN>
+cudaError_t x_adj_n(const cplx<T>* V, cplx<T>* out, double kf, double coef, cudaStream_t st) {
+    typedef Shape<T, LOGN> S;
+    const size_t smem = sizeof(cplx<T>) * (S::N + 2 * (size_t)S::N * (S::CB + 1));
+    cudaError_t e = set_smem((const void*)k_x_adj<T, LOGN>, smem);
+    if (e != cudaSuccess) return e;
+    k_x_adj<T, LOGN><<<dim3(S::N / S::CB, S::M + 1), S::CB * S::QN, smem, st>>>(V, out, kf, coef);
+    return cudaGetLastError();
+}
+
+template <typename T, int LOGN>
 cudaError_t x_cols_kind(cplx<T>* data, cplx<T>* out2, int nplanes, const SpecOp& op, cudaStream_t st) {
     switch (op.kind) {
         case OP_FWD_STORE: return x_cols_n<T, LOGN, OP_FWD_STORE>(data, out2, nplanes, op, st);
@@ -631,6 +705,11 @@ cudaError_t y_rows_grad3(cplx<T>* A, cplx<T>* B, cplx<T>* Cc, int64_t nrows, int
 }
 
 template <typename T>
+cudaError_t x_adj(const cplx<T>* V, cplx<T>* out, int n, double kf, double coef, cudaStream_t st) {
+    PM_DISPATCH_LOGN(n, (x_adj_n<T, LG>(V, out, kf, coef, st)))
+}
+
+template <typename T>
 cudaError_t forward_zy(const T* in, cplx<T>* spec, int n, int batch, cudaStream_t st) {
     PM_DISPATCH_LOGN(n, (forward_zy_n<T, LG>(in, spec, batch, st)))
 }
@@ -656,6 +735,7 @@ cudaError_t x_cols(cplx<T>* data, cplx<T>* out2, int nplanes, int n, const SpecO
                                          cudaStream_t, const double*, int64_t);                        \
     template cudaError_t x_cols<T>(cplx<T>*, cplx<T>*, int, int, const SpecOp&, cudaStream_t);      \
     template cudaError_t forward_zy<T>(const T*, cplx<T>*, int, int, cudaStream_t);                     \
+    template cudaError_t x_adj<T>(const cplx<T>*, cplx<T>*, int, double, double, cudaStream_t);         \
     template cudaError_t inverse_yz_grad<T>(cplx<T>*, cplx<T>*, cplx<T>*, T* const*, int, int, double,   \
                                             cudaStream_t, const double*);
 

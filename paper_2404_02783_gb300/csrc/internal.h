@@ -72,6 +72,11 @@ cudaError_t y_rows_grad3(cplx<T>* A, cplx<T>* B, cplx<T>* C, int64_t nrows, int 
                          cudaStream_t st, const double* kf_arr = nullptr, int64_t rows_per_field = 0);
 template <typename T>
 cudaError_t x_cols(cplx<T>* data, cplx<T>* out2, int nplanes, int n, const SpecOp& op, cudaStream_t st);
+// Transposed force chain on the x pass (adjoint): V holds the three y-transformed spectra
+// of the deposited adjoint momenta back to back; out = IFFT_x[sum_j i k_j c(k) FFT_x V_j]
+// with c = coef / (kf^2 |n|^2).
+template <typename T>
+cudaError_t x_adj(const cplx<T>* V, cplx<T>* out, int n, double kf, double coef, cudaStream_t st);
 // Forward z (r2c) and y passes of `batch` real meshes into spec ([field][kz][kx][ky]
 // before the x pass).
 template <typename T>

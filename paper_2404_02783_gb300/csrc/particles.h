@@ -53,7 +53,12 @@ cudaError_t adj_gather(const uint32_t* x, int64_t count, int n, const float* F, 
                        float* lam_u, cudaStream_t st);
 cudaError_t adj_direct(const uint32_t* x, int64_t count, int n, const float* v, const float* const* G, float K,
                        float* lam_u, cudaStream_t st);
-cudaError_t deposit_vec(const uint32_t* x, int64_t count, int n, const float* v, float* const* V, cudaStream_t st);
+// lam_u += K sum_j v_j grad interp(G_j) + Km grad interp(rho_bar); then v += drift_next lam_u.
+cudaError_t adj_kick_particles(const uint32_t* x, int64_t count, int n, float* v, const float* const* G,
+                               const float* rho_bar, float K, float Km, float drift_next, float* lam_u,
+                               cudaStream_t st);
+// V_j += CIC deposit of v_j for the np^3 lattice-ordered particles x (V_j zeroed by the caller).
+cudaError_t deposit_vec(const uint32_t* x, int np, int n, const float* v, float* const* V, cudaStream_t st);
 cudaError_t adj_combine(const float2* const* in, float2* out, int n, double kf, double coef, const double* amp,
                         int mode, cudaStream_t st);
 cudaError_t loss_mse(float* delta, const float* target, int64_t n3, double* acc, cudaStream_t st);
