@@ -94,14 +94,30 @@ __host__ __device__ constexpr int tw_stage_offset(int L, int Ns, int s = 1, int 
 __host__ __device__ constexpr int tw_stage_entries(int L) { return tw_stage_offset(L, L); }
 
 // ---------------------------------------------------------------- exchangers
-// Rows: sequence s of row b at base[((p NSEQ + s) RB + b) RS + spad(i)]; two
+// Shared-memory rows of the exchanges: element i of a row sits at slot
+// i ^ ((i >> SH) & MK) (a permutation within aligned blocks of MK + 1 elements), rows
+// RS slots apart.  The parameters are chosen per transform length, and for the z passes
+// (rows of n/2 + 1 elements that the r2c / c2r post-processing also walks across rows),
+// by enumerating every access pattern of a warp so that the 8-byte accesses of each
+// half-warp fall in distinct banks (no pattern replays for y rows of 16..1024 elements
+// and z rows of 128..512; z rows of 8..64 replay less than the plain padded layout).
+template <int L, bool ZPASS>
+struct RowLayout {
+    static constexpr int SH = ZPASS ? (L >= 128 ? 3 : L == 64 ? 2 : L == 32 ? 1 : L == 16 ? 4 : 1) : 3;
+    static constexpr int MK = ZPASS ? (L >= 64 || L == 32 ? 15 : 7) : (L >= 128 ? 15 : 7);
+    static constexpr int RS = ZPASS ? (L == 512 ? 514 : L >= 128 ? L + 1 : L == 64 ? 65 : L == 32 ? 35 : L == 16 ? 19 : 13)
+                                    : (L >= 128 ? L + 1 : L == 64 ? 72 : L == 32 ? 44 : 22);
+    __host__ __device__ static constexpr int slot(int i) { return i ^ ((i >> SH) & MK); }
+};
+
+// Rows: sequence s of row b at base[((p NSEQ + s) RB + b) RS + slot(i)]; two
 // buffers alternate (p) when PP, so one barrier per exchange suffices.
-template <typename C, int NSEQ, bool PP>
+template <typename C, int NSEQ, bool PP, class LAY>
 struct RowEx {
     C* base;
     int RB, RS, b, p;
     __device__ __forceinline__ C& at(int s, int i) {
-        return base[((size_t)((PP ? p : 0) * NSEQ + s) * RB + b) * RS + spad(i)];
+        return base[((size_t)((PP ? p : 0) * NSEQ + s) * RB + b) * RS + LAY::slot(i)];
     }
     __device__ __forceinline__ void begin() {
         if (!PP) __syncthreads();

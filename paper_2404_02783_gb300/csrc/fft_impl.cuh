@@ -49,9 +49,6 @@ __device__ __forceinline__ void load_twiddles_head(cplx<T>* tw, int L, int count
     for (int k = threadIdx.x; k < count; k += blockDim.x) tw[k] = tw_global<T>(k * stride);
 }
 
-// Padded row stride (complex elements) holding `len` elements; odd so lanes walking
-// across rows hit different banks.
-__host__ __device__ constexpr int row_stride(int len) { return (len + (len >> 3) + 1) | 1; }
 
 // Opts a kernel into more than 48 KB of dynamic shared memory once per device, so that
 // launches (including those recorded into a CUDA graph) make no further attribute calls.
@@ -84,11 +81,12 @@ __device__ __forceinline__ size_t spec_row(int gl, int kz, int xcl) {
 
 // =============================================================== z: r2c
 template <typename T, int LOGN>
-__global__ void __launch_bounds__(512) k_z_r2c(const T* __restrict__ in, cplx<T>* __restrict__ out, int g0, int xcl) {
+__global__ void __launch_bounds__(512, sizeof(T) == 4 ? 4 : 2) k_z_r2c(const T* __restrict__ in, cplx<T>* __restrict__ out, int g0, int xcl) {
     typedef cplx<T> C;
     typedef Shape<T, LOGN> S;
     constexpr int N = S::N, M = S::M, Q = S::QM, YB = S::YB;
-    constexpr int RS = row_stride(M + 1);
+    typedef RowLayout<M, true> LAY;
+    constexpr int RS = LAY::RS;
     constexpr int TWN = (M + 2) & ~1;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* twM = reinterpret_cast<C*>(smem_raw);
@@ -106,12 +104,12 @@ __global__ void __launch_bounds__(512) k_z_r2c(const T* __restrict__ in, cplx<T>
 #pragma unroll
     for (int m = 0; m < 8; ++m) v[0][m] = row[t + m * Q];
     __syncthreads();
-    RowEx<C, 1, false> ex{buf, YB, RS, b, 0};
+    RowEx<C, 1, false, LAY> ex{buf, YB, RS, b, 0};
     fft_regs<M, 1, false>(v, t, twM, ex);
     C* z = buf;
     __syncthreads();  // every thread has read its last exchange before the buffer is reused
 #pragma unroll
-    for (int m = 0; m < 8; ++m) z[b * RS + spad(t + m * Q)] = v[0][m];
+    for (int m = 0; m < 8; ++m) z[b * RS + LAY::slot(t + m * Q)] = v[0][m];
     __syncthreads();
     constexpr int NT = YB * Q, ITERS = ((M + 1) * YB + NT - 1) / NT;
 #pragma unroll
@@ -119,8 +117,8 @@ __global__ void __launch_bounds__(512) k_z_r2c(const T* __restrict__ in, cplx<T>
         const int e = tid + it * NT;
         if (e >= (M + 1) * YB) break;
         const int k = e / YB, bb = e % YB;
-        const C z1 = z[bb * RS + spad(k == M ? 0 : k)];
-        const C z2 = cconj(z[bb * RS + spad(k == 0 ? 0 : M - k)]);
+        const C z1 = z[bb * RS + LAY::slot(k == M ? 0 : k)];
+        const C z2 = cconj(z[bb * RS + LAY::slot(k == 0 ? 0 : M - k)]);
         const C E = cscale(cadd(z1, z2), T(0.5));
         const C O = cscale(cmul_mi<false>(csub(z1, z2)), T(0.5));
         out[spec_row<M>(gl, k, xcl) * N + y0 + bb] = cadd(E, cmul(twN[k], O));
@@ -134,12 +132,13 @@ template <typename T> struct Ptr3 {
 };
 
 template <typename T, int LOGN>
-__global__ void __launch_bounds__(512) k_z_c2r(Ptr3<T> P, unsigned gradz_mask, T kf0, const double* __restrict__ kf_arr,
+__global__ void __launch_bounds__(512, sizeof(T) == 4 ? 4 : 2) k_z_c2r(Ptr3<T> P, unsigned gradz_mask, T kf0, const double* __restrict__ kf_arr,
                                                int g0, int xcl) {
     typedef cplx<T> C;
     typedef Shape<T, LOGN> S;
     constexpr int N = S::N, M = S::M, Q = S::QM, YB = S::YB;
-    constexpr int RS = row_stride(M + 1);
+    typedef RowLayout<M, true> LAY;
+    constexpr int RS = LAY::RS;
     constexpr int TWN = (M + 2) & ~1;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* twM = reinterpret_cast<C*>(smem_raw);
@@ -168,15 +167,15 @@ __global__ void __launch_bounds__(512) k_z_c2r(Ptr3<T> P, unsigned gradz_mask, T
             const T kz = (k == M) ? T(0) : kf * T(k);
             X = cmake<C>(X.y * kz, -X.x * kz);
         }
-        xb[bb * RS + spad(k)] = X;
+        xb[bb * RS + LAY::slot(k)] = X;
     }
     __syncthreads();
     // Y_k = (X_k + X*_{M-k}) + i (X_k - X*_{M-k}) exp(+2 pi i k / N), pairs (k, M-k) per thread
     for (int e = tid; e < (M / 2 + 1) * YB; e += YB * Q) {
         const int k = e / YB, bb = e % YB;
         C* r = xb + bb * RS;
-        C a = r[spad(k)];
-        C c = r[spad(M - k)];
+        C a = r[LAY::slot(k)];
+        C c = r[LAY::slot(M - k)];
         if (k == 0) {
             a.y = T(0);
             c.y = T(0);
@@ -187,16 +186,16 @@ __global__ void __launch_bounds__(512) k_z_c2r(Ptr3<T> P, unsigned gradz_mask, T
         if (k > 0 && k < M - k) {
             const C aconj = cconj(a);
             const C d2 = cmul(csub(c, aconj), cconj(twN[M - k]));
-            r[spad(M - k)] = cadd(cadd(c, aconj), cmake<C>(-d2.y, d2.x));
+            r[LAY::slot(M - k)] = cadd(cadd(c, aconj), cmake<C>(-d2.y, d2.x));
         }
-        r[spad(k)] = y;
+        r[LAY::slot(k)] = y;
     }
     __syncthreads();
     const int b = tid / Q, t = tid % Q;
     C v[1][8];
 #pragma unroll
-    for (int m = 0; m < 8; ++m) v[0][m] = xb[b * RS + spad(t + m * Q)];
-    RowEx<C, 1, false> ex{buf, YB, RS, b, 0};
+    for (int m = 0; m < 8; ++m) v[0][m] = xb[b * RS + LAY::slot(t + m * Q)];
+    RowEx<C, 1, false, LAY> ex{buf, YB, RS, b, 0};
     fft_regs<M, 1, true>(v, t, twM, ex);
     C* orow = reinterpret_cast<C*>(pout + (g * N + y0 + b) * N);
 #pragma unroll
@@ -210,7 +209,8 @@ __global__ void __launch_bounds__(512) k_y_rows(const cplx<T>* in, cplx<T>* out,
     typedef cplx<T> C;
     typedef Shape<T, LOGN> S;
     constexpr int N = S::N, Q = S::QN, RB = S::RB;
-    constexpr int RS = row_stride(N);
+    typedef RowLayout<N, false> LAY;
+    constexpr int RS = LAY::RS;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* tw = reinterpret_cast<C*>(smem_raw);
     C* buf = tw + N;
@@ -226,7 +226,7 @@ __global__ void __launch_bounds__(512) k_y_rows(const cplx<T>* in, cplx<T>* out,
         for (int m = 0; m < 8; ++m) v[0][m] = irow[t + m * Q];
     }
     __syncthreads();
-    RowEx<C, 1, true> ex{buf, RB, RS, b, 0};
+    RowEx<C, 1, true, LAY> ex{buf, RB, RS, b, 0};
     fft_regs<N, 1, INV>(v, t, tw, ex);
     C* orow = out + r * N;
     if (ok) {
@@ -243,7 +243,8 @@ __global__ void __launch_bounds__(512) k_y_grad3(const cplx<T>* A, const cplx<T>
     typedef cplx<T> C;
     typedef Shape<T, LOGN> S;
     constexpr int N = S::N, Q = S::QN, RB = S::RB3;
-    constexpr int RS = row_stride(N);
+    typedef RowLayout<N, false> LAY;
+    constexpr int RS = LAY::RS;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* tw = reinterpret_cast<C*>(smem_raw);
     C* buf = tw + N;
@@ -268,7 +269,7 @@ __global__ void __launch_bounds__(512) k_y_grad3(const cplx<T>* A, const cplx<T>
         }
     }
     __syncthreads();
-    RowEx<C, 2, false> ex{buf, RB, RS, b, 0};
+    RowEx<C, 2, false, LAY> ex{buf, RB, RS, b, 0};
     fft_regs<N, 2, true>(v, t, tw, ex);
     if (ok) {
 #pragma unroll
@@ -281,7 +282,7 @@ __global__ void __launch_bounds__(512) k_y_grad3(const cplx<T>* A, const cplx<T>
 #pragma unroll
         for (int m = 0; m < 8; ++m) v[0][m] = B[ri * N + t + m * Q];
     }
-    RowEx<C, 1, false> ex1{buf, RB, RS, b, 0};
+    RowEx<C, 1, false, LAY> ex1{buf, RB, RS, b, 0};
     fft_regs<N, 1, true>(v, t, tw, ex1);
     if (ok) {
 #pragma unroll
@@ -556,7 +557,7 @@ __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) k_x_adj(const cpl
 template <typename T, int LOGN>
 cudaError_t z_r2c_n(const T* in, cplx<T>* out, int g0, int rows, int xcl, cudaStream_t st) {
     typedef Shape<T, LOGN> S;
-    const size_t smem = sizeof(cplx<T>) * (S::M + ((S::M + 2) & ~1) + (size_t)S::YB * row_stride(S::M + 1));
+    const size_t smem = sizeof(cplx<T>) * (S::M + ((S::M + 2) & ~1) + (size_t)S::YB * RowLayout<S::M, true>::RS);
     cudaError_t e = set_smem((const void*)k_z_r2c<T, LOGN>, smem);
     if (e != cudaSuccess) return e;
     k_z_r2c<T, LOGN><<<dim3(S::N / S::YB, rows), S::YB * S::QM, smem, st>>>(in, out, g0, xcl);
@@ -567,7 +568,7 @@ template <typename T, int LOGN>
 cudaError_t z_c2r_n(const Ptr3<T>& P, int ncomp, int g0, int rows, int xcl, unsigned mask, double kf, cudaStream_t st,
                     const double* kf_arr) {
     typedef Shape<T, LOGN> S;
-    const size_t smem = sizeof(cplx<T>) * (S::M + ((S::M + 2) & ~1) + (size_t)S::YB * row_stride(S::M + 1));
+    const size_t smem = sizeof(cplx<T>) * (S::M + ((S::M + 2) & ~1) + (size_t)S::YB * RowLayout<S::M, true>::RS);
     cudaError_t e = set_smem((const void*)k_z_c2r<T, LOGN>, smem);
     if (e != cudaSuccess) return e;
     k_z_c2r<T, LOGN><<<dim3(S::N / S::YB, rows, ncomp), S::YB * S::QM, smem, st>>>(P, mask, (T)kf, kf_arr, g0, xcl);
@@ -577,7 +578,7 @@ cudaError_t z_c2r_n(const Ptr3<T>& P, int ncomp, int g0, int rows, int xcl, unsi
 template <typename T, int LOGN, bool INV>
 cudaError_t y_rows_n(const cplx<T>* in, cplx<T>* out, int64_t nrows, cudaStream_t st) {
     typedef Shape<T, LOGN> S;
-    const size_t smem = sizeof(cplx<T>) * (S::N + 2 * (size_t)S::RB * row_stride(S::N));
+    const size_t smem = sizeof(cplx<T>) * (S::N + 2 * (size_t)S::RB * RowLayout<S::N, false>::RS);
     cudaError_t e = set_smem((const void*)k_y_rows<T, LOGN, INV>, smem);
     if (e != cudaSuccess) return e;
     const int64_t nblk = (nrows + S::RB - 1) / S::RB;
@@ -589,7 +590,7 @@ template <typename T, int LOGN>
 cudaError_t y_grad3_n(const cplx<T>* A, const cplx<T>* B, cplx<T>* Ao, cplx<T>* Bo, cplx<T>* Co, int64_t nrows, double kf,
                       cudaStream_t st, const double* kf_arr, int64_t rows_per_field) {
     typedef Shape<T, LOGN> S;
-    const size_t smem = sizeof(cplx<T>) * (S::N + 2 * (size_t)S::RB3 * row_stride(S::N));
+    const size_t smem = sizeof(cplx<T>) * (S::N + 2 * (size_t)S::RB3 * RowLayout<S::N, false>::RS);
     cudaError_t e = set_smem((const void*)k_y_grad3<T, LOGN>, smem);
     if (e != cudaSuccess) return e;
     const int64_t nblk = (nrows + S::RB3 - 1) / S::RB3;
