@@ -367,6 +367,105 @@ def adjoint(pm, torch, args):
             "value": np_side**3 * steps / t_grad, "unit": "particle-steps/s (forward + reverse)"}
 
 
+def estimators(pm, torch, args):
+    """The per-output steps on the headline configuration (FP32, 512^3 particles on a 512^3
+    mesh, L = 5000 Mpc/h, a few steps from the ZA ICs): P(k) in 64 log bins from the particles
+    and from a mesh, B(k) for all triplets of 24 linear bins up to k = 0.05 h/Mpc on the
+    alias-free m = 128 grid, the halo-proxy linear-bias fit (top 5%, k < 0.02 h/Mpc), and the GR
+    displacement combination from a 256^3 pair onto the 512^3 lattice.  Each is timed with CUDA
+    events (median of a few calls) next to the FP64 oracle on a small sample of the same kind."""
+    import numpy as np
+    from oracle import cic as ocic, combine as ocomb, stats as ostats
+    peak, _ = peaks()
+    np_side, n, box = args.np, args.nmesh, args.box
+    s = 4
+    R, S, P = s * n**3, 8 * (n // 2 + 1) * n * n, np_side**3
+    run = pm.PMRun(pm.make_config(np_side, n, box, A_INIT, A_FINAL, 100))
+    run.ic(seed=1)
+    run.step(3)
+    delta = run.density()
+    st = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def timed(fn, reps=5):
+        fn()
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(reps):
+            e0.record(st)
+            fn()
+            e1.record(st)
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return float(np.median(ts))
+
+    def host_timed(fn, reps=3):
+        fn()
+        ts = []
+        for _ in range(reps):
+            t0 = time.perf_counter()
+            fn()
+            ts.append(time.perf_counter() - t0)
+        return 1e3 * float(np.median(ts))
+
+    def line(ms, nbytes, what):
+        gbs = nbytes / (ms * 1e-3) / 1e9
+        return {"ms": round(ms, 4), "algorithmic_bytes": int(nbytes), "GBps": round(gbs, 1),
+                "frac": round(gbs / peak, 4), "bytes_model": what}
+
+    out = {"workload": f"{np_side}^3 particles on a {n}^3 mesh, L={box:g} Mpc/h, FP32, after 3 steps from z=50"}
+    e64 = pm.log_edges(64, 1.0, n / 2.0)
+    out["power_particles"] = line(timed(lambda: run.power(e64)), 12 * P + 16 * n**3,
+                                  "read x (12 B/particle), deposit and transform (16 B/cell)")
+    out["power_field"] = line(timed(lambda: run.power(e64, field=delta)), R + S,
+                              "read the field, one pass over its half spectrum")
+    kf = 2 * np.pi / box
+    e24 = np.linspace(0.0, 0.05 / kf, 25)
+    ms_bk = timed(lambda: run.bispectrum(e24, 128, field=delta), reps=3)
+    ntri = 24 * 25 * 26 // 6
+    flops = 6.0 * ntri * 128**3
+    out["bispectrum"] = {"ms": round(ms_bk, 3), "bins": 24, "triangles": ntri, "m": 128,
+                         "triangle_sum_flops": flops, "TFLOPs": round(flops / (ms_bk * 1e-3) / 1e12, 2),
+                         "bound": "alu (FP32 triangle sums on the m-grid) plus 48 inverse FFTs of 128^3"}
+    dh = torch.empty_like(delta)
+    e32 = pm.log_edges(32, 1.0, n / 2.0)
+
+    def bias():
+        pm.pm_halo_proxy(run.ctx, dh, field=delta, fraction=0.05)
+        pm.pm_linear_bias(run.ctx, dh, delta, e32, 0.02, terms=1)
+    out["bias_fit"] = line(timed(bias, reps=3), 2 * R + 2 * (R + S),
+                           "select the top 5% (read the field twice), cross and auto spectra")
+    pair = [pm.PMRun(pm.make_config(np_side // 2, n // 2, box, A_INIT, A_FINAL, 100, mode=mode)) for mode in
+            (pm.PM_GR_POISSON, pm.PM_NEWTON)]
+    for r in pair:
+        r.ic(seed=1)
+    out["displacement_combination"] = line(
+        timed(lambda: pm.pm_displacement_correction(run.ctx, pair[0].ctx, pair[1].ctx)),
+        24 * P + 2 * 12 * (np_side // 2)**3, "read + write the target positions, read both pair positions")
+    del pair, run, delta, dh
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    # the FP64 oracle beside them, on small samples of the same kind (one host core)
+    rng = np.random.default_rng(5)
+    f64 = rng.standard_normal((64, 64, 64))
+    f32 = rng.standard_normal((32, 32, 32))
+    e_o = ostats.log_edges(16, 1.0, 32.0)
+    ms_pk = host_timed(lambda: ostats.power_spectrum(f64, 625.0, e_o))
+    ms_bko = host_timed(lambda: ostats.bispectrum(f32, 312.5, np.linspace(0.0, 10.0, 7), M=32), reps=1)
+    xt = (rng.integers(0, 2**32, size=(3, 64**3), dtype=np.uint64)).astype(np.uint32)
+    xg = (rng.integers(0, 2**32, size=(3, 32**3), dtype=np.uint64)).astype(np.uint32)
+    ms_co = host_timed(lambda: ocomb.combine(xt, ocomb.interpolate_lagrangian(ocomb.displacement(xg, xg), 32, 64)))
+    out["cpu_oracle"] = {"cores": 1, "kind": "oracle",
+                         "power_field_64^3_ms": round(ms_pk, 2),
+                         "power_field_cells_per_s": round(64**3 / (ms_pk * 1e-3), 1),
+                         "bispectrum_32^3_6bins_M32_ms": round(ms_bko, 2),
+                         "combination_32^3_to_64^3_ms": round(ms_co, 2),
+                         "combination_particles_per_s": round(64**3 / (ms_co * 1e-3), 1)}
+    out["gpu_power_field_cells_per_s"] = round(n**3 / (out["power_field"]["ms"] * 1e-3), 1)
+    out["gpu_combination_particles_per_s"] = round(P / (out["displacement_combination"]["ms"] * 1e-3), 1)
+    return out
+
+
 def cpu_oracle(seconds, np_side=64):
     """The FP64 oracle on this host: a 64^3 sample of the workload at the same mesh spacing."""
     import numpy as np
@@ -402,6 +501,7 @@ def main():
     ap.add_argument("--batch", type=int, default=64)
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--no-estimators", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("at least 3 warm-up steps")
@@ -470,6 +570,8 @@ def main():
         out["batched"] = batched(pm, torch, args)
     if not args.no_adjoint:
         out["adjoint"] = adjoint(pm, torch, args)
+    if not args.no_estimators and rank == 0:
+        out["estimators"] = estimators(pm, torch, args)
     if rank == 0:
         out["cpu_baseline"] = cpu_oracle(args.cpu_seconds)
         print(json.dumps(out))

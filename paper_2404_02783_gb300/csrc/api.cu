@@ -3,6 +3,8 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -99,7 +101,7 @@ Layout plan(const pm_config& c) {
     L.amp = take((3 * (size_t)(c.np / 2) * (c.np / 2) + 1) * 8);
     L.bin_of = take((3 * (n / 2) * (n / 2) + 1) * 2);
     L.wtab = take((n / 2 + 1) * 8);
-    L.acc = take(3 * kMaxBins * 8);
+    L.acc = take(kMaxBins * 8);
     L.total = off;
     return L;
 }
@@ -286,6 +288,28 @@ void build_bin_table(int n, int nbins, const double* edges, std::vector<int16_t>
     }
 }
 
+// Weighted number of modes with |n|^2 = s for s <= (n/2)^2 over the stored half spectrum
+// (kx, ky in [-n/2, n/2), kz in [0, n/2]): weight 1 on the kz = 0 and n/2 planes and 2
+// elsewhere, which counts the mirrored half.  Geometry only, so one table per mesh size.
+const std::vector<double>& mode_counts(int n) {
+    static std::mutex mu;
+    static std::map<int, std::vector<double>> cache;
+    std::lock_guard<std::mutex> g(mu);
+    const auto it = cache.find(n);
+    if (it != cache.end()) return it->second;
+    const int64_t M = n / 2, top = M * M;
+    std::vector<double> c2(top + 1, 0.0);  // (kx, ky) pairs with kx^2 + ky^2 = s
+    for (int64_t a = -M; a < M; ++a)
+        for (int64_t b = -M; b < M; ++b)
+            if (a * a + b * b <= top) c2[a * a + b * b] += 1.0;
+    std::vector<double> cnt(top + 1, 0.0);
+    for (int64_t z = 0; z <= M; ++z) {
+        const double w = (z == 0 || z == M) ? 1.0 : 2.0;
+        for (int64_t s = 0; s + z * z <= top; ++s) cnt[s + z * z] += w * c2[s];
+    }
+    return cache.emplace(n, std::move(cnt)).first->second;
+}
+
 pm_status check_edges(int nbins, const double* edges) {
     if (nbins < 1 || nbins > kMaxBins || !edges) return fail(PM_ERR_INVALID_ARG, "need 1..256 bins and edges");
     for (int b = 0; b < nbins; ++b)
@@ -309,30 +333,45 @@ pm_status power_t(pm_ctx* c, const void* field, const void* field2, int nbins, c
     std::vector<int16_t> tab;
     build_bin_table(n, nbins, edges, tab);
     PM_CK(cudaMemcpyAsync(c->at(c->L.bin_of), tab.data(), tab.size() * 2, cudaMemcpyHostToDevice, c->st));
-    double* acc = (double*)c->at(c->L.acc);
-    PM_CK(cudaMemsetAsync(acc, 0, sizeof(double) * 3 * nbins, c->st));
+    // per-CTA rows of bin sums in the third spectrum buffer (free here), reduced in a fixed order
+    double* rows = (double*)c->at(c->L.spec[2]);
+    const size_t spec_bytes = (size_t)(n / 2 + 1) * n * n * 2 * c->sT();
+    const int nrows = (int)std::min<size_t>(4 * (size_t)num_sms(), spec_bytes / (sizeof(double) * nbins));
+    PM_CK(cudaMemsetAsync(rows, 0, sizeof(double) * nrows * nbins, c->st));
     SpecOp op;
     op.kind = OP_BIN;
     op.fwd = 1;
     op.kf = c->kf;
     op.bin_of = (const int16_t*)c->at(c->L.bin_of);
     op.wtab = (const double*)c->at(c->L.wtab);
-    op.acc = acc;
+    op.acc = rows;
+    op.acc_rows = nrows;
     op.nbins = nbins;
     op.deconv = deconv ? 1 : 0;
     op.in2 = field2 ? s1 : nullptr;
     PM_CK(x_cols<T>((cplx<T>*)s0, nullptr, n / 2 + 1, n, op, c->st));
-    std::vector<double> h(3 * nbins);
-    PM_CK(cudaMemcpyAsync(h.data(), acc, sizeof(double) * 3 * nbins, cudaMemcpyDeviceToHost, c->st));
+    double* acc = (double*)c->at(c->L.acc);
+    PM_CK(bin_rows_sum(rows, nrows, nbins, acc, c->st));
+    std::vector<double> h(nbins);
+    PM_CK(cudaMemcpyAsync(h.data(), acc, sizeof(double) * nbins, cudaMemcpyDeviceToHost, c->st));
+    // mode counts and mean |k| per bin follow from the geometry alone
+    const std::vector<double>& cnt = mode_counts(n);
+    std::vector<double> nm(nbins, 0.0), ks(nbins, 0.0);
+    for (size_t s = 1; s < cnt.size(); ++s) {
+        const int b = tab[s];
+        if (b < 0) continue;
+        nm[b] += cnt[s];
+        ks[b] += cnt[s] * std::sqrt((double)s);
+    }
     PM_CK(cudaStreamSynchronize(c->st));
     const double V = c->cfg.box * c->cfg.box * c->cfg.box;
     const double n6 = std::pow((double)n, 6);
     for (int b = 0; b < nbins; ++b) {
-        const double w = h[b];
+        const double w = nm[b];
         if (nmodes_out) nmodes_out[b] = w;
         if (w > 0) {
-            if (p_out) p_out[b] = V / n6 * h[nbins + b] / w;
-            if (k_out) k_out[b] = h[2 * nbins + b] / w;
+            if (p_out) p_out[b] = V / n6 * h[b] / w;
+            if (k_out) k_out[b] = c->kf * ks[b] / w;
         } else {
             if (p_out) p_out[b] = NAN;
             if (k_out) k_out[b] = NAN;
@@ -1032,7 +1071,7 @@ void batch_plan(pm_batch& b) {
     b.SCALE = take(B * 8);
     b.BIN = take((3 * (n / 2) * (n / 2) + 1) * 2);
     b.WTAB = take((n / 2 + 1) * 8);
-    b.ACC = take(3 * kMaxBins * 8);
+    b.ACC = take(kMaxBins * 8);
     b.total = off;
 }
 

@@ -12,4 +12,19 @@ cudaError_t upload_twiddles_f32(const float2* host) {
 
 PM_INST(float)
 
+// out[b] = sum over rows r (in order) of rows[r nbins + b]: the per-CTA bin sums of the
+// binning x pass, combined in a fixed order.
+__global__ void k_sum_rows(const double* __restrict__ rows, int nrows, int nbins, double* __restrict__ out) {
+    for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nbins; b += gridDim.x * blockDim.x) {
+        double s = 0.0;
+        for (int r = 0; r < nrows; ++r) s += rows[(size_t)r * nbins + b];
+        out[b] = s;
+    }
+}
+
+cudaError_t bin_rows_sum(const double* rows, int nrows, int nbins, double* out, cudaStream_t st) {
+    k_sum_rows<<<1, 256, 0, st>>>(rows, nrows, nbins, out);
+    return cudaGetLastError();
+}
+
 }  // namespace pm

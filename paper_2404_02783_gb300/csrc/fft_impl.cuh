@@ -318,13 +318,16 @@ __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) k_x_cols(cplx<T>*
     C* buf = tw + N;
     const bool cross = (KIND == OP_BIN) && op.in2 != nullptr;
     C* stage = buf + (size_t)2 * N * CS;                     // [1 + cross][N][CB]: field (and in2)
-    double* acc = reinterpret_cast<double*>(stage + (size_t)(cross ? 2 : 1) * N * CB);
+    // OP_BIN: 1 / W^2 of the CIC window per |n_j| (W per axis from the FP64 table), in T
+    T* iw2 = reinterpret_cast<T*>(stage + (size_t)(cross ? 2 : 1) * N * CB);
     const int tid = threadIdx.x;
     const int b = tid % CB, t = tid / CB;
     const int64_t nblk = (int64_t)nplanes * NCG;
     load_stage_twiddles<T, N>(tw);
     if (KIND == OP_BIN)
-        for (int e = tid; e < 3 * op.nbins; e += blockDim.x) acc[e] = 0.0;
+        for (int e = tid; e <= M; e += blockDim.x) iw2[e] = op.deconv ? T(1.0 / (op.wtab[e] * op.wtab[e])) : T(1);
+    // OP_BIN: this CTA's row of per-bin sums in global memory (zeroed by the caller)
+    double* acc_row = (KIND == OP_BIN) ? op.acc + (size_t)blockIdx.x * op.nbins : nullptr;
     auto issue = [&](int64_t blk) {
         const size_t pb = (size_t)(blk / NCG) * N * N + (size_t)(blk % NCG) * CB;
         for (int q = tid; q < N * CHUNKS_ROW; q += blockDim.x) {
@@ -382,6 +385,11 @@ __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) k_x_cols(cplx<T>*
         const T kfT = T(kf);
         const T coefT = T(op.coef) / (kfT * kfT);
         const T kf2T = T(kf * kf);
+        // OP_BIN: consecutive modes of a thread that fall in the same bin are summed in
+        // registers, each run added once to the CTA's row (native FP64 reduction in L2)
+        int run_bin = -1;
+        T run_sum = T(0);
+        const T wyz = (KIND == OP_BIN) ? iw2[ny < 0 ? -ny : ny] * iw2[nz] * T((nz == 0 || nz == M) ? 1 : 2) : T(1);
     #pragma unroll
         for (int m = 0; m < 8; ++m) {
             const int i = t + m * Q;
@@ -392,21 +400,16 @@ __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) k_x_cols(cplx<T>*
                 if (n2 == 0 || n2 > M * M) continue;
                 const int bin = op.bin_of[n2];
                 if (bin < 0) continue;
-                const double w = (nz == 0 || nz == M) ? 1.0 : 2.0;
-                double val;
-                if (cross) {
-                    const C u = v[1][m];
-                    val = (double)vv.x * (double)u.x + (double)vv.y * (double)u.y;
+                const C u = cross ? v[1][m] : vv;
+                // w |delta_n|^2 / W^2 (or the cross product), w = 1 on the kz = 0, n/2 planes, 2 elsewhere
+                const T val = (vv.x * u.x + vv.y * u.y) * (iw2[nx < 0 ? -nx : nx] * wyz);
+                if (bin != run_bin) {
+                    if (run_bin >= 0) atomicAdd(acc_row + run_bin, (double)run_sum);
+                    run_bin = bin;
+                    run_sum = val;
                 } else {
-                    val = (double)vv.x * (double)vv.x + (double)vv.y * (double)vv.y;
+                    run_sum += val;
                 }
-                if (op.deconv) {
-                    const double W = op.wtab[nx < 0 ? -nx : nx] * op.wtab[ny < 0 ? -ny : ny] * op.wtab[nz];
-                    val /= W * W;
-                }
-                atomicAdd(&acc[bin], w);
-                atomicAdd(&acc[op.nbins + bin], w * val);
-                atomicAdd(&acc[2 * op.nbins + bin], w * kf * sqrt((double)n2));
             } else {
                 C phi;
                 if constexpr (KIND == OP_NEWTON || KIND == OP_POTENTIAL) {
@@ -468,7 +471,10 @@ __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) k_x_cols(cplx<T>*
                 }
             }
         }
-        if constexpr (KIND == OP_BIN) continue;
+        if constexpr (KIND == OP_BIN) {
+            if (run_bin >= 0) atomicAdd(acc_row + run_bin, (double)run_sum);
+            continue;
+        }
         if constexpr (KIND == OP_POTENTIAL) {
             fft_regs<N, 1, true>(v, t, tw, ex);
     #pragma unroll
@@ -481,11 +487,6 @@ __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) k_x_cols(cplx<T>*
                 out2[pbase + (size_t)(t + m * Q) * N + c] = v[1][m];
             }
         }
-    }
-    if constexpr (KIND == OP_BIN) {
-        __syncthreads();
-        for (int e = tid; e < 3 * op.nbins; e += blockDim.x)
-            if (acc[e] != 0.0) atomicAdd(&op.acc[e], acc[e]);
     }
 }
 
@@ -629,7 +630,7 @@ cudaError_t x_cols_n(cplx<T>* data, cplx<T>* out2, int nplanes, const SpecOp& op
     typedef Shape<T, LOGN> S;
     const int nstage = (KIND == OP_BIN && op.in2 != nullptr) ? 2 : 1;
     const size_t smem = sizeof(cplx<T>) * (S::N + 2 * (size_t)S::N * (S::CB + 1) + nstage * (size_t)S::N * S::CB) +
-                        sizeof(double) * 3 * op.nbins;
+                        (KIND == OP_BIN ? sizeof(T) * (S::M + 1) : 0);
     const void* fn = (const void*)k_x_cols<T, LOGN, KIND>;
     cudaError_t e = set_smem(fn, smem);
     if (e != cudaSuccess) return e;
@@ -637,7 +638,8 @@ cudaError_t x_cols_n(cplx<T>* data, cplx<T>* out2, int nplanes, const SpecOp& op
     e = resident_ctas(fn, S::CB * S::QN, smem, &per_sm);
     if (e != cudaSuccess) return e;
     const int64_t nblk = (int64_t)nplanes * (S::N / S::CB);
-    const int64_t grid = std::min<int64_t>(nblk, (int64_t)per_sm * num_sms());
+    int64_t grid = std::min<int64_t>(nblk, (int64_t)per_sm * num_sms());
+    if (KIND == OP_BIN) grid = std::min<int64_t>(grid, op.acc_rows);  // one row of bin sums per CTA
     k_x_cols<T, LOGN, KIND><<<(unsigned)grid, S::CB * S::QN, smem, st>>>(data, out2, op, nplanes);
     return cudaGetLastError();
 }

@@ -38,7 +38,8 @@ struct SpecOp {
     // power spectrum
     const int16_t* bin_of = nullptr;  // bin per integer |n|^2 (-1 = none)
     const double* wtab = nullptr;     // CIC sinc^2(pi m / n) for m = 0..n/2
-    double* acc = nullptr;            // [3][nbins]: sum w, sum w P, sum w k
+    double* acc = nullptr;            // [acc_rows][nbins]: per-CTA sums of w |delta|^2 / W^2 (zeroed)
+    int acc_rows = 0;                 // rows available (the x pass runs at most this many CTAs)
     int nbins = 0;
     int deconv = 0;
     const void* in2 = nullptr;        // second (y-transformed) field for the cross spectrum
@@ -72,6 +73,8 @@ cudaError_t y_rows_grad3(cplx<T>* A, cplx<T>* B, cplx<T>* C, int64_t nrows, int 
                          cudaStream_t st, const double* kf_arr = nullptr, int64_t rows_per_field = 0);
 template <typename T>
 cudaError_t x_cols(cplx<T>* data, cplx<T>* out2, int nplanes, int n, const SpecOp& op, cudaStream_t st);
+// out[b] = sum_r rows[r nbins + b] in row order (deterministic), r < nrows.
+cudaError_t bin_rows_sum(const double* rows, int nrows, int nbins, double* out, cudaStream_t st);
 // Transposed force chain on the x pass (adjoint): V holds the three y-transformed spectra
 // of the deposited adjoint momenta back to back; out = IFFT_x[sum_j i k_j c(k) FFT_x V_j]
 // with c = coef / (kf^2 |n|^2).
