@@ -1419,12 +1419,10 @@ pm_status pm_fft_r2c(const void* real, void* spec, int n, int precision, void* s
     fw.kind = OP_FWD_STORE;
     fw.fwd = 1;
     if (precision == PM_FP64) {
-        PM_CK(z_r2c<double>((const double*)real, (double2*)spec, n, 1, st));
-        PM_CK((y_rows<double, false>((double2*)spec, (int64_t)(n / 2 + 1) * n, n, st)));
+        PM_CK(forward_zy<double>((const double*)real, (double2*)spec, n, 1, st));
         PM_CK(x_cols<double>((double2*)spec, nullptr, n / 2 + 1, n, fw, st));
     } else {
-        PM_CK(z_r2c<float>((const float*)real, (float2*)spec, n, 1, st));
-        PM_CK((y_rows<float, false>((float2*)spec, (int64_t)(n / 2 + 1) * n, n, st)));
+        PM_CK(forward_zy<float>((const float*)real, (float2*)spec, n, 1, st));
         PM_CK(x_cols<float>((float2*)spec, nullptr, n / 2 + 1, n, fw, st));
     }
     return PM_OK;

@@ -157,17 +157,26 @@ __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 4 : 2) k_z_c2r(Ptr3<T> P
     T* pout = comp == 0 ? P.out[0] : (comp == 1 ? P.out[1] : P.out[2]);
     C* xb = buf;  // gathered half spectrum; the FFT exchanges reuse the buffer afterwards
     constexpr int NT = YB * Q, ITERS = ((M + 1) * YB + NT - 1) / NT;
+    // all of the thread's loads are issued before the first shared-memory store, so the
+    // (M + 1) strided row segments are in flight together
+    C X[ITERS];
 #pragma unroll
     for (int it = 0; it < ITERS; ++it) {
         const int e = tid + it * NT;
-        if (e >= (M + 1) * YB) break;
-        const int k = e / YB, bb = e % YB;
-        C X = inp[spec_row<M>(gl, k, xcl) * N + y0 + bb];
-        if (grad) {  // (-i kz) X, Nyquist kz -> 0
-            const T kz = (k == M) ? T(0) : kf * T(k);
-            X = cmake<C>(X.y * kz, -X.x * kz);
+        if (e < (M + 1) * YB) X[it] = inp[spec_row<M>(gl, e / YB, xcl) * N + y0 + e % YB];
+    }
+#pragma unroll
+    for (int it = 0; it < ITERS; ++it) {
+        const int e = tid + it * NT;
+        if (e < (M + 1) * YB) {
+            const int k = e / YB, bb = e % YB;
+            C Xk = X[it];
+            if (grad) {  // (-i kz) X, Nyquist kz -> 0
+                const T kz = (k == M) ? T(0) : kf * T(k);
+                Xk = cmake<C>(Xk.y * kz, -Xk.x * kz);
+            }
+            xb[bb * RS + LAY::slot(k)] = Xk;
         }
-        xb[bb * RS + LAY::slot(k)] = X;
     }
     __syncthreads();
     // Y_k = (X_k + X*_{M-k}) + i (X_k - X*_{M-k}) exp(+2 pi i k / N), pairs (k, M-k) per thread
