@@ -83,10 +83,11 @@ def step_bytes(np_side, n, fp64):
     return f * (60 * np_side**3 + 40 * n**3)
 
 
-def csrc_sha():
+def csrc_sha(names=None):
+    """Digest of the named files of the CUDA sources (all of them by default)."""
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_2404_02783_gb300", "csrc")
-    for name in sorted(os.listdir(d)):
+    for name in sorted(names if names else os.listdir(d)):
         with open(os.path.join(d, name), "rb") as f:
             h.update(name.encode() + f.read())
     return h.hexdigest()[:16]
@@ -99,7 +100,7 @@ def ncu_traffic(kernel):
         return None
     with open(path) as f:
         d = json.load(f)
-    if d.get("source_sha") != csrc_sha():
+    if d.get("source_sha") != csrc_sha(d.get("sources")):  # the kernel's own sources
         return None
     v = d.get("bytes_per_launch", {}).get(kernel)
     return None if v is None else float(v)

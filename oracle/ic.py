@@ -69,6 +69,47 @@ def za_displacement(delta_k, n, box):
     return psi
 
 
+def za_displacement_at(cosmo, n, box, seed, ids, paired=False):
+    """Psi_j(q) at the lattice nodes of the given particle ids, shape (3, len(ids)) in Mpc/h.
+
+    The same field as za_displacement(linear_delta_k(cosmo, n, box, seed)), evaluated by the
+    direct sum over modes one x frequency at a time, so that memory stays at one plane of
+    modes times the number of nodes (for full-size meshes).  The inverse transform of a
+    Hermitian half spectrum is N^-3 sum over the half grid of w Re(Psi_n exp(2 pi i n.q / N))
+    with w = 1 on the nz = 0 plane and 2 elsewhere (the nz = n/2 plane is zero here).
+    """
+    ids = np.asarray(ids, dtype=np.int64).ravel()
+    q = np.stack([ids // (n * n), (ids // n) % n, ids % n])
+    kf = 2.0 * np.pi / box
+    f = philox.signed_freqs(n)
+    fz = np.arange(n // 2 + 1, dtype=np.int64)
+    NY, NZ = np.meshgrid(f, fz, indexing="ij")
+    w = np.where(NZ == 0, 1.0, 2.0)
+    ey = np.exp(2j * np.pi * np.outer(f, q[1]) / n)    # (n, S)
+    ez = np.exp(2j * np.pi * np.outer(fz, q[2]) / n)   # (n/2+1, S)
+    dNY = np.where(np.abs(NY) == n // 2, 0, NY).astype(np.float64)
+    dNZ = np.where(NZ == n // 2, 0, NZ).astype(np.float64)
+    out = np.zeros((3, ids.size))
+    for ix in range(n):
+        nx = int(f[ix])
+        g = philox.hermitian_noise_plane(seed, n, ix)
+        if paired:
+            g = -g
+        n2 = nx * nx + NY * NY + NZ * NZ
+        pos = n2 > 0
+        pk = np.zeros(n2.shape)
+        pk[pos] = cosmo.power_linear(kf * np.sqrt(n2[pos].astype(np.float64)))
+        inv_k2 = np.zeros(n2.shape)
+        inv_k2[pos] = 1.0 / (kf * kf * n2[pos])
+        dk = n**3 * g * np.sqrt(pk / box**3)
+        ex = np.exp(2j * np.pi * nx * q[0] / n)
+        dnx = 0.0 if abs(nx) == n // 2 else float(nx)
+        for j, Nj in enumerate((dnx, dNY, dNZ)):
+            coef = 1j * kf * Nj * dk * inv_k2 * w
+            out[j] += np.real(ex * np.sum((coef @ ez) * ey, axis=0))
+    return out / n**3
+
+
 def lattice_ticks(n):
     """Lattice node coordinates in ticks, particle id = (ix n + iy) n + iz."""
     step = 2**32 // n

@@ -65,6 +65,17 @@ def signed_freqs(n):
     return np.fft.fftfreq(n, d=1.0 / n).round().astype(np.int64)
 
 
+def _hermitian_noise(seed, n, NX, NY, NZ):
+    """g_n on the given integer wavevectors (nz >= 0) with the rule of hermitian_noise_half."""
+    canonical = (NZ > 0) | ((NZ == 0) & ((NY > 0) | ((NY == 0) & (NX > 0))))
+    cx = np.where(canonical, NX, -NX)
+    cy = np.where(canonical, NY, -NY)
+    g = unit_gaussian_modes(seed, cx, cy, NZ)
+    g = np.where(canonical, g, np.conj(g))
+    zero = (np.abs(NX) == n // 2) | (np.abs(NY) == n // 2) | (NZ == n // 2) | ((NX == 0) & (NY == 0) & (NZ == 0))
+    return np.where(zero, 0.0, g)
+
+
 def hermitian_noise_half(seed, n):
     """g_n on the rfftn half grid (n, n, n/2+1), Hermitian on the nz = 0 plane.
 
@@ -77,12 +88,12 @@ def hermitian_noise_half(seed, n):
     f = signed_freqs(n)
     fz = np.arange(n // 2 + 1, dtype=np.int64)
     NX, NY, NZ = np.meshgrid(f, f, fz, indexing="ij")
-    canonical = (NZ > 0) | ((NZ == 0) & ((NY > 0) | ((NY == 0) & (NX > 0))))
-    cx = np.where(canonical, NX, -NX)
-    cy = np.where(canonical, NY, -NY)
-    g = unit_gaussian_modes(seed, cx, cy, NZ)
-    g = np.where(canonical, g, np.conj(g))
-    nyq = (np.abs(NX) == n // 2) | (np.abs(NY) == n // 2) | (NZ == n // 2)
-    g[nyq] = 0.0
-    g[0, 0, 0] = 0.0
-    return g
+    return _hermitian_noise(seed, n, NX, NY, NZ)
+
+
+def hermitian_noise_plane(seed, n, ix):
+    """hermitian_noise_half(seed, n)[ix]: the (ny, nz) plane of one x frequency."""
+    f = signed_freqs(n)
+    fz = np.arange(n // 2 + 1, dtype=np.int64)
+    NY, NZ = np.meshgrid(f, fz, indexing="ij")
+    return _hermitian_noise(seed, n, np.full_like(NY, f[ix]), NY, NZ)

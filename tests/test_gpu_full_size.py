@@ -1,0 +1,168 @@
+"""Parity at the size of the timed workload: 512^3 particles on a 512^3 mesh, L = 5000 Mpc/h,
+FP32, ZA initial conditions at z = 50 -- the configuration and launch path of bench.py.
+
+The oracle cannot run this workload in seconds, so the checks are (a) outputs the oracle
+computes one by one (the Zel'dovich displacement of sampled particles by direct sums over
+all modes; the P(k) of a seeded field, when the host has the memory for one FP64 FFT of
+the mesh) and (b) properties that hold at any size (a uniformly shifted lattice feels no
+force; total momentum is conserved by the CIC + spectral-gradient force; the density is
+the CIC deposit of the positions at sampled cells)."""
+import numpy as np
+import pytest
+
+import inputs
+from oracle import ic, stats
+from oracle.cosmology import Cosmology
+from tests.gpu_util import lib, rel_l2, to_dev, to_host, torch
+
+pytestmark = pytest.mark.gpu
+
+NP = NMESH = 512
+BOX, A_I, A_F, STEPS = 5000.0, 1.0 / 51.0, 1.0, 100
+TICK = BOX / 2.0**32
+
+
+@pytest.fixture(scope="module")
+def run():
+    pm = lib()
+    r = pm.PMRun(pm.make_config(NP, NMESH, BOX, A_I, A_F, STEPS))
+    yield r
+    del r
+    torch.cuda.empty_cache()
+
+
+def _ticks64(x):
+    """uint32 ticks stored as int32 -> int64 in [0, 2^32)."""
+    return x.to(torch.int64) & 0xFFFFFFFF
+
+
+def test_zeldovich_ics_at_sampled_particles(run):
+    seed = 3
+    run.ic(seed=seed)
+    x, p = run.particles()
+    ids = np.concatenate([[0, NP**3 - 1, NP * NP * 17 + NP * 300 + 5],
+                          inputs.rng(4).integers(0, NP**3, size=11)])
+    idt = torch.from_numpy(ids).cuda()
+    xs = to_host(_ticks64(x[:, idt]))
+    ps = to_host(p[:, idt]).astype(np.float64)
+    c = Cosmology()
+    psi = ic.za_displacement_at(c, NP, BOX, seed, ids)
+    D, f, E = c.growth_D(A_I), c.growth_f(A_I), float(c.E(A_I))
+    p_ref = A_I**2 * E * f * D * psi
+    assert rel_l2(ps, p_ref) < 1e-5
+    assert np.max(np.abs(ps - p_ref)) < 1e-5 * np.max(np.abs(p_ref))
+    q = np.stack([ids // NP**2, (ids // NP) % NP, ids % NP]) * (2**32 // NP)  # lattice node ticks
+    disp = ((xs - q + 2**31) % 2**32 - 2**31) * TICK
+    assert np.max(np.abs(disp - D * psi)) < 1e-5 * np.max(np.abs(D * psi)) + 2 * TICK
+
+
+def test_shifted_lattice_feels_no_force(run):
+    # every cell receives CIC weights summing to one: delta = 0 up to rounding, no force
+    i = torch.arange(NP**3, dtype=torch.int64, device="cuda")
+    q = torch.stack([i // NP**2, (i // NP) % NP, i % NP]) * (2**32 // NP)  # lattice node ticks
+    del i
+    shift = torch.tensor([0.3, 0.55, 0.8], dtype=torch.float64, device="cuda") * 2**32 / NMESH
+    x64 = (q + shift.to(torch.int64)[:, None]) % 2**32
+    del q
+    xd = torch.where(x64 >= 2**31, x64 - 2**32, x64).to(torch.int32).contiguous()  # uint32 bits
+    del x64
+    pd = torch.tensor([1.5, -0.7, 0.2], dtype=torch.float32, device="cuda")[:, None].expand(3, NP**3).contiguous()
+    run.ic(seed=1)  # resets the run to the start of the a-grid
+    import paper_2404_02783_gb300 as pm
+    pm.pm_set_particles(run.ctx, xd, pd)
+    run.step(1)
+    x, p = run.particles()
+    dp = (p.to(torch.float64) - pd.to(torch.float64)).abs().max().item()
+    assert dp < 1e-6
+    dx = ((_ticks64(x) - _ticks64(xd) + 2**31) % 2**32) - 2**31
+    spread = (dx.max(dim=1).values - dx.min(dim=1).values).max().item()
+    assert spread <= 1
+    assert dx[:, 0].abs().min().item() > 0  # the uniform drift moved the particles
+    assert run.density().abs().max().item() < 1e-5
+
+
+def test_za_step_conserves_momentum_and_pulls_along_the_displacement(run):
+    run.ic(seed=1)
+    _, p = run.particles()
+    p0 = p.to(torch.float64)
+    run.step(1)
+    _, p = run.particles()
+    dp = p.to(torch.float64) - p0
+    for j in range(3):
+        total = dp[j].sum().abs().item()
+        scale = dp[j].abs().sum().item()
+        assert scale > 0
+        assert total < 1e-5 * scale
+        # linear theory: the kick is parallel to the ZA displacement, hence to p0
+        r = torch.corrcoef(torch.stack([dp[j], p0[j]]))[0, 1].item()
+        assert r > 0.95
+
+
+def test_density_is_the_cic_deposit_of_the_positions(run):
+    run.ic(seed=2)
+    run.step(2)
+    x, _ = run.particles()
+    delta = run.density()
+    torch.cuda.synchronize()
+    t = _ticks64(x)
+    sh = 32 - 9
+    half = 1 << (sh - 1)
+    base = (t - half) & 0xFFFFFFFF
+    i0 = base >> sh  # lower CIC cell per axis
+    w1 = (base & ((1 << sh) - 1)).to(torch.float64) * 2.0**-sh
+    cells = inputs.rng(6).integers(0, NMESH, size=(12, 3))
+    for c in cells:
+        m = torch.ones(NP**3, dtype=torch.bool, device="cuda")
+        for a in range(3):
+            d = (int(c[a]) - i0[a]) % NMESH
+            m &= d <= 1
+        sel = torch.nonzero(m).squeeze(1)
+        rho = 1.0
+        if sel.numel():
+            w = torch.ones(sel.numel(), dtype=torch.float64, device="cuda")
+            for a in range(3):
+                upper = ((int(c[a]) - i0[a, sel]) % NMESH) == 1
+                w = w * torch.where(upper, w1[a, sel], 1.0 - w1[a, sel])
+            rho = w.sum().item()
+        got = float(delta[c[0], c[1], c[2]]) + 1.0
+        assert abs(got - rho) < 2e-6 * max(1.0, rho)
+
+
+def _mem_available_gb():
+    """Host memory this process may still use: MemAvailable, capped by a cgroup limit."""
+    avail = 0.0
+    try:
+        with open("/proc/meminfo") as f:
+            for line in f:
+                if line.startswith("MemAvailable:"):
+                    avail = int(line.split()[1]) / 2**20
+    except OSError:
+        return 0.0
+    try:
+        with open("/sys/fs/cgroup/memory.max") as f:
+            lim = f.read().strip()
+        with open("/sys/fs/cgroup/memory.current") as f:
+            cur = int(f.read().strip())
+        if lim != "max":
+            avail = min(avail, (int(lim) - cur) / 2**30)
+    except (OSError, ValueError):
+        pass
+    return avail
+
+
+def test_power_spectrum_of_a_full_size_field(run):
+    if _mem_available_gb() < 48:
+        pytest.skip("the FP64 oracle spectrum of a 512^3 mesh needs about 20 GB of host memory")
+    f = inputs.lognormal_field(11, NMESH, sigma=0.5)
+    f32 = f.astype(np.float32)
+    edges = stats.log_edges(32, 1.0, NMESH / 2.0)
+    k, pk, nm = run.power(edges, field=to_dev(f32))
+    del f
+    ko, po, nmo = stats.power_spectrum(f32.astype(np.float64), BOX, edges)
+    assert np.array_equal(nm, nmo)
+    ok = nmo > 0
+    # the oracle sums kf |n| over up to ~1e7 modes a bin in FP64 (the library sums its
+    # per-|n|^2 mode counts): both agree to the rounding of the long sum
+    np.testing.assert_allclose(k[ok], ko[ok], rtol=1e-10)
+    # a 512^3 FP32 transform: a few 1e-7 per mode, bins of as few as 6 modes
+    np.testing.assert_allclose(pk[ok], po[ok], rtol=5e-6)

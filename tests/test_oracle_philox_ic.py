@@ -98,3 +98,19 @@ def test_zeldovich_particles_fixed_and_float_agree():
     d -= np.rint(d)
     assert np.max(np.abs(d)) <= 2**-32
     assert abs(pt.mean()) < 1e-12 * np.abs(pt).max()
+
+
+def test_plane_noise_and_direct_mode_sum_match_the_full_grid():
+    # the one-plane-at-a-time forms used for full-size meshes against the full-grid FFT forms
+    c = Cosmology()
+    for n, box, seed in ((16, 300.0, 7), (32, 700.0, 11)):
+        g = philox.hermitian_noise_half(seed, n)
+        for i in range(n):
+            assert np.array_equal(philox.hermitian_noise_plane(seed, n, i), g[i])
+        psi = ic.za_displacement(ic.linear_delta_k(c, n, box, seed=seed), n, box).reshape(3, -1)
+        ids = np.array([0, 1, n * n * 3 + n * 5 + 7, n**3 - 1, 977 % n**3])
+        got = ic.za_displacement_at(c, n, box, seed, ids)
+        assert np.max(np.abs(got - psi[:, ids])) < 1e-12 * np.max(np.abs(psi))
+    # paired phases flip the sign
+    assert np.allclose(ic.za_displacement_at(c, 16, 300.0, 7, [5], paired=True),
+                       -ic.za_displacement_at(c, 16, 300.0, 7, [5]), rtol=0, atol=0)
