@@ -312,7 +312,11 @@ cudaError_t adj_kick_particles(const uint32_t* x, int64_t count, int n, float* v
 
 cudaError_t deposit_vec(const uint32_t* x, int np, int n, const float* v, float* const* V, cudaStream_t st) {
     const int lognp = ilog2(np), logn = ilog2(n);
-    const int run = np < 16 ? np : 16;
+    // rows of `run` particles a thread: long rows share more corners, short rows give more
+    // threads; about two waves of full occupancy when the lattice is small
+    int run = 4;
+    while (run < 16 && (int64_t)np * np * np / run > 2 * 152 * 2048) run *= 2;
+    if (run > np) run = np;
     const int64_t threads = (int64_t)np * np * (np / run);
     const unsigned blocks = (unsigned)((threads + 255) / 256);
     const float inv = (float)ldexp(1.0, -(32 - logn));

@@ -130,6 +130,11 @@ struct pm_ctx {
     // instead of L.force (the gradient's forward re-run writes them straight into its record)
     void* force_at = nullptr;
     void* force(int j) { return force_at ? (void*)((char*)force_at + (size_t)j * n * n * n * sT()) : at(L.force[j]); }
+    // when set, the positions of the step are read from x_at and the fused update writes the
+    // drifted ones to x_out (the gradient's re-run records each step's positions this way)
+    void* x_at = nullptr;
+    void* x_out = nullptr;
+    void* xpos() { return x_at ? x_at : at(L.x); }
     // per-phase timing (pm_profile / pm_timings)
     bool prof = false;
     std::vector<cudaEvent_t> pool;
@@ -148,7 +153,10 @@ struct pm_ctx {
         cudaEventCreate(&e);
         return e;
     }
+    // second stream of the gradient's overlapped forward re-runs (created on first use)
+    cudaStream_t st2 = nullptr;
     ~pm_ctx() {
+        if (st2) cudaStreamDestroy(st2);
         for (auto& r : recs) {
             cudaEventDestroy(r.a);
             cudaEventDestroy(r.b);
@@ -196,7 +204,7 @@ pm_status deposit_particles(pm_ctx* c, void* rho) {
     Phase ph(c, PM_PHASE_DEPOSIT);
     PM_CK(cudaMemsetAsync(rho, 0, c->sT() * (size_t)c->n * c->n * c->n, c->st));
     const double mass = std::pow((double)c->n / c->np, 3);
-    PM_CK(deposit_lattice(c->at(c->L.x), c->np, c->cfg.precision, c->n, mass, rho, c->st));
+    PM_CK(deposit_lattice(c->xpos(), c->np, c->cfg.precision, c->n, mass, rho, c->st));
     return PM_OK;
 }
 
@@ -260,11 +268,13 @@ pm_status kick_drift(pm_ctx* c, double kick, double drift) {
     Phase ph(c, PM_PHASE_KICK_DRIFT);
     void* g[3] = {c->force(0), c->force(1), c->force(2)};
     if (fused_update(c)) {
-        PM_CK(interp_kick_drift_deposit(c->at(c->L.x), c->at(c->L.p), c->np, c->cfg.precision, c->n, g, kick, drift,
-                                        c->cfg.box, std::pow((double)c->n / c->np, 3), c->at(c->L.rho), c->st));
+        PM_CK(interp_kick_drift_deposit(c->xpos(), c->at(c->L.p), c->np, c->cfg.precision, c->n, g, kick, drift,
+                                        c->cfg.box, std::pow((double)c->n / c->np, 3), c->at(c->L.rho), c->st, 1,
+                                        nullptr, c->x_out));
         c->rho_valid = true;
         return PM_OK;
     }
+    if (c->x_at || c->x_out) return fail(PM_ERR_UNSUPPORTED, "out-of-place positions need the fused update");
     PM_CK(interp_kick_drift(c->at(c->L.x), c->at(c->L.p), c->np3, c->cfg.precision, c->n, g, kick, drift,
                             c->cfg.box, c->st));
     return PM_OK;
@@ -829,7 +839,11 @@ pm_status pm_bispectrum(pm_ctx* c, const void* field, int nbins, const double* e
 namespace {
 
 struct AdjLayout {
-    size_t ckpt = 0, seg_x = 0, seg_g = 0, lam_u = 0, lam_p = 0, acc = 0, total = 0;
+    // two segment records (positions and force meshes of C steps) so that the re-run of one
+    // segment overlaps the reverse sweep of the next; the re-runs' own density, spectra and
+    // end positions
+    size_t ckpt = 0, seg_x[2] = {0, 0}, seg_g[2] = {0, 0}, lam_u = 0, lam_p = 0, acc = 0;
+    size_t re_rho = 0, re_spec[3] = {0, 0, 0}, re_x = 0, total = 0;
     int nseg = 0, C = 0;
 };
 
@@ -845,12 +859,18 @@ AdjLayout adj_plan(const pm_ctx* c, int C) {
         off = align256(off + bytes);
         return o;
     };
+    const size_t n = c->n, spec = 2 * (n / 2 + 1) * n * n * 4;
     A.ckpt = take((size_t)A.nseg * 2 * P);
-    A.seg_x = take((size_t)C * P);
-    A.seg_g = take((size_t)C * G);
+    for (int b = 0; b < 2; ++b) {
+        A.seg_x[b] = take((size_t)C * P);
+        A.seg_g[b] = take((size_t)C * G);
+    }
     A.lam_u = take(P);
     A.lam_p = take(P);
     A.acc = take(8);
+    A.re_rho = take(n * n * n * 4);
+    for (int j = 0; j < 3; ++j) A.re_spec[j] = take(spec);
+    A.re_x = take(P);
     A.total = off;
     return A;
 }
@@ -881,6 +901,7 @@ pm_status fft_inverse_f32(pm_ctx* c, float2* spec, float* real, int n) {
 
 // lambda_u += K J(u)^T lambda_p at positions xs with force meshes gs (three n^3 meshes),
 // then lambda_p += drift_next lambda_u (the transposed drift of the step before; 0: none).
+// V (the context's force meshes) is zero on entry and left zero.
 pm_status adj_kick(pm_ctx* c, const uint32_t* xs, const float* gs, double K, float* lam_u, float* lam_p,
                    double drift_next) {
     const int n = c->n;
@@ -888,14 +909,15 @@ pm_status adj_kick(pm_ctx* c, const uint32_t* xs, const float* gs, double K, flo
     const float* G[3] = {gs, gs + n3, gs + 2 * n3};
     // V_j and the spectra are three meshes back to back (256-byte multiples): one batched transform
     float* V[3] = {(float*)c->at(c->L.force[0]), (float*)c->at(c->L.force[1]), (float*)c->at(c->L.force[2])};
-    PM_CK(cudaMemsetAsync(V[0], 0, 3 * n3 * 4, c->st));
     PM_CK(deposit_vec(xs, c->np, n, lam_p, V, c->st));
     float2* sp[3] = {(float2*)c->at(c->L.spec[0]), (float2*)c->at(c->L.spec[1]), (float2*)c->at(c->L.spec[2])};
     // forward z and y passes of the three meshes, then the x pass that combines them
-    // (sum_j i k_j C V_j) and transforms back, then the inverse y and z passes
+    // (sum_j i k_j C V_j), transforms back and clears V for the next deposit, then the
+    // inverse y and z passes
     PM_CK(forward_zy<float>(V[0], sp[0], n, 3, c->st));
     // in place over field 0: each CTA reads and writes only its own columns
-    PM_CK(x_adj<float>(sp[0], sp[0], n, c->kf, -1.5 * c->cfg.omega_m / ((double)n * n * n), c->st));
+    PM_CK(x_adj<float>(sp[0], sp[0], n, c->kf, -1.5 * c->cfg.omega_m / ((double)n * n * n), c->st, V[0],
+                       3 * (int64_t)n3));
     float* rho_bar = (float*)c->at(c->L.rho);
     PM_CK((y_rows<float, true>(sp[0], (int64_t)(n / 2 + 1) * n, n, c->st)));
     const float2* zin[1] = {sp[0]};
@@ -927,6 +949,7 @@ pm_status pm_loss_grad(pm_ctx* c, const void* white_noise, const void* target, i
     const AdjLayout A = adj_plan(c, C);
     if (!scratch || scratch_bytes < A.total || (uintptr_t)scratch % 256)
         return fail(PM_ERR_WORKSPACE, "adjoint scratch too small or not 256-byte aligned");
+    if (!c->st2) PM_CK(cudaStreamCreateWithFlags(&c->st2, cudaStreamNonBlocking));
     unsigned char* sc = (unsigned char*)scratch;
     const int n = c->n, np = c->np;
     const size_t n3 = (size_t)n * n * n, P = 3 * (size_t)c->np3 * 4;
@@ -943,78 +966,145 @@ pm_status pm_loss_grad(pm_ctx* c, const void* white_noise, const void* target, i
     };
     auto drift_of = [&](int s) { return pmhost::drift_integral(c->cosmo, c->a_grid(s), c->a_grid(s + 1)); };
     const size_t Gb = 3 * n3 * 4;
-    // steps s0..s1-1 from the current state, keeping each step's positions and force meshes
-    auto record = [&](int s0, int s1) -> pm_status {
+    auto seg_x = [&](int k, int i) { return at(A.seg_x[k & 1] + (size_t)i * P); };
+    auto seg_g = [&](int k, int i) { return at(A.seg_g[k & 1] + (size_t)i * Gb); };
+    // Steps s0..s1-1 of segment k on context r from the positions at rx (p in place), keeping
+    // each step's positions and force meshes in record k & 1.  With the fused update each
+    // step reads its positions from the record and writes the drifted ones into the next
+    // slot (the last step's to x_end), so only the segment's first positions are copied.
+    const bool oop = fused_update(c);
+    auto record = [&](pm_ctx* r, int k, void* rx, void* x_end) -> pm_status {
+        const int s0 = k * C, s1 = std::min(S, s0 + C);
+        if (oop) PM_CK(cudaMemcpyAsync(seg_x(k, 0), rx, P, cudaMemcpyDeviceToDevice, r->st));
         for (int s = s0; s < s1; ++s) {
-            PM_CK(cudaMemcpyAsync(at(A.seg_x + (size_t)(s - s0) * P), x, P, cudaMemcpyDeviceToDevice, c->st));
-            c->force_at = at(A.seg_g + (size_t)(s - s0) * Gb);
-            pm_status st = compute_forces(c, c->a_grid(s));
-            if (st == PM_OK) st = kick_drift(c, kick_of(s), drift_of(s));
-            c->force_at = nullptr;
+            void* xs = seg_x(k, s - s0);
+            if (oop) {
+                r->x_at = xs;
+                r->x_out = (s + 1 < s1) ? seg_x(k, s + 1 - s0) : x_end;
+            } else {
+                PM_CK(cudaMemcpyAsync(xs, r->xpos(), P, cudaMemcpyDeviceToDevice, r->st));
+            }
+            r->force_at = seg_g(k, s - s0);
+            pm_status st = compute_forces(r, r->a_grid(s));
+            if (st == PM_OK) st = kick_drift(r, kick_of(s), drift_of(s));
+            r->force_at = nullptr;
+            r->x_at = r->x_out = nullptr;
             if (st != PM_OK) return st;
-            c->step = s + 1;
-            c->synced = false;
+            r->step = s + 1;
+            r->synced = false;
         }
         return PM_OK;
     };
-    // ---- forward with checkpoints; the last segment is recorded as it runs.  The closing
-    // half kick after the last step changes only p, which the loss does not see, so it is
-    // neither run nor transposed.
-    PM_TRY(pm_ic_zeldovich(c, 0, white_noise, 0));
+    // The re-runs run on a context of their own: the second stream, density and spectra in
+    // the scratch, p and (without the fused update) x in place over the segment's checkpoint
+    // (each checkpoint is used once).  They overlap the forward run and the reverse sweep.
+    pm_ctx re = *c;
+    re.pool.clear();
+    re.recs.clear();
+    re.prof = false;
+    re.st = c->st2;
+    re.st2 = nullptr;
+    re.ws = sc;
+    re.L.rho = A.re_rho;
+    for (int j = 0; j < 3; ++j) re.L.spec[j] = A.re_spec[j];
+    std::vector<cudaEvent_t> evs;
+    auto event = [&]() {
+        cudaEvent_t e = nullptr;
+        if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) == cudaSuccess) evs.push_back(e);
+        return e;
+    };
+    std::vector<cudaEvent_t> ev_ckpt(A.nseg), ev_rerun(A.nseg), ev_rev(A.nseg);
     for (int k = 0; k < A.nseg; ++k) {
-        const int s0 = k * C, s1 = std::min(S, s0 + C);
-        PM_CK(cudaMemcpyAsync(at(A.ckpt + (size_t)k * 2 * P), x, P, cudaMemcpyDeviceToDevice, c->st));
-        PM_CK(cudaMemcpyAsync(at(A.ckpt + (size_t)k * 2 * P + P), p, P, cudaMemcpyDeviceToDevice, c->st));
-        if (k < A.nseg - 1) PM_TRY(pm_step(c, s1 - s0));
-        else PM_TRY(record(s0, s1));
+        ev_ckpt[k] = event();
+        ev_rerun[k] = event();
+        ev_rev[k] = event();
     }
-    // ---- loss and its mesh adjoint
-    float* rho = (float*)c->at(c->L.rho);
-    PM_CK(fill(rho, (int64_t)n3, PM_FP32_FIXED, -1.0, c->st));
-    PM_CK(deposit_lattice(x, np, PM_FP32_FIXED, n, mass, rho, c->st));
-    c->rho_valid = false;
-    double* acc = (double*)at(A.acc);
-    PM_CK(cudaMemsetAsync(acc, 0, 8, c->st));
-    PM_CK(loss_mse(rho, (const float*)target, (int64_t)n3, acc, c->st));
-    double hsum = 0.0;
-    PM_CK(cudaMemcpyAsync(&hsum, acc, 8, cudaMemcpyDeviceToHost, c->st));
-    PM_CK(cudaStreamSynchronize(c->st));
-    *loss_out = hsum / (double)n3;
-    PM_CK(adj_gather((const uint32_t*)x, c->np3, n, rho, (float)mass, 0, lam_u, c->st));
-    // lam_p = 0 after the closing kick; the transposed drift of the last step gives lam_p
-    PM_CK(axpby(lam_p, lam_u, nullptr, 3 * c->np3, (float)(drift_of(S - 1) / box), 0.0f, c->st));
-    // ---- reverse sweep, segment by segment: kick of step s, then the drift of step s - 1
-    for (int k = A.nseg - 1; k >= 0; --k) {
-        const int s0 = k * C, s1 = std::min(S, s0 + C);
-        if (k < A.nseg - 1) {
-            PM_CK(cudaMemcpyAsync(x, at(A.ckpt + (size_t)k * 2 * P), P, cudaMemcpyDeviceToDevice, c->st));
-            PM_CK(cudaMemcpyAsync(p, at(A.ckpt + (size_t)k * 2 * P + P), P, cudaMemcpyDeviceToDevice, c->st));
-            c->step = s0;
-            c->synced = (s0 == 0);
-            c->rho_valid = false;
-            PM_TRY(record(s0, s1));
+    pm_status status = (int)evs.size() == 3 * A.nseg ? PM_OK : fail(PM_ERR_CUDA, "cudaEventCreate failed");
+    auto rerun = [&](int k) -> pm_status {
+        PM_CK(cudaStreamWaitEvent(re.st, ev_ckpt[k], 0));
+        if (k + 2 < A.nseg) PM_CK(cudaStreamWaitEvent(re.st, ev_rev[k + 2], 0));  // record k & 1 is free
+        re.L.x = A.ckpt + (size_t)k * 2 * P;
+        re.L.p = re.L.x + P;
+        re.step = k * C;
+        re.synced = (k == 0);
+        re.rho_valid = false;
+        PM_TRY(record(&re, k, re.at(re.L.x), at(A.re_x)));
+        PM_CK(cudaEventRecord(ev_rerun[k], re.st));
+        return PM_OK;
+    };
+    auto body = [&]() -> pm_status {
+        // ---- forward with checkpoints; the last two segments are recorded as they run (one
+        // record each), so the reverse sweep starts without a re-run.  The closing half kick
+        // after the last step changes only p, which the loss does not see, so it is neither
+        // run nor transposed.
+        PM_TRY(pm_ic_zeldovich(c, 0, white_noise, 0));
+        for (int k = 0; k < A.nseg; ++k) {
+            const int s0 = k * C, s1 = std::min(S, s0 + C);
+            PM_CK(cudaMemcpyAsync(at(A.ckpt + (size_t)k * 2 * P), x, P, cudaMemcpyDeviceToDevice, c->st));
+            PM_CK(cudaMemcpyAsync(at(A.ckpt + (size_t)k * 2 * P + P), p, P, cudaMemcpyDeviceToDevice, c->st));
+            PM_CK(cudaEventRecord(ev_ckpt[k], c->st));
+            if (k < A.nseg - 2) PM_TRY(pm_step(c, s1 - s0));
+            else PM_TRY(record(c, k, x, x));
         }
-        for (int s = s1 - 1; s >= s0; --s)
-            PM_TRY(adj_kick(c, (const uint32_t*)at(A.seg_x + (size_t)(s - s0) * P),
-                            (const float*)at(A.seg_g + (size_t)(s - s0) * Gb), kick_of(s), lam_u, lam_p,
-                            s > 0 ? drift_of(s - 1) / box : 0.0));
+        // ---- loss and its mesh adjoint
+        float* rho = (float*)c->at(c->L.rho);
+        PM_CK(fill(rho, (int64_t)n3, PM_FP32_FIXED, -1.0, c->st));
+        PM_CK(deposit_lattice(x, np, PM_FP32_FIXED, n, mass, rho, c->st));
+        c->rho_valid = false;
+        double* acc = (double*)at(A.acc);
+        PM_CK(cudaMemsetAsync(acc, 0, 8, c->st));
+        PM_CK(loss_mse(rho, (const float*)target, (int64_t)n3, acc, c->st));
+        PM_CK(cudaMemsetAsync(c->at(c->L.force[0]), 0, 3 * n3 * 4, c->st));  // V for the first adjoint deposit
+        PM_CK(adj_gather((const uint32_t*)x, c->np3, n, rho, (float)mass, 0, lam_u, c->st));
+        // lam_p = 0 after the closing kick; the transposed drift of the last step gives lam_p
+        PM_CK(axpby(lam_p, lam_u, nullptr, 3 * c->np3, (float)(drift_of(S - 1) / box), 0.0f, c->st));
+        // ---- reverse sweep, segment by segment (kick of step s, then the drift of step
+        // s - 1); the re-run of segment k - 2 (into the record segment k has just released)
+        // overlaps the reverse sweep of segment k - 1
+        for (int k = A.nseg - 1; k >= 0; --k) {
+            const int s0 = k * C, s1 = std::min(S, s0 + C);
+            if (k < A.nseg - 2) PM_CK(cudaStreamWaitEvent(c->st, ev_rerun[k], 0));
+            for (int s = s1 - 1; s >= s0; --s)
+                PM_TRY(adj_kick(c, (const uint32_t*)seg_x(k, s - s0), (const float*)seg_g(k, s - s0), kick_of(s),
+                                lam_u, lam_p, s > 0 ? drift_of(s - 1) / box : 0.0));
+            PM_CK(cudaEventRecord(ev_rev[k], c->st));
+            if (k >= 2) PM_TRY(rerun(k - 2));
+        }
+        // ---- transposed Zel'dovich map: grad = sum_j A_j^T (D/L lam_u_j + a^2 E f D lam_p_j)
+        const double a = c->cfg.a_init;
+        const double D = pmhost::growth_D(c->cosmo, a), f = pmhost::growth_f(c->cosmo, a),
+                     E = pmhost::E(c->cosmo, a);
+        const int64_t np3 = c->np3;
+        float* s_j[3] = {(float*)c->at(c->L.force[0]), (float*)c->at(c->L.force[1]), (float*)c->at(c->L.force[2])};
+        float2* sp[3] = {(float2*)c->at(c->L.spec[0]), (float2*)c->at(c->L.spec[1]), (float2*)c->at(c->L.spec[2])};
+        for (int j = 0; j < 3; ++j) {
+            PM_CK(axpby(s_j[j], lam_u + j * np3, lam_p + j * np3, np3, (float)(D / box), (float)(a * a * E * f * D),
+                        c->st));
+            PM_TRY(fft_forward_f32(c, s_j[j], sp[j], np));
+        }
+        const float2* in[3] = {sp[0], sp[1], sp[2]};
+        PM_CK(adj_combine(in, sp[0], np, c->kf, -std::pow((double)np, -1.5), (const double*)c->at(c->L.amp), 1,
+                          c->st));
+        PM_TRY(fft_inverse_f32(c, sp[0], (float*)grad_out, np));
+        return PM_OK;
+    };
+    double hsum = 0.0;
+    if (status == PM_OK) status = body();
+    if (status == PM_OK) {
+        cudaError_t e = cudaMemcpyAsync(&hsum, at(A.acc), 8, cudaMemcpyDeviceToHost, c->st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
+        if (e != cudaSuccess) status = fail(PM_ERR_CUDA, cudaGetErrorString(e));
     }
-    // ---- transposed Zel'dovich map: grad = sum_j A_j^T (D/L lam_u_j + a^2 E f D lam_p_j)
-    const double a = c->cfg.a_init;
-    const double D = pmhost::growth_D(c->cosmo, a), f = pmhost::growth_f(c->cosmo, a), E = pmhost::E(c->cosmo, a);
-    const int64_t np3 = c->np3;
-    float* s_j[3] = {(float*)c->at(c->L.force[0]), (float*)c->at(c->L.force[1]), (float*)c->at(c->L.force[2])};
-    float2* sp[3] = {(float2*)c->at(c->L.spec[0]), (float2*)c->at(c->L.spec[1]), (float2*)c->at(c->L.spec[2])};
-    for (int j = 0; j < 3; ++j) {
-        PM_CK(axpby(s_j[j], lam_u + j * np3, lam_p + j * np3, np3, (float)(D / box), (float)(a * a * E * f * D),
-                    c->st));
-        PM_TRY(fft_forward_f32(c, s_j[j], sp[j], np));
-    }
-    const float2* in[3] = {sp[0], sp[1], sp[2]};
-    PM_CK(adj_combine(in, sp[0], np, c->kf, -std::pow((double)np, -1.5), (const double*)c->at(c->L.amp), 1, c->st));
-    PM_TRY(fft_inverse_f32(c, sp[0], (float*)grad_out, np));
+    // the second stream is idle here on success; after an error wait for it before the
+    // scratch goes back to the caller
+    cudaStreamSynchronize(re.st);
+    for (auto e : evs) cudaEventDestroy(e);
+    // the context holds the forward run's last positions and momenta (before the closing kick)
+    c->step = S;
+    c->synced = false;
     c->rho_valid = false;
-    return PM_OK;
+    if (status == PM_OK) *loss_out = hsum / (double)n3;
+    return status;
 }
 
 }  // extern "C"

@@ -508,7 +508,8 @@ __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) k_x_cols(cplx<T>*
 template <typename T, int LOGN>
 __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) k_x_adj(const cplx<T>* V,
                                                                       cplx<T>* out, double kf,
-                                                                      double coef) {
+                                                                      double coef, float4* __restrict__ zero,
+                                                                      int64_t nzero4) {
     typedef cplx<T> C;
     typedef Shape<T, LOGN> S;
     constexpr int N = S::N, M = S::M, Q = S::QN, CB = S::CB;
@@ -523,6 +524,11 @@ __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) k_x_adj(const cpl
     const size_t pbase = (size_t)kz * N * N;
     const size_t field = (size_t)(M + 1) * N * N;
     load_stage_twiddles<T, N>(tw);
+    {  // side job: clear `zero` (a buffer the caller has finished with), grid-stride
+        const int64_t nthr = (int64_t)gridDim.x * gridDim.y * blockDim.x;
+        for (int64_t e = ((int64_t)blockIdx.y * gridDim.x + blockIdx.x) * blockDim.x + tid; e < nzero4; e += nthr)
+            zero[e] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
     const T kfT = T(kf);
     const T coefT = T(coef) / (kfT * kfT);
     const int ny = (c < M) ? c : c - N;
@@ -654,12 +660,15 @@ cudaError_t x_cols_n(cplx<T>* data, cplx<T>* out2, int nplanes, const SpecOp& op
 }
 
 template <typename T, int LOGN>
-cudaError_t x_adj_n(const cplx<T>* V, cplx<T>* out, double kf, double coef, cudaStream_t st) {
+cudaError_t x_adj_n(const cplx<T>* V, cplx<T>* out, double kf, double coef, float* zero, int64_t nzero,
+                    cudaStream_t st) {
     typedef Shape<T, LOGN> S;
     const size_t smem = sizeof(cplx<T>) * (S::N + 2 * (size_t)S::N * (S::CB + 1));
     cudaError_t e = set_smem((const void*)k_x_adj<T, LOGN>, smem);
     if (e != cudaSuccess) return e;
-    k_x_adj<T, LOGN><<<dim3(S::N / S::CB, S::M + 1), S::CB * S::QN, smem, st>>>(V, out, kf, coef);
+    if (nzero % 4 != 0 || (zero && (uintptr_t)zero % 16 != 0)) return cudaErrorInvalidValue;
+    k_x_adj<T, LOGN><<<dim3(S::N / S::CB, S::M + 1), S::CB * S::QN, smem, st>>>(V, out, kf, coef, (float4*)zero,
+                                                                                zero ? nzero / 4 : 0);
     return cudaGetLastError();
 }
 
@@ -717,8 +726,9 @@ cudaError_t y_rows_grad3(cplx<T>* A, cplx<T>* B, cplx<T>* Cc, int64_t nrows, int
 }
 
 template <typename T>
-cudaError_t x_adj(const cplx<T>* V, cplx<T>* out, int n, double kf, double coef, cudaStream_t st) {
-    PM_DISPATCH_LOGN(n, (x_adj_n<T, LG>(V, out, kf, coef, st)))
+cudaError_t x_adj(const cplx<T>* V, cplx<T>* out, int n, double kf, double coef, cudaStream_t st, float* zero,
+                  int64_t nzero) {
+    PM_DISPATCH_LOGN(n, (x_adj_n<T, LG>(V, out, kf, coef, zero, nzero, st)))
 }
 
 template <typename T>
@@ -747,7 +757,8 @@ cudaError_t x_cols(cplx<T>* data, cplx<T>* out2, int nplanes, int n, const SpecO
                                          cudaStream_t, const double*, int64_t);                        \
     template cudaError_t x_cols<T>(cplx<T>*, cplx<T>*, int, int, const SpecOp&, cudaStream_t);      \
     template cudaError_t forward_zy<T>(const T*, cplx<T>*, int, int, cudaStream_t);                     \
-    template cudaError_t x_adj<T>(const cplx<T>*, cplx<T>*, int, double, double, cudaStream_t);         \
+    template cudaError_t x_adj<T>(const cplx<T>*, cplx<T>*, int, double, double, cudaStream_t, float*, \
+                                  int64_t);                                                             \
     template cudaError_t inverse_yz_grad<T>(cplx<T>*, cplx<T>*, cplx<T>*, T* const*, int, int, double,   \
                                             cudaStream_t, const double*);
 

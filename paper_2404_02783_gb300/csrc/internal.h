@@ -77,9 +77,11 @@ cudaError_t x_cols(cplx<T>* data, cplx<T>* out2, int nplanes, int n, const SpecO
 cudaError_t bin_rows_sum(const double* rows, int nrows, int nbins, double* out, cudaStream_t st);
 // Transposed force chain on the x pass (adjoint): V holds the three y-transformed spectra
 // of the deposited adjoint momenta back to back; out = IFFT_x[sum_j i k_j c(k) FFT_x V_j]
-// with c = coef / (kf^2 |n|^2).
+// with c = coef / (kf^2 |n|^2).  Also sets zero[0 .. nzero) to 0 (a buffer the caller is
+// done with; nzero a multiple of 4, zero 16-byte aligned; null: nothing).
 template <typename T>
-cudaError_t x_adj(const cplx<T>* V, cplx<T>* out, int n, double kf, double coef, cudaStream_t st);
+cudaError_t x_adj(const cplx<T>* V, cplx<T>* out, int n, double kf, double coef, cudaStream_t st,
+                  float* zero = nullptr, int64_t nzero = 0);
 // Forward z (r2c) and y passes of `batch` real meshes into spec ([field][kz][kx][ky]
 // before the x pass).
 template <typename T>

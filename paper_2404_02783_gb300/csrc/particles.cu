@@ -467,7 +467,7 @@ cudaError_t interp_kick_drift(void* x, void* p, int64_t count, int precision, in
 // blockIdx.y selects the field of a batch of independent runs stored back to back
 // (particles [field][3][np^3], meshes [field][n^3]); scale = 2^32 / L of that field.
 template <int R>
-__global__ void __launch_bounds__(512, 2) k_ikd_deposit(uint32_t* __restrict__ x, float* __restrict__ p, int lognp,
+__global__ void __launch_bounds__(512, 2) k_ikd_deposit(const uint32_t* x, uint32_t* xo, float* __restrict__ p, int lognp,
                                                      int logn, float inv_cell_ticks, const float* __restrict__ gx,
                                                      const float* __restrict__ gy, const float* __restrict__ gz,
                                                      float kick, double drift, double scale0,
@@ -483,6 +483,7 @@ __global__ void __launch_bounds__(512, 2) k_ikd_deposit(uint32_t* __restrict__ x
         const int64_t fb = blockIdx.y;
         const int64_t n3 = (int64_t)1 << (3 * logn);
         x += fb * 3 * count;
+        xo += fb * 3 * count;
         p += fb * 3 * count;
         gx += fb * n3;
         gy += fb * n3;
@@ -521,9 +522,9 @@ __global__ void __launch_bounds__(512, 2) k_ikd_deposit(uint32_t* __restrict__ x
         p[id] = p0;
         p[count + id] = p1;
         p[2 * count + id] = p2;
-        x[id] = u0;
-        x[count + id] = u1;
-        x[2 * count + id] = u2;
+        xo[id] = u0;
+        xo[count + id] = u1;
+        xo[2 * count + id] = u2;
         tile_deposit<D>(lo, carry, rho, u0, u1, u2, logn, inv_cell_ticks, ox, oy, oz, mass);
     }
     __syncthreads();
@@ -537,7 +538,7 @@ __global__ void __launch_bounds__(512, 2) k_ikd_deposit(uint32_t* __restrict__ x
 // carries the upper-plane weights in registers, adds them to the next particle's
 // lower-plane weights and issues 4 tile atomics a particle instead of 8.  Any other
 // particle takes the full path, so the result is the same CIC gather and deposit.
-__global__ void __launch_bounds__(512, 2) k_ikd_deposit_sweep(uint32_t* __restrict__ x, float* __restrict__ p,
+__global__ void __launch_bounds__(512, 2) k_ikd_deposit_sweep(const uint32_t* x, uint32_t* xo, float* __restrict__ p,
                                                               int lognp, int logn, float inv_cell_ticks,
                                                               const float* __restrict__ gx,
                                                               const float* __restrict__ gy,
@@ -555,6 +556,7 @@ __global__ void __launch_bounds__(512, 2) k_ikd_deposit_sweep(uint32_t* __restri
         const int64_t fb = blockIdx.y;
         const int64_t n3 = (int64_t)1 << (3 * logn);
         x += fb * 3 * count;
+        xo += fb * 3 * count;
         p += fb * 3 * count;
         gx += fb * n3;
         gy += fb * n3;
@@ -649,9 +651,9 @@ __global__ void __launch_bounds__(512, 2) k_ikd_deposit_sweep(uint32_t* __restri
         p[id] = p0;
         p[count + id] = p1;
         p[2 * count + id] = p2;
-        x[id] = u0;
-        x[count + id] = u1;
-        x[2 * count + id] = u2;
+        xo[id] = u0;
+        xo[count + id] = u1;
+        xo[2 * count + id] = u2;
         // ---- deposit at the new position
         {
             const CicF cx = cic_ticks(u0, logn, inv_cell_ticks);
@@ -718,7 +720,7 @@ __global__ void __launch_bounds__(512, 2) k_ikd_deposit_sweep(uint32_t* __restri
 template <int R>
 static cudaError_t ikd_deposit_r(void* x, void* p, int np, int n, void* const* g, double kick, double drift,
                                  double box, double mass, void* rho, cudaStream_t st, int nfields,
-                                 const double* scale_arr) {
+                                 const double* scale_arr, void* x_out) {
     typedef DepTile<R> D;
     const int lognp = ilog2(np), logn = ilog2(n);
     const unsigned blocks = (unsigned)((np / D::TX) * (np / D::TY) * (np / D::TZ));
@@ -728,13 +730,15 @@ static cudaError_t ikd_deposit_r(void* x, void* p, int np, int n, void* const* g
         cudaError_t e = set_smem_once((const void*)k_ikd_deposit_sweep, smem);
         if (e != cudaSuccess) return e;
         k_ikd_deposit_sweep<<<dim3(blocks, nfields), 512, smem, st>>>(
-            (uint32_t*)x, (float*)p, lognp, logn, inv, (const float*)g[0], (const float*)g[1], (const float*)g[2],
+            (const uint32_t*)x, (uint32_t*)(x_out ? x_out : x), (float*)p, lognp, logn, inv, (const float*)g[0],
+            (const float*)g[1], (const float*)g[2],
             (float)kick, drift, 4294967296.0 / box, scale_arr, (float)mass, (float*)rho);
     } else {
         cudaError_t e = set_smem_once((const void*)k_ikd_deposit<R>, smem);
         if (e != cudaSuccess) return e;
         k_ikd_deposit<R><<<dim3(blocks, nfields), 512, smem, st>>>(
-            (uint32_t*)x, (float*)p, lognp, logn, inv, (const float*)g[0], (const float*)g[1], (const float*)g[2],
+            (const uint32_t*)x, (uint32_t*)(x_out ? x_out : x), (float*)p, lognp, logn, inv, (const float*)g[0],
+            (const float*)g[1], (const float*)g[2],
             (float)kick, drift, 4294967296.0 / box, scale_arr, (float)mass, (float*)rho);
     }
     return cudaGetLastError();
@@ -747,13 +751,13 @@ bool ikd_deposit_supported(int np, int precision, int n) {
 
 cudaError_t interp_kick_drift_deposit(void* x, void* p, int np, int precision, int n, void* const* g, double kick,
                                       double drift, double box, double mass, void* rho, cudaStream_t st, int nfields,
-                                      const double* scale_arr) {
+                                      const double* scale_arr, void* x_out) {
     if (!ikd_deposit_supported(np, precision, n) || nfields < 1 || (uintptr_t)rho % 16 != 0)
         return cudaErrorInvalidValue;
     const int R = n / np;
-    if (R == 1) return ikd_deposit_r<1>(x, p, np, n, g, kick, drift, box, mass, rho, st, nfields, scale_arr);
-    if (R == 2) return ikd_deposit_r<2>(x, p, np, n, g, kick, drift, box, mass, rho, st, nfields, scale_arr);
-    return ikd_deposit_r<4>(x, p, np, n, g, kick, drift, box, mass, rho, st, nfields, scale_arr);
+    if (R == 1) return ikd_deposit_r<1>(x, p, np, n, g, kick, drift, box, mass, rho, st, nfields, scale_arr, x_out);
+    if (R == 2) return ikd_deposit_r<2>(x, p, np, n, g, kick, drift, box, mass, rho, st, nfields, scale_arr, x_out);
+    return ikd_deposit_r<4>(x, p, np, n, g, kick, drift, box, mass, rho, st, nfields, scale_arr, x_out);
 }
 
 // ---------------------------------------------------------------- Zel'dovich placement

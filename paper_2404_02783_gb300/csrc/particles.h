@@ -21,10 +21,11 @@ cudaError_t interp_kick_drift(void* x, void* p, int64_t count, int precision, in
 // drifted positions into rho (which must be zero on entry); FP32 ticks, n / np in {1,2,4}.
 bool ikd_deposit_supported(int np, int precision, int n);
 // nfields > 1: a batch of runs stored back to back, box given per field as
-// scale_arr[f] = 2^32 / L_f (box is then ignored).
+// scale_arr[f] = 2^32 / L_f (box is then ignored).  x_out: where the drifted positions go
+// (null: back into x); p is always updated in place.
 cudaError_t interp_kick_drift_deposit(void* x, void* p, int np, int precision, int n, void* const* g, double kick,
                                       double drift, double box, double mass, void* rho, cudaStream_t st,
-                                      int nfields = 1, const double* scale_arr = nullptr);
+                                      int nfields = 1, const double* scale_arr = nullptr, void* x_out = nullptr);
 cudaError_t ic_place(void* x, void* p, void* const* psi, int np, int precision, double D, double pfac, double box,
                      cudaStream_t st);
 template <typename T>
