@@ -220,13 +220,17 @@ pm_status pm_bispectrum(pm_ctx* ctx, const void* field, int nbins, const double*
  * from the Zel'dovich ICs of the white-noise field w (device, np^3, as pm_ic_zeldovich
  * with white_noise) and delta_t a device target mesh n^3.  pm_loss_grad returns L and
  * writes dL/dw (device, np^3) by a reverse sweep: (x, p) checkpoints every
- * checkpoint_every steps; each segment is re-run forward keeping its positions and
- * force meshes; then the transposed drift, kick (direct CIC-gradient term plus the
+ * checkpoint_every steps; the forward run keeps the positions and force meshes of its
+ * last two segments, every earlier segment is re-run from its checkpoint (on a second
+ * CUDA stream the context creates on first use, overlapping the reverse sweep of the
+ * segment after it); then the transposed drift, kick (direct CIC-gradient term plus the
  * transposed deposit -> Green -> gradient chain) and Zel'dovich map are applied.  CIC
  * weight derivatives are taken on the side of the forward floor().  FP32 Newtonian
- * contexts only; scratch: pm_adjoint_scratch_size bytes (256-byte aligned).  Leaves the
- * context's particles at an intermediate step (run pm_ic_zeldovich before stepping
- * again).  Synchronises. */
+ * contexts only; scratch: pm_adjoint_scratch_size bytes (256-byte aligned): the
+ * checkpoints, two segment records of checkpoint_every steps and the re-runs' density,
+ * spectra and positions.  Leaves the context's particles at the last step of the forward
+ * run, before its closing half kick (run pm_ic_zeldovich before stepping again).
+ * Synchronises both streams before returning, also on error. */
 pm_status pm_adjoint_scratch_size(const pm_ctx* ctx, int checkpoint_every, size_t* bytes);
 pm_status pm_loss_grad(pm_ctx* ctx, const void* white_noise, const void* delta_target, int checkpoint_every,
                        void* scratch, size_t scratch_bytes, double* loss, void* grad_w);

@@ -467,7 +467,7 @@ cudaError_t interp_kick_drift(void* x, void* p, int64_t count, int precision, in
 // blockIdx.y selects the field of a batch of independent runs stored back to back
 // (particles [field][3][np^3], meshes [field][n^3]); scale = 2^32 / L of that field.
 template <int R>
-__global__ void __launch_bounds__(512, 2) k_ikd_deposit(const uint32_t* x, uint32_t* xo, float* __restrict__ p, int lognp,
+__global__ void __launch_bounds__(512, 2) k_ikd_deposit(const uint32_t* __restrict__ x, uint32_t* __restrict__ xo, float* __restrict__ p, int lognp,
                                                      int logn, float inv_cell_ticks, const float* __restrict__ gx,
                                                      const float* __restrict__ gy, const float* __restrict__ gz,
                                                      float kick, double drift, double scale0,
@@ -531,6 +531,8 @@ __global__ void __launch_bounds__(512, 2) k_ikd_deposit(const uint32_t* x, uint3
     tile_flush<D>(lo, carry, rho, ox, oy, oz, logn);
 }
 
+// x and xo may be the same array (in-place update): every particle's position is read once,
+// one iteration before its own thread writes it, and no thread touches another's particles.
 // R = 1: each thread walks its lattice row along x (lx = 0..15 at fixed ly, lz), so the
 // next particle usually sits one cell further in x with the same y and z cells.  Then
 // its lower-x CIC corners are this particle's upper-x corners: the gather keeps the 12
@@ -538,7 +540,7 @@ __global__ void __launch_bounds__(512, 2) k_ikd_deposit(const uint32_t* x, uint3
 // carries the upper-plane weights in registers, adds them to the next particle's
 // lower-plane weights and issues 4 tile atomics a particle instead of 8.  Any other
 // particle takes the full path, so the result is the same CIC gather and deposit.
-__global__ void __launch_bounds__(512, 2) k_ikd_deposit_sweep(const uint32_t* x, uint32_t* xo, float* __restrict__ p,
+__global__ void __launch_bounds__(512, 2) k_ikd_deposit_sweep(const uint32_t* __restrict__ x, uint32_t* __restrict__ xo, float* __restrict__ p,
                                                               int lognp, int logn, float inv_cell_ticks,
                                                               const float* __restrict__ gx,
                                                               const float* __restrict__ gy,
