@@ -166,3 +166,62 @@ def test_power_spectrum_of_a_full_size_field(run):
     np.testing.assert_allclose(k[ok], ko[ok], rtol=1e-10)
     # a 512^3 FP32 transform: a few 1e-7 per mode, bins of as few as 6 modes
     np.testing.assert_allclose(pk[ok], po[ok], rtol=5e-6)
+
+
+# ---------------------------------------------------------------- the largest mesh (1024^3)
+def _plane_wave(n, k0, dt):
+    """cos(2 pi k0.x / n) - 0.5 sin(2 pi k0.x / n) on the device, x the cell index."""
+    i = torch.arange(n, dtype=torch.float64, device="cuda") * (2 * np.pi / n)
+    ph = (k0[0] * i)[:, None, None] + (k0[1] * i)[None, :, None] + (k0[2] * i)[None, None, :]
+    f = (torch.cos(ph) - 0.5 * torch.sin(ph)).to(dt)
+    del ph
+    return f
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_fft_of_a_plane_wave_on_the_largest_mesh(prec):
+    # the transform of a single Fourier mode is one coefficient: n^3 / 2 (1 + 0.5 i) at
+    # (kz, kx, ky) = (k0z, k0x, k0y) (kz > 0, so its mirror is not stored); every other
+    # coefficient vanishes, and the inverse brings the wave back (times n^3)
+    pm = lib()
+    n = 1024
+    dt = torch.float64 if prec == 1 else torch.float32
+    k0 = (3, -5, 7)
+    f = _plane_wave(n, k0, dt)
+    spec = torch.empty((n // 2 + 1, n, n, 2), dtype=dt, device="cuda")
+    pm.pm_fft_r2c(f, spec, n, prec)
+    torch.cuda.synchronize()
+    peak = spec[k0[2], k0[0] % n, k0[1] % n].to(torch.float64).cpu().numpy()
+    # FP32: the twiddle roundings of the ~9 stages a coefficient passes add up to a few 1e-7
+    np.testing.assert_allclose(peak, np.array([0.5, 0.25]) * n**3, rtol=3e-6 if prec == 0 else 1e-12)
+    spec[k0[2], k0[0] % n, k0[1] % n] = 0
+    tol = 1e-6 if prec == 0 else 1e-12
+    assert spec.abs().max().item() < tol * n**3
+    spec[k0[2], k0[0] % n, k0[1] % n] = torch.tensor(peak, dtype=dt, device="cuda")
+    out = torch.empty((n, n, n), dtype=dt, device="cuda")
+    pm.pm_fft_c2r(spec, out, n, prec)
+    torch.cuda.synchronize()
+    del spec
+    assert (out / n**3 - f).abs().max().item() < (2e-5 if prec == 0 else 1e-11)
+
+
+def test_pm_step_on_the_largest_mesh():
+    # 1024^3 particles on a 1024^3 mesh (the largest the library takes), L = 10000 Mpc/h:
+    # one step from the ZA ICs conserves momentum and kicks along the displacement
+    pm = lib()
+    n = 1024
+    r = pm.PMRun(pm.make_config(n, n, 10000.0, A_I, A_F, STEPS))
+    r.ic(seed=5)
+    _, p = r.particles()
+    p0 = p.clone()
+    r.step(1)
+    torch.cuda.synchronize()
+    for j in range(3):
+        dp = p[j].to(torch.float64) - p0[j].to(torch.float64)
+        assert dp.abs().sum().item() > 0
+        assert dp.sum().abs().item() < 1e-5 * dp.abs().sum().item()
+        c = torch.corrcoef(torch.stack([dp, p0[j].to(torch.float64)]))[0, 1].item()
+        assert c > 0.95
+        del dp
+    del r, p, p0
+    torch.cuda.empty_cache()
