@@ -12,6 +12,7 @@
 #include <math.h>
 
 #include <mutex>
+#include <type_traits>
 
 #include "internal.h"
 #include "particles.h"
@@ -934,6 +935,74 @@ __global__ void k_combine_ticks(uint32_t* __restrict__ xt, const uint32_t* __res
     }
 }
 
+// The same combination by blocks: one thread per coarse node b, for the r^3 targets whose
+// lower coarse node is b (trilinear from the 8 nodes b + {0,1}^3; xi formed once per node).
+// The r targets of a z-run sit together: their positions are read and written as one
+// r-wide vector (r = 1, 2, 4), consecutive threads covering consecutive runs.
+template <int LOGR>
+__global__ void __launch_bounds__(256) k_combine_blocks(uint32_t* __restrict__ xt, const uint32_t* __restrict__ xg,
+                                                        const uint32_t* __restrict__ xn, int32_t* __restrict__ xi_out,
+                                                        int lognc) {
+    constexpr int r = 1 << LOGR, s = 3 * LOGR;
+    typedef typename std::conditional<r == 4, uint4, typename std::conditional<r == 2, uint2, uint32_t>::type>::type V;
+    const int maskc = (1 << lognc) - 1, lognt = lognc + LOGR;
+    const int64_t countc = (int64_t)1 << (3 * lognc), countt = (int64_t)1 << (3 * lognt);
+    for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b < countc;
+         b += (int64_t)gridDim.x * blockDim.x) {
+        const int bx = (int)(b >> (2 * lognc)), by = (int)((b >> lognc) & maskc), bz = (int)(b & maskc);
+        int32_t xi[3][8];  // corner q = 4 dx + 2 dy + dz
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const int64_t c = ((int64_t)((bx + (q >> 2)) & maskc) << (2 * lognc)) |
+                              ((int64_t)((by + ((q >> 1) & 1)) & maskc) << lognc) | ((bz + (q & 1)) & maskc);
+#pragma unroll
+            for (int j = 0; j < 3; ++j) xi[j][q] = (int32_t)(xg[j * countc + c] - xn[j * countc + c]);
+        }
+#pragma unroll 1
+        for (int ox = 0; ox < r; ++ox)
+#pragma unroll 1
+            for (int oy = 0; oy < r; ++oy) {
+                const int64_t t0 = ((((int64_t)(r * bx + ox) << lognt) + (r * by + oy)) << lognt) + r * bz;
+#pragma unroll
+                for (int j = 0; j < 3; ++j) {
+                    uint32_t add[r];
+#pragma unroll
+                    for (int oz = 0; oz < r; ++oz) {
+                        // S = sum over the corners of (weights in units of 1/r per axis) xi; exact in 64 bits
+                        int64_t S = 0;
+#pragma unroll
+                        for (int q = 0; q < 8; ++q) {
+                            const int wx = (q >> 2) ? ox : r - ox, wy = ((q >> 1) & 1) ? oy : r - oy,
+                                      wz = (q & 1) ? oz : r - oz;
+                            S += (int64_t)xi[j][q] * (wx * wy * wz);
+                        }
+                        int64_t qv = S;
+                        if (s > 0) {  // round-half-even of S / r^3
+                            const int64_t fl = S >> s;
+                            const int64_t rem = S - (fl << s);
+                            const int64_t half = (int64_t)1 << (s > 0 ? s - 1 : 0);
+                            qv = fl + ((rem > half || (rem == half && (fl & 1))) ? 1 : 0);
+                        }
+                        add[oz] = (uint32_t)qv;
+                    }
+                    V* dst = reinterpret_cast<V*>(xt + j * countt + t0);
+                    V v = *dst;
+                    uint32_t* vv = reinterpret_cast<uint32_t*>(&v);
+#pragma unroll
+                    for (int oz = 0; oz < r; ++oz) vv[oz] += add[oz];
+                    *dst = v;
+                    if (xi_out) {
+                        V w;
+                        uint32_t* ww = reinterpret_cast<uint32_t*>(&w);
+#pragma unroll
+                        for (int oz = 0; oz < r; ++oz) ww[oz] = add[oz];
+                        *reinterpret_cast<V*>(xi_out + j * countt + t0) = w;
+                    }
+                }
+            }
+    }
+}
+
 __global__ void k_combine_frac(double* __restrict__ xt, const double* __restrict__ xg, const double* __restrict__ xn,
                                double* __restrict__ xi_out, int lognt, int lognc) {
     const int64_t countt = (int64_t)1 << (3 * lognt);
@@ -979,7 +1048,21 @@ cudaError_t combine(void* xt, const void* xg, const void* xn, void* xi_out, int 
                     cudaStream_t st) {
     const int lognt = ilog2(npt), lognc = ilog2(npc);
     const int64_t count = (int64_t)npt * npt * npt;
-    if (precision == PM_FP32_FIXED)
+    const int64_t countc = (int64_t)npc * npc * npc;
+    // vector accesses need 4 r-byte alignment (the library's particle arrays are 256-byte aligned)
+    const bool aligned = (uintptr_t)xt % 16 == 0 && (uintptr_t)xi_out % 16 == 0;
+    if (precision == PM_FP32_FIXED && aligned && lognt - lognc <= 2) {
+        const unsigned g = grid_for(countc, 256);
+        if (lognt == lognc)
+            k_combine_blocks<0><<<g, 256, 0, st>>>((uint32_t*)xt, (const uint32_t*)xg, (const uint32_t*)xn,
+                                                   (int32_t*)xi_out, lognc);
+        else if (lognt == lognc + 1)
+            k_combine_blocks<1><<<g, 256, 0, st>>>((uint32_t*)xt, (const uint32_t*)xg, (const uint32_t*)xn,
+                                                   (int32_t*)xi_out, lognc);
+        else
+            k_combine_blocks<2><<<g, 256, 0, st>>>((uint32_t*)xt, (const uint32_t*)xg, (const uint32_t*)xn,
+                                                   (int32_t*)xi_out, lognc);
+    } else if (precision == PM_FP32_FIXED)
         k_combine_ticks<<<grid_for(count, 256), 256, 0, st>>>((uint32_t*)xt, (const uint32_t*)xg,
                                                               (const uint32_t*)xn, (int32_t*)xi_out, lognt, lognc);
     else
