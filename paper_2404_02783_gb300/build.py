@@ -16,7 +16,7 @@ CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(PKG, "libpm.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["fft_f32.cu", "fft_f64.cu", "tables.cu", "particles.cu", "bias.cu", "adjoint.cu", "stats.cu", "api.cu", "host_cosmo.cpp"]
+SOURCES = ["fft_f32.cu", "fft_f64.cu", "tables.cu", "particles.cu", "update.cu", "bias.cu", "adjoint.cu", "stats.cu", "api.cu", "host_cosmo.cpp"]
 
 
 def nvcc():

@@ -1,7 +1,8 @@
-// Particle-side kernels of the PM step: CIC deposit (counting density, Sec. 4),
-// fused CIC interpolation + kick + drift (KDK in a), Zel'dovich placement, the
-// per-wavevector Philox phases, the GR displacement combination (Eqs. xiGR and
-// combined) and the cell keys / stable cell order of the particles.
+// Particle-side kernels of the PM step: CIC deposit (counting density, Sec. 4), CIC
+// interpolation and the unfused kick + drift (KDK in a; the fused update with the next
+// deposit is in update.cu), Zel'dovich placement, the per-wavevector Philox phases, the GR
+// displacement combination (Eqs. xiGR and combined) and the cell keys / stable cell order
+// of the particles.
 //
 // Position encodings (units of the box side):
 //   FP32 path: uint32 ticks, 2^32 per side; the periodic wrap is integer overflow.
@@ -16,23 +17,11 @@
 
 #include "internal.h"
 #include "particles.h"
+#include "update_dev.cuh"
 
 namespace pm {
 
-// ---------------------------------------------------------------- CIC decode
-struct CicF {
-    int i0, i1;
-    float w1;
-};
-__device__ __forceinline__ CicF cic_ticks(uint32_t u, int logn, float inv_cell_ticks) {
-    const int sh = 32 - logn;
-    const uint32_t t = u - (1u << (sh - 1));
-    CicF c;
-    c.i0 = (int)(t >> sh);
-    c.i1 = (c.i0 + 1) & ((1 << logn) - 1);
-    c.w1 = __uint2float_rn(t & ((1u << sh) - 1u)) * inv_cell_ticks;
-    return c;
-}
+// ---------------------------------------------------------------- CIC decode (FP64 fractions)
 struct CicD {
     int i0, i1;
     double w1;
@@ -67,113 +56,6 @@ __global__ void __launch_bounds__(256) k_deposit_ticks(const uint32_t* __restric
                 atomicAdd(row + iz[0], wab * wz[0]);
                 atomicAdd(row + iz[1], wab * wz[1]);
             }
-    }
-}
-
-// Deposit of lattice-ordered particles (count = np^3, id = (ix np + iy) np + iz) by
-// Lagrangian tiles.  A CTA owns a TX x TY x TZ block of lattice sites (16 x 16 x 32
-// mesh cells' worth, R = n / np cells per lattice step); particles that have not
-// travelled far land in that mesh box widened by H cells on every side, which the CTA
-// accumulates in shared memory and then adds to the global mesh once per cell.  A
-// particle whose CIC stencil leaves the box adds its weights to global memory directly,
-// so the result is the same CIC density for any displacement.
-//
-// The tile accumulates in fixed point: each weight is rounded to a multiple of 2^-24
-// (half a quantum at most, 3e-8, below the FP32 rounding of a sum near 1) and added
-// with a native 32-bit integer atomic (shared-memory float atomics are a compare-and-
-// swap loop on this part).  A wrap of the 32-bit word is seen in the atomic's return
-// value and counted in an 8-bit carry per cell.  A tile holds at most 8192 mass units
-// (TX TY TZ R^3 = 8192 for every R), i.e. 2^37 quanta, so a cell's carry stays below 32
-// and the tile sum is exact and independent of the order of the additions.
-// The box starts HZ = 4 cells below the tile in z so that its rows are made of 16-byte
-// chunks aligned in the mesh: the flush adds four cells per vector reduction.
-template <int R>
-struct DepTile {
-    static constexpr int TX = 16 / R, TY = 16 / R, TZ = 32 / R, H = 2, HZ = 4;
-    static constexpr int DX = TX * R + 2 * H, DY = TY * R + 2 * H, DZ = TZ * R + 2 * HZ;
-    static constexpr int CELLS = DX * DY * DZ, CHUNKS = CELLS / 4;
-    static constexpr int CARRY_WORDS = CHUNKS;  // one word of four 8-bit carries per chunk
-    static constexpr int WORDS = CELLS + CARRY_WORDS;  // shared memory: lo[CELLS], carry[CARRY_WORDS]
-    static constexpr int PER = TX * TY * TZ;
-    static_assert(PER * R * R * R == 8192, "tile mass bound");
-    static_assert(DZ % 4 == 0 && (TZ * R) % 4 == 0 && HZ % 4 == 0, "z box made of aligned 16-byte chunks");
-};
-
-__device__ __forceinline__ void red_add_v4(float* dst, float4 v) {
-    asm volatile("red.relaxed.gpu.global.add.v4.f32 [%0], {%1, %2, %3, %4};\n" ::"l"(dst), "f"(v.x), "f"(v.y),
-                 "f"(v.z), "f"(v.w)
-                 : "memory");
-}
-
-constexpr float kTileQuanta = 16777216.0f;  // 2^24 quanta per unit mass
-constexpr float kTileQuantum = 5.9604644775390625e-08f;  // 2^-24
-
-__device__ __forceinline__ void tile_add(uint32_t* lo, uint32_t* carry, int c, float w) {
-    const uint32_t v = __float2uint_rn(w * kTileQuanta);
-    const uint32_t old = atomicAdd(lo + c, v);
-    if (old + v < old) atomicAdd(carry + (c >> 2), 1u << (8 * (c & 3)));
-}
-
-template <class D>
-__device__ __forceinline__ void tile_zero(uint32_t* words) {
-    for (int c = threadIdx.x; c < D::WORDS; c += blockDim.x) words[c] = 0u;
-}
-
-// One particle's CIC weights into the tile (box origin o*) or, outside it, into rho.
-template <class D>
-__device__ __forceinline__ void tile_deposit(uint32_t* lo, uint32_t* carry, float* __restrict__ rho, uint32_t u0,
-                                             uint32_t u1, uint32_t u2, int logn, float inv_cell_ticks, int ox,
-                                             int oy, int oz, float mass) {
-    const int nm = (1 << logn) - 1;
-    const CicF cx = cic_ticks(u0, logn, inv_cell_ticks);
-    const CicF cy = cic_ticks(u1, logn, inv_cell_ticks);
-    const CicF cz = cic_ticks(u2, logn, inv_cell_ticks);
-    const float wx[2] = {1.0f - cx.w1, cx.w1}, wy[2] = {1.0f - cy.w1, cy.w1}, wz[2] = {1.0f - cz.w1, cz.w1};
-    const int dx = (cx.i0 - ox) & nm, dy = (cy.i0 - oy) & nm, dz = (cz.i0 - oz) & nm;
-    if (dx < D::DX - 1 && dy < D::DY - 1 && dz < D::DZ - 1) {
-        const int c0 = (dx * D::DY + dy) * D::DZ + dz;
-#pragma unroll
-        for (int a = 0; a < 2; ++a)
-#pragma unroll
-            for (int b = 0; b < 2; ++b) {
-                const float wab = mass * wx[a] * wy[b];
-                const int c = c0 + (a * D::DY + b) * D::DZ;
-                tile_add(lo, carry, c, wab * wz[0]);
-                tile_add(lo, carry, c + 1, wab * wz[1]);
-            }
-    } else {
-        const uint32_t ix[2] = {(uint32_t)cx.i0, (uint32_t)cx.i1}, iy[2] = {(uint32_t)cy.i0, (uint32_t)cy.i1};
-#pragma unroll
-        for (int a = 0; a < 2; ++a)
-#pragma unroll
-            for (int b = 0; b < 2; ++b) {
-                const float wab = mass * wx[a] * wy[b];
-                float* row = rho + (((ix[a] << logn) + iy[b]) << logn);
-                atomicAdd(row + cz.i0, wab * wz[0]);
-                atomicAdd(row + cz.i1, wab * wz[1]);
-            }
-    }
-}
-
-// Adds the tile's cells (box origin o*, oz a multiple of 4, rho 16-byte aligned) to rho,
-// four z-cells per reduction.
-template <class D>
-__device__ __forceinline__ void tile_flush(const uint32_t* lo, const uint32_t* carry, float* __restrict__ rho, int ox,
-                                           int oy, int oz, int logn) {
-    const int nm = (1 << logn) - 1;
-    for (int c = threadIdx.x; c < D::CHUNKS; c += blockDim.x) {
-        const uint4 l = reinterpret_cast<const uint4*>(lo)[c];
-        const uint32_t h = carry[c];
-        if (l.x | l.y | l.z | l.w | h) {
-            const int lz4 = c % (D::DZ / 4), ly = (c / (D::DZ / 4)) % D::DY, lx = c / ((D::DZ / 4) * D::DY);
-            const float4 v = make_float4(__uint2float_rn(l.x) * kTileQuantum + (float)(h & 255u) * 256.0f,
-                                         __uint2float_rn(l.y) * kTileQuantum + (float)((h >> 8) & 255u) * 256.0f,
-                                         __uint2float_rn(l.z) * kTileQuantum + (float)((h >> 16) & 255u) * 256.0f,
-                                         __uint2float_rn(l.w) * kTileQuantum + (float)(h >> 24) * 256.0f);
-            red_add_v4(rho + ((((uint32_t)((ox + lx) & nm) << logn) + (uint32_t)((oy + ly) & nm)) << logn) +
-                           ((oz + 4 * lz4) & nm),
-                       v);
-        }
     }
 }
 
@@ -333,40 +215,6 @@ cudaError_t interp(const void* field, int n, const void* x, int64_t count, int p
 }
 
 // ---------------------------------------------------------------- interp + kick + drift
-// p += kick * g(x);  x += drift * p   (g = -grad phi gathered with the deposit's weights).
-// The eight corner offsets are formed once in 32 bits (n^3 <= 2^30) and serve the
-// three force meshes.
-__device__ __forceinline__ void ikd_particle(uint32_t& u0, uint32_t& u1, uint32_t& u2, float& p0, float& p1,
-                                             float& p2, int logn, float inv_cell_ticks, const float* __restrict__ gx,
-                                             const float* __restrict__ gy, const float* __restrict__ gz, float kick,
-                                             float drift_ticks) {
-    const CicF cx = cic_ticks(u0, logn, inv_cell_ticks);
-    const CicF cy = cic_ticks(u1, logn, inv_cell_ticks);
-    const CicF cz = cic_ticks(u2, logn, inv_cell_ticks);
-    const float wx[2] = {1.0f - cx.w1, cx.w1}, wy[2] = {1.0f - cy.w1, cy.w1}, wz[2] = {1.0f - cz.w1, cz.w1};
-    const uint32_t ix[2] = {(uint32_t)cx.i0, (uint32_t)cx.i1}, iy[2] = {(uint32_t)cy.i0, (uint32_t)cy.i1};
-    float f0 = 0.f, f1 = 0.f, f2 = 0.f;
-#pragma unroll
-    for (int a = 0; a < 2; ++a)
-#pragma unroll
-        for (int b = 0; b < 2; ++b) {
-            const uint32_t row = ((ix[a] << logn) + iy[b]) << logn;
-            const uint32_t o0 = row + (uint32_t)cz.i0, o1 = row + (uint32_t)cz.i1;
-            const float w0 = wx[a] * wy[b] * wz[0], w1 = wx[a] * wy[b] * wz[1];
-            f0 = fmaf(w0, __ldg(gx + o0), fmaf(w1, __ldg(gx + o1), f0));
-            f1 = fmaf(w0, __ldg(gy + o0), fmaf(w1, __ldg(gy + o1), f1));
-            f2 = fmaf(w0, __ldg(gz + o0), fmaf(w1, __ldg(gz + o1), f2));
-        }
-    p0 = fmaf(kick, f0, p0);
-    p1 = fmaf(kick, f1, p1);
-    p2 = fmaf(kick, f2, p2);
-    // 32-bit conversion (the 64-bit one is several times slower here): exact for drifts under
-    // half the box per step, i.e. |p drift_ticks| < 2^31, the range of any meaningful step
-    u0 += (uint32_t)__float2int_rn(p0 * drift_ticks);
-    u1 += (uint32_t)__float2int_rn(p1 * drift_ticks);
-    u2 += (uint32_t)__float2int_rn(p2 * drift_ticks);
-}
-
 __global__ void __launch_bounds__(256) k_ikd_ticks(uint32_t* __restrict__ x, float* __restrict__ p, int64_t count,
                                                    int logn, float inv_cell_ticks, const float* __restrict__ gx,
                                                    const float* __restrict__ gy, const float* __restrict__ gz,
@@ -458,309 +306,6 @@ cudaError_t interp_kick_drift(void* x, void* p, int64_t count, int precision, in
                                                          (const double*)g[1], (const double*)g[2], kick, drift / box);
     }
     return cudaGetLastError();
-}
-
-// ---------------------------------------------------------------- kick + drift + next deposit
-// One pass per step over the lattice-ordered particles by Lagrangian tiles: gather the
-// force at x, kick, drift, and deposit the new position into the (zeroed) next
-// density mesh through the tile's shared-memory accumulator, exactly as
-// k_deposit_tiled would have done from the drifted positions.
-// blockIdx.y selects the field of a batch of independent runs stored back to back
-// (particles [field][3][np^3], meshes [field][n^3]); scale = 2^32 / L of that field.
-template <int R>
-__global__ void __launch_bounds__(512, 2) k_ikd_deposit(const uint32_t* __restrict__ x, uint32_t* __restrict__ xo, float* __restrict__ p, int lognp,
-                                                     int logn, float inv_cell_ticks, const float* __restrict__ gx,
-                                                     const float* __restrict__ gy, const float* __restrict__ gz,
-                                                     float kick, double drift, double scale0,
-                                                     const double* __restrict__ scale_arr, float mass,
-                                                     float* __restrict__ rho) {
-    typedef DepTile<R> D;
-    extern __shared__ __align__(16) uint32_t tile_words[];  // D::WORDS
-    uint32_t* lo = tile_words;
-    uint32_t* carry = tile_words + D::CELLS;
-    const int np = 1 << lognp;
-    const int64_t count = (int64_t)1 << (3 * lognp);
-    {
-        const int64_t fb = blockIdx.y;
-        const int64_t n3 = (int64_t)1 << (3 * logn);
-        x += fb * 3 * count;
-        xo += fb * 3 * count;
-        p += fb * 3 * count;
-        gx += fb * n3;
-        gy += fb * n3;
-        gz += fb * n3;
-        rho += fb * n3;
-    }
-    const float drift_ticks = (float)(drift * (scale_arr ? scale_arr[blockIdx.y] : scale0));
-    const int ntz = np / D::TZ, nty = np / D::TY;
-    const int bz = blockIdx.x % ntz, by = (blockIdx.x / ntz) % nty, bx = blockIdx.x / (ntz * nty);
-    const int ox = bx * D::TX * R - D::H, oy = by * D::TY * R - D::H, oz = bz * D::TZ * R - D::HZ;
-    tile_zero<D>(tile_words);
-    __syncthreads();
-    auto pid = [&](int e) -> int64_t {
-        const int lz = e % D::TZ, ly = (e / D::TZ) % D::TY, lx = e / (D::TZ * D::TY);
-        return ((((int64_t)(bx * D::TX + lx) << lognp) + by * D::TY + ly) << lognp) + bz * D::TZ + lz;
-    };
-    // the next particle is loaded one iteration ahead (its latency overlaps this one's work)
-    int64_t idn = pid(threadIdx.x);
-    uint32_t nu0 = x[idn], nu1 = x[count + idn], nu2 = x[2 * count + idn];
-    float np0 = p[idn], np1 = p[count + idn], np2 = p[2 * count + idn];
-#pragma unroll 1
-    for (int e = threadIdx.x; e < D::PER; e += 512) {
-        const int64_t id = idn;
-        uint32_t u0 = nu0, u1 = nu1, u2 = nu2;
-        float p0 = np0, p1 = np1, p2 = np2;
-        if (e + 512 < D::PER) {
-            idn = pid(e + 512);
-            nu0 = x[idn];
-            nu1 = x[count + idn];
-            nu2 = x[2 * count + idn];
-            np0 = p[idn];
-            np1 = p[count + idn];
-            np2 = p[2 * count + idn];
-        }
-        ikd_particle(u0, u1, u2, p0, p1, p2, logn, inv_cell_ticks, gx, gy, gz, kick, drift_ticks);
-        p[id] = p0;
-        p[count + id] = p1;
-        p[2 * count + id] = p2;
-        xo[id] = u0;
-        xo[count + id] = u1;
-        xo[2 * count + id] = u2;
-        tile_deposit<D>(lo, carry, rho, u0, u1, u2, logn, inv_cell_ticks, ox, oy, oz, mass);
-    }
-    __syncthreads();
-    tile_flush<D>(lo, carry, rho, ox, oy, oz, logn);
-}
-
-// x and xo may be the same array (in-place update): every particle's position is read once,
-// one iteration before its own thread writes it, and no thread touches another's particles.
-// R = 1: each thread walks its lattice row along x (lx = 0..15 at fixed ly, lz), so the
-// next particle usually sits one cell further in x with the same y and z cells.  Then
-// its lower-x CIC corners are this particle's upper-x corners: the gather keeps the 12
-// upper-plane force values in registers and loads only the new plane, and the deposit
-// carries the upper-plane weights in registers, adds them to the next particle's
-// lower-plane weights and issues 4 tile atomics a particle instead of 8.  Any other
-// particle takes the full path, so the result is the same CIC gather and deposit.
-__global__ void __launch_bounds__(512, 2) k_ikd_deposit_sweep(const uint32_t* __restrict__ x, uint32_t* __restrict__ xo, float* __restrict__ p,
-                                                              int lognp, int logn, float inv_cell_ticks,
-                                                              const float* __restrict__ gx,
-                                                              const float* __restrict__ gy,
-                                                              const float* __restrict__ gz, float kick, double drift,
-                                                              double scale0, const double* __restrict__ scale_arr,
-                                                              float mass, float* __restrict__ rho) {
-    typedef DepTile<1> D;
-    static_assert(D::TY * D::TZ == 512, "one thread per (ly, lz); lx runs over the loop");
-    extern __shared__ __align__(16) uint32_t tile_words[];  // D::WORDS
-    uint32_t* lo = tile_words;
-    uint32_t* carry = tile_words + D::CELLS;
-    const int np = 1 << lognp, nm = (1 << logn) - 1;
-    const int64_t count = (int64_t)1 << (3 * lognp);
-    {
-        const int64_t fb = blockIdx.y;
-        const int64_t n3 = (int64_t)1 << (3 * logn);
-        x += fb * 3 * count;
-        xo += fb * 3 * count;
-        p += fb * 3 * count;
-        gx += fb * n3;
-        gy += fb * n3;
-        gz += fb * n3;
-        rho += fb * n3;
-    }
-    const float drift_ticks = (float)(drift * (scale_arr ? scale_arr[blockIdx.y] : scale0));
-    const int ntz = np / D::TZ, nty = np / D::TY;
-    const int bz = blockIdx.x % ntz, by = (blockIdx.x / ntz) % nty, bx = blockIdx.x / (ntz * nty);
-    const int ox = bx * D::TX - D::H, oy = by * D::TY - D::H, oz = bz * D::TZ - D::HZ;
-    tile_zero<D>(tile_words);
-    __syncthreads();
-    const int lz = threadIdx.x % D::TZ, ly = threadIdx.x / D::TZ;
-    const int64_t id0 = ((((int64_t)(bx * D::TX) << lognp) + by * D::TY + ly) << lognp) + bz * D::TZ + lz;
-    const int64_t xstride = (int64_t)1 << (2 * lognp);
-    uint32_t next_cell = 0xffffffffu;  // packed (ix, iy, iz) whose lower plane the registers hold
-    float U[4][3];                      // force at the carried plane, corner (b, c) = 2 b + c
-    int dnext = -1;                     // tile cell whose a = 0 plane the carried weights belong to
-    float W[4];
-    // the next particle's position and momentum are loaded one iteration ahead, so their
-    // memory latency overlaps the current particle's gather, update and deposit
-    uint32_t nu0 = x[id0], nu1 = x[count + id0], nu2 = x[2 * count + id0];
-    float np0 = p[id0], np1 = p[count + id0], np2 = p[2 * count + id0];
-#pragma unroll 1
-    for (int lx = 0; lx < D::TX; ++lx) {
-        const int64_t id = id0 + lx * xstride;
-        uint32_t u0 = nu0, u1 = nu1, u2 = nu2;
-        float p0 = np0, p1 = np1, p2 = np2;
-        if (lx + 1 < D::TX) {
-            const int64_t idn = id + xstride;
-            nu0 = x[idn];
-            nu1 = x[count + idn];
-            nu2 = x[2 * count + idn];
-            np0 = p[idn];
-            np1 = p[count + idn];
-            np2 = p[2 * count + idn];
-        }
-        // ---- gather at the old position
-        {
-            const CicF cx = cic_ticks(u0, logn, inv_cell_ticks);
-            const CicF cy = cic_ticks(u1, logn, inv_cell_ticks);
-            const CicF cz = cic_ticks(u2, logn, inv_cell_ticks);
-            const uint32_t cell = ((((uint32_t)cx.i0 << logn) | (uint32_t)cy.i0) << logn) | (uint32_t)cz.i0;
-            const uint32_t iy[2] = {(uint32_t)cy.i0, (uint32_t)cy.i1}, iz[2] = {(uint32_t)cz.i0, (uint32_t)cz.i1};
-            float L[4][3];
-            if (cell == next_cell) {
-#pragma unroll
-                for (int q = 0; q < 4; ++q)
-#pragma unroll
-                    for (int j = 0; j < 3; ++j) L[q][j] = U[q][j];
-            } else {
-#pragma unroll
-                for (int b = 0; b < 2; ++b)
-#pragma unroll
-                    for (int c = 0; c < 2; ++c) {
-                        const uint32_t o = ((((uint32_t)cx.i0 << logn) + iy[b]) << logn) + iz[c];
-                        L[2 * b + c][0] = __ldg(gx + o);
-                        L[2 * b + c][1] = __ldg(gy + o);
-                        L[2 * b + c][2] = __ldg(gz + o);
-                    }
-            }
-#pragma unroll
-            for (int b = 0; b < 2; ++b)
-#pragma unroll
-                for (int c = 0; c < 2; ++c) {
-                    const uint32_t o = ((((uint32_t)cx.i1 << logn) + iy[b]) << logn) + iz[c];
-                    U[2 * b + c][0] = __ldg(gx + o);
-                    U[2 * b + c][1] = __ldg(gy + o);
-                    U[2 * b + c][2] = __ldg(gz + o);
-                }
-            next_cell = ((((uint32_t)cx.i1 << logn) | (uint32_t)cy.i0) << logn) | (uint32_t)cz.i0;
-            const float wy[2] = {1.0f - cy.w1, cy.w1}, wz[2] = {1.0f - cz.w1, cz.w1};
-            const float wx0 = 1.0f - cx.w1, wx1 = cx.w1;
-            float f0 = 0.f, f1 = 0.f, f2 = 0.f;
-#pragma unroll
-            for (int b = 0; b < 2; ++b)
-#pragma unroll
-                for (int c = 0; c < 2; ++c) {
-                    const float w = wy[b] * wz[c];
-                    const int q = 2 * b + c;
-                    f0 = fmaf(w, fmaf(wx0, L[q][0], wx1 * U[q][0]), f0);
-                    f1 = fmaf(w, fmaf(wx0, L[q][1], wx1 * U[q][1]), f1);
-                    f2 = fmaf(w, fmaf(wx0, L[q][2], wx1 * U[q][2]), f2);
-                }
-            p0 = fmaf(kick, f0, p0);
-            p1 = fmaf(kick, f1, p1);
-            p2 = fmaf(kick, f2, p2);
-            u0 += (uint32_t)__float2int_rn(p0 * drift_ticks);
-            u1 += (uint32_t)__float2int_rn(p1 * drift_ticks);
-            u2 += (uint32_t)__float2int_rn(p2 * drift_ticks);
-        }
-        p[id] = p0;
-        p[count + id] = p1;
-        p[2 * count + id] = p2;
-        xo[id] = u0;
-        xo[count + id] = u1;
-        xo[2 * count + id] = u2;
-        // ---- deposit at the new position
-        {
-            const CicF cx = cic_ticks(u0, logn, inv_cell_ticks);
-            const CicF cy = cic_ticks(u1, logn, inv_cell_ticks);
-            const CicF cz = cic_ticks(u2, logn, inv_cell_ticks);
-            const float wy[2] = {1.0f - cy.w1, cy.w1}, wz[2] = {1.0f - cz.w1, cz.w1};
-            const float m0 = mass * (1.0f - cx.w1), m1 = mass * cx.w1;
-            const int dx = (cx.i0 - ox) & nm, dy = (cy.i0 - oy) & nm, dz = (cz.i0 - oz) & nm;
-            if (dx < D::DX - 1 && dy < D::DY - 1 && dz < D::DZ - 1) {
-                const int c0 = (dx * D::DY + dy) * D::DZ + dz;
-                float w0[4];
-#pragma unroll
-                for (int b = 0; b < 2; ++b)
-#pragma unroll
-                    for (int c = 0; c < 2; ++c) w0[2 * b + c] = m0 * wy[b] * wz[c];
-                if (c0 == dnext) {
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) w0[q] += W[q];
-                } else if (dnext >= 0) {
-#pragma unroll
-                    for (int b = 0; b < 2; ++b)
-#pragma unroll
-                        for (int c = 0; c < 2; ++c) tile_add(lo, carry, dnext + b * D::DZ + c, W[2 * b + c]);
-                }
-#pragma unroll
-                for (int b = 0; b < 2; ++b)
-#pragma unroll
-                    for (int c = 0; c < 2; ++c) {
-                        tile_add(lo, carry, c0 + b * D::DZ + c, w0[2 * b + c]);
-                        W[2 * b + c] = m1 * wy[b] * wz[c];
-                    }
-                dnext = c0 + D::DY * D::DZ;
-            } else {
-                if (dnext >= 0) {
-#pragma unroll
-                    for (int b = 0; b < 2; ++b)
-#pragma unroll
-                        for (int c = 0; c < 2; ++c) tile_add(lo, carry, dnext + b * D::DZ + c, W[2 * b + c]);
-                }
-                dnext = -1;
-                const uint32_t ix[2] = {(uint32_t)cx.i0, (uint32_t)cx.i1}, iy[2] = {(uint32_t)cy.i0, (uint32_t)cy.i1};
-                const float mx[2] = {m0, m1};
-#pragma unroll
-                for (int a = 0; a < 2; ++a)
-#pragma unroll
-                    for (int b = 0; b < 2; ++b) {
-                        float* row = rho + (((ix[a] << logn) + iy[b]) << logn);
-                        atomicAdd(row + cz.i0, mx[a] * wy[b] * wz[0]);
-                        atomicAdd(row + cz.i1, mx[a] * wy[b] * wz[1]);
-                    }
-            }
-        }
-    }
-    if (dnext >= 0) {
-#pragma unroll
-        for (int b = 0; b < 2; ++b)
-#pragma unroll
-            for (int c = 0; c < 2; ++c) tile_add(lo, carry, dnext + b * D::DZ + c, W[2 * b + c]);
-    }
-    __syncthreads();
-    tile_flush<D>(lo, carry, rho, ox, oy, oz, logn);
-}
-
-template <int R>
-static cudaError_t ikd_deposit_r(void* x, void* p, int np, int n, void* const* g, double kick, double drift,
-                                 double box, double mass, void* rho, cudaStream_t st, int nfields,
-                                 const double* scale_arr, void* x_out) {
-    typedef DepTile<R> D;
-    const int lognp = ilog2(np), logn = ilog2(n);
-    const unsigned blocks = (unsigned)((np / D::TX) * (np / D::TY) * (np / D::TZ));
-    const float inv = (float)ldexp(1.0, -(32 - logn));
-    const size_t smem = sizeof(uint32_t) * D::WORDS;
-    if constexpr (R == 1) {
-        cudaError_t e = set_smem_once((const void*)k_ikd_deposit_sweep, smem);
-        if (e != cudaSuccess) return e;
-        k_ikd_deposit_sweep<<<dim3(blocks, nfields), 512, smem, st>>>(
-            (const uint32_t*)x, (uint32_t*)(x_out ? x_out : x), (float*)p, lognp, logn, inv, (const float*)g[0],
-            (const float*)g[1], (const float*)g[2],
-            (float)kick, drift, 4294967296.0 / box, scale_arr, (float)mass, (float*)rho);
-    } else {
-        cudaError_t e = set_smem_once((const void*)k_ikd_deposit<R>, smem);
-        if (e != cudaSuccess) return e;
-        k_ikd_deposit<R><<<dim3(blocks, nfields), 512, smem, st>>>(
-            (const uint32_t*)x, (uint32_t*)(x_out ? x_out : x), (float*)p, lognp, logn, inv, (const float*)g[0],
-            (const float*)g[1], (const float*)g[2],
-            (float)kick, drift, 4294967296.0 / box, scale_arr, (float)mass, (float*)rho);
-    }
-    return cudaGetLastError();
-}
-
-bool ikd_deposit_supported(int np, int precision, int n) {
-    const int R = n / np;
-    return precision == PM_FP32_FIXED && n >= 64 && (R == 1 || R == 2 || R == 4) && np >= 32 / R;
-}
-
-cudaError_t interp_kick_drift_deposit(void* x, void* p, int np, int precision, int n, void* const* g, double kick,
-                                      double drift, double box, double mass, void* rho, cudaStream_t st, int nfields,
-                                      const double* scale_arr, void* x_out) {
-    if (!ikd_deposit_supported(np, precision, n) || nfields < 1 || (uintptr_t)rho % 16 != 0)
-        return cudaErrorInvalidValue;
-    const int R = n / np;
-    if (R == 1) return ikd_deposit_r<1>(x, p, np, n, g, kick, drift, box, mass, rho, st, nfields, scale_arr, x_out);
-    if (R == 2) return ikd_deposit_r<2>(x, p, np, n, g, kick, drift, box, mass, rho, st, nfields, scale_arr, x_out);
-    return ikd_deposit_r<4>(x, p, np, n, g, kick, drift, box, mass, rho, st, nfields, scale_arr, x_out);
 }
 
 // ---------------------------------------------------------------- Zel'dovich placement
