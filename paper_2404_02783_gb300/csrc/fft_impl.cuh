@@ -312,12 +312,23 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 // plane (plane = blk / (N / CB)).  The next block's columns are copied into a shared
 // stage with cp.async while the current block is transformed, so the loads of one block
 // overlap the butterflies and stores of the previous one.
+// Column groups of the x pass: FP32 meshes of 256 and more take 1024-thread CTAs of twice
+// the columns (full 128-byte row segments; the binning pass keeps 512 threads, its
+// cross-spectrum stage would not fit).
+template <typename T, int LOGN, int KIND> struct XShape {
+    typedef Shape<T, LOGN> S;
+    static constexpr bool WIDE = sizeof(T) == 4 && S::N >= 256 && KIND != OP_BIN;
+    static constexpr int CB = WIDE ? 1024 / S::QN : S::CB;
+    static constexpr int THREADS = CB * S::QN;
+    static constexpr int MINB = WIDE ? 1 : (sizeof(T) == 4 ? 2 : 1);
+};
+
 template <typename T, int LOGN, int KIND>
-__global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) k_x_cols(cplx<T>* __restrict__ data, cplx<T>* __restrict__ out2, SpecOp op,
-                                                int nplanes) {
+__global__ void __launch_bounds__(XShape<T, LOGN, KIND>::THREADS, XShape<T, LOGN, KIND>::MINB)
+    k_x_cols(cplx<T>* __restrict__ data, cplx<T>* __restrict__ out2, SpecOp op, int nplanes) {
     typedef cplx<T> C;
     typedef Shape<T, LOGN> S;
-    constexpr int N = S::N, M = S::M, Q = S::QN, CB = S::CB;
+    constexpr int N = S::N, M = S::M, Q = S::QN, CB = XShape<T, LOGN, KIND>::CB;
     constexpr int CS = CB + 1;
     constexpr int NCG = N / CB;                              // column groups per plane
     constexpr int CHUNKS_ROW = CB * (int)sizeof(C) / 16;     // 16-byte chunks per row of a group
@@ -643,19 +654,20 @@ cudaError_t inverse_yz_grad_n(cplx<T>* A, cplx<T>* B, cplx<T>* scratch, T* const
 template <typename T, int LOGN, int KIND>
 cudaError_t x_cols_n(cplx<T>* data, cplx<T>* out2, int nplanes, const SpecOp& op, cudaStream_t st) {
     typedef Shape<T, LOGN> S;
+    typedef XShape<T, LOGN, KIND> X;
     const int nstage = (KIND == OP_BIN && op.in2 != nullptr) ? 2 : 1;
-    const size_t smem = sizeof(cplx<T>) * (S::N + 2 * (size_t)S::N * (S::CB + 1) + nstage * (size_t)S::N * S::CB) +
+    const size_t smem = sizeof(cplx<T>) * (S::N + 2 * (size_t)S::N * (X::CB + 1) + nstage * (size_t)S::N * X::CB) +
                         (KIND == OP_BIN ? sizeof(T) * (S::M + 1) : 0);
     const void* fn = (const void*)k_x_cols<T, LOGN, KIND>;
     cudaError_t e = set_smem(fn, smem);
     if (e != cudaSuccess) return e;
     int per_sm = 1;
-    e = resident_ctas(fn, S::CB * S::QN, smem, &per_sm);
+    e = resident_ctas(fn, X::THREADS, smem, &per_sm);
     if (e != cudaSuccess) return e;
-    const int64_t nblk = (int64_t)nplanes * (S::N / S::CB);
+    const int64_t nblk = (int64_t)nplanes * (S::N / X::CB);
     int64_t grid = std::min<int64_t>(nblk, (int64_t)per_sm * num_sms());
     if (KIND == OP_BIN) grid = std::min<int64_t>(grid, op.acc_rows);  // one row of bin sums per CTA
-    k_x_cols<T, LOGN, KIND><<<(unsigned)grid, S::CB * S::QN, smem, st>>>(data, out2, op, nplanes);
+    k_x_cols<T, LOGN, KIND><<<(unsigned)grid, X::THREADS, smem, st>>>(data, out2, op, nplanes);
     return cudaGetLastError();
 }
 
