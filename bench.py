@@ -245,6 +245,35 @@ def roofline(phases, np_side, n, fp64, peak, peak_kind):
             "peak_source": f"{peak_kind} hbm_gbs (MEASURED_PEAKS.json)" if peak_kind == "measured" else "fallback"}, table
 
 
+FP64_NOMINAL_TFLOPS = 1.25  # GB300 dense FP64 (no measured FP64 peak is recorded)
+
+
+def fft_flops(n):
+    """Flops of the FFT passes per phase of one FP32/FP64 force evaluation on an n^3 mesh,
+    counting 5 L log2 L for a length-L complex transform and 10 flops per element of the
+    r2c / c2r half-length split and of the per-mode Green / gradient operators."""
+    import math
+    M = n // 2
+    cfft = lambda L: 5.0 * L * math.log2(L)
+    rows = (M + 1) * n                      # rows of the half spectrum along y and columns along x
+    zero = n * n * (cfft(M) + 10.0 * M)     # one r2c or c2r z pass of one mesh
+    return {"fft_zy_fwd": zero + rows * cfft(n),
+            "fft_x_green": rows * (cfft(n) + 20.0 * n),
+            "fft_yz_inv": 3 * rows * cfft(n) + 3 * zero}
+
+
+def alu_roofline(phases, n):
+    """The FP64 passes are bound by FP64 arithmetic on this part: flops per launch of the
+    slowest FFT phase against the nominal FP64 rate."""
+    fl = fft_flops(n)
+    dom = max(fl, key=lambda p: phases[p][0] / max(phases[p][1], 1))
+    ms = phases[dom][0] / max(phases[dom][1], 1)
+    achieved = fl[dom] / (ms * 1e-3) / 1e12
+    return {"kernel": dom, "bound": "alu", "achieved": round(achieved, 3), "peak": FP64_NOMINAL_TFLOPS,
+            "unit": "TFLOP/s", "frac": round(achieved / FP64_NOMINAL_TFLOPS, 4), "flops_per_launch": fl[dom],
+            "peak_source": "nominal GB300 dense FP64 (not measured)"}
+
+
 def e2e(pm, torch, args, rank, world, n_jobs=2):
     """Public-API end to end: ICs from pinned host memory -> k steps -> P(k) back to the host."""
     n_steps = max(100, args.steps + 2)
@@ -564,7 +593,7 @@ def main():
         out["fp64_plain"] = {"value": world * args.np**3 * args.steps / (ms64 * 1e-3), "unit": UNIT,
                              "ms_per_step": ms64 / args.steps,
                              "step_roofline_frac": round(sb64 / (ms64 / args.steps * 1e-3) / 1e9 / peak, 4),
-                             "dominant": roof64, "phases": table64}
+                             "dominant": roof64, "alu_roofline": alu_roofline(ph64, args.nmesh), "phases": table64}
     if not args.no_e2e:
         out["e2e"] = e2e(pm, torch, args, rank, world)
     if not args.no_batch:

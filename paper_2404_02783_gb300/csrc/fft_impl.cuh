@@ -50,6 +50,17 @@ __device__ __forceinline__ void load_twiddles_head(cplx<T>* tw, int L, int count
 }
 
 
+// a / d in the per-mode operators.  FP32 divides as written.  FP64 divides are slow on this
+// part, so FP64 takes the FP32 reciprocal of d refined by two Newton steps
+// r <- r + r (1 - d r) (relative error ~2^-23, then ~2^-46, then below the FP64 rounding).
+template <typename T> __device__ __forceinline__ T div_mode(T a, T d) { return a / d; }
+template <> __device__ __forceinline__ double div_mode<double>(double a, double d) {
+    double r = (double)__frcp_rn((float)d);
+    r = fma(r, fma(-d, r, 1.0), r);
+    r = fma(r, fma(-d, r, 1.0), r);
+    return a * r;
+}
+
 // Opts a kernel into more than 48 KB of dynamic shared memory once per device, so that
 // launches (including those recorded into a CUDA graph) make no further attribute calls.
 static inline cudaError_t set_smem(const void* fn, size_t bytes) {
@@ -433,7 +444,7 @@ __global__ void __launch_bounds__(XShape<T, LOGN, KIND>::THREADS, XShape<T, LOGN
             } else {
                 C phi;
                 if constexpr (KIND == OP_NEWTON || KIND == OP_POTENTIAL) {
-                    phi = (n2 == 0) ? cmake<C>(T(0), T(0)) : cscale(vv, coefT / T(n2));
+                    phi = (n2 == 0) ? cmake<C>(T(0), T(0)) : cscale(vv, div_mode(coefT, T(n2)));
                 } else if constexpr (KIND == OP_ZA) {
                     const bool nyq = (2 * nx == -N) || (2 * ny == -N) || (nz == M);
                     const double* amp = op.amp + (int64_t)field * op.amp_stride;
@@ -479,7 +490,7 @@ __global__ void __launch_bounds__(XShape<T, LOGN, KIND>::THREADS, XShape<T, LOGN
                             Pc.y += cc * o.y;
                             den += cc;
                         }
-                        Pc = cscale(Pc, T(1) / den);
+                        Pc = cscale(Pc, div_mode(T(1), den));
                         *old = Pc;
                         phi = cscale(Pc, T(op.ac2_over_n3));
                     }
