@@ -409,7 +409,23 @@ __global__ void __launch_bounds__(XShape<T, LOGN, KIND>::THREADS, XShape<T, LOGN
             for (int m = 0; m < 8; ++m) base[(size_t)(t + m * Q) * N + c] = v[0][m];
             continue;
         }
-        // ---- per-mode operator on modes (kx = t + m Q, ky = c, kz)
+        if constexpr (KIND == OP_BIN) {
+            // regroup through the exchange buffer so that the thread holds kx = 8 t + m
+            // (m = 0..7): neighbouring kx mostly share a |k| bin, so runs merge in registers
+            __syncthreads();  // the transform's last exchange has been read
+#pragma unroll
+            for (int m = 0; m < 8; ++m) {
+                buf[(size_t)(t + m * Q) * CS + b] = v[0][m];
+                if (cross) buf[(size_t)(N + t + m * Q) * CS + b] = v[1][m];
+            }
+            __syncthreads();
+#pragma unroll
+            for (int m = 0; m < 8; ++m) {
+                v[0][m] = buf[(size_t)(8 * t + m) * CS + b];
+                if (cross) v[1][m] = buf[(size_t)(N + 8 * t + m) * CS + b];
+            }
+        }
+        // ---- per-mode operator on modes (kx = t + m Q, or 8 t + m when binning; ky = c, kz)
         const int ny = (c < M) ? c : c - N;
         const int nz = kz;
         // per-CTA constants, formed once in the working precision (no FP64 work per mode in FP32)
@@ -423,7 +439,7 @@ __global__ void __launch_bounds__(XShape<T, LOGN, KIND>::THREADS, XShape<T, LOGN
         const T wyz = (KIND == OP_BIN) ? iw2[ny < 0 ? -ny : ny] * iw2[nz] * T((nz == 0 || nz == M) ? 1 : 2) : T(1);
     #pragma unroll
         for (int m = 0; m < 8; ++m) {
-            const int i = t + m * Q;
+            const int i = (KIND == OP_BIN) ? 8 * t + m : t + m * Q;
             const int nx = (i < M) ? i : i - N;
             const int n2 = nx * nx + ny * ny + nz * nz;
             const C vv = v[0][m];
