@@ -444,6 +444,13 @@ def estimators(pm, torch, args):
                 "frac": round(gbs / peak, 4), "bytes_model": what}
 
     out = {"workload": f"{np_side}^3 particles on a {n}^3 mesh, L={box:g} Mpc/h, FP32, after 3 steps from z=50"}
+    # the ICs themselves (Philox phases and Box-Muller in FP64, the Zel'dovich x pass, three
+    # inverse transforms, placement); timed on a second context so the run above stays put
+    ic_run = pm.PMRun(pm.make_config(np_side, n, box, A_INIT, A_FINAL, 100))
+    ms_ic = timed(lambda: ic_run.ic(seed=2), reps=3)
+    out["zeldovich_ics"] = {"ms": round(ms_ic, 3), "particles_per_s": round(P / (ms_ic * 1e-3), 1),
+                            "bound": "FP64 Box-Muller of the phases (once per run)"}
+    del ic_run
     e64 = pm.log_edges(64, 1.0, n / 2.0)
     out["power_particles"] = line(timed(lambda: run.power(e64)), 12 * P + 16 * n**3,
                                   "read x (12 B/particle), deposit and transform (16 B/cell)")
