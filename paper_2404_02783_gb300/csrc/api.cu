@@ -445,18 +445,19 @@ pm_status bispectrum_t(pm_ctx* c, const void* field, int nbins, const double* ed
     const cplx<T>* in[1] = {specs};
     T* out[1] = {fields};
     PM_CK(z_c2r<T>(in, out, 1, m, nspec, 0u, 0.0, c->st));
-    std::vector<int4> tri;
-    tri.reserve(B.ntri);
-    for (int i = 0; i < nbins; ++i)
-        for (int j = i; j < nbins; ++j)
-            for (int l = j; l < nbins; ++l) tri.push_back(make_int4(i, j, l, 0));
-    int4* dtri = (int4*)(scratch + B.tri);
+    // units of up to eight triangles sharing (i, j) (see bk_units); never more units than triangles
+    std::vector<int4> units;
+    units.reserve(B.ntri);
+    for (int i = 0, t = 0; i < nbins; ++i)
+        for (int j = i; j < nbins; t += nbins - j, ++j)
+            for (int lb = j / 8; 8 * lb < nbins; ++lb) units.push_back(make_int4(i, j, lb, t + std::max(j, 8 * lb) - j));
+    int4* dunits = (int4*)(scratch + B.tri);
     double* accS = (double*)(scratch + B.accS);
     double* accC = (double*)(scratch + B.accC);
-    PM_CK(cudaMemcpyAsync(dtri, tri.data(), sizeof(int4) * tri.size(), cudaMemcpyHostToDevice, c->st));
+    PM_CK(cudaMemcpyAsync(dunits, units.data(), sizeof(int4) * units.size(), cudaMemcpyHostToDevice, c->st));
     PM_CK(cudaMemsetAsync(accS, 0, sizeof(double) * B.ntri, c->st));
     PM_CK(cudaMemsetAsync(accC, 0, sizeof(double) * B.ntri, c->st));
-    PM_CK(bk_triangles<T>(fields, m, nbins, dtri, B.ntri, accS, accC, c->st));
+    PM_CK(bk_units<T>(fields, m, nbins, dunits, (int)units.size(), accS, accC, c->st));
     std::vector<double> hs(B.ntri), hc(B.ntri);
     PM_CK(cudaMemcpyAsync(hs.data(), accS, sizeof(double) * B.ntri, cudaMemcpyDeviceToHost, c->st));
     PM_CK(cudaMemcpyAsync(hc.data(), accC, sizeof(double) * B.ntri, cudaMemcpyDeviceToHost, c->st));

@@ -70,8 +70,10 @@ cudaError_t axpby(float* y, const float* a, const float* b, int64_t m, float alp
 template <typename T>
 cudaError_t bk_masks(const cplx<T>* spec_n, int n, cplx<T>* out, int m, int nbins, const int16_t* bin_of,
                      const double* wtab, int deconv, cudaStream_t st);
+// unit[u] = (i, j, lb, t): the triangles (i, j, l), l in [max(j, 8 lb), min(nbins, 8 lb + 8)),
+// whose first has index t in the i <= j <= l order; accS / accC indexed by triangle.
 template <typename T>
-cudaError_t bk_triangles(const T* fields, int m, int nbins, const int4* tri, int ntri, double* accS, double* accC,
-                         cudaStream_t st);
+cudaError_t bk_units(const T* fields, int m, int nbins, const int4* unit, int nunit, double* accS, double* accC,
+                     cudaStream_t st);
 
 }  // namespace pm

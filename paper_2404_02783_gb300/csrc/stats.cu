@@ -4,7 +4,7 @@
 // with I_b = IFFT_m[delta 1_b] (unnormalised) and the triangle count is the same sum
 // over N_b = IFFT_m[1_b].  bk_masks builds the 2 nbins masked half spectra on the m
 // grid (first the nbins data fields, then the nbins indicator fields); after their
-// inverse transforms bk_triangles accumulates both sums for every bin triplet.
+// inverse transforms bk_units accumulates both sums for every bin triplet.
 #include "internal.h"
 #include "particles.h"
 
@@ -52,73 +52,100 @@ cudaError_t bk_masks(const cplx<T>* spec_n, int n, cplx<T>* out, int m, int nbin
     return cudaGetLastError();
 }
 
-constexpr int kTriPoints = 64;   // points staged per chunk
-constexpr int kTriPerThread = 8; // triangles per thread per block row
+// Blocked form of the triangle sums: a unit is (i, j, l-block of 8) and covers the triangles
+// (i, j, l) with l in [max(j, 8 lb), min(nbins, 8 lb + 8)); per point it forms I_i I_j once and
+// multiplies it into the eight I_l (read as aligned vectors), so shared-memory traffic per
+// triangle is a fraction of one scalar load.  Rows of a staged point hold the data fields at
+// [0, nbp) and the indicator fields at [nbp, 2 nbp), nbp = nbins rounded up to 8 (zero padded).
+// unit = (i, j, lb, index of triangle (i, j, max(j, 8 lb)) in the i <= j <= l order).
+template <typename T> struct Vec4;
+template <> struct Vec4<float> { typedef float4 type; static constexpr int W = 4; };
+template <> struct Vec4<double> { typedef double2 type; static constexpr int W = 2; };
 
 template <typename T>
-__global__ void __launch_bounds__(512) k_bk_triangles(const T* __restrict__ f, int64_t m3, int nbins,
-                                                      const int4* __restrict__ tri, int ntri,
-                                                      double* __restrict__ accS, double* __restrict__ accC) {
+__global__ void __launch_bounds__(256, 4) k_bk_units(const T* __restrict__ f, int64_t m3, int nbins, int nbp, int npts,
+                                                  const int4* __restrict__ unit, int nunit,
+                                                  double* __restrict__ accS, double* __restrict__ accC) {
+    typedef typename Vec4<T>::type V;
+    constexpr int W = Vec4<T>::W;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* s = reinterpret_cast<T*>(smem_raw);
-    const int nb2 = 2 * nbins;
+    const int stride = 2 * nbp;
     const int tid = threadIdx.x, nthr = blockDim.x;
-    const int t0 = blockIdx.y * kTriPerThread * nthr;
-    int4 my[kTriPerThread];
-    double sS[kTriPerThread], sC[kTriPerThread];
+    const int u = blockIdx.y * nthr + tid;
+    const int4 my = (u < nunit) ? unit[u] : make_int4(0, 0, 0, -1);
+    const int i = my.x, j = my.y, l0 = 8 * my.z;
+    double sS[8], sC[8];
 #pragma unroll
-    for (int k = 0; k < kTriPerThread; ++k) {
-        const int t = t0 + tid + k * nthr;
-        my[k] = (t < ntri) ? tri[t] : make_int4(0, 0, 0, -1);
-        sS[k] = 0.0;
-        sC[k] = 0.0;
-    }
-    for (int64_t c0 = (int64_t)blockIdx.x * kTriPoints; c0 < m3; c0 += (int64_t)gridDim.x * kTriPoints) {
+    for (int q = 0; q < 8; ++q) sS[q] = sC[q] = 0.0;
+    // npts points per chunk: FP32 partial sums over a chunk, FP64 across chunks
+    for (int64_t c0 = (int64_t)blockIdx.x * npts; c0 < m3; c0 += (int64_t)gridDim.x * npts) {
         __syncthreads();
-        for (int e = tid; e < kTriPoints * nb2; e += nthr) {
-            const int b = e / kTriPoints, pnt = e - b * kTriPoints;
-            s[pnt * nb2 + b] = (c0 + pnt < m3) ? f[(size_t)b * m3 + c0 + pnt] : T(0);
+        for (int e = tid; e < npts * stride; e += nthr) {
+            const int b = e / npts, pnt = e - b * npts;
+            const int fb = (b < nbp) ? (b < nbins ? b : -1) : (b - nbp < nbins ? nbins + b - nbp : -1);
+            s[pnt * stride + b] = (fb >= 0 && c0 + pnt < m3) ? f[(size_t)fb * m3 + c0 + pnt] : T(0);
         }
         __syncthreads();
+        if (my.w < 0) continue;
+        T ps[8], pc[8];
 #pragma unroll
-        for (int k = 0; k < kTriPerThread; ++k) {
-            if (my[k].w < 0) continue;
-            const int i = my[k].x, j = my[k].y, l = my[k].z;
-            T ps = T(0), pc = T(0);
-#pragma unroll 8
-            for (int pnt = 0; pnt < kTriPoints; ++pnt) {
-                const T* row = s + pnt * nb2;
-                ps += row[i] * row[j] * row[l];
-                pc += row[nbins + i] * row[nbins + j] * row[nbins + l];
+        for (int q = 0; q < 8; ++q) ps[q] = pc[q] = T(0);
+#pragma unroll 4
+        for (int pnt = 0; pnt < npts; ++pnt) {
+            const T* row = s + pnt * stride;
+            const T a = row[i] * row[j], ac = row[nbp + i] * row[nbp + j];
+            const V* dl = reinterpret_cast<const V*>(row + l0);
+            const V* cl = reinterpret_cast<const V*>(row + nbp + l0);
+#pragma unroll
+            for (int h = 0; h < 8 / W; ++h) {
+                const V d = dl[h], c = cl[h];
+                const T* dv = reinterpret_cast<const T*>(&d);
+                const T* cv = reinterpret_cast<const T*>(&c);
+#pragma unroll
+                for (int w = 0; w < W; ++w) {
+                    ps[h * W + w] += a * dv[w];
+                    pc[h * W + w] += ac * cv[w];
+                }
             }
-            sS[k] += (double)ps;
-            sC[k] += (double)pc;
+        }
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            sS[q] += (double)ps[q];
+            sC[q] += (double)pc[q];
         }
     }
+    if (my.w < 0) return;
+    const int lstart = max(j, l0), lend = min(nbins, l0 + 8);
 #pragma unroll
-    for (int k = 0; k < kTriPerThread; ++k) {
-        if (my[k].w < 0) continue;
-        const int t = t0 + tid + k * nthr;
-        atomicAdd(&accS[t], sS[k]);
-        atomicAdd(&accC[t], sC[k]);
+    for (int q = 0; q < 8; ++q) {
+        const int l = l0 + q;
+        if (l < lstart || l >= lend) continue;
+        atomicAdd(&accS[my.w + (l - lstart)], sS[q]);
+        atomicAdd(&accC[my.w + (l - lstart)], sC[q]);
     }
 }
 
 template <typename T>
-cudaError_t bk_triangles(const T* fields, int m, int nbins, const int4* tri, int ntri, double* accS, double* accC,
-                         cudaStream_t st) {
+cudaError_t bk_units(const T* fields, int m, int nbins, const int4* unit, int nunit, double* accS, double* accC,
+                     cudaStream_t st) {
     const int nthr = 256;
+    const int nbp = (nbins + 7) & ~7;
     const int64_t m3 = (int64_t)m * m * m;
-    int64_t gx = (m3 + kTriPoints - 1) / kTriPoints;
-    if (gx > 152 * 4) gx = 152 * 4;
-    const int gy = (ntri + kTriPerThread * nthr - 1) / (kTriPerThread * nthr);
-    const size_t smem = sizeof(T) * kTriPoints * 2 * nbins;
+    // points per chunk: up to 256, the staged rows within 96 KB of shared memory
+    int npts = (int)((96 * 1024) / (sizeof(T) * 2 * nbp));
+    npts = npts > 256 ? 256 : (npts < 32 ? 32 : npts & ~31);
+    const int gy = (nunit + nthr - 1) / nthr;
+    int64_t gx = (m3 + npts - 1) / npts;
+    const int64_t cap = (152 * 8 + gy - 1) / gy;  // about eight CTAs per SM in all
+    if (gx > cap) gx = cap;
+    const size_t smem = sizeof(T) * (size_t)npts * 2 * nbp;
     if (smem > 48 * 1024) {
-        cudaError_t e = set_smem_once((const void*)k_bk_triangles<T>, smem);
+        cudaError_t e = set_smem_once((const void*)k_bk_units<T>, smem);
         if (e != cudaSuccess) return e;
     }
-    dim3 grid((unsigned)gx, (unsigned)gy);
-    k_bk_triangles<T><<<grid, nthr, smem, st>>>(fields, m3, nbins, tri, ntri, accS, accC);
+    k_bk_units<T><<<dim3((unsigned)gx, (unsigned)gy), nthr, smem, st>>>(fields, m3, nbins, nbp, npts, unit, nunit,
+                                                                         accS, accC);
     return cudaGetLastError();
 }
 
@@ -126,7 +153,7 @@ template cudaError_t bk_masks<float>(const float2*, int, float2*, int, int, cons
                                      cudaStream_t);
 template cudaError_t bk_masks<double>(const double2*, int, double2*, int, int, const int16_t*, const double*, int,
                                       cudaStream_t);
-template cudaError_t bk_triangles<float>(const float*, int, int, const int4*, int, double*, double*, cudaStream_t);
-template cudaError_t bk_triangles<double>(const double*, int, int, const int4*, int, double*, double*, cudaStream_t);
+template cudaError_t bk_units<float>(const float*, int, int, const int4*, int, double*, double*, cudaStream_t);
+template cudaError_t bk_units<double>(const double*, int, int, const int4*, int, double*, double*, cudaStream_t);
 
 }  // namespace pm
