@@ -150,11 +150,9 @@ __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 4 : 2) k_z_c2r(Ptr3<T> P
     constexpr int N = S::N, M = S::M, Q = S::QM, YB = S::YB;
     typedef RowLayout<M, true> LAY;
     constexpr int RS = LAY::RS;
-    constexpr int TWN = (M + 2) & ~1;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* twM = reinterpret_cast<C*>(smem_raw);
-    C* twN = twM + M;
-    C* buf = twN + TWN;
+    C* buf = twM + M;
     const int tid = threadIdx.x;
     const int comp = blockIdx.z;
     const bool grad = (gradz_mask >> comp) & 1u;
@@ -162,53 +160,51 @@ __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 4 : 2) k_z_c2r(Ptr3<T> P
     const int gl = blockIdx.y;
     const size_t g = (size_t)g0 + gl;
     load_stage_twiddles<T, M>(twM);
-    load_twiddles_head<T>(twN, N, M + 1);
     const T kf = kf_arr ? T(kf_arr[g >> LOGN]) : kf0;
     const C* inp = comp == 0 ? P.in[0] : (comp == 1 ? P.in[1] : P.in[2]);
     T* pout = comp == 0 ? P.out[0] : (comp == 1 ? P.out[1] : P.out[2]);
-    C* xb = buf;  // gathered half spectrum; the FFT exchanges reuse the buffer afterwards
-    constexpr int NT = YB * Q, ITERS = ((M + 1) * YB + NT - 1) / NT;
-    // all of the thread's loads are issued before the first shared-memory store, so the
-    // (M + 1) strided row segments are in flight together
-    C X[ITERS];
+    C* xb = buf;  // the pre-processed half spectrum; the FFT exchanges reuse the buffer afterwards
+    // Each thread loads the pairs (X_k, X_{M-k}), k = 0..M/2, of its columns -- all of its
+    // strided row segments in flight together -- and forms in registers
+    //   Y_k = (X_k + X*_{M-k}) + i (X_k - X*_{M-k}) exp(+2 pi i k / N)   (and Y_{M-k} likewise),
+    // the M-point sequence whose inverse transform interleaves the real output.
+    constexpr int NT = YB * Q, NP = (M / 2 + 1) * YB, ITERS = (NP + NT - 1) / NT;
+    C X1[ITERS], X2[ITERS];
 #pragma unroll
     for (int it = 0; it < ITERS; ++it) {
         const int e = tid + it * NT;
-        if (e < (M + 1) * YB) X[it] = inp[spec_row<M>(gl, e / YB, xcl) * N + y0 + e % YB];
+        if (e < NP) {
+            const int k = e / YB, col = y0 + e % YB;
+            X1[it] = inp[spec_row<M>(gl, k, xcl) * N + col];
+            X2[it] = inp[spec_row<M>(gl, M - k, xcl) * N + col];
+        }
     }
+    constexpr int TWS = 1024 / N;  // exp(-2 pi i k / N) = global table entry k TWS
 #pragma unroll
     for (int it = 0; it < ITERS; ++it) {
         const int e = tid + it * NT;
-        if (e < (M + 1) * YB) {
+        if (e < NP) {
             const int k = e / YB, bb = e % YB;
-            C Xk = X[it];
+            C a = X1[it], c = X2[it];
             if (grad) {  // (-i kz) X, Nyquist kz -> 0
-                const T kz = (k == M) ? T(0) : kf * T(k);
-                Xk = cmake<C>(Xk.y * kz, -Xk.x * kz);
+                const T kza = kf * T(k), kzc = (k == 0) ? T(0) : kf * T(M - k);
+                a = cmake<C>(a.y * kza, -a.x * kza);
+                c = cmake<C>(c.y * kzc, -c.x * kzc);
             }
-            xb[bb * RS + LAY::slot(k)] = Xk;
+            if (k == 0) {
+                a.y = T(0);
+                c.y = T(0);
+            }
+            C* r = xb + bb * RS;
+            const C bconj = cconj(c);
+            const C d = cmul(csub(a, bconj), cconj(tw_global<T>(k * TWS)));
+            r[LAY::slot(k)] = cadd(cadd(a, bconj), cmake<C>(-d.y, d.x));
+            if (k > 0 && k < M - k) {
+                const C aconj = cconj(a);
+                const C d2 = cmul(csub(c, aconj), cconj(tw_global<T>((M - k) * TWS)));
+                r[LAY::slot(M - k)] = cadd(cadd(c, aconj), cmake<C>(-d2.y, d2.x));
+            }
         }
-    }
-    __syncthreads();
-    // Y_k = (X_k + X*_{M-k}) + i (X_k - X*_{M-k}) exp(+2 pi i k / N), pairs (k, M-k) per thread
-    for (int e = tid; e < (M / 2 + 1) * YB; e += YB * Q) {
-        const int k = e / YB, bb = e % YB;
-        C* r = xb + bb * RS;
-        C a = r[LAY::slot(k)];
-        C c = r[LAY::slot(M - k)];
-        if (k == 0) {
-            a.y = T(0);
-            c.y = T(0);
-        }
-        const C bconj = cconj(c);
-        const C d = cmul(csub(a, bconj), cconj(twN[k]));
-        const C y = cadd(cadd(a, bconj), cmake<C>(-d.y, d.x));
-        if (k > 0 && k < M - k) {
-            const C aconj = cconj(a);
-            const C d2 = cmul(csub(c, aconj), cconj(twN[M - k]));
-            r[LAY::slot(M - k)] = cadd(cadd(c, aconj), cmake<C>(-d2.y, d2.x));
-        }
-        r[LAY::slot(k)] = y;
     }
     __syncthreads();
     const int b = tid / Q, t = tid % Q;
@@ -622,7 +618,7 @@ template <typename T, int LOGN>
 cudaError_t z_c2r_n(const Ptr3<T>& P, int ncomp, int g0, int rows, int xcl, unsigned mask, double kf, cudaStream_t st,
                     const double* kf_arr) {
     typedef Shape<T, LOGN> S;
-    const size_t smem = sizeof(cplx<T>) * (S::M + ((S::M + 2) & ~1) + (size_t)S::YB * RowLayout<S::M, true>::RS);
+    const size_t smem = sizeof(cplx<T>) * (S::M + (size_t)S::YB * RowLayout<S::M, true>::RS);
     cudaError_t e = set_smem((const void*)k_z_c2r<T, LOGN>, smem);
     if (e != cudaSuccess) return e;
     k_z_c2r<T, LOGN><<<dim3(S::N / S::YB, rows, ncomp), S::YB * S::QM, smem, st>>>(P, mask, (T)kf, kf_arr, g0, xcl);
