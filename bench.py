@@ -259,7 +259,7 @@ def fft_flops(n):
     rows = (M + 1) * n                      # rows of the half spectrum along y and columns along x
     zero = n * n * (cfft(M) + 10.0 * M)     # one r2c or c2r z pass of one mesh
     return {"fft_zy_fwd": zero + rows * cfft(n),
-            "fft_x_green": rows * (cfft(n) + 20.0 * n),
+            "fft_x_green": rows * (3 * cfft(n) + 20.0 * n),   # forward, then phi and -i kx phi back
             "fft_yz_inv": 3 * rows * cfft(n) + 3 * zero}
 
 
