@@ -69,3 +69,17 @@ def test_loss_differences_match_oracle_and_autograd():
     loss.backward()
     assert float(loss) == pytest.approx(L, rel=1e-6)
     assert rel_l2(to_host(wv.grad), to_host(g)) < 1e-5
+
+
+def test_overlapped_reruns_match_a_single_segment():
+    # 9 steps with checkpoints every 2: five segments (the last one of a single step); the
+    # forward run records the last two, the first three are re-run on the second stream
+    # into alternating records while the reverse sweep runs.  One segment of 9 re-runs nothing.
+    pm = lib()
+    c, w, target, run, (box, a_i, a_f, _) = _setup(pm, 32, 64, steps=9)
+    wd, td = to_dev(w), to_dev(target)
+    L1, g1 = run.loss_grad(wd, td, checkpoint_every=9)
+    for every in (2, 1):
+        L, g = run.loss_grad(wd, td, checkpoint_every=every)
+        assert L == pytest.approx(L1, rel=1e-6)
+        assert rel_l2(to_host(g), to_host(g1)) < 1e-5
