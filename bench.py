@@ -499,6 +499,21 @@ def estimators(pm, torch, args):
                          "bispectrum_32^3_6bins_M32_ms": round(ms_bko, 2),
                          "combination_32^3_to_64^3_ms": round(ms_co, 2),
                          "combination_particles_per_s": round(64**3 / (ms_co * 1e-3), 1)}
+    # the linearised Poisson-gauge step (Newtonian-form kick with the GR constraint, |n| <= 4 in FP64)
+    gsteps, gwarm = 20, 3
+    gr = pm.PMRun(pm.make_config(np_side, n, box, A_INIT, A_FINAL, gsteps + gwarm, mode=pm.PM_GR_POISSON, n_lo=4))
+    gr.ic(seed=3)
+    gr.step(gwarm)
+    e0.record(st)
+    gr.step(gsteps)
+    e1.record(st)
+    e1.synchronize()
+    out["gr_poisson_step"] = {"ms_per_step": round(e0.elapsed_time(e1) / gsteps, 4), "steps": gsteps,
+                              "what": f"{np_side}^3 particles, {n}^3 mesh, Poisson-gauge Green's function "
+                                      "with Phi_old and the FP64 island |n| <= 4, otherwise as the headline"}
+    del gr
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
     out["gpu_power_field_cells_per_s"] = round(n**3 / (out["power_field"]["ms"] * 1e-3), 1)
     out["gpu_combination_particles_per_s"] = round(P / (out["displacement_combination"]["ms"] * 1e-3), 1)
     return out
