@@ -80,6 +80,26 @@ def test_bispectrum_matches_oracle(prec):
     np.testing.assert_allclose(b[big], bo[big], rtol=1e-3 if prec == FP32 else 1e-9)
 
 
+@pytest.mark.parametrize("prec", [FP32, FP64])
+def test_bispectrum_many_bins_matches_oracle(prec):
+    # 20 bins: triangles (i, j, l) span three blocks of eight l's, with partial first and last
+    # blocks, as in the 24-bin estimator of the benchmark
+    pm = lib()
+    n, box, m = 64, 2000.0, 64
+    run = _ctx(pm, 16, n, box, prec)
+    f = inputs.lognormal_field(57, n, sigma=0.6)
+    edges = np.linspace(0.5, 20.5, 21)  # |n| <= 20 -> alias free on m = 64 (3 * 20 < 64)
+    b, nt = run.bispectrum(edges, m, field=_field(f, prec))
+    cast = f if prec == FP64 else f.astype(np.float32).astype(np.float64)
+    tri, bo, nto = stats.bispectrum(cast, box, edges, M=m)
+    assert len(b) == len(bo) == 20 * 21 * 22 // 6
+    np.testing.assert_allclose(nt, nto, rtol=1e-5 if prec == FP32 else 1e-12, atol=0.1 if prec == FP32 else 1e-6)
+    ok = nto > 0
+    assert np.array_equal(np.isnan(b), ~ok)
+    scale = np.max(np.abs(bo[ok]))
+    assert np.max(np.abs(b[ok] - bo[ok])) < (1e-4 if prec == FP32 else 1e-10) * scale
+
+
 def test_bispectrum_refuses_aliasing_grid():
     pm = lib()
     run = _ctx(pm, 16, 32, 1000.0, FP32)
