@@ -33,12 +33,14 @@
  * Bin edges are given in units of the fundamental mode k_f = 2 pi / L; a mode with
  * integer wavevector n is in bin b when e_b^2 <= |n|^2 < e_{b+1}^2 (last bin closed).
  *
- * Memory ownership: the library never allocates device memory.  Every device
+ * Memory ownership: the library allocates no device memory per call.  Every device
  * buffer (the context workspace, outputs, scratch) is owned by the caller, who
- * sizes it with the *_size queries.  Host output arrays are caller-owned too.
+ * sizes it with the *_size queries; the one exception is the fixed static array of
+ * pm_cell_sort_static.  Host output arrays are caller-owned too.
  * Streams: calls are asynchronous on the stream given at pm_init (or per call for
  * the stateless operators) except pm_power and pm_bispectrum, which synchronise
- * that stream before returning host results.
+ * that stream before returning host results, and pm_loss_grad, which also runs on a
+ * second stream of the context's own and synchronises both.
  * Errors: every call returns a pm_status; pm_last_error() gives a static,
  * thread-local message for the last failure.  A CUDA error inside a call is
  * returned as PM_ERR_CUDA and leaves the context unusable (pm_destroy it).
