@@ -101,7 +101,7 @@ Layout plan(const pm_config& c) {
     L.amp = take((3 * (size_t)(c.np / 2) * (c.np / 2) + 1) * 8);
     L.bin_of = take((3 * (n / 2) * (n / 2) + 1) * 2);
     L.wtab = take((n / 2 + 1) * 8);
-    L.acc = take(kMaxBins * 8);
+    L.acc = take(2 * kMaxBins * 8);
     L.total = off;
     return L;
 }
@@ -327,9 +327,10 @@ pm_status check_edges(int nbins, const double* edges) {
     return PM_OK;
 }
 
+// p2_out (with field2 only): the auto spectrum of field2 from the same pass.
 template <typename T>
 pm_status power_t(pm_ctx* c, const void* field, const void* field2, int nbins, const double* edges, int deconv,
-                  double* k_out, double* p_out, double* nmodes_out) {
+                  double* k_out, double* p_out, double* nmodes_out, double* p2_out = nullptr) {
     const int n = c->n;
     const void* f1 = field;
     if (!f1) {
@@ -344,10 +345,12 @@ pm_status power_t(pm_ctx* c, const void* field, const void* field2, int nbins, c
     build_bin_table(n, nbins, edges, tab);
     PM_CK(cudaMemcpyAsync(c->at(c->L.bin_of), tab.data(), tab.size() * 2, cudaMemcpyHostToDevice, c->st));
     // per-CTA rows of bin sums in the third spectrum buffer (free here), reduced in a fixed order
+    const bool two = field2 && p2_out;
     double* rows = (double*)c->at(c->L.spec[2]);
     const size_t spec_bytes = (size_t)(n / 2 + 1) * n * n * 2 * c->sT();
-    const int nrows = (int)std::min<size_t>(4 * (size_t)num_sms(), spec_bytes / (sizeof(double) * nbins));
-    PM_CK(cudaMemsetAsync(rows, 0, sizeof(double) * nrows * nbins, c->st));
+    const int nrows = (int)std::min<size_t>(4 * (size_t)num_sms(), spec_bytes / (sizeof(double) * nbins * (two ? 2 : 1)));
+    double* rows2 = two ? rows + (size_t)nrows * nbins : nullptr;
+    PM_CK(cudaMemsetAsync(rows, 0, sizeof(double) * nrows * nbins * (two ? 2 : 1), c->st));
     SpecOp op;
     op.kind = OP_BIN;
     op.fwd = 1;
@@ -355,6 +358,7 @@ pm_status power_t(pm_ctx* c, const void* field, const void* field2, int nbins, c
     op.bin_of = (const int16_t*)c->at(c->L.bin_of);
     op.wtab = (const double*)c->at(c->L.wtab);
     op.acc = rows;
+    op.acc2 = rows2;
     op.acc_rows = nrows;
     op.nbins = nbins;
     op.deconv = deconv ? 1 : 0;
@@ -362,8 +366,9 @@ pm_status power_t(pm_ctx* c, const void* field, const void* field2, int nbins, c
     PM_CK(x_cols<T>((cplx<T>*)s0, nullptr, n / 2 + 1, n, op, c->st));
     double* acc = (double*)c->at(c->L.acc);
     PM_CK(bin_rows_sum(rows, nrows, nbins, acc, c->st));
-    std::vector<double> h(nbins);
-    PM_CK(cudaMemcpyAsync(h.data(), acc, sizeof(double) * nbins, cudaMemcpyDeviceToHost, c->st));
+    if (two) PM_CK(bin_rows_sum(rows2, nrows, nbins, acc + nbins, c->st));
+    std::vector<double> h((two ? 2 : 1) * nbins);
+    PM_CK(cudaMemcpyAsync(h.data(), acc, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, c->st));
     // mode counts and mean |k| per bin follow from the geometry alone
     const std::vector<double>& cnt = mode_counts(n);
     std::vector<double> nm(nbins, 0.0), ks(nbins, 0.0);
@@ -382,9 +387,11 @@ pm_status power_t(pm_ctx* c, const void* field, const void* field2, int nbins, c
         if (w > 0) {
             if (p_out) p_out[b] = V / n6 * h[b] / w;
             if (k_out) k_out[b] = c->kf * ks[b] / w;
+            if (two) p2_out[b] = V / n6 * h[nbins + b] / w;
         } else {
             if (p_out) p_out[b] = NAN;
             if (k_out) k_out[b] = NAN;
+            if (two) p2_out[b] = NAN;
         }
     }
     return PM_OK;
@@ -765,8 +772,9 @@ pm_status pm_linear_bias(pm_ctx* c, const void* delta_h, const void* delta_m, in
     if (terms < 1 || terms > 3) return fail(PM_ERR_INVALID_ARG, "terms must be 1 (b1), 2 (+ b1GR) or 3 (+ k^2)");
     PM_TRY(check_edges(nbins, edges));
     std::vector<double> k(nbins), phm(nbins), pmm(nbins), nm(nbins);
-    PM_TRY(pm_power(c, delta_h, delta_m, nbins, edges, 1, k.data(), phm.data(), nm.data()));
-    PM_TRY(pm_power(c, delta_m, nullptr, nbins, edges, 1, nullptr, pmm.data(), nullptr));
+    // P_hm and P_mm from one pass over the two transforms
+    PM_TRY(c->fp64() ? power_t<double>(c, delta_h, delta_m, nbins, edges, 1, k.data(), phm.data(), nm.data(), pmm.data())
+                     : power_t<float>(c, delta_h, delta_m, nbins, edges, 1, k.data(), phm.data(), nm.data(), pmm.data()));
     const double a = c->a_grid(c->step);
     const double H = pmhost::conformal_hubble(c->cosmo, a);
     // weighted least squares (weights = mode counts) of P_hm/P_mm = b1 [+ b1GR H^2/k^2] [+ c k^2] on k < k_max
@@ -1162,7 +1170,7 @@ void batch_plan(pm_batch& b) {
     b.SCALE = take(B * 8);
     b.BIN = take((3 * (n / 2) * (n / 2) + 1) * 2);
     b.WTAB = take((n / 2 + 1) * 8);
-    b.ACC = take(kMaxBins * 8);
+    b.ACC = take(2 * kMaxBins * 8);
     b.total = off;
 }
 

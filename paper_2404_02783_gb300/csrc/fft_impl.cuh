@@ -355,6 +355,8 @@ __global__ void __launch_bounds__(XShape<T, LOGN, KIND>::THREADS, XShape<T, LOGN
         for (int e = tid; e <= M; e += blockDim.x) iw2[e] = op.deconv ? T(1.0 / (op.wtab[e] * op.wtab[e])) : T(1);
     // OP_BIN: this CTA's row of per-bin sums in global memory (zeroed by the caller)
     double* acc_row = (KIND == OP_BIN) ? op.acc + (size_t)blockIdx.x * op.nbins : nullptr;
+    // with a cross spectrum, optionally the auto spectrum of the second field in the same pass
+    double* acc2_row = (KIND == OP_BIN && cross && op.acc2) ? op.acc2 + (size_t)blockIdx.x * op.nbins : nullptr;
     auto issue = [&](int64_t blk) {
         const size_t pb = (size_t)(blk / NCG) * N * N + (size_t)(blk % NCG) * CB;
         for (int q = tid; q < N * CHUNKS_ROW; q += blockDim.x) {
@@ -431,7 +433,7 @@ __global__ void __launch_bounds__(XShape<T, LOGN, KIND>::THREADS, XShape<T, LOGN
         // OP_BIN: consecutive modes of a thread that fall in the same bin are summed in
         // registers, each run added once to the CTA's row (native FP64 reduction in L2)
         int run_bin = -1;
-        T run_sum = T(0);
+        T run_sum = T(0), run_sum2 = T(0);
         const T wyz = (KIND == OP_BIN) ? iw2[ny < 0 ? -ny : ny] * iw2[nz] * T((nz == 0 || nz == M) ? 1 : 2) : T(1);
     #pragma unroll
         for (int m = 0; m < 8; ++m) {
@@ -445,13 +447,20 @@ __global__ void __launch_bounds__(XShape<T, LOGN, KIND>::THREADS, XShape<T, LOGN
                 if (bin < 0) continue;
                 const C u = cross ? v[1][m] : vv;
                 // w |delta_n|^2 / W^2 (or the cross product), w = 1 on the kz = 0, n/2 planes, 2 elsewhere
-                const T val = (vv.x * u.x + vv.y * u.y) * (iw2[nx < 0 ? -nx : nx] * wyz);
+                const T wgt = iw2[nx < 0 ? -nx : nx] * wyz;
+                const T val = (vv.x * u.x + vv.y * u.y) * wgt;
+                const T val2 = acc2_row ? (u.x * u.x + u.y * u.y) * wgt : T(0);
                 if (bin != run_bin) {
-                    if (run_bin >= 0) atomicAdd(acc_row + run_bin, (double)run_sum);
+                    if (run_bin >= 0) {
+                        atomicAdd(acc_row + run_bin, (double)run_sum);
+                        if (acc2_row) atomicAdd(acc2_row + run_bin, (double)run_sum2);
+                    }
                     run_bin = bin;
                     run_sum = val;
+                    run_sum2 = val2;
                 } else {
                     run_sum += val;
+                    run_sum2 += val2;
                 }
             } else {
                 C phi;
@@ -515,7 +524,10 @@ __global__ void __launch_bounds__(XShape<T, LOGN, KIND>::THREADS, XShape<T, LOGN
             }
         }
         if constexpr (KIND == OP_BIN) {
-            if (run_bin >= 0) atomicAdd(acc_row + run_bin, (double)run_sum);
+            if (run_bin >= 0) {
+                atomicAdd(acc_row + run_bin, (double)run_sum);
+                if (acc2_row) atomicAdd(acc2_row + run_bin, (double)run_sum2);
+            }
             continue;
         }
         if constexpr (KIND == OP_POTENTIAL) {

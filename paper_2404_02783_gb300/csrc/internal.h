@@ -39,6 +39,7 @@ struct SpecOp {
     const int16_t* bin_of = nullptr;  // bin per integer |n|^2 (-1 = none)
     const double* wtab = nullptr;     // CIC sinc^2(pi m / n) for m = 0..n/2
     double* acc = nullptr;            // [acc_rows][nbins]: per-CTA sums of w |delta|^2 / W^2 (zeroed)
+    double* acc2 = nullptr;           // cross spectra only: the same rows for |in2|^2 (null: not wanted)
     int acc_rows = 0;                 // rows available (the x pass runs at most this many CTAs)
     int nbins = 0;
     int deconv = 0;
