@@ -183,7 +183,7 @@ cudaError_t halo_proxy(const T* field, int64_t count, int64_t K, T* out, void* s
 }
 
 size_t halo_proxy_scratch_bytes(int64_t count) {
-    return 256 * sizeof(unsigned long long) + sizeof(uint32_t) * (size_t)(2 * count) + scan_scratch_bytes(count);
+    return 256 * sizeof(unsigned long long) + sizeof(uint32_t) * (size_t)blocks_for(count);
 }
 
 template cudaError_t halo_proxy<float>(const float*, int64_t, int64_t, float*, void*, cudaStream_t);
