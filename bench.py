@@ -480,6 +480,17 @@ def estimators(pm, torch, args):
     out["displacement_combination"] = line(
         timed(lambda: pm.pm_displacement_correction(run.ctx, pair[0].ctx, pair[1].ctx)),
         24 * P + 2 * 12 * (np_side // 2)**3, "read + write the target positions, read both pair positions")
+    # cuFFT (through torch.fft) as a timing baseline for the transforms of one force evaluation:
+    # one r2c of the density and three c2r of the gradient spectra (its Green's function and
+    # gradient multiplies would be extra elementwise passes, not counted)
+    spec = torch.fft.rfftn(delta)
+    ms_r2c = timed(lambda: torch.fft.rfftn(delta), reps=5)
+    ms_c2r = timed(lambda: torch.fft.irfftn(spec, s=delta.shape), reps=5)
+    out["cufft_baseline"] = {"r2c_ms": round(ms_r2c, 4), "c2r_ms": round(ms_c2r, 4),
+                             "force_transforms_ms": round(ms_r2c + 3 * ms_c2r, 4),
+                             "what": f"torch.fft (cuFFT) on a {n}^3 FP32 mesh: one r2c + three c2r, without the "
+                                     "Green's function and gradient passes; never on the product path"}
+    del spec
     del pair, run, delta, dh
     torch.cuda.synchronize()
     torch.cuda.empty_cache()
@@ -625,6 +636,9 @@ def main():
         out["adjoint"] = adjoint(pm, torch, args)
     if not args.no_estimators and rank == 0:
         out["estimators"] = estimators(pm, torch, args)
+        cb = out["estimators"]["cufft_baseline"]
+        cb["ours_fft_phases_ms"] = round(sum(table32[p]["ms_per_launch"] for p in ("fft_zy_fwd", "fft_x_green",
+                                                                                   "fft_yz_inv")), 4)
     if rank == 0:
         out["cpu_baseline"] = cpu_oracle(args.cpu_seconds)
         print(json.dumps(out))
