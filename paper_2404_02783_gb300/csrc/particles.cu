@@ -94,6 +94,43 @@ __global__ void __launch_bounds__(512) k_deposit_tiled(const uint32_t* __restric
     tile_flush<D>(lo, carry, rho, ox, oy, oz, logn);
 }
 
+// R = 1: each thread walks one lattice row of the CTA's block along x and carries the upper-x
+// plane of its CIC stencil to the next particle (the deposit half of the fused update kernel).
+__global__ void __launch_bounds__(512, 2) k_deposit_sweep(const uint32_t* __restrict__ x, int lognp, int logn,
+                                                          float inv_cell_ticks, float mass, float* __restrict__ rho) {
+    typedef DepTile<1> D;
+    static_assert(D::TY * D::TZ == 512, "one thread per (ly, lz); lx runs over the loop");
+    extern __shared__ __align__(16) uint32_t tile_words[];  // D::WORDS
+    uint32_t* lo = tile_words;
+    uint32_t* carry = tile_words + D::CELLS;
+    const int np = 1 << lognp;
+    const int64_t count = (int64_t)1 << (3 * lognp);
+    const int ntz = np / D::TZ, nty = np / D::TY;
+    const int bz = blockIdx.x % ntz, by = (blockIdx.x / ntz) % nty, bx = blockIdx.x / (ntz * nty);
+    const int ox = bx * D::TX - D::H, oy = by * D::TY - D::H, oz = bz * D::TZ - D::HZ;
+    tile_zero<D>(tile_words);
+    __syncthreads();
+    const int lz = threadIdx.x % D::TZ, ly = threadIdx.x / D::TZ;
+    const int64_t id0 = ((((int64_t)(bx * D::TX) << lognp) + by * D::TY + ly) << lognp) + bz * D::TZ + lz;
+    const int64_t xstride = (int64_t)1 << (2 * lognp);
+    SweepCarry sc;
+    uint32_t nu0 = x[id0], nu1 = x[count + id0], nu2 = x[2 * count + id0];
+#pragma unroll 1
+    for (int lx = 0; lx < D::TX; ++lx) {
+        const uint32_t u0 = nu0, u1 = nu1, u2 = nu2;
+        if (lx + 1 < D::TX) {
+            const int64_t idn = id0 + (lx + 1) * xstride;
+            nu0 = x[idn];
+            nu1 = x[count + idn];
+            nu2 = x[2 * count + idn];
+        }
+        sweep_deposit<D>(lo, carry, rho, u0, u1, u2, logn, inv_cell_ticks, ox, oy, oz, mass, sc);
+    }
+    sweep_finish<D>(lo, carry, sc);
+    __syncthreads();
+    tile_flush<D>(lo, carry, rho, ox, oy, oz, logn);
+}
+
 __global__ void k_deposit_frac(const double* __restrict__ x, int64_t count, int n, double mass,
                                double* __restrict__ rho) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count;
@@ -128,6 +165,12 @@ static cudaError_t deposit_tiled_r(const void* x, int np, int n, double mass, vo
     const unsigned blocks = (unsigned)((np / D::TX) * (np / D::TY) * (np / D::TZ));
     const float inv = (float)ldexp(1.0, -(32 - logn));
     const size_t smem = sizeof(uint32_t) * D::WORDS;
+    if (R == 1) {
+        cudaError_t e = set_smem_once((const void*)k_deposit_sweep, smem);
+        if (e != cudaSuccess) return e;
+        k_deposit_sweep<<<blocks, 512, smem, st>>>((const uint32_t*)x, lognp, logn, inv, (float)mass, (float*)rho);
+        return cudaGetLastError();
+    }
     cudaError_t e = set_smem_once((const void*)k_deposit_tiled<R>, smem);
     if (e != cudaSuccess) return e;
     k_deposit_tiled<R><<<blocks, 512, smem, st>>>((const uint32_t*)x, lognp, logn, inv, (float)mass, (float*)rho);

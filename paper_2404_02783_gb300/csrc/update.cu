@@ -125,8 +125,7 @@ __global__ void __launch_bounds__(512, 2) k_ikd_deposit_sweep(const uint32_t* __
     const int64_t xstride = (int64_t)1 << (2 * lognp);
     uint32_t next_cell = 0xffffffffu;  // packed (ix, iy, iz) whose lower plane the registers hold
     float U[4][3];                      // force at the carried plane, corner (b, c) = 2 b + c
-    int dnext = -1;                     // tile cell whose a = 0 plane the carried weights belong to
-    float W[4];
+    SweepCarry sc;                      // deposit weights carried to the next particle's plane
     // the next particle's position and momentum are loaded one iteration ahead, so their
     // memory latency overlaps the current particle's gather, update and deposit
     uint32_t nu0 = x[id0], nu1 = x[count + id0], nu2 = x[2 * count + id0];
@@ -206,64 +205,9 @@ __global__ void __launch_bounds__(512, 2) k_ikd_deposit_sweep(const uint32_t* __
         xo[count + id] = u1;
         xo[2 * count + id] = u2;
         // ---- deposit at the new position
-        {
-            const CicF cx = cic_ticks(u0, logn, inv_cell_ticks);
-            const CicF cy = cic_ticks(u1, logn, inv_cell_ticks);
-            const CicF cz = cic_ticks(u2, logn, inv_cell_ticks);
-            const float wy[2] = {1.0f - cy.w1, cy.w1}, wz[2] = {1.0f - cz.w1, cz.w1};
-            const float m0 = mass * (1.0f - cx.w1), m1 = mass * cx.w1;
-            const int dx = (cx.i0 - ox) & nm, dy = (cy.i0 - oy) & nm, dz = (cz.i0 - oz) & nm;
-            if (dx < D::DX - 1 && dy < D::DY - 1 && dz < D::DZ - 1) {
-                const int c0 = (dx * D::DY + dy) * D::DZ + dz;
-                float w0[4];
-#pragma unroll
-                for (int b = 0; b < 2; ++b)
-#pragma unroll
-                    for (int c = 0; c < 2; ++c) w0[2 * b + c] = m0 * wy[b] * wz[c];
-                if (c0 == dnext) {
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) w0[q] += W[q];
-                } else if (dnext >= 0) {
-#pragma unroll
-                    for (int b = 0; b < 2; ++b)
-#pragma unroll
-                        for (int c = 0; c < 2; ++c) tile_add(lo, carry, dnext + b * D::DZ + c, W[2 * b + c]);
-                }
-#pragma unroll
-                for (int b = 0; b < 2; ++b)
-#pragma unroll
-                    for (int c = 0; c < 2; ++c) {
-                        tile_add(lo, carry, c0 + b * D::DZ + c, w0[2 * b + c]);
-                        W[2 * b + c] = m1 * wy[b] * wz[c];
-                    }
-                dnext = c0 + D::DY * D::DZ;
-            } else {
-                if (dnext >= 0) {
-#pragma unroll
-                    for (int b = 0; b < 2; ++b)
-#pragma unroll
-                        for (int c = 0; c < 2; ++c) tile_add(lo, carry, dnext + b * D::DZ + c, W[2 * b + c]);
-                }
-                dnext = -1;
-                const uint32_t ix[2] = {(uint32_t)cx.i0, (uint32_t)cx.i1}, iy[2] = {(uint32_t)cy.i0, (uint32_t)cy.i1};
-                const float mx[2] = {m0, m1};
-#pragma unroll
-                for (int a = 0; a < 2; ++a)
-#pragma unroll
-                    for (int b = 0; b < 2; ++b) {
-                        float* row = rho + (((ix[a] << logn) + iy[b]) << logn);
-                        atomicAdd(row + cz.i0, mx[a] * wy[b] * wz[0]);
-                        atomicAdd(row + cz.i1, mx[a] * wy[b] * wz[1]);
-                    }
-            }
-        }
+        sweep_deposit<D>(lo, carry, rho, u0, u1, u2, logn, inv_cell_ticks, ox, oy, oz, mass, sc);
     }
-    if (dnext >= 0) {
-#pragma unroll
-        for (int b = 0; b < 2; ++b)
-#pragma unroll
-            for (int c = 0; c < 2; ++c) tile_add(lo, carry, dnext + b * D::DZ + c, W[2 * b + c]);
-    }
+    sweep_finish<D>(lo, carry, sc);
     __syncthreads();
     tile_flush<D>(lo, carry, rho, ox, oy, oz, logn);
 }

@@ -130,6 +130,83 @@ __device__ __forceinline__ void tile_flush(const uint32_t* lo, const uint32_t* c
     }
 }
 
+// Deposit of a thread walking its lattice row along x (R = 1).  The next particle usually
+// sits one cell further in x with the same y and z cells; its lower-x CIC corners are then
+// this particle's upper-x corners, so the upper-plane weights are carried (W, for the cell
+// dnext) and added with the next particle's lower plane: 4 tile atomics a particle instead
+// of 8.  A particle whose stencil leaves the box adds to rho directly.
+struct SweepCarry {
+    int dnext = -1;  // tile cell of the carried plane's (b, c) = (0, 0) corner, -1: none
+    float W[4];      // carried weights, corner (b, c) = 2 b + c
+};
+
+template <class D>
+__device__ __forceinline__ void sweep_deposit(uint32_t* lo, uint32_t* carry, float* __restrict__ rho, uint32_t u0,
+                                              uint32_t u1, uint32_t u2, int logn, float inv_cell_ticks, int ox,
+                                              int oy, int oz, float mass, SweepCarry& sc) {
+    const int nm = (1 << logn) - 1;
+    const CicF cx = cic_ticks(u0, logn, inv_cell_ticks);
+    const CicF cy = cic_ticks(u1, logn, inv_cell_ticks);
+    const CicF cz = cic_ticks(u2, logn, inv_cell_ticks);
+    const float wy[2] = {1.0f - cy.w1, cy.w1}, wz[2] = {1.0f - cz.w1, cz.w1};
+    const float m0 = mass * (1.0f - cx.w1), m1 = mass * cx.w1;
+    const int dx = (cx.i0 - ox) & nm, dy = (cy.i0 - oy) & nm, dz = (cz.i0 - oz) & nm;
+    if (dx < D::DX - 1 && dy < D::DY - 1 && dz < D::DZ - 1) {
+        const int c0 = (dx * D::DY + dy) * D::DZ + dz;
+        float w0[4];
+#pragma unroll
+        for (int b = 0; b < 2; ++b)
+#pragma unroll
+            for (int c = 0; c < 2; ++c) w0[2 * b + c] = m0 * wy[b] * wz[c];
+        if (c0 == sc.dnext) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) w0[q] += sc.W[q];
+        } else if (sc.dnext >= 0) {
+#pragma unroll
+            for (int b = 0; b < 2; ++b)
+#pragma unroll
+                for (int c = 0; c < 2; ++c) tile_add(lo, carry, sc.dnext + b * D::DZ + c, sc.W[2 * b + c]);
+        }
+#pragma unroll
+        for (int b = 0; b < 2; ++b)
+#pragma unroll
+            for (int c = 0; c < 2; ++c) {
+                tile_add(lo, carry, c0 + b * D::DZ + c, w0[2 * b + c]);
+                sc.W[2 * b + c] = m1 * wy[b] * wz[c];
+            }
+        sc.dnext = c0 + D::DY * D::DZ;
+    } else {
+        if (sc.dnext >= 0) {
+#pragma unroll
+            for (int b = 0; b < 2; ++b)
+#pragma unroll
+                for (int c = 0; c < 2; ++c) tile_add(lo, carry, sc.dnext + b * D::DZ + c, sc.W[2 * b + c]);
+        }
+        sc.dnext = -1;
+        const uint32_t ix[2] = {(uint32_t)cx.i0, (uint32_t)cx.i1}, iy[2] = {(uint32_t)cy.i0, (uint32_t)cy.i1};
+        const float mx[2] = {m0, m1};
+#pragma unroll
+        for (int a = 0; a < 2; ++a)
+#pragma unroll
+            for (int b = 0; b < 2; ++b) {
+                float* row = rho + (((ix[a] << logn) + iy[b]) << logn);
+                atomicAdd(row + cz.i0, mx[a] * wy[b] * wz[0]);
+                atomicAdd(row + cz.i1, mx[a] * wy[b] * wz[1]);
+            }
+    }
+}
+
+// The carried plane of the row's last particle.
+template <class D>
+__device__ __forceinline__ void sweep_finish(uint32_t* lo, uint32_t* carry, const SweepCarry& sc) {
+    if (sc.dnext >= 0) {
+#pragma unroll
+        for (int b = 0; b < 2; ++b)
+#pragma unroll
+            for (int c = 0; c < 2; ++c) tile_add(lo, carry, sc.dnext + b * D::DZ + c, sc.W[2 * b + c]);
+    }
+}
+
 // ---------------------------------------------------------------- interp + kick + drift
 // p += kick * g(x);  x += drift * p   (g = -grad phi gathered with the deposit's weights).
 // The eight corner offsets are formed once in 32 bits (n^3 <= 2^30) and serve the
