@@ -70,6 +70,8 @@ typedef enum {
 
 enum { PM_NEWTON = 0, PM_GR_POISSON = 1 };
 enum { PM_FP32_FIXED = 0, PM_FP64 = 1 };
+/* Initial-condition flags (pm_ic_zeldovich, pm_batch_ic). */
+enum { PM_IC_PAIRED = 1, PM_IC_FIXED = 2 };
 
 /* Run configuration (Sec. 3 "Simulation setup"; sizes are powers of two). */
 typedef struct {
@@ -112,10 +114,13 @@ pm_status pm_destroy(pm_ctx* ctx);
  * wavevector from Philox4x32-10 (key = seed, counter = (nx, ny, nz, 0)) with a
  * Box-Muller transform, so every resolution shares its common modes; otherwise
  * white_noise is a device real field w[np][np][np] (ctx precision) of unit variance
- * and the phases are FFT(w) / np^{3/2}.  paired != 0 flips the sign of every phase
- * (the pairing of Sec. 4.2).  Modes with a Nyquist component and the zero mode are 0.
+ * and the phases are FFT(w) / np^{3/2}.  flags: PM_IC_PAIRED flips the sign of every
+ * phase, PM_IC_FIXED scales every phase to unit modulus (|g| = 1, the phase kept), and
+ * both together give the paired-and-fixed pair of the pairing method cited in Sec. 4.2
+ * (B(k) is averaged over the PAIRED and plain runs of one seed).  Modes with a Nyquist
+ * component and the zero mode are 0.  Other flag bits: PM_ERR_INVALID_ARG.
  * Resets the step counter to 0 and the GR potential history. */
-pm_status pm_ic_zeldovich(pm_ctx* ctx, uint64_t seed, const void* white_noise, int paired);
+pm_status pm_ic_zeldovich(pm_ctx* ctx, uint64_t seed, const void* white_noise, int flags);
 
 /* Advance n_steps KDK steps along the a-grid (one force evaluation per step; after
  * the last step of the grid a closing half kick synchronises the momenta).
@@ -214,6 +219,13 @@ pm_status pm_bispectrum(pm_ctx* ctx, const void* field, int nbins, const double*
                         int m, int deconvolve, void* scratch, size_t scratch_bytes,
                         double* b_out, double* ntri_out);
 
+/* Position of triangle (i, j, l), 0 <= i <= j <= l < nbins, in pm_bispectrum's output:
+ * the number of triangles before it in lexicographic order.  Host only (no GPU, no
+ * context).  Sec. 4.2 reports two slices of the table: the equilateral configurations
+ * (j, j, j) and the squeezed ones (b3, j, j), j >= b3, with b3 the bin holding
+ * k3 = 4 k_f.  Indices out of order or range: PM_ERR_INVALID_ARG. */
+pm_status pm_triangle_index(int nbins, int i, int j, int l, int64_t* index);
+
 /* ------------------------------------------------------- gradient of a field loss
  * Field-level fits (the paper's GR displacement and bias are field-level quantities,
  * Secs. 2 and 5) need the gradient of a loss on the final density with respect to the
@@ -255,8 +267,8 @@ pm_status pm_batch_destroy(pm_batch* batch);
 /* Context view of realisation r (particles, density, estimators); valid while the batch
  * lives.  Must not be stepped or destroyed by the caller. */
 pm_status pm_batch_context(pm_batch* batch, int r, pm_ctx** view);
-/* Zel'dovich ICs of every realisation from seeds[r] (as pm_ic_zeldovich). */
-pm_status pm_batch_ic(pm_batch* batch, const uint64_t* seeds, int paired);
+/* Zel'dovich ICs of every realisation from seeds[r] (as pm_ic_zeldovich, same flags). */
+pm_status pm_batch_ic(pm_batch* batch, const uint64_t* seeds, int flags);
 /* n_steps KDK steps of every realisation; use_graph != 0 records the run once (cached for
  * the same start step and length) and replays it as one graph launch ordered after the
  * batch stream's prior work.  PM_ERR_STATE when the a-grid would be overrun. */

@@ -9,6 +9,9 @@ positions.  Sec. 3 starts the runs at z = 50.  Reading used here:
 * delta_n = N^3 g_n sqrt(P(k_n)/V) on the N_p^3 lattice, with g_n the unit complex
   Gaussian of ``philox.hermitian_noise_half`` or g = FFT(w)/N^{3/2} for a caller's
   real white-noise field w; P is the z = 0 linear spectrum (D(1) = 1).
+* Pairing (Sec. 4.2 uses the pairing method of Angulo & Pontzen 2016): "paired" flips
+  the sign of every g_n; "fixed amplitude" replaces g_n by g_n/|g_n| (unit modulus,
+  the same phase), so that |delta_n|^2 = N^6 P(k_n)/V holds mode by mode.
 * Psi_n = i k delta_n / k^2 (the zero mode and Nyquist components are zero).
 * x = q + D(a) Psi(q),  p = a^2 E(a) f(a) D(a) Psi(q), with q the lattice node
   i L / N_p and p = a^2 dx/dt / H0 (Mpc/h in H0 = 1 units).
@@ -20,7 +23,13 @@ import numpy as np
 from . import philox
 
 
-def linear_delta_k(cosmo, n, box, seed=None, white_noise=None, paired=False):
+def fix_amplitude(g):
+    """g / |g| where g != 0, else 0 (the fixed-amplitude phases)."""
+    r = np.abs(g)
+    return np.where(r > 0, g / np.where(r > 0, r, 1.0), 0.0)
+
+
+def linear_delta_k(cosmo, n, box, seed=None, white_noise=None, paired=False, fixed_amplitude=False):
     """delta_n at a = 1 on the rfftn half grid (n, n, n/2+1)."""
     if white_noise is not None:
         w = np.asarray(white_noise, dtype=np.float64).reshape(n, n, n)
@@ -33,6 +42,8 @@ def linear_delta_k(cosmo, n, box, seed=None, white_noise=None, paired=False):
         g[0, 0, 0] = 0.0
     else:
         g = philox.hermitian_noise_half(seed, n)
+    if fixed_amplitude:
+        g = fix_amplitude(g)
     if paired:
         g = -g
     kf = 2.0 * np.pi / box
@@ -69,7 +80,7 @@ def za_displacement(delta_k, n, box):
     return psi
 
 
-def za_displacement_at(cosmo, n, box, seed, ids, paired=False):
+def za_displacement_at(cosmo, n, box, seed, ids, paired=False, fixed_amplitude=False):
     """Psi_j(q) at the lattice nodes of the given particle ids, shape (3, len(ids)) in Mpc/h.
 
     The same field as za_displacement(linear_delta_k(cosmo, n, box, seed)), evaluated by the
@@ -93,6 +104,8 @@ def za_displacement_at(cosmo, n, box, seed, ids, paired=False):
     for ix in range(n):
         nx = int(f[ix])
         g = philox.hermitian_noise_plane(seed, n, ix)
+        if fixed_amplitude:
+            g = fix_amplitude(g)
         if paired:
             g = -g
         n2 = nx * nx + NY * NY + NZ * NZ
@@ -118,9 +131,12 @@ def lattice_ticks(n):
     return np.stack([X.ravel(), Y.ravel(), Z.ravel()]).astype(np.uint32)
 
 
-def zeldovich(cosmo, n, box, a_init, seed=None, white_noise=None, paired=False, fixed=True):
-    """ZA particles at a_init: returns (x, p) with x (3, n^3) ticks or fractions, p (3, n^3)."""
-    dk = linear_delta_k(cosmo, n, box, seed=seed, white_noise=white_noise, paired=paired)
+def zeldovich(cosmo, n, box, a_init, seed=None, white_noise=None, paired=False, fixed=True,
+              fixed_amplitude=False):
+    """ZA particles at a_init: returns (x, p) with x (3, n^3) ticks (fixed=True) or
+    fractions, p (3, n^3); fixed_amplitude selects unit-modulus phases."""
+    dk = linear_delta_k(cosmo, n, box, seed=seed, white_noise=white_noise, paired=paired,
+                        fixed_amplitude=fixed_amplitude)
     psi = za_displacement(dk, n, box).reshape(3, -1)
     D = cosmo.growth_D(a_init)
     f = cosmo.growth_f(a_init)

@@ -21,13 +21,14 @@ LIB_PATH = os.path.join(_HERE, "libpm.so")
 PM_OK = 0
 PM_NEWTON, PM_GR_POISSON = 0, 1
 PM_FP32_FIXED, PM_FP64 = 0, 1
+PM_IC_PAIRED, PM_IC_FIXED = 1, 2
 _STATUS = {0: "PM_OK", 1: "PM_ERR_INVALID_ARG", 2: "PM_ERR_CUDA", 3: "PM_ERR_WORKSPACE", 4: "PM_ERR_TIMEOUT",
            5: "PM_ERR_BOUNDS", 6: "PM_ERR_UNSUPPORTED", 7: "PM_ERR_STATE"}
 
 # every entry point declared in include/pm.h
 EXPORTS = ("pm_workspace_size", "pm_init", "pm_destroy", "pm_ic_zeldovich", "pm_step", "pm_particles",
            "pm_set_particles", "pm_state", "pm_profile", "pm_timings", "pm_density", "pm_potential", "pm_displacement_correction", "pm_power", "pm_halo_proxy", "pm_linear_bias",
-           "pm_bispectrum_scratch_size", "pm_bispectrum", "pm_cic_deposit", "pm_cic_interp",
+           "pm_bispectrum_scratch_size", "pm_bispectrum", "pm_triangle_index", "pm_cic_deposit", "pm_cic_interp",
            "pm_adjoint_scratch_size", "pm_loss_grad", "pm_batch_workspace_size", "pm_batch_init", "pm_batch_destroy", "pm_batch_context", "pm_batch_ic",
            "pm_batch_step", "pm_batch_state", "pm_batch_power", "pm_batch_bias",
            "pm_cell_sort_scratch_size", "pm_cell_sort", "pm_cell_sort_static", "pm_fft_r2c", "pm_fft_c2r", "pm_version", "pm_last_error")
@@ -89,6 +90,7 @@ def lib():
         "pm_linear_bias": (vp, vp, vp, i, pd, d, i, pd, pd, pd, pd),
         "pm_bispectrum_scratch_size": (vp, i, i, ctypes.POINTER(sz)),
         "pm_bispectrum": (vp, vp, i, pd, i, i, vp, sz, pd, pd),
+        "pm_triangle_index": (i, i, i, i, ctypes.POINTER(i64)),
         "pm_adjoint_scratch_size": (vp, i, ctypes.POINTER(sz)),
         "pm_loss_grad": (vp, vp, vp, i, vp, sz, pd, vp),
         "pm_batch_workspace_size": (cfgp, i, ctypes.POINTER(sz)),
@@ -167,8 +169,12 @@ def pm_destroy(ctx):
     _check(lib().pm_destroy(ctx))
 
 
-def pm_ic_zeldovich(ctx, seed, white_noise=None, paired=False):
-    _check(lib().pm_ic_zeldovich(ctx, ctypes.c_uint64(seed), _ptr(white_noise), int(bool(paired))))
+def _ic_flags(paired, fixed):
+    return (PM_IC_PAIRED if paired else 0) | (PM_IC_FIXED if fixed else 0)
+
+
+def pm_ic_zeldovich(ctx, seed, white_noise=None, paired=False, fixed=False):
+    _check(lib().pm_ic_zeldovich(ctx, ctypes.c_uint64(seed), _ptr(white_noise), _ic_flags(paired, fixed)))
 
 
 def pm_step(ctx, n_steps=1):
@@ -261,6 +267,20 @@ def pm_bispectrum(ctx, edges, m, scratch, field=None, deconvolve=True):
     return b, c
 
 
+def pm_triangle_index(nbins, i, j, l):
+    out = ctypes.c_int64()
+    _check(lib().pm_triangle_index(int(nbins), int(i), int(j), int(l), ctypes.byref(out)))
+    return out.value
+
+
+def bispectrum_configurations(nbins, k3_bin):
+    """Rows of pm_bispectrum's table for the equilateral triangles (j, j, j), j = 0..nbins-1,
+    and the squeezed ones (k3_bin, j, j), j = k3_bin..nbins-1 (Sec. 4.2, Fig. Bk)."""
+    eq = np.array([pm_triangle_index(nbins, j, j, j) for j in range(nbins)], dtype=np.int64)
+    sq = np.array([pm_triangle_index(nbins, k3_bin, j, j) for j in range(k3_bin, nbins)], dtype=np.int64)
+    return eq, sq
+
+
 def pm_cic_deposit(x, count, precision, n, mass, rho, stream=None):
     _check(lib().pm_cic_deposit(_ptr(x), int(count), precision, int(n), float(mass), _ptr(rho), _stream(stream)))
 
@@ -328,8 +348,8 @@ class PMRun:
             _lib.pm_destroy(ctx)
             self.ctx = None
 
-    def ic(self, seed=0, white_noise=None, paired=False):
-        pm_ic_zeldovich(self.ctx, seed, white_noise, paired)
+    def ic(self, seed=0, white_noise=None, paired=False, fixed=False):
+        pm_ic_zeldovich(self.ctx, seed, white_noise, paired, fixed)
 
     def step(self, n=1):
         pm_step(self.ctx, n)
@@ -439,9 +459,10 @@ class PMBatch:
             _lib.pm_batch_destroy(h)
             self.h = None
 
-    def ic(self, seeds, paired=False):
+    def ic(self, seeds, paired=False, fixed=False):
         s = np.ascontiguousarray(seeds, dtype=np.uint64)
-        _check(lib().pm_batch_ic(self.h, s.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)), int(bool(paired))))
+        _check(lib().pm_batch_ic(self.h, s.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)),
+                                 _ic_flags(paired, fixed)))
 
     def step(self, n=1, graph=True):
         _check(lib().pm_batch_step(self.h, int(n), int(bool(graph))))

@@ -580,8 +580,10 @@ pm_status pm_state(pm_ctx* c, int* step, double* a, int* synchronised) {
     return PM_OK;
 }
 
-pm_status pm_ic_zeldovich(pm_ctx* c, uint64_t seed, const void* white_noise, int paired) {
+pm_status pm_ic_zeldovich(pm_ctx* c, uint64_t seed, const void* white_noise, int flags) {
     if (!c) return fail(PM_ERR_INVALID_ARG, "null context");
+    if (flags & ~(PM_IC_PAIRED | PM_IC_FIXED)) return fail(PM_ERR_INVALID_ARG, "unknown IC flags");
+    const bool paired = (flags & PM_IC_PAIRED) != 0;
     const int np = c->np;
     const double a = c->cfg.a_init;
     const double D = pmhost::growth_D(c->cosmo, a);
@@ -594,13 +596,14 @@ pm_status pm_ic_zeldovich(pm_ctx* c, uint64_t seed, const void* white_noise, int
     op.kind = OP_ZA;
     op.kf = c->kf;
     op.amp = (const double*)c->at(c->L.amp);
+    op.fixed_amp = (flags & PM_IC_FIXED) ? 1 : 0;
     const double sign = paired ? -1.0 : 1.0;
     double scale = 1.0;
     if (white_noise) {
         if (c->fp64()) PM_TRY(forward_to_y<double>(c, white_noise, s0, np));
         else PM_TRY(forward_to_y<float>(c, white_noise, s0, np));
         op.fwd = 1;
-        scale = std::pow((double)np, -1.5);
+        if (!op.fixed_amp) scale = std::pow((double)np, -1.5);
     } else {
         if (c->fp64()) PM_CK(noise<double>((double2*)s0, np, seed, c->st));
         else PM_CK(noise<float>((float2*)s0, np, seed, c->st));
@@ -821,6 +824,16 @@ pm_status pm_bispectrum_scratch_size(const pm_ctx* c, int m, int nbins, size_t* 
     if (!pow2(m) || m < 16 || m > 1024) return fail(PM_ERR_INVALID_ARG, "m must be a power of two in 16..1024");
     if (nbins < 1 || nbins > 64) return fail(PM_ERR_INVALID_ARG, "bispectrum needs 1..64 bins");
     *bytes = bk_plan((int)c->sT(), m, nbins).total;
+    return PM_OK;
+}
+
+pm_status pm_triangle_index(int nbins, int i, int j, int l, int64_t* index) {
+    if (!index) return fail(PM_ERR_INVALID_ARG, "null argument");
+    if (nbins < 1 || i < 0 || i > j || j > l || l >= nbins) return fail(PM_ERR_INVALID_ARG, "not a triangle i <= j <= l");
+    int64_t before = 0;
+    for (int a = 0; a < i; ++a) before += (int64_t)(nbins - a) * (nbins - a + 1) / 2;  // (j, l) pairs with a <= j <= l
+    for (int b = i; b < j; ++b) before += nbins - b;                                  // l in [b, nbins)
+    *index = before + (l - j);
     return PM_OK;
 }
 
@@ -1352,9 +1365,9 @@ pm_status pm_batch_context(pm_batch* b, int r, pm_ctx** view) {
     return PM_OK;
 }
 
-pm_status pm_batch_ic(pm_batch* b, const uint64_t* seeds, int paired) {
+pm_status pm_batch_ic(pm_batch* b, const uint64_t* seeds, int flags) {
     if (!b || !seeds) return fail(PM_ERR_INVALID_ARG, "null argument");
-    for (int r = 0; r < b->B; ++r) PM_TRY(pm_ic_zeldovich(b->views[r], seeds[r], nullptr, paired));
+    for (int r = 0; r < b->B; ++r) PM_TRY(pm_ic_zeldovich(b->views[r], seeds[r], nullptr, flags));
     b->step = 0;
     b->synced = true;
     b->rho_valid = false;

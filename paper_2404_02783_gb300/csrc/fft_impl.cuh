@@ -469,8 +469,13 @@ __global__ void __launch_bounds__(XShape<T, LOGN, KIND>::THREADS, XShape<T, LOGN
                 } else if constexpr (KIND == OP_ZA) {
                     const bool nyq = (2 * nx == -N) || (2 * ny == -N) || (nz == M);
                     const double* amp = op.amp + (int64_t)field * op.amp_stride;
+                    C g = vv;
+                    if (op.fixed_amp) {  // keep the phase, set |g| = 1
+                        const T r2 = g.x * g.x + g.y * g.y;
+                        g = (r2 > T(0)) ? cscale(g, rsqrt(r2)) : cmake<C>(T(0), T(0));
+                    }
                     phi = (n2 == 0 || nyq) ? cmake<C>(T(0), T(0))
-                                           : cscale(vv, T(op.coef / (kf * kf) * amp[n2] / (double)n2));
+                                           : cscale(g, T(op.coef / (kf * kf) * amp[n2] / (double)n2));
                 } else {  // OP_GR
                     if (n2 == 0) {
                         phi = cmake<C>(T(0), T(0));

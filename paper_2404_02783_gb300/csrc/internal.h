@@ -35,6 +35,7 @@ struct SpecOp {
     double2* island = nullptr;  // double2 [(n_lo+1)(2 n_lo+1)^2]
     // Zel'dovich
     const double* amp = nullptr;  // sqrt(P(k)/V) per integer |n|^2
+    int fixed_amp = 0;            // phases scaled to unit modulus first (fixed amplitudes)
     // power spectrum
     const int16_t* bin_of = nullptr;  // bin per integer |n|^2 (-1 = none)
     const double* wtab = nullptr;     // CIC sinc^2(pi m / n) for m = 0..n/2

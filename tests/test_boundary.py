@@ -85,3 +85,22 @@ def test_no_cpu_fallback_without_a_device(pm):
     st = L.pm_cic_deposit(ctypes.c_void_p(4096), 1, 0, 16, 1.0, ctypes.c_void_p(4096), None)
     assert st == 6
     assert "device" in L.pm_last_error().decode().lower()
+
+
+def test_triangle_index_follows_the_bispectrum_table_order(pm):
+    # host-only: the position of (i, j, l) in pm_bispectrum's output is the oracle's
+    # lexicographic enumeration of the triangles i <= j <= l
+    from oracle import stats
+    for nb in (1, 2, 5, 24):
+        tri = stats.triangles(nb)
+        assert len(tri) == nb * (nb + 1) * (nb + 2) // 6
+        for k, (i, j, l) in enumerate(tri):
+            assert pm.pm_triangle_index(nb, i, j, l) == k
+    for bad in ((5, 2, 1, 3), (5, 0, 0, 5), (5, -1, 0, 0), (0, 0, 0, 0)):
+        with pytest.raises(pm.PMError) as e:
+            pm.pm_triangle_index(*bad)
+        assert e.value.status == 1
+    eq, sq = pm.bispectrum_configurations(6, 2)
+    tri = stats.triangles(6)
+    assert [tri[k] for k in eq] == [(j, j, j) for j in range(6)]
+    assert [tri[k] for k in sq] == [(2, j, j) for j in range(2, 6)]

@@ -35,21 +35,23 @@ def _disp(x, np_side):
 
 
 @pytest.mark.parametrize("prec", [FP32, FP64])
-@pytest.mark.parametrize("source", ["philox", "white_noise", "paired"])
+@pytest.mark.parametrize("source", ["philox", "white_noise", "paired", "fixed", "paired_fixed", "white_noise_fixed"])
 def test_zeldovich_ic_matches_oracle(prec, source):
     pm = lib()
     np_side, nmesh, box, a_i = 32, 64, 1000.0, 1.0 / 51.0
     run = _run(pm, np_side, nmesh, box, a_i, 1.0, 10, prec)
     c = Cosmology()
-    kw = {}
-    if source == "white_noise":
+    fixed = source.endswith("fixed")
+    kw = {"fixed_amplitude": fixed}
+    if source.startswith("white_noise"):
         w = inputs.gaussian_field(41, np_side)
-        run.ic(white_noise=to_dev(w if prec == FP64 else w.astype(np.float32)))
+        run.ic(white_noise=to_dev(w if prec == FP64 else w.astype(np.float32)), fixed=fixed)
         kw["white_noise"] = w if prec == FP64 else w.astype(np.float32).astype(np.float64)
     else:
-        run.ic(seed=12345, paired=(source == "paired"))
+        paired = source.startswith("paired")
+        run.ic(seed=12345, paired=paired, fixed=fixed)
         kw["seed"] = 12345
-        kw["paired"] = source == "paired"
+        kw["paired"] = paired
     xg, pg = _host_particles(run)
     xo, po = ic.zeldovich(c, np_side, box, a_i, fixed=(prec == FP32), **kw)
     tol = 2e-6 if prec == FP32 else 1e-11

@@ -170,3 +170,41 @@ def test_paired_gr_newton_combination_pipeline(prec):
     d_o = min_image(positions_box_units(want) - positions_box_units(ref["t"]))
     # FP32: the GR displacement is a difference of two FP32 runs (~0.5% relative noise)
     assert np.linalg.norm(d_g - d_o) < (2e-2 if prec == FP32 else 1e-9) * np.linalg.norm(d_o)
+
+
+@pytest.mark.parametrize("prec", [FP32, FP64])
+def test_paired_fixed_bispectrum_slices_match_oracle(prec):
+    # Sec. 4.2: B(k) averaged over a paired-and-fixed pair of Zel'dovich ICs, reported on
+    # the equilateral and the squeezed (k3 = 4 k_f) triangles of the table
+    pm = lib()
+    np_side, n, box, m, a_i = 32, 32, 1000.0, 64, 0.5
+    run = _ctx(pm, np_side, n, box, prec, a_i=a_i)
+    edges = np.arange(0.5, 16.0, 1.0)       # unit-width shells centred on |n| = 1..15
+    nb = len(edges) - 1
+    k3_bin = int(np.searchsorted(edges, 4.0)) - 1
+    assert edges[k3_bin] < 4.0 < edges[k3_bin + 1]
+    c = Cosmology()
+    got, want, scale = [], [], 0.0
+    for paired in (False, True):
+        run.ic(seed=21, paired=paired, fixed=True)
+        b, nt = run.bispectrum(edges, m)
+        x, _ = ic.zeldovich(c, np_side, box, a_i, seed=21, paired=paired, fixed=(prec == FP32),
+                            fixed_amplitude=True)
+        _, bo, nto = stats.bispectrum(cic.density_contrast(x, n), box, edges, M=m)
+        np.testing.assert_allclose(nt, nto, rtol=1e-5 if prec == FP32 else 1e-12, atol=0.1 if prec == FP32 else 1e-6)
+        got.append(b)
+        want.append(bo)
+        scale = max(scale, np.nanmax(np.abs(bo)))
+    ok = nto > 0
+    b_avg, bo_avg = 0.5 * (got[0] + got[1]), 0.5 * (want[0] + want[1])
+    assert np.array_equal(np.isnan(b_avg), ~ok)
+    # the pair average cancels the leading (Gaussian) part: tolerances against the single-run scale
+    tol = (2e-4 if prec == FP32 else 1e-9) * scale
+    assert np.max(np.abs(b_avg[ok] - bo_avg[ok])) < tol
+    eq, sq = pm.bispectrum_configurations(nb, k3_bin)
+    tri = stats.triangles(nb)
+    assert [tri[t] for t in sq] == [(k3_bin, j, j) for j in range(k3_bin, nb)]
+    for rows in (eq, sq):
+        live = ok[rows]
+        assert live.sum() >= 3
+        assert np.max(np.abs(b_avg[rows][live] - bo_avg[rows][live])) < tol

@@ -114,3 +114,67 @@ def test_plane_noise_and_direct_mode_sum_match_the_full_grid():
     # paired phases flip the sign
     assert np.allclose(ic.za_displacement_at(c, 16, 300.0, 7, [5], paired=True),
                        -ic.za_displacement_at(c, 16, 300.0, 7, [5]), rtol=0, atol=0)
+
+
+def _bin_mean_linear_power(c, n, box, edges):
+    """Per bin, the mean of P_lin(k_n) over every full-grid wavevector n (components in
+    [-n/2, n/2), |n| <= n/2, n != 0) of the bin, counting the modes with a Nyquist
+    component (which carry no phase) as zero power: brute force over the whole grid."""
+    f = np.arange(-(n // 2), n // 2)
+    NX, NY, NZ = np.meshgrid(f, f, f, indexing="ij")
+    n2 = (NX * NX + NY * NY + NZ * NZ).ravel()
+    nyq = ((NX == -(n // 2)) | (NY == -(n // 2)) | (NZ == -(n // 2))).ravel()
+    kf = 2 * np.pi / box
+    nb = len(edges) - 1
+    num, den = np.zeros(nb), np.zeros(nb)
+    for m2, q in zip(n2, nyq):
+        if m2 == 0 or m2 > (n // 2)**2:
+            continue
+        kn = np.sqrt(float(m2))
+        b = int(np.searchsorted(edges, kn, side="right")) - 1
+        if kn == edges[-1]:
+            b = nb - 1
+        if not 0 <= b < nb:
+            continue
+        den[b] += 1.0
+        if not q:
+            num[b] += c.power_linear(kf * kn)
+    return num / den
+
+
+def test_fixed_amplitude_ic_has_the_input_spectrum_exactly():
+    # Fixed amplitudes (|g_n| = 1): the measured P(k) of the linear field equals the bin
+    # mean of the input spectrum with no cosmic variance; Gaussian amplitudes scatter.
+    from oracle import stats
+    n, box, c = 16, 800.0, Cosmology()
+    # edges between integer |n|^2 (no mode on an inner edge), the last one at n/2, closed
+    edges = np.sqrt([0.5, 2.5, 6.5, 12.5, 24.5, 40.5, 64.0])
+    want = _bin_mean_linear_power(c, n, box, edges)
+    for seed in (3, 4):
+        for paired in (False, True):
+            dk = ic.linear_delta_k(c, n, box, seed=seed, paired=paired, fixed_amplitude=True)
+            delta = np.fft.irfftn(dk, s=(n, n, n), axes=(0, 1, 2))
+            _, pk, _ = stats.power_spectrum(delta, box, edges, deconvolve=False)
+            np.testing.assert_allclose(pk, want, rtol=1e-12)
+    dk = ic.linear_delta_k(c, n, box, seed=3)
+    _, pk, _ = stats.power_spectrum(np.fft.irfftn(dk, s=(n, n, n), axes=(0, 1, 2)), box, edges, deconvolve=False)
+    assert np.max(np.abs(pk / want - 1.0)) > 1e-2
+
+
+def test_fixed_amplitude_keeps_phases_and_hermitian_symmetry():
+    n = 16
+    g = philox.hermitian_noise_half(5, n)
+    gf = ic.fix_amplitude(g)
+    live = np.abs(g) > 0
+    assert np.max(np.abs(np.abs(gf[live]) - 1.0)) < 1e-15
+    assert np.array_equal(gf[~live], g[~live])
+    # same phase: g_fixed * |g| reproduces g
+    assert np.max(np.abs(gf * np.abs(g) - g)) < 1e-15 * np.max(np.abs(g))
+    back = np.fft.rfftn(np.fft.irfftn(gf, s=(n, n, n), axes=(0, 1, 2)))
+    assert np.max(np.abs(back - gf)) < 1e-12
+    # the one-plane form for full-size meshes agrees with the full grid
+    c = Cosmology()
+    psi = ic.za_displacement(ic.linear_delta_k(c, n, 300.0, seed=5, fixed_amplitude=True), n, 300.0).reshape(3, -1)
+    ids = np.array([0, 7, n**3 - 1, 1234])
+    got = ic.za_displacement_at(c, n, 300.0, 5, ids, fixed_amplitude=True)
+    assert np.max(np.abs(got - psi[:, ids])) < 1e-12 * np.max(np.abs(psi))
