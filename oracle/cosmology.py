@@ -64,6 +64,15 @@ class Cosmology:
         return dlnE + 1.0 / (a**2 * E**3 * self._growth_integral(a))
 
     # ---------------------------------------------------------------- leapfrog
+    def growth_D2(self, a):
+        """Second-order growth D2 = -(3/7) D^2 Om(a)^(-1/143) (Bouchet et al. 1995 fit;
+        exact -3/7 D^2 for Om = 1).  Sec. 3: the paper's ICs are second-order LPT."""
+        return -3.0 / 7.0 * self.growth_D(a)**2 * self.omega_m_a(a)**(-1.0 / 143.0)
+
+    def growth_f2(self, a):
+        """dln D2 / dln a = 2 Om(a)^(6/11) (Bouchet et al. 1995 fit)."""
+        return 2.0 * self.omega_m_a(a)**(6.0 / 11.0)
+
     def kick_factor(self, a0, a1):
         """K(a0, a1) = int_{a0}^{a1} da / (a^2 E(a)): dp/da = -grad(phi)/(a^2 E)."""
         val, _ = integrate.quad(lambda a: 1.0 / (a * a * self.E(a)), float(a0), float(a1),

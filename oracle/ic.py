@@ -1,4 +1,4 @@
-"""Zel'dovich (first-order LPT) initial conditions on a particle lattice.
+"""Zel'dovich (first-order LPT) and second-order LPT initial conditions on a particle lattice.
 
 Oracle (test infrastructure only).
 
@@ -123,6 +123,39 @@ def za_displacement_at(cosmo, n, box, seed, ids, paired=False, fixed_amplitude=F
     return out / n**3
 
 
+def lpt2_displacement(delta_k, n, box):
+    """Second-order Lagrangian displacement Psi2 (shape (3, n, n, n), Mpc/h) at D = 1.
+
+    Bouchet et al. (1995), Scoccimarro (1998): with the first-order potential
+    laplacian(phi1) = delta (so Psi1 = -grad phi1), the second-order potential solves
+    laplacian(phi2) = sum_{i<j} (phi1_ii phi1_jj - phi1_ij^2), and Psi2 = grad phi2; the
+    position is x = q + D Psi1 + D2 Psi2 with D2 < 0.  Derivatives are spectral on the
+    n^3 lattice; the source is the product of the mesh fields (no de-aliasing); the zero
+    mode and every mode with a Nyquist component of phi2 are dropped (as for Psi1).
+    """
+    kf = 2.0 * np.pi / box
+    f = philox.signed_freqs(n).astype(np.float64)
+    fz = np.arange(n // 2 + 1, dtype=np.float64)
+    KX, KY, KZ = np.meshgrid(kf * f, kf * f, kf * fz, indexing="ij")
+    K = (KX, KY, KZ)
+    k2 = KX * KX + KY * KY + KZ * KZ
+    inv_k2 = np.zeros_like(k2)
+    inv_k2[k2 > 0] = 1.0 / k2[k2 > 0]
+    phi1_k = -delta_k * inv_k2
+    # phi1_ij = IFFT[(i k_i)(i k_j) phi1_k] = IFFT[-k_i k_j phi1_k]
+    d2 = {}
+    for i in range(3):
+        for j in range(i, 3):
+            d2[i, j] = np.fft.irfftn(-K[i] * K[j] * phi1_k, s=(n, n, n), axes=(0, 1, 2))
+    src = (d2[0, 0] * d2[1, 1] - d2[0, 1]**2) + (d2[0, 0] * d2[2, 2] - d2[0, 2]**2) \
+        + (d2[1, 1] * d2[2, 2] - d2[1, 2]**2)
+    src_k = np.fft.rfftn(src)
+    NX, NY, NZ = np.meshgrid(philox.signed_freqs(n), philox.signed_freqs(n), np.arange(n // 2 + 1), indexing="ij")
+    nyq = (np.abs(NX) == n // 2) | (np.abs(NY) == n // 2) | (NZ == n // 2)
+    phi2_k = np.where(nyq, 0.0, -src_k * inv_k2)
+    return np.stack([np.fft.irfftn(1j * K[j] * phi2_k, s=(n, n, n), axes=(0, 1, 2)) for j in range(3)])
+
+
 def lattice_ticks(n):
     """Lattice node coordinates in ticks, particle id = (ix n + iy) n + iz."""
     step = 2**32 // n
@@ -132,24 +165,30 @@ def lattice_ticks(n):
 
 
 def zeldovich(cosmo, n, box, a_init, seed=None, white_noise=None, paired=False, fixed=True,
-              fixed_amplitude=False):
-    """ZA particles at a_init: returns (x, p) with x (3, n^3) ticks (fixed=True) or
-    fractions, p (3, n^3); fixed_amplitude selects unit-modulus phases."""
+              fixed_amplitude=False, lpt_order=1):
+    """Lagrangian ICs at a_init: returns (x, p) with x (3, n^3) ticks (fixed=True) or
+    fractions, p (3, n^3); fixed_amplitude selects unit-modulus phases; lpt_order = 2
+    adds D2 Psi2 to the positions and a^2 E f2 D2 Psi2 to the momenta."""
     dk = linear_delta_k(cosmo, n, box, seed=seed, white_noise=white_noise, paired=paired,
                         fixed_amplitude=fixed_amplitude)
     psi = za_displacement(dk, n, box).reshape(3, -1)
     D = cosmo.growth_D(a_init)
     f = cosmo.growth_f(a_init)
     E = float(cosmo.E(a_init))
+    disp = D * psi
     p = a_init**2 * E * f * D * psi
+    if lpt_order == 2:
+        psi2 = lpt2_displacement(dk, n, box).reshape(3, -1)
+        D2 = cosmo.growth_D2(a_init)
+        disp = disp + D2 * psi2
+        p = p + a_init**2 * E * cosmo.growth_f2(a_init) * D2 * psi2
     if fixed:
         q = lattice_ticks(n).astype(np.int64)
-        disp = np.rint(D * psi * (2.0**32 / box)).astype(np.int64)
-        x = ((q + disp) % 2**32).astype(np.uint32)
+        x = ((q + np.rint(disp * (2.0**32 / box)).astype(np.int64)) % 2**32).astype(np.uint32)
     else:
         i = np.arange(n, dtype=np.float64) / n
         X, Y, Z = np.meshgrid(i, i, i, indexing="ij")
         q = np.stack([X.ravel(), Y.ravel(), Z.ravel()])
-        x = q + D * psi / box
+        x = q + disp / box
         x = x - np.floor(x)
     return x, p
