@@ -451,6 +451,10 @@ def estimators(pm, torch, args):
     ms_ic = timed(lambda: ic_run.ic(seed=2), reps=3)
     out["zeldovich_ics"] = {"ms": round(ms_ic, 3), "particles_per_s": round(P / (ms_ic * 1e-3), 1),
                             "bound": "FP64 Box-Muller of the phases (once per run)"}
+    ms_ic2 = timed(lambda: ic_run.ic(seed=2, lpt_order=2), reps=3)
+    out["lpt2_ics"] = {"ms": round(ms_ic2, 3), "particles_per_s": round(P / (ms_ic2 * 1e-3), 1),
+                       "what": "second-order LPT ICs: the Zel'dovich chain plus four more three-output "
+                               "FFT chains (derivatives of each Psi1 component, then Psi2) and the source"}
     del ic_run
     e64 = pm.log_edges(64, 1.0, n / 2.0)
     out["power_particles"] = line(timed(lambda: run.power(e64)), 12 * P + 16 * n**3,

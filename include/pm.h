@@ -10,7 +10,8 @@
  * (Eq. powerspectrum) and bispectrum (Eq. bispectre) of the counting density
  * (Sec. 4).  This library implements that data path on one GPU:
  *
- *   pm_ic_zeldovich            Zel'dovich initial conditions (Sec. 2 nLPT, n = 1; Sec. 3 IC at z = 50)
+ *   pm_ic_zeldovich            Lagrangian initial conditions, first (Zel'dovich) or second order
+ *                              (Sec. 2 nLPT, n = 1, 2; Sec. 3 ICs at z = 50)
  *   pm_step                    CIC deposit, r2c FFT, Green's function (Newtonian, or the
  *                              linearised Poisson-gauge constraint), spectral gradient,
  *                              c2r FFT, CIC interpolation + kick + drift (KDK in a)
@@ -71,7 +72,7 @@ typedef enum {
 enum { PM_NEWTON = 0, PM_GR_POISSON = 1 };
 enum { PM_FP32_FIXED = 0, PM_FP64 = 1 };
 /* Initial-condition flags (pm_ic_zeldovich, pm_batch_ic). */
-enum { PM_IC_PAIRED = 1, PM_IC_FIXED = 2 };
+enum { PM_IC_PAIRED = 1, PM_IC_FIXED = 2, PM_IC_2LPT = 4 };
 
 /* Run configuration (Sec. 3 "Simulation setup"; sizes are powers of two). */
 typedef struct {
@@ -117,8 +118,13 @@ pm_status pm_destroy(pm_ctx* ctx);
  * and the phases are FFT(w) / np^{3/2}.  flags: PM_IC_PAIRED flips the sign of every
  * phase, PM_IC_FIXED scales every phase to unit modulus (|g| = 1, the phase kept), and
  * both together give the paired-and-fixed pair of the pairing method cited in Sec. 4.2
- * (B(k) is averaged over the PAIRED and plain runs of one seed).  Modes with a Nyquist
- * component and the zero mode are 0.  Other flag bits: PM_ERR_INVALID_ARG.
+ * (B(k) is averaged over the PAIRED and plain runs of one seed).  PM_IC_2LPT adds the
+ * second-order Lagrangian displacement (Sec. 3: the paper's ICs at z = 50 are 2LPT):
+ * x = q + D Psi1 + D2 Psi2, p = a^2 E (f D Psi1 + f2 D2 Psi2), Psi2 = grad phi2 with
+ * laplacian(phi2) = sum_{i<j} (phi1_ii phi1_jj - phi1_ij^2), Psi1 = -grad phi1,
+ * D2 = -(3/7) D^2 Om(a)^(-1/143), f2 = 2 Om(a)^(6/11); derivatives are spectral on the
+ * np^3 lattice, the source is formed there without de-aliasing.  Modes with a Nyquist
+ * component and the zero mode are 0 (Psi1 and Psi2).  Other flag bits: PM_ERR_INVALID_ARG.
  * Resets the step counter to 0 and the GR potential history. */
 pm_status pm_ic_zeldovich(pm_ctx* ctx, uint64_t seed, const void* white_noise, int flags);
 

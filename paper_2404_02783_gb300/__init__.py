@@ -21,7 +21,7 @@ LIB_PATH = os.path.join(_HERE, "libpm.so")
 PM_OK = 0
 PM_NEWTON, PM_GR_POISSON = 0, 1
 PM_FP32_FIXED, PM_FP64 = 0, 1
-PM_IC_PAIRED, PM_IC_FIXED = 1, 2
+PM_IC_PAIRED, PM_IC_FIXED, PM_IC_2LPT = 1, 2, 4
 _STATUS = {0: "PM_OK", 1: "PM_ERR_INVALID_ARG", 2: "PM_ERR_CUDA", 3: "PM_ERR_WORKSPACE", 4: "PM_ERR_TIMEOUT",
            5: "PM_ERR_BOUNDS", 6: "PM_ERR_UNSUPPORTED", 7: "PM_ERR_STATE"}
 
@@ -169,12 +169,14 @@ def pm_destroy(ctx):
     _check(lib().pm_destroy(ctx))
 
 
-def _ic_flags(paired, fixed):
-    return (PM_IC_PAIRED if paired else 0) | (PM_IC_FIXED if fixed else 0)
+def _ic_flags(paired, fixed, lpt_order):
+    if lpt_order not in (1, 2):
+        raise ValueError("lpt_order must be 1 (Zel'dovich) or 2")
+    return (PM_IC_PAIRED if paired else 0) | (PM_IC_FIXED if fixed else 0) | (PM_IC_2LPT if lpt_order == 2 else 0)
 
 
-def pm_ic_zeldovich(ctx, seed, white_noise=None, paired=False, fixed=False):
-    _check(lib().pm_ic_zeldovich(ctx, ctypes.c_uint64(seed), _ptr(white_noise), _ic_flags(paired, fixed)))
+def pm_ic_zeldovich(ctx, seed, white_noise=None, paired=False, fixed=False, lpt_order=1):
+    _check(lib().pm_ic_zeldovich(ctx, ctypes.c_uint64(seed), _ptr(white_noise), _ic_flags(paired, fixed, lpt_order)))
 
 
 def pm_step(ctx, n_steps=1):
@@ -348,8 +350,8 @@ class PMRun:
             _lib.pm_destroy(ctx)
             self.ctx = None
 
-    def ic(self, seed=0, white_noise=None, paired=False, fixed=False):
-        pm_ic_zeldovich(self.ctx, seed, white_noise, paired, fixed)
+    def ic(self, seed=0, white_noise=None, paired=False, fixed=False, lpt_order=1):
+        pm_ic_zeldovich(self.ctx, seed, white_noise, paired, fixed, lpt_order)
 
     def step(self, n=1):
         pm_step(self.ctx, n)
@@ -459,10 +461,10 @@ class PMBatch:
             _lib.pm_batch_destroy(h)
             self.h = None
 
-    def ic(self, seeds, paired=False, fixed=False):
+    def ic(self, seeds, paired=False, fixed=False, lpt_order=1):
         s = np.ascontiguousarray(seeds, dtype=np.uint64)
         _check(lib().pm_batch_ic(self.h, s.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)),
-                                 _ic_flags(paired, fixed)))
+                                 _ic_flags(paired, fixed, lpt_order)))
 
     def step(self, n=1, graph=True):
         _check(lib().pm_batch_step(self.h, int(n), int(bool(graph))))

@@ -199,6 +199,49 @@ pm_status forward_to_y(pm_ctx* c, const void* real, void* spec, int n) {
     return PM_OK;
 }
 
+// The three-output gradient chain on the np^3 lattice: out_j = sum_n (-i k_j) F(g_n) e^{i n.q}
+// with g the spectrum in spec[0] (real_in == null) or the forward transform of real_in,
+// and F the OP_ZA filter of op (Zel'dovich amplitude, identity or inverse Laplacian).
+template <typename T>
+pm_status za_chain(pm_ctx* c, const void* real_in, SpecOp op, void* const* out) {
+    const int np = c->np;
+    cplx<T>* s0 = (cplx<T>*)c->at(c->L.spec[0]);
+    cplx<T>* s1 = (cplx<T>*)c->at(c->L.spec[1]);
+    cplx<T>* s2 = (cplx<T>*)c->at(c->L.spec[2]);
+    op.kind = OP_ZA;
+    op.kf = c->kf;
+    op.fwd = real_in ? 1 : 0;
+    if (real_in) PM_TRY(forward_to_y<T>(c, real_in, s0, np));
+    PM_CK(x_cols<T>(s0, s1, np / 2 + 1, np, op, c->st));
+    PM_CK(y_rows_grad3<T>(s0, s1, s2, (int64_t)(np / 2 + 1) * np, np, c->kf, c->st));
+    const cplx<T>* in[3] = {s1, s2, s0};
+    T* o[3] = {(T*)out[0], (T*)out[1], (T*)out[2]};
+    PM_CK(z_c2r<T>(in, o, 3, np, 1, 4u, c->kf, c->st));
+    return PM_OK;
+}
+
+// Second-order LPT displacement Psi2 (into out) from Psi1 (three np^3 meshes): the
+// derivatives of each Psi1 component build the source S in two scratch meshes, then
+// Psi2 = grad phi2 with laplacian(phi2) = S.  Modes with a Nyquist component are dropped,
+// as in the first-order displacement.
+template <typename T>
+pm_status lpt2_displacement(pm_ctx* c, void* const* psi1, void* s, void* a, void* const* out) {
+    const double inv_n3 = std::pow((double)c->np, -3.0);
+    for (int comp = 0; comp < 3; ++comp) {
+        SpecOp od;
+        od.za_filter = ZA_IDENTITY;  // out_j = d_j Psi1_comp
+        od.coef = -inv_n3;
+        od.amp = (const double*)c->at(c->L.amp);
+        PM_TRY(za_chain<T>(c, psi1[comp], od, out));
+        PM_CK(lpt2_source(comp, out, s, a, c->np3, c->cfg.precision, c->st));
+    }
+    SpecOp o2;
+    o2.za_filter = ZA_INV_LAPLACE;  // out_j = d_j phi2, phi2 = laplacian^-1 S
+    o2.coef = inv_n3;
+    o2.amp = (const double*)c->at(c->L.amp);
+    return za_chain<T>(c, s, o2, out);
+}
+
 // Counting density of the context's particles (mass (n/np)^3 per particle) on rho.
 pm_status deposit_particles(pm_ctx* c, void* rho) {
     Phase ph(c, PM_PHASE_DEPOSIT);
@@ -582,51 +625,56 @@ pm_status pm_state(pm_ctx* c, int* step, double* a, int* synchronised) {
 
 pm_status pm_ic_zeldovich(pm_ctx* c, uint64_t seed, const void* white_noise, int flags) {
     if (!c) return fail(PM_ERR_INVALID_ARG, "null context");
-    if (flags & ~(PM_IC_PAIRED | PM_IC_FIXED)) return fail(PM_ERR_INVALID_ARG, "unknown IC flags");
+    if (flags & ~(PM_IC_PAIRED | PM_IC_FIXED | PM_IC_2LPT)) return fail(PM_ERR_INVALID_ARG, "unknown IC flags");
     const bool paired = (flags & PM_IC_PAIRED) != 0;
     const int np = c->np;
     const double a = c->cfg.a_init;
     const double D = pmhost::growth_D(c->cosmo, a);
     const double f = pmhost::growth_f(c->cosmo, a);
     const double E = pmhost::E(c->cosmo, a);
-    void* s0 = c->at(c->L.spec[0]);
-    void* s1 = c->at(c->L.spec[1]);
-    void* s2 = c->at(c->L.spec[2]);
     SpecOp op;
-    op.kind = OP_ZA;
-    op.kf = c->kf;
+    op.za_filter = ZA_AMP;
     op.amp = (const double*)c->at(c->L.amp);
     op.fixed_amp = (flags & PM_IC_FIXED) ? 1 : 0;
     const double sign = paired ? -1.0 : 1.0;
     double scale = 1.0;
     if (white_noise) {
-        if (c->fp64()) PM_TRY(forward_to_y<double>(c, white_noise, s0, np));
-        else PM_TRY(forward_to_y<float>(c, white_noise, s0, np));
-        op.fwd = 1;
         if (!op.fixed_amp) scale = std::pow((double)np, -1.5);
     } else {
+        void* s0 = c->at(c->L.spec[0]);
         if (c->fp64()) PM_CK(noise<double>((double2*)s0, np, seed, c->st));
         else PM_CK(noise<float>((float2*)s0, np, seed, c->st));
-        op.fwd = 0;
     }
     op.coef = -sign * scale;
-    void* psi[3] = {c->at(c->L.force[0]), c->at(c->L.force[1]), c->at(c->L.force[2])};
-    if (c->fp64()) {
-        PM_CK(x_cols<double>((double2*)s0, (double2*)s1, np / 2 + 1, np, op, c->st));
-        PM_CK(y_rows_grad3<double>((double2*)s0, (double2*)s1, (double2*)s2, (int64_t)(np / 2 + 1) * np, np, c->kf,
-                                   c->st));
-        const double2* in[3] = {(double2*)s1, (double2*)s2, (double2*)s0};
-        double* out[3] = {(double*)psi[0], (double*)psi[1], (double*)psi[2]};
-        PM_CK(z_c2r<double>(in, out, 3, np, 1, 4u, c->kf, c->st));
+    void* force[3] = {c->at(c->L.force[0]), c->at(c->L.force[1]), c->at(c->L.force[2])};
+    if (!(flags & PM_IC_2LPT)) {
+        if (c->fp64()) PM_TRY(za_chain<double>(c, white_noise, op, force));
+        else PM_TRY(za_chain<float>(c, white_noise, op, force));
+        PM_CK(ic_place(c->at(c->L.x), c->at(c->L.p), force, np, c->cfg.precision, D, a * a * E * f * D, c->cfg.box,
+                       c->st));
     } else {
-        PM_CK(x_cols<float>((float2*)s0, (float2*)s1, np / 2 + 1, np, op, c->st));
-        PM_CK(y_rows_grad3<float>((float2*)s0, (float2*)s1, (float2*)s2, (int64_t)(np / 2 + 1) * np, np, c->kf,
-                                  c->st));
-        const float2* in[3] = {(float2*)s1, (float2*)s2, (float2*)s0};
-        float* out[3] = {(float*)psi[0], (float*)psi[1], (float*)psi[2]};
-        PM_CK(z_c2r<float>(in, out, 3, np, 1, 4u, c->kf, c->st));
+        // Psi1 in the momentum array, the source and its partial sum in the position array
+        // (both are written last, by the placement), Psi2 in the force meshes
+        const size_t sT = c->sT();
+        char* pb = (char*)c->at(c->L.p);
+        char* xb = (char*)c->at(c->L.x);
+        void* psi1[3] = {pb, pb + c->np3 * sT, pb + 2 * c->np3 * sT};
+        void* s = xb;
+        void* acc = xb + c->np3 * sT;
+        if (c->fp64()) {
+            PM_TRY(za_chain<double>(c, white_noise, op, psi1));
+            PM_TRY(lpt2_displacement<double>(c, psi1, s, acc, force));
+        } else {
+            PM_TRY(za_chain<float>(c, white_noise, op, psi1));
+            PM_TRY(lpt2_displacement<float>(c, psi1, s, acc, force));
+        }
+        // second-order growth, D2 = -(3/7) D^2 Om(a)^(-1/143), f2 = 2 Om(a)^(6/11) (Bouchet et al. 1995)
+        const double om = pmhost::omega_m_a(c->cosmo, a);
+        const double D2 = -3.0 / 7.0 * D * D * std::pow(om, -1.0 / 143.0);
+        const double f2 = 2.0 * std::pow(om, 6.0 / 11.0);
+        PM_CK(ic_place2(c->at(c->L.x), c->at(c->L.p), psi1, force, np, c->cfg.precision, D, D2, a * a * E * f * D,
+                        a * a * E * f2 * D2, c->cfg.box, c->st));
     }
-    PM_CK(ic_place(c->at(c->L.x), c->at(c->L.p), psi, np, c->cfg.precision, D, a * a * E * f * D, c->cfg.box, c->st));
     c->step = 0;
     c->synced = true;
     c->have_phi = false;

@@ -474,8 +474,10 @@ __global__ void __launch_bounds__(XShape<T, LOGN, KIND>::THREADS, XShape<T, LOGN
                         const T r2 = g.x * g.x + g.y * g.y;
                         g = (r2 > T(0)) ? cscale(g, rsqrt(r2)) : cmake<C>(T(0), T(0));
                     }
-                    phi = (n2 == 0 || nyq) ? cmake<C>(T(0), T(0))
-                                           : cscale(g, T(op.coef / (kf * kf) * amp[n2] / (double)n2));
+                    const double filt = op.za_filter == ZA_IDENTITY  ? op.coef
+                                        : op.za_filter == ZA_INV_LAPLACE ? op.coef / (kf * kf * (double)n2)
+                                                                         : op.coef / (kf * kf) * amp[n2] / (double)n2;
+                    phi = (n2 == 0 || nyq) ? cmake<C>(T(0), T(0)) : cscale(g, T(filt));
                 } else {  // OP_GR
                     if (n2 == 0) {
                         phi = cmake<C>(T(0), T(0));

@@ -20,6 +20,10 @@ enum OpKind {
     OP_POTENTIAL = 6   // Newtonian potential only: IFFT_x(phi)
 };
 
+// Per-mode filter of OP_ZA (the same three-output gradient chain serves the Zel'dovich
+// displacement, the derivatives of a real mesh and the second-order LPT displacement).
+enum ZaFilter { ZA_AMP = 0, ZA_IDENTITY = 1, ZA_INV_LAPLACE = 2 };
+
 struct SpecOp {
     int kind = OP_FWD_STORE;
     int fwd = 1;              // forward x-FFT of the input first
@@ -36,6 +40,7 @@ struct SpecOp {
     // Zel'dovich
     const double* amp = nullptr;  // sqrt(P(k)/V) per integer |n|^2
     int fixed_amp = 0;            // phases scaled to unit modulus first (fixed amplitudes)
+    int za_filter = 0;            // ZA_AMP: coef amp[|n|^2] / k^2; ZA_IDENTITY: coef; ZA_INV_LAPLACE: coef / k^2
     // power spectrum
     const int16_t* bin_of = nullptr;  // bin per integer |n|^2 (-1 = none)
     const double* wtab = nullptr;     // CIC sinc^2(pi m / n) for m = 0..n/2

@@ -409,6 +409,112 @@ cudaError_t ic_place(void* x, void* p, void* const* psi, int np, int precision, 
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------- second-order LPT
+// With Psi1 = -grad phi1, phi1_ij = -d_j Psi1_i, and the 2LPT source
+//   S = sum_{i<j} (phi1_ii phi1_jj - phi1_ij^2)
+// (Bouchet et al. 1995; Scoccimarro 1998) is gathered over the three components:
+//   stage 0 (Psi1_x): S = -(d_y Psi_x)^2 - (d_z Psi_x)^2,   A = d_x Psi_x
+//   stage 1 (Psi1_y): S += A d_y Psi_y - (d_z Psi_y)^2,      A += d_y Psi_y
+//   stage 2 (Psi1_z): S += A d_z Psi_z
+template <typename T>
+__global__ void k_lpt2_source(int stage, const T* __restrict__ d0, const T* __restrict__ d1, const T* __restrict__ d2,
+                              T* __restrict__ s, T* __restrict__ a, int64_t count) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        if (stage == 0) {
+            const T y = d1[i], z = d2[i];
+            s[i] = -(y * y) - z * z;
+            a[i] = d0[i];
+        } else if (stage == 1) {
+            const T y = d1[i], z = d2[i], ai = a[i];
+            s[i] += ai * y - z * z;
+            a[i] = ai + y;
+        } else {
+            s[i] += a[i] * d2[i];
+        }
+    }
+}
+
+cudaError_t lpt2_source(int stage, void* const* d, void* s, void* a, int64_t count, int precision, cudaStream_t st) {
+    if (precision == PM_FP32_FIXED)
+        k_lpt2_source<float><<<grid_for(count, 256), 256, 0, st>>>(stage, (const float*)d[0], (const float*)d[1],
+                                                                   (const float*)d[2], (float*)s, (float*)a, count);
+    else
+        k_lpt2_source<double><<<grid_for(count, 256), 256, 0, st>>>(stage, (const double*)d[0], (const double*)d[1],
+                                                                    (const double*)d[2], (double*)s, (double*)a, count);
+    return cudaGetLastError();
+}
+
+// x = q + D1 Psi1 + D2 Psi2, p = pfac1 Psi1 + pfac2 Psi2.  Psi1 may live in p: each thread
+// reads the three components of its particle before writing them (no __restrict__ there).
+struct Psi3 {
+    const void* c[3];
+};
+
+__global__ void k_ic2_ticks(uint32_t* __restrict__ x, float* p, Psi3 ps1, Psi3 ps2, int lognp, double disp1,
+                            double disp2, double pfac1, double pfac2) {
+    const int64_t count = (int64_t)1 << (3 * lognp);
+    const int sh = 32 - lognp;
+    const int mask = (1 << lognp) - 1;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t q[3] = {(uint32_t)((i >> (2 * lognp)) & mask) << sh, (uint32_t)((i >> lognp) & mask) << sh,
+                               (uint32_t)(i & mask) << sh};
+        double a1[3], a2[3];
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            a1[j] = (double)((const float*)ps1.c[j])[i];
+            a2[j] = (double)((const float*)ps2.c[j])[i];
+        }
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            x[j * count + i] = q[j] + (uint32_t)__double2ll_rn(a1[j] * disp1 + a2[j] * disp2);
+            p[j * count + i] = (float)(pfac1 * a1[j] + pfac2 * a2[j]);
+        }
+    }
+}
+
+__global__ void k_ic2_frac(double* __restrict__ x, double* p, Psi3 ps1, Psi3 ps2, int lognp, double disp1,
+                           double disp2, double pfac1, double pfac2) {
+    const int64_t count = (int64_t)1 << (3 * lognp);
+    const int mask = (1 << lognp) - 1;
+    const double inv_np = ldexp(1.0, -lognp);
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const double q[3] = {(double)((i >> (2 * lognp)) & mask) * inv_np, (double)((i >> lognp) & mask) * inv_np,
+                             (double)(i & mask) * inv_np};
+        double a1[3], a2[3];
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            a1[j] = ((const double*)ps1.c[j])[i];
+            a2[j] = ((const double*)ps2.c[j])[i];
+        }
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            double xj = q[j] + (disp1 * a1[j] + disp2 * a2[j]);
+            xj -= floor(xj);
+            x[j * count + i] = xj;
+            p[j * count + i] = pfac1 * a1[j] + pfac2 * a2[j];
+        }
+    }
+}
+
+cudaError_t ic_place2(void* x, void* p, void* const* psi1, void* const* psi2, int np, int precision, double D1,
+                      double D2, double pfac1, double pfac2, double box, cudaStream_t st) {
+    const int lognp = ilog2(np);
+    const int64_t count = (int64_t)np * np * np;
+    const Psi3 a = {{psi1[0], psi1[1], psi1[2]}}, b = {{psi2[0], psi2[1], psi2[2]}};
+    if (precision == PM_FP32_FIXED) {
+        k_ic2_ticks<<<grid_for(count, 256), 256, 0, st>>>((uint32_t*)x, (float*)p, a, b, lognp,
+                                                          D1 * 4294967296.0 / box, D2 * 4294967296.0 / box, pfac1,
+                                                          pfac2);
+    } else {
+        k_ic2_frac<<<grid_for(count, 256), 256, 0, st>>>((double*)x, (double*)p, a, b, lognp, D1 / box, D2 / box,
+                                                         pfac1, pfac2);
+    }
+    return cudaGetLastError();
+}
+
 // ---------------------------------------------------------------- Philox phases
 // Philox4x32-10 (Salmon, Moraes, Dror & Shaw, SC'11): ten rounds of two 32x32->64
 // multiplies with the Philox multipliers, xor with the key, word permutation, and

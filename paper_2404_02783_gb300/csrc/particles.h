@@ -28,6 +28,12 @@ cudaError_t interp_kick_drift_deposit(void* x, void* p, int np, int precision, i
                                       int nfields = 1, const double* scale_arr = nullptr, void* x_out = nullptr);
 cudaError_t ic_place(void* x, void* p, void* const* psi, int np, int precision, double D, double pfac, double box,
                      cudaStream_t st);
+// Second-order LPT source, accumulated over three stages, one per displacement component c:
+// d[j] = d Psi1_c / d x_j on the np^3 lattice; s and a are np^3 meshes (ctx precision).
+cudaError_t lpt2_source(int stage, void* const* d, void* s, void* a, int64_t count, int precision, cudaStream_t st);
+// x = q + D1 Psi1 + D2 Psi2, p = pfac1 Psi1 + pfac2 Psi2; psi1 may be the p array itself.
+cudaError_t ic_place2(void* x, void* p, void* const* psi1, void* const* psi2, int np, int precision, double D1,
+                      double D2, double pfac1, double pfac2, double box, cudaStream_t st);
 template <typename T>
 cudaError_t noise(cplx<T>* spec, int n, uint64_t seed, cudaStream_t st);
 cudaError_t combine(void* xt, const void* xg, const void* xn, void* xi_out, int npt, int npc, int precision,

@@ -117,3 +117,16 @@ def test_batched_paired_fixed_ics_match_the_oracle():
         q = ic.lattice_ticks(NP)
         assert rel_l2(_disp(xb, q), _disp(xo, q)) < 2e-6
         assert rel_l2(pb, po) < 2e-6
+
+
+def test_batched_2lpt_ics_match_the_oracle():
+    pm = lib()
+    b = pm.PMBatch(_cfg(pm), boxes=BOXES)
+    b.ic(SEEDS, lpt_order=2)
+    c = Cosmology()
+    for r, (box, seed) in enumerate(zip(BOXES, SEEDS)):
+        xb, pb = _batch_particles(b, r)
+        xo, po = ic.zeldovich(c, NP, box, A_I, seed=seed, lpt_order=2)
+        q = ic.lattice_ticks(NP)
+        assert rel_l2(_disp(xb, q), _disp(xo, q)) < 2e-6
+        assert rel_l2(pb, po) < 2e-6

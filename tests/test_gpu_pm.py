@@ -35,21 +35,23 @@ def _disp(x, np_side):
 
 
 @pytest.mark.parametrize("prec", [FP32, FP64])
-@pytest.mark.parametrize("source", ["philox", "white_noise", "paired", "fixed", "paired_fixed", "white_noise_fixed"])
+@pytest.mark.parametrize("source", ["philox", "white_noise", "paired", "fixed", "paired_fixed", "white_noise_fixed",
+                                    "lpt2", "white_noise_lpt2", "paired_fixed_lpt2"])
 def test_zeldovich_ic_matches_oracle(prec, source):
     pm = lib()
     np_side, nmesh, box, a_i = 32, 64, 1000.0, 1.0 / 51.0
     run = _run(pm, np_side, nmesh, box, a_i, 1.0, 10, prec)
     c = Cosmology()
-    fixed = source.endswith("fixed")
-    kw = {"fixed_amplitude": fixed}
+    fixed = "fixed" in source
+    order = 2 if source.endswith("lpt2") else 1
+    kw = {"fixed_amplitude": fixed, "lpt_order": order}
     if source.startswith("white_noise"):
         w = inputs.gaussian_field(41, np_side)
-        run.ic(white_noise=to_dev(w if prec == FP64 else w.astype(np.float32)), fixed=fixed)
+        run.ic(white_noise=to_dev(w if prec == FP64 else w.astype(np.float32)), fixed=fixed, lpt_order=order)
         kw["white_noise"] = w if prec == FP64 else w.astype(np.float32).astype(np.float64)
     else:
         paired = source.startswith("paired")
-        run.ic(seed=12345, paired=paired, fixed=fixed)
+        run.ic(seed=12345, paired=paired, fixed=fixed, lpt_order=order)
         kw["seed"] = 12345
         kw["paired"] = paired
     xg, pg = _host_particles(run)
@@ -58,6 +60,31 @@ def test_zeldovich_ic_matches_oracle(prec, source):
     assert rel_l2(_disp(xg, np_side), _disp(xo, np_side)) < tol
     assert rel_l2(pg, po) < tol
     assert run.state() == (0, a_i, True)
+
+
+@pytest.mark.parametrize("prec", [FP32, FP64])
+@pytest.mark.parametrize("np_side,nmesh", [(32, 32), (32, 64), (16, 64)])
+def test_second_order_lpt_term_matches_oracle(prec, np_side, nmesh):
+    # late start (a = 0.5, delta_rms ~ 0.2 per cell) so that D2 Psi2 is resolved in ticks:
+    # the second-order part alone, x_2LPT - x_ZA and p_2LPT - p_ZA, against the oracle's
+    pm = lib()
+    box, a_i = 1000.0, 0.5
+    run = _run(pm, np_side, nmesh, box, a_i, 1.0, 4, prec)
+    c = Cosmology()
+    out = []
+    for order in (1, 2):
+        run.ic(seed=77, lpt_order=order)
+        out.append(_host_particles(run))
+    (x1, p1), (x2, p2) = out
+    xo1, po1 = ic.zeldovich(c, np_side, box, a_i, seed=77, fixed=(prec == FP32))
+    xo2, po2 = ic.zeldovich(c, np_side, box, a_i, seed=77, fixed=(prec == FP32), lpt_order=2)
+    dg = min_image(positions_box_units(x2) - positions_box_units(x1))
+    do = min_image(positions_box_units(xo2) - positions_box_units(xo1))
+    assert np.max(np.abs(do)) > 1e-4
+    tol = 2e-3 if prec == FP32 else 1e-9
+    assert rel_l2(dg, do) < tol
+    assert rel_l2(p2 - p1, po2 - po1) < tol
+    assert rel_l2(_disp(x2, np_side), _disp(xo2, np_side)) < (1e-5 if prec == FP32 else 1e-11)
 
 
 @pytest.mark.parametrize("prec", [FP32, FP64])
