@@ -13,7 +13,9 @@ with a_{n+1/2} the arithmetic midpoint, g = -grad(phi) interpolated with CIC, an
 K, D the FP64 integrals of ``cosmology``.  A force evaluation is: CIC deposit of
 the counting density, FFT, Green's function (Newtonian or the linearised
 Poisson-gauge constraint of ``gravity``), spectral gradient, inverse FFT, CIC
-interpolation.  Fixed-point drift: Delta u = round-half-even(D p 2^32 / L),
+interpolation.  With gradient = FD1 the potential itself is transformed back and
+g = -grad of its CIC interpolant at the particle (the first-order finite difference
+across the particle's cell, ``cic.interpolate_gradient``).  Fixed-point drift: Delta u = round-half-even(D p 2^32 / L),
 u <- (u + Delta u) mod 2^32; FP64 drift: u <- frac(u + D p / L).
 """
 import numpy as np
@@ -22,10 +24,12 @@ from . import cic, gravity
 
 NEWTON = 0
 GR_POISSON = 1
+SPECTRAL = 0
+FD1 = 1
 
 
 class PMRun:
-    def __init__(self, cosmo, n_mesh, box, a_init, a_final, n_steps, x, p, mode=NEWTON):
+    def __init__(self, cosmo, n_mesh, box, a_init, a_final, n_steps, x, p, mode=NEWTON, gradient=SPECTRAL):
         self.cosmo = cosmo
         self.n = int(n_mesh)
         self.box = float(box)
@@ -35,6 +39,7 @@ class PMRun:
         self.p = np.array(p, dtype=np.float64, copy=True)
         self.fixed = self.x.dtype == np.uint32
         self.mode = mode
+        self.gradient = gradient
         self.i = 0
         self.synced = True
         self.phi_old_k = None
@@ -59,6 +64,8 @@ class PMRun:
     def accel(self, a):
         """g(x) = -grad(phi) at the particles, shape (3, Np)."""
         phi_k = self.potential_k(a)
+        if self.gradient == FD1:
+            return -cic.interpolate_gradient(gravity.potential_mesh(phi_k, self.n), self.x, self.box)
         g_mesh = gravity.gradient_force(phi_k, self.n, self.box)
         return np.stack([cic.interpolate(g_mesh[j], self.x) for j in range(3)])
 
