@@ -529,6 +529,37 @@ def estimators(pm, torch, args):
     del gr
     torch.cuda.synchronize()
     torch.cuda.empty_cache()
+    # the first-order gradient option (the paper's PM force): one inverse transform of the
+    # potential, the update differentiating its CIC interpolant from eight corners
+    fd = pm.PMRun(pm.make_config(np_side, n, box, A_INIT, A_FINAL, gsteps + gwarm, gradient=pm.PM_GRAD_FD1))
+    fd.ic(seed=1)
+    fd.step(gwarm)
+    e0.record(st)
+    fd.step(gsteps)
+    e1.record(st)
+    e1.synchronize()
+    ms_fd = e0.elapsed_time(e1) / gsteps
+    fd.ic(seed=1)
+    fd.step(gwarm)
+    pm.pm_profile(fd.ctx, True)
+    pm.pm_timings(fd.ctx)
+    fd.step(gsteps)
+    ph = pm.pm_timings(fd.ctx)
+    pm.pm_profile(fd.ctx, False)
+    fd_bytes = 60 * P + 24 * n**3
+    peak = peaks()[0]
+    out["fd1_step"] = {"ms_per_step": round(ms_fd, 4), "steps": gsteps,
+                       "particle_steps_per_s": round(P / (ms_fd * 1e-3), 1),
+                       "step_roofline": {"bytes_per_step": fd_bytes,
+                                         "frac": round(fd_bytes / (ms_fd * 1e-3) / 1e9 / peak, 4),
+                                         "bytes_model": "60 B/particle + 24 B/cell (one inverse transform, "
+                                                        "one mesh gathered)"},
+                       "phases_ms_per_launch": {k: round(v[0] / max(v[1], 1), 4) for k, v in ph.items() if v[1]},
+                       "what": f"{np_side}^3 particles, {n}^3 mesh, PM_GRAD_FD1 (first-order gradient of the CIC "
+                               "interpolant of the potential), otherwise as the headline"}
+    del fd
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
     out["gpu_power_field_cells_per_s"] = round(n**3 / (out["power_field"]["ms"] * 1e-3), 1)
     out["gpu_combination_particles_per_s"] = round(P / (out["displacement_combination"]["ms"] * 1e-3), 1)
     return out

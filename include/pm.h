@@ -71,6 +71,12 @@ typedef enum {
 
 enum { PM_NEWTON = 0, PM_GR_POISSON = 1 };
 enum { PM_FP32_FIXED = 0, PM_FP64 = 1 };
+/* Force gradient: spectral (-i k phi, three inverse transforms), or the first-order
+ * finite difference of the paper's PM code (Sec. 4.1): the gradient of the CIC
+ * (trilinear) interpolant of the real-space potential inside the particle's cell, i.e.
+ * the difference across the cell over L/nmesh, weighted bilinearly on the other axes
+ * (one inverse transform; the update gathers the potential's eight corners). */
+enum { PM_GRAD_SPECTRAL = 0, PM_GRAD_FD1 = 1 };
 /* Initial-condition flags (pm_ic_zeldovich, pm_batch_ic). */
 enum { PM_IC_PAIRED = 1, PM_IC_FIXED = 2, PM_IC_2LPT = 4 };
 
@@ -90,6 +96,8 @@ typedef struct {
     int mode;          /* PM_NEWTON or PM_GR_POISSON */
     int precision;     /* PM_FP32_FIXED or PM_FP64 */
     int n_lo;          /* GR only: modes with |n|^2 <= n_lo^2 are solved and stored in FP64 */
+    int gradient;      /* PM_GRAD_SPECTRAL (0) or PM_GRAD_FD1; pm_batch_* refuse FD1
+                          (PM_ERR_INVALID_ARG), pm_loss_grad too (PM_ERR_UNSUPPORTED) */
 } pm_config;
 
 typedef struct pm_ctx pm_ctx;   /* opaque host object owned by the library */

@@ -75,6 +75,7 @@ pm_status validate(const pm_config* c) {
     if (c->mode != PM_NEWTON && c->mode != PM_GR_POISSON) return fail(PM_ERR_INVALID_ARG, "bad mode");
     if (c->precision != PM_FP32_FIXED && c->precision != PM_FP64) return fail(PM_ERR_INVALID_ARG, "bad precision");
     if (c->n_lo < 0 || 2 * c->n_lo >= c->nmesh) return fail(PM_ERR_INVALID_ARG, "n_lo must be in [0, nmesh/2)");
+    if (c->gradient != PM_GRAD_SPECTRAL && c->gradient != PM_GRAD_FD1) return fail(PM_ERR_INVALID_ARG, "bad gradient");
     return PM_OK;
 }
 
@@ -287,11 +288,24 @@ pm_status compute_forces_t(pm_ctx* c, double a) {
         op.phi_old = c->at(c->L.phi_old);
         op.island = c->L.has_island ? (double2*)c->at(c->L.island) : nullptr;
     }
-    {
-        Phase ph(c, PM_PHASE_FFT_X_GREEN);
-        PM_CK(x_cols<T>(s0, s1, n / 2 + 1, n, op, c->st));
-    }
-    {
+    if (c->cfg.gradient == PM_GRAD_FD1) {
+        // the potential alone goes back to real space (force(0)); the update differentiates
+        // its CIC interpolant (the Poisson-gauge pass still writes its x gradient, unused)
+        if (op.kind == OP_NEWTON) op.kind = OP_POTENTIAL;
+        {
+            Phase ph(c, PM_PHASE_FFT_X_GREEN);
+            PM_CK(x_cols<T>(s0, op.kind == OP_POTENTIAL ? nullptr : s1, n / 2 + 1, n, op, c->st));
+        }
+        Phase ph(c, PM_PHASE_FFT_YZ_INV);
+        PM_CK((y_rows<T, true>(s0, (int64_t)(n / 2 + 1) * n, n, c->st)));
+        const cplx<T>* in[1] = {s0};
+        T* out[1] = {(T*)c->force(0)};
+        PM_CK(z_c2r<T>(in, out, 1, n, 1, 0u, 0.0, c->st));
+    } else {
+        {
+            Phase ph(c, PM_PHASE_FFT_X_GREEN);
+            PM_CK(x_cols<T>(s0, s1, n / 2 + 1, n, op, c->st));
+        }
         Phase ph(c, PM_PHASE_FFT_YZ_INV);
         T* out[3] = {(T*)c->force(0), (T*)c->force(1), (T*)c->force(2)};
         PM_CK(inverse_yz_grad<T>(s0, s1, s2, out, n, 1, c->kf, c->st));
@@ -310,16 +324,18 @@ pm_status compute_forces(pm_ctx* c, double a) {
 pm_status kick_drift(pm_ctx* c, double kick, double drift) {
     Phase ph(c, PM_PHASE_KICK_DRIFT);
     void* g[3] = {c->force(0), c->force(1), c->force(2)};
+    // first-order gradient: force(0) holds the potential, differentiated across the cell of spacing L/n
+    const double fd_inv_d = c->cfg.gradient == PM_GRAD_FD1 ? c->n / c->cfg.box : 0.0;
     if (fused_update(c)) {
         PM_CK(interp_kick_drift_deposit(c->xpos(), c->at(c->L.p), c->np, c->cfg.precision, c->n, g, kick, drift,
                                         c->cfg.box, std::pow((double)c->n / c->np, 3), c->at(c->L.rho), c->st, 1,
-                                        nullptr, c->x_out));
+                                        nullptr, c->x_out, fd_inv_d));
         c->rho_valid = true;
         return PM_OK;
     }
     if (c->x_at || c->x_out) return fail(PM_ERR_UNSUPPORTED, "out-of-place positions need the fused update");
     PM_CK(interp_kick_drift(c->at(c->L.x), c->at(c->L.p), c->np3, c->cfg.precision, c->n, g, kick, drift,
-                            c->cfg.box, c->st));
+                            c->cfg.box, c->st, fd_inv_d));
     return PM_OK;
 }
 
@@ -1013,8 +1029,8 @@ pm_status pm_loss_grad(pm_ctx* c, const void* white_noise, const void* target, i
                        size_t scratch_bytes, double* loss_out, void* grad_out) {
     if (!c || !white_noise || !target || !loss_out || !grad_out || checkpoint_every < 1)
         return fail(PM_ERR_INVALID_ARG, "null argument or bad checkpoint interval");
-    if (c->cfg.precision != PM_FP32_FIXED || c->cfg.mode != PM_NEWTON)
-        return fail(PM_ERR_UNSUPPORTED, "the gradient is implemented for the FP32 Newtonian step");
+    if (c->cfg.precision != PM_FP32_FIXED || c->cfg.mode != PM_NEWTON || c->cfg.gradient != PM_GRAD_SPECTRAL)
+        return fail(PM_ERR_UNSUPPORTED, "the gradient is implemented for the FP32 Newtonian step with the spectral force");
     const int S = c->cfg.n_steps, C = std::min(checkpoint_every, S);
     const AdjLayout A = adj_plan(c, C);
     if (!scratch || scratch_bytes < A.total || (uintptr_t)scratch % 256)
@@ -1238,8 +1254,8 @@ void batch_plan(pm_batch& b) {
 pm_status batch_validate(const pm_config* cfg, int B, const double* boxes) {
     PM_TRY(validate(cfg));
     if (B < 1 || B > 4096) return fail(PM_ERR_INVALID_ARG, "batch size must be in 1..4096");
-    if (cfg->precision != PM_FP32_FIXED || cfg->mode != PM_NEWTON)
-        return fail(PM_ERR_INVALID_ARG, "batches run the FP32 Newtonian step");
+    if (cfg->precision != PM_FP32_FIXED || cfg->mode != PM_NEWTON || cfg->gradient != PM_GRAD_SPECTRAL)
+        return fail(PM_ERR_INVALID_ARG, "batches run the FP32 Newtonian step with the spectral force");
     if (!ikd_deposit_supported(cfg->np, cfg->precision, cfg->nmesh))
         return fail(PM_ERR_INVALID_ARG, "batches need nmesh >= 64 and nmesh / np in {1, 2, 4}");
     if (boxes)

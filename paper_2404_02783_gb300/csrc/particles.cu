@@ -258,15 +258,16 @@ cudaError_t interp(const void* field, int n, const void* x, int64_t count, int p
 }
 
 // ---------------------------------------------------------------- interp + kick + drift
+template <bool FD>
 __global__ void __launch_bounds__(256) k_ikd_ticks(uint32_t* __restrict__ x, float* __restrict__ p, int64_t count,
                                                    int logn, float inv_cell_ticks, const float* __restrict__ gx,
                                                    const float* __restrict__ gy, const float* __restrict__ gz,
-                                                   float kick, float drift_ticks) {
+                                                   float kick, float drift_ticks, float inv_d) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count;
          i += (int64_t)gridDim.x * blockDim.x) {
         uint32_t u0 = x[i], u1 = x[count + i], u2 = x[2 * count + i];
         float p0 = p[i], p1 = p[count + i], p2 = p[2 * count + i];
-        ikd_particle(u0, u1, u2, p0, p1, p2, logn, inv_cell_ticks, gx, gy, gz, kick, drift_ticks);
+        ikd_particle<FD>(u0, u1, u2, p0, p1, p2, logn, inv_cell_ticks, gx, gy, gz, kick, drift_ticks, inv_d);
         p[i] = p0;
         p[count + i] = p1;
         p[2 * count + i] = p2;
@@ -279,10 +280,11 @@ __global__ void __launch_bounds__(256) k_ikd_ticks(uint32_t* __restrict__ x, flo
 // Same update, two neighbouring particles per thread through 8-byte loads and stores
 // (count even, arrays 8-byte aligned): neighbours share most CIC corners, so the
 // second particle's gathers mostly hit L1.
+template <bool FD>
 __global__ void __launch_bounds__(256) k_ikd_ticks2(uint32_t* __restrict__ x, float* __restrict__ p, int64_t count,
                                                     int logn, float inv_cell_ticks, const float* __restrict__ gx,
                                                     const float* __restrict__ gy, const float* __restrict__ gz,
-                                                    float kick, float drift_ticks) {
+                                                    float kick, float drift_ticks, float inv_d) {
     const int64_t pairs = count >> 1;
     uint2* x0 = reinterpret_cast<uint2*>(x);
     uint2* x1 = reinterpret_cast<uint2*>(x + count);
@@ -294,8 +296,8 @@ __global__ void __launch_bounds__(256) k_ikd_ticks2(uint32_t* __restrict__ x, fl
          i += (int64_t)gridDim.x * blockDim.x) {
         uint2 a = x0[i], b = x1[i], c = x2[i];
         float2 pa = p0[i], pb = p1[i], pc = p2[i];
-        ikd_particle(a.x, b.x, c.x, pa.x, pb.x, pc.x, logn, inv_cell_ticks, gx, gy, gz, kick, drift_ticks);
-        ikd_particle(a.y, b.y, c.y, pa.y, pb.y, pc.y, logn, inv_cell_ticks, gx, gy, gz, kick, drift_ticks);
+        ikd_particle<FD>(a.x, b.x, c.x, pa.x, pb.x, pc.x, logn, inv_cell_ticks, gx, gy, gz, kick, drift_ticks, inv_d);
+        ikd_particle<FD>(a.y, b.y, c.y, pa.y, pb.y, pc.y, logn, inv_cell_ticks, gx, gy, gz, kick, drift_ticks, inv_d);
         p0[i] = pa;
         p1[i] = pb;
         p2[i] = pc;
@@ -305,18 +307,32 @@ __global__ void __launch_bounds__(256) k_ikd_ticks2(uint32_t* __restrict__ x, fl
     }
 }
 
+template <bool FD>
 __global__ void __launch_bounds__(256) k_ikd_frac(double* __restrict__ x, double* __restrict__ p, int64_t count,
                                                   int n, const double* __restrict__ gx, const double* __restrict__ gy,
-                                                  const double* __restrict__ gz, double kick, double drift_box) {
+                                                  const double* __restrict__ gz, double kick, double drift_box,
+                                                  double inv_d) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count;
          i += (int64_t)gridDim.x * blockDim.x) {
         double xs[3] = {x[i], x[count + i], x[2 * count + i]};
         const CicD cx = cic_frac(xs[0], n), cy = cic_frac(xs[1], n), cz = cic_frac(xs[2], n);
         const double wx[2] = {1.0 - cx.w1, cx.w1}, wy[2] = {1.0 - cy.w1, cy.w1}, wz[2] = {1.0 - cz.w1, cz.w1};
         const int ix[2] = {cx.i0, cx.i1}, iy[2] = {cy.i0, cy.i1}, iz[2] = {cz.i0, cz.i1};
-        const double f[3] = {gather8<double, double>(gx, (size_t)n, ix, iy, iz, wx, wy, wz),
-                             gather8<double, double>(gy, (size_t)n, ix, iy, iz, wx, wy, wz),
-                             gather8<double, double>(gz, (size_t)n, ix, iy, iz, wx, wy, wz)};
+        double f[3];
+        if constexpr (FD) {
+            double P[2][4];
+#pragma unroll
+            for (int a = 0; a < 2; ++a)
+#pragma unroll
+                for (int b = 0; b < 2; ++b)
+#pragma unroll
+                    for (int c = 0; c < 2; ++c) P[a][2 * b + c] = gx[((size_t)ix[a] * n + iy[b]) * n + iz[c]];
+            fd1_force<double>(P[0], P[1], wx[0], wx[1], wy, wz, inv_d, f[0], f[1], f[2]);
+        } else {
+            f[0] = gather8<double, double>(gx, (size_t)n, ix, iy, iz, wx, wy, wz);
+            f[1] = gather8<double, double>(gy, (size_t)n, ix, iy, iz, wx, wy, wz);
+            f[2] = gather8<double, double>(gz, (size_t)n, ix, iy, iz, wx, wy, wz);
+        }
 #pragma unroll
         for (int j = 0; j < 3; ++j) {
             const double pj = p[j * count + i] + kick * f[j];
@@ -328,27 +344,36 @@ __global__ void __launch_bounds__(256) k_ikd_frac(double* __restrict__ x, double
     }
 }
 
-cudaError_t interp_kick_drift(void* x, void* p, int64_t count, int precision, int n, void* const* g,
-                              double kick, double drift, double box, cudaStream_t st) {
-    if (count == 0) return cudaSuccess;
+template <bool FD>
+static cudaError_t interp_kick_drift_t(void* x, void* p, int64_t count, int precision, int n, void* const* g,
+                                       double kick, double drift, double box, double inv_d, cudaStream_t st) {
     const int logn = ilog2(n);
     if (precision == PM_FP32_FIXED) {
         const float inv = (float)ldexp(1.0, -(32 - logn));
         const float dt = (float)(drift * (4294967296.0 / box));
         const bool pairs = (count % 2 == 0) && ((uintptr_t)x % 8 == 0) && ((uintptr_t)p % 8 == 0);
         if (pairs)
-            k_ikd_ticks2<<<grid_for(count / 2, 256), 256, 0, st>>>((uint32_t*)x, (float*)p, count, logn, inv,
-                                                                   (const float*)g[0], (const float*)g[1],
-                                                                   (const float*)g[2], (float)kick, dt);
+            k_ikd_ticks2<FD><<<grid_for(count / 2, 256), 256, 0, st>>>((uint32_t*)x, (float*)p, count, logn, inv,
+                                                                       (const float*)g[0], (const float*)g[1],
+                                                                       (const float*)g[2], (float)kick, dt,
+                                                                       (float)inv_d);
         else
-            k_ikd_ticks<<<grid_for(count, 256), 256, 0, st>>>((uint32_t*)x, (float*)p, count, logn, inv,
-                                                              (const float*)g[0], (const float*)g[1],
-                                                              (const float*)g[2], (float)kick, dt);
+            k_ikd_ticks<FD><<<grid_for(count, 256), 256, 0, st>>>((uint32_t*)x, (float*)p, count, logn, inv,
+                                                                  (const float*)g[0], (const float*)g[1],
+                                                                  (const float*)g[2], (float)kick, dt, (float)inv_d);
     } else {
-        k_ikd_frac<<<grid_for(count, 256), 256, 0, st>>>((double*)x, (double*)p, count, n, (const double*)g[0],
-                                                         (const double*)g[1], (const double*)g[2], kick, drift / box);
+        k_ikd_frac<FD><<<grid_for(count, 256), 256, 0, st>>>((double*)x, (double*)p, count, n, (const double*)g[0],
+                                                             (const double*)g[1], (const double*)g[2], kick,
+                                                             drift / box, inv_d);
     }
     return cudaGetLastError();
+}
+
+cudaError_t interp_kick_drift(void* x, void* p, int64_t count, int precision, int n, void* const* g,
+                              double kick, double drift, double box, cudaStream_t st, double fd_inv_d) {
+    if (count == 0) return cudaSuccess;
+    if (fd_inv_d > 0.0) return interp_kick_drift_t<true>(x, p, count, precision, n, g, kick, drift, box, fd_inv_d, st);
+    return interp_kick_drift_t<false>(x, p, count, precision, n, g, kick, drift, box, 0.0, st);
 }
 
 // ---------------------------------------------------------------- Zel'dovich placement

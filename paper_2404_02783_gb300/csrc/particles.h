@@ -15,8 +15,9 @@ cudaError_t deposit_lattice(const void* x, int np, int precision, int n, double 
 cudaError_t interp(const void* field, int n, const void* x, int64_t count, int precision, void* out,
                    cudaStream_t st);
 // g: three force meshes; kick = K(a, b); drift = D(a, b) in Mpc/h per unit p
+// fd_inv_d > 0: first-order gradient (g[0] is the potential, g[1], g[2] unused), inv_d = n / L.
 cudaError_t interp_kick_drift(void* x, void* p, int64_t count, int precision, int n, void* const* g, double kick,
-                              double drift, double box, cudaStream_t st);
+                              double drift, double box, cudaStream_t st, double fd_inv_d = 0.0);
 // Kick + drift of the np^3 lattice-ordered particles fused with the deposit of the
 // drifted positions into rho (which must be zero on entry); FP32 ticks, n / np in {1,2,4}.
 bool ikd_deposit_supported(int np, int precision, int n);
@@ -25,7 +26,8 @@ bool ikd_deposit_supported(int np, int precision, int n);
 // (null: back into x); p is always updated in place.
 cudaError_t interp_kick_drift_deposit(void* x, void* p, int np, int precision, int n, void* const* g, double kick,
                                       double drift, double box, double mass, void* rho, cudaStream_t st,
-                                      int nfields = 1, const double* scale_arr = nullptr, void* x_out = nullptr);
+                                      int nfields = 1, const double* scale_arr = nullptr, void* x_out = nullptr,
+                                      double fd_inv_d = 0.0);
 cudaError_t ic_place(void* x, void* p, void* const* psi, int np, int precision, double D, double pfac, double box,
                      cudaStream_t st);
 // Second-order LPT source, accumulated over three stages, one per displacement component c:

@@ -15,13 +15,13 @@ namespace pm {
 // k_deposit_tiled would have done from the drifted positions.
 // blockIdx.y selects the field of a batch of independent runs stored back to back
 // (particles [field][3][np^3], meshes [field][n^3]); scale = 2^32 / L of that field.
-template <int R>
+template <int R, bool FD>
 __global__ void __launch_bounds__(512, 2) k_ikd_deposit(const uint32_t* __restrict__ x, uint32_t* __restrict__ xo, float* __restrict__ p, int lognp,
                                                      int logn, float inv_cell_ticks, const float* __restrict__ gx,
                                                      const float* __restrict__ gy, const float* __restrict__ gz,
                                                      float kick, double drift, double scale0,
                                                      const double* __restrict__ scale_arr, float mass,
-                                                     float* __restrict__ rho) {
+                                                     float* __restrict__ rho, float inv_d) {
     typedef DepTile<R> D;
     extern __shared__ __align__(16) uint32_t tile_words[];  // D::WORDS
     uint32_t* lo = tile_words;
@@ -35,8 +35,10 @@ __global__ void __launch_bounds__(512, 2) k_ikd_deposit(const uint32_t* __restri
         xo += fb * 3 * count;
         p += fb * 3 * count;
         gx += fb * n3;
-        gy += fb * n3;
-        gz += fb * n3;
+        if (!FD) {
+            gy += fb * n3;
+            gz += fb * n3;
+        }
         rho += fb * n3;
     }
     const float drift_ticks = (float)(drift * (scale_arr ? scale_arr[blockIdx.y] : scale0));
@@ -67,7 +69,7 @@ __global__ void __launch_bounds__(512, 2) k_ikd_deposit(const uint32_t* __restri
             np1 = p[count + idn];
             np2 = p[2 * count + idn];
         }
-        ikd_particle(u0, u1, u2, p0, p1, p2, logn, inv_cell_ticks, gx, gy, gz, kick, drift_ticks);
+        ikd_particle<FD>(u0, u1, u2, p0, p1, p2, logn, inv_cell_ticks, gx, gy, gz, kick, drift_ticks, inv_d);
         p[id] = p0;
         p[count + id] = p1;
         p[2 * count + id] = p2;
@@ -89,13 +91,14 @@ __global__ void __launch_bounds__(512, 2) k_ikd_deposit(const uint32_t* __restri
 // carries the upper-plane weights in registers, adds them to the next particle's
 // lower-plane weights and issues 4 tile atomics a particle instead of 8.  Any other
 // particle takes the full path, so the result is the same CIC gather and deposit.
+template <bool FD>
 __global__ void __launch_bounds__(512, 2) k_ikd_deposit_sweep(const uint32_t* __restrict__ x, uint32_t* __restrict__ xo, float* __restrict__ p,
                                                               int lognp, int logn, float inv_cell_ticks,
                                                               const float* __restrict__ gx,
                                                               const float* __restrict__ gy,
                                                               const float* __restrict__ gz, float kick, double drift,
                                                               double scale0, const double* __restrict__ scale_arr,
-                                                              float mass, float* __restrict__ rho) {
+                                                              float mass, float* __restrict__ rho, float inv_d) {
     typedef DepTile<1> D;
     static_assert(D::TY * D::TZ == 512, "one thread per (ly, lz); lx runs over the loop");
     extern __shared__ __align__(16) uint32_t tile_words[];  // D::WORDS
@@ -110,8 +113,10 @@ __global__ void __launch_bounds__(512, 2) k_ikd_deposit_sweep(const uint32_t* __
         xo += fb * 3 * count;
         p += fb * 3 * count;
         gx += fb * n3;
-        gy += fb * n3;
-        gz += fb * n3;
+        if (!FD) {
+            gy += fb * n3;
+            gz += fb * n3;
+        }
         rho += fb * n3;
     }
     const float drift_ticks = (float)(drift * (scale_arr ? scale_arr[blockIdx.y] : scale0));
@@ -124,7 +129,7 @@ __global__ void __launch_bounds__(512, 2) k_ikd_deposit_sweep(const uint32_t* __
     const int64_t id0 = ((((int64_t)(bx * D::TX) << lognp) + by * D::TY + ly) << lognp) + bz * D::TZ + lz;
     const int64_t xstride = (int64_t)1 << (2 * lognp);
     uint32_t next_cell = 0xffffffffu;  // packed (ix, iy, iz) whose lower plane the registers hold
-    float U[4][3];                      // force at the carried plane, corner (b, c) = 2 b + c
+    float U[4][FD ? 1 : 3];             // force (FD: potential) at the carried plane, corner (b, c) = 2 b + c
     SweepCarry sc;                      // deposit weights carried to the next particle's plane
     // the next particle's position and momentum are loaded one iteration ahead, so their
     // memory latency overlaps the current particle's gather, update and deposit
@@ -151,21 +156,22 @@ __global__ void __launch_bounds__(512, 2) k_ikd_deposit_sweep(const uint32_t* __
             const CicF cz = cic_ticks(u2, logn, inv_cell_ticks);
             const uint32_t cell = ((((uint32_t)cx.i0 << logn) | (uint32_t)cy.i0) << logn) | (uint32_t)cz.i0;
             const uint32_t iy[2] = {(uint32_t)cy.i0, (uint32_t)cy.i1}, iz[2] = {(uint32_t)cz.i0, (uint32_t)cz.i1};
-            float L[4][3];
+            constexpr int NC = FD ? 1 : 3;
+            const float* g3[3] = {gx, gy, gz};
+            float L[4][NC];
             if (cell == next_cell) {
 #pragma unroll
                 for (int q = 0; q < 4; ++q)
 #pragma unroll
-                    for (int j = 0; j < 3; ++j) L[q][j] = U[q][j];
+                    for (int j = 0; j < NC; ++j) L[q][j] = U[q][j];
             } else {
 #pragma unroll
                 for (int b = 0; b < 2; ++b)
 #pragma unroll
                     for (int c = 0; c < 2; ++c) {
                         const uint32_t o = ((((uint32_t)cx.i0 << logn) + iy[b]) << logn) + iz[c];
-                        L[2 * b + c][0] = __ldg(gx + o);
-                        L[2 * b + c][1] = __ldg(gy + o);
-                        L[2 * b + c][2] = __ldg(gz + o);
+#pragma unroll
+                        for (int j = 0; j < NC; ++j) L[2 * b + c][j] = __ldg(g3[j] + o);
                     }
             }
 #pragma unroll
@@ -173,24 +179,29 @@ __global__ void __launch_bounds__(512, 2) k_ikd_deposit_sweep(const uint32_t* __
 #pragma unroll
                 for (int c = 0; c < 2; ++c) {
                     const uint32_t o = ((((uint32_t)cx.i1 << logn) + iy[b]) << logn) + iz[c];
-                    U[2 * b + c][0] = __ldg(gx + o);
-                    U[2 * b + c][1] = __ldg(gy + o);
-                    U[2 * b + c][2] = __ldg(gz + o);
+#pragma unroll
+                    for (int j = 0; j < NC; ++j) U[2 * b + c][j] = __ldg(g3[j] + o);
                 }
             next_cell = ((((uint32_t)cx.i1 << logn) | (uint32_t)cy.i0) << logn) | (uint32_t)cz.i0;
             const float wy[2] = {1.0f - cy.w1, cy.w1}, wz[2] = {1.0f - cz.w1, cz.w1};
             const float wx0 = 1.0f - cx.w1, wx1 = cx.w1;
             float f0 = 0.f, f1 = 0.f, f2 = 0.f;
+            if constexpr (FD) {
+                const float Lp[4] = {L[0][0], L[1][0], L[2][0], L[3][0]};
+                const float Up[4] = {U[0][0], U[1][0], U[2][0], U[3][0]};
+                fd1_force<float>(Lp, Up, wx0, wx1, wy, wz, inv_d, f0, f1, f2);
+            } else {
 #pragma unroll
-            for (int b = 0; b < 2; ++b)
+                for (int b = 0; b < 2; ++b)
 #pragma unroll
-                for (int c = 0; c < 2; ++c) {
-                    const float w = wy[b] * wz[c];
-                    const int q = 2 * b + c;
-                    f0 = fmaf(w, fmaf(wx0, L[q][0], wx1 * U[q][0]), f0);
-                    f1 = fmaf(w, fmaf(wx0, L[q][1], wx1 * U[q][1]), f1);
-                    f2 = fmaf(w, fmaf(wx0, L[q][2], wx1 * U[q][2]), f2);
-                }
+                    for (int c = 0; c < 2; ++c) {
+                        const float w = wy[b] * wz[c];
+                        const int q = 2 * b + c;
+                        f0 = fmaf(w, fmaf(wx0, L[q][0], wx1 * U[q][0]), f0);
+                        f1 = fmaf(w, fmaf(wx0, L[q][1], wx1 * U[q][1]), f1);
+                        f2 = fmaf(w, fmaf(wx0, L[q][2], wx1 * U[q][2]), f2);
+                    }
+            }
             p0 = fmaf(kick, f0, p0);
             p1 = fmaf(kick, f1, p1);
             p2 = fmaf(kick, f2, p2);
@@ -212,29 +223,29 @@ __global__ void __launch_bounds__(512, 2) k_ikd_deposit_sweep(const uint32_t* __
     tile_flush<D>(lo, carry, rho, ox, oy, oz, logn);
 }
 
-template <int R>
+template <int R, bool FD>
 static cudaError_t ikd_deposit_r(void* x, void* p, int np, int n, void* const* g, double kick, double drift,
                                  double box, double mass, void* rho, cudaStream_t st, int nfields,
-                                 const double* scale_arr, void* x_out) {
+                                 const double* scale_arr, void* x_out, double inv_d) {
     typedef DepTile<R> D;
     const int lognp = ilog2(np), logn = ilog2(n);
     const unsigned blocks = (unsigned)((np / D::TX) * (np / D::TY) * (np / D::TZ));
     const float inv = (float)ldexp(1.0, -(32 - logn));
     const size_t smem = sizeof(uint32_t) * D::WORDS;
     if constexpr (R == 1) {
-        cudaError_t e = set_smem_once((const void*)k_ikd_deposit_sweep, smem);
+        cudaError_t e = set_smem_once((const void*)k_ikd_deposit_sweep<FD>, smem);
         if (e != cudaSuccess) return e;
-        k_ikd_deposit_sweep<<<dim3(blocks, nfields), 512, smem, st>>>(
+        k_ikd_deposit_sweep<FD><<<dim3(blocks, nfields), 512, smem, st>>>(
             (const uint32_t*)x, (uint32_t*)(x_out ? x_out : x), (float*)p, lognp, logn, inv, (const float*)g[0],
             (const float*)g[1], (const float*)g[2],
-            (float)kick, drift, 4294967296.0 / box, scale_arr, (float)mass, (float*)rho);
+            (float)kick, drift, 4294967296.0 / box, scale_arr, (float)mass, (float*)rho, (float)inv_d);
     } else {
-        cudaError_t e = set_smem_once((const void*)k_ikd_deposit<R>, smem);
+        cudaError_t e = set_smem_once((const void*)k_ikd_deposit<R, FD>, smem);
         if (e != cudaSuccess) return e;
-        k_ikd_deposit<R><<<dim3(blocks, nfields), 512, smem, st>>>(
+        k_ikd_deposit<R, FD><<<dim3(blocks, nfields), 512, smem, st>>>(
             (const uint32_t*)x, (uint32_t*)(x_out ? x_out : x), (float*)p, lognp, logn, inv, (const float*)g[0],
             (const float*)g[1], (const float*)g[2],
-            (float)kick, drift, 4294967296.0 / box, scale_arr, (float)mass, (float*)rho);
+            (float)kick, drift, 4294967296.0 / box, scale_arr, (float)mass, (float*)rho, (float)inv_d);
     }
     return cudaGetLastError();
 }
@@ -244,15 +255,27 @@ bool ikd_deposit_supported(int np, int precision, int n) {
     return precision == PM_FP32_FIXED && n >= 64 && (R == 1 || R == 2 || R == 4) && np >= 32 / R;
 }
 
+template <bool FD>
+static cudaError_t ikd_deposit_any(void* x, void* p, int np, int n, void* const* g, double kick, double drift,
+                                   double box, double mass, void* rho, cudaStream_t st, int nfields,
+                                   const double* scale_arr, void* x_out, double inv_d) {
+    const int R = n / np;
+    if (R == 1)
+        return ikd_deposit_r<1, FD>(x, p, np, n, g, kick, drift, box, mass, rho, st, nfields, scale_arr, x_out, inv_d);
+    if (R == 2)
+        return ikd_deposit_r<2, FD>(x, p, np, n, g, kick, drift, box, mass, rho, st, nfields, scale_arr, x_out, inv_d);
+    return ikd_deposit_r<4, FD>(x, p, np, n, g, kick, drift, box, mass, rho, st, nfields, scale_arr, x_out, inv_d);
+}
+
 cudaError_t interp_kick_drift_deposit(void* x, void* p, int np, int precision, int n, void* const* g, double kick,
                                       double drift, double box, double mass, void* rho, cudaStream_t st, int nfields,
-                                      const double* scale_arr, void* x_out) {
+                                      const double* scale_arr, void* x_out, double fd_inv_d) {
     if (!ikd_deposit_supported(np, precision, n) || nfields < 1 || (uintptr_t)rho % 16 != 0)
         return cudaErrorInvalidValue;
-    const int R = n / np;
-    if (R == 1) return ikd_deposit_r<1>(x, p, np, n, g, kick, drift, box, mass, rho, st, nfields, scale_arr, x_out);
-    if (R == 2) return ikd_deposit_r<2>(x, p, np, n, g, kick, drift, box, mass, rho, st, nfields, scale_arr, x_out);
-    return ikd_deposit_r<4>(x, p, np, n, g, kick, drift, box, mass, rho, st, nfields, scale_arr, x_out);
+    if (fd_inv_d > 0.0)
+        return ikd_deposit_any<true>(x, p, np, n, g, kick, drift, box, mass, rho, st, nfields, scale_arr, x_out,
+                                     fd_inv_d);
+    return ikd_deposit_any<false>(x, p, np, n, g, kick, drift, box, mass, rho, st, nfields, scale_arr, x_out, 0.0);
 }
 
 }  // namespace pm

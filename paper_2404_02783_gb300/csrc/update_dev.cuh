@@ -208,30 +208,67 @@ __device__ __forceinline__ void sweep_finish(uint32_t* lo, uint32_t* carry, cons
 }
 
 // ---------------------------------------------------------------- interp + kick + drift
+// First-order gradient (PM_GRAD_FD1): the force -grad of the CIC interpolant of the
+// potential inside the particle's cell, from its eight corners: L[q] on the lower x plane,
+// U[q] on the upper one, corner (b, c) = 2 b + c for (y, z); inv_d = nmesh / L.
+//   g_x = inv_d sum_bc wy_b wz_c (L - U)
+//   g_y = inv_d sum_c wz_c [wx0 (L_0c - L_1c) + wx1 (U_0c - U_1c)]
+//   g_z = inv_d sum_b wy_b [wx0 (L_b0 - L_b1) + wx1 (U_b0 - U_b1)]
+template <typename T>
+__device__ __forceinline__ void fd1_force(const T* L, const T* U, T wx0, T wx1, const T* wy, const T* wz, T inv_d,
+                                          T& f0, T& f1, T& f2) {
+    T gx = T(0), gy = T(0), gz = T(0);
+#pragma unroll
+    for (int b = 0; b < 2; ++b)
+#pragma unroll
+        for (int c = 0; c < 2; ++c) gx += wy[b] * wz[c] * (L[2 * b + c] - U[2 * b + c]);
+#pragma unroll
+    for (int c = 0; c < 2; ++c) gy += wz[c] * (wx0 * (L[c] - L[2 + c]) + wx1 * (U[c] - U[2 + c]));
+#pragma unroll
+    for (int b = 0; b < 2; ++b) gz += wy[b] * (wx0 * (L[2 * b] - L[2 * b + 1]) + wx1 * (U[2 * b] - U[2 * b + 1]));
+    f0 = inv_d * gx;
+    f1 = inv_d * gy;
+    f2 = inv_d * gz;
+}
+
 // p += kick * g(x);  x += drift * p   (g = -grad phi gathered with the deposit's weights).
 // The eight corner offsets are formed once in 32 bits (n^3 <= 2^30) and serve the
-// three force meshes.
+// three force meshes.  FD: gx is the potential and g its first-order gradient (fd1_force).
+template <bool FD>
 __device__ __forceinline__ void ikd_particle(uint32_t& u0, uint32_t& u1, uint32_t& u2, float& p0, float& p1,
                                              float& p2, int logn, float inv_cell_ticks, const float* __restrict__ gx,
                                              const float* __restrict__ gy, const float* __restrict__ gz, float kick,
-                                             float drift_ticks) {
+                                             float drift_ticks, float inv_d) {
     const CicF cx = cic_ticks(u0, logn, inv_cell_ticks);
     const CicF cy = cic_ticks(u1, logn, inv_cell_ticks);
     const CicF cz = cic_ticks(u2, logn, inv_cell_ticks);
     const float wx[2] = {1.0f - cx.w1, cx.w1}, wy[2] = {1.0f - cy.w1, cy.w1}, wz[2] = {1.0f - cz.w1, cz.w1};
     const uint32_t ix[2] = {(uint32_t)cx.i0, (uint32_t)cx.i1}, iy[2] = {(uint32_t)cy.i0, (uint32_t)cy.i1};
     float f0 = 0.f, f1 = 0.f, f2 = 0.f;
+    if constexpr (FD) {
+        float P[2][4];
 #pragma unroll
-    for (int a = 0; a < 2; ++a)
+        for (int a = 0; a < 2; ++a)
 #pragma unroll
-        for (int b = 0; b < 2; ++b) {
-            const uint32_t row = ((ix[a] << logn) + iy[b]) << logn;
-            const uint32_t o0 = row + (uint32_t)cz.i0, o1 = row + (uint32_t)cz.i1;
-            const float w0 = wx[a] * wy[b] * wz[0], w1 = wx[a] * wy[b] * wz[1];
-            f0 = fmaf(w0, __ldg(gx + o0), fmaf(w1, __ldg(gx + o1), f0));
-            f1 = fmaf(w0, __ldg(gy + o0), fmaf(w1, __ldg(gy + o1), f1));
-            f2 = fmaf(w0, __ldg(gz + o0), fmaf(w1, __ldg(gz + o1), f2));
-        }
+            for (int b = 0; b < 2; ++b) {
+                const uint32_t row = ((ix[a] << logn) + iy[b]) << logn;
+                P[a][2 * b] = __ldg(gx + row + (uint32_t)cz.i0);
+                P[a][2 * b + 1] = __ldg(gx + row + (uint32_t)cz.i1);
+            }
+        fd1_force<float>(P[0], P[1], wx[0], wx[1], wy, wz, inv_d, f0, f1, f2);
+    } else {
+#pragma unroll
+        for (int a = 0; a < 2; ++a)
+#pragma unroll
+            for (int b = 0; b < 2; ++b) {
+                const uint32_t row = ((ix[a] << logn) + iy[b]) << logn;
+                const uint32_t o0 = row + (uint32_t)cz.i0, o1 = row + (uint32_t)cz.i1;
+                const float w0 = wx[a] * wy[b] * wz[0], w1 = wx[a] * wy[b] * wz[1];
+                f0 = fmaf(w0, __ldg(gx + o0), fmaf(w1, __ldg(gx + o1), f0));
+                f1 = fmaf(w0, __ldg(gy + o0), fmaf(w1, __ldg(gy + o1), f1));
+                f2 = fmaf(w0, __ldg(gz + o0), fmaf(w1, __ldg(gz + o1), f2));
+            }
+    }
     p0 = fmaf(kick, f0, p0);
     p1 = fmaf(kick, f1, p1);
     p2 = fmaf(kick, f2, p2);

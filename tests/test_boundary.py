@@ -60,7 +60,8 @@ def test_workspace_size_and_validation(pm):
                 pm.make_config(32, 64, 1000.0, 1.0, 0.5, 10),       # a-grid
                 pm.make_config(32, 64, 1000.0, 0.02, 1.0, 0),       # steps
                 pm.make_config(32, 64, 1000.0, 0.02, 1.0, 10, mode=5),
-                pm.make_config(32, 64, 1000.0, 0.02, 1.0, 10, n_lo=40)):
+                pm.make_config(32, 64, 1000.0, 0.02, 1.0, 10, n_lo=40),
+                pm.make_config(32, 64, 1000.0, 0.02, 1.0, 10, gradient=2)):
         with pytest.raises(pm.PMError) as e:
             pm.pm_workspace_size(bad)
         assert e.value.status == 1

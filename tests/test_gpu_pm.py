@@ -183,3 +183,49 @@ def test_poisson_gauge_run_matches_oracle(prec):
         # FP32 stores rho ~ 1 + delta and resolves delta to ~6e-8; with delta ~ 1e-4 on these
         # Gpc-sized cells at z = 100 the FP32 forces, hence displacements, carry ~1e-3 errors
         assert rel_l2(d_g, d_o) < (3e-3 if prec == FP32 else 1e-11)
+
+
+@pytest.mark.parametrize("prec,np_side,nmesh", [(FP32, 32, 32), (FP32, 32, 64), (FP32, 64, 64), (FP32, 16, 64),
+                                                (FP64, 32, 32), (FP64, 16, 32)])
+@pytest.mark.parametrize("mode", [0, 1])
+def test_first_order_gradient_run_matches_oracle(prec, np_side, nmesh, mode):
+    # PM_GRAD_FD1: the force is the gradient of the CIC interpolant of the potential (one
+    # inverse transform; the update gathers the potential's eight corners).  Covers the
+    # unfused update (nmesh 32), the fused row sweep (64/64) and the fused tiles (32/64, 16/64).
+    pm = lib()
+    box, a_i, a_f, steps = 500.0 if mode == 0 else 20000.0, 0.1, 1.0, 10
+    c = Cosmology()
+    x0, p0 = ic.zeldovich(c, np_side, box, a_i, seed=31, fixed=(prec == FP32))
+    ref = opm.PMRun(c, nmesh, box, a_i, a_f, steps, x0, p0, mode=mode, gradient=opm.FD1)
+    ref.step(3)
+    cfg = pm.make_config(np_side, nmesh, box, a_i, a_f, steps, mode=mode, precision=prec, gradient=pm.PM_GRAD_FD1)
+    run = pm.PMRun(cfg)
+    run.ic(seed=31)
+    run.step(3)
+    xg, pg = _host_particles(run)
+    d_g = min_image(positions_box_units(xg) - positions_box_units(x0))
+    d_o = min_image(positions_box_units(ref.x) - positions_box_units(x0))
+    # FP32 on the 20 Gpc/h box: rho ~ 1 + delta with delta ~ 1e-4 per cell carries ~1e-3
+    # relative density errors (as in the Poisson-gauge run test)
+    tol = (1e-4 if mode == 0 else 3e-3) if prec == FP32 else 1e-10
+    assert rel_l2(d_g, d_o) < tol
+    assert rel_l2(pg, ref.p) < tol
+    # and it is not the spectral force
+    spec = _run(pm, np_side, nmesh, box, a_i, a_f, steps, prec, mode=mode)
+    spec.ic(seed=31)
+    spec.step(3)
+    _, ps = _host_particles(spec)
+    assert rel_l2(pg, ps) > 1e-3
+
+
+def test_first_order_gradient_is_refused_by_batches_and_the_loss_gradient():
+    pm = lib()
+    cfg = pm.make_config(32, 64, 500.0, 0.1, 1.0, 4, gradient=pm.PM_GRAD_FD1)
+    with pytest.raises(pm.PMError) as e:
+        pm.PMBatch(cfg, boxes=[500.0, 600.0])
+    assert e.value.status == 1
+    run = pm.PMRun(cfg)
+    w = to_dev(inputs.gaussian_field(3, 32).astype(np.float32))
+    with pytest.raises(pm.PMError) as e:
+        run.loss_grad(w, torch.zeros((64, 64, 64), dtype=torch.float32, device="cuda"))
+    assert e.value.status == 6
