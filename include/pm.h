@@ -219,6 +219,13 @@ pm_status pm_linear_bias(pm_ctx* ctx, const void* delta_h, const void* delta_m, 
                          double k_max, int terms, double* coef, double* k_out, double* ratio_out,
                          double* nmodes_out);
 
+/* Eq. bgr, the linear relativistic bias of the counting density in Poisson gauge,
+ * b1^GR = 3 (f(a) + (3/2) Omega_m(a)) (1 - b1), with the growth rate and Omega_m(a) of
+ * cfg's background (only its cosmological fields are read).  Sec. 5.2 compares it with
+ * the fitted b1^GR of the relativistic run minus that of the Newtonian run (the
+ * Newtonian systematic).  Host only.  omega_m outside (0, 1] or a <= 0: PM_ERR_INVALID_ARG. */
+pm_status pm_b1_gr_theory(const pm_config* cfg, double a, double b1, double* b1_gr);
+
 /* Device scratch bytes pm_bispectrum needs for grid m and nbins bins. */
 pm_status pm_bispectrum_scratch_size(const pm_ctx* ctx, int m, int nbins, size_t* bytes);
 

@@ -29,7 +29,7 @@ _STATUS = {0: "PM_OK", 1: "PM_ERR_INVALID_ARG", 2: "PM_ERR_CUDA", 3: "PM_ERR_WOR
 # every entry point declared in include/pm.h
 EXPORTS = ("pm_workspace_size", "pm_init", "pm_destroy", "pm_ic_zeldovich", "pm_step", "pm_particles",
            "pm_set_particles", "pm_state", "pm_profile", "pm_timings", "pm_density", "pm_potential", "pm_displacement_correction", "pm_power", "pm_halo_proxy", "pm_linear_bias",
-           "pm_bispectrum_scratch_size", "pm_bispectrum", "pm_triangle_index", "pm_cic_deposit", "pm_cic_interp",
+           "pm_bispectrum_scratch_size", "pm_bispectrum", "pm_triangle_index", "pm_b1_gr_theory", "pm_cic_deposit", "pm_cic_interp",
            "pm_adjoint_scratch_size", "pm_loss_grad", "pm_batch_workspace_size", "pm_batch_init", "pm_batch_destroy", "pm_batch_context", "pm_batch_ic",
            "pm_batch_step", "pm_batch_state", "pm_batch_power", "pm_batch_bias",
            "pm_cell_sort_scratch_size", "pm_cell_sort", "pm_cell_sort_static", "pm_fft_r2c", "pm_fft_c2r", "pm_version", "pm_last_error")
@@ -92,6 +92,7 @@ def lib():
         "pm_bispectrum_scratch_size": (vp, i, i, ctypes.POINTER(sz)),
         "pm_bispectrum": (vp, vp, i, pd, i, i, vp, sz, pd, pd),
         "pm_triangle_index": (i, i, i, i, ctypes.POINTER(i64)),
+        "pm_b1_gr_theory": (cfgp, d, d, pd),
         "pm_adjoint_scratch_size": (vp, i, ctypes.POINTER(sz)),
         "pm_loss_grad": (vp, vp, vp, i, vp, sz, pd, vp),
         "pm_batch_workspace_size": (cfgp, i, ctypes.POINTER(sz)),
@@ -273,6 +274,12 @@ def pm_bispectrum(ctx, edges, m, scratch, field=None, deconvolve=True):
 def pm_triangle_index(nbins, i, j, l):
     out = ctypes.c_int64()
     _check(lib().pm_triangle_index(int(nbins), int(i), int(j), int(l), ctypes.byref(out)))
+    return out.value
+
+
+def pm_b1_gr_theory(cfg, a, b1):
+    out = ctypes.c_double()
+    _check(lib().pm_b1_gr_theory(ctypes.byref(cfg), float(a), float(b1), ctypes.byref(out)))
     return out.value
 
 

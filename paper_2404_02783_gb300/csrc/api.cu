@@ -548,6 +548,20 @@ const char* pm_version(void) { return "pm-gb300 0.1 (sm_103a)"; }
 
 const char* pm_last_error(void) { return g_err.c_str(); }
 
+pm_status pm_b1_gr_theory(const pm_config* cfg, double a, double b1, double* b1_gr) {
+    if (!cfg || !b1_gr) return fail(PM_ERR_INVALID_ARG, "null argument");
+    if (!(cfg->omega_m > 0 && cfg->omega_m <= 1) || !(a > 0)) return fail(PM_ERR_INVALID_ARG, "bad omega_m or a");
+    pmhost::Cosmo cosmo;
+    cosmo.omega_m = cfg->omega_m;
+    cosmo.omega_b = cfg->omega_b;
+    cosmo.h = cfg->h;
+    cosmo.n_s = cfg->n_s;
+    cosmo.sigma8 = cfg->sigma8;
+    // Eq. bgr: b1^GR = 3 (f + (3/2) Omega_m(a)) (1 - b1)
+    *b1_gr = 3.0 * (pmhost::growth_f(cosmo, a) + 1.5 * pmhost::omega_m_a(cosmo, a)) * (1.0 - b1);
+    return PM_OK;
+}
+
 pm_status pm_workspace_size(const pm_config* cfg, size_t* bytes) {
     PM_TRY(validate(cfg));
     if (!bytes) return fail(PM_ERR_INVALID_ARG, "null bytes");

@@ -105,3 +105,19 @@ def test_triangle_index_follows_the_bispectrum_table_order(pm):
     tri = stats.triangles(6)
     assert [tri[k] for k in eq] == [(j, j, j) for j in range(6)]
     assert [tri[k] for k in sq] == [(2, j, j) for j in range(2, 6)]
+
+
+def test_b1_gr_theory_matches_the_oracle(pm):
+    # host-only Eq. bgr from the library's background against the oracle's growth rate and
+    # Omega_m(a), at the four redshifts of the paper's bias table
+    from oracle.cosmology import Cosmology
+    from oracle.stats import b1_gr_theory
+    cfg = pm.make_config(32, 64, 1000.0, 0.02, 1.0, 10)
+    c = Cosmology()
+    for z, b1 in ((1.0, 9.0), (0.5, 5.7), (0.1, 3.9), (0.0, 3.6)):
+        a = 1.0 / (1.0 + z)
+        want = b1_gr_theory(b1, c.growth_f(a), float(c.omega_m_a(a)))
+        assert pm.pm_b1_gr_theory(cfg, a, b1) == pytest.approx(want, rel=1e-9)
+    assert pm.pm_b1_gr_theory(cfg, 0.7, 1.0) == 0.0
+    with pytest.raises(pm.PMError):
+        pm.pm_b1_gr_theory(cfg, -1.0, 2.0)
