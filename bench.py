@@ -321,6 +321,7 @@ def batched(pm, torch, args):
     seeds = list(range(1, B + 1))
     cfg = pm.make_config(np_side, n, 1000.0, A_INIT, A_FINAL, grid_steps)
     b = pm.PMBatch(cfg, boxes=boxes)
+    chunk, tune_ms = b.autotune()  # realisations per launch, picked by timing each candidate
     b.ic(seeds)
     b.step(1, graph=False)  # initial deposits + attribute set-up, untimed
     b.step(k, graph=True)   # records the graph (untimed warm-up of the replay path)
@@ -353,7 +354,9 @@ def batched(pm, torch, args):
                         "{1000, 2000, 4000} Mpc/h, FP32, one CUDA graph launch for all steps",
             "value": units / t_batch, "unit": UNIT, "ms_per_step": 1e3 * t_batch / k,
             "sequential_value": units / t_seq, "sequential_ms_per_step": 1e3 * t_seq / k,
-            "speedup_vs_sequential": t_seq / t_batch, "steps": k}
+            "speedup_vs_sequential": t_seq / t_batch, "steps": k,
+            "autotune": {"chunk": chunk, "ms_per_step_at_tuning": round(tune_ms, 4),
+                         "candidates": "realisations per launch: B, B/2, ..., 1"}}
 
 
 def adjoint(pm, torch, args):

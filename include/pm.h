@@ -288,6 +288,17 @@ pm_status pm_batch_destroy(pm_batch* batch);
 /* Context view of realisation r (particles, density, estimators); valid while the batch
  * lives.  Must not be stepped or destroyed by the caller. */
 pm_status pm_batch_context(pm_batch* batch, int r, pm_ctx** view);
+/* Realisations per launch of the batched step: every pass runs on chunks of `chunk`
+ * realisations, the passes of one chunk back to back (a chunk whose meshes fit in L2 keeps
+ * them there between its passes); 0 or nreal = one launch per pass for the whole batch
+ * (the default).  The results do not depend on it.  Outside 0..nreal: PM_ERR_INVALID_ARG. */
+pm_status pm_batch_set_chunk(pm_batch* batch, int chunk);
+/* Autotuner of the batch's launch shape: times one step (replayed from a CUDA graph) for
+ * chunk = nreal, nreal/2, ..., 1 (rounded up) and keeps the fastest (chunk_out, and its
+ * ms per step in ms_out; either may be NULL).  It runs the step on the unperturbed
+ * lattice, so it overwrites the particles: call it before pm_batch_ic (PM_ERR_STATE once
+ * the run has started).  Synchronises. */
+pm_status pm_batch_autotune(pm_batch* batch, int* chunk_out, double* ms_out);
 /* Zel'dovich ICs of every realisation from seeds[r] (as pm_ic_zeldovich, same flags). */
 pm_status pm_batch_ic(pm_batch* batch, const uint64_t* seeds, int flags);
 /* n_steps KDK steps of every realisation; use_graph != 0 records the run once (cached for

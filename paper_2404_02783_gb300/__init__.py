@@ -31,7 +31,7 @@ EXPORTS = ("pm_workspace_size", "pm_init", "pm_destroy", "pm_ic_zeldovich", "pm_
            "pm_set_particles", "pm_state", "pm_profile", "pm_timings", "pm_density", "pm_potential", "pm_displacement_correction", "pm_power", "pm_halo_proxy", "pm_linear_bias",
            "pm_bispectrum_scratch_size", "pm_bispectrum", "pm_triangle_index", "pm_b1_gr_theory", "pm_cic_deposit", "pm_cic_interp",
            "pm_adjoint_scratch_size", "pm_loss_grad", "pm_batch_workspace_size", "pm_batch_init", "pm_batch_destroy", "pm_batch_context", "pm_batch_ic",
-           "pm_batch_step", "pm_batch_state", "pm_batch_power", "pm_batch_bias",
+           "pm_batch_step", "pm_batch_state", "pm_batch_power", "pm_batch_bias", "pm_batch_set_chunk", "pm_batch_autotune",
            "pm_cell_sort_scratch_size", "pm_cell_sort", "pm_cell_sort_static", "pm_fft_r2c", "pm_fft_c2r", "pm_version", "pm_last_error")
 
 
@@ -104,6 +104,8 @@ def lib():
         "pm_batch_state": (vp, ctypes.POINTER(i), pd, ctypes.POINTER(i)),
         "pm_batch_power": (vp, i, pd, i, pd, pd, pd),
         "pm_batch_bias": (vp, d, i, pd, d, i, pd),
+        "pm_batch_set_chunk": (vp, i),
+        "pm_batch_autotune": (vp, ctypes.POINTER(i), pd),
         "pm_cic_deposit": (vp, i64, i, i, d, vp, vp),
         "pm_cic_interp": (vp, i, vp, i64, i, vp, vp),
         "pm_cell_sort_scratch_size": (i64, i, ctypes.POINTER(sz)),
@@ -468,6 +470,17 @@ class PMBatch:
         if h is not None and _lib is not None:
             _lib.pm_batch_destroy(h)
             self.h = None
+
+    def set_chunk(self, chunk):
+        """Realisations per launch of every pass (0: the whole batch)."""
+        _check(lib().pm_batch_set_chunk(self.h, int(chunk)))
+
+    def autotune(self):
+        """Pick the realisations per launch by timing one step of each candidate (before ic);
+        returns (chunk, ms per step)."""
+        c, ms = ctypes.c_int(), ctypes.c_double()
+        _check(lib().pm_batch_autotune(self.h, ctypes.byref(c), ctypes.byref(ms)))
+        return c.value, ms.value
 
     def ic(self, seeds, paired=False, fixed=False, lpt_order=1):
         s = np.ascontiguousarray(seeds, dtype=np.uint64)

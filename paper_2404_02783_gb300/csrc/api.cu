@@ -1226,6 +1226,7 @@ struct pm_batch {
     int step = 0;
     bool synced = true;
     bool rho_valid = false;
+    int chunk = 0;  // realisations per launch of every pass (0: the whole batch)
     pmhost::Cosmo cosmo;
     void* at(size_t off) const { return ws + off; }
     double a_grid(int i) const { return cfg.a_init + ((cfg.a_final - cfg.a_init) * i) / cfg.n_steps; }
@@ -1278,49 +1279,76 @@ pm_status batch_validate(const pm_config* cfg, int B, const double* boxes) {
     return PM_OK;
 }
 
-// Force meshes of every realisation from rho (one launch per pass for the whole batch).
-pm_status batch_forces(pm_batch* b, cudaStream_t s) {
-    const int n = b->cfg.nmesh, B = b->B, M = n / 2;
-    float* rho = (float*)b->at(b->RHO);
-    float2* s0 = (float2*)b->at(b->SPEC[0]);
-    float2* s1 = (float2*)b->at(b->SPEC[1]);
-    float2* s2 = (float2*)b->at(b->SPEC[2]);
-    const double* kf = (const double*)b->at(b->KF);
-    PM_CK(forward_zy<float>(rho, s0, n, B, s));
-    PM_CK(cudaMemsetAsync(rho, 0, sizeof(float) * (size_t)B * n * n * n, s));
+// Force meshes of realisations r0 .. r0 + c - 1 from their rho (one launch per pass).
+pm_status batch_forces(pm_batch* b, cudaStream_t s, int r0, int c) {
+    const int n = b->cfg.nmesh, M = n / 2;
+    const size_t n3 = (size_t)n * n * n, nspec = (size_t)(M + 1) * n * n;
+    float* rho = (float*)b->at(b->RHO) + r0 * n3;
+    float2* s0 = (float2*)b->at(b->SPEC[0]) + r0 * nspec;
+    float2* s1 = (float2*)b->at(b->SPEC[1]) + r0 * nspec;
+    float2* s2 = (float2*)b->at(b->SPEC[2]) + r0 * nspec;
+    const double* kf = (const double*)b->at(b->KF) + r0;
+    PM_CK(forward_zy<float>(rho, s0, n, c, s));
+    PM_CK(cudaMemsetAsync(rho, 0, sizeof(float) * c * n3, s));
     SpecOp op;
     op.kind = OP_NEWTON;
     op.fwd = 1;
     op.coef = -1.5 * b->cfg.omega_m / ((double)n * n * n);
     op.kf_arr = kf;
-    PM_CK(x_cols<float>(s0, s1, B * (M + 1), n, op, s));
-    float* out[3] = {(float*)b->at(b->FORCE[0]), (float*)b->at(b->FORCE[1]), (float*)b->at(b->FORCE[2])};
-    PM_CK(inverse_yz_grad<float>(s0, s1, s2, out, n, B, 0.0, s, kf));
+    PM_CK(x_cols<float>(s0, s1, c * (M + 1), n, op, s));
+    float* out[3] = {(float*)b->at(b->FORCE[0]) + r0 * n3, (float*)b->at(b->FORCE[1]) + r0 * n3,
+                     (float*)b->at(b->FORCE[2]) + r0 * n3};
+    PM_CK(inverse_yz_grad<float>(s0, s1, s2, out, n, c, 0.0, s, kf));
     return PM_OK;
 }
 
-pm_status batch_update(pm_batch* b, double kick, double drift, cudaStream_t s) {
-    void* g[3] = {b->at(b->FORCE[0]), b->at(b->FORCE[1]), b->at(b->FORCE[2])};
+pm_status batch_update(pm_batch* b, double kick, double drift, cudaStream_t s, int r0, int c) {
+    const size_t n3 = (size_t)b->cfg.nmesh * b->cfg.nmesh * b->cfg.nmesh;
+    const size_t np3 = (size_t)b->cfg.np * b->cfg.np * b->cfg.np;
+    void* g[3] = {(float*)b->at(b->FORCE[0]) + r0 * n3, (float*)b->at(b->FORCE[1]) + r0 * n3,
+                  (float*)b->at(b->FORCE[2]) + r0 * n3};
     const double mass = std::pow((double)b->cfg.nmesh / b->cfg.np, 3);
-    PM_CK(interp_kick_drift_deposit(b->at(b->X), b->at(b->P), b->cfg.np, PM_FP32_FIXED, b->cfg.nmesh, g, kick, drift,
-                                    1.0, mass, b->at(b->RHO), s, b->B, (const double*)b->at(b->SCALE)));
+    PM_CK(interp_kick_drift_deposit((uint32_t*)b->at(b->X) + r0 * 3 * np3, (float*)b->at(b->P) + r0 * 3 * np3,
+                                    b->cfg.np, PM_FP32_FIXED, b->cfg.nmesh, g, kick, drift, 1.0, mass,
+                                    (float*)b->at(b->RHO) + r0 * n3, s, c, (const double*)b->at(b->SCALE) + r0));
+    return PM_OK;
+}
+
+// Forces and update of every realisation, chunk by chunk: each chunk's passes follow one
+// another, so a chunk small enough for L2 keeps its meshes there between the passes.
+pm_status batch_forces_update(pm_batch* b, double kick, double drift, cudaStream_t s) {
+    const int c = (b->chunk > 0 && b->chunk < b->B) ? b->chunk : b->B;
+    for (int r0 = 0; r0 < b->B; r0 += c) {
+        const int cc = std::min(c, b->B - r0);
+        PM_TRY(batch_forces(b, s, r0, cc));
+        PM_TRY(batch_update(b, kick, drift, s, r0, cc));
+    }
     return PM_OK;
 }
 
 // One KDK step of every realisation (the same a-grid for all), enqueued on s.
 pm_status batch_enqueue_step(pm_batch* b, cudaStream_t s) {
     const double a0 = b->a_grid(b->step), a1 = b->a_grid(b->step + 1), ah = 0.5 * (a0 + a1);
-    PM_TRY(batch_forces(b, s));
     const double a_from = b->synced ? a0 : 0.5 * (b->a_grid(b->step - 1) + a0);
-    PM_TRY(batch_update(b, pmhost::kick_integral(b->cosmo, a_from, ah), pmhost::drift_integral(b->cosmo, a0, a1), s));
+    PM_TRY(batch_forces_update(b, pmhost::kick_integral(b->cosmo, a_from, ah),
+                               pmhost::drift_integral(b->cosmo, a0, a1), s));
     b->step += 1;
     b->synced = false;
     if (b->step == b->cfg.n_steps) {
-        PM_TRY(batch_forces(b, s));
-        PM_TRY(batch_update(b, pmhost::kick_integral(b->cosmo, ah, a1), 0.0, s));
+        PM_TRY(batch_forces_update(b, pmhost::kick_integral(b->cosmo, ah, a1), 0.0, s));
         b->synced = true;
     }
     return PM_OK;
+}
+
+void batch_drop_graph(pm_batch* b) {
+    if (b->exec) {
+        cudaStreamSynchronize(b->cap);
+        cudaGraphExecDestroy(b->exec);
+        b->exec = nullptr;
+    }
+    b->exec_from = -1;
+    b->exec_steps = 0;
 }
 
 }  // namespace
@@ -1468,11 +1496,7 @@ pm_status pm_batch_step(pm_batch* b, int n_steps, int use_graph) {
     // the whole run is recorded once on the capture stream and replayed as one graph launch
     const int from = b->step;
     if (!(b->exec && b->exec_from == from && b->exec_steps == n_steps)) {
-        if (b->exec) {
-            PM_CK(cudaStreamSynchronize(b->cap));
-            cudaGraphExecDestroy(b->exec);
-            b->exec = nullptr;
-        }
+        batch_drop_graph(b);
         const bool synced0 = b->synced;
         PM_CK(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeRelaxed));
         pm_status s = PM_OK;
@@ -1502,6 +1526,78 @@ pm_status pm_batch_step(pm_batch* b, int n_steps, int use_graph) {
         b->step += 1;
         b->synced = (b->step == b->cfg.n_steps);
     }
+    return PM_OK;
+}
+
+pm_status pm_batch_set_chunk(pm_batch* b, int chunk) {
+    if (!b || chunk < 0 || chunk > b->B) return fail(PM_ERR_INVALID_ARG, "chunk must be in 0..nreal");
+    if (chunk != b->chunk) batch_drop_graph(b);
+    b->chunk = chunk;
+    return PM_OK;
+}
+
+pm_status pm_batch_autotune(pm_batch* b, int* chunk_out, double* ms_out) {
+    if (!b) return fail(PM_ERR_INVALID_ARG, "null batch");
+    if (b->step != 0) return fail(PM_ERR_STATE, "autotune before the run starts (it overwrites the particles)");
+    const size_t n3 = (size_t)b->cfg.nmesh * b->cfg.nmesh * b->cfg.nmesh;
+    // the unperturbed lattice (x = q, p = 0) in every realisation, and its density
+    PM_CK(cudaMemsetAsync(b->at(b->FORCE[0]), 0, sizeof(float) * b->B * n3, b->st));
+    for (int r = 0; r < b->B; ++r) {
+        pm_ctx* v = b->views[r];
+        void* zero[3] = {v->at(v->L.force[0]), v->at(v->L.force[0]), v->at(v->L.force[0])};
+        PM_CK(ic_place(v->at(v->L.x), v->at(v->L.p), zero, v->np, PM_FP32_FIXED, 0.0, 0.0, v->cfg.box, b->st));
+    }
+    for (int r = 0; r < b->B; ++r) PM_TRY(deposit_particles(b->views[r], b->at(b->views[r]->L.rho)));
+    PM_CK(cudaEventRecord(b->ev_in, b->st));
+    PM_CK(cudaStreamWaitEvent(b->cap, b->ev_in, 0));
+    batch_drop_graph(b);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    PM_CK(cudaEventCreate(&e0));
+    PM_CK(cudaEventCreate(&e1));
+    int best = b->B;
+    double best_ms = 1e300;
+    pm_status st = PM_OK;
+    // candidates: the whole batch, then halves down to one realisation per launch; each is
+    // one step (kick 0, drift 0: the state stays the lattice) replayed from a graph
+    for (int c = b->B;; c = (c + 1) / 2) {
+        b->chunk = c;
+        cudaGraph_t g = nullptr;
+        cudaGraphExec_t ex = nullptr;
+        if (cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeRelaxed) != cudaSuccess) {
+            st = fail(PM_ERR_CUDA, "autotune: capture");
+            break;
+        }
+        st = batch_forces_update(b, 0.0, 0.0, b->cap);
+        const cudaError_t ce = cudaStreamEndCapture(b->cap, &g);
+        if (st == PM_OK && ce != cudaSuccess) st = fail(PM_ERR_CUDA, std::string("autotune: ") + cudaGetErrorString(ce));
+        if (st == PM_OK && cudaGraphInstantiate(&ex, g, 0) != cudaSuccess) st = fail(PM_ERR_CUDA, "autotune: instantiate");
+        if (g) cudaGraphDestroy(g);
+        if (st != PM_OK) break;
+        float ms = 0.f;
+        cudaError_t le = cudaGraphLaunch(ex, b->cap);
+        if (le == cudaSuccess) le = cudaEventRecord(e0, b->cap);
+        for (int k = 0; k < 3 && le == cudaSuccess; ++k) le = cudaGraphLaunch(ex, b->cap);
+        if (le == cudaSuccess) le = cudaEventRecord(e1, b->cap);
+        if (le == cudaSuccess) le = cudaEventSynchronize(e1);
+        if (le == cudaSuccess) le = cudaEventElapsedTime(&ms, e0, e1);
+        cudaGraphExecDestroy(ex);
+        if (le != cudaSuccess) {
+            st = fail(PM_ERR_CUDA, std::string("autotune: ") + cudaGetErrorString(le));
+            break;
+        }
+        if (ms / 3.0 < best_ms) {
+            best_ms = ms / 3.0;
+            best = c;
+        }
+        if (c == 1) break;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    b->chunk = best;
+    b->rho_valid = false;
+    if (st != PM_OK) return st;
+    if (chunk_out) *chunk_out = best;
+    if (ms_out) *ms_out = best_ms;
     return PM_OK;
 }
 

@@ -130,3 +130,41 @@ def test_batched_2lpt_ics_match_the_oracle():
         q = ic.lattice_ticks(NP)
         assert rel_l2(_disp(xb, q), _disp(xo, q)) < 2e-6
         assert rel_l2(pb, po) < 2e-6
+
+
+@pytest.mark.parametrize("chunk", [1, 2])
+@pytest.mark.parametrize("graph", [True, False])
+def test_chunked_batch_matches_whole_batch(chunk, graph):
+    # realisations per launch change only the launch shape (chunk 2 of 3 leaves a partial chunk)
+    pm = lib()
+    out = []
+    for c in (0, chunk):
+        b = pm.PMBatch(_cfg(pm), boxes=BOXES)
+        b.set_chunk(c)
+        b.ic(SEEDS)
+        b.step(STEPS, graph=graph)
+        out.append([_batch_particles(b, r) for r in range(3)])
+    for r in range(3):
+        q = ic.lattice_ticks(NP)
+        assert rel_l2(_disp(out[1][r][0], q), _disp(out[0][r][0], q)) < 1e-6
+        assert rel_l2(out[1][r][1], out[0][r][1]) < 1e-6
+
+
+def test_autotuned_batch_matches_single_runs():
+    pm = lib()
+    b = pm.PMBatch(_cfg(pm), boxes=BOXES)
+    chunk, ms = b.autotune()
+    assert chunk in (3, 2, 1) and ms > 0
+    b.ic(SEEDS)
+    b.step(STEPS)
+    for r, (box, seed) in enumerate(zip(BOXES, SEEDS)):
+        xs, ps = _single(pm, box, seed, STEPS)
+        xb, pb = _batch_particles(b, r)
+        q = ic.lattice_ticks(NP)
+        assert rel_l2(_disp(xb, q), _disp(xs, q)) < 1e-5
+        assert rel_l2(pb, ps) < 1e-5
+    with pytest.raises(pm.PMError) as e:
+        b.autotune()  # the run has started
+    assert e.value.status == 7
+    with pytest.raises(pm.PMError):
+        b.set_chunk(4)
