@@ -339,22 +339,27 @@ pm_status kick_drift(pm_ctx* c, double kick, double drift) {
     return PM_OK;
 }
 
-void build_bin_table(int n, int nbins, const double* edges, std::vector<int16_t>& tab) {
-    const int64_t nmax = 3 * (int64_t)(n / 2) * (n / 2);
-    tab.assign(nmax + 1, (int16_t)-1);
+// Bin table of the context mesh on the device (every |n|^2 <= 3 (n/2)^2), built by a kernel
+// from the squared edges staged in the context's accumulator area; the host keeps the same
+// table for |n|^2 <= (n/2)^2 (the binned modes) in host_tab, from the same comparisons.
+pm_status upload_bin_table(pm_ctx* c, int nbins, const double* edges, std::vector<int16_t>& host_tab) {
+    const int n = c->n;
     std::vector<double> e2(nbins + 1);
     for (int b = 0; b <= nbins; ++b) e2[b] = edges[b] * edges[b];
-    for (int64_t n2 = 0; n2 <= nmax; ++n2) {
-        const double v = (double)n2;
-        int b = -1;
-        for (int q = nbins; q >= 0; --q)
-            if (e2[q] <= v) {
-                b = q;
-                break;
-            }
+    double* e2_dev = (double*)c->at(c->L.acc);
+    PM_CK(cudaMemcpyAsync(e2_dev, e2.data(), sizeof(double) * (nbins + 1), cudaMemcpyHostToDevice, c->st));
+    PM_CK(bin_table((int16_t*)c->at(c->L.bin_of), 3 * (int64_t)(n / 2) * (n / 2), e2_dev, nbins, c->st));
+    const int64_t top = (int64_t)(n / 2) * (n / 2);
+    host_tab.assign(top + 1, (int16_t)-1);
+    int q = -1;  // largest edge index with e2[q] <= s, advanced as s grows
+    for (int64_t s = 0; s <= top; ++s) {
+        const double v = (double)s;
+        while (q < nbins && e2[q + 1] <= v) ++q;
+        int b = q;
         if (v == e2[nbins]) b = nbins - 1;
-        tab[n2] = (b >= 0 && b < nbins) ? (int16_t)b : (int16_t)-1;
+        host_tab[s] = (b >= 0 && b < nbins) ? (int16_t)b : (int16_t)-1;
     }
+    return PM_OK;
 }
 
 // Weighted number of modes with |n|^2 = s for s <= (n/2)^2 over the stored half spectrum
@@ -401,8 +406,7 @@ pm_status power_t(pm_ctx* c, const void* field, const void* field2, int nbins, c
     PM_TRY(forward_to_y<T>(c, f1, s0, n));
     if (field2) PM_TRY(forward_to_y<T>(c, field2, s1, n));
     std::vector<int16_t> tab;
-    build_bin_table(n, nbins, edges, tab);
-    PM_CK(cudaMemcpyAsync(c->at(c->L.bin_of), tab.data(), tab.size() * 2, cudaMemcpyHostToDevice, c->st));
+    PM_TRY(upload_bin_table(c, nbins, edges, tab));
     // per-CTA rows of bin sums in the third spectrum buffer (free here), reduced in a fixed order
     const bool two = field2 && p2_out;
     double* rows = (double*)c->at(c->L.spec[2]);
@@ -496,8 +500,7 @@ pm_status bispectrum_t(pm_ctx* c, const void* field, int nbins, const double* ed
     fw.fwd = 1;
     PM_CK(x_cols<T>(s0, nullptr, n / 2 + 1, n, fw, c->st));
     std::vector<int16_t> tab;
-    build_bin_table(n, nbins, edges, tab);
-    PM_CK(cudaMemcpyAsync(c->at(c->L.bin_of), tab.data(), tab.size() * 2, cudaMemcpyHostToDevice, c->st));
+    PM_TRY(upload_bin_table(c, nbins, edges, tab));
     cplx<T>* specs = (cplx<T>*)(scratch + B.specs);
     T* fields = (T*)(scratch + B.fields);
     PM_CK(bk_masks<T>(s0, n, specs, m, nbins, (const int16_t*)c->at(c->L.bin_of), (const double*)c->at(c->L.wtab),

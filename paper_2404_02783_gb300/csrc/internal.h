@@ -80,6 +80,9 @@ cudaError_t y_rows_grad3(cplx<T>* A, cplx<T>* B, cplx<T>* C, int64_t nrows, int 
                          cudaStream_t st, const double* kf_arr = nullptr, int64_t rows_per_field = 0);
 template <typename T>
 cudaError_t x_cols(cplx<T>* data, cplx<T>* out2, int nplanes, int n, const SpecOp& op, cudaStream_t st);
+// tab[s] = bin of |n|^2 = s for s <= nmax from the squared edges e2[0..nbins] (device),
+// e2[b] <= s < e2[b+1], the last edge closed, -1 outside.
+cudaError_t bin_table(int16_t* tab, int64_t nmax, const double* e2, int nbins, cudaStream_t st);
 // out[b] = sum_r rows[r nbins + b] in row order (deterministic), r < nrows.
 cudaError_t bin_rows_sum(const double* rows, int nrows, int nbins, double* out, cudaStream_t st);
 // Transposed force chain on the x pass (adjoint): V holds the three y-transformed spectra

@@ -10,6 +10,34 @@
 
 namespace pm {
 
+// Bin of every integer |n|^2 <= nmax: the largest b with e2[b] <= |n|^2 (binary search on the
+// squared edges), the last edge closed, -1 outside [e2[0], e2[nbins]].  The host applies the
+// same comparisons to the same doubles, so both sides agree mode by mode.
+__global__ void k_bin_table(int16_t* __restrict__ tab, int64_t nmax, const double* __restrict__ e2, int nbins) {
+    for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s <= nmax; s += (int64_t)gridDim.x * blockDim.x) {
+        const double v = (double)s;
+        int b = -1;
+        if (e2[0] <= v) {
+            int lo = 0, hi = nbins;  // e2[lo] <= v; find the largest such index
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (e2[mid] <= v) lo = mid;
+                else hi = mid - 1;
+            }
+            b = lo;
+        }
+        if (v == e2[nbins]) b = nbins - 1;
+        tab[s] = (b >= 0 && b < nbins) ? (int16_t)b : (int16_t)-1;
+    }
+}
+
+cudaError_t bin_table(int16_t* tab, int64_t nmax, const double* e2, int nbins, cudaStream_t st) {
+    int64_t blocks = (nmax + 256) / 256;
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    k_bin_table<<<(unsigned)blocks, 256, 0, st>>>(tab, nmax, e2, nbins);
+    return cudaGetLastError();
+}
+
 template <typename T>
 __global__ void k_bk_masks(const cplx<T>* __restrict__ spec_n, int n, cplx<T>* __restrict__ out, int m, int nbins,
                            const int16_t* __restrict__ bin_of, const double* __restrict__ wtab, int deconv) {
