@@ -296,8 +296,8 @@ pm_status pm_batch_set_chunk(pm_batch* batch, int chunk);
 /* Autotuner of the batch's launch shape: times one step (replayed from a CUDA graph) for
  * chunk = nreal, nreal/2, ..., 1 (rounded up) and keeps the fastest (chunk_out, and its
  * ms per step in ms_out; either may be NULL).  It runs the step on the unperturbed
- * lattice, so it overwrites the particles: call it before pm_batch_ic (PM_ERR_STATE once
- * the run has started).  Synchronises. */
+ * lattice, so it overwrites the particles: call it before pm_batch_ic (PM_ERR_STATE after
+ * it).  Synchronises. */
 pm_status pm_batch_autotune(pm_batch* batch, int* chunk_out, double* ms_out);
 /* Zel'dovich ICs of every realisation from seeds[r] (as pm_ic_zeldovich, same flags). */
 pm_status pm_batch_ic(pm_batch* batch, const uint64_t* seeds, int flags);

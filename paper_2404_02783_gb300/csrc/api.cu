@@ -1230,6 +1230,7 @@ struct pm_batch {
     bool synced = true;
     bool rho_valid = false;
     int chunk = 0;  // realisations per launch of every pass (0: the whole batch)
+    bool have_ic = false;  // pm_batch_ic has run (the autotuner would overwrite the particles)
     pmhost::Cosmo cosmo;
     void* at(size_t off) const { return ws + off; }
     double a_grid(int i) const { return cfg.a_init + ((cfg.a_final - cfg.a_init) * i) / cfg.n_steps; }
@@ -1477,6 +1478,7 @@ pm_status pm_batch_context(pm_batch* b, int r, pm_ctx** view) {
 pm_status pm_batch_ic(pm_batch* b, const uint64_t* seeds, int flags) {
     if (!b || !seeds) return fail(PM_ERR_INVALID_ARG, "null argument");
     for (int r = 0; r < b->B; ++r) PM_TRY(pm_ic_zeldovich(b->views[r], seeds[r], nullptr, flags));
+    b->have_ic = true;
     b->step = 0;
     b->synced = true;
     b->rho_valid = false;
@@ -1541,7 +1543,8 @@ pm_status pm_batch_set_chunk(pm_batch* b, int chunk) {
 
 pm_status pm_batch_autotune(pm_batch* b, int* chunk_out, double* ms_out) {
     if (!b) return fail(PM_ERR_INVALID_ARG, "null batch");
-    if (b->step != 0) return fail(PM_ERR_STATE, "autotune before the run starts (it overwrites the particles)");
+    if (b->step != 0 || b->have_ic)
+        return fail(PM_ERR_STATE, "autotune before pm_batch_ic (it overwrites the particles)");
     const size_t n3 = (size_t)b->cfg.nmesh * b->cfg.nmesh * b->cfg.nmesh;
     // the unperturbed lattice (x = q, p = 0) in every realisation, and its density
     PM_CK(cudaMemsetAsync(b->at(b->FORCE[0]), 0, sizeof(float) * b->B * n3, b->st));

@@ -166,5 +166,10 @@ def test_autotuned_batch_matches_single_runs():
     with pytest.raises(pm.PMError) as e:
         b.autotune()  # the run has started
     assert e.value.status == 7
+    b2 = pm.PMBatch(_cfg(pm), boxes=BOXES)
+    b2.ic(SEEDS)
+    with pytest.raises(pm.PMError) as e:
+        b2.autotune()  # would overwrite the ICs
+    assert e.value.status == 7
     with pytest.raises(pm.PMError):
         b.set_chunk(4)
