@@ -17,19 +17,22 @@ Modules (each function cites the passage it follows):
 * ``philox``     -- Philox4x32-10 counter-based generator (Salmon et al. 2011) and
   the per-wavevector Gaussian draw used for the initial phases ("same initial
   random perturbation phases", Sec. 2).
-* ``ic``         -- Zel'dovich (1LPT) initial conditions (Sec. 2, nLPT with n=1).
-* ``cic``        -- cloud-in-cell deposit / interpolation, cell keys and sort order
+* ``ic``         -- Zel'dovich (1LPT) and second-order LPT initial conditions (Sec. 2,
+  nLPT with n = 1, 2; Sec. 3), paired and fixed-amplitude phases (Sec. 4.2).
+* ``cic``        -- cloud-in-cell deposit / interpolation, the gradient of the CIC
+  interpolant (the first-order force option, Sec. 4.1), cell keys and sort order
   (counting density, Sec. 4).
 * ``gravity``    -- Newtonian Poisson solve, spectral gradient, linearised
   Poisson-gauge scalar constraint (Sec. 2; Eq. physical_density).
-* ``pm``         -- kick-drift-kick leapfrog in the scale factor.
+* ``pm``         -- kick-drift-kick leapfrog in the scale factor (spectral or first-order
+  gradient).
 * ``combine``    -- GR displacement field and combination (Eqs. xiGR and combined).
 * ``stats``      -- power spectrum (Eq. powerspectrum), bispectrum (Eq. bispectre),
-  halo-proxy linear-bias fit (Eq. b1).
+  halo-proxy linear-bias fit (Eq. b1) and the relativistic bias of Eq. bgr.
 
 Parity status: every function is pinned by a ``-m "not gpu"`` test against a
 closed form, an invariant, a brute-force evaluation or a textbook special case,
 except the amplitude of the horizon-scale GR displacement, for which the paper
 prints no values (parity unpinned beyond the k >> H limit and the matter-era
-identity tested in ``tests/test_oracle_gravity.py``).
+identity tested in ``tests/test_oracle_cic_gravity.py``).
 """
