@@ -360,7 +360,8 @@ pm_status pm_fft_r2c(const void* real, void* spec, int n, int precision, void* s
  * (sum over modes of F_n exp(+2 pi i n.x / n)). */
 pm_status pm_fft_c2r(void* spec, void* real, int n, int precision, void* stream);
 
-/* Library version string and last error message. */
+/* Library version string and last error message.  0.2: pm_config gained `gradient`;
+ * pm_ic_zeldovich and pm_batch_ic take PM_IC_* flags. */
 const char* pm_version(void);
 const char* pm_last_error(void);
 

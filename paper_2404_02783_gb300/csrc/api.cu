@@ -547,7 +547,7 @@ pm_status bispectrum_t(pm_ctx* c, const void* field, int nbins, const double* ed
 // ====================================================================== C ABI
 extern "C" {
 
-const char* pm_version(void) { return "pm-gb300 0.1 (sm_103a)"; }
+const char* pm_version(void) { return "pm-gb300 0.2 (sm_103a)"; }
 
 const char* pm_last_error(void) { return g_err.c_str(); }
 
