@@ -460,8 +460,25 @@ def estimators(pm, torch, args):
                                "FFT chains (derivatives of each Psi1 component, then Psi2) and the source"}
     del ic_run
     e64 = pm.log_edges(64, 1.0, n / 2.0)
-    out["power_particles"] = line(timed(lambda: run.power(e64)), 12 * P + 16 * n**3,
-                                  "read x (12 B/particle), deposit and transform (16 B/cell)")
+    # after a step the fused update has left the density of the current positions in rho, which
+    # P(k) of the particles then transforms directly
+    out["power_particles"] = line(timed(lambda: run.power(e64)), R + S,
+                                  "after a step: the step's density, one pass over its half spectrum")
+    # standalone: the positions just set (pm_set_particles, untimed), so each call deposits them
+    xs, ps = (t.clone() for t in run.particles())
+    ts = []
+    for rep in range(4):
+        pm.pm_set_particles(run.ctx, xs, ps)
+        torch.cuda.synchronize()
+        e0.record(st)
+        run.power(e64)
+        e1.record(st)
+        e1.synchronize()
+        if rep:
+            ts.append(e0.elapsed_time(e1))
+    del xs, ps
+    out["power_particles_standalone"] = line(float(np.median(ts)), 12 * P + 16 * n**3,
+                                             "read x (12 B/particle), deposit and transform (16 B/cell)")
     out["power_field"] = line(timed(lambda: run.power(e64, field=delta)), R + S,
                               "read the field, one pass over its half spectrum")
     kf = 2 * np.pi / box

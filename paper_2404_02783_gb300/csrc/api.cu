@@ -252,6 +252,18 @@ pm_status deposit_particles(pm_ctx* c, void* rho) {
     return PM_OK;
 }
 
+// rho holding the counting density of the current particles: the one the last fused update
+// left there when it is still valid (the positions have not moved since), else a new deposit.
+pm_status current_density(pm_ctx* c, const void** rho_out) {
+    void* rho = c->at(c->L.rho);
+    if (!c->rho_valid) {
+        PM_TRY(deposit_particles(c, rho));
+        c->rho_valid = true;
+    }
+    *rho_out = rho;
+    return PM_OK;
+}
+
 // Force meshes g = -grad phi of the current particles at scale factor a.
 bool fused_update(const pm_ctx* c) { return ikd_deposit_supported(c->np, c->cfg.precision, c->n); }
 
@@ -397,10 +409,7 @@ pm_status power_t(pm_ctx* c, const void* field, const void* field2, int nbins, c
                   double* k_out, double* p_out, double* nmodes_out, double* p2_out = nullptr) {
     const int n = c->n;
     const void* f1 = field;
-    if (!f1) {
-        PM_TRY(deposit_particles(c, c->at(c->L.rho)));
-        f1 = c->at(c->L.rho);
-    }
+    if (!f1) PM_TRY(current_density(c, &f1));
     void* s0 = c->at(c->L.spec[0]);
     void* s1 = c->at(c->L.spec[1]);
     PM_TRY(forward_to_y<T>(c, f1, s0, n));
@@ -489,10 +498,7 @@ pm_status bispectrum_t(pm_ctx* c, const void* field, int nbins, const double* ed
                        unsigned char* scratch, const BkLayout& B, double* b_out, double* ntri_out) {
     const int n = c->n;
     const void* f1 = field;
-    if (!f1) {
-        PM_TRY(deposit_particles(c, c->at(c->L.rho)));
-        f1 = c->at(c->L.rho);
-    }
+    if (!f1) PM_TRY(current_density(c, &f1));
     cplx<T>* s0 = (cplx<T>*)c->at(c->L.spec[0]);
     PM_TRY(forward_to_y<T>(c, f1, s0, n));
     SpecOp fw;
@@ -775,7 +781,8 @@ pm_status pm_density(pm_ctx* c, void* delta) {
 pm_status pm_potential(pm_ctx* c, void* phi) {
     if (!c || !phi) return fail(PM_ERR_INVALID_ARG, "null argument");
     const int n = c->n;
-    PM_TRY(deposit_particles(c, c->at(c->L.rho)));
+    const void* rho = nullptr;
+    PM_TRY(current_density(c, &rho));
     SpecOp op;
     op.kind = OP_POTENTIAL;
     op.fwd = 1;
@@ -783,7 +790,7 @@ pm_status pm_potential(pm_ctx* c, void* phi) {
     op.coef = -1.5 * c->cfg.omega_m / ((double)n * n * n);
     if (c->fp64()) {
         double2* s0 = (double2*)c->at(c->L.spec[0]);
-        PM_TRY(forward_to_y<double>(c, c->at(c->L.rho), s0, n));
+        PM_TRY(forward_to_y<double>(c, rho, s0, n));
         PM_CK(x_cols<double>(s0, nullptr, n / 2 + 1, n, op, c->st));
         PM_CK((y_rows<double, true>(s0, (int64_t)(n / 2 + 1) * n, n, c->st)));
         const double2* in[1] = {s0};
@@ -791,7 +798,7 @@ pm_status pm_potential(pm_ctx* c, void* phi) {
         PM_CK(z_c2r<double>(in, out, 1, n, 1, 0u, 0.0, c->st));
     } else {
         float2* s0 = (float2*)c->at(c->L.spec[0]);
-        PM_TRY(forward_to_y<float>(c, c->at(c->L.rho), s0, n));
+        PM_TRY(forward_to_y<float>(c, rho, s0, n));
         PM_CK(x_cols<float>(s0, nullptr, n / 2 + 1, n, op, c->st));
         PM_CK((y_rows<float, true>(s0, (int64_t)(n / 2 + 1) * n, n, c->st)));
         const float2* in[1] = {s0};

@@ -208,3 +208,31 @@ def test_paired_fixed_bispectrum_slices_match_oracle(prec):
         live = ok[rows]
         assert live.sum() >= 3
         assert np.max(np.abs(b_avg[rows][live] - bo_avg[rows][live])) < tol
+
+
+@pytest.mark.parametrize("np_side,n", [(64, 64), (32, 64), (32, 32)])
+def test_power_after_a_step_reuses_the_step_density(np_side, n):
+    # after a step P(k) of the particles and the potential transform the density the update
+    # left in rho (fused update), or a deposit made once (unfused); the same numbers as a
+    # fresh deposit of the same positions, up to FP32 summation order
+    pm = lib()
+    run = _ctx(pm, np_side, n, 800.0, FP32, steps=6)
+    run.ic(seed=44)
+    run.step(2)
+    edges = stats.log_edges(12, 1.0, n / 2.0)
+    _, p_step, nm = run.power(edges)
+    phi_step = torch.empty((n, n, n), dtype=torch.float32, device="cuda")
+    pm.pm_potential(run.ctx, phi_step)
+    _, p_again, _ = run.power(edges)
+    x, p = run.particles()
+    xs, ps = x.clone(), p.clone()
+    pm.pm_set_particles(run.ctx, xs, ps)
+    _, p_fresh, nm2 = run.power(edges)
+    phi_fresh = torch.empty_like(phi_step)
+    pm.pm_potential(run.ctx, phi_fresh)
+    np.testing.assert_array_equal(nm, nm2)
+    ok = nm > 0
+    np.testing.assert_allclose(p_step[ok], p_fresh[ok], rtol=1e-5)
+    np.testing.assert_allclose(p_step[ok], p_again[ok], rtol=1e-12)  # FP64 bin sums, any order
+    d = (phi_step - phi_fresh).double().norm() / phi_fresh.double().norm()
+    assert float(d) < 1e-5
