@@ -165,16 +165,17 @@ static cudaError_t deposit_tiled_r(const void* x, int np, int n, double mass, vo
     const unsigned blocks = (unsigned)((np / D::TX) * (np / D::TY) * (np / D::TZ));
     const float inv = (float)ldexp(1.0, -(32 - logn));
     const size_t smem = sizeof(uint32_t) * D::WORDS;
-    if (R == 1) {
+    if constexpr (R == 1) {
         cudaError_t e = set_smem_once((const void*)k_deposit_sweep, smem);
         if (e != cudaSuccess) return e;
         k_deposit_sweep<<<blocks, 512, smem, st>>>((const uint32_t*)x, lognp, logn, inv, (float)mass, (float*)rho);
         return cudaGetLastError();
+    } else {
+        cudaError_t e = set_smem_once((const void*)k_deposit_tiled<R>, smem);
+        if (e != cudaSuccess) return e;
+        k_deposit_tiled<R><<<blocks, 512, smem, st>>>((const uint32_t*)x, lognp, logn, inv, (float)mass, (float*)rho);
+        return cudaGetLastError();
     }
-    cudaError_t e = set_smem_once((const void*)k_deposit_tiled<R>, smem);
-    if (e != cudaSuccess) return e;
-    k_deposit_tiled<R><<<blocks, 512, smem, st>>>((const uint32_t*)x, lognp, logn, inv, (float)mass, (float*)rho);
-    return cudaGetLastError();
 }
 
 cudaError_t deposit_lattice(const void* x, int np, int precision, int n, double mass, void* rho, cudaStream_t st) {
