@@ -13,10 +13,13 @@
  *   pm_ic_zeldovich            Lagrangian initial conditions, first (Zel'dovich) or second order
  *                              (Sec. 2 nLPT, n = 1, 2; Sec. 3 ICs at z = 50)
  *   pm_step                    CIC deposit, r2c FFT, Green's function (Newtonian, or the
- *                              linearised Poisson-gauge constraint), spectral gradient,
- *                              c2r FFT, CIC interpolation + kick + drift (KDK in a)
+ *                              linearised Poisson-gauge constraint), spectral or first-order
+ *                              gradient, c2r FFT, CIC interpolation + kick + drift (KDK in a)
  *   pm_displacement_correction Eqs. xiGR and combined
  *   pm_power / pm_bispectrum   Eqs. powerspectrum / bispectre on the CIC counting density
+ *   pm_linear_bias             Eq. b1 on a halo proxy (pm_halo_proxy), Eq. bgr (pm_b1_gr_theory)
+ *   pm_loss_grad               gradient of a field-level loss through the whole run
+ *   pm_batch_*                 many realisations stepped together from one CUDA graph
  *
  * Conventions shared by every entry point
  * --------------------------------------
@@ -39,9 +42,10 @@
  * sizes it with the *_size queries; the one exception is the fixed static array of
  * pm_cell_sort_static.  Host output arrays are caller-owned too.
  * Streams: calls are asynchronous on the stream given at pm_init (or per call for
- * the stateless operators) except pm_power and pm_bispectrum, which synchronise
- * that stream before returning host results, and pm_loss_grad, which also runs on a
- * second stream of the context's own and synchronises both.
+ * the stateless operators) except pm_power, pm_bispectrum and pm_linear_bias, which
+ * synchronise that stream before returning host results, and pm_loss_grad, which also
+ * runs on a second stream of the context's own and synchronises both.  Host-only calls
+ * (pm_triangle_index, pm_b1_gr_theory, the *_size queries) touch no device.
  * Errors: every call returns a pm_status; pm_last_error() gives a static,
  * thread-local message for the last failure.  A CUDA error inside a call is
  * returned as PM_ERR_CUDA and leaves the context unusable (pm_destroy it).
