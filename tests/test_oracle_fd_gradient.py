@@ -1,6 +1,7 @@
 """Pins of the first-order (CIC-interpolant) gradient used by the finite-difference force
 option (Sec. 4.1: the paper's PM code computes the force with a first-order gradient)."""
 import numpy as np
+import pytest
 
 import inputs
 from oracle import cic, gravity, ic, pm as opm
@@ -77,3 +78,37 @@ def test_fd1_run_differs_from_spectral_only_at_the_force():
     g_sp = spec.accel(a_i)
     # the two gradients agree on large scales: correlated to better than 10% here
     assert np.linalg.norm(g_fd - g_sp) < 0.2 * np.linalg.norm(g_sp)
+
+
+def test_fd1_force_is_minus_the_gradient_of_the_mesh_energy():
+    # With rho(c) = m sum_p W(x_p - c) (CIC) and a symmetric Green's function, the mesh energy
+    # E = 1/2 sum_c delta(c) phi(c) has dE/dx_p = m sum_c dW(x_p - c)/dx_p phi(c), i.e. m times
+    # the gradient of the CIC interpolant of phi at x_p: the first-order force is the exact
+    # negative gradient of the energy (E is piecewise quadratic in x_p, so a central difference
+    # inside the cell reproduces it to rounding)
+    n, box, om = 16, 400.0, 0.31
+    rng = np.random.default_rng(9)
+    x = rng.random((3, 6))
+    m = n**3 / x.shape[1]
+
+    def energy(xx):
+        delta = cic.density_contrast(xx, n)
+        phi = gravity.potential_mesh(gravity.newton_potential_k(np.fft.rfftn(delta), n, box, om), n)
+        return 0.5 * np.sum(delta * phi), phi
+
+    _, phi = energy(x)
+    grad = cic.interpolate_gradient(phi, x, box)
+    s = x * n - 0.5
+    frac = s - np.floor(s)
+    eps = 1e-4 / n
+    checked = 0
+    for p in range(x.shape[1]):
+        for j in range(3):
+            if not (0.01 < frac[j, p] < 0.99):
+                continue
+            e = np.zeros_like(x)
+            e[j, p] = eps
+            dE = (energy(x + e)[0] - energy(x - e)[0]) / (2 * eps * box)
+            assert dE == pytest.approx(m * grad[j, p], rel=1e-7, abs=1e-10 * m * np.abs(grad).max())
+            checked += 1
+    assert checked >= 12
