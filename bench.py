@@ -611,11 +611,16 @@ def cpu_oracle(seconds, np_side=64):
     for var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
         os.environ[var] = "1"  # one thread per process; the spawned workers inherit it
     t0 = time.perf_counter()
-    if cores == 1:
+    res = None
+    if cores > 1:
+        try:
+            with mp.get_context("spawn").Pool(cores) as pool:
+                res = pool.starmap(_oracle_sample, [(seconds, np_side, 1 + i) for i in range(cores)])
+        except OSError:  # no process pool on this host (e.g. no shared memory): one core
+            cores, res = 1, None
+            t0 = time.perf_counter()
+    if res is None:
         res = [_oracle_sample(seconds, np_side)]
-    else:
-        with mp.get_context("spawn").Pool(cores) as pool:
-            res = pool.starmap(_oracle_sample, [(seconds, np_side, 1 + i) for i in range(cores)])
     wall = time.perf_counter() - t0
     rates = [np_side**3 * s / dt for s, dt in res]
     box = 5000.0 * np_side / 512.0
