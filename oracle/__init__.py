@@ -31,8 +31,14 @@ Modules (each function cites the passage it follows):
   halo-proxy linear-bias fit (Eq. b1) and the relativistic bias of Eq. bgr.
 
 Parity status: every function is pinned by a ``-m "not gpu"`` test against a
-closed form, an invariant, a brute-force evaluation or a textbook special case,
-except the amplitude of the horizon-scale GR displacement, for which the paper
-prints no values (parity unpinned beyond the k >> H limit and the matter-era
-identity tested in ``tests/test_oracle_cic_gravity.py``).
+closed form, an invariant, a brute-force evaluation or a textbook special case.
+The Poisson-gauge lag term (Phi' as a backward difference) is pinned to linear
+Lambda-CDM theory, Phi = Phi_0 D(a)/a on every scale, through both the solve and
+the run's bookkeeping of Phi_old and dtau.  Two parts are pinned only partly:
+the amplitude of the horizon-scale GR displacement itself (the paper prints no
+values; pinned through the k >> calH limit, the matter-era identity and the
+linear-theory history above) and the Eisenstein-Hu constants of
+``cosmology.transfer_eh_nowiggle`` (checked by eye against EH98 Eqs. 26 and
+28-31; pinned only through the BBKS shape within 8%, so a change of a few percent
+in one constant would pass).
 """

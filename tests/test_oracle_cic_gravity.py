@@ -145,3 +145,65 @@ def test_gr_lag_fixed_point():
     Phi1 = gravity.gr_potential_k(dk, n, box, c, a, phi_old_k=Phi0, dtau=37.0)
     assert np.max(np.abs(Phi1 - Phi0)) < 1e-14 * np.max(np.abs(Phi0))
     assert C_LIGHT == pytest.approx(299792.458 / 100.0)
+
+
+def _linear_theory_history(c, n, box, a):
+    """Linear Lambda-CDM in Poisson gauge for pressureless matter: Phi(k, a) = Phi_0(k) D(a)/a
+    on every scale, so Phi' = (f - 1) calH Phi, and the 00 constraint fixes
+    delta_phys = -Phi (k^2 + 3 calH^2 f) / ((3/2) calH^2 Om(a)); delta_count = delta_phys - 3 Phi
+    (Eq. physical_density).  Returns (Phi, delta_count) at a."""
+    _, _, k2 = gravity._wavenumbers(n, box)
+    phi0 = np.fft.rfftn(inputs.gaussian_field(12, n)) * 1e-5
+    phi0[0, 0, 0] = 0.0
+    H, om, f = float(c.conformal_hubble(a)), float(c.omega_m_a(a)), c.growth_f(a)
+    phi = phi0 * c.growth_D(a) / a
+    dcount = -phi * (k2 + 3.0 * H * H * f) / (1.5 * H * H * om) - 3.0 * phi
+    dcount[0, 0, 0] = 0.0
+    return phi, dcount
+
+
+def _lagged_history_error(c, steps, n=8, box=40000.0, a_i=1.0 / 101.0):
+    """Largest error of the lagged solve along a uniform a-grid, fed the closed-form counting
+    density (Phi' = 0 at the first evaluation, backward difference over dtau afterwards)."""
+    grid = a_i + (1.0 - a_i) * np.arange(steps + 1) / steps
+    old, a_old, err = None, None, 0.0
+    for a in grid:
+        truth, dcount = _linear_theory_history(c, n, box, a)
+        if old is None:
+            Phi = gravity.gr_potential_k(dcount, n, box, c, a)
+        else:
+            Phi = gravity.gr_potential_k(dcount, n, box, c, a, phi_old_k=old, dtau=c.delta_tau(a_old, a))
+        err = max(err, np.max(np.abs(Phi - truth)) / np.max(np.abs(truth)))
+        old, a_old = Phi, a
+    return err
+
+
+def test_gr_lag_term_follows_linear_theory_on_superhorizon_modes():
+    # L = 40 Gpc/h on 8^3: k = 1.6e-4 .. 6e-4 h/Mpc, at or above the horizon (calH(a = 1) = 3.3e-4),
+    # where Phi' weighs as much as calH Phi.  The lagged constraint must follow Phi_0 D(a)/a with an
+    # error of first order in dtau (halving the step halves it), 1e-3 at 100 steps; a lag term with
+    # another coefficient than 3 calH misses it by 5-12%.
+    c = Cosmology()
+    e50, e100, e200 = (_lagged_history_error(c, s) for s in (50, 100, 200))
+    assert e100 < 1.5e-3
+    assert 1.8 < e50 / e100 < 2.2 and 1.8 < e100 / e200 < 2.2
+
+
+def test_pm_run_threads_phi_old_and_dtau_through_its_force_evaluations(monkeypatch):
+    # the same history through PMRun's own bookkeeping of Phi_old and dtau between the force
+    # evaluations of its steps (the counting density is handed in, the particles are not used)
+    from oracle import pm as opm
+    n, box, steps, a_i = 8, 40000.0, 100, 1.0 / 101.0
+    c = Cosmology()
+    now = {}
+    monkeypatch.setattr(opm.cic, "density_contrast",
+                        lambda x, nn: np.fft.irfftn(_linear_theory_history(c, n, box, now["a"])[1], s=(n, n, n), axes=(0, 1, 2)))
+    x = np.zeros((3, 1), dtype=np.uint32)
+    run = opm.PMRun(c, n, box, a_i, 1.0, steps, x, np.zeros((3, 1)), mode=opm.GR_POISSON)
+    err = 0.0
+    for a in run.a_grid:
+        now["a"] = a
+        Phi = run.potential_k(a) / (a * C_LIGHT**2)
+        truth = _linear_theory_history(c, n, box, a)[0]
+        err = max(err, np.max(np.abs(Phi - truth)) / np.max(np.abs(truth)))
+    assert err < 1.5e-3

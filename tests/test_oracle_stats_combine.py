@@ -50,10 +50,22 @@ def test_single_cosine_power():
     assert np.count_nonzero(np.nan_to_num(pk) > 1e-20) == 1
 
 
-def _brute_bispectrum(delta, box, edges):
+def _cic_window(n, nvec):
+    """Prod_j [sin(pi n_j / N) / (pi n_j / N)]^2: the Fourier transform of the CIC kernel."""
+    w = 1.0
+    for nj in nvec:
+        x = np.pi * nj / n
+        w *= 1.0 if nj == 0 else (np.sin(x) / x)**2
+    return w
+
+
+def _brute_bispectrum(delta, box, edges, deconvolve=False):
     n = delta.shape[0]
     dk, f = _full_dft(delta)
     NX, NY, NZ = np.meshgrid(f, f, f, indexing="ij")
+    if deconvolve:
+        for i in np.ndindex(dk.shape):
+            dk[i] /= _cic_window(n, (NX[i], NY[i], NZ[i]))
     n2 = NX**2 + NY**2 + NZ**2
     b = stats.assign_bins(n2, edges)
     nyq = (np.abs(NX) == n // 2) | (np.abs(NY) == n // 2) | (np.abs(NZ) == n // 2)
@@ -73,12 +85,14 @@ def _brute_bispectrum(delta, box, edges):
     return S, C
 
 
-def test_bispectrum_against_brute_force_triplets():
+@pytest.mark.parametrize("deconvolve", [False, True])
+def test_bispectrum_against_brute_force_triplets(deconvolve):
+    # each mode divided by its own CIC window W(n) before the triplet product when deconvolving
     n, box = 8, 300.0
     delta = inputs.lognormal_field(22, n, sigma=0.8)
     edges = np.array([0.5, 1.5, 2.5, 3.5])
-    tri, B, ntri = stats.bispectrum(delta, box, edges, deconvolve=False)
-    S, C = _brute_bispectrum(delta, box, edges)
+    tri, B, ntri = stats.bispectrum(delta, box, edges, deconvolve=deconvolve)
+    S, C = _brute_bispectrum(delta, box, edges, deconvolve)
     for (i, j, l), bval, nt in zip(tri, B, ntri):
         assert nt == C[i, j, l]
         if nt > 0:
