@@ -33,6 +33,7 @@ sys.path.insert(0, ROOT)
 METRIC = "PM particle-steps/s and fraction of HBM roofline at 512^3, FP32 vs FP64 plain"
 UNIT = "particle-steps/s"
 A_INIT, A_FINAL = 1.0 / 51.0, 1.0
+GRID_STEPS = 100  # the headline run: 100 KDK steps from z = 50 to z = 0, whatever --steps asks to time
 PHASES = ("deposit", "fft_zy_fwd", "fft_x_green", "fft_yz_inv", "kick_drift")
 
 
@@ -198,25 +199,32 @@ def time_steps(pm, torch, run, k, world):
     return e0.elapsed_time(e1)
 
 
-def bench_precision(pm, torch, args, prec, rank, world, clocks=None):
-    """K timed steps after W warm-up steps of a run whose a-grid has exactly W + K steps, so the
-    timed steps end at z = 0; then the same W + K steps again from the same ICs with the
-    library's per-phase events on (the kernel rooflines cover the same steps as the headline)."""
-    fp64 = prec == pm.PM_FP64
-    n_steps = args.warmup + args.steps
-    cfg = pm.make_config(args.np, args.nmesh, args.box, A_INIT, A_FINAL, n_steps, precision=prec)
-    run = pm.PMRun(cfg)
-    run.ic(seed=1 + rank)
-    run.step(args.warmup)
+def start_of_timed_steps(pm, torch, run, k):
+    """Put the run at step GRID_STEPS - k of its a-grid (ICs, then the untimed steps before
+    the timed ones), so that the k timed steps end at z = 0."""
+    run.ic(seed=run.seed)
+    run.step(GRID_STEPS - k)
     torch.cuda.synchronize()
+
+
+def bench_precision(pm, torch, args, prec, rank, world, clocks=None):
+    """The last K steps of the fixed GRID_STEPS-step run (z = 50 -> 0; the closing half kick
+    included), after W warm-up steps taken on the same context from the ICs; then the same K
+    steps again with the library's per-phase events on (the kernel rooflines cover the same
+    steps as the headline)."""
+    cfg = pm.make_config(args.np, args.nmesh, args.box, A_INIT, A_FINAL, GRID_STEPS, precision=prec)
+    run = pm.PMRun(cfg)
+    run.seed = 1 + rank
+    run.ic(seed=run.seed)
+    run.step(args.warmup)
+    start_of_timed_steps(pm, torch, run, args.steps)
     if clocks:
         clocks.mark("t0")
     ms = time_steps(pm, torch, run, args.steps, world)
     if clocks:
         clocks.mark("t1")
     ms = max_over_ranks(ms, world)
-    run.ic(seed=1 + rank)
-    run.step(args.warmup)
+    start_of_timed_steps(pm, torch, run, args.steps)
     pm.pm_profile(run.ctx, True)
     pm.pm_timings(run.ctx)
     run.step(args.steps)
@@ -225,7 +233,7 @@ def bench_precision(pm, torch, args, prec, rank, world, clocks=None):
     del run
     torch.cuda.synchronize()
     torch.cuda.empty_cache()
-    return ms, phases, n_steps
+    return ms, phases
 
 
 def roofline(phases, np_side, n, fp64, peak, peak_kind):
@@ -246,7 +254,31 @@ def roofline(phases, np_side, n, fp64, peak, peak_kind):
             "peak_source": f"{peak_kind} hbm_gbs (MEASURED_PEAKS.json)" if peak_kind == "measured" else "fallback"}, table
 
 
-FP64_NOMINAL_TFLOPS = 1.25  # GB300 dense FP64 (no measured FP64 peak is recorded)
+FP64_NOMINAL_TFLOPS = 1.25  # GB300 dense FP64, nominal
+
+
+def fp64_peak(torch):
+    """Measured FP64 arithmetic ceiling of this GPU: a float64 torch.matmul (cuBLAS DGEMM) of
+    4096^3, best of 5 (TFLOP/s); the nominal figure if the measurement fails."""
+    try:
+        n = 4096
+        a = torch.randn((n, n), dtype=torch.float64, device="cuda")
+        b = torch.randn((n, n), dtype=torch.float64, device="cuda")
+        st = torch.cuda.current_stream()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.matmul(a, b)
+        best = float("inf")
+        for _ in range(5):
+            e0.record(st)
+            torch.matmul(a, b)
+            e1.record(st)
+            e1.synchronize()
+            best = min(best, e0.elapsed_time(e1) * 1e-3)
+        del a, b
+        torch.cuda.empty_cache()
+        return {"tflops": 2.0 * n**3 / best / 1e12, "source": "measured: float64 torch.matmul 4096^3, best of 5"}
+    except RuntimeError:
+        return {"tflops": FP64_NOMINAL_TFLOPS, "source": "nominal GB300 dense FP64 (measurement failed)"}
 
 
 def fft_flops(n):
@@ -263,24 +295,27 @@ def fft_flops(n):
             "fft_yz_inv": 3 * rows * cfft(n) + 3 * zero}
 
 
-def alu_roofline(phases, n):
+def alu_roofline(phases, n, peak):
     """The FP64 passes are bound by FP64 arithmetic on this part: flops per launch of the
-    slowest FFT phase against the nominal FP64 rate."""
+    slowest FFT phase against the measured FP64 matmul rate."""
     fl = fft_flops(n)
     dom = max(fl, key=lambda p: phases[p][0] / max(phases[p][1], 1))
     ms = phases[dom][0] / max(phases[dom][1], 1)
     achieved = fl[dom] / (ms * 1e-3) / 1e12
-    return {"kernel": dom, "bound": "alu", "achieved": round(achieved, 3), "peak": FP64_NOMINAL_TFLOPS,
-            "unit": "TFLOP/s", "frac": round(achieved / FP64_NOMINAL_TFLOPS, 4), "flops_per_launch": fl[dom],
-            "peak_source": "nominal GB300 dense FP64 (not measured)"}
+    return {"kernel": dom, "bound": "alu", "achieved": round(achieved, 3), "peak": round(peak["tflops"], 3),
+            "unit": "TFLOP/s", "frac": round(achieved / peak["tflops"], 4), "flops_per_launch": fl[dom],
+            "peak_source": peak["source"]}
 
 
 def e2e(pm, torch, args, rank, world, n_jobs=2):
-    """Public-API end to end: ICs from pinned host memory -> k steps -> P(k) back to the host."""
-    n_steps = max(100, args.steps + 2)
-    cfg = pm.make_config(args.np, args.nmesh, args.box, A_INIT, A_FINAL, n_steps)
+    """Public-API end to end over the headline's own steps: the state at step GRID_STEPS - K
+    (positions and momenta, held in pinned host memory) copied to the device, restored with
+    pm_set_state, the last K steps to z = 0, P(k) in 64 bins read back to the host."""
+    cfg = pm.make_config(args.np, args.nmesh, args.box, A_INIT, A_FINAL, GRID_STEPS)
     run = pm.PMRun(cfg)
-    run.ic(seed=1 + rank)
+    run.seed = 1 + rank
+    start_of_timed_steps(pm, torch, run, args.steps)
+    s0, _, sync0 = run.state()
     x0, p0 = run.particles()
     x_h = torch.empty_like(x0, device="cpu").pin_memory()
     p_h = torch.empty_like(p0, device="cpu").pin_memory()
@@ -298,7 +333,7 @@ def e2e(pm, torch, args, rank, world, n_jobs=2):
         t0 = time.perf_counter()
         x.copy_(x_h, non_blocking=True)
         p.copy_(p_h, non_blocking=True)
-        pm.pm_set_particles(run.ctx, x, p)
+        pm.pm_set_state(run.ctx, x, p, s0, sync0)
         run.step(args.steps)
         k, pk, nm = run.power(edges)  # synchronises and copies P(k) to the host
         times.append(time.perf_counter() - t0)
@@ -309,7 +344,8 @@ def e2e(pm, torch, args, rank, world, n_jobs=2):
     torch.cuda.empty_cache()
     return {"value": world * args.np**3 * args.steps / t, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
             "d2h_bytes_per_step": int(d2h),
-            "what": "IC particles copied from pinned host memory, k PM steps, P(k) (64 bins) read back"}
+            "what": f"the state at step {s0} of {GRID_STEPS} copied from pinned host memory and restored "
+                    f"(pm_set_state), the last {args.steps} PM steps to z = 0, P(k) (64 bins) read back"}
 
 
 def batched(pm, torch, args):
@@ -585,50 +621,162 @@ def estimators(pm, torch, args):
     return out
 
 
-def _oracle_sample(seconds, np_side=64, seed=1):
-    """One process: the FP64 oracle on a 64^3 sample of the workload at the same mesh spacing;
-    returns (steps, seconds)."""
+def host_cores():
+    """(cores this process may run on, how that was found): the affinity mask where the
+    platform has one, else the logical CPU count."""
+    try:
+        return len(os.sched_getaffinity(0)), "sched_getaffinity"
+    except (AttributeError, OSError):
+        return max(1, os.cpu_count() or 1), "os.cpu_count"
+
+
+def gr_pair(pm, torch, n_lo=None):
+    """The paired runs of the horizon-scale configuration: 128^3 particles on a 256^3 mesh,
+    L = 4000 Mpc/h, the same Zel'dovich ICs at z = 100, 100 steps to z = 0 in the Newtonian and
+    the Poisson-gauge (GR) mode, then the per-particle GR - Newtonian displacement xi and P(k)
+    of both runs (32 log bins).  One job = both ICs, both runs, xi and both spectra."""
+    import numpy as np
+    np_side, n, box, a_i, steps = 128, 256, 4000.0, 1.0 / 101.0, 100
+    lo = pm.DEFAULT_N_LO if n_lo is None else n_lo
+    runs = [pm.PMRun(pm.make_config(np_side, n, box, a_i, 1.0, steps, mode=mode, n_lo=lo if mode else 0))
+            for mode in (pm.PM_NEWTON, pm.PM_GR_POISSON)]
+    target = pm.PMRun(pm.make_config(np_side, n, box, a_i, 1.0, steps))
+    xi = torch.empty((3, np_side**3), dtype=torch.int32, device="cuda")
+    edges = pm.log_edges(32, 1.0, n / 2.0)
+    st = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def job():
+        for r in runs:
+            r.ic(seed=1)
+            r.step(steps)
+        target.ic(seed=1)
+        pm.pm_displacement_correction(target.ctx, runs[1].ctx, runs[0].ctx, xi)
+        return [r.power(edges) for r in runs]
+
+    job()
+    best = float("inf")
+    for _ in range(3):
+        torch.cuda.synchronize()
+        e0.record(st)
+        job()
+        e1.record(st)
+        e1.synchronize()
+        best = min(best, e0.elapsed_time(e1))
+    xi_rms = float(xi.to(torch.float64).pow(2).mean().sqrt().item()) * box / 2.0**32
+    del runs, target, xi
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    return {"workload": f"{np_side}^3 particles on a {n}^3 mesh, L={box:g} Mpc/h, Zel'dovich ICs at z=100, {steps} "
+                        f"steps to z=0, Newtonian and Poisson-gauge (n_lo={lo}) runs from the same seed, xi = "
+                        "x_GR - x_N per particle, P(k) of both (32 log bins)",
+            "ms_per_job": round(best, 3), "ms_per_step_per_run": round(best / (2 * steps), 4),
+            "particle_steps_per_s": round(2 * np_side**3 * steps / (best * 1e-3), 1),
+            "xi_rms_mpc_h": xi_rms}
+
+
+def _oracle_sample(seconds, np_side=64, seed=1, gate=None, max_steps=99):
+    """One process: the FP64 oracle on an np_side^3 sample of the workload at the same mesh
+    spacing (L = 5000 np_side / 512 Mpc/h).  The ICs are built first; then the process waits
+    at `gate` (shared by all processes, so their timed windows line up) and steps for about
+    `seconds` (at least one step).  Returns (steps, wall start, wall end)."""
     from oracle import ic, pm as opm
     from oracle.cosmology import Cosmology
     box = 5000.0 * np_side / 512.0
     c = Cosmology()
     x, p = ic.zeldovich(c, np_side, box, A_INIT, seed=seed, fixed=True)
-    run = opm.PMRun(c, np_side, box, A_INIT, A_FINAL, 100, x, p)
-    t0 = time.perf_counter()
+    run = opm.PMRun(c, np_side, box, A_INIT, A_FINAL, GRID_STEPS, x, p)
+    if gate is not None:
+        gate.wait()
+    t0 = time.time()
     steps = 0
-    while steps < 99 and (time.perf_counter() - t0 < seconds or steps < 2):
+    while steps < max_steps and (time.time() - t0 < seconds or steps < 1):
         run.step(1)
         steps += 1
-    return steps, time.perf_counter() - t0
+    return steps, t0, time.time()
+
+
+class _OneThread:
+    """OMP / OpenBLAS / MKL thread counts of 1 for spawned workers, restored on exit."""
+    VARS = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")
+
+    def __enter__(self):
+        self.saved = {v: os.environ.get(v) for v in self.VARS}
+        for v in self.VARS:
+            os.environ[v] = "1"
+
+    def __exit__(self, *exc):
+        for v, old in self.saved.items():
+            if old is None:
+                os.environ.pop(v, None)
+            else:
+                os.environ[v] = old
+
+
+def _oracle_processes(nproc, seconds, np_side, max_steps):
+    """nproc spawned single-threaded oracle processes released together by a barrier
+    (spawned, so nothing forks after CUDA started).  Returns their results, or None when
+    this host cannot start a process pool."""
+    import multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    try:
+        with _OneThread(), ctx.Manager() as mgr:
+            gate = mgr.Barrier(nproc)
+            with ctx.Pool(nproc) as pool:
+                return pool.starmap(_oracle_sample,
+                                    [(seconds, np_side, 1 + i, gate, max_steps) for i in range(nproc)])
+    except (OSError, EOFError):
+        return None
 
 
 def cpu_oracle(seconds, np_side=64):
-    """The FP64 oracle on this host's cores: one single-threaded process per core (a spawned
-    pool, so no process is forked after CUDA started), each running the 64^3 sample for about
-    `seconds`; value = the sum of their particle-steps/s."""
-    import multiprocessing as mp
-    cores = max(1, os.cpu_count() or 1)
-    for var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
-        os.environ[var] = "1"  # one thread per process; the spawned workers inherit it
+    """The FP64 oracle on this host's cores: one single-threaded process per core, each
+    stepping its own np_side^3 sample for about `seconds` after a common start; value =
+    the particle-steps of all processes / the wall time from the common start to the
+    last end."""
+    cores, how = host_cores()
     t0 = time.perf_counter()
-    res = None
-    if cores > 1:
-        try:
-            with mp.get_context("spawn").Pool(cores) as pool:
-                res = pool.starmap(_oracle_sample, [(seconds, np_side, 1 + i) for i in range(cores)])
-        except OSError:  # no process pool on this host (e.g. no shared memory): one core
-            cores, res = 1, None
-            t0 = time.perf_counter()
-    if res is None:
-        res = [_oracle_sample(seconds, np_side)]
+    res = _oracle_processes(cores, seconds, np_side, 99) if cores > 1 else None
+    threads = "one thread a process"
+    if res is None:  # no process pool on this host: one in-process sample
+        cores, res = 1, [_oracle_sample(seconds, np_side)]
+        threads = "numpy's thread pools as inherited"
     wall = time.perf_counter() - t0
-    rates = [np_side**3 * s / dt for s, dt in res]
+    units = np_side**3
+    span = max(e for _, _, e in res) - min(b for _, b, _ in res)
+    rates = [units * n / (e - b) for n, b, e in res]
     box = 5000.0 * np_side / 512.0
-    return {"value": sum(rates), "unit": UNIT, "cores": cores, "kind": "oracle",
-            "per_core_value": statistics.median(rates),
+    per_step_ms = statistics.median(1e3 * (e - b) / n for n, b, e in res)
+    return {"value": units * sum(n for n, _, _ in res) / span, "unit": UNIT, "cores": cores, "cores_from": how,
+            "kind": "oracle", "per_core_value": statistics.median(rates), "ms_per_step_per_process": per_step_ms,
             "sample": f"{cores} processes x {np_side}^3 particles on a {np_side}^3 mesh, L={box:g} Mpc/h "
-                      f"(same cell size), {min(s for s, _ in res)}-{max(s for s, _ in res)} KDK steps from "
-                      f"z=50 each, FP64 numpy oracle, one thread a process, {wall:.1f} s wall"}
+                      f"(same cell size as 512^3 at L=5000), {min(n for n, _, _ in res)}-"
+                      f"{max(n for n, _, _ in res)} KDK steps of the 100-step run from z=50 each, timed from a "
+                      f"common start, FP64 numpy oracle, {threads}, {wall:.1f} s wall"}
+
+
+def cpu_rows(sizes, all_cores_up_to=256):
+    """Per-step wall time of the oracle at each size: one process alone (one step after
+    its ICs), and -- up to all_cores_up_to^3 -- one process per core stepping together
+    (aggregate particle-steps/s over their common window)."""
+    cores, how = host_cores()
+    rows = {}
+    for n in sizes:
+        steps, b, e = _oracle_sample(0.0, n, 1, None, 1)
+        row = {"one_process_ms_per_step": round(1e3 * (e - b) / steps, 1),
+               "one_process_particle_steps_per_s": round(n**3 * steps / (e - b), 1)}
+        if n <= all_cores_up_to and cores > 1:
+            res = _oracle_processes(cores, 0.0, n, 1)
+            if res:
+                span = max(t for _, _, t in res) - min(t for _, t, _ in res)
+                row["all_cores_particle_steps_per_s"] = round(n**3 * sum(k for k, _, _ in res) / span, 1)
+                row["all_cores_ms_per_step_per_process"] = round(
+                    statistics.median(1e3 * (t1 - t0) / k for k, t0, t1 in res), 1)
+                row["cores"] = cores
+        rows[f"{n}^3"] = row
+    return {"kind": "oracle", "cores_from": how, "rows": rows,
+            "what": "FP64 numpy oracle, particles = mesh cells, L = 5000 n / 512 Mpc/h (the headline's cell "
+                    "size), one KDK step of the 100-step run from z = 50 after the ICs"}
 
 
 def main():
@@ -647,13 +795,19 @@ def main():
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-estimators", action="store_true")
+    ap.add_argument("--cpu-rows", default="128",
+                    help="comma-separated oracle sizes timed per step (e.g. 128,256,512); empty: none")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("at least 3 warm-up steps")
+    if not 1 <= args.steps <= GRID_STEPS:
+        ap.error(f"--steps times the last K steps of the {GRID_STEPS}-step run: 1 <= K <= {GRID_STEPS}")
     world, rank, local = dist_setup()
     workload = (f"{args.np}^3 particles, {args.nmesh}^3 CIC mesh, L={args.box:g} Mpc/h, Newtonian PM, "
-                f"ZA ICs at z=50, KDK on a uniform a-grid to z=0 (LCDM Om=0.31, EH no-wiggle, sigma8=0.81)")
+                f"ZA ICs at z=50, {GRID_STEPS} KDK steps on a uniform a-grid to z=0 (LCDM Om=0.31, EH no-wiggle, "
+                f"sigma8=0.81); the last {args.steps} steps timed")
     config = {"workload": workload, "np": args.np, "nmesh": args.nmesh, "box_mpc_h": args.box,
+              "a_grid_steps": GRID_STEPS, "timed_steps": f"{GRID_STEPS - args.steps}..{GRID_STEPS - 1} (ending at z=0)",
               "positions": "uint32 fixed point", "parallelism": f"replicas x{world}",
               "l2": "inputs larger than L2 (3.2 GB particles, 0.5 GB per mesh); no flush"}
 
@@ -663,13 +817,17 @@ def main():
         ms_t0 = time.perf_counter()
         cb = cpu_oracle(max(args.cpu_seconds, 5.0))
         total = time.perf_counter() - ms_t0
+        sample_cfg = {"workload": "the FP64 oracle on a sample of the workload: " + cb["sample"],
+                      "np": 64, "nmesh": 64, "box_mpc_h": 625.0, "a_grid_steps": GRID_STEPS,
+                      "parallelism": f"{cb['cores']} host processes", "sample_of": workload}
         line = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": UNIT, "n_gpus": args.gpus,
-                "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * args.np**3 / cb["value"],
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": cb["ms_per_step_per_process"],
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-                "data": "synthetic (seeded Philox phases)", "config": config,
+                "data": "synthetic (seeded Philox phases)", "config": sample_cfg,
                 "cpu_baseline": {**cb}, "e2e": {"value": cb["value"], "unit": UNIT, "h2d_bytes_per_step": 0,
                                                 "d2h_bytes_per_step": 0},
-                "note": f"FP64 CPU oracle timed on a bounded sample ({total:.1f} s wall)"}
+                "note": f"FP64 CPU oracle timed on a bounded sample ({total:.1f} s wall); ms_per_step is the "
+                        "median wall time of one oracle step of one 64^3 process"}
         print(json.dumps(line))
         return
 
@@ -685,7 +843,7 @@ def main():
     peak, peak_kind = peaks()
     clocks = Clocks(local if world > 1 else 0)
     clocks.start()
-    ms32, ph32, n_steps = bench_precision(pm, torch, args, pm.PM_FP32_FIXED, rank, world, clocks)
+    ms32, ph32 = bench_precision(pm, torch, args, pm.PM_FP32_FIXED, rank, world, clocks)
     clk = clocks.stop()
     value = world * args.np**3 * args.steps / (ms32 * 1e-3)
     ms_step = ms32 / args.steps
@@ -694,7 +852,7 @@ def main():
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded Philox phases, EH no-wiggle LCDM)",
-           "config": {**config, "a_grid_steps": n_steps}, "clocks": clk,
+           "config": config, "clocks": clk,
            "gpu_launches": launches_per_step(args.np, args.nmesh, False) * args.steps,
            "roofline": roof,
            "step_roofline": {"bytes_per_step": sb, "achieved": round(sb / (ms_step * 1e-3) / 1e9, 1),
@@ -702,13 +860,14 @@ def main():
                              "bytes_model": "60 B/particle + 40 B/cell"},
            "phases_fp32": table32}
     if not args.no_fp64:
-        ms64, ph64, _ = bench_precision(pm, torch, args, pm.PM_FP64, rank, world)
+        ms64, ph64 = bench_precision(pm, torch, args, pm.PM_FP64, rank, world)
         sb64 = step_bytes(args.np, args.nmesh, True)
         roof64, table64 = roofline(ph64, args.np, args.nmesh, True, peak, peak_kind)
         out["fp64_plain"] = {"value": world * args.np**3 * args.steps / (ms64 * 1e-3), "unit": UNIT,
                              "ms_per_step": ms64 / args.steps,
                              "step_roofline_frac": round(sb64 / (ms64 / args.steps * 1e-3) / 1e9 / peak, 4),
-                             "dominant": roof64, "alu_roofline": alu_roofline(ph64, args.nmesh), "phases": table64}
+                             "dominant": roof64, "alu_roofline": alu_roofline(ph64, args.nmesh, fp64_peak(torch)),
+                             "phases": table64}
     if not args.no_e2e:
         out["e2e"] = e2e(pm, torch, args, rank, world)
     if not args.no_batch:
@@ -720,8 +879,13 @@ def main():
         cb = out["estimators"]["cufft_baseline"]
         cb["ours_fft_phases_ms"] = round(sum(table32[p]["ms_per_launch"] for p in ("fft_zy_fwd", "fft_x_green",
                                                                                    "fft_yz_inv")), 4)
+    if not args.no_estimators and rank == 0:
+        out["gr_pair"] = gr_pair(pm, torch)
     if rank == 0:
         out["cpu_baseline"] = cpu_oracle(args.cpu_seconds)
+        sizes = [int(v) for v in args.cpu_rows.split(",") if v.strip()]
+        if sizes:
+            out["cpu_baseline"]["per_size"] = cpu_rows(sizes)
         print(json.dumps(out))
     if world > 1:
         import torch.distributed as dist

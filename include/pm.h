@@ -68,7 +68,7 @@ typedef enum {
     PM_ERR_CUDA = 2,          /* a CUDA runtime call or kernel launch failed */
     PM_ERR_WORKSPACE = 3,     /* caller buffer too small or misaligned (256 B) */
     PM_ERR_TIMEOUT = 4,       /* a bounded device wait gave up (reserved) */
-    PM_ERR_BOUNDS = 5,        /* a device-side index check failed */
+    PM_ERR_BOUNDS = 5,        /* input outside the mesh's bounds (FP64 positions outside [0, 1)) */
     PM_ERR_UNSUPPORTED = 6,   /* no suitable GPU */
     PM_ERR_STATE = 7          /* call out of order (e.g. stepping past a_final) */
 } pm_status;
@@ -149,8 +149,22 @@ pm_status pm_step(pm_ctx* ctx, int n_steps);
 pm_status pm_particles(pm_ctx* ctx, void** x, void** p);
 
 /* Copy particles in (device-to-device, caller layout = context layout) and reset
- * the step counter to 0 with synchronised momenta at a_init. */
+ * the step counter to 0 with synchronised momenta at a_init.  FP64 positions must be
+ * finite box fractions in [0, 1): otherwise PM_ERR_BOUNDS and nothing is copied (the
+ * check runs on the device and synchronises the context stream; uint32 ticks are valid
+ * by construction and are not checked). */
 pm_status pm_set_particles(pm_ctx* ctx, const void* x, const void* p);
+
+/* Resume a run at a point of its a-grid (checkpoint / restart; the paper's runs write
+ * snapshots at fixed redshifts, Secs. 3-5): copy x, p in as pm_set_particles does and set
+ * the integrator to `step` (0..n_steps) with momenta synchronised with the positions
+ * (synchronised != 0) or half a step behind (0, the state pm_step leaves between steps:
+ * p at the midpoint a_{step-1/2}).  The momenta are synchronised at step 0 and at
+ * n_steps (otherwise PM_ERR_INVALID_ARG).  A Poisson-gauge context resumes only at step 0
+ * (PM_ERR_UNSUPPORTED otherwise: its lagged constraint needs the Phi history, which this
+ * call does not carry).  A snapshot taken with pm_particles + pm_state and restored here
+ * continues exactly as the original run.  FP64 positions: as pm_set_particles. */
+pm_status pm_set_state(pm_ctx* ctx, const void* x, const void* p, int step, int synchronised);
 
 /* Host view of the integrator (no device work): current step index, scale factor
  * and whether the momenta are synchronised with the positions (1) or half a step
@@ -348,8 +362,9 @@ pm_status pm_cell_sort(const void* x, int64_t count, int precision, int n,
  * and passing a scratch buffer is not an option.  It allocates nothing itself.
  * Limits: n^3 <= PM_CELL_SORT_STATIC_MAX_CELLS (a 64^3 mesh); larger meshes return
  * PM_ERR_INVALID_ARG.  The array (about 3 MB) is held on every GPU that loads the
- * library until the process exits.  The first call on each device looks up the
- * array's device address (cudaGetSymbolAddress); make that first call before any
+ * library until the process exits.  The first call in each CUDA context (per device;
+ * again after a context is torn down and made anew, e.g. by cudaDeviceReset) looks up
+ * the array's device address (cudaGetSymbolAddress); make that first call before any
  * stream capture.  Every call on a device shares the one array and clears the part it
  * counts in before use, so calls that overlap on the GPU (different streams or host
  * threads without ordering) race and give wrong results: serialise them. */

@@ -23,12 +23,14 @@ PM_NEWTON, PM_GR_POISSON = 0, 1
 PM_FP32_FIXED, PM_FP64 = 0, 1
 PM_GRAD_SPECTRAL, PM_GRAD_FD1 = 0, 1
 PM_IC_PAIRED, PM_IC_FIXED, PM_IC_2LPT = 1, 2, 4
+# FP64 island of the Poisson-gauge constraint used by the workloads: |n| <= DEFAULT_N_LO
+DEFAULT_N_LO = 4
 _STATUS = {0: "PM_OK", 1: "PM_ERR_INVALID_ARG", 2: "PM_ERR_CUDA", 3: "PM_ERR_WORKSPACE", 4: "PM_ERR_TIMEOUT",
            5: "PM_ERR_BOUNDS", 6: "PM_ERR_UNSUPPORTED", 7: "PM_ERR_STATE"}
 
 # every entry point declared in include/pm.h
 EXPORTS = ("pm_workspace_size", "pm_init", "pm_destroy", "pm_ic_zeldovich", "pm_step", "pm_particles",
-           "pm_set_particles", "pm_state", "pm_profile", "pm_timings", "pm_density", "pm_potential", "pm_displacement_correction", "pm_power", "pm_halo_proxy", "pm_linear_bias",
+           "pm_set_particles", "pm_set_state", "pm_state", "pm_profile", "pm_timings", "pm_density", "pm_potential", "pm_displacement_correction", "pm_power", "pm_halo_proxy", "pm_linear_bias",
            "pm_bispectrum_scratch_size", "pm_bispectrum", "pm_triangle_index", "pm_b1_gr_theory", "pm_cic_deposit", "pm_cic_interp",
            "pm_adjoint_scratch_size", "pm_loss_grad", "pm_batch_workspace_size", "pm_batch_init", "pm_batch_destroy", "pm_batch_context", "pm_batch_ic",
            "pm_batch_step", "pm_batch_state", "pm_batch_power", "pm_batch_bias", "pm_batch_set_chunk", "pm_batch_autotune",
@@ -80,6 +82,7 @@ def lib():
         "pm_step": (vp, i),
         "pm_particles": (vp, ctypes.POINTER(vp), ctypes.POINTER(vp)),
         "pm_set_particles": (vp, vp, vp),
+        "pm_set_state": (vp, vp, vp, i, i),
         "pm_state": (vp, ctypes.POINTER(i), pd, ctypes.POINTER(i)),
         "pm_profile": (vp, i),
         "pm_timings": (vp, pd, ctypes.POINTER(i64)),
@@ -195,6 +198,10 @@ def pm_particles(ctx):
 
 def pm_set_particles(ctx, x, p):
     _check(lib().pm_set_particles(ctx, _ptr(x), _ptr(p)))
+
+
+def pm_set_state(ctx, x, p, step, synchronised):
+    _check(lib().pm_set_state(ctx, _ptr(x), _ptr(p), int(step), int(bool(synchronised))))
 
 
 def pm_state(ctx):

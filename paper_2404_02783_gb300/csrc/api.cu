@@ -642,16 +642,53 @@ pm_status pm_particles(pm_ctx* c, void** x, void** p) {
     return PM_OK;
 }
 
-pm_status pm_set_particles(pm_ctx* c, const void* x, const void* p) {
-    if (!c || !x || !p) return fail(PM_ERR_INVALID_ARG, "null argument");
+}  // extern "C"
+
+namespace {
+
+// FP64 positions are box fractions: every one must be finite and in [0, 1) before it
+// reaches the CIC index arithmetic (uint32 ticks are valid by construction).  Counted on
+// the device into the context's accumulator area; synchronises the context stream.
+pm_status check_positions(pm_ctx* c, const void* x) {
+    if (!c->fp64()) return PM_OK;
+    unsigned long long* bad = (unsigned long long*)c->at(c->L.acc);
+    unsigned long long h = 0;
+    PM_CK(count_outside_box((const double*)x, 3 * c->np3, bad, c->st));
+    PM_CK(cudaMemcpyAsync(&h, bad, sizeof(h), cudaMemcpyDeviceToHost, c->st));
+    PM_CK(cudaStreamSynchronize(c->st));
+    if (h) return fail(PM_ERR_BOUNDS, std::to_string(h) + " FP64 positions are not finite or outside [0, 1) box units");
+    return PM_OK;
+}
+
+pm_status copy_state(pm_ctx* c, const void* x, const void* p, int step, bool synced) {
+    PM_TRY(check_positions(c, x));
     const size_t bytes = 3 * (size_t)c->np3 * c->sT();
     PM_CK(cudaMemcpyAsync(c->at(c->L.x), x, bytes, cudaMemcpyDeviceToDevice, c->st));
     PM_CK(cudaMemcpyAsync(c->at(c->L.p), p, bytes, cudaMemcpyDeviceToDevice, c->st));
-    c->step = 0;
-    c->synced = true;
+    c->step = step;
+    c->synced = synced;
     c->have_phi = false;
     c->rho_valid = false;
     return PM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+pm_status pm_set_particles(pm_ctx* c, const void* x, const void* p) {
+    if (!c || !x || !p) return fail(PM_ERR_INVALID_ARG, "null argument");
+    return copy_state(c, x, p, 0, true);
+}
+
+pm_status pm_set_state(pm_ctx* c, const void* x, const void* p, int step, int synchronised) {
+    if (!c || !x || !p) return fail(PM_ERR_INVALID_ARG, "null argument");
+    if (step < 0 || step > c->cfg.n_steps) return fail(PM_ERR_INVALID_ARG, "step outside 0..n_steps");
+    if ((step == 0 || step == c->cfg.n_steps) && !synchronised)
+        return fail(PM_ERR_INVALID_ARG, "the momenta are synchronised at the ends of the a-grid");
+    if (c->cfg.mode == PM_GR_POISSON && step > 0)
+        return fail(PM_ERR_UNSUPPORTED, "a Poisson-gauge run resumes only at step 0 (its Phi history is not restored)");
+    return copy_state(c, x, p, step, synchronised != 0);
 }
 
 pm_status pm_state(pm_ctx* c, int* step, double* a, int* synchronised) {

@@ -805,6 +805,26 @@ cudaError_t fill(void* a, int64_t count, int precision, double v, cudaStream_t s
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------- position check
+// Counts FP64 box-fraction positions that are not finite or lie outside [0, 1) (one
+// warp-aggregated atomic a warp).
+__global__ void k_count_outside(const double* __restrict__ x, int64_t count, unsigned long long* __restrict__ bad) {
+    unsigned long long mine = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x) {
+        const double v = x[i];
+        mine += (v >= 0.0 && v < 1.0) ? 0ull : 1ull;  // false for NaN: counted
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mine += __shfl_down_sync(0xffffffffu, mine, o);
+    if ((threadIdx.x & 31) == 0 && mine) atomicAdd(bad, mine);
+}
+cudaError_t count_outside_box(const double* x, int64_t count, unsigned long long* bad, cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(bad, 0, sizeof(unsigned long long), st);
+    if (e != cudaSuccess || count == 0) return e;
+    k_count_outside<<<grid_for(count, 256), 256, 0, st>>>(x, count, bad);
+    return cudaGetLastError();
+}
+
 // ---------------------------------------------------------------- cell keys and stable order
 __global__ void k_cell_keys(const void* __restrict__ xv, int64_t count, int precision, int logn, float inv_cell_ticks,
                             uint32_t* __restrict__ keys, uint32_t* __restrict__ counts) {
@@ -974,25 +994,61 @@ constexpr int64_t kStaticSortWords = 3 * kStaticSortCells + 4096;
 static __device__ __align__(256) uint32_t g_sort_scratch[kStaticSortWords];
 
 static std::mutex g_sort_mutex;
-static uint32_t* g_sort_ptr[128];
+struct StaticSortAddr {
+    unsigned long long ctx_id = 0;  // CUDA context the address belongs to (0: none yet)
+    uint32_t* ptr = nullptr;
+};
+static StaticSortAddr g_sort_addr[128];
 
 int64_t cell_sort_static_max_cells() { return kStaticSortCells; }
 
-// Looks up the device address of g_sort_scratch for the current device (first call
-// on each device only).
+// Unique id of the calling thread's current CUDA context (0 when there is none), from the
+// driver's cuCtxGetCurrent / cuCtxGetId reached through the runtime's entry-point query.
+static unsigned long long current_context_id() {
+    typedef int (*GetCurrent)(void**);
+    typedef int (*GetId)(void*, unsigned long long*);
+    static GetCurrent get_current = nullptr;
+    static GetId get_id = nullptr;
+    if (!get_current || !get_id) {
+        void* f1 = nullptr;
+        void* f2 = nullptr;
+        cudaDriverEntryPointQueryResult q1, q2;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault, &q1) != cudaSuccess ||
+            cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2) != cudaSuccess ||
+            q1 != cudaDriverEntryPointSuccess || q2 != cudaDriverEntryPointSuccess) {
+            cudaGetLastError();
+            return 0;
+        }
+        get_current = (GetCurrent)f1;
+        get_id = (GetId)f2;
+    }
+    void* ctx = nullptr;
+    unsigned long long id = 0;
+    if (get_current(&ctx) != 0 || !ctx || get_id(ctx, &id) != 0) return 0;
+    return id;
+}
+
+// Device address of g_sort_scratch in the current device's current context.  It is looked
+// up (cudaGetSymbolAddress) on the first call in each context and cached under the
+// context's id, so a context that is torn down and made again (cudaDeviceReset, a new
+// primary context) gets a fresh lookup instead of a stale address.
 static cudaError_t static_sort_scratch(uint32_t** out) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= 128) return cudaErrorInvalidDevice;
     std::lock_guard<std::mutex> lock(g_sort_mutex);
-    if (!g_sort_ptr[dev]) {
+    StaticSortAddr& a = g_sort_addr[dev];
+    unsigned long long id = current_context_id();
+    if (id == 0 || id != a.ctx_id || !a.ptr) {
         void* p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_sort_scratch);
+        e = cudaGetSymbolAddress(&p, g_sort_scratch);  // makes the runtime's context current if needed
         if (e != cudaSuccess) return e;
-        g_sort_ptr[dev] = (uint32_t*)p;
+        if (id == 0) id = current_context_id();
+        a.ctx_id = id;
+        a.ptr = (uint32_t*)p;
     }
-    *out = g_sort_ptr[dev];
+    *out = a.ptr;
     return cudaSuccess;
 }
 

@@ -1,0 +1,130 @@
+"""FP32 parity at the configurations the headline numbers are quoted on.
+
+* The combined-run configuration's FP64 check case: 64^3 particles on a 64^3 mesh,
+  L = 5000 Mpc/h, the same seed, Zel'dovich ICs at z = 50, 100 KDK steps to z = 0; P(k) in
+  64 log bins on [k_f, k_Ny] and B(k) for every triangle of the 24 linear bins of width
+  0.05/24 h/Mpc that lie below the 64^3 Nyquist frequency (Sec. 4.1 Eq. powerspectrum, Sec. 4.2
+  Eq. bispectre), the GPU's FP32 run against the oracle's FP64 run.
+* One step of the timed workload itself (512^3 particles on a 512^3 mesh, L = 5000 Mpc/h):
+  the kick of sampled particles against an oracle force evaluation of the same positions.
+
+Each B(k) triangle is a sum of products delta_1 delta_2 delta_3 over its configurations; its
+error is bounded against the same sum of |delta_1 delta_2 delta_3| (the scale any floating
+point evaluation of the sum is accurate to), which the oracle evaluates with the same estimator
+on the spectrum of moduli.
+"""
+import numpy as np
+import pytest
+
+import inputs
+from oracle import cic, gravity, ic, pm as opm, stats
+from oracle.cosmology import Cosmology
+from tests.gpu_util import lib, to_dev, to_host, torch
+
+pytestmark = pytest.mark.gpu
+
+A_I, A_F = 1.0 / 51.0, 1.0
+
+
+def _bk_abs_scale(delta, box, edges, m):
+    """Per triangle (V^2/N^9) sum |d1 d2 d3| / N_tri: the estimator on the moduli |delta_n|."""
+    n = delta.shape[0]
+    mod = np.fft.irfftn(np.abs(np.fft.rfftn(delta)), s=(n, n, n), axes=(0, 1, 2))
+    return stats.bispectrum(mod, box, edges, M=m)[1]
+
+
+@pytest.mark.slow
+def test_combined_run_check_case_fp32_matches_fp64_oracle():
+    pm = lib()
+    n, box, steps, seed = 64, 5000.0, 100, 1
+    run = pm.PMRun(pm.make_config(n, n, box, A_I, A_F, steps))
+    run.ic(seed=seed)
+    run.step(steps)
+    assert run.state()[0] == steps and run.state()[2]
+    e64 = stats.log_edges(64, 1.0, n / 2.0)
+    kg, pg, ng = run.power(e64)
+    kf = 2.0 * np.pi / box
+    e24 = np.linspace(0.0, 0.05 / kf, 25)
+    eb = e24[: int(np.count_nonzero(e24 <= n / 2.0))]  # the bins below the 64^3 Nyquist frequency
+    assert len(eb) - 1 == 19
+    m = 128  # alias-free for |n| < 32: m > 3 max|n_i|
+    bg, cg = run.bispectrum(eb, m)
+    torch.cuda.synchronize()
+
+    c = Cosmology()
+    x0, p0 = ic.zeldovich(c, n, box, A_I, seed=seed, fixed=True)
+    ref = opm.PMRun(c, n, box, A_I, A_F, steps, x0, p0)
+    ref.step(steps)
+    delta_o = cic.density_contrast(ref.x, n)
+    ko, po, no = stats.power_spectrum(delta_o, box, e64)
+    tri, bo, co = stats.bispectrum(delta_o, box, eb, M=m)
+    scale = _bk_abs_scale(delta_o, box, eb, m)
+
+    np.testing.assert_array_equal(ng, no)
+    ok = no > 0
+    assert np.count_nonzero(ok) > 40
+    np.testing.assert_allclose(kg[ok], ko[ok], rtol=1e-12)
+    assert np.max(np.abs(pg[ok] / po[ok] - 1.0)) < 1e-3
+
+    np.testing.assert_array_equal(cg, co)
+    has = co > 0
+    assert np.count_nonzero(has) > 700
+    assert np.array_equal(np.isnan(bg), ~has)
+    err = np.abs(bg[has] - bo[has])
+    assert np.all(err <= 1e-3 * scale[has])
+    # and relative to B itself on every triangle whose sum does not cancel below 1% of its scale
+    big = np.abs(bo[has]) > 1e-2 * scale[has]
+    assert np.count_nonzero(big) > 0.5 * np.count_nonzero(has)
+    assert np.max(err[big] / np.abs(bo[has][big])) < 1e-3
+
+
+def _mem_available_gb():
+    avail = 0.0
+    try:
+        with open("/proc/meminfo") as f:
+            for line in f:
+                if line.startswith("MemAvailable:"):
+                    avail = int(line.split()[1]) / 2**20
+    except OSError:
+        return 0.0
+    return avail
+
+
+@pytest.mark.slow
+def test_one_step_kick_at_the_timed_size_matches_an_oracle_force_evaluation():
+    # the timed workload's launch path (512^3 particles on 512^3 cells, FP32, row-sweep update):
+    # from seeded lattice-order positions at rest, one step kicks each particle by
+    # K(a_0, a_1/2) g(x_0); the oracle evaluates g = -grad phi by its own FP64 deposit, FFT,
+    # Green's function, gradient and CIC gather at 64 sampled particles
+    if _mem_available_gb() < 64:
+        pytest.skip("the FP64 oracle force of a 512^3 mesh needs about 30 GB of host memory")
+    pm = lib()
+    n, box, steps = 512, 5000.0, 100
+    x = inputs.lattice_order_ticks(61, n, 1.5, tail_fraction=0.01)
+    run = pm.PMRun(pm.make_config(n, n, box, A_I, A_F, steps))
+    xd = to_dev(x)
+    pd = torch.zeros((3, n**3), dtype=torch.float32, device="cuda")
+    pm.pm_set_particles(run.ctx, xd, pd)
+    run.step(1)
+    _, p = run.particles()
+    ids = np.concatenate([[0, n**3 - 1], inputs.rng(62).integers(0, n**3, size=62)])
+    pg = to_host(p[:, torch.from_numpy(ids).cuda()]).astype(np.float64)
+    del xd, pd, p, run
+    torch.cuda.empty_cache()
+
+    c = Cosmology()
+    a0, a1 = A_I, A_I + (A_F - A_I) / steps
+    K = c.kick_factor(a0, 0.5 * (a0 + a1))
+    delta = cic.density_contrast(x, n)
+    phi_k = gravity.newton_potential_k(np.fft.rfftn(delta), n, box, c.omega_m)
+    del delta
+    xs = x[:, ids]
+    g_mesh = gravity.gradient_force(phi_k, n, box)
+    del phi_k
+    g = np.stack([cic.interpolate(g_mesh[j], xs) for j in range(3)])
+    del g_mesh
+    want = K * g
+    assert np.max(np.abs(want)) > 0
+    # the FP32 force chain (deposit, five FFT passes, gather) against FP64: ~1e-6 of the largest kick
+    assert np.linalg.norm(pg - want) < 1e-5 * np.linalg.norm(want)
+    assert np.max(np.abs(pg - want)) < 1e-5 * np.max(np.abs(want))

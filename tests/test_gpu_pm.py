@@ -229,3 +229,67 @@ def test_first_order_gradient_is_refused_by_batches_and_the_loss_gradient():
     with pytest.raises(pm.PMError) as e:
         run.loss_grad(w, torch.zeros((64, 64, 64), dtype=torch.float32, device="cuda"))
     assert e.value.status == 6
+
+
+def test_set_state_resumes_a_run_where_it_was_saved():
+    # a snapshot (x, p, step, synchronised) taken between steps and restored into a fresh
+    # context continues as the original run: the same integrator position and the same
+    # particles after the remaining steps (up to the summation order of the deposit atomics)
+    pm = lib()
+    np_side = nmesh = 64
+    box, steps, k = 1000.0, 40, 25
+    runs = [pm.PMRun(pm.make_config(np_side, nmesh, box, 1.0 / 51.0, 1.0, steps)) for _ in range(2)]
+    a, b = runs
+    a.ic(seed=9)
+    a.step(k)
+    st = a.state()
+    assert st[0] == k and not st[2]
+    x, p = (t.clone() for t in a.particles())
+    pm.pm_set_state(b.ctx, x, p, st[0], st[2])
+    assert b.state() == st
+    a.step(steps - k)
+    b.step(steps - k)
+    assert a.state() == b.state() and a.state()[2]
+    xa, pa = _host_particles(a)
+    xb, pb = _host_particles(b)
+    da = min_image(positions_box_units(xa) - positions_box_units(x.cpu().numpy().view(np.uint32)))
+    db = min_image(positions_box_units(xb) - positions_box_units(x.cpu().numpy().view(np.uint32)))
+    assert rel_l2(db, da) < 1e-5
+    assert rel_l2(pb, pa) < 1e-5
+
+
+def test_set_state_checks_its_arguments():
+    pm = lib()
+    run = _run(pm, 16, 16, 100.0, 0.5, 1.0, 4, FP32)
+    run.ic(seed=3)
+    x, p = (t.clone() for t in run.particles())
+    for step, sync in ((5, 1), (-1, 1), (0, 0), (4, 0)):
+        with pytest.raises(pm.PMError) as e:
+            pm.pm_set_state(run.ctx, x, p, step, sync)
+        assert e.value.status == 1
+    gr = _run(pm, 16, 16, 20000.0, 0.5, 1.0, 4, FP32, mode=1)
+    with pytest.raises(pm.PMError) as e:
+        pm.pm_set_state(gr.ctx, x, p, 2, 0)
+    assert e.value.status == 6
+    pm.pm_set_state(gr.ctx, x, p, 0, 1)
+
+
+@pytest.mark.parametrize("bad", [1.0, 1.5, -1e-3, float("nan"), float("inf")])
+def test_fp64_positions_outside_the_box_are_refused(bad):
+    # FP64 positions are box fractions in [0, 1): anything else is outside the mesh's bounds
+    pm = lib()
+    run = _run(pm, 16, 16, 100.0, 0.5, 1.0, 4, FP64)
+    run.ic(seed=3)
+    run.step(1)
+    x, p = (t.clone() for t in run.particles())
+    x[1, 77] = bad
+    with pytest.raises(pm.PMError) as e:
+        pm.pm_set_particles(run.ctx, x, p)
+    assert e.value.status == 5
+    with pytest.raises(pm.PMError) as e:
+        pm.pm_set_state(run.ctx, x, p, 2, 0)
+    assert e.value.status == 5
+    assert run.state()[0] == 1  # nothing was taken over
+    x[1, 77] = 0.25
+    pm.pm_set_particles(run.ctx, x, p)
+    assert run.state()[0] == 0

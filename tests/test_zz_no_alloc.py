@@ -4,7 +4,7 @@ Some hosts hand all GPU memory to their own fixed pool, or drive the library fro
 plain C / Fortran with no device allocator; they cannot provide the scratch buffer
 pm_cell_sort asks for.  pm_cell_sort_static keeps that scratch in a fixed array
 inside the library instead.  This test checks, through the C ABI, that it returns
-exactly what pm_cell_sort returns, on two calls in a row with different sizes (so
+exactly what pm_cell_sort returns (and what the oracle's cell keys and stable order are), on two calls in a row with different sizes (so
 stale contents of the shared array would show), and that it refuses meshes above
 its 64^3-cell limit.  It lives in its own file so that a run stopping at the first
 failure has already run every other test.
@@ -13,6 +13,7 @@ import numpy as np
 import pytest
 
 import inputs
+from oracle import cic
 from tests.gpu_util import lib, to_dev, to_host, torch
 
 pytestmark = pytest.mark.gpu
@@ -40,6 +41,9 @@ def test_static_cell_sort_matches_scratch_version_on_consecutive_calls():
         (ka, oa), (kb, ob) = _both(pm, xs, count, prec, n)
         np.testing.assert_array_equal(kb, ka)
         np.testing.assert_array_equal(ob, oa)
+        # and both equal the oracle's cell keys and stable order, bit for bit
+        np.testing.assert_array_equal(kb.astype(np.int64), cic.cell_keys(xs, n))
+        np.testing.assert_array_equal(ob.astype(np.int64), cic.cell_order(xs, n))
 
 
 def test_static_cell_sort_refuses_meshes_above_its_limit():
