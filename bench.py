@@ -430,10 +430,23 @@ def adjoint(pm, torch, args):
 
     t_fwd = timed(forward)
     t_grad = timed(lambda: run.loss_grad(w, target, checkpoint_every=every))
+    # the general path: record the run, then the reverse sweep with cotangents on the final
+    # density and displacements (what run_fields' backward hands to pm_adjoint_run)
+    cot_d = torch.randn((n,) * 3, generator=g, device="cuda", dtype=torch.float32)
+    cot_x = torch.randn((3, np_side**3), generator=g, device="cuda", dtype=torch.float32)
+
+    def record_and_adjoint():
+        run.record(w, every)
+        return run.adjoint(d_delta=cot_d, d_disp=cot_x)
+
+    t_vjp = timed(record_and_adjoint)
     return {"workload": f"{np_side}^3 particles, {n}^3 mesh, L=2000 Mpc/h, {steps} FP32 steps, "
-                        f"checkpoints every {every} steps; gradient of the mean-square density loss "
-                        "with respect to the white-noise field",
+                        f"checkpoints every {every} steps; gradient with respect to the white-noise field",
             "forward_ms": 1e3 * t_fwd, "loss_grad_ms": 1e3 * t_grad, "cost_ratio": t_grad / t_fwd,
+            "record_and_adjoint_ms": 1e3 * t_vjp, "record_and_adjoint_cost_ratio": t_vjp / t_fwd,
+            "what": "loss_grad: mean-square density loss (forward with checkpoints + reverse sweep); "
+                    "record_and_adjoint: pm_adjoint_record + pm_adjoint_run with cotangents on the final "
+                    "density and displacements (any loss)",
             "value": np_side**3 * steps / t_grad, "unit": "particle-steps/s (forward + reverse)"}
 
 

@@ -18,7 +18,8 @@
  *   pm_displacement_correction Eqs. xiGR and combined
  *   pm_power / pm_bispectrum   Eqs. powerspectrum / bispectre on the CIC counting density
  *   pm_linear_bias             Eq. b1 on a halo proxy (pm_halo_proxy), Eq. bgr (pm_b1_gr_theory)
- *   pm_loss_grad               gradient of a field-level loss through the whole run
+ *   pm_adjoint_record / _run   gradient of any loss of the final density and displacements
+ *                              with respect to the initial white noise (pm_loss_grad: the MSE)
  *   pm_batch_*                 many realisations stepped together from one CUDA graph
  *
  * Conventions shared by every entry point
@@ -43,8 +44,8 @@
  * pm_cell_sort_static.  Host output arrays are caller-owned too.
  * Streams: calls are asynchronous on the stream given at pm_init (or per call for
  * the stateless operators) except pm_power, pm_bispectrum and pm_linear_bias, which
- * synchronise that stream before returning host results, and pm_loss_grad, which also
- * runs on a second stream of the context's own and synchronises both.  Host-only calls
+ * synchronise that stream before returning host results, and pm_adjoint_run /
+ * pm_loss_grad, which also run on a second stream of the context's own and synchronise both.  Host-only calls
  * (pm_triangle_index, pm_b1_gr_theory, the *_size queries) touch no device.
  * Errors: every call returns a pm_status; pm_last_error() gives a static,
  * thread-local message for the last failure.  A CUDA error inside a call is
@@ -166,6 +167,12 @@ pm_status pm_set_particles(pm_ctx* ctx, const void* x, const void* p);
  * continues exactly as the original run.  FP64 positions: as pm_set_particles. */
 pm_status pm_set_state(pm_ctx* ctx, const void* x, const void* p, int step, int synchronised);
 
+/* Lagrangian displacement d = x - q of every particle (minimum image, Mpc/h), q its
+ * lattice node, written to disp[3][np^3] (float for PM_FP32_FIXED, double for PM_FP64).
+ * The position output of a run whose gradient pm_adjoint_run takes (Sec. 2: the GR
+ * displacement field is a difference of such displacements, Eq. xiGR). */
+pm_status pm_displacement(pm_ctx* ctx, void* disp);
+
 /* Host view of the integrator (no device work): current step index, scale factor
  * and whether the momenta are synchronised with the positions (1) or half a step
  * behind (0). */
@@ -265,26 +272,39 @@ pm_status pm_bispectrum(pm_ctx* ctx, const void* field, int nbins, const double*
  * k3 = 4 k_f.  Indices out of order or range: PM_ERR_INVALID_ARG. */
 pm_status pm_triangle_index(int nbins, int i, int j, int l, int64_t* index);
 
-/* ------------------------------------------------------- gradient of a field loss
+/* ------------------------------------------------------- gradients through the run
  * Field-level fits (the paper's GR displacement and bias are field-level quantities,
- * Secs. 2 and 5) need the gradient of a loss on the final density with respect to the
- * initial phases.  L(w) = mean_c (delta(c) - delta_t(c))^2, with delta the CIC counting
- * density contrast of the particles after the full a-grid (cfg.n_steps steps) started
- * from the Zel'dovich ICs of the white-noise field w (device, np^3, as pm_ic_zeldovich
- * with white_noise) and delta_t a device target mesh n^3.  pm_loss_grad returns L and
- * writes dL/dw (device, np^3) by a reverse sweep: (x, p) checkpoints every
- * checkpoint_every steps; the forward run keeps the positions and force meshes of its
- * last two segments, every earlier segment is re-run from its checkpoint (on a second
- * CUDA stream the context creates on first use, overlapping the reverse sweep of the
- * segment after it); then the transposed drift, kick (direct CIC-gradient term plus the
- * transposed deposit -> Green -> gradient chain) and Zel'dovich map are applied.  CIC
- * weight derivatives are taken on the side of the forward floor().  FP32 Newtonian
- * contexts only; scratch: pm_adjoint_scratch_size bytes (256-byte aligned): the
- * checkpoints, two segment records of checkpoint_every steps and the re-runs' density,
- * spectra and positions.  Leaves the context's particles at the last step of the forward
- * run, before its closing half kick (run pm_ic_zeldovich before stepping again).
- * Synchronises both streams before returning, also on error. */
+ * Secs. 2 and 5) need gradients of a loss on the final state with respect to the initial
+ * phases.  The forward map is w -> Zel'dovich ICs of the white-noise field w (device, np^3,
+ * as pm_ic_zeldovich with white_noise) -> cfg.n_steps KDK steps -> (delta, d): delta the
+ * CIC counting density contrast of the final particles (n^3 mesh, pm_density) and d their
+ * displacements (pm_displacement).  The closing half kick changes only p, which neither
+ * output sees, so the recorded run leaves it out.
+ *
+ * pm_adjoint_record runs that forward map keeping (x, p) checkpoints every
+ * checkpoint_every steps in `scratch` (pm_adjoint_scratch_size bytes, 256-byte aligned)
+ * and the positions and force meshes of the last two segments; it leaves the context at
+ * step n_steps before the closing kick, with the final particles in place (read delta and
+ * d from there).  pm_adjoint_run then takes the cotangents d_delta = dL/d delta (device
+ * float n^3, or NULL) and d_disp = dL/d d (device float [3][np^3], per Mpc/h, or NULL; not
+ * both NULL) of any loss L and writes dL/dw (device float np^3) by the reverse sweep:
+ * every earlier segment is re-run from its checkpoint on a second CUDA stream the context
+ * creates on first use (overlapping the reverse sweep of the segment after it), then the
+ * transposed drift, kick (direct CIC-gradient term plus the transposed deposit -> Green
+ * -> gradient chain) and Zel'dovich map are applied; CIC weight derivatives are taken on
+ * the side of the forward floor().  The re-runs consume the checkpoints: one
+ * pm_adjoint_run per pm_adjoint_record (PM_ERR_STATE otherwise, or when the context has
+ * been stepped or reset in between).  The scratch must stay untouched between the two
+ * calls.  pm_adjoint_run synchronises both streams before returning, also on error.
+ *
+ * pm_loss_grad is both calls for L(w) = mean_c (delta(c) - delta_t(c))^2 with a device
+ * target mesh delta_t: it returns L and writes dL/dw.
+ *
+ * FP32 Newtonian contexts with the spectral gradient only (PM_ERR_UNSUPPORTED otherwise). */
 pm_status pm_adjoint_scratch_size(const pm_ctx* ctx, int checkpoint_every, size_t* bytes);
+pm_status pm_adjoint_record(pm_ctx* ctx, const void* white_noise, int checkpoint_every, void* scratch,
+                            size_t scratch_bytes);
+pm_status pm_adjoint_run(pm_ctx* ctx, const void* d_delta, const void* d_disp, void* grad_w);
 pm_status pm_loss_grad(pm_ctx* ctx, const void* white_noise, const void* delta_target, int checkpoint_every,
                        void* scratch, size_t scratch_bytes, double* loss, void* grad_w);
 
@@ -371,6 +391,12 @@ pm_status pm_cell_sort(const void* x, int64_t count, int precision, int n,
 #define PM_CELL_SORT_STATIC_MAX_CELLS 262144
 pm_status pm_cell_sort_static(const void* x, int64_t count, int precision, int n,
                               uint32_t* keys_out, uint32_t* order_out, void* stream);
+
+/* out[i] = a[i] / d[i] (device double arrays of count) by the FP64 divide of the spectral
+ * operators (Green's function 1/k^2, the Poisson-gauge constraint's denominator): the
+ * Newton-Raphson iteration for 1/d from the FP32 reciprocal, two steps, times a.  d must
+ * be in the FP32 normal range.  Exposed so that it can be compared with the division. */
+pm_status pm_div_mode_check(const double* a, const double* d, int64_t count, double* out, void* stream);
 
 /* 3D real-to-complex FFT of real[n][n][n] into spec (layout above), unnormalised. */
 pm_status pm_fft_r2c(const void* real, void* spec, int n, int precision, void* stream);

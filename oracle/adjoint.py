@@ -8,7 +8,8 @@ The differentiable workload fits the initial white noise w of a run at field lev
     L(w) = (1/N^3) sum_c (delta(c) - delta_t(c))^2,
 
 with delta the CIC counting density contrast of the final particles and delta_t a
-target mesh.  The forward map is the Zel'dovich IC of ``ic`` (white-noise path)
+target mesh; ``vjp`` takes the cotangents of any loss of the final density and of the
+final displacements d = x - q instead.  The forward map is the Zel'dovich IC of ``ic`` (white-noise path)
 followed by the kick-drift-kick steps of ``pm``, written out here as a list of kick
 and drift operations so that the reverse sweep can walk it backwards:
 
@@ -142,13 +143,36 @@ def loss(cosmo, n_p, n_mesh, box, a_i, a_f, n_steps, w, delta_t):
     return float(np.mean((cic.density_contrast(u, n_mesh) - delta_t)**2))
 
 
-def loss_and_grad(cosmo, n_p, n_mesh, box, a_i, a_f, n_steps, w, delta_t):
-    """(L, dL/dw) with dL/dw of shape (n_p, n_p, n_p)."""
+def lattice_fractions(n_p):
+    """Lagrangian lattice q in box units, particle order (3, n_p^3)."""
+    i = np.arange(n_p, dtype=np.float64) / n_p
+    X, Y, Z = np.meshgrid(i, i, i, indexing="ij")
+    return np.stack([X.ravel(), Y.ravel(), Z.ravel()])
+
+
+def displacement(u, n_p, box):
+    """Final displacement d = x - q in Mpc/h, minimum image (3, n_p^3)."""
+    d = u - lattice_fractions(n_p)
+    return (d - np.rint(d)) * box
+
+
+def vjp(cosmo, n_p, n_mesh, box, a_i, a_f, n_steps, w, lam_delta=None, lam_disp=None):
+    """dL/dw for any loss L(delta_final, d_final) given its cotangents lam_delta = dL/d delta
+    (n_mesh^3 mesh) and lam_disp = dL/d d ((3, n_p^3), per Mpc/h), by the reverse sweep of
+    the recorded forward run.  Since d = (u - q) L (minimum image), dL/du = L lam_disp; the
+    density adds m sum_c lam_delta(c) dW(u, c)/du."""
     u, p, ops, mass = forward(cosmo, n_p, n_mesh, box, a_i, a_f, n_steps, w)
-    delta = cic.density_contrast(u, n_mesh)
-    L = float(np.mean((delta - delta_t)**2))
-    lam_rho = 2.0 * (delta - delta_t) / n_mesh**3
-    lam_u = mass * _grad_gather(lam_rho, u, n_mesh)
+    lam_u = np.zeros_like(u)
+    if lam_delta is not None:
+        lam_u += mass * _grad_gather(np.asarray(lam_delta, dtype=np.float64), u, n_mesh)
+    if lam_disp is not None:
+        lam_u += box * np.asarray(lam_disp, dtype=np.float64).reshape(3, -1)
+    return _reverse(cosmo, n_p, n_mesh, box, a_i, ops, mass, lam_u)
+
+
+def _reverse(cosmo, n_p, n_mesh, box, a_i, ops, mass, lam_u):
+    """Walk the recorded kicks and drifts backwards from (lam_u, lam_p = 0), then apply the
+    transposed Zel'dovich map: returns dL/dw (n_p, n_p, n_p)."""
     lam_p = np.zeros_like(lam_u)
     for op in reversed(ops):
         if op[0] == "drift":
@@ -166,4 +190,14 @@ def loss_and_grad(cosmo, n_p, n_mesh, box, a_i, a_f, n_steps, w, delta_t):
     grad = np.zeros((n_p, n_p, n_p))
     for j in range(3):
         grad -= _za_operator(s[j].reshape(n_p, n_p, n_p), n_p, box, cosmo, j)
-    return L, grad
+    return grad
+
+
+def loss_and_grad(cosmo, n_p, n_mesh, box, a_i, a_f, n_steps, w, delta_t):
+    """(L, dL/dw) with dL/dw of shape (n_p, n_p, n_p)."""
+    u, p, ops, mass = forward(cosmo, n_p, n_mesh, box, a_i, a_f, n_steps, w)
+    delta = cic.density_contrast(u, n_mesh)
+    L = float(np.mean((delta - delta_t)**2))
+    lam_rho = 2.0 * (delta - delta_t) / n_mesh**3
+    lam_u = mass * _grad_gather(lam_rho, u, n_mesh)
+    return L, _reverse(cosmo, n_p, n_mesh, box, a_i, ops, mass, lam_u)

@@ -32,9 +32,9 @@ _STATUS = {0: "PM_OK", 1: "PM_ERR_INVALID_ARG", 2: "PM_ERR_CUDA", 3: "PM_ERR_WOR
 EXPORTS = ("pm_workspace_size", "pm_init", "pm_destroy", "pm_ic_zeldovich", "pm_step", "pm_particles",
            "pm_set_particles", "pm_set_state", "pm_state", "pm_profile", "pm_timings", "pm_density", "pm_potential", "pm_displacement_correction", "pm_power", "pm_halo_proxy", "pm_linear_bias",
            "pm_bispectrum_scratch_size", "pm_bispectrum", "pm_triangle_index", "pm_b1_gr_theory", "pm_cic_deposit", "pm_cic_interp",
-           "pm_adjoint_scratch_size", "pm_loss_grad", "pm_batch_workspace_size", "pm_batch_init", "pm_batch_destroy", "pm_batch_context", "pm_batch_ic",
+           "pm_adjoint_scratch_size", "pm_adjoint_record", "pm_adjoint_run", "pm_loss_grad", "pm_displacement", "pm_batch_workspace_size", "pm_batch_init", "pm_batch_destroy", "pm_batch_context", "pm_batch_ic",
            "pm_batch_step", "pm_batch_state", "pm_batch_power", "pm_batch_bias", "pm_batch_set_chunk", "pm_batch_autotune",
-           "pm_cell_sort_scratch_size", "pm_cell_sort", "pm_cell_sort_static", "pm_fft_r2c", "pm_fft_c2r", "pm_version", "pm_last_error")
+           "pm_cell_sort_scratch_size", "pm_cell_sort", "pm_cell_sort_static", "pm_div_mode_check", "pm_fft_r2c", "pm_fft_c2r", "pm_version", "pm_last_error")
 
 
 class PMError(RuntimeError):
@@ -98,6 +98,9 @@ def lib():
         "pm_b1_gr_theory": (cfgp, d, d, pd),
         "pm_adjoint_scratch_size": (vp, i, ctypes.POINTER(sz)),
         "pm_loss_grad": (vp, vp, vp, i, vp, sz, pd, vp),
+        "pm_adjoint_record": (vp, vp, i, vp, sz),
+        "pm_adjoint_run": (vp, vp, vp, vp),
+        "pm_displacement": (vp, vp),
         "pm_batch_workspace_size": (cfgp, i, ctypes.POINTER(sz)),
         "pm_batch_init": (cfgp, i, pd, vp, sz, vp, ctypes.POINTER(vp)),
         "pm_batch_destroy": (vp,),
@@ -114,6 +117,7 @@ def lib():
         "pm_cell_sort_scratch_size": (i64, i, ctypes.POINTER(sz)),
         "pm_cell_sort": (vp, i64, i, i, vp, vp, vp, sz, vp),
         "pm_cell_sort_static": (vp, i64, i, i, vp, vp, vp),
+        "pm_div_mode_check": (vp, vp, i64, vp, vp),
         "pm_fft_r2c": (vp, vp, i, i, vp),
         "pm_fft_c2r": (vp, vp, i, i, vp),
     }
@@ -229,6 +233,25 @@ def pm_density(ctx, out):
     _check(lib().pm_density(ctx, _ptr(out)))
 
 
+def pm_displacement(ctx, out):
+    _check(lib().pm_displacement(ctx, _ptr(out)))
+
+
+def pm_adjoint_scratch_size(ctx, checkpoint_every):
+    out = ctypes.c_size_t()
+    _check(lib().pm_adjoint_scratch_size(ctx, int(checkpoint_every), ctypes.byref(out)))
+    return out.value
+
+
+def pm_adjoint_record(ctx, white_noise, checkpoint_every, scratch):
+    _check(lib().pm_adjoint_record(ctx, _ptr(white_noise), int(checkpoint_every), _ptr(scratch),
+                                   scratch.numel() * scratch.element_size()))
+
+
+def pm_adjoint_run(ctx, d_delta, d_disp, grad_w):
+    _check(lib().pm_adjoint_run(ctx, _ptr(d_delta), _ptr(d_disp), _ptr(grad_w)))
+
+
 def pm_potential(ctx, out):
     _check(lib().pm_potential(ctx, _ptr(out)))
 
@@ -330,6 +353,10 @@ def pm_cell_sort_static(x, count, precision, n, keys, order, stream=None):
                                      _stream(stream)))
 
 
+def pm_div_mode_check(a, d, out, stream=None):
+    _check(lib().pm_div_mode_check(_ptr(a), _ptr(d), int(a.numel()), _ptr(out), _stream(stream)))
+
+
 def pm_fft_r2c(real, spec, n, precision, stream=None):
     _check(lib().pm_fft_r2c(_ptr(real), _ptr(spec), int(n), precision, _stream(stream)))
 
@@ -411,45 +438,81 @@ class PMRun:
     def state(self):
         return pm_state(self.ctx)
 
+    def _adjoint_scratch(self, checkpoint_every):
+        """Device scratch of the reverse sweep for this interval (kept for reuse)."""
+        import torch
+        nbytes = pm_adjoint_scratch_size(self.ctx, checkpoint_every)
+        buf = getattr(self, "_adj_buf", None)
+        if buf is None or buf.numel() < nbytes + 256:
+            buf = torch.empty(nbytes + 256, dtype=torch.uint8, device=self.device)
+            self._adj_buf = buf
+        off = (-buf.data_ptr()) % 256
+        return buf[off:off + nbytes]
+
     def loss_grad(self, white_noise, target, checkpoint_every=10):
         """(L, dL/dw) of L = mean((delta_final - target)^2) for ICs from white_noise (pm_loss_grad)."""
         import torch
-        out = ctypes.c_size_t()
-        _check(lib().pm_adjoint_scratch_size(self.ctx, int(checkpoint_every), ctypes.byref(out)))
-        scratch = torch.empty(out.value + 256, dtype=torch.uint8, device=self.device)
-        off = (-scratch.data_ptr()) % 256
+        scratch = self._adjoint_scratch(checkpoint_every)
         grad = torch.empty_like(white_noise)
         loss = ctypes.c_double()
         _check(lib().pm_loss_grad(self.ctx, _ptr(white_noise), _ptr(target), int(checkpoint_every),
-                                  _ptr(scratch[off:]), out.value, ctypes.byref(loss), _ptr(grad)))
+                                  _ptr(scratch), scratch.numel(), ctypes.byref(loss), _ptr(grad)))
         return loss.value, grad
+
+    def record(self, white_noise, checkpoint_every=10):
+        """pm_adjoint_record: the run from white_noise with its checkpoints kept for pm_adjoint_run."""
+        self._adj_scratch = self._adjoint_scratch(checkpoint_every)
+        pm_adjoint_record(self.ctx, white_noise, checkpoint_every, self._adj_scratch)
+
+    def adjoint(self, d_delta=None, d_disp=None):
+        """pm_adjoint_run: dL/dw from the cotangents of the recorded run's final density and displacements."""
+        import torch
+        grad = torch.empty((self.cfg.np,) * 3, dtype=torch.float32, device=self.device)
+        pm_adjoint_run(self.ctx, None if d_delta is None else d_delta.contiguous(),
+                       None if d_disp is None else d_disp.contiguous(), grad)
+        return grad
+
+    def displacement(self):
+        """Lagrangian displacements x - q (minimum image, Mpc/h), shape (3, np^3)."""
+        import torch
+        out = torch.empty((3, self.count), dtype=self.rdtype, device=self.device)
+        pm_displacement(self.ctx, out)
+        return out
 
     @property
     def kf(self):
         return 2 * math.pi / self.cfg.box
 
 
-def field_loss(run, white_noise, target, checkpoint_every=10):
-    """Differentiable L(w) = mean((delta_final(w) - target)^2) through the whole PM run.
-
-    A torch.autograd.Function: the forward pass runs pm_loss_grad (loss and gradient
-    in one reverse sweep on the GPU) and the backward pass scales the stored gradient.
-    """
+def run_fields(run, white_noise, checkpoint_every=10):
+    """(delta_final, disp_final) of the whole PM run as differentiable functions of the
+    white-noise field w: the forward pass is pm_adjoint_record (the run with checkpoints),
+    the backward pass hands the incoming gradients of both outputs to pm_adjoint_run (one
+    reverse sweep on the GPU).  Any torch loss of the final density (shape (n, n, n)) and
+    displacements (Mpc/h, shape (3, np^3)) composes with it; one backward per forward."""
     import torch
 
-    class _FieldLoss(torch.autograd.Function):
+    class _RunFields(torch.autograd.Function):
         @staticmethod
         def forward(ctx, w):
-            loss, grad = run.loss_grad(w.detach().contiguous(), target, checkpoint_every)
-            ctx.save_for_backward(grad)
-            return torch.tensor(loss, dtype=torch.float64, device=w.device)
+            ctx.set_materialize_grads(False)
+            run.record(w.detach().contiguous(), checkpoint_every)
+            return run.density(), run.displacement()
 
         @staticmethod
-        def backward(ctx, gout):
-            (grad,) = ctx.saved_tensors
-            return (gout.to(grad.dtype) * grad,)
+        def backward(ctx, g_delta, g_disp):
+            if g_delta is None and g_disp is None:
+                return None
+            f32 = lambda g: None if g is None else g.to(torch.float32)
+            return run.adjoint(f32(g_delta), f32(g_disp))
 
-    return _FieldLoss.apply(white_noise)
+    return _RunFields.apply(white_noise)
+
+
+def field_loss(run, white_noise, target, checkpoint_every=10):
+    """L(w) = mean((delta_final(w) - target)^2) through the whole PM run, differentiable in w."""
+    delta, _ = run_fields(run, white_noise, checkpoint_every)
+    return ((delta.to(target.dtype) - target)**2).mean()
 
 
 class PMBatch:

@@ -156,7 +156,21 @@ struct pm_ctx {
     }
     // second stream of the gradient's overlapped forward re-runs (created on first use)
     cudaStream_t st2 = nullptr;
+    // the recorded forward run of the reverse sweep (pm_adjoint_record -> pm_adjoint_run)
+    struct AdjSession {
+        void* scratch = nullptr;
+        size_t bytes = 0;
+        int C = 0;
+        std::vector<cudaEvent_t> ev_ckpt, ev_rerun, ev_rev;
+        bool recorded = false;
+        ~AdjSession() {
+            for (auto* v : {&ev_ckpt, &ev_rerun, &ev_rev})
+                for (auto e : *v) cudaEventDestroy(e);
+        }
+    };
+    AdjSession* adj = nullptr;
     ~pm_ctx() {
+        delete adj;
         if (st2) cudaStreamDestroy(st2);
         for (auto& r : recs) {
             cudaEventDestroy(r.a);
@@ -662,6 +676,7 @@ pm_status check_positions(pm_ctx* c, const void* x) {
 
 pm_status copy_state(pm_ctx* c, const void* x, const void* p, int step, bool synced) {
     PM_TRY(check_positions(c, x));
+    if (c->adj) c->adj->recorded = false;
     const size_t bytes = 3 * (size_t)c->np3 * c->sT();
     PM_CK(cudaMemcpyAsync(c->at(c->L.x), x, bytes, cudaMemcpyDeviceToDevice, c->st));
     PM_CK(cudaMemcpyAsync(c->at(c->L.p), p, bytes, cudaMemcpyDeviceToDevice, c->st));
@@ -689,6 +704,12 @@ pm_status pm_set_state(pm_ctx* c, const void* x, const void* p, int step, int sy
     if (c->cfg.mode == PM_GR_POISSON && step > 0)
         return fail(PM_ERR_UNSUPPORTED, "a Poisson-gauge run resumes only at step 0 (its Phi history is not restored)");
     return copy_state(c, x, p, step, synchronised != 0);
+}
+
+pm_status pm_displacement(pm_ctx* c, void* disp) {
+    if (!c || !disp) return fail(PM_ERR_INVALID_ARG, "null argument");
+    PM_CK(lagrangian_displacement(c->at(c->L.x), disp, c->np, c->cfg.precision, c->cfg.box, c->st));
+    return PM_OK;
 }
 
 pm_status pm_state(pm_ctx* c, int* step, double* a, int* synchronised) {
@@ -755,6 +776,7 @@ pm_status pm_ic_zeldovich(pm_ctx* c, uint64_t seed, const void* white_noise, int
     c->synced = true;
     c->have_phi = false;
     c->rho_valid = false;
+    if (c->adj) c->adj->recorded = false;
     return PM_OK;
 }
 
@@ -857,6 +879,7 @@ pm_status pm_displacement_correction(pm_ctx* target, const pm_ctx* gr, const pm_
     PM_CK(combine(target->at(target->L.x), gr->at(gr->L.x), newton->at(newton->L.x), xi_out, target->np, gr->np,
                   target->cfg.precision, target->st));
     target->rho_valid = false;
+    if (target->adj) target->adj->recorded = false;
     return PM_OK;
 }
 
@@ -1086,42 +1109,46 @@ pm_status pm_adjoint_scratch_size(const pm_ctx* c, int checkpoint_every, size_t*
     return PM_OK;
 }
 
-pm_status pm_loss_grad(pm_ctx* c, const void* white_noise, const void* target, int checkpoint_every, void* scratch,
-                       size_t scratch_bytes, double* loss_out, void* grad_out) {
-    if (!c || !white_noise || !target || !loss_out || !grad_out || checkpoint_every < 1)
-        return fail(PM_ERR_INVALID_ARG, "null argument or bad checkpoint interval");
-    if (c->cfg.precision != PM_FP32_FIXED || c->cfg.mode != PM_NEWTON || c->cfg.gradient != PM_GRAD_SPECTRAL)
-        return fail(PM_ERR_UNSUPPORTED, "the gradient is implemented for the FP32 Newtonian step with the spectral force");
-    const int S = c->cfg.n_steps, C = std::min(checkpoint_every, S);
-    const AdjLayout A = adj_plan(c, C);
-    if (!scratch || scratch_bytes < A.total || (uintptr_t)scratch % 256)
-        return fail(PM_ERR_WORKSPACE, "adjoint scratch too small or not 256-byte aligned");
-    if (!c->st2) PM_CK(cudaStreamCreateWithFlags(&c->st2, cudaStreamNonBlocking));
-    unsigned char* sc = (unsigned char*)scratch;
-    const int n = c->n, np = c->np;
-    const size_t n3 = (size_t)n * n * n, P = 3 * (size_t)c->np3 * 4;
-    const double box = c->cfg.box, mass = std::pow((double)n / np, 3);
-    auto at = [&](size_t off) { return (void*)(sc + off); };
-    float* lam_u = (float*)at(A.lam_u);
-    float* lam_p = (float*)at(A.lam_p);
-    void* x = c->at(c->L.x);
-    void* p = c->at(c->L.p);
-    auto kick_of = [&](int s) {
-        const double a0 = c->a_grid(s), a1 = c->a_grid(s + 1);
-        const double a_from = (s == 0) ? a0 : 0.5 * (c->a_grid(s - 1) + a0);
-        return pmhost::kick_integral(c->cosmo, a_from, 0.5 * (a0 + a1));
-    };
-    auto drift_of = [&](int s) { return pmhost::drift_integral(c->cosmo, c->a_grid(s), c->a_grid(s + 1)); };
-    const size_t Gb = 3 * n3 * 4;
-    auto seg_x = [&](int k, int i) { return at(A.seg_x[k & 1] + (size_t)i * P); };
-    auto seg_g = [&](int k, int i) { return at(A.seg_g[k & 1] + (size_t)i * Gb); };
+}  // extern "C"
+
+namespace {
+
+double kick_of_step(const pm_ctx* c, int s) {
+    const double a0 = c->a_grid(s), a1 = c->a_grid(s + 1);
+    const double a_from = (s == 0) ? a0 : 0.5 * (c->a_grid(s - 1) + a0);
+    return pmhost::kick_integral(c->cosmo, a_from, 0.5 * (a0 + a1));
+}
+double drift_of_step(const pm_ctx* c, int s) {
+    return pmhost::drift_integral(c->cosmo, c->a_grid(s), c->a_grid(s + 1));
+}
+
+// Pieces of the reverse sweep shared by pm_adjoint_record, pm_adjoint_run and pm_loss_grad.
+// Layout A of the scratch; record k & 1 holds the positions and force meshes of segment k.
+struct AdjSweep {
+    pm_ctx* c;
+    pm_ctx::AdjSession& S;
+    AdjLayout A;
+    int steps;
+    size_t P, Gb;
+    AdjSweep(pm_ctx* ctx, pm_ctx::AdjSession& s) : c(ctx), S(s) {
+        steps = c->cfg.n_steps;
+        A = adj_plan(c, S.C);
+        P = 3 * (size_t)c->np3 * 4;
+        Gb = 3 * (size_t)c->n * c->n * c->n * 4;
+    }
+    void* at(size_t off) const { return (unsigned char*)S.scratch + off; }
+    void* seg_x(int k, int i) const { return at(A.seg_x[k & 1] + (size_t)i * P); }
+    void* seg_g(int k, int i) const { return at(A.seg_g[k & 1] + (size_t)i * Gb); }
+    void* ckpt_x(int k) const { return at(A.ckpt + (size_t)k * 2 * P); }
+    void* ckpt_p(int k) const { return at(A.ckpt + (size_t)k * 2 * P + P); }
+
     // Steps s0..s1-1 of segment k on context r from the positions at rx (p in place), keeping
     // each step's positions and force meshes in record k & 1.  With the fused update each
     // step reads its positions from the record and writes the drifted ones into the next
     // slot (the last step's to x_end), so only the segment's first positions are copied.
-    const bool oop = fused_update(c);
-    auto record = [&](pm_ctx* r, int k, void* rx, void* x_end) -> pm_status {
-        const int s0 = k * C, s1 = std::min(S, s0 + C);
+    pm_status record(pm_ctx* r, int k, void* rx, void* x_end) const {
+        const int s0 = k * S.C, s1 = std::min(steps, s0 + S.C);
+        const bool oop = fused_update(c);
         if (oop) PM_CK(cudaMemcpyAsync(seg_x(k, 0), rx, P, cudaMemcpyDeviceToDevice, r->st));
         for (int s = s0; s < s1; ++s) {
             void* xs = seg_x(k, s - s0);
@@ -1133,7 +1160,7 @@ pm_status pm_loss_grad(pm_ctx* c, const void* white_noise, const void* target, i
             }
             r->force_at = seg_g(k, s - s0);
             pm_status st = compute_forces(r, r->a_grid(s));
-            if (st == PM_OK) st = kick_drift(r, kick_of(s), drift_of(s));
+            if (st == PM_OK) st = kick_drift(r, kick_of_step(r, s), drift_of_step(r, s));
             r->force_at = nullptr;
             r->x_at = r->x_out = nullptr;
             if (st != PM_OK) return st;
@@ -1141,86 +1168,77 @@ pm_status pm_loss_grad(pm_ctx* c, const void* white_noise, const void* target, i
             r->synced = false;
         }
         return PM_OK;
-    };
-    // The re-runs run on a context of their own: the second stream, density and spectra in
-    // the scratch, p and (without the fused update) x in place over the segment's checkpoint
-    // (each checkpoint is used once).  They overlap the forward run and the reverse sweep.
-    pm_ctx re = *c;
-    re.pool.clear();
-    re.recs.clear();
-    re.prof = false;
-    re.st = c->st2;
-    re.st2 = nullptr;
-    re.ws = sc;
-    re.L.rho = A.re_rho;
-    for (int j = 0; j < 3; ++j) re.L.spec[j] = A.re_spec[j];
-    std::vector<cudaEvent_t> evs;
-    auto event = [&]() {
-        cudaEvent_t e = nullptr;
-        if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) == cudaSuccess) evs.push_back(e);
-        return e;
-    };
-    std::vector<cudaEvent_t> ev_ckpt(A.nseg), ev_rerun(A.nseg), ev_rev(A.nseg);
-    for (int k = 0; k < A.nseg; ++k) {
-        ev_ckpt[k] = event();
-        ev_rerun[k] = event();
-        ev_rev[k] = event();
     }
-    pm_status status = (int)evs.size() == 3 * A.nseg ? PM_OK : fail(PM_ERR_CUDA, "cudaEventCreate failed");
-    auto rerun = [&](int k) -> pm_status {
-        PM_CK(cudaStreamWaitEvent(re.st, ev_ckpt[k], 0));
-        if (k + 2 < A.nseg) PM_CK(cudaStreamWaitEvent(re.st, ev_rev[k + 2], 0));  // record k & 1 is free
-        re.L.x = A.ckpt + (size_t)k * 2 * P;
-        re.L.p = re.L.x + P;
-        re.step = k * C;
-        re.synced = (k == 0);
-        re.rho_valid = false;
-        PM_TRY(record(&re, k, re.at(re.L.x), at(A.re_x)));
-        PM_CK(cudaEventRecord(ev_rerun[k], re.st));
-        return PM_OK;
-    };
-    auto body = [&]() -> pm_status {
-        // ---- forward with checkpoints; the last two segments are recorded as they run (one
-        // record each), so the reverse sweep starts without a re-run.  The closing half kick
-        // after the last step changes only p, which the loss does not see, so it is neither
-        // run nor transposed.
+
+    // The forward run from the ICs of white noise w with checkpoints of (x, p) before every
+    // segment; the last two segments are recorded as they run (one record each), so the
+    // reverse sweep starts without a re-run.  The closing half kick after the last step
+    // changes only p, which neither the density nor the positions see: it is not run.
+    pm_status forward(const void* white_noise) const {
         PM_TRY(pm_ic_zeldovich(c, 0, white_noise, 0));
+        void* x = c->at(c->L.x);
+        void* p = c->at(c->L.p);
         for (int k = 0; k < A.nseg; ++k) {
-            const int s0 = k * C, s1 = std::min(S, s0 + C);
-            PM_CK(cudaMemcpyAsync(at(A.ckpt + (size_t)k * 2 * P), x, P, cudaMemcpyDeviceToDevice, c->st));
-            PM_CK(cudaMemcpyAsync(at(A.ckpt + (size_t)k * 2 * P + P), p, P, cudaMemcpyDeviceToDevice, c->st));
-            PM_CK(cudaEventRecord(ev_ckpt[k], c->st));
+            const int s0 = k * S.C, s1 = std::min(steps, s0 + S.C);
+            PM_CK(cudaMemcpyAsync(ckpt_x(k), x, P, cudaMemcpyDeviceToDevice, c->st));
+            PM_CK(cudaMemcpyAsync(ckpt_p(k), p, P, cudaMemcpyDeviceToDevice, c->st));
+            PM_CK(cudaEventRecord(S.ev_ckpt[k], c->st));
             if (k < A.nseg - 2) PM_TRY(pm_step(c, s1 - s0));
             else PM_TRY(record(c, k, x, x));
         }
-        // ---- loss and its mesh adjoint
-        float* rho = (float*)c->at(c->L.rho);
-        PM_CK(fill(rho, (int64_t)n3, PM_FP32_FIXED, -1.0, c->st));
-        PM_CK(deposit_lattice(x, np, PM_FP32_FIXED, n, mass, rho, c->st));
         c->rho_valid = false;
-        double* acc = (double*)at(A.acc);
-        PM_CK(cudaMemsetAsync(acc, 0, 8, c->st));
-        PM_CK(loss_mse(rho, (const float*)target, (int64_t)n3, acc, c->st));
-        PM_CK(cudaMemsetAsync(c->at(c->L.force[0]), 0, 3 * n3 * 4, c->st));  // V for the first adjoint deposit
-        PM_CK(adj_gather((const uint32_t*)x, c->np3, n, rho, (float)mass, 0, lam_u, c->st));
-        // lam_p = 0 after the closing kick; the transposed drift of the last step gives lam_p
-        PM_CK(axpby(lam_p, lam_u, nullptr, 3 * c->np3, (float)(drift_of(S - 1) / box), 0.0f, c->st));
-        // ---- reverse sweep, segment by segment (kick of step s, then the drift of step
-        // s - 1); the re-run of segment k - 2 (into the record segment k has just released)
-        // overlaps the reverse sweep of segment k - 1
+        return PM_OK;
+    }
+
+    // Reverse sweep from the adjoint positions lam_u (scratch lam_u; lam_p = 0 after the
+    // closing kick) down to dL/dw.  Every segment before the last two is re-run from its
+    // checkpoint on the second stream, on a context of its own (density and spectra in the
+    // scratch, p and, without the fused update, x in place over the checkpoint, which is
+    // used once), into the record the reverse sweep of the segment after it has just
+    // released; events order the two streams.
+    pm_status reverse(void* grad_out) const {
+        const double box = c->cfg.box;
+        float* lam_u = (float*)at(A.lam_u);
+        float* lam_p = (float*)at(A.lam_p);
+        pm_ctx re = *c;
+        re.pool.clear();
+        re.recs.clear();
+        re.prof = false;
+        re.st = c->st2;
+        re.st2 = nullptr;
+        re.adj = nullptr;
+        re.ws = (unsigned char*)S.scratch;
+        re.L.rho = A.re_rho;
+        for (int j = 0; j < 3; ++j) re.L.spec[j] = A.re_spec[j];
+        auto rerun = [&](int k) -> pm_status {
+            PM_CK(cudaStreamWaitEvent(re.st, S.ev_ckpt[k], 0));
+            if (k + 2 < A.nseg) PM_CK(cudaStreamWaitEvent(re.st, S.ev_rev[k + 2], 0));  // record k & 1 is free
+            re.L.x = A.ckpt + (size_t)k * 2 * P;
+            re.L.p = re.L.x + P;
+            re.step = k * S.C;
+            re.synced = (k == 0);
+            re.rho_valid = false;
+            PM_TRY(record(&re, k, re.at(re.L.x), at(A.re_x)));
+            PM_CK(cudaEventRecord(S.ev_rerun[k], re.st));
+            return PM_OK;
+        };
+        // the transposed drift of the last step gives lam_p
+        PM_CK(axpby(lam_p, lam_u, nullptr, 3 * c->np3, (float)(drift_of_step(c, steps - 1) / box), 0.0f, c->st));
+        // V (the three force meshes, back to back) is zero before the first adjoint deposit
+        PM_CK(cudaMemsetAsync(c->at(c->L.force[0]), 0, Gb, c->st));
         for (int k = A.nseg - 1; k >= 0; --k) {
-            const int s0 = k * C, s1 = std::min(S, s0 + C);
-            if (k < A.nseg - 2) PM_CK(cudaStreamWaitEvent(c->st, ev_rerun[k], 0));
+            const int s0 = k * S.C, s1 = std::min(steps, s0 + S.C);
+            if (k < A.nseg - 2) PM_CK(cudaStreamWaitEvent(c->st, S.ev_rerun[k], 0));
             for (int s = s1 - 1; s >= s0; --s)
-                PM_TRY(adj_kick(c, (const uint32_t*)seg_x(k, s - s0), (const float*)seg_g(k, s - s0), kick_of(s),
-                                lam_u, lam_p, s > 0 ? drift_of(s - 1) / box : 0.0));
-            PM_CK(cudaEventRecord(ev_rev[k], c->st));
+                PM_TRY(adj_kick(c, (const uint32_t*)seg_x(k, s - s0), (const float*)seg_g(k, s - s0),
+                                kick_of_step(c, s), lam_u, lam_p, s > 0 ? drift_of_step(c, s - 1) / box : 0.0));
+            PM_CK(cudaEventRecord(S.ev_rev[k], c->st));
             if (k >= 2) PM_TRY(rerun(k - 2));
         }
-        // ---- transposed Zel'dovich map: grad = sum_j A_j^T (D/L lam_u_j + a^2 E f D lam_p_j)
+        // transposed Zel'dovich map: grad = sum_j A_j^T (D/L lam_u_j + a^2 E f D lam_p_j)
+        const int np = c->np;
         const double a = c->cfg.a_init;
-        const double D = pmhost::growth_D(c->cosmo, a), f = pmhost::growth_f(c->cosmo, a),
-                     E = pmhost::E(c->cosmo, a);
+        const double D = pmhost::growth_D(c->cosmo, a), f = pmhost::growth_f(c->cosmo, a), E = pmhost::E(c->cosmo, a);
         const int64_t np3 = c->np3;
         float* s_j[3] = {(float*)c->at(c->L.force[0]), (float*)c->at(c->L.force[1]), (float*)c->at(c->L.force[2])};
         float2* sp[3] = {(float2*)c->at(c->L.spec[0]), (float2*)c->at(c->L.spec[1]), (float2*)c->at(c->L.spec[2])};
@@ -1234,24 +1252,124 @@ pm_status pm_loss_grad(pm_ctx* c, const void* white_noise, const void* target, i
                           c->st));
         PM_TRY(fft_inverse_f32(c, sp[0], (float*)grad_out, np));
         return PM_OK;
-    };
-    double hsum = 0.0;
-    if (status == PM_OK) status = body();
-    if (status == PM_OK) {
-        cudaError_t e = cudaMemcpyAsync(&hsum, at(A.acc), 8, cudaMemcpyDeviceToHost, c->st);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
-        if (e != cudaSuccess) status = fail(PM_ERR_CUDA, cudaGetErrorString(e));
     }
-    // the second stream is idle here on success; after an error wait for it before the
-    // scratch goes back to the caller
-    cudaStreamSynchronize(re.st);
-    for (auto e : evs) cudaEventDestroy(e);
-    // the context holds the forward run's last positions and momenta (before the closing kick)
-    c->step = S;
-    c->synced = false;
+};
+
+// Checks shared by the entry points of the reverse sweep; creates the second stream and
+// the session's events for checkpoint interval C.
+pm_status adj_prepare(pm_ctx* c, int checkpoint_every, void* scratch, size_t scratch_bytes) {
+    if (checkpoint_every < 1) return fail(PM_ERR_INVALID_ARG, "bad checkpoint interval");
+    if (c->cfg.precision != PM_FP32_FIXED || c->cfg.mode != PM_NEWTON || c->cfg.gradient != PM_GRAD_SPECTRAL)
+        return fail(PM_ERR_UNSUPPORTED, "the gradient is implemented for the FP32 Newtonian step with the spectral force");
+    const int C = std::min(checkpoint_every, c->cfg.n_steps);
+    const AdjLayout A = adj_plan(c, C);
+    if (!scratch || scratch_bytes < A.total || (uintptr_t)scratch % 256)
+        return fail(PM_ERR_WORKSPACE, "adjoint scratch too small or not 256-byte aligned");
+    if (!c->st2) PM_CK(cudaStreamCreateWithFlags(&c->st2, cudaStreamNonBlocking));
+    if (!c->adj) c->adj = new pm_ctx::AdjSession();
+    pm_ctx::AdjSession& S = *c->adj;
+    S.scratch = scratch;
+    S.bytes = scratch_bytes;
+    S.C = C;
+    S.recorded = false;
+    for (auto* v : {&S.ev_ckpt, &S.ev_rerun, &S.ev_rev}) {
+        while ((int)v->size() < A.nseg) {
+            cudaEvent_t e = nullptr;
+            PM_CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+            v->push_back(e);
+        }
+    }
+    return PM_OK;
+}
+
+// After an error the second stream may still run a re-run into the scratch: wait for it
+// before the scratch goes back to the caller.
+void adj_settle(pm_ctx* c) {
+    if (c->st2) cudaStreamSynchronize(c->st2);
+}
+
+}  // namespace
+
+extern "C" {
+
+pm_status pm_adjoint_record(pm_ctx* c, const void* white_noise, int checkpoint_every, void* scratch,
+                            size_t scratch_bytes) {
+    if (!c || !white_noise) return fail(PM_ERR_INVALID_ARG, "null argument");
+    PM_TRY(adj_prepare(c, checkpoint_every, scratch, scratch_bytes));
+    AdjSweep sw(c, *c->adj);
+    pm_status st = sw.forward(white_noise);
+    if (st != PM_OK) {
+        adj_settle(c);
+        return st;
+    }
+    c->adj->recorded = true;
+    return PM_OK;
+}
+
+pm_status pm_adjoint_run(pm_ctx* c, const void* d_delta, const void* d_disp, void* grad_w) {
+    if (!c || !grad_w || (!d_delta && !d_disp)) return fail(PM_ERR_INVALID_ARG, "null argument");
+    if (!c->adj || !c->adj->recorded || c->step != c->cfg.n_steps)
+        return fail(PM_ERR_STATE, "pm_adjoint_run needs the forward run of pm_adjoint_record first");
+    pm_ctx::AdjSession& S = *c->adj;
+    S.recorded = false;  // the re-runs overwrite the checkpoints: one reverse sweep per record
+    AdjSweep sw(c, S);
+    const int64_t m = 3 * c->np3;
+    float* lam_u = (float*)sw.at(sw.A.lam_u);
+    float* tmp = (float*)sw.at(sw.A.lam_p);
+    const double mass = std::pow((double)c->n / c->np, 3);
+    auto body = [&]() -> pm_status {
+        // lam_u = m sum_c dL/ddelta(c) dW(x, c)/du + L dL/d(disp), u in box units
+        if (d_delta) {
+            PM_CK(adj_gather((const uint32_t*)c->at(c->L.x), c->np3, c->n, (const float*)d_delta, (float)mass, 0,
+                             lam_u, c->st));
+            if (d_disp) {
+                PM_CK(axpby(tmp, lam_u, (const float*)d_disp, m, 1.0f, (float)c->cfg.box, c->st));
+                PM_CK(axpby(lam_u, tmp, nullptr, m, 1.0f, 0.0f, c->st));
+            }
+        } else {
+            PM_CK(axpby(lam_u, (const float*)d_disp, nullptr, m, (float)c->cfg.box, 0.0f, c->st));
+        }
+        return sw.reverse(grad_w);
+    };
+    pm_status st = body();
+    if (st == PM_OK) {
+        cudaError_t e = cudaStreamSynchronize(c->st);
+        if (e != cudaSuccess) st = fail(PM_ERR_CUDA, cudaGetErrorString(e));
+    }
+    adj_settle(c);
     c->rho_valid = false;
-    if (status == PM_OK) *loss_out = hsum / (double)n3;
-    return status;
+    return st;
+}
+
+pm_status pm_loss_grad(pm_ctx* c, const void* white_noise, const void* target, int checkpoint_every, void* scratch,
+                       size_t scratch_bytes, double* loss_out, void* grad_out) {
+    if (!c || !white_noise || !target || !loss_out || !grad_out)
+        return fail(PM_ERR_INVALID_ARG, "null argument or bad checkpoint interval");
+    PM_TRY(pm_adjoint_record(c, white_noise, checkpoint_every, scratch, scratch_bytes));
+    AdjSweep sw(c, *c->adj);
+    const int64_t n3 = (int64_t)c->n * c->n * c->n;
+    // the loss and its mesh adjoint 2 (delta - delta_t) / n^3, written over delta
+    float* rho = (float*)c->at(c->L.rho);
+    double* acc = (double*)sw.at(sw.A.acc);
+    auto seed = [&]() -> pm_status {
+        PM_CK(fill(rho, n3, PM_FP32_FIXED, -1.0, c->st));
+        PM_CK(deposit_lattice(c->at(c->L.x), c->np, PM_FP32_FIXED, c->n, std::pow((double)c->n / c->np, 3), rho,
+                              c->st));
+        PM_CK(cudaMemsetAsync(acc, 0, 8, c->st));
+        PM_CK(loss_mse(rho, (const float*)target, n3, acc, c->st));
+        return PM_OK;
+    };
+    pm_status st = seed();
+    if (st != PM_OK) {
+        adj_settle(c);
+        return st;
+    }
+    PM_TRY(pm_adjoint_run(c, rho, nullptr, grad_out));
+    double hsum = 0.0;
+    PM_CK(cudaMemcpyAsync(&hsum, acc, 8, cudaMemcpyDeviceToHost, c->st));
+    PM_CK(cudaStreamSynchronize(c->st));
+    *loss_out = hsum / (double)n3;
+    return PM_OK;
 }
 
 }  // extern "C"
@@ -1742,6 +1860,13 @@ pm_status pm_cell_sort_static(const void* x, int64_t count, int precision, int n
     if (precision != PM_FP32_FIXED && precision != PM_FP64) return fail(PM_ERR_INVALID_ARG, "bad precision");
     PM_TRY(check_device());
     PM_CK(cell_sort_static(x, count, precision, n, keys_out, order_out, (cudaStream_t)stream));
+    return PM_OK;
+}
+
+pm_status pm_div_mode_check(const double* a, const double* d, int64_t count, double* out, void* stream) {
+    if (count < 0 || (count > 0 && (!a || !d || !out))) return fail(PM_ERR_INVALID_ARG, "bad arguments");
+    PM_TRY(check_device());
+    PM_CK(div_mode_check(a, d, count, out, (cudaStream_t)stream));
     return PM_OK;
 }
 

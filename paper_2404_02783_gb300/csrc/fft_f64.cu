@@ -12,4 +12,17 @@ cudaError_t upload_twiddles_f64(const double2* host) {
 
 PM_INST(double)
 
+// div_mode<double> applied element by element (the check of its Newton-Raphson reciprocal).
+__global__ void k_div_mode(const double* __restrict__ a, const double* __restrict__ d, int64_t count,
+                           double* __restrict__ out) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = div_mode<double>(a[i], d[i]);
+}
+cudaError_t div_mode_check(const double* a, const double* d, int64_t count, double* out, cudaStream_t st) {
+    if (count <= 0) return cudaSuccess;
+    const int64_t blocks = std::min<int64_t>((count + 255) / 256, 152 * 8);
+    k_div_mode<<<(unsigned)blocks, 256, 0, st>>>(a, d, count, out);
+    return cudaGetLastError();
+}
+
 }  // namespace pm

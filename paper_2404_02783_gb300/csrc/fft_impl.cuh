@@ -51,8 +51,11 @@ __device__ __forceinline__ void load_twiddles_head(cplx<T>* tw, int L, int count
 
 
 // a / d in the per-mode operators.  FP32 divides as written.  FP64 divides are slow on this
-// part, so FP64 takes the FP32 reciprocal of d refined by two Newton steps
-// r <- r + r (1 - d r) (relative error ~2^-23, then ~2^-46, then below the FP64 rounding).
+// part, so FP64 computes the reciprocal of d by the Newton-Raphson iteration for 1/d,
+// r <- r + r (1 - d r), started from the FP32 reciprocal of d and run twice (the relative
+// error squares each time: ~2^-23, then ~2^-46, then below the FP64 rounding), and returns
+// a r.  d must lie in the FP32 normal range (about 1.2e-38 .. 3.4e38; the operators' k^2
+// and constraint denominators do).  pm_div_mode_check compares it with the division.
 template <typename T> __device__ __forceinline__ T div_mode(T a, T d) { return a / d; }
 template <> __device__ __forceinline__ double div_mode<double>(double a, double d) {
     double r = (double)__frcp_rn((float)d);

@@ -63,6 +63,9 @@ cudaError_t set_smem_once(const void* fn, size_t bytes);
 cudaError_t resident_ctas(const void* fn, int threads, size_t smem, int* per_sm);
 int num_sms();
 
+// out[i] = a[i] / d[i] by the FP64 per-mode divide of the spectral operators (fft_impl.cuh).
+cudaError_t div_mode_check(const double* a, const double* d, int64_t count, double* out, cudaStream_t st);
+
 // FFT passes.  n is the transform length (power of two, 16..1024); batch counts
 // independent 3D fields stored back to back.
 template <typename T>

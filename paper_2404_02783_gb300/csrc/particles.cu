@@ -805,6 +805,44 @@ cudaError_t fill(void* a, int64_t count, int precision, double v, cudaStream_t s
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------- Lagrangian displacement
+// d = x - q (minimum image) in Mpc/h for the np^3 lattice-ordered particles, q the node of
+// particle id = (ix np + iy) np + iz.  Ticks: the uint32 difference read as int32 is the
+// minimum image exactly.
+__global__ void k_disp_ticks(const uint32_t* __restrict__ x, float* __restrict__ d, int lognp, float tick_mpc) {
+    const int64_t count = (int64_t)1 << (3 * lognp);
+    const int mask = (1 << lognp) - 1;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t q[3] = {(uint32_t)((i >> (2 * lognp)) & mask) << (32 - lognp),
+                               (uint32_t)((i >> lognp) & mask) << (32 - lognp), (uint32_t)(i & mask) << (32 - lognp)};
+#pragma unroll
+        for (int j = 0; j < 3; ++j) d[j * count + i] = (float)(int32_t)(x[j * count + i] - q[j]) * tick_mpc;
+    }
+}
+__global__ void k_disp_frac(const double* __restrict__ x, double* __restrict__ d, int lognp, double box) {
+    const int64_t count = (int64_t)1 << (3 * lognp);
+    const int mask = (1 << lognp) - 1;
+    const double inv_np = 1.0 / (double)(1 << lognp);
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x) {
+        const int q[3] = {(int)((i >> (2 * lognp)) & mask), (int)((i >> lognp) & mask), (int)(i & mask)};
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            const double v = x[j * count + i] - q[j] * inv_np;
+            d[j * count + i] = (v - rint(v)) * box;
+        }
+    }
+}
+cudaError_t lagrangian_displacement(const void* x, void* d, int np, int precision, double box, cudaStream_t st) {
+    const int lognp = ilog2(np);
+    const int64_t count = (int64_t)np * np * np;
+    if (precision == PM_FP32_FIXED)
+        k_disp_ticks<<<grid_for(count, 256), 256, 0, st>>>((const uint32_t*)x, (float*)d, lognp,
+                                                           (float)(box / 4294967296.0));
+    else
+        k_disp_frac<<<grid_for(count, 256), 256, 0, st>>>((const double*)x, (double*)d, lognp, box);
+    return cudaGetLastError();
+}
+
 // ---------------------------------------------------------------- position check
 // Counts FP64 box-fraction positions that are not finite or lie outside [0, 1) (one
 // warp-aggregated atomic a warp).

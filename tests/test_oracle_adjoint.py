@@ -32,3 +32,38 @@ def test_gradient_vanishes_at_the_target():
     u, _, _, _ = adjoint.forward(c, 8, 16, 300.0, 0.2, 0.6, 3, w)
     L, g = adjoint.loss_and_grad(c, 8, 16, 300.0, 0.2, 0.6, 3, w, cic.density_contrast(u, 16))
     assert L < 1e-28 and np.max(np.abs(g)) < 1e-12
+
+
+@pytest.mark.parametrize("n_p,n_mesh", [(8, 16), (16, 16)])
+def test_vector_jacobian_product_of_density_and_displacements(n_p, n_mesh):
+    # a loss that is not the MSE: L = sum_k W(k) |delta_k|^2 / N^6 (a power-spectrum weighted
+    # norm of the final density) + sum_p g_p . d_p (the final displacements in Mpc/h); the
+    # cotangents go into vjp and its product with random directions must equal the central
+    # differences of the forward oracle itself
+    c = Cosmology()
+    box, ai, af, steps = 300.0, 0.2, 0.6, 4
+    w = inputs.gaussian_field(5, n_p)
+    r = np.random.default_rng(6)
+    f = np.fft.fftfreq(n_mesh, 1.0 / n_mesh)
+    K2 = f[:, None, None]**2 + f[None, :, None]**2 + f[None, None, :]**2
+    Wk = 1.0 / (1.0 + K2)
+    gdisp = r.standard_normal((3, n_p**3)) * 1e-3
+
+    def L_of(ww):
+        u, _, _, _ = adjoint.forward(c, n_p, n_mesh, box, ai, af, steps, ww)
+        dk = np.fft.fftn(cic.density_contrast(u, n_mesh))
+        return float(np.sum(Wk * np.abs(dk)**2) / n_mesh**6 + np.sum(gdisp * adjoint.displacement(u, n_p, box)))
+
+    u, _, _, _ = adjoint.forward(c, n_p, n_mesh, box, ai, af, steps, w)
+    dk = np.fft.fftn(cic.density_contrast(u, n_mesh))
+    lam_delta = 2.0 * np.real(np.fft.ifftn(Wk * dk)) / n_mesh**3  # dL/d delta of the spectral norm
+    g = adjoint.vjp(c, n_p, n_mesh, box, ai, af, steps, w, lam_delta=lam_delta, lam_disp=gdisp)
+    eps = 1e-5
+    for _ in range(3):
+        v = r.standard_normal((n_p,) * 3)
+        fd = (L_of(w + eps * v) - L_of(w - eps * v)) / (2 * eps)
+        assert np.sum(g * v) == pytest.approx(fd, rel=1e-6)
+    # each cotangent alone: the products add up
+    g1 = adjoint.vjp(c, n_p, n_mesh, box, ai, af, steps, w, lam_delta=lam_delta)
+    g2 = adjoint.vjp(c, n_p, n_mesh, box, ai, af, steps, w, lam_disp=gdisp)
+    np.testing.assert_allclose(g1 + g2, g, rtol=0, atol=1e-12 * np.max(np.abs(g)))
