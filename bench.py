@@ -52,14 +52,22 @@ def fused_update(np_side, n, fp64):
     return (not fp64) and n >= 64 and r in (1, 2, 4) and np_side >= 32 // r
 
 
-def launches_per_step(np_side, n, fp64):
-    """Kernels of this library launched per step (one force evaluation + one update):
-    z r2c, y, x with the Green's function, y with the y gradient, z c2r of the three force
-    components, and the update (+ the deposit when it is not fused into the update)."""
-    return 5 + (1 if fused_update(np_side, n, fp64) else 2)
+def fused_middle(n, fp64):
+    """FP32 meshes of 256^3 and up run the forward y, x and inverse y passes as one persistent
+    kernel over the kz planes (pm_set_fused_fft)."""
+    return (not fp64) and n >= 256
 
 
-def kernel_bytes(np_side, n, fp64):
+def launches_per_step(np_side, n, fp64, fused_fft=True):
+    """Kernels of this library launched per step (one force evaluation + one update): z r2c,
+    the middle passes (one fused kernel, or y, x with the Green's function and y with the y
+    gradient), z c2r of the three force components, and the update (+ the deposit when it is
+    not fused into the update)."""
+    fft = 3 if (fused_fft and fused_middle(n, fp64)) else 5
+    return fft + (1 if fused_update(np_side, n, fp64) else 2)
+
+
+def kernel_bytes(np_side, n, fp64, fused_fft=True):
     """Algorithmic bytes per launch of each phase (each array it must touch, once)."""
     s = 8 if fp64 else 4
     P = np_side**3
@@ -72,6 +80,10 @@ def kernel_bytes(np_side, n, fp64):
         "fft_yz_inv": 2 * S + 3 * R,         # read the two x-inverted spectra, write 3 force meshes
         "kick_drift": 12 * s * P + 3 * R,    # read + write x, p; gather 3 meshes once
     }
+    if fused_fft and fused_middle(n, fp64):
+        kb["fft_zy_fwd"] = R + S             # z r2c only: read rho, write its half spectrum
+        kb["fft_x_green"] = 4 * S            # read the z pass's spectrum, write the three y-inverted ones
+        kb["fft_yz_inv"] = 3 * S + 3 * R     # the three z c2r
     if fused_update(np_side, n, fp64):
         kb["deposit"] = R                    # only the zeroing of rho remains in this phase
         kb["kick_drift"] += R                # the drifted positions are deposited in the same pass
@@ -207,13 +219,14 @@ def start_of_timed_steps(pm, torch, run, k):
     torch.cuda.synchronize()
 
 
-def bench_precision(pm, torch, args, prec, rank, world, clocks=None):
+def bench_precision(pm, torch, args, prec, rank, world, clocks=None, fused_fft=True):
     """The last K steps of the fixed GRID_STEPS-step run (z = 50 -> 0; the closing half kick
     included), after W warm-up steps taken on the same context from the ICs; then the same K
     steps again with the library's per-phase events on (the kernel rooflines cover the same
     steps as the headline)."""
     cfg = pm.make_config(args.np, args.nmesh, args.box, A_INIT, A_FINAL, GRID_STEPS, precision=prec)
     run = pm.PMRun(cfg)
+    pm.pm_set_fused_fft(run.ctx, fused_fft)
     run.seed = 1 + rank
     run.ic(seed=run.seed)
     run.step(args.warmup)
@@ -236,8 +249,8 @@ def bench_precision(pm, torch, args, prec, rank, world, clocks=None):
     return ms, phases
 
 
-def roofline(phases, np_side, n, fp64, peak, peak_kind):
-    kb = kernel_bytes(np_side, n, fp64)
+def roofline(phases, np_side, n, fp64, peak, peak_kind, fused_fft=True):
+    kb = kernel_bytes(np_side, n, fp64, fused_fft)
     dom = max(PHASES, key=lambda p: phases[p][0])
     ms, launches = phases[dom]
     per_launch_ms = ms / max(launches, 1)
@@ -808,6 +821,7 @@ def main():
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-estimators", action="store_true")
+    ap.add_argument("--no-compare", action="store_true", help="skip the separate-FFT-passes comparison")
     ap.add_argument("--cpu-rows", default="128",
                     help="comma-separated oracle sizes timed per step (e.g. 128,256,512); empty: none")
     args = ap.parse_args()
@@ -866,12 +880,22 @@ def main():
            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded Philox phases, EH no-wiggle LCDM)",
            "config": config, "clocks": clk,
-           "gpu_launches": launches_per_step(args.np, args.nmesh, False) * args.steps,
+           "gpu_launches": launches_per_step(args.np, args.nmesh, False) * (args.steps + 1),  # + the closing kick
            "roofline": roof,
            "step_roofline": {"bytes_per_step": sb, "achieved": round(sb / (ms_step * 1e-3) / 1e9, 1),
                              "peak": peak, "unit": "GB/s", "frac": round(sb / (ms_step * 1e-3) / 1e9 / peak, 4),
                              "bytes_model": "60 B/particle + 40 B/cell"},
            "phases_fp32": table32}
+    if fused_middle(args.nmesh, False) and not args.no_compare:
+        ms_sep, ph_sep = bench_precision(pm, torch, args, pm.PM_FP32_FIXED, rank, world, fused_fft=False)
+        _, table_sep = roofline(ph_sep, args.np, args.nmesh, False, peak, peak_kind, fused_fft=False)
+        out["separate_fft_passes"] = {
+            "ms_per_step": ms_sep / args.steps,
+            "value": world * args.np**3 * args.steps / (ms_sep * 1e-3),
+            "step_roofline_frac": round(sb / (ms_sep / args.steps * 1e-3) / 1e9 / peak, 4),
+            "phases": table_sep,
+            "what": "the same steps with the forward y, x and inverse y passes as three launches "
+                    "(pm_set_fused_fft off) instead of the fused persistent kernel"}
     if not args.no_fp64:
         ms64, ph64 = bench_precision(pm, torch, args, pm.PM_FP64, rank, world)
         sb64 = step_bytes(args.np, args.nmesh, True)

@@ -68,7 +68,7 @@ typedef enum {
     PM_ERR_INVALID_ARG = 1,   /* bad size, null pointer, unsupported combination */
     PM_ERR_CUDA = 2,          /* a CUDA runtime call or kernel launch failed */
     PM_ERR_WORKSPACE = 3,     /* caller buffer too small or misaligned (256 B) */
-    PM_ERR_TIMEOUT = 4,       /* a bounded device wait gave up (reserved) */
+    PM_ERR_TIMEOUT = 4,       /* a bounded device wait gave up (the fused FFT passes; results invalid) */
     PM_ERR_BOUNDS = 5,        /* input outside the mesh's bounds (FP64 positions outside [0, 1)) */
     PM_ERR_UNSUPPORTED = 6,   /* no suitable GPU */
     PM_ERR_STATE = 7          /* call out of order (e.g. stepping past a_final) */
@@ -178,6 +178,16 @@ pm_status pm_displacement(pm_ctx* ctx, void* disp);
  * behind (0). */
 pm_status pm_state(pm_ctx* ctx, int* step, double* a, int* synchronised);
 
+/* The three middle passes of a force evaluation with the spectral gradient in FP32 on meshes
+ * of 256^3 and up -- forward y, x with the Green's function or Poisson-gauge constraint and the
+ * x gradient, inverse y with the y gradient -- run as one persistent kernel, kz plane by kz
+ * plane, so that each plane's intermediate spectra are re-read from L2 instead of HBM
+ * (enable != 0, the default), or as three separate launches (0).  The results are the same
+ * bit for bit.  The persistent kernel's items wait for the items they depend on with bounded
+ * polls; a wait that gives up (it cannot under correct operation) sets an error word that
+ * pm_power and pm_timings report as PM_ERR_TIMEOUT. */
+pm_status pm_set_fused_fft(pm_ctx* ctx, int enable);
+
 /* Per-phase device timing of pm_step with CUDA events recorded on the context
  * stream around each kernel of a force evaluation and update.  pm_profile(ctx, 1)
  * starts recording (0 stops); pm_timings synchronises the stream, writes the summed
@@ -185,10 +195,12 @@ pm_status pm_state(pm_ctx* ctx, int* step, double* a, int* synchronised);
  * call into caller arrays of PM_NPHASES entries, and resets the counters. */
 enum {
     PM_PHASE_DEPOSIT = 0,      /* zeroing + CIC deposit */
-    PM_PHASE_FFT_ZY_FWD = 1,   /* z (real to half spectrum) and forward y passes, by x-slab chunks */
-    PM_PHASE_FFT_X_GREEN = 2,  /* x pass with Green's function / constraint and x gradient */
-    PM_PHASE_FFT_YZ_INV = 3,   /* inverse y (with y gradient) and z passes of the three force
-                                  components (z gradient fused), by x-slab chunks */
+    PM_PHASE_FFT_ZY_FWD = 1,   /* z (real to half spectrum) and forward y passes (z alone when the
+                                  fused middle passes run, pm_set_fused_fft) */
+    PM_PHASE_FFT_X_GREEN = 2,  /* x pass with Green's function / constraint and x gradient (with the
+                                  forward and inverse y passes when fused) */
+    PM_PHASE_FFT_YZ_INV = 3,   /* inverse y (with y gradient; not when fused) and z passes of the
+                                  three force components (z gradient fused) */
     PM_PHASE_KICK_DRIFT = 4,   /* CIC interpolation + kick + drift (+ next deposit when fused) */
     PM_NPHASES = 5
 };
@@ -259,7 +271,8 @@ pm_status pm_bispectrum_scratch_size(const pm_ctx* ctx, int m, int nbins, size_t
  * nbins (nbins+1)(nbins+2)/6 entries), by the FFT identity on an m^3 grid:
  * sum_x I_i I_j I_l with I_b = IFFT_m[delta 1_b].  Exact (no aliasing) when every
  * mode of every bin has |n_i| < m/3; PM_ERR_INVALID_ARG otherwise.  field as in
- * pm_power.  b_out and ntri_out are host arrays (NaN where N_ijl = 0).
+ * pm_power.  b_out and ntri_out are host arrays (NaN where N_ijl = 0); N_ijl, an integer
+ * count of configurations, is the rounded FFT-identity sum, and B divides by it exactly.
  * scratch is caller device memory of pm_bispectrum_scratch_size bytes.  Synchronises. */
 pm_status pm_bispectrum(pm_ctx* ctx, const void* field, int nbins, const double* edges,
                         int m, int deconvolve, void* scratch, size_t scratch_bytes,

@@ -55,7 +55,7 @@ pm_status check_device() {
 
 struct Layout {
     size_t x = 0, p = 0, rho = 0, spec[3] = {0, 0, 0}, force[3] = {0, 0, 0};
-    size_t phi_old = 0, island = 0, amp = 0, bin_of = 0, wtab = 0, acc = 0, total = 0;
+    size_t phi_old = 0, island = 0, amp = 0, bin_of = 0, wtab = 0, acc = 0, mid = 0, total = 0;
     bool gr = false, has_island = false;
 };
 
@@ -103,6 +103,7 @@ Layout plan(const pm_config& c) {
     L.bin_of = take((3 * (n / 2) * (n / 2) + 1) * 2);
     L.wtab = take((n / 2 + 1) * 8);
     L.acc = take(2 * kMaxBins * 8);
+    L.mid = take(mid_sync_words_count((int)(n / 2 + 1)) * 4);
     L.total = off;
     return L;
 }
@@ -169,6 +170,8 @@ struct pm_ctx {
         }
     };
     AdjSession* adj = nullptr;
+    // the fused middle passes of the force evaluation are used where they apply (pm_tune)
+    bool mid_enabled = true;
     ~pm_ctx() {
         delete adj;
         if (st2) cudaStreamDestroy(st2);
@@ -280,6 +283,22 @@ pm_status current_density(pm_ctx* c, const void** rho_out) {
 
 // Force meshes g = -grad phi of the current particles at scale factor a.
 bool fused_update(const pm_ctx* c) { return ikd_deposit_supported(c->np, c->cfg.precision, c->n); }
+// The forward y, x and inverse y passes of the spectral force as one persistent launch (FP32,
+// meshes of 256^3 and up), unless switched off for the context.
+bool fused_middle(const pm_ctx* c) {
+    return !c->fp64() && c->cfg.gradient == PM_GRAD_SPECTRAL && c->n >= 256 && c->mid_enabled;
+}
+
+// The fused middle passes' error word (set when one of their bounded waits gave up; it stays
+// set): PM_ERR_TIMEOUT if it is.  Synchronises the context stream.
+pm_status check_wait_error(pm_ctx* c) {
+    unsigned err = 0;
+    const size_t word = mid_sync_words_count(c->n / 2 + 1) - 1;
+    PM_CK(cudaMemcpyAsync(&err, (unsigned*)c->at(c->L.mid) + word, sizeof(err), cudaMemcpyDeviceToHost, c->st));
+    PM_CK(cudaStreamSynchronize(c->st));
+    if (err) return fail(PM_ERR_TIMEOUT, "a bounded device wait of the fused FFT passes gave up; results are invalid");
+    return PM_OK;
+}
 
 template <typename T>
 pm_status compute_forces_t(pm_ctx* c, double a) {
@@ -289,7 +308,13 @@ pm_status compute_forces_t(pm_ctx* c, double a) {
     cplx<T>* s0 = (cplx<T>*)c->at(c->L.spec[0]);
     cplx<T>* s1 = (cplx<T>*)c->at(c->L.spec[1]);
     cplx<T>* s2 = (cplx<T>*)c->at(c->L.spec[2]);
-    PM_TRY(forward_to_y<T>(c, rho, s0, n));
+    if (fused_middle(c)) {
+        // the forward y pass runs inside the fused middle passes
+        Phase ph(c, PM_PHASE_FFT_ZY_FWD);
+        PM_CK(z_r2c<T>((const T*)rho, s0, n, 1, c->st));
+    } else {
+        PM_TRY(forward_to_y<T>(c, rho, s0, n));
+    }
     if (fused_update(c)) {
         // the forward z pass has consumed rho: clear it for the fused deposit of the update
         Phase ph(c, PM_PHASE_DEPOSIT);
@@ -327,6 +352,16 @@ pm_status compute_forces_t(pm_ctx* c, double a) {
         const cplx<T>* in[1] = {s0};
         T* out[1] = {(T*)c->force(0)};
         PM_CK(z_c2r<T>(in, out, 1, n, 1, 0u, 0.0, c->st));
+    } else if (fused_middle(c)) {
+        // z r2c above left the half spectrum in s0 before its forward y pass (see forward_to_y)
+        {
+            Phase ph(c, PM_PHASE_FFT_X_GREEN);
+            PM_CK(fft_middle<T>(s0, s1, s2, n / 2 + 1, n, op, (unsigned*)c->at(c->L.mid), c->st));
+        }
+        Phase ph(c, PM_PHASE_FFT_YZ_INV);
+        const cplx<T>* in[3] = {s1, s2, s0};  // IFFT_y(-i kx phi), IFFT_y(-i ky phi), IFFT_y(phi) (-i kz)
+        T* out[3] = {(T*)c->force(0), (T*)c->force(1), (T*)c->force(2)};
+        PM_CK(z_c2r<T>(in, out, 3, n, 1, 4u, c->kf, c->st));
     } else {
         {
             Phase ph(c, PM_PHASE_FFT_X_GREEN);
@@ -554,10 +589,12 @@ pm_status bispectrum_t(pm_ctx* c, const void* field, int nbins, const double* ed
     const double V = c->cfg.box * c->cfg.box * c->cfg.box;
     const double n9 = std::pow((double)n, 9);
     const double m3 = (double)m * m * m;
+    // the count of configurations is an integer: the FFT identity gives it up to rounding, so
+    // it is rounded and B divides the triangle sum by the exact count
     for (int t = 0; t < B.ntri; ++t) {
-        const double cnt = hc[t] / m3;
+        const double cnt = std::rint(hc[t] / m3);
         if (ntri_out) ntri_out[t] = cnt;
-        if (b_out) b_out[t] = (cnt > 0.5) ? V * V / n9 * hs[t] / hc[t] : NAN;
+        if (b_out) b_out[t] = (cnt > 0.0) ? V * V / n9 * (hs[t] / m3) / cnt : NAN;
     }
     return PM_OK;
 }
@@ -632,6 +669,8 @@ pm_status pm_init(const pm_config* cfg, void* workspace, size_t bytes, void* str
     cudaError_t e = cudaMemcpyAsync(c->at(L.amp), amp.data(), amp.size() * 8, cudaMemcpyHostToDevice, c->st);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(c->at(L.wtab), wtab.data(), wtab.size() * 8, cudaMemcpyHostToDevice, c->st);
+    if (e == cudaSuccess)
+        e = cudaMemsetAsync(c->at(L.mid), 0, mid_sync_words_count(c->n / 2 + 1) * 4, c->st);
     if (e == cudaSuccess && L.has_island)
         e = cudaMemsetAsync(c->at(L.island), 0, (size_t)(cfg->n_lo + 1) * (2 * cfg->n_lo + 1) * (2 * cfg->n_lo + 1) * 16,
                             c->st);
@@ -801,6 +840,12 @@ pm_status pm_step(pm_ctx* c, int n_steps) {
     return PM_OK;
 }
 
+pm_status pm_set_fused_fft(pm_ctx* c, int enable) {
+    if (!c) return fail(PM_ERR_INVALID_ARG, "null context");
+    c->mid_enabled = enable != 0;
+    return PM_OK;
+}
+
 pm_status pm_profile(pm_ctx* c, int enable) {
     if (!c) return fail(PM_ERR_INVALID_ARG, "null context");
     c->prof = enable != 0;
@@ -809,7 +854,7 @@ pm_status pm_profile(pm_ctx* c, int enable) {
 
 pm_status pm_timings(pm_ctx* c, double* ms, int64_t* launches) {
     if (!c) return fail(PM_ERR_INVALID_ARG, "null context");
-    PM_CK(cudaStreamSynchronize(c->st));
+    PM_TRY(check_wait_error(c));
     double acc[PM_NPHASES] = {0};
     int64_t cnt[PM_NPHASES] = {0};
     for (auto& r : c->recs) {
@@ -887,6 +932,7 @@ pm_status pm_power(pm_ctx* c, const void* field, const void* field2, int nbins, 
                    double* k_out, double* p_out, double* nmodes_out) {
     if (!c) return fail(PM_ERR_INVALID_ARG, "null context");
     PM_TRY(check_edges(nbins, edges));
+    PM_TRY(check_wait_error(c));
     return c->fp64() ? power_t<double>(c, field, field2, nbins, edges, deconvolve, k_out, p_out, nmodes_out)
                      : power_t<float>(c, field, field2, nbins, edges, deconvolve, k_out, p_out, nmodes_out);
 }
@@ -1207,6 +1253,7 @@ struct AdjSweep {
         re.st = c->st2;
         re.st2 = nullptr;
         re.adj = nullptr;
+        re.mid_enabled = false;  // its workspace is the scratch: no sync words of its own there
         re.ws = (unsigned char*)S.scratch;
         re.L.rho = A.re_rho;
         for (int j = 0; j < 3; ++j) re.L.spec[j] = A.re_spec[j];

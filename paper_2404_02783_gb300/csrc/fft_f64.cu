@@ -12,6 +12,12 @@ cudaError_t upload_twiddles_f64(const double2* host) {
 
 PM_INST(double)
 
+// The fused middle passes are built for FP32 only (FP64 runs the separate passes).
+template <>
+cudaError_t fft_middle<double>(double2*, double2*, double2*, int, int, const SpecOp&, unsigned*, cudaStream_t) {
+    return cudaErrorNotSupported;
+}
+
 // div_mode<double> applied element by element (the check of its Newton-Raphson reciprocal).
 __global__ void k_div_mode(const double* __restrict__ a, const double* __restrict__ d, int64_t count,
                            double* __restrict__ out) {

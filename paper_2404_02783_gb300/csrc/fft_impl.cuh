@@ -333,6 +333,77 @@ template <typename T, int LOGN, int KIND> struct XShape {
     static constexpr int MINB = WIDE ? 1 : (sizeof(T) == 4 ? 2 : 1);
 };
 
+// The per-mode operator of the x pass on mode (nx, ny, nz), |n|^2 = n2, of field `field`:
+// the Newtonian Green's function (or the potential alone), the Zel'dovich filter, or the
+// linearised Poisson-gauge constraint (which reads and updates its Phi history at `old` and,
+// for |n| <= n_lo, the FP64 island).  Returns phi for the mode.
+template <typename T, int KIND, int N>
+__device__ __forceinline__ cplx<T> mode_op(const SpecOp& op, cplx<T> vv, int nx, int ny, int nz, int n2, int field,
+                                           double kf, T kfT, T coefT, T kf2T, cplx<T>* old) {
+    typedef cplx<T> C;
+    constexpr int M = N / 2;
+    C phi;
+    if constexpr (KIND == OP_NEWTON || KIND == OP_POTENTIAL) {
+        phi = (n2 == 0) ? cmake<C>(T(0), T(0)) : cscale(vv, div_mode(coefT, T(n2)));
+    } else if constexpr (KIND == OP_ZA) {
+        const bool nyq = (2 * nx == -N) || (2 * ny == -N) || (nz == M);
+        const double* amp = op.amp + (int64_t)field * op.amp_stride;
+        C g = vv;
+        if (op.fixed_amp) {  // keep the phase, set |g| = 1
+            const T r2 = g.x * g.x + g.y * g.y;
+            g = (r2 > T(0)) ? cscale(g, rsqrt(r2)) : cmake<C>(T(0), T(0));
+        }
+        const double filt = op.za_filter == ZA_IDENTITY  ? op.coef
+                            : op.za_filter == ZA_INV_LAPLACE ? op.coef / (kf * kf * (double)n2)
+                                                             : op.coef / (kf * kf) * amp[n2] / (double)n2;
+        phi = (n2 == 0 || nyq) ? cmake<C>(T(0), T(0)) : cscale(g, T(filt));
+    } else {  // OP_GR
+        if (n2 == 0) {
+            phi = cmake<C>(T(0), T(0));
+            if (op.n_lo > 0) {
+                const int L = op.n_lo, W2 = 2 * L + 1;
+                op.island[((size_t)nz * W2 + L) * W2 + L] = make_double2(0.0, 0.0);
+            }
+        } else if (n2 <= op.n_lo * op.n_lo) {
+            const int L = op.n_lo, W2 = 2 * L + 1;
+            const size_t id = ((size_t)nz * W2 + (nx + L)) * W2 + (ny + L);
+            const double k2 = kf * kf * (double)n2;
+            const double H = op.calH;
+            const double num_s = -1.5 * H * H * op.omm_a;
+            double den = k2 + 3.0 * H * H + 4.5 * H * H * op.omm_a;
+            double2 P = make_double2(num_s * (double)vv.x, num_s * (double)vv.y);
+            if (!op.first) {
+                const double2 old = op.island[id];
+                const double cc = 3.0 * H * op.inv_dtau;
+                P.x += cc * old.x;
+                P.y += cc * old.y;
+                den += cc;
+            }
+            P.x /= den;
+            P.y /= den;
+            op.island[id] = P;
+            phi = cmake<C>(T(P.x * op.ac2_over_n3), T(P.y * op.ac2_over_n3));
+        } else {
+            const T k2 = kf2T * T(n2);
+            const T H = T(op.calH), om = T(op.omm_a);
+            const T num_s = T(-1.5) * H * H * om;
+            T den = k2 + T(3) * H * H + T(4.5) * H * H * om;
+            C Pc = cscale(vv, num_s);
+            if (!op.first) {
+                const T cc = T(3) * H * T(op.inv_dtau);
+                const C o = *old;
+                Pc.x += cc * o.x;
+                Pc.y += cc * o.y;
+                den += cc;
+            }
+            Pc = cscale(Pc, div_mode(T(1), den));
+            *old = Pc;
+            phi = cscale(Pc, T(op.ac2_over_n3));
+        }
+    }
+    return phi;
+}
+
 template <typename T, int LOGN, int KIND>
 __global__ void __launch_bounds__(XShape<T, LOGN, KIND>::THREADS, XShape<T, LOGN, KIND>::MINB)
     k_x_cols(cplx<T>* __restrict__ data, cplx<T>* __restrict__ out2, SpecOp op, int nplanes) {
@@ -466,66 +537,8 @@ __global__ void __launch_bounds__(XShape<T, LOGN, KIND>::THREADS, XShape<T, LOGN
                     run_sum2 += val2;
                 }
             } else {
-                C phi;
-                if constexpr (KIND == OP_NEWTON || KIND == OP_POTENTIAL) {
-                    phi = (n2 == 0) ? cmake<C>(T(0), T(0)) : cscale(vv, div_mode(coefT, T(n2)));
-                } else if constexpr (KIND == OP_ZA) {
-                    const bool nyq = (2 * nx == -N) || (2 * ny == -N) || (nz == M);
-                    const double* amp = op.amp + (int64_t)field * op.amp_stride;
-                    C g = vv;
-                    if (op.fixed_amp) {  // keep the phase, set |g| = 1
-                        const T r2 = g.x * g.x + g.y * g.y;
-                        g = (r2 > T(0)) ? cscale(g, rsqrt(r2)) : cmake<C>(T(0), T(0));
-                    }
-                    const double filt = op.za_filter == ZA_IDENTITY  ? op.coef
-                                        : op.za_filter == ZA_INV_LAPLACE ? op.coef / (kf * kf * (double)n2)
-                                                                         : op.coef / (kf * kf) * amp[n2] / (double)n2;
-                    phi = (n2 == 0 || nyq) ? cmake<C>(T(0), T(0)) : cscale(g, T(filt));
-                } else {  // OP_GR
-                    if (n2 == 0) {
-                        phi = cmake<C>(T(0), T(0));
-                        if (op.n_lo > 0) {
-                            const int L = op.n_lo, W2 = 2 * L + 1;
-                            op.island[((size_t)nz * W2 + L) * W2 + L] = make_double2(0.0, 0.0);
-                        }
-                    } else if (n2 <= op.n_lo * op.n_lo) {
-                        const int L = op.n_lo, W2 = 2 * L + 1;
-                        const size_t id = ((size_t)nz * W2 + (nx + L)) * W2 + (ny + L);
-                        const double k2 = kf * kf * (double)n2;
-                        const double H = op.calH;
-                        const double num_s = -1.5 * H * H * op.omm_a;
-                        double den = k2 + 3.0 * H * H + 4.5 * H * H * op.omm_a;
-                        double2 P = make_double2(num_s * (double)vv.x, num_s * (double)vv.y);
-                        if (!op.first) {
-                            const double2 old = op.island[id];
-                            const double cc = 3.0 * H * op.inv_dtau;
-                            P.x += cc * old.x;
-                            P.y += cc * old.y;
-                            den += cc;
-                        }
-                        P.x /= den;
-                        P.y /= den;
-                        op.island[id] = P;
-                        phi = cmake<C>(T(P.x * op.ac2_over_n3), T(P.y * op.ac2_over_n3));
-                    } else {
-                        C* old = reinterpret_cast<C*>(op.phi_old) + pbase + (size_t)i * N + c;
-                        const T k2 = kf2T * T(n2);
-                        const T H = T(op.calH), om = T(op.omm_a);
-                        const T num_s = T(-1.5) * H * H * om;
-                        T den = k2 + T(3) * H * H + T(4.5) * H * H * om;
-                        C Pc = cscale(vv, num_s);
-                        if (!op.first) {
-                            const T cc = T(3) * H * T(op.inv_dtau);
-                            const C o = *old;
-                            Pc.x += cc * o.x;
-                            Pc.y += cc * o.y;
-                            den += cc;
-                        }
-                        Pc = cscale(Pc, div_mode(T(1), den));
-                        *old = Pc;
-                        phi = cscale(Pc, T(op.ac2_over_n3));
-                    }
-                }
+                const C phi = mode_op<T, KIND, N>(op, vv, nx, ny, nz, n2, field, kf, kfT, coefT, kf2T,
+                                                  reinterpret_cast<C*>(op.phi_old) + pbase + (size_t)i * N + c);
                 v[0][m] = phi;
                 if constexpr (KIND != OP_POTENTIAL) {
                     const T kx = (2 * nx == -N) ? T(0) : kfT * T(nx);
@@ -550,6 +563,179 @@ __global__ void __launch_bounds__(XShape<T, LOGN, KIND>::THREADS, XShape<T, LOGN
             for (int m = 0; m < 8; ++m) {
                 base[(size_t)(t + m * Q) * N + c] = v[0][m];
                 out2[pbase + (size_t)(t + m * Q) * N + c] = v[1][m];
+            }
+        }
+    }
+}
+
+// =============================================================== fused middle passes
+// The three passes between the forward z and the inverse z transforms of a force
+// evaluation -- forward y, x with the Green's function (or the Poisson-gauge constraint)
+// and the x gradient, inverse y with the y gradient -- touch only one kz plane of the half
+// spectrum each.  One persistent launch runs them plane by plane: a CTA takes items from a
+// queue (item = one phase on a block of rows or columns of one plane) in rounds; round r
+// holds the forward-y items of plane r, the x items of plane r - LAG and the inverse-y items
+// of plane r - 2 LAG, so a plane's intermediate spectra are read back a few planes after they
+// were written, from L2, and only the z pass's spectrum (read) and the three y-inverted
+// spectra (written) go through HBM: 4 half spectra instead of 10.
+// An item of the x phase waits for the plane's forward-y items to be done, an inverse-y item
+// for its x items.  Every item waited on was handed out earlier, to a CTA that is running,
+// so every wait ends; each wait still gives up after kMidSpinLimit polls (about a second),
+// sets the error word and lets the CTA go on, so that a fault cannot hang the GPU.
+struct MidSync {
+    unsigned* queue;   // next item
+    unsigned* done_y;  // [nplanes] finished forward-y items
+    unsigned* done_x;  // [nplanes] finished x items
+    unsigned* error;   // nonzero: a wait gave up
+};
+constexpr unsigned kMidSpinLimit = 1u << 23;
+
+template <typename T, int LOGN> struct MidShape {
+    static constexpr int N = 1 << LOGN, M = N / 2, QN = N / 8;
+    static constexpr int THREADS = 512;
+    static constexpr int RB = THREADS / QN;  // rows of a y item
+    static constexpr int CB = THREADS / QN;  // columns of an x item
+    static constexpr int ITEMS = N / RB;     // items of each phase per plane
+    static constexpr int LAG = 3;            // rounds between the phases of one plane
+    typedef RowLayout<N, false> LAY;
+    // twiddles + the larger of the y exchange (two rows buffers of RB rows) and the x exchange
+    // (two sequences of N x (CB + 1))
+    static constexpr int XWORDS = 2 * N * (CB + 1), YWORDS = 2 * RB * LAY::RS;
+    static constexpr size_t SMEM = sizeof(cplx<T>) * (N + (XWORDS > YWORDS ? XWORDS : YWORDS));
+};
+
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];\n" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Thread 0 waits until *cnt reaches target (bounded), then the CTA proceeds.
+__device__ __forceinline__ void mid_wait(const unsigned* cnt, unsigned target, unsigned* error) {
+    if (threadIdx.x == 0) {
+        unsigned polls = 0;
+        while (ld_acquire_u32(cnt) < target) {
+            if (++polls > kMidSpinLimit || *(volatile unsigned*)error) {
+                atomicExch(error, 1u);
+                break;
+            }
+            __nanosleep(128);
+        }
+    }
+    __syncthreads();
+}
+
+template <typename T, int LOGN, int KIND>
+__global__ void __launch_bounds__(MidShape<T, LOGN>::THREADS, 2)
+    k_mid(cplx<T>* __restrict__ A, cplx<T>* __restrict__ B, cplx<T>* __restrict__ Cs, SpecOp op, int nplanes,
+          MidSync sync) {
+    typedef cplx<T> C;
+    typedef MidShape<T, LOGN> SH;
+    constexpr int N = SH::N, M = SH::M, Q = SH::QN, RB = SH::RB, CB = SH::CB, ITEMS = SH::ITEMS, LAG = SH::LAG;
+    typedef typename SH::LAY LAY;
+    constexpr int RS = LAY::RS, CS = CB + 1;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* tw = reinterpret_cast<C*>(smem_raw);
+    C* buf = tw + N;
+    __shared__ unsigned s_item;
+    const int tid = threadIdx.x;
+    load_stage_twiddles<T, N>(tw);
+    const unsigned rounds = (unsigned)nplanes + 2 * LAG;
+    const unsigned total = rounds * 3 * ITEMS;
+#pragma unroll 1
+    for (;;) {
+        __syncthreads();  // the previous item's last reads of s_item and of the exchange buffers
+        if (tid == 0) s_item = *(volatile unsigned*)sync.error ? total : atomicAdd(sync.queue, 1u);
+        __syncthreads();
+        const unsigned it = s_item;
+        if (it >= total) break;
+        const int r = (int)(it / (3 * ITEMS)), k = (int)(it % (3 * ITEMS));
+        const int phase = k / ITEMS, blk = k % ITEMS;
+        const int plane = r - phase * LAG;
+        if (plane < 0 || plane >= nplanes) continue;
+        const size_t pbase = (size_t)plane * N * N;
+        const int kz = plane % (M + 1);
+        const int field = plane / (M + 1);
+        const double kf = op.kf_arr ? op.kf_arr[field] : op.kf;
+        const T kfT = T(kf);
+        if (phase == 0) {
+            // ---- forward y of rows x = blk RB .. + RB (in place in A)
+            const int b = tid / Q, t = tid % Q;
+            C* row = A + pbase + (size_t)(blk * RB + b) * N;
+            C v[1][8];
+#pragma unroll
+            for (int m = 0; m < 8; ++m) v[0][m] = __ldcg(row + t + m * Q);
+            RowEx<C, 1, true, LAY> ex{buf, RB, RS, b, 0};
+            fft_regs<N, 1, false>(v, t, tw, ex);
+#pragma unroll
+            for (int m = 0; m < 8; ++m) row[t + m * Q] = v[0][m];
+        } else if (phase == 1) {
+            // ---- x pass of columns c = blk CB .. + CB: forward x, per-mode operator, phi and
+            //      -i kx phi back along x (phi in place in A, -i kx phi to B)
+            mid_wait(sync.done_y + plane, ITEMS, sync.error);
+            const int b = tid % CB, t = tid / CB;
+            const int c = blk * CB + b;
+            C* base = A + pbase;
+            C v[2][8];
+#pragma unroll
+            for (int m = 0; m < 8; ++m) v[0][m] = __ldcg(base + (size_t)(t + m * Q) * N + c);
+            ColEx<C, N> ex{buf, CS, b};
+            fft_regs<N, 1, false>(v, t, tw, ex);
+            const int ny = (c < M) ? c : c - N;
+            const T coefT = T(op.coef) / (kfT * kfT);
+            const T kf2T = T(kf * kf);
+#pragma unroll
+            for (int m = 0; m < 8; ++m) {
+                const int i = t + m * Q;
+                const int nx = (i < M) ? i : i - N;
+                const int n2 = nx * nx + ny * ny + kz * kz;
+                const C phi = mode_op<T, KIND, N>(op, v[0][m], nx, ny, kz, n2, field, kf, kfT, coefT, kf2T,
+                                                  reinterpret_cast<C*>(op.phi_old) + pbase + (size_t)i * N + c);
+                v[0][m] = phi;
+                const T kx = (2 * nx == -N) ? T(0) : kfT * T(nx);
+                v[1][m] = cmake<C>(phi.y * kx, -phi.x * kx);  // -i kx phi
+            }
+            fft_regs<N, 2, true>(v, t, tw, ex);
+#pragma unroll
+            for (int m = 0; m < 8; ++m) {
+                base[(size_t)(t + m * Q) * N + c] = v[0][m];
+                B[pbase + (size_t)(t + m * Q) * N + c] = v[1][m];
+            }
+        } else {
+            // ---- inverse y of rows x = blk RB .. + RB: A <- IFFT_y(A), C <- IFFT_y(-i ky A),
+            //      B <- IFFT_y(B)
+            mid_wait(sync.done_x + plane, ITEMS, sync.error);
+            const int b = tid / Q, t = tid % Q;
+            const size_t ro = pbase + (size_t)(blk * RB + b) * N;
+            C v[2][8];
+#pragma unroll
+            for (int m = 0; m < 8; ++m) {
+                const int i = t + m * Q;
+                const C a = __ldcg(A + ro + i);
+                v[0][m] = a;
+                const int ny = (i < M) ? i : i - N;
+                const T ky = (2 * ny == -N) ? T(0) : kfT * T(ny);
+                v[1][m] = cmake<C>(a.y * ky, -a.x * ky);
+            }
+            RowEx<C, 2, false, LAY> ex{buf, RB, RS, b, 0};
+            fft_regs<N, 2, true>(v, t, tw, ex);
+#pragma unroll
+            for (int m = 0; m < 8; ++m) {
+                A[ro + t + m * Q] = v[0][m];
+                Cs[ro + t + m * Q] = v[1][m];
+            }
+#pragma unroll
+            for (int m = 0; m < 8; ++m) v[0][m] = __ldcg(B + ro + t + m * Q);
+            RowEx<C, 1, false, LAY> ex1{buf, RB, RS, b, 0};
+            fft_regs<N, 1, true>(v, t, tw, ex1);
+#pragma unroll
+            for (int m = 0; m < 8; ++m) B[ro + t + m * Q] = v[0][m];
+        }
+        if (phase < 2) {
+            __syncthreads();  // every store of the item is made before it is counted
+            if (tid == 0) {
+                __threadfence();
+                atomicAdd((phase == 0 ? sync.done_y : sync.done_x) + plane, 1u);
             }
         }
     }
@@ -716,6 +902,30 @@ cudaError_t x_cols_n(cplx<T>* data, cplx<T>* out2, int nplanes, const SpecOp& op
     return cudaGetLastError();
 }
 
+
+template <typename T, int LOGN>
+cudaError_t middle_n(cplx<T>* A, cplx<T>* B, cplx<T>* Cs, int nplanes, const SpecOp& op, unsigned* sync_words,
+                     cudaStream_t st) {
+    typedef MidShape<T, LOGN> SH;
+    const void* fn = op.kind == OP_GR ? (const void*)k_mid<T, LOGN, OP_GR> : (const void*)k_mid<T, LOGN, OP_NEWTON>;
+    cudaError_t e = set_smem(fn, SH::SMEM);
+    if (e != cudaSuccess) return e;
+    int per_sm = 1;
+    e = resident_ctas(fn, SH::THREADS, SH::SMEM, &per_sm);
+    if (e != cudaSuccess) return e;
+    // the queue and the counters start at zero; the error word after them stays set once set
+    e = cudaMemsetAsync(sync_words, 0, sizeof(unsigned) * (4 + 2 * (size_t)nplanes), st);
+    if (e != cudaSuccess) return e;
+    MidSync sync{sync_words, sync_words + 4, sync_words + 4 + nplanes, sync_words + 4 + 2 * (size_t)nplanes};
+    const int64_t items = (int64_t)(nplanes + 2 * SH::LAG) * 3 * SH::ITEMS;
+    const unsigned grid = (unsigned)std::min<int64_t>(items, (int64_t)per_sm * num_sms());
+    if (op.kind == OP_GR)
+        k_mid<T, LOGN, OP_GR><<<grid, SH::THREADS, SH::SMEM, st>>>(A, B, Cs, op, nplanes, sync);
+    else
+        k_mid<T, LOGN, OP_NEWTON><<<grid, SH::THREADS, SH::SMEM, st>>>(A, B, Cs, op, nplanes, sync);
+    return cudaGetLastError();
+}
+
 template <typename T, int LOGN>
 cudaError_t x_adj_n(const cplx<T>* V, cplx<T>* out, double kf, double coef, float* zero, int64_t nzero,
                     cudaStream_t st) {
@@ -780,6 +990,20 @@ template <typename T>
 cudaError_t y_rows_grad3(cplx<T>* A, cplx<T>* B, cplx<T>* Cc, int64_t nrows, int n, double kf, cudaStream_t st,
                          const double* kf_arr, int64_t rows_per_field) {
     PM_DISPATCH_LOGN(n, (y_grad3_n<T, LG>(A, B, A, B, Cc, nrows, kf, st, kf_arr, rows_per_field)))
+}
+
+// The fused middle passes (forward y, x with op, inverse y with the y gradient) on meshes of
+// 256^3 and up; cudaErrorNotSupported for other sizes (the caller runs the separate passes).
+template <typename T>
+cudaError_t fft_middle(cplx<T>* A, cplx<T>* B, cplx<T>* Cs, int nplanes, int n, const SpecOp& op, unsigned* sync_words,
+                       cudaStream_t st) {
+    if (op.kind != OP_NEWTON && op.kind != OP_GR) return cudaErrorInvalidValue;
+    switch (ilog2(n)) {
+        case 8: return middle_n<T, 8>(A, B, Cs, nplanes, op, sync_words, st);
+        case 9: return middle_n<T, 9>(A, B, Cs, nplanes, op, sync_words, st);
+        case 10: return middle_n<T, 10>(A, B, Cs, nplanes, op, sync_words, st);
+        default: return cudaErrorNotSupported;
+    }
 }
 
 template <typename T>

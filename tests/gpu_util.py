@@ -51,3 +51,13 @@ def min_image(d):
 def positions_box_units(x):
     """Box-fraction positions from ticks (exact) or FP64 fractions."""
     return x.astype(np.float64) * 2.0**-32 if x.dtype == np.uint32 else x
+
+
+def bk_abs_scale(delta, box, edges, m):
+    """Per triangle (V^2/N^9) sum |d1 d2 d3| / N_tri, the oracle's estimator applied to the mode
+    moduli |delta_n|: the scale to which any floating-point evaluation of a triangle's sum of
+    products is accurate (its terms' absolute sum)."""
+    from oracle import stats
+    n = delta.shape[0]
+    mod = np.fft.irfftn(np.abs(np.fft.rfftn(delta)), s=(n, n, n), axes=(0, 1, 2))
+    return stats.bispectrum(mod, box, edges, M=m)[1]

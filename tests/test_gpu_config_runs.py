@@ -19,18 +19,11 @@ import pytest
 import inputs
 from oracle import cic, gravity, ic, pm as opm, stats
 from oracle.cosmology import Cosmology
-from tests.gpu_util import lib, to_dev, to_host, torch
+from tests.gpu_util import bk_abs_scale, lib, to_dev, to_host, torch
 
 pytestmark = pytest.mark.gpu
 
 A_I, A_F = 1.0 / 51.0, 1.0
-
-
-def _bk_abs_scale(delta, box, edges, m):
-    """Per triangle (V^2/N^9) sum |d1 d2 d3| / N_tri: the estimator on the moduli |delta_n|."""
-    n = delta.shape[0]
-    mod = np.fft.irfftn(np.abs(np.fft.rfftn(delta)), s=(n, n, n), axes=(0, 1, 2))
-    return stats.bispectrum(mod, box, edges, M=m)[1]
 
 
 @pytest.mark.slow
@@ -58,7 +51,7 @@ def test_combined_run_check_case_fp32_matches_fp64_oracle():
     delta_o = cic.density_contrast(ref.x, n)
     ko, po, no = stats.power_spectrum(delta_o, box, e64)
     tri, bo, co = stats.bispectrum(delta_o, box, eb, M=m)
-    scale = _bk_abs_scale(delta_o, box, eb, m)
+    scale = bk_abs_scale(delta_o, box, eb, m)
 
     np.testing.assert_array_equal(ng, no)
     ok = no > 0

@@ -1,0 +1,59 @@
+"""The fused middle passes of the force evaluation (forward y, x with the Green's function or
+the Poisson-gauge constraint, inverse y, in one persistent launch over the kz planes) against
+the three separate passes and against the FP64 oracle, on the mesh sizes that use them
+(FP32, 256^3 and up)."""
+import numpy as np
+import pytest
+
+from oracle import cic, gravity, ic
+from oracle.cosmology import Cosmology
+from tests.gpu_util import lib, rel_l2, to_host, torch
+
+pytestmark = pytest.mark.gpu
+
+
+def _kicks(pm, cfg, seed, steps, fused):
+    run = pm.PMRun(cfg)
+    pm.pm_set_fused_fft(run.ctx, fused)
+    run.ic(seed=seed)
+    _, p = run.particles()
+    p0 = p.to(torch.float64).clone()
+    run.step(steps)
+    _, p = run.particles()
+    dp = (p.to(torch.float64) - p0).cpu().numpy()
+    x = run.density().cpu().numpy()
+    del run
+    torch.cuda.empty_cache()
+    return dp, x
+
+
+@pytest.mark.parametrize("mode,n_lo", [(0, 0), (1, 4)])
+@pytest.mark.parametrize("np_side,nmesh", [(128, 256), (256, 256), (256, 512)])
+def test_fused_middle_passes_equal_the_separate_passes(mode, n_lo, np_side, nmesh):
+    # the same butterflies, twiddles and per-mode operator in either form: the runs differ only
+    # by the summation order of the deposit's float atomics (~1e-7 of the density)
+    pm = lib()
+    box = 2000.0 if mode == 0 else 8000.0
+    cfg = pm.make_config(np_side, nmesh, box, 1.0 / 51.0, 1.0, 20, mode=mode, n_lo=n_lo)
+    dpf, df = _kicks(pm, cfg, 4, 3, True)
+    dps, ds = _kicks(pm, cfg, 4, 3, False)
+    assert np.max(np.abs(dpf)) > 0
+    assert rel_l2(dpf, dps) < 1e-5
+    assert rel_l2(df, ds) < 1e-5
+
+
+@pytest.mark.slow
+def test_fused_force_of_one_step_matches_the_oracle():
+    # 128^3 particles on a 256^3 mesh, L = 2000 Mpc/h: the kick of the first step from the ZA ICs
+    # is K(a0, a_1/2) g(x0); the oracle evaluates g from its own ICs of the same seed
+    pm = lib()
+    np_side, n, box, steps, a_i = 128, 256, 2000.0, 20, 1.0 / 51.0
+    dp, _ = _kicks(pm, pm.make_config(np_side, n, box, a_i, 1.0, steps), 6, 1, True)
+    c = Cosmology()
+    x0, _ = ic.zeldovich(c, np_side, box, a_i, seed=6, fixed=True)
+    a1 = a_i + (1.0 - a_i) / steps
+    K = c.kick_factor(a_i, 0.5 * (a_i + a1))
+    phik = gravity.newton_potential_k(np.fft.rfftn(cic.density_contrast(x0, n)), n, box, c.omega_m)
+    g = gravity.gradient_force(phik, n, box)
+    want = K * np.stack([cic.interpolate(g[j], x0) for j in range(3)])
+    assert rel_l2(dp, want) < 1e-5
