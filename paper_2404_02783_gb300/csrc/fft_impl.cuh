@@ -596,7 +596,9 @@ template <typename T, int LOGN> struct MidShape {
     static constexpr int RB = THREADS / QN;  // rows of a y item
     static constexpr int CB = THREADS / QN;  // columns of an x item
     static constexpr int ITEMS = N / RB;     // items of each phase per plane
-    static constexpr int LAG = 3;            // rounds between the phases of one plane
+    // rounds between the phases of one plane: a dependency is handed out at least ~640 items
+    // (two CTAs per SM on 152 SMs, twice over) before the items that wait for it
+    static constexpr int LAG = (3 * ITEMS >= 640) ? 3 : 640 / (3 * ITEMS) + 1;
     typedef RowLayout<N, false> LAY;
     // twiddles + the larger of the y exchange (two rows buffers of RB rows) and the x exchange
     // (two sequences of N x (CB + 1))
