@@ -219,17 +219,21 @@ def start_of_timed_steps(pm, torch, run, k):
     torch.cuda.synchronize()
 
 
-def bench_precision(pm, torch, args, prec, rank, world, clocks=None, fused_fft=True):
+def bench_precision(pm, torch, args, prec, rank, world, clocks=None, fft_threads=None):
     """The last K steps of the fixed GRID_STEPS-step run (z = 50 -> 0; the closing half kick
     included), after W warm-up steps taken on the same context from the ICs; then the same K
     steps again with the library's per-phase events on (the kernel rooflines cover the same
     steps as the headline)."""
     cfg = pm.make_config(args.np, args.nmesh, args.box, A_INIT, A_FINAL, GRID_STEPS, precision=prec)
     run = pm.PMRun(cfg)
-    pm.pm_set_fused_fft(run.ctx, fused_fft)
     run.seed = 1 + rank
     run.ic(seed=run.seed)
     run.step(args.warmup)
+    if fft_threads is None:  # the autotuner picks the form of the middle FFT passes
+        tuned = pm.pm_autotune_fft(run.ctx)
+    else:
+        pm.pm_set_fused_fft(run.ctx, fft_threads)
+        tuned = (fft_threads, None)
     start_of_timed_steps(pm, torch, run, args.steps)
     if clocks:
         clocks.mark("t0")
@@ -246,7 +250,7 @@ def bench_precision(pm, torch, args, prec, rank, world, clocks=None, fused_fft=T
     del run
     torch.cuda.synchronize()
     torch.cuda.empty_cache()
-    return ms, phases
+    return ms, phases, tuned
 
 
 def roofline(phases, np_side, n, fp64, peak, peak_kind, fused_fft=True):
@@ -870,34 +874,37 @@ def main():
     peak, peak_kind = peaks()
     clocks = Clocks(local if world > 1 else 0)
     clocks.start()
-    ms32, ph32 = bench_precision(pm, torch, args, pm.PM_FP32_FIXED, rank, world, clocks)
+    ms32, ph32, tuned = bench_precision(pm, torch, args, pm.PM_FP32_FIXED, rank, world, clocks)
     clk = clocks.stop()
     value = world * args.np**3 * args.steps / (ms32 * 1e-3)
     ms_step = ms32 / args.steps
-    roof, table32 = roofline(ph32, args.np, args.nmesh, False, peak, peak_kind)
+    fused = tuned[0] > 0
+    roof, table32 = roofline(ph32, args.np, args.nmesh, False, peak, peak_kind, fused_fft=fused)
     sb = step_bytes(args.np, args.nmesh, False)
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded Philox phases, EH no-wiggle LCDM)",
            "config": config, "clocks": clk,
-           "gpu_launches": launches_per_step(args.np, args.nmesh, False) * (args.steps + 1),  # + the closing kick
+           "gpu_launches": launches_per_step(args.np, args.nmesh, False, fused) * (args.steps + 1),  # + closing kick
            "roofline": roof,
            "step_roofline": {"bytes_per_step": sb, "achieved": round(sb / (ms_step * 1e-3) / 1e9, 1),
                              "peak": peak, "unit": "GB/s", "frac": round(sb / (ms_step * 1e-3) / 1e9 / peak, 4),
                              "bytes_model": "60 B/particle + 40 B/cell"},
-           "phases_fp32": table32}
+           "phases_fp32": table32,
+           "fft_middle": {"threads": tuned[0], "tuned_ms": tuned[1],
+                          "what": "form of the forward y / x / inverse y passes picked by pm_autotune_fft: "
+                                  "0 = three launches, else the CTA size of the fused persistent kernel"}}
     if fused_middle(args.nmesh, False) and not args.no_compare:
-        ms_sep, ph_sep = bench_precision(pm, torch, args, pm.PM_FP32_FIXED, rank, world, fused_fft=False)
-        _, table_sep = roofline(ph_sep, args.np, args.nmesh, False, peak, peak_kind, fused_fft=False)
-        out["separate_fft_passes"] = {
-            "ms_per_step": ms_sep / args.steps,
-            "value": world * args.np**3 * args.steps / (ms_sep * 1e-3),
-            "step_roofline_frac": round(sb / (ms_sep / args.steps * 1e-3) / 1e9 / peak, 4),
-            "phases": table_sep,
-            "what": "the same steps with the forward y, x and inverse y passes as three launches "
-                    "(pm_set_fused_fft off) instead of the fused persistent kernel"}
+        other = 0 if fused else 512
+        ms_o, ph_o, _ = bench_precision(pm, torch, args, pm.PM_FP32_FIXED, rank, world, fft_threads=other)
+        _, table_o = roofline(ph_o, args.np, args.nmesh, False, peak, peak_kind, fused_fft=other > 0)
+        out["fft_middle"]["other_form"] = {
+            "threads": other, "ms_per_step": ms_o / args.steps,
+            "value": world * args.np**3 * args.steps / (ms_o * 1e-3),
+            "step_roofline_frac": round(sb / (ms_o / args.steps * 1e-3) / 1e9 / peak, 4),
+            "phases": table_o}
     if not args.no_fp64:
-        ms64, ph64 = bench_precision(pm, torch, args, pm.PM_FP64, rank, world)
+        ms64, ph64, _ = bench_precision(pm, torch, args, pm.PM_FP64, rank, world)
         sb64 = step_bytes(args.np, args.nmesh, True)
         roof64, table64 = roofline(ph64, args.np, args.nmesh, True, peak, peak_kind)
         out["fp64_plain"] = {"value": world * args.np**3 * args.steps / (ms64 * 1e-3), "unit": UNIT,

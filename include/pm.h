@@ -180,13 +180,20 @@ pm_status pm_state(pm_ctx* ctx, int* step, double* a, int* synchronised);
 
 /* The three middle passes of a force evaluation with the spectral gradient in FP32 on meshes
  * of 256^3 and up -- forward y, x with the Green's function or Poisson-gauge constraint and the
- * x gradient, inverse y with the y gradient -- run as one persistent kernel, kz plane by kz
- * plane, so that each plane's intermediate spectra are re-read from L2 instead of HBM
- * (enable != 0, the default), or as three separate launches (0).  The results are the same
- * bit for bit.  The persistent kernel's items wait for the items they depend on with bounded
- * polls; a wait that gives up (it cannot under correct operation) sets an error word that
- * pm_power and pm_timings report as PM_ERR_TIMEOUT. */
-pm_status pm_set_fused_fft(pm_ctx* ctx, int enable);
+ * x gradient, inverse y with the y gradient -- run either as three separate launches
+ * (threads = 0, the default) or as one persistent kernel of CTAs of `threads` (256, 512 or
+ * 1024) that walks the kz planes, so that each plane's intermediate spectra are re-read from L2
+ * instead of HBM.  The results are the same up to the summation order of the deposit.  The
+ * persistent kernel's items wait for the items they depend on with bounded polls; a wait that
+ * gives up (it cannot under correct operation) sets an error word that pm_power and pm_timings
+ * report as PM_ERR_TIMEOUT.  Other values: PM_ERR_INVALID_ARG.  Contexts the fused form does not
+ * apply to ignore the setting.
+ * pm_autotune_fft times the middle passes in each form (three runs each on the context's
+ * spectrum buffers, after a warm-up, CUDA events on the context stream) and keeps the fastest:
+ * *threads_out its CTA size (0 = separate), *ms_out its time (either may be NULL).  It touches
+ * only the spectrum buffers, so it may run at any point of a run.  Synchronises. */
+pm_status pm_set_fused_fft(pm_ctx* ctx, int threads);
+pm_status pm_autotune_fft(pm_ctx* ctx, int* threads_out, double* ms_out);
 
 /* Per-phase device timing of pm_step with CUDA events recorded on the context
  * stream around each kernel of a force evaluation and update.  pm_profile(ctx, 1)

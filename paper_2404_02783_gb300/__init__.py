@@ -30,7 +30,7 @@ _STATUS = {0: "PM_OK", 1: "PM_ERR_INVALID_ARG", 2: "PM_ERR_CUDA", 3: "PM_ERR_WOR
 
 # every entry point declared in include/pm.h
 EXPORTS = ("pm_workspace_size", "pm_init", "pm_destroy", "pm_ic_zeldovich", "pm_step", "pm_particles",
-           "pm_set_particles", "pm_set_state", "pm_state", "pm_set_fused_fft", "pm_profile", "pm_timings", "pm_density", "pm_potential", "pm_displacement_correction", "pm_power", "pm_halo_proxy", "pm_linear_bias",
+           "pm_set_particles", "pm_set_state", "pm_state", "pm_set_fused_fft", "pm_autotune_fft", "pm_profile", "pm_timings", "pm_density", "pm_potential", "pm_displacement_correction", "pm_power", "pm_halo_proxy", "pm_linear_bias",
            "pm_bispectrum_scratch_size", "pm_bispectrum", "pm_triangle_index", "pm_b1_gr_theory", "pm_cic_deposit", "pm_cic_interp",
            "pm_adjoint_scratch_size", "pm_adjoint_record", "pm_adjoint_run", "pm_loss_grad", "pm_displacement", "pm_batch_workspace_size", "pm_batch_init", "pm_batch_destroy", "pm_batch_context", "pm_batch_ic",
            "pm_batch_step", "pm_batch_state", "pm_batch_power", "pm_batch_bias", "pm_batch_set_chunk", "pm_batch_autotune",
@@ -85,6 +85,7 @@ def lib():
         "pm_set_state": (vp, vp, vp, i, i),
         "pm_state": (vp, ctypes.POINTER(i), pd, ctypes.POINTER(i)),
         "pm_set_fused_fft": (vp, i),
+        "pm_autotune_fft": (vp, ctypes.POINTER(i), pd),
         "pm_profile": (vp, i),
         "pm_timings": (vp, pd, ctypes.POINTER(i64)),
         "pm_density": (vp, vp),
@@ -218,8 +219,16 @@ def pm_state(ctx):
 PHASES = ("deposit", "fft_zy_fwd", "fft_x_green", "fft_yz_inv", "kick_drift")
 
 
-def pm_set_fused_fft(ctx, enable=True):
-    _check(lib().pm_set_fused_fft(ctx, int(bool(enable))))
+def pm_set_fused_fft(ctx, threads):
+    """CTA size of the fused middle FFT passes (256, 512, 1024), or 0 for the separate passes."""
+    _check(lib().pm_set_fused_fft(ctx, int(threads)))
+
+
+def pm_autotune_fft(ctx):
+    """Time the middle FFT passes in each form and keep the fastest: (threads, ms)."""
+    t, ms = ctypes.c_int(), ctypes.c_double()
+    _check(lib().pm_autotune_fft(ctx, ctypes.byref(t), ctypes.byref(ms)))
+    return t.value, ms.value
 
 
 def pm_profile(ctx, enable=True):

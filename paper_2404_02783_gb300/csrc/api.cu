@@ -170,8 +170,15 @@ struct pm_ctx {
         }
     };
     AdjSession* adj = nullptr;
-    // the fused middle passes of the force evaluation are used where they apply (pm_tune)
-    bool mid_enabled = true;
+    // CTA size of the fused middle passes of the force evaluation (0: the separate passes;
+    // pm_set_fused_fft, pm_autotune_fft)
+    int mid_threads = 0;
+    // integer triangle counts of the last bispectrum geometry (pm_bispectrum)
+    struct BkCounts {
+        int n = 0, m = 0;
+        std::vector<double> edges, counts;
+    };
+    BkCounts bk_counts;
     ~pm_ctx() {
         delete adj;
         if (st2) cudaStreamDestroy(st2);
@@ -284,10 +291,11 @@ pm_status current_density(pm_ctx* c, const void** rho_out) {
 // Force meshes g = -grad phi of the current particles at scale factor a.
 bool fused_update(const pm_ctx* c) { return ikd_deposit_supported(c->np, c->cfg.precision, c->n); }
 // The forward y, x and inverse y passes of the spectral force as one persistent launch (FP32,
-// meshes of 256^3 and up), unless switched off for the context.
-bool fused_middle(const pm_ctx* c) {
-    return !c->fp64() && c->cfg.gradient == PM_GRAD_SPECTRAL && c->n >= 256 && c->mid_enabled;
+// meshes of 256^3 and up) when the context has a CTA size for it.
+bool fused_middle_applies(const pm_ctx* c) {
+    return !c->fp64() && c->cfg.gradient == PM_GRAD_SPECTRAL && c->n >= 256;
 }
+bool fused_middle(const pm_ctx* c) { return fused_middle_applies(c) && c->mid_threads > 0; }
 
 // The fused middle passes' error word (set when one of their bounded waits gave up; it stays
 // set): PM_ERR_TIMEOUT if it is.  Synchronises the context stream.
@@ -356,7 +364,7 @@ pm_status compute_forces_t(pm_ctx* c, double a) {
         // z r2c above left the half spectrum in s0 before its forward y pass (see forward_to_y)
         {
             Phase ph(c, PM_PHASE_FFT_X_GREEN);
-            PM_CK(fft_middle<T>(s0, s1, s2, n / 2 + 1, n, op, (unsigned*)c->at(c->L.mid), c->st));
+            PM_CK(fft_middle<T>(s0, s1, s2, n / 2 + 1, n, op, (unsigned*)c->at(c->L.mid), c->mid_threads, c->st));
         }
         Phase ph(c, PM_PHASE_FFT_YZ_INV);
         const cplx<T>* in[3] = {s1, s2, s0};  // IFFT_y(-i kx phi), IFFT_y(-i ky phi), IFFT_y(phi) (-i kz)
@@ -542,33 +550,51 @@ BkLayout bk_plan(int sT, int m, int nbins) {
     return B;
 }
 
+// Integer triangle counts N_ijl of the bin triplets on the m grid for an n^3 field, cached per
+// (n, m, edges): the FFT identity on the indicator fields, run in FP64 (the FP32 sums of counts of
+// 1e6 - 1e7 configurations are off by units) in the scratch's spectrum and field areas, which
+// hold nbins FP64 spectra and fields in either precision.
+pm_status bk_counts(pm_ctx* c, int nbins, const double* edges, int m, unsigned char* scratch, const BkLayout& B,
+                    const int4* dunits, int nunits, const std::vector<double>** out) {
+    pm_ctx::BkCounts& K = c->bk_counts;
+    const std::vector<double> e(edges, edges + nbins + 1);
+    if (!(K.n == c->n && K.m == m && K.edges == e)) {
+        double2* specs = (double2*)(scratch + B.specs);
+        double* fields = (double*)(scratch + B.fields);
+        double* acc = (double*)(scratch + B.accC);
+        PM_CK(bk_indicators(c->n, specs, m, nbins, (const int16_t*)c->at(c->L.bin_of), c->st));
+        SpecOp inv;
+        inv.kind = OP_INV;
+        inv.fwd = 0;
+        PM_CK(x_cols<double>(specs, nullptr, nbins * (m / 2 + 1), m, inv, c->st));
+        PM_CK((y_rows<double, true>(specs, (int64_t)nbins * (m / 2 + 1) * m, m, c->st)));
+        const double2* in[1] = {specs};
+        double* o[1] = {fields};
+        PM_CK(z_c2r<double>(in, o, 1, m, nbins, 0u, 0.0, c->st));
+        PM_CK(cudaMemsetAsync(acc, 0, sizeof(double) * B.ntri, c->st));
+        PM_CK(bk_units<double>(fields, m, nbins, dunits, nunits, acc, c->st));
+        std::vector<double> hc(B.ntri);
+        PM_CK(cudaMemcpyAsync(hc.data(), acc, sizeof(double) * B.ntri, cudaMemcpyDeviceToHost, c->st));
+        PM_CK(cudaStreamSynchronize(c->st));
+        const double m3 = (double)m * m * m;
+        K.counts.resize(B.ntri);
+        for (int t = 0; t < B.ntri; ++t) K.counts[t] = std::rint(hc[t] / m3);
+        K.n = c->n;
+        K.m = m;
+        K.edges = e;
+    }
+    *out = &K.counts;
+    return PM_OK;
+}
+
 template <typename T>
 pm_status bispectrum_t(pm_ctx* c, const void* field, int nbins, const double* edges, int m, int deconv,
                        unsigned char* scratch, const BkLayout& B, double* b_out, double* ntri_out) {
     const int n = c->n;
     const void* f1 = field;
     if (!f1) PM_TRY(current_density(c, &f1));
-    cplx<T>* s0 = (cplx<T>*)c->at(c->L.spec[0]);
-    PM_TRY(forward_to_y<T>(c, f1, s0, n));
-    SpecOp fw;
-    fw.kind = OP_FWD_STORE;
-    fw.fwd = 1;
-    PM_CK(x_cols<T>(s0, nullptr, n / 2 + 1, n, fw, c->st));
     std::vector<int16_t> tab;
     PM_TRY(upload_bin_table(c, nbins, edges, tab));
-    cplx<T>* specs = (cplx<T>*)(scratch + B.specs);
-    T* fields = (T*)(scratch + B.fields);
-    PM_CK(bk_masks<T>(s0, n, specs, m, nbins, (const int16_t*)c->at(c->L.bin_of), (const double*)c->at(c->L.wtab),
-                      deconv ? 1 : 0, c->st));
-    const int nspec = 2 * nbins;
-    SpecOp inv;
-    inv.kind = OP_INV;
-    inv.fwd = 0;
-    PM_CK(x_cols<T>(specs, nullptr, nspec * (m / 2 + 1), m, inv, c->st));
-    PM_CK((y_rows<T, true>(specs, (int64_t)nspec * (m / 2 + 1) * m, m, c->st)));
-    const cplx<T>* in[1] = {specs};
-    T* out[1] = {fields};
-    PM_CK(z_c2r<T>(in, out, 1, m, nspec, 0u, 0.0, c->st));
     // units of up to eight triangles sharing (i, j) (see bk_units); never more units than triangles
     std::vector<int4> units;
     units.reserve(B.ntri);
@@ -576,23 +602,41 @@ pm_status bispectrum_t(pm_ctx* c, const void* field, int nbins, const double* ed
         for (int j = i; j < nbins; t += nbins - j, ++j)
             for (int lb = j / 8; 8 * lb < nbins; ++lb) units.push_back(make_int4(i, j, lb, t + std::max(j, 8 * lb) - j));
     int4* dunits = (int4*)(scratch + B.tri);
-    double* accS = (double*)(scratch + B.accS);
-    double* accC = (double*)(scratch + B.accC);
     PM_CK(cudaMemcpyAsync(dunits, units.data(), sizeof(int4) * units.size(), cudaMemcpyHostToDevice, c->st));
+    const std::vector<double>* counts = nullptr;
+    PM_TRY(bk_counts(c, nbins, edges, m, scratch, B, dunits, (int)units.size(), &counts));
+    // the data: forward transform of the field, masked spectra on the m grid, their inverse
+    // transforms, the triple-product sums
+    cplx<T>* s0 = (cplx<T>*)c->at(c->L.spec[0]);
+    PM_TRY(forward_to_y<T>(c, f1, s0, n));
+    SpecOp fw;
+    fw.kind = OP_FWD_STORE;
+    fw.fwd = 1;
+    PM_CK(x_cols<T>(s0, nullptr, n / 2 + 1, n, fw, c->st));
+    cplx<T>* specs = (cplx<T>*)(scratch + B.specs);
+    T* fields = (T*)(scratch + B.fields);
+    PM_CK(bk_masks<T>(s0, n, specs, m, nbins, (const int16_t*)c->at(c->L.bin_of), (const double*)c->at(c->L.wtab),
+                      deconv ? 1 : 0, c->st));
+    SpecOp inv;
+    inv.kind = OP_INV;
+    inv.fwd = 0;
+    PM_CK(x_cols<T>(specs, nullptr, nbins * (m / 2 + 1), m, inv, c->st));
+    PM_CK((y_rows<T, true>(specs, (int64_t)nbins * (m / 2 + 1) * m, m, c->st)));
+    const cplx<T>* in[1] = {specs};
+    T* out[1] = {fields};
+    PM_CK(z_c2r<T>(in, out, 1, m, nbins, 0u, 0.0, c->st));
+    double* accS = (double*)(scratch + B.accS);
     PM_CK(cudaMemsetAsync(accS, 0, sizeof(double) * B.ntri, c->st));
-    PM_CK(cudaMemsetAsync(accC, 0, sizeof(double) * B.ntri, c->st));
-    PM_CK(bk_units<T>(fields, m, nbins, dunits, (int)units.size(), accS, accC, c->st));
-    std::vector<double> hs(B.ntri), hc(B.ntri);
+    PM_CK(bk_units<T>(fields, m, nbins, dunits, (int)units.size(), accS, c->st));
+    std::vector<double> hs(B.ntri);
     PM_CK(cudaMemcpyAsync(hs.data(), accS, sizeof(double) * B.ntri, cudaMemcpyDeviceToHost, c->st));
-    PM_CK(cudaMemcpyAsync(hc.data(), accC, sizeof(double) * B.ntri, cudaMemcpyDeviceToHost, c->st));
     PM_CK(cudaStreamSynchronize(c->st));
     const double V = c->cfg.box * c->cfg.box * c->cfg.box;
     const double n9 = std::pow((double)n, 9);
     const double m3 = (double)m * m * m;
-    // the count of configurations is an integer: the FFT identity gives it up to rounding, so
-    // it is rounded and B divides the triangle sum by the exact count
+    // B divides the triangle sum by the exact integer count of configurations
     for (int t = 0; t < B.ntri; ++t) {
-        const double cnt = std::rint(hc[t] / m3);
+        const double cnt = (*counts)[t];
         if (ntri_out) ntri_out[t] = cnt;
         if (b_out) b_out[t] = (cnt > 0.0) ? V * V / n9 * (hs[t] / m3) / cnt : NAN;
     }
@@ -840,9 +884,71 @@ pm_status pm_step(pm_ctx* c, int n_steps) {
     return PM_OK;
 }
 
-pm_status pm_set_fused_fft(pm_ctx* c, int enable) {
+pm_status pm_set_fused_fft(pm_ctx* c, int threads) {
     if (!c) return fail(PM_ERR_INVALID_ARG, "null context");
-    c->mid_enabled = enable != 0;
+    if (threads != 0 && threads != 256 && threads != 512 && threads != 1024)
+        return fail(PM_ERR_INVALID_ARG, "threads must be 0 (separate passes), 256, 512 or 1024");
+    c->mid_threads = threads;
+    return PM_OK;
+}
+
+pm_status pm_autotune_fft(pm_ctx* c, int* threads_out, double* ms_out) {
+    if (!c) return fail(PM_ERR_INVALID_ARG, "null context");
+    if (threads_out) *threads_out = 0;
+    if (ms_out) *ms_out = 0.0;
+    if (!fused_middle_applies(c)) {
+        c->mid_threads = 0;
+        return PM_OK;
+    }
+    // the candidates run on the context's spectrum buffers (scratch between force evaluations)
+    // with the Newtonian operator, which touches no other state
+    const int n = c->n;
+    float2* s0 = (float2*)c->at(c->L.spec[0]);
+    float2* s1 = (float2*)c->at(c->L.spec[1]);
+    float2* s2 = (float2*)c->at(c->L.spec[2]);
+    SpecOp op;
+    op.kind = OP_NEWTON;
+    op.fwd = 1;
+    op.kf = c->kf;
+    op.coef = -1.5 * c->cfg.omega_m / ((double)n * n * n);
+    const int64_t rows = (int64_t)(n / 2 + 1) * n;
+    auto run = [&](int threads) -> cudaError_t {
+        if (threads == 0) {
+            cudaError_t e = y_rows<float, false>(s0, rows, n, c->st);
+            if (e == cudaSuccess) e = x_cols<float>(s0, s1, n / 2 + 1, n, op, c->st);
+            if (e == cudaSuccess) e = y_rows_grad3<float>(s0, s1, s2, rows, n, c->kf, c->st);
+            return e;
+        }
+        return fft_middle<float>(s0, s1, s2, n / 2 + 1, n, op, (unsigned*)c->at(c->L.mid), threads, c->st);
+    };
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    PM_CK(cudaEventCreate(&e0));
+    cudaError_t err = cudaEventCreate(&e1);
+    int best_t = 0;
+    double best_ms = 1e30;
+    const int cand[4] = {0, 256, 512, 1024};
+    for (int q = 0; q < 4 && err == cudaSuccess; ++q) {
+        err = run(cand[q]);  // warm-up (and the one-time attribute set-up)
+        for (int rep = 0; rep < 3 && err == cudaSuccess; ++rep) {
+            err = cudaEventRecord(e0, c->st);
+            if (err == cudaSuccess) err = run(cand[q]);
+            if (err == cudaSuccess) err = cudaEventRecord(e1, c->st);
+            if (err == cudaSuccess) err = cudaEventSynchronize(e1);
+            float ms = 0.0f;
+            if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
+            if (err == cudaSuccess && ms < best_ms) {
+                best_ms = ms;
+                best_t = cand[q];
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (err != cudaSuccess) return fail(PM_ERR_CUDA, std::string("pm_autotune_fft: ") + cudaGetErrorString(err));
+    PM_TRY(check_wait_error(c));
+    c->mid_threads = best_t;
+    if (threads_out) *threads_out = best_t;
+    if (ms_out) *ms_out = best_ms;
     return PM_OK;
 }
 
@@ -1253,7 +1359,7 @@ struct AdjSweep {
         re.st = c->st2;
         re.st2 = nullptr;
         re.adj = nullptr;
-        re.mid_enabled = false;  // its workspace is the scratch: no sync words of its own there
+        re.mid_threads = 0;  // its workspace is the scratch: no sync words of its own there
         re.ws = (unsigned char*)S.scratch;
         re.L.rho = A.re_rho;
         for (int j = 0; j < 3; ++j) re.L.spec[j] = A.re_spec[j];

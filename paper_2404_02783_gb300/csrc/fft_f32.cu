@@ -11,7 +11,8 @@ cudaError_t upload_twiddles_f32(const float2* host) {
 }
 
 PM_INST(float)
-template cudaError_t fft_middle<float>(float2*, float2*, float2*, int, int, const SpecOp&, unsigned*, cudaStream_t);
+template cudaError_t fft_middle<float>(float2*, float2*, float2*, int, int, const SpecOp&, unsigned*, int,
+                                       cudaStream_t);
 
 // out[b] = sum over rows r (in order) of rows[r nbins + b]: the per-CTA bin sums of the
 // binning x pass, combined in a fixed order.

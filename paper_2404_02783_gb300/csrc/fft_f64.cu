@@ -14,7 +14,7 @@ PM_INST(double)
 
 // The fused middle passes are built for FP32 only (FP64 runs the separate passes).
 template <>
-cudaError_t fft_middle<double>(double2*, double2*, double2*, int, int, const SpecOp&, unsigned*, cudaStream_t) {
+cudaError_t fft_middle<double>(double2*, double2*, double2*, int, int, const SpecOp&, unsigned*, int, cudaStream_t) {
     return cudaErrorNotSupported;
 }
 

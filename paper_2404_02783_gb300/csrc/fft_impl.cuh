@@ -590,15 +590,13 @@ struct MidSync {
 };
 constexpr unsigned kMidSpinLimit = 1u << 23;
 
-template <typename T, int LOGN> struct MidShape {
+template <typename T, int LOGN, int THREADS_> struct MidShape {
     static constexpr int N = 1 << LOGN, M = N / 2, QN = N / 8;
-    static constexpr int THREADS = 512;
+    static constexpr int THREADS = THREADS_;
     static constexpr int RB = THREADS / QN;  // rows of a y item
     static constexpr int CB = THREADS / QN;  // columns of an x item
     static constexpr int ITEMS = N / RB;     // items of each phase per plane
-    // rounds between the phases of one plane: a dependency is handed out at least ~640 items
-    // (two CTAs per SM on 152 SMs, twice over) before the items that wait for it
-    static constexpr int LAG = (3 * ITEMS >= 640) ? 3 : 640 / (3 * ITEMS) + 1;
+    static constexpr int MINB = 1024 / THREADS;  // 64 registers a thread
     typedef RowLayout<N, false> LAY;
     // twiddles + the larger of the y exchange (two rows buffers of RB rows) and the x exchange
     // (two sequences of N x (CB + 1))
@@ -627,13 +625,15 @@ __device__ __forceinline__ void mid_wait(const unsigned* cnt, unsigned target, u
     __syncthreads();
 }
 
-template <typename T, int LOGN, int KIND>
-__global__ void __launch_bounds__(MidShape<T, LOGN>::THREADS, 2)
-    k_mid(cplx<T>* __restrict__ A, cplx<T>* __restrict__ B, cplx<T>* __restrict__ Cs, SpecOp op, int nplanes,
+// lag: rounds between the phases of one plane, chosen by the launcher so that an item's
+// dependencies were handed out more items earlier than there are CTAs in flight.
+template <typename T, int LOGN, int KIND, int THREADS>
+__global__ void __launch_bounds__(THREADS, 1024 / THREADS)
+    k_mid(cplx<T>* __restrict__ A, cplx<T>* __restrict__ B, cplx<T>* __restrict__ Cs, SpecOp op, int nplanes, int lag,
           MidSync sync) {
     typedef cplx<T> C;
-    typedef MidShape<T, LOGN> SH;
-    constexpr int N = SH::N, M = SH::M, Q = SH::QN, RB = SH::RB, CB = SH::CB, ITEMS = SH::ITEMS, LAG = SH::LAG;
+    typedef MidShape<T, LOGN, THREADS> SH;
+    constexpr int N = SH::N, M = SH::M, Q = SH::QN, RB = SH::RB, CB = SH::CB, ITEMS = SH::ITEMS;
     typedef typename SH::LAY LAY;
     constexpr int RS = LAY::RS, CS = CB + 1;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -642,7 +642,7 @@ __global__ void __launch_bounds__(MidShape<T, LOGN>::THREADS, 2)
     __shared__ unsigned s_item;
     const int tid = threadIdx.x;
     load_stage_twiddles<T, N>(tw);
-    const unsigned rounds = (unsigned)nplanes + 2 * LAG;
+    const unsigned rounds = (unsigned)(nplanes + 2 * lag);
     const unsigned total = rounds * 3 * ITEMS;
 #pragma unroll 1
     for (;;) {
@@ -653,7 +653,7 @@ __global__ void __launch_bounds__(MidShape<T, LOGN>::THREADS, 2)
         if (it >= total) break;
         const int r = (int)(it / (3 * ITEMS)), k = (int)(it % (3 * ITEMS));
         const int phase = k / ITEMS, blk = k % ITEMS;
-        const int plane = r - phase * LAG;
+        const int plane = r - phase * lag;
         if (plane < 0 || plane >= nplanes) continue;
         const size_t pbase = (size_t)plane * N * N;
         const int kz = plane % (M + 1);
@@ -905,11 +905,12 @@ cudaError_t x_cols_n(cplx<T>* data, cplx<T>* out2, int nplanes, const SpecOp& op
 }
 
 
-template <typename T, int LOGN>
+template <typename T, int LOGN, int THREADS>
 cudaError_t middle_n(cplx<T>* A, cplx<T>* B, cplx<T>* Cs, int nplanes, const SpecOp& op, unsigned* sync_words,
                      cudaStream_t st) {
-    typedef MidShape<T, LOGN> SH;
-    const void* fn = op.kind == OP_GR ? (const void*)k_mid<T, LOGN, OP_GR> : (const void*)k_mid<T, LOGN, OP_NEWTON>;
+    typedef MidShape<T, LOGN, THREADS> SH;
+    const void* fn = op.kind == OP_GR ? (const void*)k_mid<T, LOGN, OP_GR, THREADS>
+                                      : (const void*)k_mid<T, LOGN, OP_NEWTON, THREADS>;
     cudaError_t e = set_smem(fn, SH::SMEM);
     if (e != cudaSuccess) return e;
     int per_sm = 1;
@@ -919,13 +920,24 @@ cudaError_t middle_n(cplx<T>* A, cplx<T>* B, cplx<T>* Cs, int nplanes, const Spe
     e = cudaMemsetAsync(sync_words, 0, sizeof(unsigned) * (4 + 2 * (size_t)nplanes), st);
     if (e != cudaSuccess) return e;
     MidSync sync{sync_words, sync_words + 4, sync_words + 4 + nplanes, sync_words + 4 + 2 * (size_t)nplanes};
-    const int64_t items = (int64_t)(nplanes + 2 * SH::LAG) * 3 * SH::ITEMS;
-    const unsigned grid = (unsigned)std::min<int64_t>(items, (int64_t)per_sm * num_sms());
+    const int grid = per_sm * num_sms();
+    const int lag = std::max(2, (grid + 3 * SH::ITEMS - 1) / (3 * SH::ITEMS) + 1);
     if (op.kind == OP_GR)
-        k_mid<T, LOGN, OP_GR><<<grid, SH::THREADS, SH::SMEM, st>>>(A, B, Cs, op, nplanes, sync);
+        k_mid<T, LOGN, OP_GR, THREADS><<<grid, SH::THREADS, SH::SMEM, st>>>(A, B, Cs, op, nplanes, lag, sync);
     else
-        k_mid<T, LOGN, OP_NEWTON><<<grid, SH::THREADS, SH::SMEM, st>>>(A, B, Cs, op, nplanes, sync);
+        k_mid<T, LOGN, OP_NEWTON, THREADS><<<grid, SH::THREADS, SH::SMEM, st>>>(A, B, Cs, op, nplanes, lag, sync);
     return cudaGetLastError();
+}
+
+template <typename T, int LOGN>
+cudaError_t middle_shape(cplx<T>* A, cplx<T>* B, cplx<T>* Cs, int nplanes, const SpecOp& op, unsigned* sync_words,
+                         int threads, cudaStream_t st) {
+    switch (threads) {
+        case 256: return middle_n<T, LOGN, 256>(A, B, Cs, nplanes, op, sync_words, st);
+        case 512: return middle_n<T, LOGN, 512>(A, B, Cs, nplanes, op, sync_words, st);
+        case 1024: return middle_n<T, LOGN, 1024>(A, B, Cs, nplanes, op, sync_words, st);
+        default: return cudaErrorInvalidValue;
+    }
 }
 
 template <typename T, int LOGN>
@@ -996,14 +1008,17 @@ cudaError_t y_rows_grad3(cplx<T>* A, cplx<T>* B, cplx<T>* Cc, int64_t nrows, int
 
 // The fused middle passes (forward y, x with op, inverse y with the y gradient) on meshes of
 // 256^3 and up; cudaErrorNotSupported for other sizes (the caller runs the separate passes).
+// The fused middle passes (forward y, x with op, inverse y with the y gradient) on meshes of
+// 256^3 and up with CTAs of `threads` (256, 512 or 1024); cudaErrorNotSupported for other sizes
+// (the caller runs the separate passes).
 template <typename T>
 cudaError_t fft_middle(cplx<T>* A, cplx<T>* B, cplx<T>* Cs, int nplanes, int n, const SpecOp& op, unsigned* sync_words,
-                       cudaStream_t st) {
+                       int threads, cudaStream_t st) {
     if (op.kind != OP_NEWTON && op.kind != OP_GR) return cudaErrorInvalidValue;
     switch (ilog2(n)) {
-        case 8: return middle_n<T, 8>(A, B, Cs, nplanes, op, sync_words, st);
-        case 9: return middle_n<T, 9>(A, B, Cs, nplanes, op, sync_words, st);
-        case 10: return middle_n<T, 10>(A, B, Cs, nplanes, op, sync_words, st);
+        case 8: return middle_shape<T, 8>(A, B, Cs, nplanes, op, sync_words, threads, st);
+        case 9: return middle_shape<T, 9>(A, B, Cs, nplanes, op, sync_words, threads, st);
+        case 10: return middle_shape<T, 10>(A, B, Cs, nplanes, op, sync_words, threads, st);
         default: return cudaErrorNotSupported;
     }
 }

@@ -96,14 +96,15 @@ template <typename T>
 cudaError_t x_adj(const cplx<T>* V, cplx<T>* out, int n, double kf, double coef, cudaStream_t st,
                   float* zero = nullptr, int64_t nzero = 0);
 // Forward y, x with the per-mode operator op (OP_NEWTON or OP_GR) and inverse y with the y
-// gradient of nplanes kz planes in one persistent launch (FP32, n = 256, 512, 1024): on entry
+// gradient of nplanes kz planes in one persistent launch of CTAs of `threads` (256, 512, 1024)
+// (FP32, n = 256, 512, 1024): on entry
 // A holds the z pass's half spectrum; on exit A = IFFT_y(phi), B = IFFT_y(-i kx phi),
 // C = IFFT_y(-i ky phi), as after x_cols + y_rows_grad3.  sync_words: mid_sync_words_count(nplanes)
 // device words; the call clears all but the last, the error word, which a bounded wait that
 // gave up sets (and nothing here clears).  cudaErrorNotSupported for other sizes.
 template <typename T>
 cudaError_t fft_middle(cplx<T>* A, cplx<T>* B, cplx<T>* C, int nplanes, int n, const SpecOp& op, unsigned* sync_words,
-                       cudaStream_t st);
+                       int threads, cudaStream_t st);
 inline size_t mid_sync_words_count(int nplanes) { return 5 + 2 * (size_t)nplanes; }
 
 // Forward z (r2c) and y passes of `batch` real meshes into spec ([field][kz][kx][ky]

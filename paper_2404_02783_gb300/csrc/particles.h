@@ -77,15 +77,16 @@ cudaError_t adj_combine(const float2* const* in, float2* out, int n, double kf, 
 cudaError_t loss_mse(float* delta, const float* target, int64_t n3, double* acc, cudaStream_t st);
 cudaError_t axpby(float* y, const float* a, const float* b, int64_t m, float alpha, float beta, cudaStream_t st);
 
-// Bispectrum: fill the m-grid masked spectra (bins x {delta 1_b, 1_b}) from the
-// n-grid spectrum, and accumulate the triangle sums of the inverse transforms.
+// Bispectrum: fill the m-grid masked data spectra (bins x delta 1_b) from the n-grid spectrum,
+// or the indicator spectra (bins x 1_b, FP64), and accumulate the triangle sums of the
+// inverse transforms of one set.
 template <typename T>
 cudaError_t bk_masks(const cplx<T>* spec_n, int n, cplx<T>* out, int m, int nbins, const int16_t* bin_of,
                      const double* wtab, int deconv, cudaStream_t st);
+cudaError_t bk_indicators(int n, double2* out, int m, int nbins, const int16_t* bin_of, cudaStream_t st);
 // unit[u] = (i, j, lb, t): the triangles (i, j, l), l in [max(j, 8 lb), min(nbins, 8 lb + 8)),
-// whose first has index t in the i <= j <= l order; accS / accC indexed by triangle.
+// whose first has index t in the i <= j <= l order; acc indexed by triangle (zeroed by the caller).
 template <typename T>
-cudaError_t bk_units(const T* fields, int m, int nbins, const int4* unit, int nunit, double* accS, double* accC,
-                     cudaStream_t st);
+cudaError_t bk_units(const T* fields, int m, int nbins, const int4* unit, int nunit, double* acc, cudaStream_t st);
 
 }  // namespace pm

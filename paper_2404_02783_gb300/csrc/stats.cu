@@ -2,9 +2,10 @@
 //
 // sum_{n1+n2+n3=0, n_a in bins} delta_1 delta_2 delta_3 = m^-3 sum_x I_i(x) I_j(x) I_l(x)
 // with I_b = IFFT_m[delta 1_b] (unnormalised) and the triangle count is the same sum
-// over N_b = IFFT_m[1_b].  bk_masks builds the 2 nbins masked half spectra on the m
-// grid (first the nbins data fields, then the nbins indicator fields); after their
-// inverse transforms bk_units accumulates both sums for every bin triplet.
+// over N_b = IFFT_m[1_b].  bk_masks builds the nbins masked data spectra on the m grid and
+// bk_indicators the nbins indicator spectra (in FP64: their sums are integer counts, which
+// FP32 sums of 1e6 - 1e7 configurations do not resolve); after their inverse transforms
+// bk_units accumulates the triple-product sums of one set for every bin triplet.
 #include "internal.h"
 #include "particles.h"
 
@@ -38,35 +39,51 @@ cudaError_t bin_table(int16_t* tab, int64_t nmax, const double* e2, int nbins, c
     return cudaGetLastError();
 }
 
+// Bin of mode e of the m-grid half spectrum [kz][kx][ky] for an n^3 field: the bin of |n|^2,
+// -1 for the zero mode, modes beyond n/2 and modes with a Nyquist component of the n-grid.
+__device__ __forceinline__ int bk_mode_bin(int64_t e, int m, int n, const int16_t* __restrict__ bin_of, int* nx_out,
+                                           int* ny_out, int* nz_out) {
+    const int hn = n >> 1;
+    const int kz = (int)(e / ((int64_t)m * m));
+    const int rem = (int)(e - (int64_t)kz * m * m);
+    const int nx = signed_k(rem / m, m), ny = signed_k(rem % m, m), nz = kz;
+    const int ax = nx < 0 ? -nx : nx, ay = ny < 0 ? -ny : ny;
+    const int n2 = nx * nx + ny * ny + nz * nz;
+    *nx_out = nx;
+    *ny_out = ny;
+    *nz_out = nz;
+    return (n2 > 0 && n2 <= hn * hn && ax < hn && ay < hn && nz < hn) ? (int)bin_of[n2] : -1;
+}
+
+// The nbins masked data spectra delta 1_b on the m grid.
 template <typename T>
 __global__ void k_bk_masks(const cplx<T>* __restrict__ spec_n, int n, cplx<T>* __restrict__ out, int m, int nbins,
                            const int16_t* __restrict__ bin_of, const double* __restrict__ wtab, int deconv) {
     typedef cplx<T> C;
     const int64_t per = (int64_t)(m / 2 + 1) * m * m;
-    const int hn = n >> 1;
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < per; e += (int64_t)gridDim.x * blockDim.x) {
-        const int kz = (int)(e / ((int64_t)m * m));
-        const int rem = (int)(e - (int64_t)kz * m * m);
-        const int nx = signed_k(rem / m, m), ny = signed_k(rem % m, m), nz = kz;
-        const int ax = nx < 0 ? -nx : nx, ay = ny < 0 ? -ny : ny;
-        const int n2 = nx * nx + ny * ny + nz * nz;
-        int bin = -1;
+        int nx, ny, nz;
+        const int bin = bk_mode_bin(e, m, n, bin_of, &nx, &ny, &nz);
         C v = cmake<C>(T(0), T(0));
-        if (n2 > 0 && n2 <= hn * hn && ax < hn && ay < hn && nz < hn) {
-            bin = bin_of[n2];
-            if (bin >= 0) {
-                v = spec_n[((size_t)nz * n + (nx & (n - 1))) * n + (ny & (n - 1))];
-                if (deconv) {
-                    const double W = wtab[ax] * wtab[ay] * wtab[nz];
-                    v = cscale(v, T(1.0 / W));
-                }
+        if (bin >= 0) {
+            v = spec_n[((size_t)nz * n + (nx & (n - 1))) * n + (ny & (n - 1))];
+            if (deconv) {
+                const double W = wtab[nx < 0 ? -nx : nx] * wtab[ny < 0 ? -ny : ny] * wtab[nz];
+                v = cscale(v, T(1.0 / W));
             }
         }
-        const C zero = cmake<C>(T(0), T(0)), one = cmake<C>(T(1), T(0));
-        for (int b = 0; b < nbins; ++b) {
-            out[(size_t)b * per + e] = (b == bin) ? v : zero;
-            out[(size_t)(nbins + b) * per + e] = (b == bin) ? one : zero;
-        }
+        const C zero = cmake<C>(T(0), T(0));
+        for (int b = 0; b < nbins; ++b) out[(size_t)b * per + e] = (b == bin) ? v : zero;
+    }
+}
+
+// The nbins indicator spectra 1_b on the m grid, in FP64 (their triangle sums are counts).
+__global__ void k_bk_indicators(int n, double2* __restrict__ out, int m, int nbins, const int16_t* __restrict__ bin_of) {
+    const int64_t per = (int64_t)(m / 2 + 1) * m * m;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < per; e += (int64_t)gridDim.x * blockDim.x) {
+        int nx, ny, nz;
+        const int bin = bk_mode_bin(e, m, n, bin_of, &nx, &ny, &nz);
+        for (int b = 0; b < nbins; ++b) out[(size_t)b * per + e] = make_double2(b == bin ? 1.0 : 0.0, 0.0);
     }
 }
 
@@ -80,11 +97,19 @@ cudaError_t bk_masks(const cplx<T>* spec_n, int n, cplx<T>* out, int m, int nbin
     return cudaGetLastError();
 }
 
+cudaError_t bk_indicators(int n, double2* out, int m, int nbins, const int16_t* bin_of, cudaStream_t st) {
+    const int64_t per = (int64_t)(m / 2 + 1) * m * m;
+    int64_t blocks = (per + 255) / 256;
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    k_bk_indicators<<<(unsigned)blocks, 256, 0, st>>>(n, out, m, nbins, bin_of);
+    return cudaGetLastError();
+}
+
 // Blocked form of the triangle sums: a unit is (i, j, l-block of 8) and covers the triangles
 // (i, j, l) with l in [max(j, 8 lb), min(nbins, 8 lb + 8)); per point it forms I_i I_j once and
 // multiplies it into the eight I_l (read as aligned vectors), so shared-memory traffic per
-// triangle is a fraction of one scalar load.  Rows of a staged point hold the data fields at
-// [0, nbp) and the indicator fields at [nbp, 2 nbp), nbp = nbins rounded up to 8 (zero padded).
+// triangle is a fraction of one scalar load.  Rows of a staged point hold the nbins fields at
+// [0, nbp), nbp = nbins rounded up to 8 (zero padded).
 // unit = (i, j, lb, index of triangle (i, j, max(j, 8 lb)) in the i <= j <= l order).
 template <typename T> struct Vec4;
 template <> struct Vec4<float> { typedef float4 type; static constexpr int W = 4; };
@@ -92,56 +117,46 @@ template <> struct Vec4<double> { typedef double2 type; static constexpr int W =
 
 template <typename T>
 __global__ void __launch_bounds__(256, 4) k_bk_units(const T* __restrict__ f, int64_t m3, int nbins, int nbp, int npts,
-                                                  const int4* __restrict__ unit, int nunit,
-                                                  double* __restrict__ accS, double* __restrict__ accC) {
+                                                  const int4* __restrict__ unit, int nunit, double* __restrict__ acc) {
     typedef typename Vec4<T>::type V;
     constexpr int W = Vec4<T>::W;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* s = reinterpret_cast<T*>(smem_raw);
-    const int stride = 2 * nbp;
+    const int stride = nbp;
     const int tid = threadIdx.x, nthr = blockDim.x;
     const int u = blockIdx.y * nthr + tid;
     const int4 my = (u < nunit) ? unit[u] : make_int4(0, 0, 0, -1);
     const int i = my.x, j = my.y, l0 = 8 * my.z;
-    double sS[8], sC[8];
+    double sS[8];
 #pragma unroll
-    for (int q = 0; q < 8; ++q) sS[q] = sC[q] = 0.0;
-    // npts points per chunk: FP32 partial sums over a chunk, FP64 across chunks
+    for (int q = 0; q < 8; ++q) sS[q] = 0.0;
+    // npts points per chunk: partial sums over a chunk in T, FP64 across chunks
     for (int64_t c0 = (int64_t)blockIdx.x * npts; c0 < m3; c0 += (int64_t)gridDim.x * npts) {
         __syncthreads();
         for (int e = tid; e < npts * stride; e += nthr) {
             const int b = e / npts, pnt = e - b * npts;
-            const int fb = (b < nbp) ? (b < nbins ? b : -1) : (b - nbp < nbins ? nbins + b - nbp : -1);
-            s[pnt * stride + b] = (fb >= 0 && c0 + pnt < m3) ? f[(size_t)fb * m3 + c0 + pnt] : T(0);
+            s[pnt * stride + b] = (b < nbins && c0 + pnt < m3) ? f[(size_t)b * m3 + c0 + pnt] : T(0);
         }
         __syncthreads();
         if (my.w < 0) continue;
-        T ps[8], pc[8];
+        T ps[8];
 #pragma unroll
-        for (int q = 0; q < 8; ++q) ps[q] = pc[q] = T(0);
+        for (int q = 0; q < 8; ++q) ps[q] = T(0);
 #pragma unroll 4
         for (int pnt = 0; pnt < npts; ++pnt) {
             const T* row = s + pnt * stride;
-            const T a = row[i] * row[j], ac = row[nbp + i] * row[nbp + j];
+            const T a = row[i] * row[j];
             const V* dl = reinterpret_cast<const V*>(row + l0);
-            const V* cl = reinterpret_cast<const V*>(row + nbp + l0);
 #pragma unroll
             for (int h = 0; h < 8 / W; ++h) {
-                const V d = dl[h], c = cl[h];
+                const V d = dl[h];
                 const T* dv = reinterpret_cast<const T*>(&d);
-                const T* cv = reinterpret_cast<const T*>(&c);
 #pragma unroll
-                for (int w = 0; w < W; ++w) {
-                    ps[h * W + w] += a * dv[w];
-                    pc[h * W + w] += ac * cv[w];
-                }
+                for (int w = 0; w < W; ++w) ps[h * W + w] += a * dv[w];
             }
         }
 #pragma unroll
-        for (int q = 0; q < 8; ++q) {
-            sS[q] += (double)ps[q];
-            sC[q] += (double)pc[q];
-        }
+        for (int q = 0; q < 8; ++q) sS[q] += (double)ps[q];
     }
     if (my.w < 0) return;
     const int lstart = max(j, l0), lend = min(nbins, l0 + 8);
@@ -149,31 +164,28 @@ __global__ void __launch_bounds__(256, 4) k_bk_units(const T* __restrict__ f, in
     for (int q = 0; q < 8; ++q) {
         const int l = l0 + q;
         if (l < lstart || l >= lend) continue;
-        atomicAdd(&accS[my.w + (l - lstart)], sS[q]);
-        atomicAdd(&accC[my.w + (l - lstart)], sC[q]);
+        atomicAdd(&acc[my.w + (l - lstart)], sS[q]);
     }
 }
 
 template <typename T>
-cudaError_t bk_units(const T* fields, int m, int nbins, const int4* unit, int nunit, double* accS, double* accC,
-                     cudaStream_t st) {
+cudaError_t bk_units(const T* fields, int m, int nbins, const int4* unit, int nunit, double* acc, cudaStream_t st) {
     const int nthr = 256;
     const int nbp = (nbins + 7) & ~7;
     const int64_t m3 = (int64_t)m * m * m;
     // points per chunk: up to 256, the staged rows within 96 KB of shared memory
-    int npts = (int)((96 * 1024) / (sizeof(T) * 2 * nbp));
+    int npts = (int)((96 * 1024) / (sizeof(T) * nbp));
     npts = npts > 256 ? 256 : (npts < 32 ? 32 : npts & ~31);
     const int gy = (nunit + nthr - 1) / nthr;
     int64_t gx = (m3 + npts - 1) / npts;
     const int64_t cap = (152 * 8 + gy - 1) / gy;  // about eight CTAs per SM in all
     if (gx > cap) gx = cap;
-    const size_t smem = sizeof(T) * (size_t)npts * 2 * nbp;
+    const size_t smem = sizeof(T) * (size_t)npts * nbp;
     if (smem > 48 * 1024) {
         cudaError_t e = set_smem_once((const void*)k_bk_units<T>, smem);
         if (e != cudaSuccess) return e;
     }
-    k_bk_units<T><<<dim3((unsigned)gx, (unsigned)gy), nthr, smem, st>>>(fields, m3, nbins, nbp, npts, unit, nunit,
-                                                                         accS, accC);
+    k_bk_units<T><<<dim3((unsigned)gx, (unsigned)gy), nthr, smem, st>>>(fields, m3, nbins, nbp, npts, unit, nunit, acc);
     return cudaGetLastError();
 }
 
@@ -181,7 +193,7 @@ template cudaError_t bk_masks<float>(const float2*, int, float2*, int, int, cons
                                      cudaStream_t);
 template cudaError_t bk_masks<double>(const double2*, int, double2*, int, int, const int16_t*, const double*, int,
                                       cudaStream_t);
-template cudaError_t bk_units<float>(const float*, int, int, const int4*, int, double*, double*, cudaStream_t);
-template cudaError_t bk_units<double>(const double*, int, int, const int4*, int, double*, double*, cudaStream_t);
+template cudaError_t bk_units<float>(const float*, int, int, const int4*, int, double*, cudaStream_t);
+template cudaError_t bk_units<double>(const double*, int, int, const int4*, int, double*, cudaStream_t);
 
 }  // namespace pm

@@ -12,9 +12,9 @@ from tests.gpu_util import lib, rel_l2, to_host, torch
 pytestmark = pytest.mark.gpu
 
 
-def _kicks(pm, cfg, seed, steps, fused):
+def _kicks(pm, cfg, seed, steps, threads):
     run = pm.PMRun(cfg)
-    pm.pm_set_fused_fft(run.ctx, fused)
+    pm.pm_set_fused_fft(run.ctx, threads)
     run.ic(seed=seed)
     _, p = run.particles()
     p0 = p.to(torch.float64).clone()
@@ -30,16 +30,37 @@ def _kicks(pm, cfg, seed, steps, fused):
 @pytest.mark.parametrize("mode,n_lo", [(0, 0), (1, 4)])
 @pytest.mark.parametrize("np_side,nmesh", [(128, 256), (256, 256), (256, 512)])
 def test_fused_middle_passes_equal_the_separate_passes(mode, n_lo, np_side, nmesh):
-    # the same butterflies, twiddles and per-mode operator in either form: the runs differ only
-    # by the summation order of the deposit's float atomics (~1e-7 of the density)
+    # the same butterflies, twiddles and per-mode operator in either form and for every CTA size:
+    # the runs differ only by the summation order of the deposit's float atomics (~1e-7 of the density)
     pm = lib()
     box = 2000.0 if mode == 0 else 8000.0
     cfg = pm.make_config(np_side, nmesh, box, 1.0 / 51.0, 1.0, 20, mode=mode, n_lo=n_lo)
-    dpf, df = _kicks(pm, cfg, 4, 3, True)
-    dps, ds = _kicks(pm, cfg, 4, 3, False)
-    assert np.max(np.abs(dpf)) > 0
-    assert rel_l2(dpf, dps) < 1e-5
-    assert rel_l2(df, ds) < 1e-5
+    dps, ds = _kicks(pm, cfg, 4, 3, 0)
+    assert np.max(np.abs(dps)) > 0
+    for threads in (256, 512, 1024):
+        dpf, df = _kicks(pm, cfg, 4, 3, threads)
+        assert rel_l2(dpf, dps) < 1e-5
+        assert rel_l2(df, ds) < 1e-5
+
+
+def test_fft_autotuner_keeps_a_candidate_and_the_run_goes_on():
+    pm = lib()
+    run = pm.PMRun(pm.make_config(128, 256, 2000.0, 1.0 / 51.0, 1.0, 20))
+    run.ic(seed=2)
+    run.step(2)
+    threads, ms = pm.pm_autotune_fft(run.ctx)
+    assert threads in (0, 256, 512, 1024) and ms > 0
+    run.step(1)  # the tuning touched only the spectrum buffers
+    ref = pm.PMRun(pm.make_config(128, 256, 2000.0, 1.0 / 51.0, 1.0, 20))
+    ref.ic(seed=2)
+    ref.step(3)
+    xa, pa = run.particles()
+    xb, pb = ref.particles()
+    assert rel_l2(to_host(pa).astype(np.float64), to_host(pb).astype(np.float64)) < 1e-5
+    small = pm.PMRun(pm.make_config(32, 64, 500.0, 0.1, 1.0, 4))
+    assert pm.pm_autotune_fft(small.ctx) == (0, 0.0)  # the fused form does not apply there
+    with pytest.raises(pm.PMError):
+        pm.pm_set_fused_fft(run.ctx, 128)
 
 
 @pytest.mark.slow
@@ -48,7 +69,7 @@ def test_fused_force_of_one_step_matches_the_oracle():
     # is K(a0, a_1/2) g(x0); the oracle evaluates g from its own ICs of the same seed
     pm = lib()
     np_side, n, box, steps, a_i = 128, 256, 2000.0, 20, 1.0 / 51.0
-    dp, _ = _kicks(pm, pm.make_config(np_side, n, box, a_i, 1.0, steps), 6, 1, True)
+    dp, _ = _kicks(pm, pm.make_config(np_side, n, box, a_i, 1.0, steps), 6, 1, 512)
     c = Cosmology()
     x0, _ = ic.zeldovich(c, np_side, box, a_i, seed=6, fixed=True)
     a1 = a_i + (1.0 - a_i) / steps
