@@ -56,7 +56,7 @@ pm_status check_device() {
 struct Layout {
     size_t x = 0, p = 0, rho = 0, spec[3] = {0, 0, 0}, force[3] = {0, 0, 0};
     size_t phi_old = 0, island = 0, amp = 0, bin_of = 0, wtab = 0, acc = 0, mid = 0, total = 0;
-    bool gr = false, has_island = false;
+    bool gr = false, has_island = false, has_mid = false;
 };
 
 constexpr int kMaxBins = 256;
@@ -104,6 +104,7 @@ Layout plan(const pm_config& c) {
     L.wtab = take((n / 2 + 1) * 8);
     L.acc = take(2 * kMaxBins * 8);
     L.mid = take(mid_sync_words_count((int)(n / 2 + 1)) * 4);
+    L.has_mid = true;
     L.total = off;
     return L;
 }
@@ -295,11 +296,12 @@ bool fused_update(const pm_ctx* c) { return ikd_deposit_supported(c->np, c->cfg.
 bool fused_middle_applies(const pm_ctx* c) {
     return !c->fp64() && c->cfg.gradient == PM_GRAD_SPECTRAL && c->n >= 256;
 }
-bool fused_middle(const pm_ctx* c) { return fused_middle_applies(c) && c->mid_threads > 0; }
+bool fused_middle(const pm_ctx* c) { return fused_middle_applies(c) && c->mid_threads > 0 && c->L.has_mid; }
 
 // The fused middle passes' error word (set when one of their bounded waits gave up; it stays
 // set): PM_ERR_TIMEOUT if it is.  Synchronises the context stream.
 pm_status check_wait_error(pm_ctx* c) {
+    if (!c->L.has_mid) return PM_OK;  // batch views: their passes never wait
     unsigned err = 0;
     const size_t word = mid_sync_words_count(c->n / 2 + 1) - 1;
     PM_CK(cudaMemcpyAsync(&err, (unsigned*)c->at(c->L.mid) + word, sizeof(err), cudaMemcpyDeviceToHost, c->st));
@@ -896,7 +898,7 @@ pm_status pm_autotune_fft(pm_ctx* c, int* threads_out, double* ms_out) {
     if (!c) return fail(PM_ERR_INVALID_ARG, "null context");
     if (threads_out) *threads_out = 0;
     if (ms_out) *ms_out = 0.0;
-    if (!fused_middle_applies(c)) {
+    if (!fused_middle_applies(c) || !c->L.has_mid) {
         c->mid_threads = 0;
         return PM_OK;
     }

