@@ -5,6 +5,8 @@ import re
 import numpy as np
 import pytest
 
+torch = pytest.importorskip("torch")
+
 pytestmark = pytest.mark.gpu
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
@@ -19,3 +21,5 @@ def test_readme_example_runs():
     B, ntri, eq, sq = scope["B"], scope["ntri"], scope["eq"], scope["sq"]
     assert len(B) == 29 * 30 * 31 // 6 and len(eq) == 29 and len(sq) == 26
     assert scope["batch"].state()[0] == 50
+    g = scope["w"].grad
+    assert g is not None and bool(torch.isfinite(g).all()) and float(g.abs().max()) > 0
