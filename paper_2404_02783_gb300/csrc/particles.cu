@@ -678,9 +678,18 @@ __global__ void __launch_bounds__(256) k_combine_blocks(uint32_t* __restrict__ x
 #pragma unroll
             for (int j = 0; j < 3; ++j) xi[j][q] = (int32_t)(xg[j * countc + c] - xn[j * countc + c]);
         }
+        // one x plane of the r^3 target block at a time: its r x 3 target vectors are loaded
+        // before any arithmetic, so their latencies overlap instead of forming r^2 x 3 chains
 #pragma unroll 1
-        for (int ox = 0; ox < r; ++ox)
-#pragma unroll 1
+        for (int ox = 0; ox < r; ++ox) {
+            V v[r][3];
+#pragma unroll
+            for (int oy = 0; oy < r; ++oy) {
+                const int64_t t0 = ((((int64_t)(r * bx + ox) << lognt) + (r * by + oy)) << lognt) + r * bz;
+#pragma unroll
+                for (int j = 0; j < 3; ++j) v[oy][j] = *reinterpret_cast<const V*>(xt + j * countt + t0);
+            }
+#pragma unroll
             for (int oy = 0; oy < r; ++oy) {
                 const int64_t t0 = ((((int64_t)(r * bx + ox) << lognt) + (r * by + oy)) << lognt) + r * bz;
 #pragma unroll
@@ -705,12 +714,10 @@ __global__ void __launch_bounds__(256) k_combine_blocks(uint32_t* __restrict__ x
                         }
                         add[oz] = (uint32_t)qv;
                     }
-                    V* dst = reinterpret_cast<V*>(xt + j * countt + t0);
-                    V v = *dst;
-                    uint32_t* vv = reinterpret_cast<uint32_t*>(&v);
+                    uint32_t* vv = reinterpret_cast<uint32_t*>(&v[oy][j]);
 #pragma unroll
                     for (int oz = 0; oz < r; ++oz) vv[oz] += add[oz];
-                    *dst = v;
+                    *reinterpret_cast<V*>(xt + j * countt + t0) = v[oy][j];
                     if (xi_out) {
                         V w;
                         uint32_t* ww = reinterpret_cast<uint32_t*>(&w);
@@ -720,6 +727,7 @@ __global__ void __launch_bounds__(256) k_combine_blocks(uint32_t* __restrict__ x
                     }
                 }
             }
+        }
     }
 }
 

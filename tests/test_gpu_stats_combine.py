@@ -114,7 +114,7 @@ def test_bispectrum_refuses_aliasing_grid():
 
 
 @pytest.mark.parametrize("prec", [FP32, FP64])
-@pytest.mark.parametrize("ratio", [1, 2])
+@pytest.mark.parametrize("ratio", [1, 2, 4])
 def test_displacement_correction_exact(prec, ratio):
     pm = lib()
     nc = 16
