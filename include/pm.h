@@ -178,21 +178,26 @@ pm_status pm_displacement(pm_ctx* ctx, void* disp);
  * behind (0). */
 pm_status pm_state(pm_ctx* ctx, int* step, double* a, int* synchronised);
 
-/* The three middle passes of a force evaluation with the spectral gradient in FP32 on meshes
- * of 256^3 and up -- forward y, x with the Green's function or Poisson-gauge constraint and the
- * x gradient, inverse y with the y gradient -- run either as three separate launches
- * (threads = 0, the default) or as one persistent kernel of CTAs of `threads` (256, 512 or
- * 1024) that walks the kz planes, so that each plane's intermediate spectra are re-read from L2
- * instead of HBM.  The results are the same up to the summation order of the deposit.  The
- * persistent kernel's items wait for the items they depend on with bounded polls; a wait that
- * gives up (it cannot under correct operation) sets an error word that pm_power and pm_timings
- * report as PM_ERR_TIMEOUT.  Other values: PM_ERR_INVALID_ARG.  Contexts the fused form does not
- * apply to ignore the setting.
- * pm_autotune_fft times the middle passes in each form (three runs each on the context's
- * spectrum buffers, after a warm-up, CUDA events on the context stream) and keeps the fastest:
- * *threads_out its CTA size (0 = separate), *ms_out its time (either may be NULL).  It touches
- * only the spectrum buffers, so it may run at any point of a run.  Synchronises. */
-pm_status pm_set_fused_fft(pm_ctx* ctx, int threads);
+/* The three middle passes of a force evaluation with the spectral gradient in FP32 -- forward
+ * y, x with the Green's function or Poisson-gauge constraint and the x gradient, inverse y with
+ * the y gradient -- run in one of these forms (`form`):
+ *   0             three separate launches (the default);
+ *   1             whole kz planes in shared memory (meshes of 64^3 and 128^3): one CTA takes a
+ *                 plane, runs the forward y and x transforms, the per-mode operator and, for each
+ *                 force component, the inverse x and y transforms of -i k_j phi there, and writes
+ *                 the three gradient spectra (HBM sees one read and three writes of the plane);
+ *   256/512/1024  one persistent kernel of CTAs of that size over the kz planes (meshes of 256^3
+ *                 and up), each plane's intermediate spectra re-read from L2 instead of HBM; its
+ *                 items wait for the items they depend on with bounded polls, and a wait that
+ *                 gives up (it cannot under correct operation) sets an error word that pm_power
+ *                 and pm_timings report as PM_ERR_TIMEOUT.
+ * The results are the same up to the summation order of the deposit.  A form that does not
+ * apply to the context runs the separate passes.  Other values: PM_ERR_INVALID_ARG.
+ * pm_autotune_fft times the middle passes in each form that applies (three runs each on the
+ * context's spectrum buffers, after a warm-up, CUDA events on the context stream) and keeps the
+ * fastest: *threads_out the form (0 = separate), *ms_out its time (either may be NULL).  It
+ * touches only the spectrum buffers, so it may run at any point of a run.  Synchronises. */
+pm_status pm_set_fused_fft(pm_ctx* ctx, int form);
 pm_status pm_autotune_fft(pm_ctx* ctx, int* threads_out, double* ms_out);
 
 /* Per-phase device timing of pm_step with CUDA events recorded on the context
@@ -351,12 +356,19 @@ pm_status pm_batch_context(pm_batch* batch, int r, pm_ctx** view);
  * them there between its passes); 0 or nreal = one launch per pass for the whole batch
  * (the default).  The results do not depend on it.  Outside 0..nreal: PM_ERR_INVALID_ARG. */
 pm_status pm_batch_set_chunk(pm_batch* batch, int chunk);
-/* Autotuner of the batch's launch shape: times one step (replayed from a CUDA graph) for
- * chunk = nreal, nreal/2, ..., 1 (rounded up) and keeps the fastest (chunk_out, and its
- * ms per step in ms_out; either may be NULL).  It runs the step on the unperturbed
- * lattice, so it overwrites the particles: call it before pm_batch_ic (PM_ERR_STATE after
- * it).  Synchronises. */
+/* Form of the batch's middle FFT passes (as pm_set_fused_fft): 0 = separate launches, 1 = whole
+ * kz planes in shared memory (nmesh 64 or 128; otherwise the separate passes run).  Other values:
+ * PM_ERR_INVALID_ARG.  The results do not depend on it. */
+pm_status pm_batch_set_fft(pm_batch* batch, int form);
+/* Autotuner of the batch's launch shape: for each form of the middle FFT passes that applies,
+ * times one step (replayed from a CUDA graph) for chunk = nreal, nreal/2, ..., 1 (rounded up)
+ * and keeps the fastest pair (chunk_out and its ms per step in ms_out; either may be NULL;
+ * pm_batch_tuning reads both settings).  It runs the step on the unperturbed lattice (the FFT
+ * passes' cost does not depend on the particles; the update's is that of an early step), so
+ * it overwrites the particles: call it before pm_batch_ic (PM_ERR_STATE after it).
+ * Synchronises. */
 pm_status pm_batch_autotune(pm_batch* batch, int* chunk_out, double* ms_out);
+pm_status pm_batch_tuning(pm_batch* batch, int* chunk, int* fft_form);
 /* Zel'dovich ICs of every realisation from seeds[r] (as pm_ic_zeldovich, same flags). */
 pm_status pm_batch_ic(pm_batch* batch, const uint64_t* seeds, int flags);
 /* n_steps KDK steps of every realisation; use_graph != 0 records the run once (cached for

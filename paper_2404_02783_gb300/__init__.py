@@ -33,7 +33,7 @@ EXPORTS = ("pm_workspace_size", "pm_init", "pm_destroy", "pm_ic_zeldovich", "pm_
            "pm_set_particles", "pm_set_state", "pm_state", "pm_set_fused_fft", "pm_autotune_fft", "pm_profile", "pm_timings", "pm_density", "pm_potential", "pm_displacement_correction", "pm_power", "pm_halo_proxy", "pm_linear_bias",
            "pm_bispectrum_scratch_size", "pm_bispectrum", "pm_triangle_index", "pm_b1_gr_theory", "pm_cic_deposit", "pm_cic_interp",
            "pm_adjoint_scratch_size", "pm_adjoint_record", "pm_adjoint_run", "pm_loss_grad", "pm_displacement", "pm_batch_workspace_size", "pm_batch_init", "pm_batch_destroy", "pm_batch_context", "pm_batch_ic",
-           "pm_batch_step", "pm_batch_state", "pm_batch_power", "pm_batch_bias", "pm_batch_set_chunk", "pm_batch_autotune",
+           "pm_batch_step", "pm_batch_state", "pm_batch_power", "pm_batch_bias", "pm_batch_set_chunk", "pm_batch_autotune", "pm_batch_set_fft", "pm_batch_tuning",
            "pm_cell_sort_scratch_size", "pm_cell_sort", "pm_cell_sort_static", "pm_div_mode_check", "pm_fft_r2c", "pm_fft_c2r", "pm_version", "pm_last_error")
 
 
@@ -114,6 +114,8 @@ def lib():
         "pm_batch_bias": (vp, d, i, pd, d, i, pd),
         "pm_batch_set_chunk": (vp, i),
         "pm_batch_autotune": (vp, ctypes.POINTER(i), pd),
+        "pm_batch_set_fft": (vp, i),
+        "pm_batch_tuning": (vp, ctypes.POINTER(i), ctypes.POINTER(i)),
         "pm_cic_deposit": (vp, i64, i, i, d, vp, vp),
         "pm_cic_interp": (vp, i, vp, i64, i, vp, vp),
         "pm_cell_sort_scratch_size": (i64, i, ctypes.POINTER(sz)),
@@ -219,9 +221,10 @@ def pm_state(ctx):
 PHASES = ("deposit", "fft_zy_fwd", "fft_x_green", "fft_yz_inv", "kick_drift")
 
 
-def pm_set_fused_fft(ctx, threads):
-    """CTA size of the fused middle FFT passes (256, 512, 1024), or 0 for the separate passes."""
-    _check(lib().pm_set_fused_fft(ctx, int(threads)))
+def pm_set_fused_fft(ctx, form):
+    """Form of the middle FFT passes: 0 separate launches, 1 whole kz planes in shared memory
+    (64^3, 128^3), 256 / 512 / 1024 the CTA size of the persistent kernel (256^3 and up)."""
+    _check(lib().pm_set_fused_fft(ctx, int(form)))
 
 
 def pm_autotune_fft(ctx):
@@ -565,6 +568,16 @@ class PMBatch:
         c, ms = ctypes.c_int(), ctypes.c_double()
         _check(lib().pm_batch_autotune(self.h, ctypes.byref(c), ctypes.byref(ms)))
         return c.value, ms.value
+
+    def set_fft(self, form):
+        """Form of the middle FFT passes: 0 separate launches, 1 whole kz planes in shared memory."""
+        _check(lib().pm_batch_set_fft(self.h, int(form)))
+
+    def tuning(self):
+        """(realisations per launch, form of the middle FFT passes) in use."""
+        c, f = ctypes.c_int(), ctypes.c_int()
+        _check(lib().pm_batch_tuning(self.h, ctypes.byref(c), ctypes.byref(f)))
+        return c.value, f.value
 
     def ic(self, seeds, paired=False, fixed=False, lpt_order=1):
         s = np.ascontiguousarray(seeds, dtype=np.uint64)

@@ -291,12 +291,19 @@ pm_status current_density(pm_ctx* c, const void** rho_out) {
 
 // Force meshes g = -grad phi of the current particles at scale factor a.
 bool fused_update(const pm_ctx* c) { return ikd_deposit_supported(c->np, c->cfg.precision, c->n); }
-// The forward y, x and inverse y passes of the spectral force as one persistent launch (FP32,
-// meshes of 256^3 and up) when the context has a CTA size for it.
-bool fused_middle_applies(const pm_ctx* c) {
-    return !c->fp64() && c->cfg.gradient == PM_GRAD_SPECTRAL && c->n >= 256;
+// Forms of the forward y, x and inverse y passes of the spectral force (FP32): 0 = three
+// separate launches; 1 = whole kz planes in shared memory (meshes of 64^3 and 128^3);
+// 256 / 512 / 1024 = one persistent launch over the planes with CTAs of that size (256^3 and up).
+constexpr int kFormPlane = 1;
+bool form_applies(int form, const pm_ctx* c) {
+    if (c->fp64() || c->cfg.gradient != PM_GRAD_SPECTRAL) return form == 0;
+    if (form == kFormPlane) return c->n == 64 || c->n == 128;
+    if (form == 256 || form == 512 || form == 1024) return c->n >= 256 && c->L.has_mid;
+    return form == 0;
 }
-bool fused_middle(const pm_ctx* c) { return fused_middle_applies(c) && c->mid_threads > 0 && c->L.has_mid; }
+bool fused_middle_applies(const pm_ctx* c) { return form_applies(512, c); }
+bool fused_middle(const pm_ctx* c) { return c->mid_threads > 1 && form_applies(c->mid_threads, c); }
+bool plane_middle(const pm_ctx* c) { return c->mid_threads == kFormPlane && form_applies(kFormPlane, c); }
 
 // The fused middle passes' error word (set when one of their bounded waits gave up; it stays
 // set): PM_ERR_TIMEOUT if it is.  Synchronises the context stream.
@@ -318,8 +325,8 @@ pm_status compute_forces_t(pm_ctx* c, double a) {
     cplx<T>* s0 = (cplx<T>*)c->at(c->L.spec[0]);
     cplx<T>* s1 = (cplx<T>*)c->at(c->L.spec[1]);
     cplx<T>* s2 = (cplx<T>*)c->at(c->L.spec[2]);
-    if (fused_middle(c)) {
-        // the forward y pass runs inside the fused middle passes
+    if (fused_middle(c) || plane_middle(c)) {
+        // the forward y pass runs inside the fused or whole-plane middle passes
         Phase ph(c, PM_PHASE_FFT_ZY_FWD);
         PM_CK(z_r2c<T>((const T*)rho, s0, n, 1, c->st));
     } else {
@@ -362,6 +369,15 @@ pm_status compute_forces_t(pm_ctx* c, double a) {
         const cplx<T>* in[1] = {s0};
         T* out[1] = {(T*)c->force(0)};
         PM_CK(z_c2r<T>(in, out, 1, n, 1, 0u, 0.0, c->st));
+    } else if (plane_middle(c)) {
+        {
+            Phase ph(c, PM_PHASE_FFT_X_GREEN);
+            PM_CK(fft_plane<T>(s0, s1, s2, n / 2 + 1, n, op, c->st));
+        }
+        Phase ph(c, PM_PHASE_FFT_YZ_INV);
+        const cplx<T>* in[3] = {s1, s2, s0};  // -i k_j phi back along x and y, j = x, y, z
+        T* out[3] = {(T*)c->force(0), (T*)c->force(1), (T*)c->force(2)};
+        PM_CK(z_c2r<T>(in, out, 3, n, 1, 0u, c->kf, c->st));
     } else if (fused_middle(c)) {
         // z r2c above left the half spectrum in s0 before its forward y pass (see forward_to_y)
         {
@@ -886,11 +902,11 @@ pm_status pm_step(pm_ctx* c, int n_steps) {
     return PM_OK;
 }
 
-pm_status pm_set_fused_fft(pm_ctx* c, int threads) {
+pm_status pm_set_fused_fft(pm_ctx* c, int form) {
     if (!c) return fail(PM_ERR_INVALID_ARG, "null context");
-    if (threads != 0 && threads != 256 && threads != 512 && threads != 1024)
-        return fail(PM_ERR_INVALID_ARG, "threads must be 0 (separate passes), 256, 512 or 1024");
-    c->mid_threads = threads;
+    if (form != 0 && form != kFormPlane && form != 256 && form != 512 && form != 1024)
+        return fail(PM_ERR_INVALID_ARG, "form must be 0 (separate passes), 1 (whole planes), 256, 512 or 1024");
+    c->mid_threads = form;
     return PM_OK;
 }
 
@@ -898,7 +914,10 @@ pm_status pm_autotune_fft(pm_ctx* c, int* threads_out, double* ms_out) {
     if (!c) return fail(PM_ERR_INVALID_ARG, "null context");
     if (threads_out) *threads_out = 0;
     if (ms_out) *ms_out = 0.0;
-    if (!fused_middle_applies(c) || !c->L.has_mid) {
+    std::vector<int> cand = {0};
+    for (int f : {kFormPlane, 256, 512, 1024})
+        if (form_applies(f, c)) cand.push_back(f);
+    if (cand.size() == 1) {
         c->mid_threads = 0;
         return PM_OK;
     }
@@ -914,22 +933,22 @@ pm_status pm_autotune_fft(pm_ctx* c, int* threads_out, double* ms_out) {
     op.kf = c->kf;
     op.coef = -1.5 * c->cfg.omega_m / ((double)n * n * n);
     const int64_t rows = (int64_t)(n / 2 + 1) * n;
-    auto run = [&](int threads) -> cudaError_t {
-        if (threads == 0) {
+    auto run = [&](int form) -> cudaError_t {
+        if (form == 0) {
             cudaError_t e = y_rows<float, false>(s0, rows, n, c->st);
             if (e == cudaSuccess) e = x_cols<float>(s0, s1, n / 2 + 1, n, op, c->st);
             if (e == cudaSuccess) e = y_rows_grad3<float>(s0, s1, s2, rows, n, c->kf, c->st);
             return e;
         }
-        return fft_middle<float>(s0, s1, s2, n / 2 + 1, n, op, (unsigned*)c->at(c->L.mid), threads, c->st);
+        if (form == kFormPlane) return fft_plane<float>(s0, s1, s2, n / 2 + 1, n, op, c->st);
+        return fft_middle<float>(s0, s1, s2, n / 2 + 1, n, op, (unsigned*)c->at(c->L.mid), form, c->st);
     };
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     PM_CK(cudaEventCreate(&e0));
     cudaError_t err = cudaEventCreate(&e1);
     int best_t = 0;
     double best_ms = 1e30;
-    const int cand[4] = {0, 256, 512, 1024};
-    for (int q = 0; q < 4 && err == cudaSuccess; ++q) {
+    for (size_t q = 0; q < cand.size() && err == cudaSuccess; ++q) {
         err = run(cand[q]);  // warm-up (and the one-time attribute set-up)
         for (int rep = 0; rep < 3 && err == cudaSuccess; ++rep) {
             err = cudaEventRecord(e0, c->st);
@@ -1361,7 +1380,8 @@ struct AdjSweep {
         re.st = c->st2;
         re.st2 = nullptr;
         re.adj = nullptr;
-        re.mid_threads = 0;  // its workspace is the scratch: no sync words of its own there
+        // its workspace is the scratch: no sync words of its own there for the persistent form
+        re.mid_threads = (c->mid_threads == kFormPlane) ? kFormPlane : 0;
         re.ws = (unsigned char*)S.scratch;
         re.L.rho = A.re_rho;
         for (int j = 0; j < 3; ++j) re.L.spec[j] = A.re_spec[j];
@@ -1547,6 +1567,7 @@ struct pm_batch {
     bool synced = true;
     bool rho_valid = false;
     int chunk = 0;  // realisations per launch of every pass (0: the whole batch)
+    int fft_form = 0;  // middle FFT passes: 0 separate launches, 1 whole kz planes in shared memory
     bool have_ic = false;  // pm_batch_ic has run (the autotuner would overwrite the particles)
     pmhost::Cosmo cosmo;
     void* at(size_t off) const { return ws + off; }
@@ -1609,16 +1630,25 @@ pm_status batch_forces(pm_batch* b, cudaStream_t s, int r0, int c) {
     float2* s1 = (float2*)b->at(b->SPEC[1]) + r0 * nspec;
     float2* s2 = (float2*)b->at(b->SPEC[2]) + r0 * nspec;
     const double* kf = (const double*)b->at(b->KF) + r0;
-    PM_CK(forward_zy<float>(rho, s0, n, c, s));
+    const bool plane = b->fft_form == 1 && (n == 64 || n == 128);
+    if (plane) PM_CK(z_r2c<float>(rho, s0, n, c, s));
+    else PM_CK(forward_zy<float>(rho, s0, n, c, s));
     PM_CK(cudaMemsetAsync(rho, 0, sizeof(float) * c * n3, s));
     SpecOp op;
     op.kind = OP_NEWTON;
     op.fwd = 1;
     op.coef = -1.5 * b->cfg.omega_m / ((double)n * n * n);
     op.kf_arr = kf;
-    PM_CK(x_cols<float>(s0, s1, c * (M + 1), n, op, s));
     float* out[3] = {(float*)b->at(b->FORCE[0]) + r0 * n3, (float*)b->at(b->FORCE[1]) + r0 * n3,
                      (float*)b->at(b->FORCE[2]) + r0 * n3};
+    if (plane) {
+        // whole kz planes in shared memory: the three gradient spectra, then the z pass
+        PM_CK(fft_plane<float>(s0, s1, s2, c * (M + 1), n, op, s));
+        const float2* in[3] = {s1, s2, s0};
+        PM_CK(z_c2r<float>(in, out, 3, n, c, 0u, 0.0, s));
+        return PM_OK;
+    }
+    PM_CK(x_cols<float>(s0, s1, c * (M + 1), n, op, s));
     PM_CK(inverse_yz_grad<float>(s0, s1, s2, out, n, c, 0.0, s, kf));
     return PM_OK;
 }
@@ -1851,6 +1881,21 @@ pm_status pm_batch_step(pm_batch* b, int n_steps, int use_graph) {
     return PM_OK;
 }
 
+pm_status pm_batch_set_fft(pm_batch* b, int form) {
+    if (!b) return fail(PM_ERR_INVALID_ARG, "null batch");
+    if (form != 0 && form != 1) return fail(PM_ERR_INVALID_ARG, "form must be 0 (separate passes) or 1 (whole planes)");
+    batch_drop_graph(b);
+    b->fft_form = form;
+    return PM_OK;
+}
+
+pm_status pm_batch_tuning(pm_batch* b, int* chunk, int* fft_form) {
+    if (!b) return fail(PM_ERR_INVALID_ARG, "null batch");
+    if (chunk) *chunk = (b->chunk > 0 && b->chunk < b->B) ? b->chunk : b->B;
+    if (fft_form) *fft_form = (b->fft_form == 1 && (b->cfg.nmesh == 64 || b->cfg.nmesh == 128)) ? 1 : 0;
+    return PM_OK;
+}
+
 pm_status pm_batch_set_chunk(pm_batch* b, int chunk) {
     if (!b || chunk < 0 || chunk > b->B) return fail(PM_ERR_INVALID_ARG, "chunk must be in 0..nreal");
     if (chunk != b->chunk) batch_drop_graph(b);
@@ -1877,13 +1922,18 @@ pm_status pm_batch_autotune(pm_batch* b, int* chunk_out, double* ms_out) {
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     PM_CK(cudaEventCreate(&e0));
     PM_CK(cudaEventCreate(&e1));
-    int best = b->B;
+    int best = b->B, best_form = 0;
     double best_ms = 1e300;
     pm_status st = PM_OK;
-    // candidates: the whole batch, then halves down to one realisation per launch; each is
-    // one step (kick 0, drift 0: the state stays the lattice) replayed from a graph
+    // candidates: the form of the middle FFT passes (separate launches; whole kz planes in
+    // shared memory on 64^3 and 128^3 meshes), and for each the whole batch per launch, then
+    // halves down to one realisation per launch; each is one step (kick 0, drift 0: the state
+    // stays the lattice) replayed from a graph
+    const int nforms = (b->cfg.nmesh == 64 || b->cfg.nmesh == 128) ? 2 : 1;
+    for (int form = 0; form < nforms && st == PM_OK; ++form)
     for (int c = b->B;; c = (c + 1) / 2) {
         b->chunk = c;
+        b->fft_form = form;
         cudaGraph_t g = nullptr;
         cudaGraphExec_t ex = nullptr;
         if (cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeRelaxed) != cudaSuccess) {
@@ -1911,12 +1961,14 @@ pm_status pm_batch_autotune(pm_batch* b, int* chunk_out, double* ms_out) {
         if (ms / 3.0 < best_ms) {
             best_ms = ms / 3.0;
             best = c;
+            best_form = form;
         }
         if (c == 1) break;
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     b->chunk = best;
+    b->fft_form = best_form;
     b->rho_valid = false;
     if (st != PM_OK) return st;
     if (chunk_out) *chunk_out = best;

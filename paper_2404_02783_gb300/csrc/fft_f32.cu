@@ -11,6 +11,7 @@ cudaError_t upload_twiddles_f32(const float2* host) {
 }
 
 PM_INST(float)
+template cudaError_t fft_plane<float>(float2*, float2*, float2*, int, int, const SpecOp&, cudaStream_t);
 template cudaError_t fft_middle<float>(float2*, float2*, float2*, int, int, const SpecOp&, unsigned*, int,
                                        cudaStream_t);
 

@@ -12,7 +12,11 @@ cudaError_t upload_twiddles_f64(const double2* host) {
 
 PM_INST(double)
 
-// The fused middle passes are built for FP32 only (FP64 runs the separate passes).
+// The fused and whole-plane middle passes are built for FP32 only (FP64 runs the separate passes).
+template <>
+cudaError_t fft_plane<double>(double2*, double2*, double2*, int, int, const SpecOp&, cudaStream_t) {
+    return cudaErrorNotSupported;
+}
 template <>
 cudaError_t fft_middle<double>(double2*, double2*, double2*, int, int, const SpecOp&, unsigned*, int, cudaStream_t) {
     return cudaErrorNotSupported;

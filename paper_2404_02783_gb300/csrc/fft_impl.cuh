@@ -743,6 +743,129 @@ __global__ void __launch_bounds__(THREADS, 1024 / THREADS)
     }
 }
 
+// =============================================================== whole kz planes in shared memory
+// On meshes of 64^3 and 128^3 one kz plane of the half spectrum (N^2 complex: 128 KB in FP32 at
+// N = 128) fits in a CTA's shared memory.  k_plane runs the middle of a force evaluation on it:
+// forward y (rows), forward x (columns) with the per-mode operator, then for each force
+// component j the inverse x and inverse y transforms of -i k_j phi, written straight to that
+// component's spectrum (x to GX, y to GY, z over A; the z pass then needs no z gradient).  HBM
+// sees one read of the plane and three writes.  A row's or a column's transform uses its own
+// slots of the plane as its exchange space; phi stays in registers between the components.
+template <typename T, int LOGN> struct PlaneShape {
+    static constexpr int N = 1 << LOGN, M = N / 2, Q = N / 8;
+    static constexpr int THREADS = 8 * N;          // 64 sequences of N at a time
+    static constexpr int SEQ = THREADS / Q;
+    static constexpr int ROUNDS = N / SEQ;
+    static constexpr int MINB = (THREADS >= 1024) ? 1 : 1024 / THREADS;  // 64 registers a thread
+    static constexpr size_t SMEM = sizeof(cplx<T>) * ((size_t)N + (size_t)N * N);
+    static_assert(ROUNDS >= 1 && SEQ * ROUNDS == N, "whole rounds of rows and columns");
+};
+
+template <typename T, int LOGN, int KIND>
+__global__ void __launch_bounds__(PlaneShape<T, LOGN>::THREADS, PlaneShape<T, LOGN>::MINB)
+    k_plane(cplx<T>* __restrict__ A, cplx<T>* __restrict__ GX, cplx<T>* __restrict__ GY, SpecOp op, int nplanes) {
+    typedef cplx<T> C;
+    typedef PlaneShape<T, LOGN> SH;
+    constexpr int N = SH::N, M = SH::M, Q = SH::Q, SEQ = SH::SEQ, ROUNDS = SH::ROUNDS;
+    typedef RowLayout<N, false> LAY;  // a permutation within each row's N slots
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* tw = reinterpret_cast<C*>(smem_raw);
+    C* P = tw + N;
+    const int tid = threadIdx.x;
+    load_stage_twiddles<T, N>(tw);
+#pragma unroll 1
+    for (int plane = blockIdx.x; plane < nplanes; plane += gridDim.x) {
+        const size_t pbase = (size_t)plane * N * N;
+        const int kz = plane % (M + 1);
+        const int field = plane / (M + 1);
+        const double kf = op.kf_arr ? op.kf_arr[field] : op.kf;
+        const T kfT = T(kf);
+        __syncthreads();  // the previous plane's last reads of P and of the twiddles' set-up
+        for (int e = tid; e < N * N; e += SH::THREADS) P[e] = __ldcs(A + pbase + e);
+        __syncthreads();
+        // ---- forward y of the N rows
+#pragma unroll 1
+        for (int r = 0; r < ROUNDS; ++r) {
+            const int b = tid / Q, t = tid % Q;
+            C* row = P + (size_t)(r * SEQ + b) * N;
+            C v[1][8];
+#pragma unroll
+            for (int m = 0; m < 8; ++m) v[0][m] = row[t + m * Q];
+            RowEx<C, 1, false, LAY> ex{P + (size_t)r * SEQ * N, SEQ, N, b, 0};
+            fft_regs<N, 1, false>(v, t, tw, ex);
+            __syncthreads();  // the row's last exchange has been read
+#pragma unroll
+            for (int m = 0; m < 8; ++m) row[t + m * Q] = v[0][m];
+        }
+        __syncthreads();
+        // ---- forward x of the N columns and the per-mode operator: phi in registers
+        C phi[ROUNDS][8];
+        const T coefT = T(op.coef) / (kfT * kfT);
+        const T kf2T = T(kf * kf);
+#pragma unroll
+        for (int r = 0; r < ROUNDS; ++r) {
+            const int b = tid % SEQ, t = tid / SEQ;
+            const int c = r * SEQ + b;
+            C v[1][8];
+#pragma unroll
+            for (int m = 0; m < 8; ++m) v[0][m] = P[(size_t)(t + m * Q) * N + c];
+            ColEx<C, N> ex{P + r * SEQ, N, b};
+            fft_regs<N, 1, false>(v, t, tw, ex);
+            const int ny = (c < M) ? c : c - N;
+#pragma unroll
+            for (int m = 0; m < 8; ++m) {
+                const int i = t + m * Q;
+                const int nx = (i < M) ? i : i - N;
+                const int n2 = nx * nx + ny * ny + kz * kz;
+                phi[r][m] = mode_op<T, KIND, N>(op, v[0][m], nx, ny, kz, n2, field, kf, kfT, coefT, kf2T,
+                                                reinterpret_cast<C*>(op.phi_old) + pbase + (size_t)i * N + c);
+            }
+        }
+        // ---- each component: -i k_j phi back along x (columns), then along y (rows), to its spectrum
+#pragma unroll 1
+        for (int j = 0; j < 3; ++j) {
+            C* out = (j == 0) ? GX : (j == 1 ? GY : A);
+            __syncthreads();  // every read of P by the previous pass is done
+#pragma unroll
+            for (int r = 0; r < ROUNDS; ++r) {
+                const int b = tid % SEQ, t = tid / SEQ;
+                const int c = r * SEQ + b;
+                const int ny = (c < M) ? c : c - N;
+                const T ky = (2 * ny == -N) ? T(0) : kfT * T(ny);
+                const T kzv = (kz == M) ? T(0) : kfT * T(kz);
+                C v[1][8];
+#pragma unroll
+                for (int m = 0; m < 8; ++m) {
+                    const int i = t + m * Q;
+                    const int nx = (i < M) ? i : i - N;
+                    const T kx = (2 * nx == -N) ? T(0) : kfT * T(nx);
+                    const T kj = (j == 0) ? kx : (j == 1 ? ky : kzv);
+                    v[0][m] = cmake<C>(phi[r][m].y * kj, -phi[r][m].x * kj);  // -i k_j phi
+                }
+                ColEx<C, N> ex{P + r * SEQ, N, b};
+                fft_regs<N, 1, true>(v, t, tw, ex);
+                __syncthreads();  // the column's last exchange has been read
+#pragma unroll
+                for (int m = 0; m < 8; ++m) P[(size_t)(t + m * Q) * N + c] = v[0][m];
+            }
+            __syncthreads();
+#pragma unroll 1
+            for (int r = 0; r < ROUNDS; ++r) {
+                const int b = tid / Q, t = tid % Q;
+                const C* row = P + (size_t)(r * SEQ + b) * N;
+                C v[1][8];
+#pragma unroll
+                for (int m = 0; m < 8; ++m) v[0][m] = row[t + m * Q];
+                RowEx<C, 1, false, LAY> ex{P + (size_t)r * SEQ * N, SEQ, N, b, 0};
+                fft_regs<N, 1, true>(v, t, tw, ex);
+                C* orow = out + pbase + (size_t)(r * SEQ + b) * N;
+#pragma unroll
+                for (int m = 0; m < 8; ++m) orow[t + m * Q] = v[0][m];
+            }
+        }
+    }
+}
+
 // =============================================================== x: adjoint combine
 // Transposed force chain on the x pass: the three y-transformed spectra of the deposited
 // adjoint momenta V_j (fields j = 0, 1, 2 back to back, [kz][x][ky]) are transformed
@@ -941,6 +1064,23 @@ cudaError_t middle_shape(cplx<T>* A, cplx<T>* B, cplx<T>* Cs, int nplanes, const
 }
 
 template <typename T, int LOGN>
+cudaError_t plane_n(cplx<T>* A, cplx<T>* GX, cplx<T>* GY, int nplanes, const SpecOp& op, cudaStream_t st) {
+    typedef PlaneShape<T, LOGN> SH;
+    const void* fn = op.kind == OP_GR ? (const void*)k_plane<T, LOGN, OP_GR> : (const void*)k_plane<T, LOGN, OP_NEWTON>;
+    cudaError_t e = set_smem(fn, SH::SMEM);
+    if (e != cudaSuccess) return e;
+    int per_sm = 1;
+    e = resident_ctas(fn, SH::THREADS, SH::SMEM, &per_sm);
+    if (e != cudaSuccess) return e;
+    const int grid = (int)std::min<int64_t>((int64_t)per_sm * num_sms(), nplanes);
+    if (op.kind == OP_GR)
+        k_plane<T, LOGN, OP_GR><<<grid, SH::THREADS, SH::SMEM, st>>>(A, GX, GY, op, nplanes);
+    else
+        k_plane<T, LOGN, OP_NEWTON><<<grid, SH::THREADS, SH::SMEM, st>>>(A, GX, GY, op, nplanes);
+    return cudaGetLastError();
+}
+
+template <typename T, int LOGN>
 cudaError_t x_adj_n(const cplx<T>* V, cplx<T>* out, double kf, double coef, float* zero, int64_t nzero,
                     cudaStream_t st) {
     typedef Shape<T, LOGN> S;
@@ -1019,6 +1159,19 @@ cudaError_t fft_middle(cplx<T>* A, cplx<T>* B, cplx<T>* Cs, int nplanes, int n, 
         case 8: return middle_shape<T, 8>(A, B, Cs, nplanes, op, sync_words, threads, st);
         case 9: return middle_shape<T, 9>(A, B, Cs, nplanes, op, sync_words, threads, st);
         case 10: return middle_shape<T, 10>(A, B, Cs, nplanes, op, sync_words, threads, st);
+        default: return cudaErrorNotSupported;
+    }
+}
+
+// The middle passes on whole kz planes in shared memory (meshes of 64^3 and 128^3):
+// GX, GY and A receive -i k_j phi transformed back along x and y (A in place); the z pass
+// then runs without its z gradient.  cudaErrorNotSupported for other sizes.
+template <typename T>
+cudaError_t fft_plane(cplx<T>* A, cplx<T>* GX, cplx<T>* GY, int nplanes, int n, const SpecOp& op, cudaStream_t st) {
+    if (op.kind != OP_NEWTON && op.kind != OP_GR) return cudaErrorInvalidValue;
+    switch (ilog2(n)) {
+        case 6: return plane_n<T, 6>(A, GX, GY, nplanes, op, st);
+        case 7: return plane_n<T, 7>(A, GX, GY, nplanes, op, st);
         default: return cudaErrorNotSupported;
     }
 }

@@ -106,6 +106,12 @@ template <typename T>
 cudaError_t fft_middle(cplx<T>* A, cplx<T>* B, cplx<T>* C, int nplanes, int n, const SpecOp& op, unsigned* sync_words,
                        int threads, cudaStream_t st);
 inline size_t mid_sync_words_count(int nplanes) { return 5 + 2 * (size_t)nplanes; }
+// The same middle passes on whole kz planes in shared memory (FP32, n = 64, 128): on entry A
+// holds the z pass's half spectrum; on exit GX = IFFT_xy(-i kx phi), GY = IFFT_xy(-i ky phi),
+// A = IFFT_xy(-i kz phi) (the z pass takes them without its z gradient).
+// cudaErrorNotSupported for other sizes.
+template <typename T>
+cudaError_t fft_plane(cplx<T>* A, cplx<T>* GX, cplx<T>* GY, int nplanes, int n, const SpecOp& op, cudaStream_t st);
 
 // Forward z (r2c) and y passes of `batch` real meshes into spec ([field][kz][kx][ky]
 // before the x pass).

@@ -173,3 +173,33 @@ def test_autotuned_batch_matches_single_runs():
     assert e.value.status == 7
     with pytest.raises(pm.PMError):
         b.set_chunk(4)
+
+
+def test_whole_plane_form_of_the_batch_matches_the_separate_passes():
+    # 64 x 128^3 is the batched workload's mesh; here three realisations on 128^3 meshes with the
+    # middle FFT passes on whole kz planes in shared memory (form 1) and as separate launches
+    pm = lib()
+    cfg = pm.make_config(32, 128, 1000.0, A_I, A_F, STEPS)
+    out = []
+    for form in (0, 1):
+        b = pm.PMBatch(cfg, boxes=BOXES)
+        b.set_fft(form)
+        assert b.tuning() == (3, form)
+        b.ic(SEEDS)
+        b.step(STEPS, graph=True)
+        out.append([_batch_particles(b, r) for r in range(3)])
+        del b
+    for (xs, ps), (xp, pp) in zip(*out):
+        assert rel_l2(pp, ps) < 1e-5
+        assert np.max(np.abs(_disp(xp, xs))) < 1e-5
+
+
+def test_batch_autotuner_picks_a_form_and_chunk():
+    pm = lib()
+    b = pm.PMBatch(pm.make_config(32, 128, 1000.0, A_I, A_F, STEPS), boxes=BOXES * 2)
+    chunk, ms = b.autotune()
+    c2, form = b.tuning()
+    assert c2 == chunk and chunk in (6, 3, 2, 1) and form in (0, 1) and ms > 0
+    b.ic(SEEDS * 2)
+    b.step(STEPS, graph=True)
+    assert b.state()[0] == STEPS

@@ -78,3 +78,35 @@ def test_fused_force_of_one_step_matches_the_oracle():
     g = gravity.gradient_force(phik, n, box)
     want = K * np.stack([cic.interpolate(g[j], x0) for j in range(3)])
     assert rel_l2(dp, want) < 1e-5
+
+
+@pytest.mark.parametrize("mode,n_lo", [(0, 0), (1, 4)])
+@pytest.mark.parametrize("np_side,nmesh", [(64, 64), (32, 128), (64, 128), (128, 128)])
+def test_whole_plane_middle_passes_equal_the_separate_passes(mode, n_lo, np_side, nmesh):
+    # form 1: each kz plane transformed in shared memory (forward y, x, per-mode operator, and the
+    # three inverse x and y transforms of -i k_j phi): the same butterflies and operator as the
+    # separate passes, so the runs differ only by the deposit's atomic order
+    pm = lib()
+    box = 1000.0 if mode == 0 else 8000.0
+    cfg = pm.make_config(np_side, nmesh, box, 1.0 / 51.0, 1.0, 20, mode=mode, n_lo=n_lo)
+    dps, ds = _kicks(pm, cfg, 5, 3, 0)
+    dpp, dp_ = _kicks(pm, cfg, 5, 3, 1)
+    assert np.max(np.abs(dps)) > 0
+    assert rel_l2(dpp, dps) < 1e-5
+    assert rel_l2(dp_, ds) < 1e-5
+
+
+def test_whole_plane_form_against_the_oracle():
+    # 64^3 particles on a 128^3 mesh, L = 1000 Mpc/h: the first kick from the ZA ICs, K g(x0),
+    # against the oracle's own force evaluation of its ICs from the same seed
+    pm = lib()
+    np_side, n, box, steps, a_i = 64, 128, 1000.0, 20, 1.0 / 51.0
+    dp, _ = _kicks(pm, pm.make_config(np_side, n, box, a_i, 1.0, steps), 8, 1, 1)
+    c = Cosmology()
+    x0, _ = ic.zeldovich(c, np_side, box, a_i, seed=8, fixed=True)
+    a1 = a_i + (1.0 - a_i) / steps
+    K = c.kick_factor(a_i, 0.5 * (a_i + a1))
+    phik = gravity.newton_potential_k(np.fft.rfftn(cic.density_contrast(x0, n)), n, box, c.omega_m)
+    g = gravity.gradient_force(phik, n, box)
+    want = K * np.stack([cic.interpolate(g[j], x0) for j in range(3)])
+    assert rel_l2(dp, want) < 1e-5
