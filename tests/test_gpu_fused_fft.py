@@ -90,10 +90,14 @@ def test_whole_plane_middle_passes_equal_the_separate_passes(mode, n_lo, np_side
     box = 1000.0 if mode == 0 else 8000.0
     cfg = pm.make_config(np_side, nmesh, box, 1.0 / 51.0, 1.0, 20, mode=mode, n_lo=n_lo)
     dps, ds = _kicks(pm, cfg, 5, 3, 0)
+    dps2, ds2 = _kicks(pm, cfg, 5, 3, 0)
     dpp, dp_ = _kicks(pm, cfg, 5, 3, 1)
     assert np.max(np.abs(dps)) > 0
-    assert rel_l2(dpp, dps) < 1e-5
-    assert rel_l2(dp_, ds) < 1e-5
+    # the run-to-run difference of the separate passes themselves (the deposit's float atomics add
+    # in any order; with delta ~ 1e-3 per cell in the large Poisson-gauge box that reaches 1e-5)
+    noise = max(rel_l2(dps2, dps), rel_l2(ds2, ds))
+    assert rel_l2(dpp, dps) < max(1e-5, 4 * noise)
+    assert rel_l2(dp_, ds) < max(1e-5, 4 * noise)
 
 
 def test_whole_plane_form_against_the_oracle():
