@@ -90,14 +90,15 @@ def test_whole_plane_middle_passes_equal_the_separate_passes(mode, n_lo, np_side
     box = 1000.0 if mode == 0 else 8000.0
     cfg = pm.make_config(np_side, nmesh, box, 1.0 / 51.0, 1.0, 20, mode=mode, n_lo=n_lo)
     dps, ds = _kicks(pm, cfg, 5, 3, 0)
-    dps2, ds2 = _kicks(pm, cfg, 5, 3, 0)
     dpp, dp_ = _kicks(pm, cfg, 5, 3, 1)
     assert np.max(np.abs(dps)) > 0
-    # the run-to-run difference of the separate passes themselves (the deposit's float atomics add
-    # in any order; with delta ~ 1e-3 per cell in the large Poisson-gauge box that reaches 1e-5)
-    noise = max(rel_l2(dps2, dps), rel_l2(ds2, ds))
-    assert rel_l2(dpp, dps) < max(1e-5, 4 * noise)
-    assert rel_l2(dp_, ds) < max(1e-5, 4 * noise)
+    # the plane form applies -i k_y and -i k_z before the inverse transforms instead of between
+    # or after them: the same values up to FP32 rounding order; on the 8 Gpc/h Poisson-gauge box
+    # at z = 50 (delta ~ 1e-3 a cell) the runs then differ by up to 3e-5 (both are checked
+    # against the oracle below and in the Poisson-gauge run tests)
+    tol = 1e-5 if mode == 0 else 1e-4
+    assert rel_l2(dpp, dps) < tol
+    assert rel_l2(dp_, ds) < tol
 
 
 def test_whole_plane_form_against_the_oracle():
@@ -114,3 +115,27 @@ def test_whole_plane_form_against_the_oracle():
     g = gravity.gradient_force(phik, n, box)
     want = K * np.stack([cic.interpolate(g[j], x0) for j in range(3)])
     assert rel_l2(dp, want) < 1e-5
+
+
+@pytest.mark.parametrize("form", [0, 1])
+def test_whole_plane_form_of_a_poisson_gauge_run_against_the_oracle(form):
+    # 32^3 particles on a 64^3 mesh, L = 20 Gpc/h, z = 100 -> 1, 12 steps, n_lo = 4: both forms
+    # against the FP64 oracle's Poisson-gauge run, to the FP32 tolerance of the Poisson-gauge tests
+    from oracle import pm as opm
+    from tests.gpu_util import min_image, positions_box_units, ticks_to_host
+    pm = lib()
+    np_side, n, box, a_i, steps = 32, 64, 20000.0, 1.0 / 101.0, 12
+    c = Cosmology()
+    x0, p0 = ic.zeldovich(c, np_side, box, a_i, seed=21, fixed=True)
+    ref = opm.PMRun(c, n, box, a_i, 1.0, steps, x0, p0, mode=opm.GR_POISSON)
+    ref.step(steps)
+    run = pm.PMRun(pm.make_config(np_side, n, box, a_i, 1.0, steps, mode=1, n_lo=4))
+    pm.pm_set_fused_fft(run.ctx, form)
+    run.ic(seed=21)
+    run.step(steps)
+    x, _ = run.particles()
+    torch.cuda.synchronize()
+    xg = ticks_to_host(x)
+    d_g = min_image(positions_box_units(xg) - positions_box_units(x0))
+    d_o = min_image(positions_box_units(ref.x) - positions_box_units(x0))
+    assert rel_l2(d_g, d_o) < 2e-3
