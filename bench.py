@@ -324,13 +324,15 @@ def alu_roofline(phases, n, peak):
             "peak_source": peak["source"]}
 
 
-def e2e(pm, torch, args, rank, world, n_jobs=2):
+def e2e(pm, torch, args, rank, world, n_jobs=2, form=0):
     """Public-API end to end over the headline's own steps: the state at step GRID_STEPS - K
     (positions and momenta, held in pinned host memory) copied to the device, restored with
-    pm_set_state, the last K steps to z = 0, P(k) in 64 bins read back to the host."""
+    pm_set_state, the last K steps to z = 0 (FFT passes in the headline's tuned form), P(k) in
+    64 bins read back to the host."""
     cfg = pm.make_config(args.np, args.nmesh, args.box, A_INIT, A_FINAL, GRID_STEPS)
     run = pm.PMRun(cfg)
     run.seed = 1 + rank
+    pm.pm_set_fused_fft(run.ctx, form)
     start_of_timed_steps(pm, torch, run, args.steps)
     s0, _, sync0 = run.state()
     x0, p0 = run.particles()
@@ -917,7 +919,7 @@ def main():
                              "dominant": roof64, "alu_roofline": alu_roofline(ph64, args.nmesh, fp64_peak(torch)),
                              "phases": table64}
     if not args.no_e2e:
-        out["e2e"] = e2e(pm, torch, args, rank, world)
+        out["e2e"] = e2e(pm, torch, args, rank, world, form=tuned[0])
     if not args.no_batch:
         out["batched"] = batched(pm, torch, args)
     if not args.no_adjoint:
