@@ -38,7 +38,9 @@ the run's bookkeeping of Phi_old and dtau.  Two parts are pinned only partly:
 the amplitude of the horizon-scale GR displacement itself (the paper prints no
 values; pinned through the k >> calH limit, the matter-era identity and the
 linear-theory history above) and the Eisenstein-Hu constants of
-``cosmology.transfer_eh_nowiggle`` (checked by eye against EH98 Eqs. 26 and
-28-31; pinned only through the BBKS shape within 8%, so a change of a few percent
-in one constant would pass).
+``cosmology.transfer_eh_nowiggle``: the sound horizon (EH98 Eq. 26) is pinned to
+Planck 2018's measured r_drag within 3% and the baryon suppression alpha_Gamma
+(Eq. 31) to Sugiyama's (1995) independent fit within 1.5%, but L0 and C0
+(Eqs. 29-30) only through the BBKS shape within 8% (checked by eye), so a change
+of a few percent in one of their constants would pass.
 """

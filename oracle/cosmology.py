@@ -90,6 +90,19 @@ class Cosmology:
         return C_LIGHT * self.kick_factor(a0, a1)
 
     # ---------------------------------------------------------------- linear P(k)
+    def sound_horizon_mpc(self):
+        """Eisenstein & Hu (1998) Eq. 26: fitted sound horizon at the drag epoch (Mpc)."""
+        omh2 = self.omega_m * self.h * self.h
+        obh2 = self.omega_b * self.h * self.h
+        return 44.5 * np.log(9.83 / omh2) / np.sqrt(1.0 + 10.0 * obh2**0.75)
+
+    def alpha_gamma(self):
+        """Eisenstein & Hu (1998) Eq. 31: the baryons' suppression of the shape parameter on
+        scales well below the sound horizon, Gamma_eff -> alpha_Gamma Omega_m h."""
+        omh2 = self.omega_m * self.h * self.h
+        fb = self.omega_b / self.omega_m
+        return 1.0 - 0.328 * np.log(431.0 * omh2) * fb + 0.38 * np.log(22.3 * omh2) * fb * fb
+
     def transfer_eh_nowiggle(self, k):
         """Eisenstein & Hu (1998) zero-baryon-oscillation transfer function.
 
@@ -97,12 +110,10 @@ class Cosmology:
         k in h/Mpc.
         """
         k = np.asarray(k, dtype=np.float64)
-        om, ob, h = self.omega_m, self.omega_b, self.h
-        omh2, obh2 = om * h * h, ob * h * h
+        om, h = self.omega_m, self.h
         theta = self.t_cmb / 2.7
-        fb = ob / om
-        s = 44.5 * np.log(9.83 / omh2) / np.sqrt(1.0 + 10.0 * obh2**0.75)  # Mpc
-        alpha = 1.0 - 0.328 * np.log(431.0 * omh2) * fb + 0.38 * np.log(22.3 * omh2) * fb * fb
+        s = self.sound_horizon_mpc()
+        alpha = self.alpha_gamma()
         k_mpc = k * h
         gamma_eff = om * h * (alpha + (1.0 - alpha) / (1.0 + (0.43 * k_mpc * s)**4))
         q = k * theta * theta / gamma_eff

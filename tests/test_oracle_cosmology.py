@@ -71,6 +71,33 @@ def test_transfer_function_limits_and_bbks_shape():
     assert np.max(np.abs(T / bbks - 1)) < 0.08
 
 
+def test_eh_sound_horizon_against_the_measured_drag_scale():
+    # Eisenstein & Hu (1998) Eq. 26 is a fit, stated to about 2%, to the sound horizon at the drag
+    # epoch.  Planck 2018 (results VI, Table 2, TT,TE,EE+lowE+lensing) measures r_drag =
+    # 147.09 +- 0.26 Mpc for Omega_m = 0.3153, Omega_b h^2 = 0.02237, h = 0.6736: a dropped square
+    # root, a log10 for ln or a wrong exponent on omega_b moves the fit far outside 3%.
+    h = 0.6736
+    c = Cosmology(omega_m=0.3153, omega_b=0.02237 / h**2, h=h)
+    assert abs(c.sound_horizon_mpc() / 147.09 - 1.0) < 0.03
+
+
+@pytest.mark.parametrize("om,ob,h", [(0.31, 0.049, 0.67), (0.25, 0.04, 0.72), (0.4, 0.05, 0.65),
+                                     (0.3, 0.02, 0.7), (0.3, 0.07, 0.7), (0.35, 0.03, 0.6)])
+def test_eh_baryon_suppression_against_sugiyama(om, ob, h):
+    # Eq. 31's alpha_Gamma (the small-scale shape Gamma_eff = alpha_Gamma Omega_m h) against the
+    # independent fit of Sugiyama (1995), Gamma = Omega_m h exp(-Omega_b - sqrt(2h) Omega_b / Omega_m):
+    # they agree to better than 1% for baryon fractions 0.07-0.23; a coefficient off by a digit
+    # or a sign moves alpha_Gamma by several percent.
+    c = Cosmology(omega_m=om, omega_b=ob, h=h)
+    sugiyama = math.exp(-ob - math.sqrt(2.0 * h) * ob / om)
+    assert abs(c.alpha_gamma() / sugiyama - 1.0) < 0.015
+    # and the transfer function takes that shape well below the sound horizon: there it is the
+    # zero-baryon transfer function (Gamma = Omega_m h) at k / alpha_Gamma
+    no_baryons = Cosmology(omega_m=om, omega_b=0.0, h=h)
+    for k in (20.0, 50.0, 200.0):
+        assert c.transfer_eh_nowiggle(k) == pytest.approx(no_baryons.transfer_eh_nowiggle(k / c.alpha_gamma()), rel=1e-9)
+
+
 def test_sigma8_normalisation_and_growth_scaling():
     c = Cosmology()
     assert c.sigma_R(8.0) == pytest.approx(0.81, rel=1e-9)
