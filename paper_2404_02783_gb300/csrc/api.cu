@@ -514,9 +514,8 @@ pm_status power_t(pm_ctx* c, const void* field, const void* field2, int nbins, c
     double* acc = (double*)c->at(c->L.acc);
     PM_CK(bin_rows_sum(rows, nrows, nbins, acc, c->st));
     if (two) PM_CK(bin_rows_sum(rows2, nrows, nbins, acc + nbins, c->st));
-    std::vector<double> h((two ? 2 : 1) * nbins);
-    PM_CK(cudaMemcpyAsync(h.data(), acc, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, c->st));
-    // mode counts and mean |k| per bin follow from the geometry alone
+    // mode counts and mean |k| per bin follow from the geometry alone: summed on the host while
+    // the device transforms and bins (the copy below waits for it)
     const std::vector<double>& cnt = mode_counts(n);
     std::vector<double> nm(nbins, 0.0), ks(nbins, 0.0);
     for (size_t s = 1; s < cnt.size(); ++s) {
@@ -525,6 +524,8 @@ pm_status power_t(pm_ctx* c, const void* field, const void* field2, int nbins, c
         nm[b] += cnt[s];
         ks[b] += cnt[s] * std::sqrt((double)s);
     }
+    std::vector<double> h((two ? 2 : 1) * nbins);
+    PM_CK(cudaMemcpyAsync(h.data(), acc, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, c->st));
     PM_CK(cudaStreamSynchronize(c->st));
     const double V = c->cfg.box * c->cfg.box * c->cfg.box;
     const double n6 = std::pow((double)n, 6);

@@ -117,7 +117,7 @@ struct RowEx {
     C* base;
     int RB, RS, b, p;
     __device__ __forceinline__ C& at(int s, int i) {
-        return base[((size_t)((PP ? p : 0) * NSEQ + s) * RB + b) * RS + LAY::slot(i)];
+        return base[(((PP ? p : 0) * NSEQ + s) * RB + b) * RS + LAY::slot(i)];
     }
     __device__ __forceinline__ void begin() {
         if (!PP) __syncthreads();
@@ -133,7 +133,7 @@ template <typename C, int L>
 struct ColEx {
     C* base;
     int CS, b;
-    __device__ __forceinline__ C& at(int s, int i) { return base[((size_t)s * L + i) * CS + b]; }
+    __device__ __forceinline__ C& at(int s, int i) { return base[(s * L + i) * CS + b]; }
     __device__ __forceinline__ void begin() { __syncthreads(); }
     __device__ __forceinline__ void end() {}
 };

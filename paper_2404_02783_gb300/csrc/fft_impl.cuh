@@ -86,16 +86,15 @@ template <typename T, int LOGN> struct Shape {
     static constexpr int CB = (sizeof(T) == 8 && N >= 64) ? CB0 / 2 : CB0;
 };
 
-// Row of (slab row gl relative to the chunk start, frequency kz) in a half spectrum whose
-// blocks hold 2^xcl slab rows.
-template <int M>
-__device__ __forceinline__ size_t spec_row(int gl, int kz, int xcl) {
-    return (((size_t)(gl >> xcl) * (M + 1) + kz) << xcl) + (gl & ((1 << xcl) - 1));
+// Row of (slab row gl = field n + x, frequency kz) in the half spectra [field][kz][x][ky].
+template <int M, int LOGN>
+__device__ __forceinline__ size_t spec_row(int gl, int kz) {
+    return ((size_t)((gl >> LOGN) * (M + 1) + kz) << LOGN) + (gl & ((1 << LOGN) - 1));
 }
 
 // =============================================================== z: r2c
 template <typename T, int LOGN>
-__global__ void __launch_bounds__(512, sizeof(T) == 4 ? 4 : 2) k_z_r2c(const T* __restrict__ in, cplx<T>* __restrict__ out, int g0, int xcl) {
+__global__ void __launch_bounds__(512, sizeof(T) == 4 ? 4 : 2) k_z_r2c(const T* __restrict__ in, cplx<T>* __restrict__ out) {
     typedef cplx<T> C;
     typedef Shape<T, LOGN> S;
     constexpr int N = S::N, M = S::M, Q = S::QM, YB = S::YB;
@@ -109,7 +108,7 @@ __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 4 : 2) k_z_r2c(const T* 
     const int tid = threadIdx.x;
     const int y0 = blockIdx.x * YB;
     const int gl = blockIdx.y;
-    const size_t g = (size_t)g0 + gl;
+    const size_t g = gl;
     load_stage_twiddles<T, M>(twM);
     load_twiddles_head<T>(twN, N, M + 1);
     const int b = tid / Q, t = tid % Q;
@@ -135,7 +134,7 @@ __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 4 : 2) k_z_r2c(const T* 
         const C z2 = cconj(z[bb * RS + LAY::slot(k == 0 ? 0 : M - k)]);
         const C E = cscale(cadd(z1, z2), T(0.5));
         const C O = cscale(cmul_mi<false>(csub(z1, z2)), T(0.5));
-        out[spec_row<M>(gl, k, xcl) * N + y0 + bb] = cadd(E, cmul(twN[k], O));
+        out[spec_row<M, LOGN>(gl, k) * N + y0 + bb] = cadd(E, cmul(twN[k], O));
     }
 }
 
@@ -146,8 +145,8 @@ template <typename T> struct Ptr3 {
 };
 
 template <typename T, int LOGN>
-__global__ void __launch_bounds__(512, sizeof(T) == 4 ? 4 : 2) k_z_c2r(Ptr3<T> P, unsigned gradz_mask, T kf0, const double* __restrict__ kf_arr,
-                                               int g0, int xcl) {
+__global__ void __launch_bounds__(512, sizeof(T) == 4 ? 4 : 2) k_z_c2r(Ptr3<T> P, unsigned gradz_mask, T kf0,
+                                                                       const double* __restrict__ kf_arr) {
     typedef cplx<T> C;
     typedef Shape<T, LOGN> S;
     constexpr int N = S::N, M = S::M, Q = S::QM, YB = S::YB;
@@ -161,9 +160,9 @@ __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 4 : 2) k_z_c2r(Ptr3<T> P
     const bool grad = (gradz_mask >> comp) & 1u;
     const int y0 = blockIdx.x * YB;
     const int gl = blockIdx.y;
-    const size_t g = (size_t)g0 + gl;
+    const size_t g = gl;
     load_stage_twiddles<T, M>(twM);
-    const T kf = kf_arr ? T(kf_arr[g >> LOGN]) : kf0;
+    const T kf = kf_arr ? T(kf_arr[gl >> LOGN]) : kf0;
     const C* inp = comp == 0 ? P.in[0] : (comp == 1 ? P.in[1] : P.in[2]);
     T* pout = comp == 0 ? P.out[0] : (comp == 1 ? P.out[1] : P.out[2]);
     C* xb = buf;  // the pre-processed half spectrum; the FFT exchanges reuse the buffer afterwards
@@ -178,8 +177,8 @@ __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 4 : 2) k_z_c2r(Ptr3<T> P
         const int e = tid + it * NT;
         if (e < NP) {
             const int k = e / YB, col = y0 + e % YB;
-            X1[it] = inp[spec_row<M>(gl, k, xcl) * N + col];
-            X2[it] = inp[spec_row<M>(gl, M - k, xcl) * N + col];
+            X1[it] = inp[spec_row<M, LOGN>(gl, k) * N + col];
+            X2[it] = inp[spec_row<M, LOGN>(gl, M - k) * N + col];
         }
     }
     constexpr int TWS = 1024 / N;  // exp(-2 pi i k / N) = global table entry k TWS
@@ -938,23 +937,23 @@ __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) k_x_adj(const cpl
 
 // =============================================================== launchers
 template <typename T, int LOGN>
-cudaError_t z_r2c_n(const T* in, cplx<T>* out, int g0, int rows, int xcl, cudaStream_t st) {
+cudaError_t z_r2c_n(const T* in, cplx<T>* out, int rows, cudaStream_t st) {
     typedef Shape<T, LOGN> S;
     const size_t smem = sizeof(cplx<T>) * (S::M + ((S::M + 2) & ~1) + (size_t)S::YB * RowLayout<S::M, true>::RS);
     cudaError_t e = set_smem((const void*)k_z_r2c<T, LOGN>, smem);
     if (e != cudaSuccess) return e;
-    k_z_r2c<T, LOGN><<<dim3(S::N / S::YB, rows), S::YB * S::QM, smem, st>>>(in, out, g0, xcl);
+    k_z_r2c<T, LOGN><<<dim3(S::N / S::YB, rows), S::YB * S::QM, smem, st>>>(in, out);
     return cudaGetLastError();
 }
 
 template <typename T, int LOGN>
-cudaError_t z_c2r_n(const Ptr3<T>& P, int ncomp, int g0, int rows, int xcl, unsigned mask, double kf, cudaStream_t st,
+cudaError_t z_c2r_n(const Ptr3<T>& P, int ncomp, int rows, unsigned mask, double kf, cudaStream_t st,
                     const double* kf_arr) {
     typedef Shape<T, LOGN> S;
     const size_t smem = sizeof(cplx<T>) * (S::M + (size_t)S::YB * RowLayout<S::M, true>::RS);
     cudaError_t e = set_smem((const void*)k_z_c2r<T, LOGN>, smem);
     if (e != cudaSuccess) return e;
-    k_z_c2r<T, LOGN><<<dim3(S::N / S::YB, rows, ncomp), S::YB * S::QM, smem, st>>>(P, mask, (T)kf, kf_arr, g0, xcl);
+    k_z_c2r<T, LOGN><<<dim3(S::N / S::YB, rows, ncomp), S::YB * S::QM, smem, st>>>(P, mask, (T)kf, kf_arr);
     return cudaGetLastError();
 }
 
@@ -985,7 +984,7 @@ cudaError_t y_grad3_n(const cplx<T>* A, const cplx<T>* B, cplx<T>* Ao, cplx<T>* 
 template <typename T, int LOGN>
 cudaError_t forward_zy_n(const T* in, cplx<T>* spec, int batch, cudaStream_t st) {
     constexpr int N = 1 << LOGN, M = N / 2;
-    cudaError_t e = z_r2c_n<T, LOGN>(in, spec, 0, N * batch, LOGN, st);
+    cudaError_t e = z_r2c_n<T, LOGN>(in, spec, N * batch, st);
     if (e != cudaSuccess) return e;
     return y_rows_n<T, LOGN, false>(spec, spec, (int64_t)batch * (M + 1) * N, st);
 }
@@ -1004,7 +1003,7 @@ cudaError_t inverse_yz_grad_n(cplx<T>* A, cplx<T>* B, cplx<T>* scratch, T* const
     P.in[1] = scratch;  // IFFT_y(-i ky phi)   -> g_y
     P.in[2] = A;        // IFFT_y(phi), -i kz  -> g_z
     for (int j = 0; j < 3; ++j) P.out[j] = out[j];
-    return z_c2r_n<T, LOGN>(P, 3, 0, N * batch, LOGN, 4u, kf, st, kf_arr);
+    return z_c2r_n<T, LOGN>(P, 3, N * batch, 4u, kf, st, kf_arr);
 }
 
 template <typename T, int LOGN, int KIND>
@@ -1121,7 +1120,7 @@ cudaError_t x_cols_kind(cplx<T>* data, cplx<T>* out2, int nplanes, const SpecOp&
 
 template <typename T>
 cudaError_t z_r2c(const T* in, cplx<T>* out, int n, int batch, cudaStream_t st) {
-    PM_DISPATCH_LOGN(n, (z_r2c_n<T, LG>(in, out, 0, n * batch, LG, st)))
+    PM_DISPATCH_LOGN(n, (z_r2c_n<T, LG>(in, out, n * batch, st)))
 }
 
 template <typename T>
@@ -1132,7 +1131,7 @@ cudaError_t z_c2r(const cplx<T>* const* in, T* const* out, int ncomp, int n, int
         P.in[j] = in[j < ncomp ? j : 0];
         P.out[j] = out[j < ncomp ? j : 0];
     }
-    PM_DISPATCH_LOGN(n, (z_c2r_n<T, LG>(P, ncomp, 0, n * batch, LG, gradz_mask, kf, st, kf_arr)))
+    PM_DISPATCH_LOGN(n, (z_c2r_n<T, LG>(P, ncomp, n * batch, gradz_mask, kf, st, kf_arr)))
 }
 
 template <typename T, bool INV>
