@@ -791,18 +791,18 @@ def cpu_oracle(seconds, np_side=64):
                       f"common start, FP64 numpy oracle, {threads}, {wall:.1f} s wall"}
 
 
-def cpu_rows(sizes, all_cores_up_to=256):
-    """Per-step wall time of the oracle at each size: one process alone (one step after
-    its ICs), and -- up to all_cores_up_to^3 -- one process per core stepping together
+def cpu_rows(sizes, all_cores_up_to=256, steps_per_row=1):
+    """Per-step wall time of the oracle at each size: one process alone (steps_per_row steps
+    after its ICs), and -- up to all_cores_up_to^3 -- one process per core stepping together
     (aggregate particle-steps/s over their common window)."""
     cores, how = host_cores()
     rows = {}
     for n in sizes:
-        steps, b, e = _oracle_sample(0.0, n, 1, None, 1)
+        steps, b, e = _oracle_sample(1e9, n, 1, None, steps_per_row)
         row = {"one_process_ms_per_step": round(1e3 * (e - b) / steps, 1),
                "one_process_particle_steps_per_s": round(n**3 * steps / (e - b), 1)}
         if n <= all_cores_up_to and cores > 1:
-            res = _oracle_processes(cores, 0.0, n, 1)
+            res = _oracle_processes(cores, 1e9, n, steps_per_row)
             if res:
                 span = max(t for _, _, t in res) - min(t for _, t, _ in res)
                 row["all_cores_particle_steps_per_s"] = round(n**3 * sum(k for k, _, _ in res) / span, 1)
@@ -812,7 +812,8 @@ def cpu_rows(sizes, all_cores_up_to=256):
         rows[f"{n}^3"] = row
     return {"kind": "oracle", "cores_from": how, "rows": rows,
             "what": "FP64 numpy oracle, particles = mesh cells, L = 5000 n / 512 Mpc/h (the headline's cell "
-                    "size), one KDK step of the 100-step run from z = 50 after the ICs"}
+                    f"size), {steps_per_row} KDK step(s) of the 100-step run from z = 50 after the ICs, "
+                    "per-step time = their wall time / their count"}
 
 
 def main():
@@ -832,6 +833,7 @@ def main():
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-estimators", action="store_true")
     ap.add_argument("--no-compare", action="store_true", help="skip the separate-FFT-passes comparison")
+    ap.add_argument("--cpu-row-steps", type=int, default=1, help="oracle steps timed per --cpu-rows size")
     ap.add_argument("--cpu-rows", default="128",
                     help="comma-separated oracle sizes timed per step (e.g. 128,256,512); empty: none")
     args = ap.parse_args()
@@ -935,7 +937,7 @@ def main():
         out["cpu_baseline"] = cpu_oracle(args.cpu_seconds)
         sizes = [int(v) for v in args.cpu_rows.split(",") if v.strip()]
         if sizes:
-            out["cpu_baseline"]["per_size"] = cpu_rows(sizes)
+            out["cpu_baseline"]["per_size"] = cpu_rows(sizes, steps_per_row=max(1, args.cpu_row_steps))
         print(json.dumps(out))
     if world > 1:
         import torch.distributed as dist
