@@ -8,8 +8,8 @@ The differentiable workload fits the initial white noise w of a run at field lev
     L(w) = (1/N^3) sum_c (delta(c) - delta_t(c))^2,
 
 with delta the CIC counting density contrast of the final particles and delta_t a
-target mesh; ``vjp`` takes the cotangents of any loss of the final density and of the
-final displacements d = x - q instead.  The forward map is the Zel'dovich IC of ``ic`` (white-noise path)
+target mesh; ``vjp`` takes the cotangents of any loss of the final density, of the
+final displacements d = x - q and of the final (synchronised) momenta p instead.  The forward map is the Zel'dovich IC of ``ic`` (white-noise path)
 followed by the kick-drift-kick steps of ``pm``, written out here as a list of kick
 and drift operations so that the reverse sweep can walk it backwards:
 
@@ -156,24 +156,27 @@ def displacement(u, n_p, box):
     return (d - np.rint(d)) * box
 
 
-def vjp(cosmo, n_p, n_mesh, box, a_i, a_f, n_steps, w, lam_delta=None, lam_disp=None):
-    """dL/dw for any loss L(delta_final, d_final) given its cotangents lam_delta = dL/d delta
-    (n_mesh^3 mesh) and lam_disp = dL/d d ((3, n_p^3), per Mpc/h), by the reverse sweep of
-    the recorded forward run.  Since d = (u - q) L (minimum image), dL/du = L lam_disp; the
-    density adds m sum_c lam_delta(c) dW(u, c)/du."""
+def vjp(cosmo, n_p, n_mesh, box, a_i, a_f, n_steps, w, lam_delta=None, lam_disp=None, lam_mom=None):
+    """dL/dw for any loss L(delta_final, d_final, p_final) given its cotangents lam_delta =
+    dL/d delta (n_mesh^3 mesh), lam_disp = dL/d d ((3, n_p^3), per Mpc/h) and lam_mom =
+    dL/dp ((3, n_p^3), per Mpc/h of momentum, p after the closing half kick), by the reverse
+    sweep of the recorded forward run.  Since d = (u - q) L (minimum image), dL/du = L
+    lam_disp; the density adds m sum_c lam_delta(c) dW(u, c)/du; lam_mom is the adjoint
+    momentum the sweep starts from (the closing kick is the first operation it reverses)."""
     u, p, ops, mass = forward(cosmo, n_p, n_mesh, box, a_i, a_f, n_steps, w)
     lam_u = np.zeros_like(u)
     if lam_delta is not None:
         lam_u += mass * _grad_gather(np.asarray(lam_delta, dtype=np.float64), u, n_mesh)
     if lam_disp is not None:
         lam_u += box * np.asarray(lam_disp, dtype=np.float64).reshape(3, -1)
-    return _reverse(cosmo, n_p, n_mesh, box, a_i, ops, mass, lam_u)
+    lam_p = None if lam_mom is None else np.asarray(lam_mom, dtype=np.float64).reshape(3, -1)
+    return _reverse(cosmo, n_p, n_mesh, box, a_i, ops, mass, lam_u, lam_p)
 
 
-def _reverse(cosmo, n_p, n_mesh, box, a_i, ops, mass, lam_u):
-    """Walk the recorded kicks and drifts backwards from (lam_u, lam_p = 0), then apply the
-    transposed Zel'dovich map: returns dL/dw (n_p, n_p, n_p)."""
-    lam_p = np.zeros_like(lam_u)
+def _reverse(cosmo, n_p, n_mesh, box, a_i, ops, mass, lam_u, lam_p0=None):
+    """Walk the recorded kicks and drifts backwards from (lam_u, lam_p = lam_p0, else 0),
+    then apply the transposed Zel'dovich map: returns dL/dw (n_p, n_p, n_p)."""
+    lam_p = np.zeros_like(lam_u) if lam_p0 is None else np.array(lam_p0, dtype=np.float64)
     for op in reversed(ops):
         if op[0] == "drift":
             lam_p += op[1] / box * lam_u

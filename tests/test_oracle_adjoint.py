@@ -67,3 +67,31 @@ def test_vector_jacobian_product_of_density_and_displacements(n_p, n_mesh):
     g1 = adjoint.vjp(c, n_p, n_mesh, box, ai, af, steps, w, lam_delta=lam_delta)
     g2 = adjoint.vjp(c, n_p, n_mesh, box, ai, af, steps, w, lam_disp=gdisp)
     np.testing.assert_allclose(g1 + g2, g, rtol=0, atol=1e-12 * np.max(np.abs(g)))
+
+
+def test_vector_jacobian_product_of_the_final_momenta():
+    # L = sum_p h_p . p_p on the synchronised final momenta (after the closing half kick), alone
+    # and with a displacement term: the reverse sweep starting from lam_p = h must equal the
+    # central differences of the forward oracle; h = 0 gives the displacement term's gradient
+    c = Cosmology()
+    n_p, n_mesh = 8, 16
+    box, ai, af, steps = 300.0, 0.2, 0.6, 4
+    w = inputs.gaussian_field(7, n_p)
+    r = np.random.default_rng(8)
+    h = r.standard_normal((3, n_p**3)) * 1e-2
+    gdisp = r.standard_normal((3, n_p**3)) * 1e-3
+
+    def L_of(ww, with_disp):
+        u, p, _, _ = adjoint.forward(c, n_p, n_mesh, box, ai, af, steps, ww)
+        extra = np.sum(gdisp * adjoint.displacement(u, n_p, box)) if with_disp else 0.0
+        return float(np.sum(h * p) + extra)
+
+    eps = 1e-5
+    for with_disp in (False, True):
+        g = adjoint.vjp(c, n_p, n_mesh, box, ai, af, steps, w, lam_disp=gdisp if with_disp else None, lam_mom=h)
+        for _ in range(3):
+            v = r.standard_normal((n_p,) * 3)
+            fd = (L_of(w + eps * v, with_disp) - L_of(w - eps * v, with_disp)) / (2 * eps)
+            assert np.sum(g * v) == pytest.approx(fd, rel=1e-6)
+    g0 = adjoint.vjp(c, n_p, n_mesh, box, ai, af, steps, w, lam_disp=gdisp, lam_mom=np.zeros_like(h))
+    np.testing.assert_array_equal(g0, adjoint.vjp(c, n_p, n_mesh, box, ai, af, steps, w, lam_disp=gdisp))
