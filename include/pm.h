@@ -18,8 +18,9 @@
  *   pm_displacement_correction Eqs. xiGR and combined
  *   pm_power / pm_bispectrum   Eqs. powerspectrum / bispectre on the CIC counting density
  *   pm_linear_bias             Eq. b1 on a halo proxy (pm_halo_proxy), Eq. bgr (pm_b1_gr_theory)
- *   pm_adjoint_record / _run   gradient of any loss of the final density and displacements
- *                              with respect to the initial white noise (pm_loss_grad: the MSE)
+ *   pm_adjoint_record / _run   gradient of any loss of the final density, displacements and
+ *                              momenta with respect to the initial white noise (pm_loss_grad:
+ *                              the MSE)
  *   pm_batch_*                 many realisations stepped together from one CUDA graph
  *
  * Conventions shared by every entry point
@@ -301,18 +302,20 @@ pm_status pm_triangle_index(int nbins, int i, int j, int l, int64_t* index);
  * Field-level fits (the paper's GR displacement and bias are field-level quantities,
  * Secs. 2 and 5) need gradients of a loss on the final state with respect to the initial
  * phases.  The forward map is w -> Zel'dovich ICs of the white-noise field w (device, np^3,
- * as pm_ic_zeldovich with white_noise) -> cfg.n_steps KDK steps -> (delta, d): delta the
- * CIC counting density contrast of the final particles (n^3 mesh, pm_density) and d their
- * displacements (pm_displacement).  The closing half kick changes only p, which neither
- * output sees, so the recorded run leaves it out.
+ * as pm_ic_zeldovich with white_noise) -> cfg.n_steps KDK steps and the closing half kick
+ * -> (delta, d, p): delta the CIC counting density contrast of the final particles (n^3
+ * mesh, pm_density), d their displacements (pm_displacement) and p their synchronised
+ * momenta (pm_particles).
  *
  * pm_adjoint_record runs that forward map keeping (x, p) checkpoints every
- * checkpoint_every steps in `scratch` (pm_adjoint_scratch_size bytes, 256-byte aligned)
- * and the positions and force meshes of the last two segments; it leaves the context at
- * step n_steps before the closing kick, with the final particles in place (read delta and
- * d from there).  pm_adjoint_run then takes the cotangents d_delta = dL/d delta (device
- * float n^3, or NULL) and d_disp = dL/d d (device float [3][np^3], per Mpc/h, or NULL; not
- * both NULL) of any loss L and writes dL/dw (device float np^3) by the reverse sweep:
+ * checkpoint_every steps in `scratch` (pm_adjoint_scratch_size bytes, 256-byte aligned),
+ * the positions and force meshes of the last two segments and the force meshes of the
+ * closing kick; it leaves the context at step n_steps with synchronised momenta, the final
+ * particles in place (read delta, d and p from there).  pm_adjoint_run then takes the
+ * cotangents d_delta = dL/d delta (device float n^3, or NULL), d_disp = dL/d d (device
+ * float [3][np^3], per Mpc/h, or NULL) and d_mom = dL/dp (device float [3][np^3], per Mpc/h
+ * of momentum, or NULL; not all three NULL) of any loss L and writes dL/dw (device float
+ * np^3) by the reverse sweep, which starts with the transposed closing kick when d_mom is given:
  * every earlier segment is re-run from its checkpoint on a second CUDA stream the context
  * creates on first use (overlapping the reverse sweep of the segment after it), then the
  * transposed drift, kick (direct CIC-gradient term plus the transposed deposit -> Green
@@ -329,7 +332,7 @@ pm_status pm_triangle_index(int nbins, int i, int j, int l, int64_t* index);
 pm_status pm_adjoint_scratch_size(const pm_ctx* ctx, int checkpoint_every, size_t* bytes);
 pm_status pm_adjoint_record(pm_ctx* ctx, const void* white_noise, int checkpoint_every, void* scratch,
                             size_t scratch_bytes);
-pm_status pm_adjoint_run(pm_ctx* ctx, const void* d_delta, const void* d_disp, void* grad_w);
+pm_status pm_adjoint_run(pm_ctx* ctx, const void* d_delta, const void* d_disp, const void* d_mom, void* grad_w);
 pm_status pm_loss_grad(pm_ctx* ctx, const void* white_noise, const void* delta_target, int checkpoint_every,
                        void* scratch, size_t scratch_bytes, double* loss, void* grad_w);
 

@@ -101,7 +101,7 @@ def lib():
         "pm_adjoint_scratch_size": (vp, i, ctypes.POINTER(sz)),
         "pm_loss_grad": (vp, vp, vp, i, vp, sz, pd, vp),
         "pm_adjoint_record": (vp, vp, i, vp, sz),
-        "pm_adjoint_run": (vp, vp, vp, vp),
+        "pm_adjoint_run": (vp, vp, vp, vp, vp),
         "pm_displacement": (vp, vp),
         "pm_batch_workspace_size": (cfgp, i, ctypes.POINTER(sz)),
         "pm_batch_init": (cfgp, i, pd, vp, sz, vp, ctypes.POINTER(vp)),
@@ -265,8 +265,8 @@ def pm_adjoint_record(ctx, white_noise, checkpoint_every, scratch):
                                    scratch.numel() * scratch.element_size()))
 
 
-def pm_adjoint_run(ctx, d_delta, d_disp, grad_w):
-    _check(lib().pm_adjoint_run(ctx, _ptr(d_delta), _ptr(d_disp), _ptr(grad_w)))
+def pm_adjoint_run(ctx, d_delta, d_disp, grad_w, d_mom=None):
+    _check(lib().pm_adjoint_run(ctx, _ptr(d_delta), _ptr(d_disp), _ptr(d_mom), _ptr(grad_w)))
 
 
 def pm_potential(ctx, out):
@@ -481,12 +481,13 @@ class PMRun:
         self._adj_scratch = self._adjoint_scratch(checkpoint_every)
         pm_adjoint_record(self.ctx, white_noise, checkpoint_every, self._adj_scratch)
 
-    def adjoint(self, d_delta=None, d_disp=None):
-        """pm_adjoint_run: dL/dw from the cotangents of the recorded run's final density and displacements."""
+    def adjoint(self, d_delta=None, d_disp=None, d_mom=None):
+        """pm_adjoint_run: dL/dw from the cotangents of the recorded run's final density,
+        displacements and momenta."""
         import torch
         grad = torch.empty((self.cfg.np,) * 3, dtype=torch.float32, device=self.device)
-        pm_adjoint_run(self.ctx, None if d_delta is None else d_delta.contiguous(),
-                       None if d_disp is None else d_disp.contiguous(), grad)
+        c = lambda t: None if t is None else t.contiguous()
+        pm_adjoint_run(self.ctx, c(d_delta), c(d_disp), grad, d_mom=c(d_mom))
         return grad
 
     def displacement(self):
@@ -501,12 +502,14 @@ class PMRun:
         return 2 * math.pi / self.cfg.box
 
 
-def run_fields(run, white_noise, checkpoint_every=10):
-    """(delta_final, disp_final) of the whole PM run as differentiable functions of the
-    white-noise field w: the forward pass is pm_adjoint_record (the run with checkpoints),
-    the backward pass hands the incoming gradients of both outputs to pm_adjoint_run (one
-    reverse sweep on the GPU).  Any torch loss of the final density (shape (n, n, n)) and
-    displacements (Mpc/h, shape (3, np^3)) composes with it; one backward per forward."""
+def run_fields(run, white_noise, checkpoint_every=10, momenta=False):
+    """(delta_final, disp_final) -- and p_final with momenta=True -- of the whole PM run as
+    differentiable functions of the white-noise field w: the forward pass is
+    pm_adjoint_record (the run with checkpoints, ending with the closing half kick), the
+    backward pass hands the incoming gradients of the outputs to pm_adjoint_run (one reverse
+    sweep on the GPU).  Any torch loss of the final density (shape (n, n, n)), displacements
+    (Mpc/h, shape (3, np^3)) and momenta (Mpc/h, shape (3, np^3)) composes with it; one
+    backward per forward."""
     import torch
 
     class _RunFields(torch.autograd.Function):
@@ -514,14 +517,17 @@ def run_fields(run, white_noise, checkpoint_every=10):
         def forward(ctx, w):
             ctx.set_materialize_grads(False)
             run.record(w.detach().contiguous(), checkpoint_every)
-            return run.density(), run.displacement()
+            out = (run.density(), run.displacement())
+            if momenta:
+                out = out + (run.particles()[1].clone(),)
+            return out
 
         @staticmethod
-        def backward(ctx, g_delta, g_disp):
-            if g_delta is None and g_disp is None:
+        def backward(ctx, g_delta, g_disp, g_mom=None):
+            if g_delta is None and g_disp is None and g_mom is None:
                 return None
             f32 = lambda g: None if g is None else g.to(torch.float32)
-            return run.adjoint(f32(g_delta), f32(g_disp))
+            return run.adjoint(f32(g_delta), f32(g_disp), f32(g_mom))
 
     return _RunFields.apply(white_noise)
 

@@ -1187,7 +1187,7 @@ struct AdjLayout {
     // segment overlaps the reverse sweep of the next; the re-runs' own density, spectra and
     // end positions
     size_t ckpt = 0, seg_x[2] = {0, 0}, seg_g[2] = {0, 0}, lam_u = 0, lam_p = 0, acc = 0;
-    size_t re_rho = 0, re_spec[3] = {0, 0, 0}, re_x = 0, total = 0;
+    size_t re_rho = 0, re_spec[3] = {0, 0, 0}, re_x = 0, close_g = 0, total = 0;
     int nseg = 0, C = 0;
 };
 
@@ -1215,6 +1215,7 @@ AdjLayout adj_plan(const pm_ctx* c, int C) {
     A.re_rho = take(n * n * n * 4);
     for (int j = 0; j < 3; ++j) A.re_spec[j] = take(spec);
     A.re_x = take(P);
+    A.close_g = take(G);  // the force meshes of the closing half kick
     A.total = off;
     return A;
 }
@@ -1346,8 +1347,9 @@ struct AdjSweep {
 
     // The forward run from the ICs of white noise w with checkpoints of (x, p) before every
     // segment; the last two segments are recorded as they run (one record each), so the
-    // reverse sweep starts without a re-run.  The closing half kick after the last step
-    // changes only p, which neither the density nor the positions see: it is not run.
+    // reverse sweep starts without a re-run.  Then the closing half kick synchronises the
+    // momenta, as at the end of any run, with its force meshes kept for the reverse sweep of
+    // a momentum cotangent.
     pm_status forward(const void* white_noise) const {
         PM_TRY(pm_ic_zeldovich(c, 0, white_noise, 0));
         void* x = c->at(c->L.x);
@@ -1360,17 +1362,26 @@ struct AdjSweep {
             if (k < A.nseg - 2) PM_TRY(pm_step(c, s1 - s0));
             else PM_TRY(record(c, k, x, x));
         }
+        c->force_at = at(A.close_g);
+        pm_status st = compute_forces(c, c->a_grid(steps));
+        if (st == PM_OK) st = kick_drift(c, close_kick(), 0.0);
+        c->force_at = nullptr;
+        PM_TRY(st);
+        c->synced = true;
         c->rho_valid = false;
         return PM_OK;
     }
+    double close_kick() const {
+        return pmhost::kick_integral(c->cosmo, 0.5 * (c->a_grid(steps - 1) + c->a_grid(steps)), c->a_grid(steps));
+    }
 
-    // Reverse sweep from the adjoint positions lam_u (scratch lam_u; lam_p = 0 after the
-    // closing kick) down to dL/dw.  Every segment before the last two is re-run from its
+    // Reverse sweep from the adjoint positions lam_u (scratch lam_u) and, with mom, the adjoint
+    // momenta in scratch lam_p (else lam_p = 0 after the closing kick) down to dL/dw.  Every segment before the last two is re-run from its
     // checkpoint on the second stream, on a context of its own (density and spectra in the
     // scratch, p and, without the fused update, x in place over the checkpoint, which is
     // used once), into the record the reverse sweep of the segment after it has just
     // released; events order the two streams.
-    pm_status reverse(void* grad_out) const {
+    pm_status reverse(void* grad_out, bool mom) const {
         const double box = c->cfg.box;
         float* lam_u = (float*)at(A.lam_u);
         float* lam_p = (float*)at(A.lam_p);
@@ -1398,10 +1409,15 @@ struct AdjSweep {
             PM_CK(cudaEventRecord(S.ev_rerun[k], re.st));
             return PM_OK;
         };
-        // the transposed drift of the last step gives lam_p
-        PM_CK(axpby(lam_p, lam_u, nullptr, 3 * c->np3, (float)(drift_of_step(c, steps - 1) / box), 0.0f, c->st));
         // V (the three force meshes, back to back) is zero before the first adjoint deposit
         PM_CK(cudaMemsetAsync(c->at(c->L.force[0]), 0, Gb, c->st));
+        // the transposed closing kick at the final positions (only a momentum cotangent sees
+        // it), then the transposed drift of the last step gives lam_p
+        if (mom)
+            PM_TRY(adj_kick(c, (const uint32_t*)c->at(c->L.x), (const float*)at(A.close_g), close_kick(), lam_u, lam_p,
+                            drift_of_step(c, steps - 1) / box));
+        else
+            PM_CK(axpby(lam_p, lam_u, nullptr, 3 * c->np3, (float)(drift_of_step(c, steps - 1) / box), 0.0f, c->st));
         for (int k = A.nseg - 1; k >= 0; --k) {
             const int s0 = k * S.C, s1 = std::min(steps, s0 + S.C);
             if (k < A.nseg - 2) PM_CK(cudaStreamWaitEvent(c->st, S.ev_rerun[k], 0));
@@ -1482,8 +1498,8 @@ pm_status pm_adjoint_record(pm_ctx* c, const void* white_noise, int checkpoint_e
     return PM_OK;
 }
 
-pm_status pm_adjoint_run(pm_ctx* c, const void* d_delta, const void* d_disp, void* grad_w) {
-    if (!c || !grad_w || (!d_delta && !d_disp)) return fail(PM_ERR_INVALID_ARG, "null argument");
+pm_status pm_adjoint_run(pm_ctx* c, const void* d_delta, const void* d_disp, const void* d_mom, void* grad_w) {
+    if (!c || !grad_w || (!d_delta && !d_disp && !d_mom)) return fail(PM_ERR_INVALID_ARG, "null argument");
     if (!c->adj || !c->adj->recorded || c->step != c->cfg.n_steps)
         return fail(PM_ERR_STATE, "pm_adjoint_run needs the forward run of pm_adjoint_record first");
     pm_ctx::AdjSession& S = *c->adj;
@@ -1502,10 +1518,14 @@ pm_status pm_adjoint_run(pm_ctx* c, const void* d_delta, const void* d_disp, voi
                 PM_CK(axpby(tmp, lam_u, (const float*)d_disp, m, 1.0f, (float)c->cfg.box, c->st));
                 PM_CK(axpby(lam_u, tmp, nullptr, m, 1.0f, 0.0f, c->st));
             }
-        } else {
+        } else if (d_disp) {
             PM_CK(axpby(lam_u, (const float*)d_disp, nullptr, m, (float)c->cfg.box, 0.0f, c->st));
+        } else {
+            PM_CK(cudaMemsetAsync(lam_u, 0, sizeof(float) * m, c->st));
         }
-        return sw.reverse(grad_w);
+        // lam_p = dL/dp of the synchronised final momenta (tmp was scratch until here)
+        if (d_mom) PM_CK(axpby(tmp, (const float*)d_mom, nullptr, m, 1.0f, 0.0f, c->st));
+        return sw.reverse(grad_w, d_mom != nullptr);
     };
     pm_status st = body();
     if (st == PM_OK) {
@@ -1540,7 +1560,7 @@ pm_status pm_loss_grad(pm_ctx* c, const void* white_noise, const void* target, i
         adj_settle(c);
         return st;
     }
-    PM_TRY(pm_adjoint_run(c, rho, nullptr, grad_out));
+    PM_TRY(pm_adjoint_run(c, rho, nullptr, nullptr, grad_out));
     double hsum = 0.0;
     PM_CK(cudaMemcpyAsync(&hsum, acc, 8, cudaMemcpyDeviceToHost, c->st));
     PM_CK(cudaStreamSynchronize(c->st));

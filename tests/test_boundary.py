@@ -45,6 +45,26 @@ def test_library_exports_every_declared_symbol(pm):
     assert set(names) <= exported
 
 
+def declared_arities():
+    """Number of parameters of every pm_* function declared in the header."""
+    src = re.sub(r"/\*.*?\*/", "", open(HEADER).read(), flags=re.S)
+    out = {}
+    for name, params in re.findall(r"^\s*(?:pm_status|const char\*)\s+(pm_\w+)\s*\(([^)]*)\)\s*;", src, flags=re.M | re.S):
+        params = params.strip()
+        out[name] = 0 if params in ("", "void") else params.count(",") + 1
+    return out
+
+
+def test_binding_argument_lists_match_the_header(pm):
+    # each ctypes argument list the binding installs has as many entries as the declaration
+    ar = declared_arities()
+    assert set(ar) == set(declared_functions())
+    L = pm.lib()
+    for name, n in ar.items():
+        argtypes = getattr(L, name).argtypes
+        assert argtypes is not None and len(argtypes) == n, (name, n, argtypes)
+
+
 def test_workspace_size_and_validation(pm):
     cfg = pm.make_config(32, 64, 1000.0, 0.02, 1.0, 10)
     n = pm.pm_workspace_size(cfg)

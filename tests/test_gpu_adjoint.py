@@ -1,5 +1,6 @@
 """GPU gradients through the PM run -- the field-level MSE (pm_loss_grad) and any torch loss of
-the final density and displacements (pm_adjoint_record / pm_adjoint_run through run_fields) --
+the final density, displacements and momenta (pm_adjoint_record / pm_adjoint_run through
+run_fields) --
 against the FP64 oracle's reverse sweep, the oracle's finite differences, and across
 checkpoint intervals."""
 import numpy as np
@@ -120,6 +121,50 @@ def test_any_torch_loss_of_density_and_displacements_matches_fp64_oracle(np_side
     # the outputs themselves are the oracle's final density and displacements
     assert rel_l2(to_host(delta).astype(np.float64), cic.density_contrast(u, nmesh)) < 1e-4
     assert rel_l2(to_host(disp).astype(np.float64), adjoint.displacement(u, np_side, box)) < 1e-4
+
+
+@pytest.mark.parametrize("np_side,nmesh", [(16, 16), (32, 64)])
+def test_a_loss_of_the_final_momenta_matches_fp64_oracle(np_side, nmesh):
+    # run_fields(momenta=True) also returns the synchronised final momenta; a loss with a term
+    # h . p gives the oracle's vector-Jacobian product with lam_mom = h (the reverse sweep then
+    # starts with the transposed closing kick), alone and with the density and displacement terms
+    pm = lib()
+    c, w, _, run, (box, a_i, a_f, steps) = _setup(pm, np_side, nmesh)
+    Wk = _spectral_weight(nmesh)
+    r = np.random.default_rng(12)
+    gdisp = r.standard_normal((3, np_side**3)) * 1e-3
+    h = r.standard_normal((3, np_side**3)) * 1e-2
+    w64 = w.astype(np.float64)
+    u, p_o, _, _ = adjoint.forward(c, np_side, nmesh, box, a_i, a_f, steps, w64)
+    dk = np.fft.fftn(cic.density_contrast(u, nmesh))
+    lam_delta = 2.0 * np.real(np.fft.ifftn(Wk * dk)) / nmesh**3
+    for full in (False, True):
+        wv = to_dev(w).requires_grad_(True)
+        delta, disp, mom = pm.run_fields(run, wv, checkpoint_every=2, momenta=True)
+        L = (to_dev(h) * mom.to(torch.float64)).sum()
+        if full:
+            L = L + _torch_loss(delta, disp, to_dev(Wk), to_dev(gdisp), nmesh)
+        L.backward()
+        g = to_host(wv.grad).astype(np.float64)
+        go = adjoint.vjp(c, np_side, nmesh, box, a_i, a_f, steps, w64, lam_delta=lam_delta if full else None,
+                         lam_disp=gdisp if full else None, lam_mom=h)
+        assert rel_l2(g, go) < 1e-3
+        assert rel_l2(to_host(mom).astype(np.float64), p_o) < 1e-4
+
+
+def test_recorded_run_ends_like_a_plain_run():
+    # pm_adjoint_record ends with the closing half kick: the same synchronised state as pm_step
+    pm = lib()
+    c, w, _, run, (box, a_i, a_f, steps) = _setup(pm, 32, 64)
+    run.record(to_dev(w), 2)
+    d1, p1 = to_host(run.displacement()).astype(np.float64), to_host(run.particles()[1]).astype(np.float64)
+    assert run.state()[0] == steps and run.state()[2]
+    run.ic(white_noise=to_dev(w))
+    run.step(steps)
+    d2, p2 = to_host(run.displacement()).astype(np.float64), to_host(run.particles()[1]).astype(np.float64)
+    # equal up to the summation order of the deposit's float atomics
+    assert rel_l2(d1, d2) < 1e-6
+    assert rel_l2(p1, p2) < 1e-6
 
 
 def test_any_torch_loss_differences_match_the_oracle():
