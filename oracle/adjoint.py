@@ -21,10 +21,21 @@ the force meshes at u, rho_bar = sum_j T_j^T V_j, V_j the CIC deposit of v_j and
 T_j the (real, antisymmetric) Fourier operator rho -> G_j, so T_j^T = -T_j.  The CIC
 weights are piecewise linear in u; their derivative is taken on the same side as the
 forward floor() (the right derivative at a cell boundary).
+
+Poisson gauge (Sec. 2, the lagged constraint of ``gravity.gr_potential_k``): force
+evaluation n gives Phi_n = src_n delta_n + carry_n Phi_{n-1} per mode, with src = s / den,
+carry = (3 calH / dtau) / den (0 at the first evaluation), and G_j = T_j (a_n c^2 Phi_n).
+G at evaluation n then depends on every earlier density through the products of the carry
+factors, and the transposed chain runs backwards with one carried spectrum:
+Z_n = K_n a_n c^2 W_n + carry_{n+1} Z_{n+1}, rho_bar_n = IFFT[src_n Z_n] = dL/d delta_n,
+where W_n = sum_j i k_j FFT(V_j) of evaluation n and K_n its kick factor.
 """
 import numpy as np
 
 from . import cic, gravity, ic, philox
+from .cosmology import C_LIGHT
+
+NEWTON, GR_POISSON = 0, 1  # the force of the run, as in oracle.pm
 
 
 def _grad_gather(field, u, n):
@@ -87,6 +98,32 @@ def _rho_bar(V, n, box, omega_m):
     return np.fft.irfftn(acc, s=(n, n, n), axes=(0, 1, 2))
 
 
+def _gr_force_meshes(u, n, box, cosmo, a, hist):
+    """Poisson-gauge force meshes at u and scale factor a; hist = [Phi_old_k, a_old] of the
+    previous force evaluation ([None, None] before the first), updated in place.  Returns
+    (G, (a, dtau)) with dtau = None at the first evaluation."""
+    dk = np.fft.rfftn(cic.density_contrast(u, n))
+    dtau = None if hist[0] is None else cosmo.delta_tau(hist[1], a)
+    Phi = gravity.gr_potential_k(dk, n, box, cosmo, a, phi_old_k=hist[0], dtau=dtau)
+    hist[0], hist[1] = Phi, a
+    return gravity.gradient_force(gravity.gr_code_potential_k(Phi, a), n, box), (a, dtau)
+
+
+def _gr_coefficients(cosmo, n, box, a, dtau):
+    """(src, carry) per mode of the lagged constraint at (a, dtau): Phi = src delta + carry
+    Phi_old, src = -(3/2) calH^2 Om(a) / den, carry = (3 calH / dtau) / den; 0 at k = 0."""
+    _, _, k2 = gravity._wavenumbers(n, box)
+    H = float(cosmo.conformal_hubble(a))
+    om = float(cosmo.omega_m_a(a))
+    cc = 0.0 if dtau is None else 3.0 * H / dtau
+    den = k2 + 3.0 * H * H + 4.5 * H * H * om + cc
+    src = -1.5 * H * H * om / den
+    carry = cc / den
+    src[0, 0, 0] = 0.0
+    carry[0, 0, 0] = 0.0
+    return src, carry
+
+
 def _za_operator(w_or_s, n_p, box, cosmo, j):
     """Psi_j = A_j w: the white-noise Zel'dovich displacement along axis j (Mpc/h)."""
     dk = ic.linear_delta_k(cosmo, n_p, box, white_noise=w_or_s)
@@ -101,8 +138,10 @@ def _za_operator(w_or_s, n_p, box, cosmo, j):
     return np.fft.irfftn(1j * kf * Nj * dk * inv_k2, s=(n_p,) * 3, axes=(0, 1, 2))
 
 
-def forward(cosmo, n_p, n_mesh, box, a_i, a_f, n_steps, w):
-    """ZA ICs from w and the KDK run; returns (u_final, p_final, ops)."""
+def forward(cosmo, n_p, n_mesh, box, a_i, a_f, n_steps, w, mode=NEWTON):
+    """ZA ICs from w and the KDK run (Newtonian or Poisson-gauge force); returns
+    (u_final, p_final, ops, mass).  A Poisson-gauge kick op also keeps its force meshes and
+    (a, dtau)."""
     psi = ic.za_displacement(ic.linear_delta_k(cosmo, n_p, box, white_noise=w), n_p, box).reshape(3, -1)
     D, f, E = cosmo.growth_D(a_i), cosmo.growth_f(a_i), float(cosmo.E(a_i))
     i = np.arange(n_p, dtype=np.float64) / n_p
@@ -114,9 +153,17 @@ def forward(cosmo, n_p, n_mesh, box, a_i, a_f, n_steps, w):
     ops = []
     mass = (n_mesh / n_p)**3
 
-    def accel(uu):
-        G = _force_meshes(uu, n_mesh, box, cosmo.omega_m)
-        return np.stack([cic.interpolate(G[j], uu) for j in range(3)])
+    hist = [None, None]
+
+    def kick(uu, a, K):
+        """The kick op at positions uu and scale factor a, and the acceleration there."""
+        if mode == NEWTON:
+            G = _force_meshes(uu, n_mesh, box, cosmo.omega_m)
+            op = ("kick", K, uu.copy())
+        else:
+            G, meta = _gr_force_meshes(uu, n_mesh, box, cosmo, a, hist)
+            op = ("kick", K, uu.copy(), G, meta)
+        return op, np.stack([cic.interpolate(G[j], uu) for j in range(3)])
 
     synced = True
     for s in range(n_steps):
@@ -124,8 +171,9 @@ def forward(cosmo, n_p, n_mesh, box, a_i, a_f, n_steps, w):
         ah = 0.5 * (a0 + a1)
         a_from = a0 if synced else 0.5 * (grid[s - 1] + a0)
         K = cosmo.kick_factor(a_from, ah)
-        ops.append(("kick", K, u.copy()))
-        p = p + K * accel(u)
+        op, g = kick(u, a0, K)
+        ops.append(op)
+        p = p + K * g
         Dd = cosmo.drift_factor(a0, a1)
         ops.append(("drift", Dd))
         u = u + Dd * p / box
@@ -133,13 +181,14 @@ def forward(cosmo, n_p, n_mesh, box, a_i, a_f, n_steps, w):
         synced = False
         if s == n_steps - 1:
             K = cosmo.kick_factor(ah, a1)
-            ops.append(("kick", K, u.copy()))
-            p = p + K * accel(u)
+            op, g = kick(u, a1, K)
+            ops.append(op)
+            p = p + K * g
     return u, p, ops, mass
 
 
-def loss(cosmo, n_p, n_mesh, box, a_i, a_f, n_steps, w, delta_t):
-    u, _, _, _ = forward(cosmo, n_p, n_mesh, box, a_i, a_f, n_steps, w)
+def loss(cosmo, n_p, n_mesh, box, a_i, a_f, n_steps, w, delta_t, mode=NEWTON):
+    u, _, _, _ = forward(cosmo, n_p, n_mesh, box, a_i, a_f, n_steps, w, mode)
     return float(np.mean((cic.density_contrast(u, n_mesh) - delta_t)**2))
 
 
@@ -156,14 +205,14 @@ def displacement(u, n_p, box):
     return (d - np.rint(d)) * box
 
 
-def vjp(cosmo, n_p, n_mesh, box, a_i, a_f, n_steps, w, lam_delta=None, lam_disp=None, lam_mom=None):
+def vjp(cosmo, n_p, n_mesh, box, a_i, a_f, n_steps, w, lam_delta=None, lam_disp=None, lam_mom=None, mode=NEWTON):
     """dL/dw for any loss L(delta_final, d_final, p_final) given its cotangents lam_delta =
     dL/d delta (n_mesh^3 mesh), lam_disp = dL/d d ((3, n_p^3), per Mpc/h) and lam_mom =
     dL/dp ((3, n_p^3), per Mpc/h of momentum, p after the closing half kick), by the reverse
     sweep of the recorded forward run.  Since d = (u - q) L (minimum image), dL/du = L
     lam_disp; the density adds m sum_c lam_delta(c) dW(u, c)/du; lam_mom is the adjoint
     momentum the sweep starts from (the closing kick is the first operation it reverses)."""
-    u, p, ops, mass = forward(cosmo, n_p, n_mesh, box, a_i, a_f, n_steps, w)
+    u, p, ops, mass = forward(cosmo, n_p, n_mesh, box, a_i, a_f, n_steps, w, mode)
     lam_u = np.zeros_like(u)
     if lam_delta is not None:
         lam_u += mass * _grad_gather(np.asarray(lam_delta, dtype=np.float64), u, n_mesh)
@@ -177,16 +226,26 @@ def _reverse(cosmo, n_p, n_mesh, box, a_i, ops, mass, lam_u, lam_p0=None):
     """Walk the recorded kicks and drifts backwards from (lam_u, lam_p = lam_p0, else 0),
     then apply the transposed Zel'dovich map: returns dL/dw (n_p, n_p, n_p)."""
     lam_p = np.zeros_like(lam_u) if lam_p0 is None else np.array(lam_p0, dtype=np.float64)
+    Z, carry_next = None, None  # Poisson gauge: the carried spectrum and carry_{n+1}
+    k = _k_components(n_mesh, box)
     for op in reversed(ops):
         if op[0] == "drift":
             lam_p += op[1] / box * lam_u
         else:
             K, uk = op[1], op[2]
-            G = _force_meshes(uk, n_mesh, box, cosmo.omega_m)
-            direct = sum(lam_p[j] * _grad_gather(G[j], uk, n_mesh) for j in range(3))
             V = np.stack([_weighted_deposit(uk, lam_p[j], n_mesh) for j in range(3)])
-            rho_bar = _rho_bar(V, n_mesh, box, cosmo.omega_m)
-            lam_u = lam_u + K * (direct + mass * _grad_gather(rho_bar, uk, n_mesh))
+            if len(op) == 3:  # Newtonian: dL/d delta of this evaluation is K rho_bar
+                G = _force_meshes(uk, n_mesh, box, cosmo.omega_m)
+                rho_bar = K * _rho_bar(V, n_mesh, box, cosmo.omega_m)
+            else:  # Poisson gauge: Z carries dL/dPhi back through the lag (each term with its own K)
+                G, (a, dtau) = op[3], op[4]
+                W = sum(1j * k[j] * np.fft.rfftn(V[j]) for j in range(3))
+                src, carry = _gr_coefficients(cosmo, n_mesh, box, a, dtau)
+                Z = K * a * C_LIGHT**2 * W + (0.0 if Z is None else carry_next * Z)
+                rho_bar = np.fft.irfftn(src * Z, s=(n_mesh,) * 3, axes=(0, 1, 2))
+                carry_next = carry
+            direct = sum(lam_p[j] * _grad_gather(G[j], uk, n_mesh) for j in range(3))
+            lam_u = lam_u + K * direct + mass * _grad_gather(rho_bar, uk, n_mesh)
     D, f, E = cosmo.growth_D(a_i), cosmo.growth_f(a_i), float(cosmo.E(a_i))
     s = (D / box) * lam_u + a_i**2 * E * f * D * lam_p
     # lambda_w = sum_j A_j^T s_j and A_j^T = -A_j (odd, real Fourier multiplier)
@@ -196,9 +255,9 @@ def _reverse(cosmo, n_p, n_mesh, box, a_i, ops, mass, lam_u, lam_p0=None):
     return grad
 
 
-def loss_and_grad(cosmo, n_p, n_mesh, box, a_i, a_f, n_steps, w, delta_t):
+def loss_and_grad(cosmo, n_p, n_mesh, box, a_i, a_f, n_steps, w, delta_t, mode=NEWTON):
     """(L, dL/dw) with dL/dw of shape (n_p, n_p, n_p)."""
-    u, p, ops, mass = forward(cosmo, n_p, n_mesh, box, a_i, a_f, n_steps, w)
+    u, p, ops, mass = forward(cosmo, n_p, n_mesh, box, a_i, a_f, n_steps, w, mode)
     delta = cic.density_contrast(u, n_mesh)
     L = float(np.mean((delta - delta_t)**2))
     lam_rho = 2.0 * (delta - delta_t) / n_mesh**3

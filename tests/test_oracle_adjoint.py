@@ -95,3 +95,67 @@ def test_vector_jacobian_product_of_the_final_momenta():
             assert np.sum(g * v) == pytest.approx(fd, rel=1e-6)
     g0 = adjoint.vjp(c, n_p, n_mesh, box, ai, af, steps, w, lam_disp=gdisp, lam_mom=np.zeros_like(h))
     np.testing.assert_array_equal(g0, adjoint.vjp(c, n_p, n_mesh, box, ai, af, steps, w, lam_disp=gdisp))
+
+
+def _ics_of(c, n_p, box, a_i, w):
+    """The Zel'dovich state the adjoint's forward map starts from (box units, Mpc/h)."""
+    from oracle import ic
+    psi = ic.za_displacement(ic.linear_delta_k(c, n_p, box, white_noise=w), n_p, box).reshape(3, -1)
+    D, f, E = c.growth_D(a_i), c.growth_f(a_i), float(c.E(a_i))
+    u = adjoint.lattice_fractions(n_p) + D * psi / box
+    return u - np.floor(u), a_i**2 * E * f * D * psi
+
+
+@pytest.mark.parametrize("mode", [adjoint.NEWTON, adjoint.GR_POISSON])
+def test_forward_map_is_the_oracle_run(mode):
+    # the adjoint's own forward map (kept as a list of kicks and drifts) against oracle.pm's run
+    # from the same ICs, Newtonian and Poisson gauge (20 Gpc/h, where the lag term matters)
+    from oracle import pm as opm
+    c = Cosmology()
+    n_p, n_mesh, box, ai, af, steps = 8, 16, 20000.0, 0.1, 0.5, 4
+    w = inputs.gaussian_field(9, n_p)
+    u, p, _, _ = adjoint.forward(c, n_p, n_mesh, box, ai, af, steps, w, mode)
+    u0, p0 = _ics_of(c, n_p, box, ai, w)
+    run = opm.PMRun(c, n_mesh, box, ai, af, steps, u0, p0, mode=opm.GR_POISSON if mode else opm.NEWTON)
+    run.step(steps)
+    d = run.x - u
+    assert np.max(np.abs(d - np.rint(d))) < 1e-13
+    np.testing.assert_allclose(run.p, p, rtol=0, atol=1e-12 * np.max(np.abs(p)))
+
+
+def test_poisson_gauge_vector_jacobian_product():
+    # Poisson gauge at 20 Gpc/h (the lag term 3 calH / dtau is larger than k^2 on the low modes):
+    # a loss of the final density, displacements and momenta; the reverse sweep with the carried
+    # spectrum Z against central differences of the forward map, and far from the Newtonian
+    # gradient of the same loss (so the Poisson-gauge chain is what is checked)
+    c = Cosmology()
+    n_p, n_mesh, box, ai, af, steps = 8, 16, 20000.0, 0.1, 0.5, 4
+    w = inputs.gaussian_field(10, n_p)
+    r = np.random.default_rng(11)
+    f = np.fft.fftfreq(n_mesh, 1.0 / n_mesh)
+    Wk = 1.0 / (1.0 + f[:, None, None]**2 + f[None, :, None]**2 + f[None, None, :]**2)
+    gdisp = r.standard_normal((3, n_p**3)) * 1e-3
+    h = r.standard_normal((3, n_p**3)) * 1e-2
+    mode = adjoint.GR_POISSON
+
+    def L_of(ww, m=mode):
+        u, p, _, _ = adjoint.forward(c, n_p, n_mesh, box, ai, af, steps, ww, m)
+        dk = np.fft.fftn(cic.density_contrast(u, n_mesh))
+        return float(np.sum(Wk * np.abs(dk)**2) / n_mesh**6 + np.sum(gdisp * adjoint.displacement(u, n_p, box))
+                     + np.sum(h * p))
+
+    def cotangents(m):
+        u, _, _, _ = adjoint.forward(c, n_p, n_mesh, box, ai, af, steps, w, m)
+        dk = np.fft.fftn(cic.density_contrast(u, n_mesh))
+        return 2.0 * np.real(np.fft.ifftn(Wk * dk)) / n_mesh**3
+
+    g = adjoint.vjp(c, n_p, n_mesh, box, ai, af, steps, w, lam_delta=cotangents(mode), lam_disp=gdisp, lam_mom=h,
+                    mode=mode)
+    eps = 1e-5
+    for _ in range(3):
+        v = r.standard_normal((n_p,) * 3)
+        fd = (L_of(w + eps * v) - L_of(w - eps * v)) / (2 * eps)
+        assert np.sum(g * v) == pytest.approx(fd, rel=1e-6)
+    gn = adjoint.vjp(c, n_p, n_mesh, box, ai, af, steps, w, lam_delta=cotangents(adjoint.NEWTON), lam_disp=gdisp,
+                     lam_mom=h, mode=adjoint.NEWTON)
+    assert np.linalg.norm(g - gn) > 0.05 * np.linalg.norm(g)
