@@ -328,7 +328,11 @@ pm_status pm_triangle_index(int nbins, int i, int j, int l, int64_t* index);
  * pm_loss_grad is both calls for L(w) = mean_c (delta(c) - delta_t(c))^2 with a device
  * target mesh delta_t: it returns L and writes dL/dw.
  *
- * FP32 Newtonian contexts with the spectral gradient only (PM_ERR_UNSUPPORTED otherwise). */
+ * Newtonian and Poisson-gauge contexts (Sec. 2): in the Poisson gauge each force evaluation's
+ * Phi depends on the previous one through the lagged constraint, so the checkpoints also keep
+ * Phi_old (and the FP64 island), and the transposed force chain carries one spectrum back
+ * through the evaluations (the scratch holds both).  FP32 positions with the spectral gradient
+ * only (PM_ERR_UNSUPPORTED otherwise). */
 pm_status pm_adjoint_scratch_size(const pm_ctx* ctx, int checkpoint_every, size_t* bytes);
 pm_status pm_adjoint_record(pm_ctx* ctx, const void* white_noise, int checkpoint_every, void* scratch,
                             size_t scratch_bytes);

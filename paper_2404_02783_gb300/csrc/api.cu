@@ -1188,6 +1188,9 @@ struct AdjLayout {
     // end positions
     size_t ckpt = 0, seg_x[2] = {0, 0}, seg_g[2] = {0, 0}, lam_u = 0, lam_p = 0, acc = 0;
     size_t re_rho = 0, re_spec[3] = {0, 0, 0}, re_x = 0, close_g = 0, total = 0;
+    // Poisson gauge: Phi_old and the FP64 island at every checkpoint, the re-runs' own, and
+    // the carried spectrum Z of the transposed lagged constraint
+    size_t ckpt_phi = 0, ckpt_isl = 0, re_phi = 0, re_isl = 0, zcarry = 0, isl = 0;
     int nseg = 0, C = 0;
 };
 
@@ -1216,6 +1219,14 @@ AdjLayout adj_plan(const pm_ctx* c, int C) {
     for (int j = 0; j < 3; ++j) A.re_spec[j] = take(spec);
     A.re_x = take(P);
     A.close_g = take(G);  // the force meshes of the closing half kick
+    if (c->L.gr) {
+        A.isl = c->L.has_island ? (size_t)(c->cfg.n_lo + 1) * (2 * c->cfg.n_lo + 1) * (2 * c->cfg.n_lo + 1) * 16 : 0;
+        A.ckpt_phi = take((size_t)A.nseg * spec);
+        A.ckpt_isl = take((size_t)A.nseg * A.isl);
+        A.re_phi = take(spec);
+        A.re_isl = take(A.isl);
+        A.zcarry = take(spec);
+    }
     A.total = off;
     return A;
 }
@@ -1248,7 +1259,7 @@ pm_status fft_inverse_f32(pm_ctx* c, float2* spec, float* real, int n) {
 // then lambda_p += drift_next lambda_u (the transposed drift of the step before; 0: none).
 // V (the context's force meshes) is zero on entry and left zero.
 pm_status adj_kick(pm_ctx* c, const uint32_t* xs, const float* gs, double K, float* lam_u, float* lam_p,
-                   double drift_next) {
+                   double drift_next, const AdjGrOp* gr = nullptr) {
     const int n = c->n;
     const size_t n3 = (size_t)n * n * n;
     const float* G[3] = {gs, gs + n3, gs + 2 * n3};
@@ -1262,15 +1273,16 @@ pm_status adj_kick(pm_ctx* c, const uint32_t* xs, const float* gs, double K, flo
     PM_CK(forward_zy<float>(V[0], sp[0], n, 3, c->st));
     // in place over field 0: each CTA reads and writes only its own columns
     PM_CK(x_adj<float>(sp[0], sp[0], n, c->kf, -1.5 * c->cfg.omega_m / ((double)n * n * n), c->st, V[0],
-                       3 * (int64_t)n3));
+                       3 * (int64_t)n3, gr));
     float* rho_bar = (float*)c->at(c->L.rho);
     PM_CK((y_rows<float, true>(sp[0], (int64_t)(n / 2 + 1) * n, n, c->st)));
     const float2* zin[1] = {sp[0]};
     float* zout[1] = {rho_bar};
     PM_CK(z_c2r<float>(zin, zout, 1, n, 1, 0u, 0.0, c->st));
+    // Newtonian: rho_bar lacks this evaluation's K; Poisson gauge: Z carries every K already
     const double mass = std::pow((double)n / c->np, 3);
-    PM_CK(adj_kick_particles(xs, c->np3, n, lam_p, G, rho_bar, (float)K, (float)(K * mass), (float)drift_next, lam_u,
-                             c->st));
+    PM_CK(adj_kick_particles(xs, c->np3, n, lam_p, G, rho_bar, (float)K, (float)(gr ? mass : K * mass),
+                             (float)drift_next, lam_u, c->st));
     return PM_OK;
 }
 
@@ -1316,6 +1328,29 @@ struct AdjSweep {
     void* seg_g(int k, int i) const { return at(A.seg_g[k & 1] + (size_t)i * Gb); }
     void* ckpt_x(int k) const { return at(A.ckpt + (size_t)k * 2 * P); }
     void* ckpt_p(int k) const { return at(A.ckpt + (size_t)k * 2 * P + P); }
+    size_t spec_bytes() const { return 2 * (size_t)(c->n / 2 + 1) * c->n * c->n * 4; }
+    void* ckpt_phi(int k) const { return at(A.ckpt_phi + (size_t)k * spec_bytes()); }
+    void* ckpt_isl(int k) const { return at(A.ckpt_isl + (size_t)k * A.isl); }
+
+    // Poisson gauge: the transposed operator of force evaluation e (steps e = 0 .. steps - 1
+    // at a_e, the closing kick e = steps at a_final) with kick factor K; its scalars as the
+    // forward evaluation forms them (dtau from the previous evaluation), and those of e + 1.
+    AdjGrOp gr_op(int e, double K) const {
+        AdjGrOp g;
+        auto scalars = [&](int i, double& H, double& om, double& cc) {
+            const double a = c->a_grid(i);
+            H = pmhost::conformal_hubble(c->cosmo, a);
+            om = pmhost::omega_m_a(c->cosmo, a);
+            cc = i > 0 ? 3.0 * H / (pmhost::kCLight * pmhost::kick_integral(c->cosmo, c->a_grid(i - 1), a)) : 0.0;
+        };
+        scalars(e, g.H, g.om, g.cc);
+        if (e < steps) scalars(e + 1, g.H1, g.om1, g.cc1);
+        else g.H1 = g.H, g.om1 = g.om, g.cc1 = 0.0;  // nothing after the closing kick: Z is 0 there
+        const double n3 = (double)c->n * c->n * c->n;
+        g.K_ac2_n3 = K * c->a_grid(e) * pmhost::kCLight * pmhost::kCLight / n3;
+        g.Z = at(A.zcarry);
+        return g;
+    }
 
     // Steps s0..s1-1 of segment k on context r from the positions at rx (p in place), keeping
     // each step's positions and force meshes in record k & 1.  With the fused update each
@@ -1358,6 +1393,12 @@ struct AdjSweep {
             const int s0 = k * S.C, s1 = std::min(steps, s0 + S.C);
             PM_CK(cudaMemcpyAsync(ckpt_x(k), x, P, cudaMemcpyDeviceToDevice, c->st));
             PM_CK(cudaMemcpyAsync(ckpt_p(k), p, P, cudaMemcpyDeviceToDevice, c->st));
+            if (c->L.gr && k > 0) {  // the lagged constraint's history at the segment's start
+                PM_CK(cudaMemcpyAsync(ckpt_phi(k), c->at(c->L.phi_old), spec_bytes(), cudaMemcpyDeviceToDevice,
+                                      c->st));
+                if (A.isl)
+                    PM_CK(cudaMemcpyAsync(ckpt_isl(k), c->at(c->L.island), A.isl, cudaMemcpyDeviceToDevice, c->st));
+            }
             PM_CK(cudaEventRecord(S.ev_ckpt[k], c->st));
             if (k < A.nseg - 2) PM_TRY(pm_step(c, s1 - s0));
             else PM_TRY(record(c, k, x, x));
@@ -1397,6 +1438,8 @@ struct AdjSweep {
         re.ws = (unsigned char*)S.scratch;
         re.L.rho = A.re_rho;
         for (int j = 0; j < 3; ++j) re.L.spec[j] = A.re_spec[j];
+        re.L.phi_old = A.re_phi;
+        re.L.island = A.re_isl;
         auto rerun = [&](int k) -> pm_status {
             PM_CK(cudaStreamWaitEvent(re.st, S.ev_ckpt[k], 0));
             if (k + 2 < A.nseg) PM_CK(cudaStreamWaitEvent(re.st, S.ev_rev[k + 2], 0));  // record k & 1 is free
@@ -1405,25 +1448,44 @@ struct AdjSweep {
             re.step = k * S.C;
             re.synced = (k == 0);
             re.rho_valid = false;
+            if (c->L.gr) {  // the lagged constraint resumes from the checkpoint's history
+                re.have_phi = k > 0;
+                re.a_last = k > 0 ? c->a_grid(k * S.C - 1) : 0.0;
+                if (k > 0) {
+                    PM_CK(cudaMemcpyAsync(re.at(re.L.phi_old), ckpt_phi(k), spec_bytes(), cudaMemcpyDeviceToDevice,
+                                          re.st));
+                    if (A.isl)
+                        PM_CK(cudaMemcpyAsync(re.at(re.L.island), ckpt_isl(k), A.isl, cudaMemcpyDeviceToDevice,
+                                              re.st));
+                }
+            }
             PM_TRY(record(&re, k, re.at(re.L.x), at(A.re_x)));
             PM_CK(cudaEventRecord(S.ev_rerun[k], re.st));
             return PM_OK;
         };
-        // V (the three force meshes, back to back) is zero before the first adjoint deposit
+        // V (the three force meshes, back to back) is zero before the first adjoint deposit,
+        // and so is the carried spectrum of the Poisson gauge before the last evaluation
         PM_CK(cudaMemsetAsync(c->at(c->L.force[0]), 0, Gb, c->st));
+        const bool gr = c->L.gr;
+        if (gr) PM_CK(cudaMemsetAsync(at(A.zcarry), 0, spec_bytes(), c->st));
         // the transposed closing kick at the final positions (only a momentum cotangent sees
         // it), then the transposed drift of the last step gives lam_p
-        if (mom)
+        if (mom) {
+            const AdjGrOp og = gr_op(steps, close_kick());
             PM_TRY(adj_kick(c, (const uint32_t*)c->at(c->L.x), (const float*)at(A.close_g), close_kick(), lam_u, lam_p,
-                            drift_of_step(c, steps - 1) / box));
-        else
+                            drift_of_step(c, steps - 1) / box, gr ? &og : nullptr));
+        } else {
             PM_CK(axpby(lam_p, lam_u, nullptr, 3 * c->np3, (float)(drift_of_step(c, steps - 1) / box), 0.0f, c->st));
+        }
         for (int k = A.nseg - 1; k >= 0; --k) {
             const int s0 = k * S.C, s1 = std::min(steps, s0 + S.C);
             if (k < A.nseg - 2) PM_CK(cudaStreamWaitEvent(c->st, S.ev_rerun[k], 0));
-            for (int s = s1 - 1; s >= s0; --s)
+            for (int s = s1 - 1; s >= s0; --s) {
+                const AdjGrOp og = gr_op(s, kick_of_step(c, s));
                 PM_TRY(adj_kick(c, (const uint32_t*)seg_x(k, s - s0), (const float*)seg_g(k, s - s0),
-                                kick_of_step(c, s), lam_u, lam_p, s > 0 ? drift_of_step(c, s - 1) / box : 0.0));
+                                kick_of_step(c, s), lam_u, lam_p, s > 0 ? drift_of_step(c, s - 1) / box : 0.0,
+                                gr ? &og : nullptr));
+            }
             PM_CK(cudaEventRecord(S.ev_rev[k], c->st));
             if (k >= 2) PM_TRY(rerun(k - 2));
         }
@@ -1451,8 +1513,8 @@ struct AdjSweep {
 // the session's events for checkpoint interval C.
 pm_status adj_prepare(pm_ctx* c, int checkpoint_every, void* scratch, size_t scratch_bytes) {
     if (checkpoint_every < 1) return fail(PM_ERR_INVALID_ARG, "bad checkpoint interval");
-    if (c->cfg.precision != PM_FP32_FIXED || c->cfg.mode != PM_NEWTON || c->cfg.gradient != PM_GRAD_SPECTRAL)
-        return fail(PM_ERR_UNSUPPORTED, "the gradient is implemented for the FP32 Newtonian step with the spectral force");
+    if (c->cfg.precision != PM_FP32_FIXED || c->cfg.gradient != PM_GRAD_SPECTRAL)
+        return fail(PM_ERR_UNSUPPORTED, "the gradient is implemented for the FP32 step with the spectral force");
     const int C = std::min(checkpoint_every, c->cfg.n_steps);
     const AdjLayout A = adj_plan(c, C);
     if (!scratch || scratch_bytes < A.total || (uintptr_t)scratch % 256)

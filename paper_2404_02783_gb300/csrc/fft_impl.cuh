@@ -870,12 +870,13 @@ __global__ void __launch_bounds__(PlaneShape<T, LOGN>::THREADS, PlaneShape<T, LO
 // adjoint momenta V_j (fields j = 0, 1, 2 back to back, [kz][x][ky]) are transformed
 // along x one after the other and accumulated as out = sum_j i k_j c(k) V_j,
 // c = coef / (kf^2 |n|^2) (zero mode 0, k_j = 0 at its Nyquist index), then transformed
-// back along x into out ([kz][x][ky], ready for the inverse y and z passes).
-template <typename T, int LOGN>
+// back along x into out ([kz][x][ky], ready for the inverse y and z passes).  GR: the
+// Poisson-gauge operator of AdjGrOp instead of c(k), with the carried spectrum gr.Z.
+template <typename T, int LOGN, bool GR>
 __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) k_x_adj(const cplx<T>* V,
                                                                       cplx<T>* out, double kf,
                                                                       double coef, float4* __restrict__ zero,
-                                                                      int64_t nzero4) {
+                                                                      int64_t nzero4, AdjGrOp gr) {
     typedef cplx<T> C;
     typedef Shape<T, LOGN> S;
     constexpr int N = S::N, M = S::M, Q = S::QN, CB = S::CB;
@@ -922,13 +923,36 @@ __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) k_x_adj(const cpl
         }
     }
     C w[1][8];
+    if constexpr (GR) {
+        // per-evaluation constants in the working precision; den and src / carry per mode
+        const T kf2 = kfT * kfT, H = T(gr.H), H1 = T(gr.H1);
+        const T base = T(3) * H * H + T(4.5) * H * H * T(gr.om) + T(gr.cc);
+        const T base1 = T(3) * H1 * H1 + T(4.5) * H1 * H1 * T(gr.om1) + T(gr.cc1);
+        const T num = T(-1.5) * H * H * T(gr.om), cc1 = T(gr.cc1), KA = T(gr.K_ac2_n3);
+        C* Zc = reinterpret_cast<C*>(gr.Z);
 #pragma unroll
-    for (int m = 0; m < 8; ++m) {
-        const int i = t + m * Q;
-        const int nx = (i < M) ? i : i - N;
-        const int n2 = nx * nx + ny * ny + kz * kz;
-        const T cc = (n2 == 0) ? T(0) : coefT / T(n2);
-        w[0][m] = cmake<C>(-cc * acc[m].y, cc * acc[m].x);  // i c sum_j k_j V_j
+        for (int m = 0; m < 8; ++m) {
+            const int i = t + m * Q;
+            const int nx = (i < M) ? i : i - N;
+            const int n2 = nx * nx + ny * ny + kz * kz;
+            const T k2 = kf2 * T(n2);
+            const T src = (n2 == 0) ? T(0) : div_mode(num, k2 + base);
+            const T carry = (n2 == 0) ? T(0) : div_mode(cc1, k2 + base1);
+            const size_t zi = pbase + (size_t)i * N + c;
+            const C zo = Zc[zi];
+            const C Z = cmake<C>(-KA * acc[m].y + carry * zo.x, KA * acc[m].x + carry * zo.y);  // K a c^2 W + carry Z
+            Zc[zi] = Z;
+            w[0][m] = cscale(Z, src);
+        }
+    } else {
+#pragma unroll
+        for (int m = 0; m < 8; ++m) {
+            const int i = t + m * Q;
+            const int nx = (i < M) ? i : i - N;
+            const int n2 = nx * nx + ny * ny + kz * kz;
+            const T cc = (n2 == 0) ? T(0) : coefT / T(n2);
+            w[0][m] = cmake<C>(-cc * acc[m].y, cc * acc[m].x);  // i c sum_j k_j V_j
+        }
     }
     fft_regs<N, 1, true>(w, t, tw, ex);
 #pragma unroll
@@ -1081,14 +1105,21 @@ cudaError_t plane_n(cplx<T>* A, cplx<T>* GX, cplx<T>* GY, int nplanes, const Spe
 
 template <typename T, int LOGN>
 cudaError_t x_adj_n(const cplx<T>* V, cplx<T>* out, double kf, double coef, float* zero, int64_t nzero,
-                    cudaStream_t st) {
+                    cudaStream_t st, const AdjGrOp* gr) {
     typedef Shape<T, LOGN> S;
     const size_t smem = sizeof(cplx<T>) * (S::N + 2 * (size_t)S::N * (S::CB + 1));
-    cudaError_t e = set_smem((const void*)k_x_adj<T, LOGN>, smem);
+    const void* fn = gr ? (const void*)k_x_adj<T, LOGN, true> : (const void*)k_x_adj<T, LOGN, false>;
+    cudaError_t e = set_smem(fn, smem);
     if (e != cudaSuccess) return e;
     if (nzero % 4 != 0 || (zero && (uintptr_t)zero % 16 != 0)) return cudaErrorInvalidValue;
-    k_x_adj<T, LOGN><<<dim3(S::N / S::CB, S::M + 1), S::CB * S::QN, smem, st>>>(V, out, kf, coef, (float4*)zero,
-                                                                                zero ? nzero / 4 : 0);
+    if (gr && !gr->Z) return cudaErrorInvalidValue;
+    const dim3 grid(S::N / S::CB, S::M + 1);
+    if (gr)
+        k_x_adj<T, LOGN, true><<<grid, S::CB * S::QN, smem, st>>>(V, out, kf, coef, (float4*)zero, zero ? nzero / 4 : 0,
+                                                                  *gr);
+    else
+        k_x_adj<T, LOGN, false><<<grid, S::CB * S::QN, smem, st>>>(V, out, kf, coef, (float4*)zero,
+                                                                   zero ? nzero / 4 : 0, AdjGrOp());
     return cudaGetLastError();
 }
 
@@ -1177,8 +1208,8 @@ cudaError_t fft_plane(cplx<T>* A, cplx<T>* GX, cplx<T>* GY, int nplanes, int n, 
 
 template <typename T>
 cudaError_t x_adj(const cplx<T>* V, cplx<T>* out, int n, double kf, double coef, cudaStream_t st, float* zero,
-                  int64_t nzero) {
-    PM_DISPATCH_LOGN(n, (x_adj_n<T, LG>(V, out, kf, coef, zero, nzero, st)))
+                  int64_t nzero, const AdjGrOp* gr) {
+    PM_DISPATCH_LOGN(n, (x_adj_n<T, LG>(V, out, kf, coef, zero, nzero, st, gr)))
 }
 
 template <typename T>
@@ -1208,7 +1239,7 @@ cudaError_t x_cols(cplx<T>* data, cplx<T>* out2, int nplanes, int n, const SpecO
     template cudaError_t x_cols<T>(cplx<T>*, cplx<T>*, int, int, const SpecOp&, cudaStream_t);      \
     template cudaError_t forward_zy<T>(const T*, cplx<T>*, int, int, cudaStream_t);                     \
     template cudaError_t x_adj<T>(const cplx<T>*, cplx<T>*, int, double, double, cudaStream_t, float*, \
-                                  int64_t);                                                             \
+                                  int64_t, const AdjGrOp*);                                             \
     template cudaError_t inverse_yz_grad<T>(cplx<T>*, cplx<T>*, cplx<T>*, T* const*, int, int, double,   \
                                             cudaStream_t, const double*);
 

@@ -92,9 +92,21 @@ cudaError_t bin_rows_sum(const double* rows, int nrows, int nbins, double* out, 
 // of the deposited adjoint momenta back to back; out = IFFT_x[sum_j i k_j c(k) FFT_x V_j]
 // with c = coef / (kf^2 |n|^2).  Also sets zero[0 .. nzero) to 0 (a buffer the caller is
 // done with; nzero a multiple of 4, zero 16-byte aligned; null: nothing).
+// Poisson gauge (gr != null): the lagged constraint Phi_n = src_n delta_n + carry_n Phi_{n-1}
+// (src = -(3/2) calH^2 Om(a) / den, carry = cc / den, den = k^2 + 3 calH^2 + (9/2) calH^2 Om(a) + cc,
+// cc = 3 calH / dtau, 0 at the first evaluation) makes the transposed chain carry one spectrum
+// back through the evaluations: Z_n = K_n a_n c^2 / n^3 W_n + carry_{n+1} Z_{n+1} (Z in gr->Z,
+// [kz][kx][ky], read and overwritten; zero before the last evaluation is reversed),
+// out = IFFT_x[src_n Z_n], W_n = sum_j i k_j FFT_x V_j.  coef is then unused.
+struct AdjGrOp {
+    double K_ac2_n3 = 0.0;             // K_n a_n c^2 / n^3 of evaluation n
+    double H = 0.0, om = 0.0, cc = 0.0;    // calH, Om(a) and cc of evaluation n
+    double H1 = 0.0, om1 = 0.0, cc1 = 0.0; // the same of evaluation n + 1 (any finite values when Z is 0)
+    void* Z = nullptr;
+};
 template <typename T>
 cudaError_t x_adj(const cplx<T>* V, cplx<T>* out, int n, double kf, double coef, cudaStream_t st,
-                  float* zero = nullptr, int64_t nzero = 0);
+                  float* zero = nullptr, int64_t nzero = 0, const AdjGrOp* gr = nullptr);
 // Forward y, x with the per-mode operator op (OP_NEWTON or OP_GR) and inverse y with the y
 // gradient of nplanes kz planes in one persistent launch of CTAs of `threads` (256, 512, 1024)
 // (FP32, n = 256, 512, 1024): on entry

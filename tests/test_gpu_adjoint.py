@@ -258,3 +258,63 @@ def test_gradient_at_the_differentiable_configuration_against_32_directions():
     assert np.mean(rel < 2e-2) >= 0.8, rel
     # against the typical size of a directional derivative, no direction is far off
     assert np.max(np.abs(fd - ad)) < 0.2 * np.sqrt(np.mean(ad**2)), rel
+
+
+def _gr_case(pm, box, n_lo, steps=4, np_side=16, nmesh=32, a_i=0.1, a_f=0.5):
+    c = Cosmology()
+    w = inputs.gaussian_field(31, np_side).astype(np.float32)
+    run = pm.PMRun(pm.make_config(np_side, nmesh, box, a_i, a_f, steps, mode=1, n_lo=n_lo))
+    return c, w, run
+
+
+@pytest.mark.parametrize("box,n_lo,vs_newton", [(2000.0, 0, 0.02), (20000.0, 0, 0.2), (20000.0, 4, 0.2)])
+def test_poisson_gauge_gradient_matches_fp64_oracle(box, n_lo, vs_newton):
+    # Sec. 2's lagged constraint: the GPU reverse sweep (checkpoints with Phi_old and the FP64
+    # island, the carried spectrum in the transposed x pass) against the oracle's Poisson-gauge
+    # vector-Jacobian product for a loss of the final density, displacements and momenta; the
+    # Newtonian gradient of the same loss differs by more than vs_newton, so the lag is exercised
+    # (measured: 2.5e-7 - 8e-5 against the oracle, 4% and 55% from the Newtonian gradient)
+    pm = lib()
+    nmesh, np_side, a_i, a_f, steps = 32, 16, 0.1, 0.5, 4
+    c, w, run = _gr_case(pm, box, n_lo)
+    Wk = _spectral_weight(nmesh)
+    r = np.random.default_rng(8)
+    gdisp = r.standard_normal((3, np_side**3)) * 1e-3
+    h = r.standard_normal((3, np_side**3)) * 1e-2
+    wv = to_dev(w).requires_grad_(True)
+    delta, disp, mom = pm.run_fields(run, wv, checkpoint_every=2, momenta=True)
+    L = _torch_loss(delta, disp, to_dev(Wk), to_dev(gdisp), nmesh) + (to_dev(h) * mom.to(torch.float64)).sum()
+    L.backward()
+    g = to_host(wv.grad).astype(np.float64)
+    w64 = w.astype(np.float64)
+    u, p_o, _, _ = adjoint.forward(c, np_side, nmesh, box, a_i, a_f, steps, w64, adjoint.GR_POISSON)
+    dk = np.fft.fftn(cic.density_contrast(u, nmesh))
+    lam_delta = 2.0 * np.real(np.fft.ifftn(Wk * dk)) / nmesh**3
+    go = adjoint.vjp(c, np_side, nmesh, box, a_i, a_f, steps, w64, lam_delta=lam_delta, lam_disp=gdisp, lam_mom=h,
+                     mode=adjoint.GR_POISSON)
+    gn = adjoint.vjp(c, np_side, nmesh, box, a_i, a_f, steps, w64, lam_delta=lam_delta, lam_disp=gdisp, lam_mom=h,
+                     mode=adjoint.NEWTON)
+    assert rel_l2(g, go) < 1e-3
+    assert rel_l2(gn, go) > vs_newton
+    assert rel_l2(to_host(mom).astype(np.float64), p_o) < 1e-3
+    assert rel_l2(to_host(disp).astype(np.float64), adjoint.displacement(u, np_side, box)) < 1e-3
+
+
+def test_poisson_gauge_gradient_across_checkpoint_intervals_and_the_mse():
+    # 8 steps at 20 Gpc/h: with checkpoints every 1 or 2 steps the earlier segments are re-run
+    # from checkpoints that restore Phi_old and the island; the gradient equals that of one
+    # segment, and pm_loss_grad's MSE gradient equals the oracle's
+    pm = lib()
+    c, w, run = _gr_case(pm, 20000.0, 4, steps=8)
+    ut, _, _, _ = adjoint.forward(c, 16, 32, 20000.0, 0.1, 0.5, 8, inputs.gaussian_field(32, 16), adjoint.GR_POISSON)
+    target = cic.density_contrast(ut, 32).astype(np.float32)
+    wd, td = to_dev(w), to_dev(target)
+    L8, g8 = run.loss_grad(wd, td, checkpoint_every=8)
+    for every in (1, 2, 3):
+        L, g = run.loss_grad(wd, td, checkpoint_every=every)
+        assert L == pytest.approx(L8, rel=1e-6)
+        assert rel_l2(to_host(g), to_host(g8)) < 1e-5
+    Lo, go = adjoint.loss_and_grad(c, 16, 32, 20000.0, 0.1, 0.5, 8, w.astype(np.float64), target.astype(np.float64),
+                                   mode=adjoint.GR_POISSON)
+    assert L8 == pytest.approx(Lo, rel=1e-3)
+    assert rel_l2(to_host(g8).astype(np.float64), go) < 1e-2
