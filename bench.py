@@ -454,22 +454,39 @@ def adjoint(pm, torch, args):
     t_fwd = timed(forward)
     t_grad = timed(lambda: run.loss_grad(w, target, checkpoint_every=every))
     # the general path: record the run, then the reverse sweep with cotangents on the final
-    # density and displacements (what run_fields' backward hands to pm_adjoint_run)
+    # density, displacements and momenta (what run_fields' backward hands to pm_adjoint_run)
     cot_d = torch.randn((n,) * 3, generator=g, device="cuda", dtype=torch.float32)
     cot_x = torch.randn((3, np_side**3), generator=g, device="cuda", dtype=torch.float32)
+    cot_p = torch.randn((3, np_side**3), generator=g, device="cuda", dtype=torch.float32)
 
-    def record_and_adjoint():
-        run.record(w, every)
-        return run.adjoint(d_delta=cot_d, d_disp=cot_x)
+    def record_and_adjoint(r):
+        r.record(w, every)
+        return r.adjoint(d_delta=cot_d, d_disp=cot_x, d_mom=cot_p)
 
-    t_vjp = timed(record_and_adjoint)
+    t_vjp = timed(lambda: record_and_adjoint(run))
+    del run
+    # the same in the Poisson gauge on the horizon-scale box (lagged constraint, FP64 island)
+    gr = pm.PMRun(pm.make_config(np_side, n, 4000.0, A_INIT, A_FINAL, steps, mode=pm.PM_GR_POISSON, n_lo=4))
+
+    def forward_gr():
+        gr.ic(white_noise=w)
+        gr.step(steps)
+        return gr.density()
+
+    t_fwd_gr = timed(forward_gr)
+    t_vjp_gr = timed(lambda: record_and_adjoint(gr))
+    del gr
+    torch.cuda.empty_cache()
     return {"workload": f"{np_side}^3 particles, {n}^3 mesh, L=2000 Mpc/h, {steps} FP32 steps, "
                         f"checkpoints every {every} steps; gradient with respect to the white-noise field",
             "forward_ms": 1e3 * t_fwd, "loss_grad_ms": 1e3 * t_grad, "cost_ratio": t_grad / t_fwd,
             "record_and_adjoint_ms": 1e3 * t_vjp, "record_and_adjoint_cost_ratio": t_vjp / t_fwd,
+            "poisson_gauge": {"workload": f"as above in the Poisson gauge at L=4000 Mpc/h (n_lo=4)",
+                              "forward_ms": 1e3 * t_fwd_gr, "record_and_adjoint_ms": 1e3 * t_vjp_gr,
+                              "record_and_adjoint_cost_ratio": t_vjp_gr / t_fwd_gr},
             "what": "loss_grad: mean-square density loss (forward with checkpoints + reverse sweep); "
                     "record_and_adjoint: pm_adjoint_record + pm_adjoint_run with cotangents on the final "
-                    "density and displacements (any loss)",
+                    "density, displacements and momenta (any loss)",
             "value": np_side**3 * steps / t_grad, "unit": "particle-steps/s (forward + reverse)"}
 
 
@@ -834,6 +851,9 @@ def main():
     ap.add_argument("--no-estimators", action="store_true")
     ap.add_argument("--no-compare", action="store_true", help="skip the separate-FFT-passes comparison")
     ap.add_argument("--cpu-row-steps", type=int, default=1, help="oracle steps timed per --cpu-rows size")
+    ap.add_argument("--fft-form", type=int, default=None,
+                    help="form of the FFT passes (pm_set_fused_fft) instead of pm_autotune_fft's pick; profiler "
+                         "runs use it, since timings taken under a profiler do not rank the forms")
     ap.add_argument("--cpu-rows", default="128",
                     help="comma-separated oracle sizes timed per step (e.g. 128,256,512); empty: none")
     args = ap.parse_args()
@@ -882,7 +902,8 @@ def main():
     peak, peak_kind = peaks()
     clocks = Clocks(local if world > 1 else 0)
     clocks.start()
-    ms32, ph32, tuned = bench_precision(pm, torch, args, pm.PM_FP32_FIXED, rank, world, clocks)
+    ms32, ph32, tuned = bench_precision(pm, torch, args, pm.PM_FP32_FIXED, rank, world, clocks,
+                                        fft_threads=args.fft_form)
     clk = clocks.stop()
     value = world * args.np**3 * args.steps / (ms32 * 1e-3)
     ms_step = ms32 / args.steps
