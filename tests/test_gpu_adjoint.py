@@ -223,15 +223,17 @@ def test_adjoint_run_needs_its_own_recorded_run():
 
 
 @pytest.mark.slow
-def test_gradient_at_the_differentiable_configuration_against_32_directions():
+@pytest.mark.parametrize("mode,box,n_lo", [(0, 2000.0, 0), (1, 4000.0, 4)])
+def test_gradient_at_the_differentiable_configuration_against_32_directions(mode, box, n_lo):
     # the differentiable workload itself: 128^3 particles on a 128^3 mesh, L = 2000 Mpc/h, 50 FP32
     # steps, checkpoints every 10, the MSE to a second-seed run; the reverse sweep's directional
     # derivatives against central differences of the GPU loss (eps = 1e-3 in noise units) on 32
     # random directions.  Measured: median relative difference 1.9e-3; a few directions with a
     # small derivative or a particle crossing a CIC cell boundary within eps differ by a few percent.
+    # The same in the Poisson gauge on the horizon-scale box (L = 4000 Mpc/h, FP64 island n_lo = 4).
     pm = lib()
     n, steps, every, eps = 128, 50, 10, 1e-3
-    run = pm.PMRun(pm.make_config(n, n, 2000.0, 1.0 / 51.0, 1.0, steps))
+    run = pm.PMRun(pm.make_config(n, n, box, 1.0 / 51.0, 1.0, steps, mode=mode, n_lo=n_lo))
     run.ic(seed=2)
     run.step(steps)
     target = run.density().clone()
