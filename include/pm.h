@@ -103,7 +103,7 @@ typedef struct {
     int precision;     /* PM_FP32_FIXED or PM_FP64 */
     int n_lo;          /* GR only: modes with |n|^2 <= n_lo^2 are solved and stored in FP64 */
     int gradient;      /* PM_GRAD_SPECTRAL (0) or PM_GRAD_FD1; pm_batch_* refuse FD1
-                          (PM_ERR_INVALID_ARG), pm_loss_grad too (PM_ERR_UNSUPPORTED) */
+                          (PM_ERR_INVALID_ARG), the gradient calls too (PM_ERR_UNSUPPORTED) */
 } pm_config;
 
 typedef struct pm_ctx pm_ctx;   /* opaque host object owned by the library */
