@@ -332,8 +332,12 @@ pm_status compute_forces_t(pm_ctx* c, double a) {
     } else {
         PM_TRY(forward_to_y<T>(c, rho, s0, n));
     }
-    if (fused_update(c)) {
-        // the forward z pass has consumed rho: clear it for the fused deposit of the update
+    // the forward z pass has consumed rho: the fused update deposits the next density there, so
+    // it is cleared, by the inverse z pass of the separate passes (beside the force rows it
+    // writes) or else here
+    const bool clear_in_z = fused_update(c) && !fused_middle(c) && !plane_middle(c) &&
+                            c->cfg.gradient == PM_GRAD_SPECTRAL;
+    if (fused_update(c) && !clear_in_z) {
         Phase ph(c, PM_PHASE_DEPOSIT);
         PM_CK(cudaMemsetAsync(rho, 0, sizeof(T) * (size_t)n * n * n, c->st));
     }
@@ -395,7 +399,7 @@ pm_status compute_forces_t(pm_ctx* c, double a) {
         }
         Phase ph(c, PM_PHASE_FFT_YZ_INV);
         T* out[3] = {(T*)c->force(0), (T*)c->force(1), (T*)c->force(2)};
-        PM_CK(inverse_yz_grad<T>(s0, s1, s2, out, n, 1, c->kf, c->st));
+        PM_CK(inverse_yz_grad<T>(s0, s1, s2, out, n, 1, c->kf, c->st, nullptr, clear_in_z ? (T*)rho : nullptr));
     }
     if (c->cfg.mode == PM_GR_POISSON) {
         c->have_phi = true;
@@ -1714,9 +1718,11 @@ pm_status batch_forces(pm_batch* b, cudaStream_t s, int r0, int c) {
     float2* s2 = (float2*)b->at(b->SPEC[2]) + r0 * nspec;
     const double* kf = (const double*)b->at(b->KF) + r0;
     const bool plane = b->fft_form == 1 && (n == 64 || n == 128);
+    // rho, consumed by the forward z pass, receives the update's deposit next: the inverse z pass
+    // of the separate passes clears it beside its force rows, else a memset does
     if (plane) PM_CK(z_r2c<float>(rho, s0, n, c, s));
     else PM_CK(forward_zy<float>(rho, s0, n, c, s));
-    PM_CK(cudaMemsetAsync(rho, 0, sizeof(float) * c * n3, s));
+    if (plane) PM_CK(cudaMemsetAsync(rho, 0, sizeof(float) * c * n3, s));
     SpecOp op;
     op.kind = OP_NEWTON;
     op.fwd = 1;
@@ -1732,7 +1738,7 @@ pm_status batch_forces(pm_batch* b, cudaStream_t s, int r0, int c) {
         return PM_OK;
     }
     PM_CK(x_cols<float>(s0, s1, c * (M + 1), n, op, s));
-    PM_CK(inverse_yz_grad<float>(s0, s1, s2, out, n, c, 0.0, s, kf));
+    PM_CK(inverse_yz_grad<float>(s0, s1, s2, out, n, c, 0.0, s, kf, rho));
     return PM_OK;
 }
 

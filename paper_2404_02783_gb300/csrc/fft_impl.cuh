@@ -142,6 +142,7 @@ __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 4 : 2) k_z_r2c(const T* 
 template <typename T> struct Ptr3 {
     const cplx<T>* in[3];
     T* out[3];
+    T* zero = nullptr;  // optional mesh of the same shape as out, set to 0 by the component-0 CTAs
 };
 
 template <typename T, int LOGN>
@@ -218,6 +219,11 @@ __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 4 : 2) k_z_c2r(Ptr3<T> P
     C* orow = reinterpret_cast<C*>(pout + (g * N + y0 + b) * N);
 #pragma unroll
     for (int m = 0; m < 8; ++m) orow[t + m * Q] = v[0][m];
+    if (P.zero && comp == 0) {  // the same rows of the mesh the caller clears for its next use
+        C* zrow = reinterpret_cast<C*>(P.zero + (g * N + y0 + b) * N);
+#pragma unroll
+        for (int m = 0; m < 8; ++m) zrow[t + m * Q] = cmake<C>(T(0), T(0));
+    }
 }
 
 // =============================================================== y: contiguous rows
@@ -1017,7 +1023,7 @@ cudaError_t forward_zy_n(const T* in, cplx<T>* spec, int batch, cudaStream_t st)
 // one half spectrum for IFFT_y(-i ky A).
 template <typename T, int LOGN>
 cudaError_t inverse_yz_grad_n(cplx<T>* A, cplx<T>* B, cplx<T>* scratch, T* const* out, int batch, double kf,
-                              const double* kf_arr, cudaStream_t st) {
+                              const double* kf_arr, cudaStream_t st, T* zero) {
     constexpr int N = 1 << LOGN, M = N / 2;
     const int64_t rows = (int64_t)batch * (M + 1) * N;
     cudaError_t e = y_grad3_n<T, LOGN>(A, B, A, B, scratch, rows, kf, st, kf_arr, (int64_t)(M + 1) * N);
@@ -1027,6 +1033,7 @@ cudaError_t inverse_yz_grad_n(cplx<T>* A, cplx<T>* B, cplx<T>* scratch, T* const
     P.in[1] = scratch;  // IFFT_y(-i ky phi)   -> g_y
     P.in[2] = A;        // IFFT_y(phi), -i kz  -> g_z
     for (int j = 0; j < 3; ++j) P.out[j] = out[j];
+    P.zero = zero;
     return z_c2r_n<T, LOGN>(P, 3, N * batch, 4u, kf, st, kf_arr);
 }
 
@@ -1219,8 +1226,8 @@ cudaError_t forward_zy(const T* in, cplx<T>* spec, int n, int batch, cudaStream_
 
 template <typename T>
 cudaError_t inverse_yz_grad(cplx<T>* A, cplx<T>* B, cplx<T>* scratch, T* const* out, int n, int batch, double kf,
-                            cudaStream_t st, const double* kf_arr) {
-    PM_DISPATCH_LOGN(n, (inverse_yz_grad_n<T, LG>(A, B, scratch, out, batch, kf, kf_arr, st)))
+                            cudaStream_t st, const double* kf_arr, T* zero) {
+    PM_DISPATCH_LOGN(n, (inverse_yz_grad_n<T, LG>(A, B, scratch, out, batch, kf, kf_arr, st, zero)))
 }
 
 template <typename T>
@@ -1241,6 +1248,6 @@ cudaError_t x_cols(cplx<T>* data, cplx<T>* out2, int nplanes, int n, const SpecO
     template cudaError_t x_adj<T>(const cplx<T>*, cplx<T>*, int, double, double, cudaStream_t, float*, \
                                   int64_t, const AdjGrOp*);                                             \
     template cudaError_t inverse_yz_grad<T>(cplx<T>*, cplx<T>*, cplx<T>*, T* const*, int, int, double,   \
-                                            cudaStream_t, const double*);
+                                            cudaStream_t, const double*, T*);
 
 }  // namespace pm

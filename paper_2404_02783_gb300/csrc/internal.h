@@ -132,8 +132,9 @@ cudaError_t forward_zy(const T* in, cplx<T>* spec, int n, int batch, cudaStream_
 // The three force meshes from phi and -i kx phi after the inverse x pass (A, B, full
 // layout; both overwritten): out[0] = c2r(IFFT_y(B)), out[1] = c2r(IFFT_y(-i ky A)),
 // out[2] = c2r(-i kz IFFT_y(A)); scratch holds one half spectrum per field.
+// zero (optional): a mesh set to 0 in the same pass (rows written beside the force rows).
 template <typename T>
 cudaError_t inverse_yz_grad(cplx<T>* A, cplx<T>* B, cplx<T>* scratch, T* const* out, int n, int batch, double kf,
-                            cudaStream_t st, const double* kf_arr = nullptr);
+                            cudaStream_t st, const double* kf_arr = nullptr, T* zero = nullptr);
 
 }  // namespace pm
