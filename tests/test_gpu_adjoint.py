@@ -320,3 +320,23 @@ def test_poisson_gauge_gradient_across_checkpoint_intervals_and_the_mse():
                                    mode=adjoint.GR_POISSON)
     assert L8 == pytest.approx(Lo, rel=1e-3)
     assert rel_l2(to_host(g8).astype(np.float64), go) < 1e-2
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_gradient_with_the_persistent_fft_form(mode):
+    # a 256^3 mesh whose forward passes run the fused persistent kernel (pm_set_fused_fft 512):
+    # the sweep's re-runs take the separate passes (their scratch has no sync words), so the
+    # records and the recorded run agree up to FP32 rounding; the gradient is the separate-pass one
+    pm = lib()
+    np_side, nmesh, steps = 32, 256, 6
+    box = 2000.0 if mode == 0 else 20000.0
+    run = pm.PMRun(pm.make_config(np_side, nmesh, box, 0.1, 0.5, steps, mode=mode, n_lo=4 if mode else 0))
+    w = to_dev(inputs.gaussian_field(41, np_side).astype(np.float32))
+    cot = to_dev(np.random.default_rng(13).standard_normal((3, np_side**3)).astype(np.float32))
+    out = {}
+    for form in (0, 512):
+        pm.pm_set_fused_fft(run.ctx, form)
+        run.record(w, 2)
+        out[form] = to_host(run.adjoint(d_disp=cot, d_mom=cot)).astype(np.float64)
+    assert np.max(np.abs(out[0])) > 0
+    assert rel_l2(out[512], out[0]) < 1e-4
