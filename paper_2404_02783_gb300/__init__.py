@@ -32,7 +32,7 @@ _STATUS = {0: "PM_OK", 1: "PM_ERR_INVALID_ARG", 2: "PM_ERR_CUDA", 3: "PM_ERR_WOR
 EXPORTS = ("pm_workspace_size", "pm_init", "pm_destroy", "pm_ic_zeldovich", "pm_step", "pm_particles",
            "pm_set_particles", "pm_set_state", "pm_state", "pm_set_fused_fft", "pm_autotune_fft", "pm_profile", "pm_timings", "pm_density", "pm_potential", "pm_displacement_correction", "pm_power", "pm_halo_proxy", "pm_linear_bias",
            "pm_bispectrum_scratch_size", "pm_bispectrum", "pm_triangle_index", "pm_b1_gr_theory", "pm_cic_deposit", "pm_cic_interp",
-           "pm_adjoint_scratch_size", "pm_adjoint_record", "pm_adjoint_run", "pm_loss_grad", "pm_displacement", "pm_batch_workspace_size", "pm_batch_init", "pm_batch_destroy", "pm_batch_context", "pm_batch_ic",
+           "pm_adjoint_scratch_size", "pm_adjoint_record", "pm_adjoint_run", "pm_loss_grad", "pm_displacement", "pm_positions", "pm_batch_workspace_size", "pm_batch_init", "pm_batch_destroy", "pm_batch_context", "pm_batch_ic",
            "pm_batch_step", "pm_batch_state", "pm_batch_power", "pm_batch_bias", "pm_batch_set_chunk", "pm_batch_autotune", "pm_batch_set_fft", "pm_batch_tuning",
            "pm_cell_sort_scratch_size", "pm_cell_sort", "pm_cell_sort_static", "pm_div_mode_check", "pm_fft_r2c", "pm_fft_c2r", "pm_version", "pm_last_error")
 
@@ -101,6 +101,7 @@ def lib():
         "pm_adjoint_scratch_size": (vp, i, ctypes.POINTER(sz)),
         "pm_loss_grad": (vp, vp, vp, i, vp, sz, pd, vp),
         "pm_adjoint_record": (vp, vp, i, vp, sz),
+        "pm_positions": (vp, vp),
         "pm_adjoint_run": (vp, vp, vp, vp, vp),
         "pm_displacement": (vp, vp),
         "pm_batch_workspace_size": (cfgp, i, ctypes.POINTER(sz)),
@@ -267,6 +268,10 @@ def pm_adjoint_record(ctx, white_noise, checkpoint_every, scratch):
 
 def pm_adjoint_run(ctx, d_delta, d_disp, grad_w, d_mom=None):
     _check(lib().pm_adjoint_run(ctx, _ptr(d_delta), _ptr(d_disp), _ptr(d_mom), _ptr(grad_w)))
+
+
+def pm_positions(ctx, out):
+    _check(lib().pm_positions(ctx, _ptr(out)))
 
 
 def pm_potential(ctx, out):
@@ -489,6 +494,13 @@ class PMRun:
         c = lambda t: None if t is None else t.contiguous()
         pm_adjoint_run(self.ctx, c(d_delta), c(d_disp), grad, d_mom=c(d_mom))
         return grad
+
+    def positions(self):
+        """Positions in Mpc/h in [0, L), shape (3, np^3) (float32 from the FP32 ticks)."""
+        import torch
+        out = torch.empty((3, self.count), dtype=self.rdtype, device=self.device)
+        pm_positions(self.ctx, out)
+        return out
 
     def displacement(self):
         """Lagrangian displacements x - q (minimum image, Mpc/h), shape (3, np^3)."""

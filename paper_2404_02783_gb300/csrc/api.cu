@@ -818,6 +818,12 @@ pm_status pm_displacement(pm_ctx* c, void* disp) {
     return PM_OK;
 }
 
+pm_status pm_positions(pm_ctx* c, void* out) {
+    if (!c || !out) return fail(PM_ERR_INVALID_ARG, "null argument");
+    PM_CK(positions_mpc(c->at(c->L.x), out, c->np3, c->cfg.precision, c->cfg.box, c->st));
+    return PM_OK;
+}
+
 pm_status pm_state(pm_ctx* c, int* step, double* a, int* synchronised) {
     if (!c) return fail(PM_ERR_INVALID_ARG, "null context");
     if (step) *step = c->step;

@@ -851,6 +851,26 @@ cudaError_t lagrangian_displacement(const void* x, void* d, int np, int precisio
     return cudaGetLastError();
 }
 
+// Positions in Mpc/h in [0, L): uint32 ticks times L / 2^32 (exact in double, then rounded
+// down to float, so that no position rounds up to L), or box fractions times L.
+__global__ void k_pos_ticks(const uint32_t* __restrict__ x, float* __restrict__ out, int64_t n, double tick_mpc) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = __double2float_rd((double)x[i] * tick_mpc);
+}
+__global__ void k_pos_frac(const double* __restrict__ x, double* __restrict__ out, int64_t n, double box) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = x[i] * box;
+}
+cudaError_t positions_mpc(const void* x, void* out, int64_t count, int precision, double box, cudaStream_t st) {
+    const int64_t n = 3 * count;
+    if (n == 0) return cudaSuccess;
+    if (precision == PM_FP32_FIXED)
+        k_pos_ticks<<<grid_for(n, 256), 256, 0, st>>>((const uint32_t*)x, (float*)out, n, box / 4294967296.0);
+    else
+        k_pos_frac<<<grid_for(n, 256), 256, 0, st>>>((const double*)x, (double*)out, n, box);
+    return cudaGetLastError();
+}
+
 // ---------------------------------------------------------------- position check
 // Counts FP64 box-fraction positions that are not finite or lie outside [0, 1) (one
 // warp-aggregated atomic a warp).

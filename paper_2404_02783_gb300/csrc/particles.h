@@ -43,6 +43,8 @@ cudaError_t combine(void* xt, const void* xg, const void* xn, void* xi_out, int 
 cudaError_t fill(void* a, int64_t count, int precision, double v, cudaStream_t st);
 // d = x - q (minimum image, Mpc/h; float for ticks, double for fractions) of the np^3 lattice particles.
 cudaError_t lagrangian_displacement(const void* x, void* d, int np, int precision, double box, cudaStream_t st);
+// Positions in Mpc/h, [3][count]: float from uint32 ticks (FP32) or double from fractions (FP64).
+cudaError_t positions_mpc(const void* x, void* out, int64_t count, int precision, double box, cudaStream_t st);
 // *bad = the number of FP64 positions that are not finite or outside [0, 1).
 cudaError_t count_outside_box(const double* x, int64_t count, unsigned long long* bad, cudaStream_t st);
 size_t cell_sort_scratch_bytes(int64_t count, int n);

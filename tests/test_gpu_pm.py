@@ -327,3 +327,26 @@ def test_fp64_positions_outside_the_box_are_refused(bad):
     x[1, 77] = 0.25
     pm.pm_set_particles(run.ctx, x, p)
     assert run.state()[0] == 0
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_positions_in_mpc(precision):
+    # pm_positions: ticks times L / 2^32 rounded down to float (FP32), fractions times L (FP64),
+    # bit for bit; all in [0, L)
+    pm = lib()
+    prec = pm.PM_FP32_FIXED if precision == "fp32" else pm.PM_FP64
+    box = 700.0
+    run = pm.PMRun(pm.make_config(16, 32, box, 0.1, 1.0, 6, precision=prec))
+    run.ic(seed=5)
+    run.step(4)
+    pos = to_host(run.positions())
+    x = to_host(run.particles()[0])
+    if precision == "fp32":
+        exact = x.view(np.uint32).astype(np.float64) * (box / 2.0**32)
+        want = exact.astype(np.float32)
+        up = want.astype(np.float64) > exact  # rounded up to nearest: one float below
+        want[up] = np.nextafter(want[up], np.float32(-np.inf))
+    else:
+        want = x * box
+    assert pos.dtype == want.dtype and np.array_equal(pos, want)
+    assert pos.min() >= 0.0 and pos.max() < box
