@@ -36,6 +36,7 @@ from . import cic, gravity, ic, philox
 from .cosmology import C_LIGHT
 
 NEWTON, GR_POISSON = 0, 1  # the force of the run, as in oracle.pm
+SPECTRAL, FD1 = 0, 1       # the gradient of the potential, as in oracle.pm
 
 
 def _grad_gather(field, u, n):
@@ -80,12 +81,6 @@ def _k_components(n, box):
     return [kf * np.where(np.abs(Nj) == n // 2, 0.0, Nj) for Nj in (NX, NY, NZ)]
 
 
-def _force_meshes(u, n, box, omega_m):
-    delta = cic.density_contrast(u, n)
-    phik = gravity.newton_potential_k(np.fft.rfftn(delta), n, box, omega_m)
-    return gravity.gradient_force(phik, n, box)
-
-
 def _rho_bar(V, n, box, omega_m):
     """sum_j T_j^T V_j with T_j rho = IFFT[-i k_j C(k) FFT(rho)], C = -(3/2) Om / k^2: T_j^T = -T_j."""
     k = _k_components(n, box)
@@ -98,15 +93,61 @@ def _rho_bar(V, n, box, omega_m):
     return np.fft.irfftn(acc, s=(n, n, n), axes=(0, 1, 2))
 
 
-def _gr_force_meshes(u, n, box, cosmo, a, hist):
-    """Poisson-gauge force meshes at u and scale factor a; hist = [Phi_old_k, a_old] of the
-    previous force evaluation ([None, None] before the first), updated in place.  Returns
-    (G, (a, dtau)) with dtau = None at the first evaluation."""
+def _potential_k(u, n, box, cosmo, a, mode, hist):
+    """Code potential spectrum phi_k at positions u and scale factor a.  Poisson gauge: hist =
+    [Phi_old_k, a_old] of the previous force evaluation ([None, None] before the first),
+    updated in place, and (a, dtau) is returned beside phi_k (dtau None at the first)."""
     dk = np.fft.rfftn(cic.density_contrast(u, n))
+    if mode == NEWTON:
+        return gravity.newton_potential_k(dk, n, box, cosmo.omega_m), None
     dtau = None if hist[0] is None else cosmo.delta_tau(hist[1], a)
     Phi = gravity.gr_potential_k(dk, n, box, cosmo, a, phi_old_k=hist[0], dtau=dtau)
     hist[0], hist[1] = Phi, a
-    return gravity.gradient_force(gravity.gr_code_potential_k(Phi, a), n, box), (a, dtau)
+    return gravity.gr_code_potential_k(Phi, a), (a, dtau)
+
+
+def _grad_weight_deposit(u, v, n, box):
+    """V(c) = sum_p sum_j v_j,p dW(u_p, c)/dx_j (x in Mpc/h): the transpose of the first-order
+    gradient gather of ``cic.interpolate_gradient``."""
+    base, frac = cic.mesh_coords(u, n)
+    inv_d = n / box
+    V = np.zeros(n**3)
+    for dx in (0, 1):
+        for dy in (0, 1):
+            for dz in (0, 1):
+                d = (dx, dy, dz)
+                idx = (((base[0] + dx) % n) * n + (base[1] + dy) % n) * n + (base[2] + dz) % n
+                w = [frac[j] if d[j] else 1.0 - frac[j] for j in range(3)]
+                sg = [inv_d if d[j] else -inv_d for j in range(3)]
+                wt = v[0] * sg[0] * w[1] * w[2] + v[1] * w[0] * sg[1] * w[2] + v[2] * w[0] * w[1] * sg[2]
+                V += np.bincount(idx, weights=wt, minlength=n**3)
+    return V.reshape(n, n, n)
+
+
+def _grad_hessian_gather(phi, u, n, box, v):
+    """out_i = sum_j v_j d/du_i [sum_c dW(u, c)/dx_j phi(c)] (u in box units): the position
+    derivative of the first-order gradient gather, contracted with v.  The trilinear weight is
+    linear along each axis, so only the mixed (i != j) derivatives survive."""
+    base, frac = cic.mesh_coords(u, n)
+    inv_d = n / box
+    flat = phi.ravel()
+    out = np.zeros((3, base.shape[1]))
+    for dx in (0, 1):
+        for dy in (0, 1):
+            for dz in (0, 1):
+                d = (dx, dy, dz)
+                idx = (((base[0] + dx) % n) * n + (base[1] + dy) % n) * n + (base[2] + dz) % n
+                f = flat[idx]
+                w = [frac[j] if d[j] else 1.0 - frac[j] for j in range(3)]
+                sg = [inv_d if d[j] else -inv_d for j in range(3)]  # d w_j / dx_j
+                du = [n * (1.0 if d[j] else -1.0) for j in range(3)]  # d w_j / du_j
+                for i in range(3):
+                    for j in range(3):
+                        if i == j:
+                            continue
+                        k = 3 - i - j
+                        out[i] += v[j] * sg[j] * du[i] * w[k] * f
+    return out
 
 
 def _gr_coefficients(cosmo, n, box, a, dtau):
@@ -138,10 +179,11 @@ def _za_operator(w_or_s, n_p, box, cosmo, j):
     return np.fft.irfftn(1j * kf * Nj * dk * inv_k2, s=(n_p,) * 3, axes=(0, 1, 2))
 
 
-def forward(cosmo, n_p, n_mesh, box, a_i, a_f, n_steps, w, mode=NEWTON):
-    """ZA ICs from w and the KDK run (Newtonian or Poisson-gauge force); returns
-    (u_final, p_final, ops, mass).  A Poisson-gauge kick op also keeps its force meshes and
-    (a, dtau)."""
+def forward(cosmo, n_p, n_mesh, box, a_i, a_f, n_steps, w, mode=NEWTON, gradient=SPECTRAL):
+    """ZA ICs from w and the KDK run (Newtonian or Poisson-gauge force, spectral or first-order
+    gradient); returns (u_final, p_final, ops, mass).  A kick op ("kick", K, u, info) keeps in
+    info the force meshes "G" (spectral) or the potential mesh "phi" (first order), and for the
+    Poisson gauge "gr" = (a, dtau)."""
     psi = ic.za_displacement(ic.linear_delta_k(cosmo, n_p, box, white_noise=w), n_p, box).reshape(3, -1)
     D, f, E = cosmo.growth_D(a_i), cosmo.growth_f(a_i), float(cosmo.E(a_i))
     i = np.arange(n_p, dtype=np.float64) / n_p
@@ -157,13 +199,17 @@ def forward(cosmo, n_p, n_mesh, box, a_i, a_f, n_steps, w, mode=NEWTON):
 
     def kick(uu, a, K):
         """The kick op at positions uu and scale factor a, and the acceleration there."""
-        if mode == NEWTON:
-            G = _force_meshes(uu, n_mesh, box, cosmo.omega_m)
-            op = ("kick", K, uu.copy())
+        phi_k, meta = _potential_k(uu, n_mesh, box, cosmo, a, mode, hist)
+        info = {"gr": meta}
+        if gradient == SPECTRAL:
+            G = gravity.gradient_force(phi_k, n_mesh, box)
+            info["G"] = G
+            g = np.stack([cic.interpolate(G[j], uu) for j in range(3)])
         else:
-            G, meta = _gr_force_meshes(uu, n_mesh, box, cosmo, a, hist)
-            op = ("kick", K, uu.copy(), G, meta)
-        return op, np.stack([cic.interpolate(G[j], uu) for j in range(3)])
+            phi = gravity.potential_mesh(phi_k, n_mesh)
+            info["phi"] = phi
+            g = -cic.interpolate_gradient(phi, uu, box)
+        return ("kick", K, uu.copy(), info), g
 
     synced = True
     for s in range(n_steps):
@@ -187,8 +233,8 @@ def forward(cosmo, n_p, n_mesh, box, a_i, a_f, n_steps, w, mode=NEWTON):
     return u, p, ops, mass
 
 
-def loss(cosmo, n_p, n_mesh, box, a_i, a_f, n_steps, w, delta_t, mode=NEWTON):
-    u, _, _, _ = forward(cosmo, n_p, n_mesh, box, a_i, a_f, n_steps, w, mode)
+def loss(cosmo, n_p, n_mesh, box, a_i, a_f, n_steps, w, delta_t, mode=NEWTON, gradient=SPECTRAL):
+    u, _, _, _ = forward(cosmo, n_p, n_mesh, box, a_i, a_f, n_steps, w, mode, gradient)
     return float(np.mean((cic.density_contrast(u, n_mesh) - delta_t)**2))
 
 
@@ -205,14 +251,15 @@ def displacement(u, n_p, box):
     return (d - np.rint(d)) * box
 
 
-def vjp(cosmo, n_p, n_mesh, box, a_i, a_f, n_steps, w, lam_delta=None, lam_disp=None, lam_mom=None, mode=NEWTON):
+def vjp(cosmo, n_p, n_mesh, box, a_i, a_f, n_steps, w, lam_delta=None, lam_disp=None, lam_mom=None, mode=NEWTON,
+        gradient=SPECTRAL):
     """dL/dw for any loss L(delta_final, d_final, p_final) given its cotangents lam_delta =
     dL/d delta (n_mesh^3 mesh), lam_disp = dL/d d ((3, n_p^3), per Mpc/h) and lam_mom =
     dL/dp ((3, n_p^3), per Mpc/h of momentum, p after the closing half kick), by the reverse
     sweep of the recorded forward run.  Since d = (u - q) L (minimum image), dL/du = L
     lam_disp; the density adds m sum_c lam_delta(c) dW(u, c)/du; lam_mom is the adjoint
     momentum the sweep starts from (the closing kick is the first operation it reverses)."""
-    u, p, ops, mass = forward(cosmo, n_p, n_mesh, box, a_i, a_f, n_steps, w, mode)
+    u, p, ops, mass = forward(cosmo, n_p, n_mesh, box, a_i, a_f, n_steps, w, mode, gradient)
     lam_u = np.zeros_like(u)
     if lam_delta is not None:
         lam_u += mass * _grad_gather(np.asarray(lam_delta, dtype=np.float64), u, n_mesh)
@@ -231,21 +278,33 @@ def _reverse(cosmo, n_p, n_mesh, box, a_i, ops, mass, lam_u, lam_p0=None):
     for op in reversed(ops):
         if op[0] == "drift":
             lam_p += op[1] / box * lam_u
-        else:
-            K, uk = op[1], op[2]
+            continue
+        K, uk, info = op[1], op[2], op[3]
+        gr = info["gr"]
+        if "G" in info:  # spectral gradient: g_j = interp(T_j phi)
+            G = info["G"]
             V = np.stack([_weighted_deposit(uk, lam_p[j], n_mesh) for j in range(3)])
-            if len(op) == 3:  # Newtonian: dL/d delta of this evaluation is K rho_bar
-                G = _force_meshes(uk, n_mesh, box, cosmo.omega_m)
-                rho_bar = K * _rho_bar(V, n_mesh, box, cosmo.omega_m)
-            else:  # Poisson gauge: Z carries dL/dPhi back through the lag (each term with its own K)
-                G, (a, dtau) = op[3], op[4]
-                W = sum(1j * k[j] * np.fft.rfftn(V[j]) for j in range(3))
-                src, carry = _gr_coefficients(cosmo, n_mesh, box, a, dtau)
-                Z = K * a * C_LIGHT**2 * W + (0.0 if Z is None else carry_next * Z)
-                rho_bar = np.fft.irfftn(src * Z, s=(n_mesh,) * 3, axes=(0, 1, 2))
-                carry_next = carry
             direct = sum(lam_p[j] * _grad_gather(G[j], uk, n_mesh) for j in range(3))
-            lam_u = lam_u + K * direct + mass * _grad_gather(rho_bar, uk, n_mesh)
+            if gr is None:  # Newtonian: dL/d delta of this evaluation is K rho_bar
+                rho_bar = K * _rho_bar(V, n_mesh, box, cosmo.omega_m)
+            else:
+                W = sum(1j * k[j] * np.fft.rfftn(V[j]) for j in range(3))
+        else:  # first-order gradient: g = -grad interp(phi), phi a real mesh
+            phi = info["phi"]
+            Vs = -_grad_weight_deposit(uk, lam_p, n_mesh, box)  # dL/dphi over K
+            direct = -_grad_hessian_gather(phi, uk, n_mesh, box, lam_p)
+            if gr is None:  # phi = IFFT[C FFT(delta)] with a real, even C: its own transpose
+                rho_bar = K * gravity.potential_mesh(
+                    gravity.newton_potential_k(np.fft.rfftn(Vs), n_mesh, box, cosmo.omega_m), n_mesh)
+            else:
+                W = np.fft.rfftn(Vs)
+        if gr is not None:  # Poisson gauge: Z carries dL/dPhi back through the lag (each term with its own K)
+            a, dtau = gr
+            src, carry = _gr_coefficients(cosmo, n_mesh, box, a, dtau)
+            Z = K * a * C_LIGHT**2 * W + (0.0 if Z is None else carry_next * Z)
+            rho_bar = np.fft.irfftn(src * Z, s=(n_mesh,) * 3, axes=(0, 1, 2))
+            carry_next = carry
+        lam_u = lam_u + K * direct + mass * _grad_gather(rho_bar, uk, n_mesh)
     D, f, E = cosmo.growth_D(a_i), cosmo.growth_f(a_i), float(cosmo.E(a_i))
     s = (D / box) * lam_u + a_i**2 * E * f * D * lam_p
     # lambda_w = sum_j A_j^T s_j and A_j^T = -A_j (odd, real Fourier multiplier)
@@ -255,9 +314,9 @@ def _reverse(cosmo, n_p, n_mesh, box, a_i, ops, mass, lam_u, lam_p0=None):
     return grad
 
 
-def loss_and_grad(cosmo, n_p, n_mesh, box, a_i, a_f, n_steps, w, delta_t, mode=NEWTON):
+def loss_and_grad(cosmo, n_p, n_mesh, box, a_i, a_f, n_steps, w, delta_t, mode=NEWTON, gradient=SPECTRAL):
     """(L, dL/dw) with dL/dw of shape (n_p, n_p, n_p)."""
-    u, p, ops, mass = forward(cosmo, n_p, n_mesh, box, a_i, a_f, n_steps, w, mode)
+    u, p, ops, mass = forward(cosmo, n_p, n_mesh, box, a_i, a_f, n_steps, w, mode, gradient)
     delta = cic.density_contrast(u, n_mesh)
     L = float(np.mean((delta - delta_t)**2))
     lam_rho = 2.0 * (delta - delta_t) / n_mesh**3

@@ -106,17 +106,20 @@ def _ics_of(c, n_p, box, a_i, w):
     return u - np.floor(u), a_i**2 * E * f * D * psi
 
 
+@pytest.mark.parametrize("gradient", [adjoint.SPECTRAL, adjoint.FD1])
 @pytest.mark.parametrize("mode", [adjoint.NEWTON, adjoint.GR_POISSON])
-def test_forward_map_is_the_oracle_run(mode):
+def test_forward_map_is_the_oracle_run(mode, gradient):
     # the adjoint's own forward map (kept as a list of kicks and drifts) against oracle.pm's run
-    # from the same ICs, Newtonian and Poisson gauge (20 Gpc/h, where the lag term matters)
+    # from the same ICs, Newtonian and Poisson gauge (20 Gpc/h, where the lag term matters),
+    # spectral and first-order gradient
     from oracle import pm as opm
     c = Cosmology()
     n_p, n_mesh, box, ai, af, steps = 8, 16, 20000.0, 0.1, 0.5, 4
     w = inputs.gaussian_field(9, n_p)
-    u, p, _, _ = adjoint.forward(c, n_p, n_mesh, box, ai, af, steps, w, mode)
+    u, p, _, _ = adjoint.forward(c, n_p, n_mesh, box, ai, af, steps, w, mode, gradient)
     u0, p0 = _ics_of(c, n_p, box, ai, w)
-    run = opm.PMRun(c, n_mesh, box, ai, af, steps, u0, p0, mode=opm.GR_POISSON if mode else opm.NEWTON)
+    run = opm.PMRun(c, n_mesh, box, ai, af, steps, u0, p0, mode=opm.GR_POISSON if mode else opm.NEWTON,
+                    gradient=opm.FD1 if gradient else opm.SPECTRAL)
     run.step(steps)
     d = run.x - u
     assert np.max(np.abs(d - np.rint(d))) < 1e-13
@@ -159,3 +162,44 @@ def test_poisson_gauge_vector_jacobian_product():
     gn = adjoint.vjp(c, n_p, n_mesh, box, ai, af, steps, w, lam_delta=cotangents(adjoint.NEWTON), lam_disp=gdisp,
                      lam_mom=h, mode=adjoint.NEWTON)
     assert np.linalg.norm(g - gn) > 0.05 * np.linalg.norm(g)
+
+
+@pytest.mark.parametrize("mode,box", [(adjoint.NEWTON, 300.0), (adjoint.GR_POISSON, 20000.0)])
+def test_first_order_gradient_vector_jacobian_product(mode, box):
+    # the first-order gradient g = -grad interp(phi): the transposed chain is a scalar deposit with
+    # the CIC derivative weights, the transposed potential map, and the interpolant's mixed second
+    # derivatives for the direct term; a loss of the final density, displacements and momenta
+    # against central differences of the forward map, and far from the spectral-gradient result
+    c = Cosmology()
+    n_p, n_mesh, ai, af, steps = 8, 16, 0.1 if mode else 0.2, 0.5 if mode else 0.6, 4
+    w = inputs.gaussian_field(12, n_p)
+    r = np.random.default_rng(13)
+    f = np.fft.fftfreq(n_mesh, 1.0 / n_mesh)
+    Wk = 1.0 / (1.0 + f[:, None, None]**2 + f[None, :, None]**2 + f[None, None, :]**2)
+    gdisp = r.standard_normal((3, n_p**3)) * 1e-3
+    h = r.standard_normal((3, n_p**3)) * 1e-2
+    fd1 = adjoint.FD1
+
+    def L_of(ww):
+        u, p, _, _ = adjoint.forward(c, n_p, n_mesh, box, ai, af, steps, ww, mode, fd1)
+        dk = np.fft.fftn(cic.density_contrast(u, n_mesh))
+        return float(np.sum(Wk * np.abs(dk)**2) / n_mesh**6 + np.sum(gdisp * adjoint.displacement(u, n_p, box))
+                     + np.sum(h * p))
+
+    def lam_delta(grad):
+        u, _, _, _ = adjoint.forward(c, n_p, n_mesh, box, ai, af, steps, w, mode, grad)
+        dk = np.fft.fftn(cic.density_contrast(u, n_mesh))
+        return 2.0 * np.real(np.fft.ifftn(Wk * dk)) / n_mesh**3
+
+    g = adjoint.vjp(c, n_p, n_mesh, box, ai, af, steps, w, lam_delta=lam_delta(fd1), lam_disp=gdisp, lam_mom=h,
+                    mode=mode, gradient=fd1)
+    # 20 Gpc/h: displacements far below a cell (1250 Mpc/h), so a larger eps crosses no CIC
+    # boundary and keeps the differences above the rounding of the positions
+    eps = 1e-4 if box > 10000.0 else 1e-5
+    for _ in range(3):
+        v = r.standard_normal((n_p,) * 3)
+        fd = (L_of(w + eps * v) - L_of(w - eps * v)) / (2 * eps)
+        assert np.sum(g * v) == pytest.approx(fd, rel=1e-6)
+    gs = adjoint.vjp(c, n_p, n_mesh, box, ai, af, steps, w, lam_delta=lam_delta(adjoint.SPECTRAL), lam_disp=gdisp,
+                     lam_mom=h, mode=mode, gradient=adjoint.SPECTRAL)
+    assert np.linalg.norm(g - gs) > 0.01 * np.linalg.norm(g)
