@@ -103,7 +103,7 @@ typedef struct {
     int precision;     /* PM_FP32_FIXED or PM_FP64 */
     int n_lo;          /* GR only: modes with |n|^2 <= n_lo^2 are solved and stored in FP64 */
     int gradient;      /* PM_GRAD_SPECTRAL (0) or PM_GRAD_FD1; pm_batch_* refuse FD1
-                          (PM_ERR_INVALID_ARG), the gradient calls too (PM_ERR_UNSUPPORTED) */
+                          (PM_ERR_INVALID_ARG) */
 } pm_config;
 
 typedef struct pm_ctx pm_ctx;   /* opaque host object owned by the library */
@@ -337,8 +337,10 @@ pm_status pm_triangle_index(int nbins, int i, int j, int l, int64_t* index);
  * Newtonian and Poisson-gauge contexts (Sec. 2): in the Poisson gauge each force evaluation's
  * Phi depends on the previous one through the lagged constraint, so the checkpoints also keep
  * Phi_old (and the FP64 island), and the transposed force chain carries one spectrum back
- * through the evaluations (the scratch holds both).  FP32 positions with the spectral gradient
- * only (PM_ERR_UNSUPPORTED otherwise). */
+ * through the evaluations (the scratch holds both).  With the first-order gradient
+ * (PM_GRAD_FD1) the transposed chain is a scalar deposit with the CIC derivative weights, the
+ * transposed potential map and the interpolant's mixed second derivatives.  FP32 positions only
+ * (PM_ERR_UNSUPPORTED for PM_FP64). */
 pm_status pm_adjoint_scratch_size(const pm_ctx* ctx, int checkpoint_every, size_t* bytes);
 pm_status pm_adjoint_record(pm_ctx* ctx, const void* white_noise, int checkpoint_every, void* scratch,
                             size_t scratch_bytes);

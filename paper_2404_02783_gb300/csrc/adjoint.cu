@@ -144,6 +144,76 @@ __global__ void __launch_bounds__(256) k_adj_kick(const uint32_t* __restrict__ x
     }
 }
 
+// First-order gradient (g = -grad of the CIC interpolant of phi, the update's fd1_force):
+// V(c) += -sum_p sum_j v_j dW(u_p, c)/dx_j with dW/dx_j = inv_d (-1, +1) along j times the other
+// two weights (x in Mpc/h, inv_d = n / L): the transposed gradient gather, one scalar mesh.
+__global__ void k_deposit_grad(const uint32_t* __restrict__ x, int64_t count, int logn, float inv_cell_ticks,
+                               const float* __restrict__ v, float inv_d, float* __restrict__ V) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x) {
+        const Cic1 cx = decode(x[i], logn, inv_cell_ticks), cy = decode(x[count + i], logn, inv_cell_ticks),
+                   cz = decode(x[2 * count + i], logn, inv_cell_ticks);
+        const float v0 = -inv_d * v[i], v1 = -inv_d * v[count + i], v2 = -inv_d * v[2 * count + i];
+        const uint32_t ix[2] = {(uint32_t)cx.i0, (uint32_t)cx.i1}, iy[2] = {(uint32_t)cy.i0, (uint32_t)cy.i1},
+                       iz[2] = {(uint32_t)cz.i0, (uint32_t)cz.i1};
+        const float wx[2] = {1.0f - cx.w1, cx.w1}, wy[2] = {1.0f - cy.w1, cy.w1}, wz[2] = {1.0f - cz.w1, cz.w1};
+        const float sg[2] = {-1.0f, 1.0f};
+#pragma unroll
+        for (int a = 0; a < 2; ++a)
+#pragma unroll
+            for (int b = 0; b < 2; ++b)
+#pragma unroll
+                for (int c = 0; c < 2; ++c) {
+                    const float w = v0 * sg[a] * wy[b] * wz[c] + v1 * wx[a] * sg[b] * wz[c] + v2 * wx[a] * wy[b] * sg[c];
+                    atomicAdd(V + (((ix[a] << logn) + iy[b]) << logn) + iz[c], w);
+                }
+    }
+}
+
+// The particle side of the first-order gradient's transposed kick:
+//   lam_u_i += K sum_j v_j d/du_i g_j(u) + Km grad_u interp(rho_bar),
+// g_j = -sum_c dW/dx_j phi(c), whose u_i derivative keeps only the mixed (i != j) terms of the
+// trilinear weight; then the transposed drift v += drift_next lam_u as in k_adj_kick.
+__global__ void __launch_bounds__(256) k_adj_kick_fd(const uint32_t* __restrict__ x, int64_t count, int logn,
+                                                     float inv_cell_ticks, float* __restrict__ v,
+                                                     const float* __restrict__ phi, const float* __restrict__ rho_bar,
+                                                     float K, float Km, float inv_d, float drift_next,
+                                                     float* __restrict__ lam_u) {
+    const float nf = (float)(1 << logn);
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x) {
+        const float v0 = v[i], v1 = v[count + i], v2 = v[2 * count + i];
+        const Cic1 cx = decode(x[i], logn, inv_cell_ticks), cy = decode(x[count + i], logn, inv_cell_ticks),
+                   cz = decode(x[2 * count + i], logn, inv_cell_ticks);
+        const uint32_t ix[2] = {(uint32_t)cx.i0, (uint32_t)cx.i1}, iy[2] = {(uint32_t)cy.i0, (uint32_t)cy.i1},
+                       iz[2] = {(uint32_t)cz.i0, (uint32_t)cz.i1};
+        const float wx[2] = {1.0f - cx.w1, cx.w1}, wy[2] = {1.0f - cy.w1, cy.w1}, wz[2] = {1.0f - cz.w1, cz.w1};
+        const float sg[2] = {-1.0f, 1.0f};
+        const float Kd = -K * inv_d * nf;  // -K (d w/dx) (d w/du) per pair of signs
+        float g0 = 0.f, g1 = 0.f, g2 = 0.f;
+#pragma unroll
+        for (int a = 0; a < 2; ++a)
+#pragma unroll
+            for (int b = 0; b < 2; ++b)
+#pragma unroll
+                for (int c = 0; c < 2; ++c) {
+                    const uint32_t o = (((ix[a] << logn) + iy[b]) << logn) + iz[c];
+                    const float f = __ldg(phi + o), r = Km * nf * __ldg(rho_bar + o);
+                    const float sx = sg[a], sy = sg[b], sz = sg[c];
+                    g0 += sx * (Kd * (v1 * sy * wz[c] + v2 * sz * wy[b]) * f + r * wy[b] * wz[c]);
+                    g1 += sy * (Kd * (v0 * sx * wz[c] + v2 * sz * wx[a]) * f + r * wx[a] * wz[c]);
+                    g2 += sz * (Kd * (v0 * sx * wy[b] + v1 * sy * wx[a]) * f + r * wx[a] * wy[b]);
+                }
+        const float l0 = lam_u[i] + g0, l1 = lam_u[count + i] + g1, l2 = lam_u[2 * count + i] + g2;
+        lam_u[i] = l0;
+        lam_u[count + i] = l1;
+        lam_u[2 * count + i] = l2;
+        if (drift_next != 0.f) {
+            v[i] = fmaf(drift_next, l0, v0);
+            v[count + i] = fmaf(drift_next, l1, v1);
+            v[2 * count + i] = fmaf(drift_next, l2, v2);
+        }
+    }
+}
+
 // V_j(c) += sum_p v_j W(u_p, c) for the three components, particles in lattice order
 // (id = (ix np + iy) np + iz) walked along x in runs of RUN (thread = (iz, iy, run); the
 // next particle is loaded one iteration ahead).  With MERGE (lattice as fine as the mesh)
@@ -307,6 +377,23 @@ cudaError_t adj_kick_particles(const uint32_t* x, int64_t count, int n, float* v
     const int logn = ilog2(n);
     k_adj_kick<<<blocks_for(count), 256, 0, st>>>(x, count, logn, (float)ldexp(1.0, -(32 - logn)), v, G[0], G[1], G[2],
                                                   rho_bar, K, Km, drift_next, lam_u);
+    return cudaGetLastError();
+}
+
+cudaError_t deposit_grad(const uint32_t* x, int64_t count, int n, const float* v, double inv_d, float* V,
+                         cudaStream_t st) {
+    const int logn = ilog2(n);
+    k_deposit_grad<<<blocks_for(count), 256, 0, st>>>(x, count, logn, (float)ldexp(1.0, -(32 - logn)), v, (float)inv_d,
+                                                      V);
+    return cudaGetLastError();
+}
+
+cudaError_t adj_kick_particles_fd(const uint32_t* x, int64_t count, int n, float* v, const float* phi,
+                                  const float* rho_bar, float K, float Km, double inv_d, float drift_next, float* lam_u,
+                                  cudaStream_t st) {
+    const int logn = ilog2(n);
+    k_adj_kick_fd<<<blocks_for(count), 256, 0, st>>>(x, count, logn, (float)ldexp(1.0, -(32 - logn)), v, phi, rho_bar,
+                                                     K, Km, (float)inv_d, drift_next, lam_u);
     return cudaGetLastError();
 }
 

@@ -1275,6 +1275,25 @@ pm_status adj_kick(pm_ctx* c, const uint32_t* xs, const float* gs, double K, flo
     const float* G[3] = {gs, gs + n3, gs + 2 * n3};
     // V_j and the spectra are three meshes back to back (256-byte multiples): one batched transform
     float* V[3] = {(float*)c->at(c->L.force[0]), (float*)c->at(c->L.force[1]), (float*)c->at(c->L.force[2])};
+    const double mass = std::pow((double)n / c->np, 3);
+    if (c->cfg.gradient == PM_GRAD_FD1) {
+        // first-order gradient: gs[0] is the recorded potential; one scalar deposit with the CIC
+        // derivative weights, its transposed potential map, then the particle side
+        const double inv_d = n / c->cfg.box;
+        float2* s0 = (float2*)c->at(c->L.spec[0]);
+        PM_CK(deposit_grad(xs, c->np3, n, lam_p, inv_d, V[0], c->st));
+        PM_CK(forward_zy<float>(V[0], s0, n, 1, c->st));
+        PM_CK(x_adj<float>(s0, s0, n, c->kf, -1.5 * c->cfg.omega_m / ((double)n * n * n), c->st, V[0], (int64_t)n3, gr,
+                           true));
+        float* rho_bar = (float*)c->at(c->L.rho);
+        PM_CK((y_rows<float, true>(s0, (int64_t)(n / 2 + 1) * n, n, c->st)));
+        const float2* zin[1] = {s0};
+        float* zout[1] = {rho_bar};
+        PM_CK(z_c2r<float>(zin, zout, 1, n, 1, 0u, 0.0, c->st));
+        PM_CK(adj_kick_particles_fd(xs, c->np3, n, lam_p, gs, rho_bar, (float)K, (float)(gr ? mass : K * mass), inv_d,
+                                    (float)drift_next, lam_u, c->st));
+        return PM_OK;
+    }
     PM_CK(deposit_vec(xs, c->np, n, lam_p, V, c->st));
     float2* sp[3] = {(float2*)c->at(c->L.spec[0]), (float2*)c->at(c->L.spec[1]), (float2*)c->at(c->L.spec[2])};
     // forward z and y passes of the three meshes, then the x pass that combines them
@@ -1290,7 +1309,6 @@ pm_status adj_kick(pm_ctx* c, const uint32_t* xs, const float* gs, double K, flo
     float* zout[1] = {rho_bar};
     PM_CK(z_c2r<float>(zin, zout, 1, n, 1, 0u, 0.0, c->st));
     // Newtonian: rho_bar lacks this evaluation's K; Poisson gauge: Z carries every K already
-    const double mass = std::pow((double)n / c->np, 3);
     PM_CK(adj_kick_particles(xs, c->np3, n, lam_p, G, rho_bar, (float)K, (float)(gr ? mass : K * mass),
                              (float)drift_next, lam_u, c->st));
     return PM_OK;
@@ -1523,8 +1541,8 @@ struct AdjSweep {
 // the session's events for checkpoint interval C.
 pm_status adj_prepare(pm_ctx* c, int checkpoint_every, void* scratch, size_t scratch_bytes) {
     if (checkpoint_every < 1) return fail(PM_ERR_INVALID_ARG, "bad checkpoint interval");
-    if (c->cfg.precision != PM_FP32_FIXED || c->cfg.gradient != PM_GRAD_SPECTRAL)
-        return fail(PM_ERR_UNSUPPORTED, "the gradient is implemented for the FP32 step with the spectral force");
+    if (c->cfg.precision != PM_FP32_FIXED)
+        return fail(PM_ERR_UNSUPPORTED, "the gradient is implemented for the FP32 step");
     const int C = std::min(checkpoint_every, c->cfg.n_steps);
     const AdjLayout A = adj_plan(c, C);
     if (!scratch || scratch_bytes < A.total || (uintptr_t)scratch % 256)

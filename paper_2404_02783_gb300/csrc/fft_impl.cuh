@@ -877,8 +877,9 @@ __global__ void __launch_bounds__(PlaneShape<T, LOGN>::THREADS, PlaneShape<T, LO
 // along x one after the other and accumulated as out = sum_j i k_j c(k) V_j,
 // c = coef / (kf^2 |n|^2) (zero mode 0, k_j = 0 at its Nyquist index), then transformed
 // back along x into out ([kz][x][ky], ready for the inverse y and z passes).  GR: the
-// Poisson-gauge operator of AdjGrOp instead of c(k), with the carried spectrum gr.Z.
-template <typename T, int LOGN, bool GR>
+// Poisson-gauge operator of AdjGrOp instead of c(k), with the carried spectrum gr.Z.  FD (the
+// first-order gradient): V is one scalar field and W = FFT_x V, without the i k_j factors.
+template <typename T, int LOGN, bool GR, bool FD>
 __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) k_x_adj(const cplx<T>* V,
                                                                       cplx<T>* out, double kf,
                                                                       double coef, float4* __restrict__ zero,
@@ -912,7 +913,7 @@ __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) k_x_adj(const cpl
     for (int m = 0; m < 8; ++m) acc[m] = cmake<C>(T(0), T(0));
     ColEx<C, N> ex{buf, CS, b};
 #pragma unroll 1
-    for (int j = 0; j < 3; ++j) {
+    for (int j = 0; j < (FD ? 1 : 3); ++j) {
         C v[1][8];
         const C* col = V + j * field + pbase + c;
 #pragma unroll
@@ -923,7 +924,7 @@ __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) k_x_adj(const cpl
         for (int m = 0; m < 8; ++m) {
             const int i = t + m * Q;
             const int nx = (i < M) ? i : i - N;
-            const T kj = (j == 0) ? ((2 * nx == -N) ? T(0) : kfT * T(nx)) : (j == 1 ? kyT : kzT);
+            const T kj = FD ? T(1) : (j == 0) ? ((2 * nx == -N) ? T(0) : kfT * T(nx)) : (j == 1 ? kyT : kzT);
             acc[m].x += kj * v[0][m].x;
             acc[m].y += kj * v[0][m].y;
         }
@@ -946,7 +947,9 @@ __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) k_x_adj(const cpl
             const T carry = (n2 == 0) ? T(0) : div_mode(cc1, k2 + base1);
             const size_t zi = pbase + (size_t)i * N + c;
             const C zo = Zc[zi];
-            const C Z = cmake<C>(-KA * acc[m].y + carry * zo.x, KA * acc[m].x + carry * zo.y);  // K a c^2 W + carry Z
+            // K a c^2 W + carry Z, W = i acc (spectral gradient) or acc (first order)
+            const C Z = FD ? cmake<C>(KA * acc[m].x + carry * zo.x, KA * acc[m].y + carry * zo.y)
+                           : cmake<C>(-KA * acc[m].y + carry * zo.x, KA * acc[m].x + carry * zo.y);
             Zc[zi] = Z;
             w[0][m] = cscale(Z, src);
         }
@@ -957,7 +960,7 @@ __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) k_x_adj(const cpl
             const int nx = (i < M) ? i : i - N;
             const int n2 = nx * nx + ny * ny + kz * kz;
             const T cc = (n2 == 0) ? T(0) : coefT / T(n2);
-            w[0][m] = cmake<C>(-cc * acc[m].y, cc * acc[m].x);  // i c sum_j k_j V_j
+            w[0][m] = FD ? cscale(acc[m], cc) : cmake<C>(-cc * acc[m].y, cc * acc[m].x);  // (i) c sum_j k_j V_j
         }
     }
     fft_regs<N, 1, true>(w, t, tw, ex);
@@ -1110,24 +1113,28 @@ cudaError_t plane_n(cplx<T>* A, cplx<T>* GX, cplx<T>* GY, int nplanes, const Spe
     return cudaGetLastError();
 }
 
-template <typename T, int LOGN>
-cudaError_t x_adj_n(const cplx<T>* V, cplx<T>* out, double kf, double coef, float* zero, int64_t nzero,
-                    cudaStream_t st, const AdjGrOp* gr) {
+template <typename T, int LOGN, bool GR, bool FD>
+cudaError_t x_adj_k(const cplx<T>* V, cplx<T>* out, double kf, double coef, float* zero, int64_t nzero, cudaStream_t st,
+                    const AdjGrOp& gr) {
     typedef Shape<T, LOGN> S;
     const size_t smem = sizeof(cplx<T>) * (S::N + 2 * (size_t)S::N * (S::CB + 1));
-    const void* fn = gr ? (const void*)k_x_adj<T, LOGN, true> : (const void*)k_x_adj<T, LOGN, false>;
-    cudaError_t e = set_smem(fn, smem);
+    cudaError_t e = set_smem((const void*)k_x_adj<T, LOGN, GR, FD>, smem);
     if (e != cudaSuccess) return e;
+    k_x_adj<T, LOGN, GR, FD><<<dim3(S::N / S::CB, S::M + 1), S::CB * S::QN, smem, st>>>(
+        V, out, kf, coef, (float4*)zero, zero ? nzero / 4 : 0, gr);
+    return cudaGetLastError();
+}
+
+template <typename T, int LOGN>
+cudaError_t x_adj_n(const cplx<T>* V, cplx<T>* out, double kf, double coef, float* zero, int64_t nzero,
+                    cudaStream_t st, const AdjGrOp* gr, bool fd) {
     if (nzero % 4 != 0 || (zero && (uintptr_t)zero % 16 != 0)) return cudaErrorInvalidValue;
     if (gr && !gr->Z) return cudaErrorInvalidValue;
-    const dim3 grid(S::N / S::CB, S::M + 1);
-    if (gr)
-        k_x_adj<T, LOGN, true><<<grid, S::CB * S::QN, smem, st>>>(V, out, kf, coef, (float4*)zero, zero ? nzero / 4 : 0,
-                                                                  *gr);
-    else
-        k_x_adj<T, LOGN, false><<<grid, S::CB * S::QN, smem, st>>>(V, out, kf, coef, (float4*)zero,
-                                                                   zero ? nzero / 4 : 0, AdjGrOp());
-    return cudaGetLastError();
+    const AdjGrOp g = gr ? *gr : AdjGrOp();
+    if (gr) return fd ? x_adj_k<T, LOGN, true, true>(V, out, kf, coef, zero, nzero, st, g)
+                      : x_adj_k<T, LOGN, true, false>(V, out, kf, coef, zero, nzero, st, g);
+    return fd ? x_adj_k<T, LOGN, false, true>(V, out, kf, coef, zero, nzero, st, g)
+              : x_adj_k<T, LOGN, false, false>(V, out, kf, coef, zero, nzero, st, g);
 }
 
 template <typename T, int LOGN>
@@ -1215,8 +1222,8 @@ cudaError_t fft_plane(cplx<T>* A, cplx<T>* GX, cplx<T>* GY, int nplanes, int n, 
 
 template <typename T>
 cudaError_t x_adj(const cplx<T>* V, cplx<T>* out, int n, double kf, double coef, cudaStream_t st, float* zero,
-                  int64_t nzero, const AdjGrOp* gr) {
-    PM_DISPATCH_LOGN(n, (x_adj_n<T, LG>(V, out, kf, coef, zero, nzero, st, gr)))
+                  int64_t nzero, const AdjGrOp* gr, bool fd) {
+    PM_DISPATCH_LOGN(n, (x_adj_n<T, LG>(V, out, kf, coef, zero, nzero, st, gr, fd)))
 }
 
 template <typename T>
@@ -1246,7 +1253,7 @@ cudaError_t x_cols(cplx<T>* data, cplx<T>* out2, int nplanes, int n, const SpecO
     template cudaError_t x_cols<T>(cplx<T>*, cplx<T>*, int, int, const SpecOp&, cudaStream_t);      \
     template cudaError_t forward_zy<T>(const T*, cplx<T>*, int, int, cudaStream_t);                     \
     template cudaError_t x_adj<T>(const cplx<T>*, cplx<T>*, int, double, double, cudaStream_t, float*, \
-                                  int64_t, const AdjGrOp*);                                             \
+                                  int64_t, const AdjGrOp*, bool);                                       \
     template cudaError_t inverse_yz_grad<T>(cplx<T>*, cplx<T>*, cplx<T>*, T* const*, int, int, double,   \
                                             cudaStream_t, const double*, T*);
 

@@ -104,9 +104,11 @@ struct AdjGrOp {
     double H1 = 0.0, om1 = 0.0, cc1 = 0.0; // the same of evaluation n + 1 (any finite values when Z is 0)
     void* Z = nullptr;
 };
+// fd: the first-order gradient's transposed chain: V is one scalar field (the deposit of the
+// adjoint momenta with the CIC derivative weights) and W = FFT_x V, without i k_j.
 template <typename T>
 cudaError_t x_adj(const cplx<T>* V, cplx<T>* out, int n, double kf, double coef, cudaStream_t st,
-                  float* zero = nullptr, int64_t nzero = 0, const AdjGrOp* gr = nullptr);
+                  float* zero = nullptr, int64_t nzero = 0, const AdjGrOp* gr = nullptr, bool fd = false);
 // Forward y, x with the per-mode operator op (OP_NEWTON or OP_GR) and inverse y with the y
 // gradient of nplanes kz planes in one persistent launch of CTAs of `threads` (256, 512, 1024)
 // (FP32, n = 256, 512, 1024): on entry

@@ -72,6 +72,14 @@ cudaError_t adj_direct(const uint32_t* x, int64_t count, int n, const float* v, 
 cudaError_t adj_kick_particles(const uint32_t* x, int64_t count, int n, float* v, const float* const* G,
                                const float* rho_bar, float K, float Km, float drift_next, float* lam_u,
                                cudaStream_t st);
+// First-order gradient: V += -sum_j v_j dW/dx_j (inv_d = n / L; V zeroed by the caller), and the
+// particle side of its transposed kick (phi the recorded potential mesh; rho_bar as in
+// adj_kick_particles).
+cudaError_t deposit_grad(const uint32_t* x, int64_t count, int n, const float* v, double inv_d, float* V,
+                         cudaStream_t st);
+cudaError_t adj_kick_particles_fd(const uint32_t* x, int64_t count, int n, float* v, const float* phi,
+                                  const float* rho_bar, float K, float Km, double inv_d, float drift_next, float* lam_u,
+                                  cudaStream_t st);
 // V_j += CIC deposit of v_j for the np^3 lattice-ordered particles x (V_j zeroed by the caller).
 cudaError_t deposit_vec(const uint32_t* x, int np, int n, const float* v, float* const* V, cudaStream_t st);
 cudaError_t adj_combine(const float2* const* in, float2* out, int n, double kf, double coef, const double* amp,

@@ -340,3 +340,46 @@ def test_gradient_with_the_persistent_fft_form(mode):
         out[form] = to_host(run.adjoint(d_disp=cot, d_mom=cot)).astype(np.float64)
     assert np.max(np.abs(out[0])) > 0
     assert rel_l2(out[512], out[0]) < 1e-4
+
+
+@pytest.mark.parametrize("mode,box,n_lo,a_i,a_f", [(0, 300.0, 0, 0.2, 0.6), (1, 20000.0, 4, 0.1, 0.5)])
+def test_first_order_gradient_matches_fp64_oracle(mode, box, n_lo, a_i, a_f):
+    # the paper's first-order gradient (PM_GRAD_FD1: g = -grad of the CIC interpolant of phi):
+    # the GPU reverse sweep (scalar deposit with the CIC derivative weights, the transposed
+    # potential map -- Green's function or the lagged constraint with its carried spectrum --,
+    # the interpolant's mixed second derivatives) against the oracle's vector-Jacobian product
+    # for a loss of the final density, displacements and momenta; checkpoints every 2 of 6 steps,
+    # so the first segments are re-run
+    pm = lib()
+    np_side, nmesh, steps = 16, 32, 6
+    c = Cosmology()
+    w = inputs.gaussian_field(31, np_side).astype(np.float32)
+    run = pm.PMRun(pm.make_config(np_side, nmesh, box, a_i, a_f, steps, mode=mode, n_lo=n_lo,
+                                  gradient=pm.PM_GRAD_FD1))
+    Wk = _spectral_weight(nmesh)
+    r = np.random.default_rng(14)
+    gdisp = r.standard_normal((3, np_side**3)) * 1e-3
+    h = r.standard_normal((3, np_side**3)) * 1e-2
+    wv = to_dev(w).requires_grad_(True)
+    delta, disp, mom = pm.run_fields(run, wv, checkpoint_every=2, momenta=True)
+    L = _torch_loss(delta, disp, to_dev(Wk), to_dev(gdisp), nmesh) + (to_dev(h) * mom.to(torch.float64)).sum()
+    L.backward()
+    g = to_host(wv.grad).astype(np.float64)
+    w64 = w.astype(np.float64)
+    om = adjoint.GR_POISSON if mode else adjoint.NEWTON
+    u, p_o, _, _ = adjoint.forward(c, np_side, nmesh, box, a_i, a_f, steps, w64, om, adjoint.FD1)
+    dk = np.fft.fftn(cic.density_contrast(u, nmesh))
+    lam_delta = 2.0 * np.real(np.fft.ifftn(Wk * dk)) / nmesh**3
+    go = adjoint.vjp(c, np_side, nmesh, box, a_i, a_f, steps, w64, lam_delta=lam_delta, lam_disp=gdisp, lam_mom=h,
+                     mode=om, gradient=adjoint.FD1)
+    gs = adjoint.vjp(c, np_side, nmesh, box, a_i, a_f, steps, w64, lam_delta=lam_delta, lam_disp=gdisp, lam_mom=h,
+                     mode=om, gradient=adjoint.SPECTRAL)
+    assert rel_l2(g, go) < 1e-3
+    assert rel_l2(gs, go) > 0.01  # the spectral gradient's chain would not pass
+    assert rel_l2(to_host(mom).astype(np.float64), p_o) < 1e-3
+    # the same gradient from one segment (no re-runs)
+    wv2 = to_dev(w).requires_grad_(True)
+    delta, disp, mom = pm.run_fields(run, wv2, checkpoint_every=steps, momenta=True)
+    L2 = _torch_loss(delta, disp, to_dev(Wk), to_dev(gdisp), nmesh) + (to_dev(h) * mom.to(torch.float64)).sum()
+    L2.backward()
+    assert rel_l2(to_host(wv2.grad).astype(np.float64), g) < 1e-5
