@@ -252,16 +252,21 @@ def test_first_order_gradient_run_matches_oracle(prec, np_side, nmesh, mode):
     assert rel_l2(pg, ps) > 1e-3
 
 
-def test_first_order_gradient_is_refused_by_batches_and_the_loss_gradient():
+def test_first_order_gradient_is_refused_by_batches_and_the_fp64_gradient():
+    # batches keep the spectral force; the loss gradient takes the first-order force in FP32
+    # (checked against the oracle in test_gpu_adjoint.py) and refuses FP64 contexts
     pm = lib()
     cfg = pm.make_config(32, 64, 500.0, 0.1, 1.0, 4, gradient=pm.PM_GRAD_FD1)
     with pytest.raises(pm.PMError) as e:
         pm.PMBatch(cfg, boxes=[500.0, 600.0])
     assert e.value.status == 1
-    run = pm.PMRun(cfg)
     w = to_dev(inputs.gaussian_field(3, 32).astype(np.float32))
+    target = torch.zeros((64, 64, 64), dtype=torch.float32, device="cuda")
+    L, g = pm.PMRun(cfg).loss_grad(w, target)
+    assert np.isfinite(L) and L > 0 and torch.isfinite(g).all()
+    run64 = pm.PMRun(pm.make_config(32, 64, 500.0, 0.1, 1.0, 4, precision=pm.PM_FP64))
     with pytest.raises(pm.PMError) as e:
-        run.loss_grad(w, torch.zeros((64, 64, 64), dtype=torch.float32, device="cuda"))
+        run64.loss_grad(w, target)
     assert e.value.status == 6
 
 
