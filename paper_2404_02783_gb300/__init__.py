@@ -623,6 +623,24 @@ class PMBatch:
         p = _view(self._ws, pp, nbytes).view(torch.float32).view(3, self.count)
         return x, p
 
+    def density(self, r):
+        """CIC density contrast of realisation r (pm_density on its context view), (n, n, n)."""
+        import torch
+        n = self.cfg.nmesh
+        out = torch.empty((n, n, n), dtype=torch.float32, device=self.workspace.device)
+        pm_density(self.context(r), out)
+        return out
+
+    def bispectrum(self, r, edges, m, field=None, deconvolve=True):
+        """B(k) of realisation r (of its particles, or of `field` on its mesh): (B, N_tri)."""
+        import torch
+        view = self.context(r)
+        nb = len(edges) - 1
+        scratch = torch.empty(pm_bispectrum_scratch_size(view, m, nb) + 256, dtype=torch.uint8,
+                              device=self.workspace.device)
+        off = (-scratch.data_ptr()) % 256
+        return pm_bispectrum(view, edges, m, scratch[off:], field, deconvolve)
+
     def power(self, edges, deconvolve=True):
         edges = np.ascontiguousarray(edges, dtype=np.float64)
         nb = len(edges) - 1

@@ -203,3 +203,37 @@ def test_batch_autotuner_picks_a_form_and_chunk():
     b.ic(SEEDS * 2)
     b.step(STEPS, graph=True)
     assert b.state()[0] == STEPS
+
+
+def test_batched_bispectrum_ratio_matches_single_pipeline():
+    # Sec. 5.3 on the batched ensemble: per realisation (its context view) the density, the halo
+    # proxy and B_hhh / B_mmm on the equilateral and squeezed (k3 = 4 k_f) slices, against the same
+    # pipeline on the realisation run alone (which test_gpu_bias.py checks against the oracle)
+    pm = lib()
+    b = pm.PMBatch(_cfg(pm), boxes=BOXES)
+    b.ic(SEEDS)
+    b.step(STEPS)
+    edges = np.arange(0.5, 16.0, 1.0)
+    nb = len(edges) - 1
+    eq, sq = pm.bispectrum_configurations(nb, 3)
+    for r in range(3):
+        dm = b.density(r)
+        dh = torch.empty_like(dm)
+        pm.pm_halo_proxy(b.context(r), dh, field=dm)
+        bh, ntri = b.bispectrum(r, edges, 64, field=dh)
+        bm, _ = b.bispectrum(r, edges, 64, field=dm)
+        run = pm.PMRun(_cfg(pm, BOXES[r]))
+        run.ic(seed=SEEDS[r])
+        run.step(STEPS)
+        dm1 = run.density()
+        dh1 = torch.empty_like(dm1)
+        pm.pm_halo_proxy(run.ctx, dh1, field=dm1)
+        bh1, ntri1 = run.bispectrum(edges, 64, field=dh1)
+        bm1, _ = run.bispectrum(edges, 64, field=dm1)
+        np.testing.assert_array_equal(ntri, ntri1)
+        for sl in (eq, sq):
+            idx = np.asarray(sl)
+            ok = ntri[idx] > 0
+            assert np.count_nonzero(ok) > 3
+            np.testing.assert_allclose(bm[idx][ok], bm1[idx][ok], rtol=1e-4, atol=1e-6 * np.max(np.abs(bm1[idx])))
+            np.testing.assert_allclose((bh / bm)[idx][ok], (bh1 / bm1)[idx][ok], rtol=1e-3)
