@@ -276,6 +276,7 @@ def roofline(phases, np_side, n, fp64, peak, peak_kind, fused_fft=True):
 
 
 FP64_NOMINAL_TFLOPS = 1.25  # GB300 dense FP64, nominal
+FP32_ALU_TFLOPS = round(152 * 128 * 2 * 2.07e9 / 1e12, 2)  # CUDA-core FP32 FMA rate at the maximum SM clock
 
 
 def fp64_peak(torch):
@@ -578,10 +579,14 @@ def estimators(pm, torch, args):
     e24 = np.linspace(0.0, 0.05 / kf, 25)
     ms_bk = timed(lambda: run.bispectrum(e24, 128, field=delta), reps=3)
     ntri = 24 * 25 * 26 // 6
-    flops = 6.0 * ntri * 128**3
+    flops = 3.0 * ntri * 128**3  # S_ijl = sum_x I_i I_j I_l: two multiplies and an add a point
+    tf = flops / (ms_bk * 1e-3) / 1e12
     out["bispectrum"] = {"ms": round(ms_bk, 3), "bins": 24, "triangles": ntri, "m": 128,
-                         "triangle_sum_flops": flops, "TFLOPs": round(flops / (ms_bk * 1e-3) / 1e12, 2),
-                         "bound": "alu (FP32 triangle sums on the m-grid) plus 48 inverse FFTs of 128^3"}
+                         "triangle_sum_flops": flops, "TFLOPs": round(tf, 2),
+                         "bound": "alu", "peak": FP32_ALU_TFLOPS, "frac": round(tf / FP32_ALU_TFLOPS, 4),
+                         "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flops x 2.07 GHz",
+                         "what": "FP32 triangle sums on the m-grid (integer counts cached) plus 24 masked "
+                                 "spectra and their inverse FFTs of 128^3, over the whole call"}
     dh = torch.empty_like(delta)
     e32 = pm.log_edges(32, 1.0, n / 2.0)
 
