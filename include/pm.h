@@ -349,13 +349,15 @@ pm_status pm_loss_grad(pm_ctx* ctx, const void* white_noise, const void* delta_t
                        void* scratch, size_t scratch_bytes, double* loss, void* grad_w);
 
 /* ------------------------------------------------------- batch of realisations
- * Many independent realisations (seeds, box sizes) of the same FP32 Newtonian run,
- * advanced together: every pass of a step is one launch over all of them, and a
- * multi-step run can be recorded once and replayed as a single CUDA graph launch.
+ * Many independent realisations (seeds, box sizes) of the same FP32 run, Newtonian or
+ * Poisson gauge, advanced together: every pass of a step is one launch over all of them,
+ * and a multi-step run can be recorded once and replayed as a single CUDA graph launch.
  * This serves the paper's ensembles of runs from shared phases (Secs. 2-3) and the
  * variance of b1 across realisations (Sec. 5.2).  Requirements: precision
- * PM_FP32_FIXED, mode PM_NEWTON, nmesh >= 64 and nmesh / np in {1, 2, 4}; cfg->box is
- * the default box, boxes[r] (may be NULL) the box of realisation r.  Memory: one
+ * PM_FP32_FIXED, the spectral gradient, nmesh >= 64 and nmesh / np in {1, 2, 4}; cfg->box
+ * is the default box, boxes[r] (may be NULL) the box of realisation r.  In the Poisson gauge
+ * each realisation keeps its own Phi history (and FP64 island), and the lag of force
+ * evaluation e reads evaluation e - 1 (none at the first after pm_batch_ic).  Memory: one
  * caller workspace of pm_batch_workspace_size bytes, particles [r][3][np^3], meshes
  * [r][n^3].  The batch owns one extra CUDA stream and two events for graph replay. */
 typedef struct pm_batch pm_batch;

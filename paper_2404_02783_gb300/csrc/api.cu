@@ -1673,6 +1673,7 @@ struct pm_batch {
     std::vector<pm_ctx*> views;  // one context per realisation on slices of the workspace
     size_t X = 0, P = 0, RHO = 0, SPEC[3] = {0, 0, 0}, FORCE[3] = {0, 0, 0}, AMP = 0, KF = 0, SCALE = 0;
     size_t BIN = 0, WTAB = 0, ACC = 0, total = 0;
+    size_t PHI = 0, ISL = 0, isl = 0;  // Poisson gauge: Phi_old and the FP64 island of every realisation
     int64_t amp_len = 0;
     int step = 0;
     bool synced = true;
@@ -1716,14 +1717,19 @@ void batch_plan(pm_batch& b) {
     b.BIN = take((3 * (n / 2) * (n / 2) + 1) * 2);
     b.WTAB = take((n / 2 + 1) * 8);
     b.ACC = take(2 * kMaxBins * 8);
+    if (c.mode == PM_GR_POISSON) {
+        b.PHI = take(B * nspec * 8);
+        b.isl = c.n_lo > 0 ? (size_t)(c.n_lo + 1) * (2 * c.n_lo + 1) * (2 * c.n_lo + 1) * 16 : 0;
+        b.ISL = take(B * b.isl);
+    }
     b.total = off;
 }
 
 pm_status batch_validate(const pm_config* cfg, int B, const double* boxes) {
     PM_TRY(validate(cfg));
     if (B < 1 || B > 4096) return fail(PM_ERR_INVALID_ARG, "batch size must be in 1..4096");
-    if (cfg->precision != PM_FP32_FIXED || cfg->mode != PM_NEWTON || cfg->gradient != PM_GRAD_SPECTRAL)
-        return fail(PM_ERR_INVALID_ARG, "batches run the FP32 Newtonian step with the spectral force");
+    if (cfg->precision != PM_FP32_FIXED || cfg->gradient != PM_GRAD_SPECTRAL)
+        return fail(PM_ERR_INVALID_ARG, "batches run the FP32 step with the spectral force");
     if (!ikd_deposit_supported(cfg->np, cfg->precision, cfg->nmesh))
         return fail(PM_ERR_INVALID_ARG, "batches need nmesh >= 64 and nmesh / np in {1, 2, 4}");
     if (boxes)
@@ -1752,6 +1758,21 @@ pm_status batch_forces(pm_batch* b, cudaStream_t s, int r0, int c) {
     op.fwd = 1;
     op.coef = -1.5 * b->cfg.omega_m / ((double)n * n * n);
     op.kf_arr = kf;
+    if (b->cfg.mode == PM_GR_POISSON) {
+        // force evaluation e = b->step (the closing kick's is n_steps) at a_e; its lagged
+        // constraint reads the previous evaluation's Phi (a_{e-1}), none at the first
+        const int e = b->step;
+        const double a = b->a_grid(e);
+        op.kind = OP_GR;
+        op.calH = pmhost::conformal_hubble(b->cosmo, a);
+        op.omm_a = pmhost::omega_m_a(b->cosmo, a);
+        op.first = e == 0 ? 1 : 0;
+        op.inv_dtau = e > 0 ? 1.0 / (pmhost::kCLight * pmhost::kick_integral(b->cosmo, b->a_grid(e - 1), a)) : 0.0;
+        op.ac2_over_n3 = a * pmhost::kCLight * pmhost::kCLight / ((double)n * n * n);
+        op.n_lo = b->cfg.n_lo;
+        op.phi_old = (float2*)b->at(b->PHI) + r0 * nspec;
+        op.island = b->isl ? (double2*)((unsigned char*)b->at(b->ISL) + r0 * b->isl) : nullptr;
+    }
     float* out[3] = {(float*)b->at(b->FORCE[0]) + r0 * n3, (float*)b->at(b->FORCE[1]) + r0 * n3,
                      (float*)b->at(b->FORCE[2]) + r0 * n3};
     if (plane) {

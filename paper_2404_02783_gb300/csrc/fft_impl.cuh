@@ -363,15 +363,16 @@ __device__ __forceinline__ cplx<T> mode_op(const SpecOp& op, cplx<T> vv, int nx,
                                                              : op.coef / (kf * kf) * amp[n2] / (double)n2;
         phi = (n2 == 0 || nyq) ? cmake<C>(T(0), T(0)) : cscale(g, T(filt));
     } else {  // OP_GR
+        // the FP64 island of field `field` ((n_lo + 1) (2 n_lo + 1)^2 modes a field)
         if (n2 == 0) {
             phi = cmake<C>(T(0), T(0));
             if (op.n_lo > 0) {
                 const int L = op.n_lo, W2 = 2 * L + 1;
-                op.island[((size_t)nz * W2 + L) * W2 + L] = make_double2(0.0, 0.0);
+                op.island[(((size_t)field * (L + 1) + nz) * W2 + L) * W2 + L] = make_double2(0.0, 0.0);
             }
         } else if (n2 <= op.n_lo * op.n_lo) {
             const int L = op.n_lo, W2 = 2 * L + 1;
-            const size_t id = ((size_t)nz * W2 + (nx + L)) * W2 + (ny + L);
+            const size_t id = (((size_t)field * (L + 1) + nz) * W2 + (nx + L)) * W2 + (ny + L);
             const double k2 = kf * kf * (double)n2;
             const double H = op.calH;
             const double num_s = -1.5 * H * H * op.omm_a;

@@ -237,3 +237,32 @@ def test_batched_bispectrum_ratio_matches_single_pipeline():
             assert np.count_nonzero(ok) > 3
             np.testing.assert_allclose(bm[idx][ok], bm1[idx][ok], rtol=1e-4, atol=1e-6 * np.max(np.abs(bm1[idx])))
             np.testing.assert_allclose((bh / bm)[idx][ok], (bh1 / bm1)[idx][ok], rtol=1e-3)
+
+
+@pytest.mark.parametrize("n_lo,graph", [(0, True), (4, True), (4, False)])
+def test_poisson_gauge_batch_matches_single_runs(n_lo, graph):
+    # the Poisson gauge in a batch (per-realisation Phi history and FP64 island, boxes of 2, 8
+    # and 20 Gpc/h where the lag matters): every realisation equals the run done alone, and the
+    # batch's realisation on the largest box equals the oracle's Poisson-gauge run
+    pm = lib()
+    boxes, seeds, steps = [2000.0, 8000.0, 20000.0], [21, 22, 23], 8
+    cfg = pm.make_config(NP, NMESH, boxes[0], 0.02, 1.0, steps, mode=1, n_lo=n_lo)
+    b = pm.PMBatch(cfg, boxes=boxes)
+    b.ic(seeds)
+    b.step(steps, graph=graph)
+    assert b.state()[0] == steps and b.state()[2]
+    for r in range(3):
+        run = pm.PMRun(pm.make_config(NP, NMESH, boxes[r], 0.02, 1.0, steps, mode=1, n_lo=n_lo))
+        run.ic(seed=seeds[r])
+        x0 = ticks_to_host(run.particles()[0]).copy()
+        run.step(steps)
+        xs, ps = ticks_to_host(run.particles()[0]).copy(), to_host(run.particles()[1]).astype(np.float64)
+        xb, pb = _batch_particles(b, r)
+        assert rel_l2(_disp(xb, x0), _disp(xs, x0)) < 1e-5
+        assert rel_l2(pb, ps) < 1e-5
+    c = Cosmology()
+    x0, p0 = ic.zeldovich(c, NP, boxes[2], 0.02, seed=seeds[2], fixed=True)
+    ref = opm.PMRun(c, NMESH, boxes[2], 0.02, 1.0, steps, x0, p0, mode=opm.GR_POISSON)
+    ref.step(steps)
+    xb, pb = _batch_particles(b, 2)
+    assert rel_l2(_disp(xb, x0), _disp(ref.x, x0)) < 2e-3
