@@ -162,11 +162,23 @@ pm_status pm_set_particles(pm_ctx* ctx, const void* x, const void* p);
  * the integrator to `step` (0..n_steps) with momenta synchronised with the positions
  * (synchronised != 0) or half a step behind (0, the state pm_step leaves between steps:
  * p at the midpoint a_{step-1/2}).  The momenta are synchronised at step 0 and at
- * n_steps (otherwise PM_ERR_INVALID_ARG).  A Poisson-gauge context resumes only at step 0
- * (PM_ERR_UNSUPPORTED otherwise: its lagged constraint needs the Phi history, which this
- * call does not carry).  A snapshot taken with pm_particles + pm_state and restored here
+ * n_steps (otherwise PM_ERR_INVALID_ARG).  A Poisson-gauge context resumes here only at
+ * step 0 (PM_ERR_UNSUPPORTED otherwise: its lagged constraint needs the Phi history, which
+ * pm_set_state_gr carries).  A snapshot taken with pm_particles + pm_state and restored here
  * continues exactly as the original run.  FP64 positions: as pm_set_particles. */
 pm_status pm_set_state(pm_ctx* ctx, const void* x, const void* p, int step, int synchronised);
+
+/* The Poisson-gauge history the lagged constraint (Sec. 2) carries between force evaluations:
+ * device pointers to the context's Phi_old spectrum (layout of the spectra, ctx precision) and
+ * FP64 island (NULL when n_lo = 0), with their sizes in bytes (any output may be NULL).  A
+ * snapshot of a Poisson-gauge run between steps is pm_particles + pm_state + copies of these;
+ * pm_set_state_gr restores it: as pm_set_state, then the history copied in (device pointers of
+ * those sizes; required for step > 0, the island too when n_lo > 0), the last force evaluation
+ * taken at a_{step-1} (at a_final after the closing kick).  The run then continues as the
+ * original.  Non-Poisson-gauge contexts: PM_ERR_UNSUPPORTED / PM_ERR_INVALID_ARG. */
+pm_status pm_gr_history(pm_ctx* ctx, void** phi_old, size_t* phi_bytes, void** island, size_t* island_bytes);
+pm_status pm_set_state_gr(pm_ctx* ctx, const void* x, const void* p, int step, int synchronised, const void* phi_old,
+                          const void* island);
 
 /* Lagrangian displacement d = x - q of every particle (minimum image, Mpc/h), q its
  * lattice node, written to disp[3][np^3] (float for PM_FP32_FIXED, double for PM_FP64).

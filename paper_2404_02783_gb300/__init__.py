@@ -32,7 +32,7 @@ _STATUS = {0: "PM_OK", 1: "PM_ERR_INVALID_ARG", 2: "PM_ERR_CUDA", 3: "PM_ERR_WOR
 EXPORTS = ("pm_workspace_size", "pm_init", "pm_destroy", "pm_ic_zeldovich", "pm_step", "pm_particles",
            "pm_set_particles", "pm_set_state", "pm_state", "pm_set_fused_fft", "pm_autotune_fft", "pm_profile", "pm_timings", "pm_density", "pm_potential", "pm_displacement_correction", "pm_power", "pm_halo_proxy", "pm_linear_bias",
            "pm_bispectrum_scratch_size", "pm_bispectrum", "pm_triangle_index", "pm_b1_gr_theory", "pm_cic_deposit", "pm_cic_interp",
-           "pm_adjoint_scratch_size", "pm_adjoint_record", "pm_adjoint_run", "pm_loss_grad", "pm_displacement", "pm_positions", "pm_batch_workspace_size", "pm_batch_init", "pm_batch_destroy", "pm_batch_context", "pm_batch_ic",
+           "pm_adjoint_scratch_size", "pm_adjoint_record", "pm_adjoint_run", "pm_loss_grad", "pm_displacement", "pm_positions", "pm_gr_history", "pm_set_state_gr", "pm_batch_workspace_size", "pm_batch_init", "pm_batch_destroy", "pm_batch_context", "pm_batch_ic",
            "pm_batch_step", "pm_batch_state", "pm_batch_power", "pm_batch_bias", "pm_batch_set_chunk", "pm_batch_autotune", "pm_batch_set_fft", "pm_batch_tuning",
            "pm_cell_sort_scratch_size", "pm_cell_sort", "pm_cell_sort_static", "pm_div_mode_check", "pm_fft_r2c", "pm_fft_c2r", "pm_version", "pm_last_error")
 
@@ -101,6 +101,8 @@ def lib():
         "pm_adjoint_scratch_size": (vp, i, ctypes.POINTER(sz)),
         "pm_loss_grad": (vp, vp, vp, i, vp, sz, pd, vp),
         "pm_adjoint_record": (vp, vp, i, vp, sz),
+        "pm_gr_history": (vp, ctypes.POINTER(vp), ctypes.POINTER(sz), ctypes.POINTER(vp), ctypes.POINTER(sz)),
+        "pm_set_state_gr": (vp, vp, vp, i, i, vp, vp),
         "pm_positions": (vp, vp),
         "pm_adjoint_run": (vp, vp, vp, vp, vp),
         "pm_displacement": (vp, vp),
@@ -268,6 +270,19 @@ def pm_adjoint_record(ctx, white_noise, checkpoint_every, scratch):
 
 def pm_adjoint_run(ctx, d_delta, d_disp, grad_w, d_mom=None):
     _check(lib().pm_adjoint_run(ctx, _ptr(d_delta), _ptr(d_disp), _ptr(d_mom), _ptr(grad_w)))
+
+
+def pm_gr_history(ctx):
+    """(phi_old address, bytes, island address or None, bytes) of a Poisson-gauge context."""
+    ph, isl = ctypes.c_void_p(), ctypes.c_void_p()
+    pb, ib = ctypes.c_size_t(), ctypes.c_size_t()
+    _check(lib().pm_gr_history(ctx, ctypes.byref(ph), ctypes.byref(pb), ctypes.byref(isl), ctypes.byref(ib)))
+    return ph.value, pb.value, isl.value, ib.value
+
+
+def pm_set_state_gr(ctx, x, p, step, synchronised, phi_old, island=None):
+    _check(lib().pm_set_state_gr(ctx, _ptr(x), _ptr(p), int(step), int(bool(synchronised)), _ptr(phi_old),
+                                 _ptr(island)))
 
 
 def pm_positions(ctx, out):
@@ -494,6 +509,14 @@ class PMRun:
         c = lambda t: None if t is None else t.contiguous()
         pm_adjoint_run(self.ctx, c(d_delta), c(d_disp), grad, d_mom=c(d_mom))
         return grad
+
+    def gr_history(self):
+        """Copies of the Poisson-gauge Phi_old spectrum and FP64 island (None when n_lo = 0), as
+        uint8 device tensors for pm_set_state_gr."""
+        ph, pb, isl, ib = pm_gr_history(self.ctx)
+        phi = _view(self._ws, ph, pb).clone()
+        island = _view(self._ws, isl, ib).clone() if isl else None
+        return phi, island
 
     def positions(self):
         """Positions in Mpc/h in [0, L), shape (3, np^3) (float32 from the FP32 ticks)."""

@@ -812,6 +812,42 @@ pm_status pm_set_state(pm_ctx* c, const void* x, const void* p, int step, int sy
     return copy_state(c, x, p, step, synchronised != 0);
 }
 
+pm_status pm_gr_history(pm_ctx* c, void** phi_old, size_t* phi_bytes, void** island, size_t* island_bytes) {
+    if (!c) return fail(PM_ERR_INVALID_ARG, "null context");
+    if (c->cfg.mode != PM_GR_POISSON) return fail(PM_ERR_UNSUPPORTED, "only a Poisson-gauge context has a Phi history");
+    const size_t nspec = (size_t)(c->n / 2 + 1) * c->n * c->n;
+    const size_t isl = c->L.has_island ? (size_t)(c->cfg.n_lo + 1) * (2 * c->cfg.n_lo + 1) * (2 * c->cfg.n_lo + 1) * 16 : 0;
+    if (phi_old) *phi_old = c->at(c->L.phi_old);
+    if (phi_bytes) *phi_bytes = nspec * 2 * c->sT();
+    if (island) *island = isl ? c->at(c->L.island) : nullptr;
+    if (island_bytes) *island_bytes = isl;
+    return PM_OK;
+}
+
+pm_status pm_set_state_gr(pm_ctx* c, const void* x, const void* p, int step, int synchronised, const void* phi_old,
+                          const void* island) {
+    if (!c || !x || !p) return fail(PM_ERR_INVALID_ARG, "null argument");
+    if (c->cfg.mode != PM_GR_POISSON) return fail(PM_ERR_INVALID_ARG, "pm_set_state_gr needs a Poisson-gauge context");
+    if (step < 0 || step > c->cfg.n_steps) return fail(PM_ERR_INVALID_ARG, "step outside 0..n_steps");
+    if ((step == 0 || step == c->cfg.n_steps) && !synchronised)
+        return fail(PM_ERR_INVALID_ARG, "the momenta are synchronised at the ends of the a-grid");
+    if (step > 0 && (!phi_old || (c->L.has_island && !island)))
+        return fail(PM_ERR_INVALID_ARG, "a resumed Poisson-gauge run needs its Phi history (and island)");
+    PM_TRY(copy_state(c, x, p, step, synchronised != 0));
+    if (step > 0) {
+        void* ph = nullptr;
+        void* is = nullptr;
+        size_t pb = 0, ib = 0;
+        PM_TRY(pm_gr_history(c, &ph, &pb, &is, &ib));
+        PM_CK(cudaMemcpyAsync(ph, phi_old, pb, cudaMemcpyDeviceToDevice, c->st));
+        if (ib) PM_CK(cudaMemcpyAsync(is, island, ib, cudaMemcpyDeviceToDevice, c->st));
+        // the last force evaluation: a_{step-1} between steps, a_final after the closing kick
+        c->have_phi = true;
+        c->a_last = step < c->cfg.n_steps ? c->a_grid(step - 1) : c->a_grid(step);
+    }
+    return PM_OK;
+}
+
 pm_status pm_displacement(pm_ctx* c, void* disp) {
     if (!c || !disp) return fail(PM_ERR_INVALID_ARG, "null argument");
     PM_CK(lagrangian_displacement(c->at(c->L.x), disp, c->np, c->cfg.precision, c->cfg.box, c->st));

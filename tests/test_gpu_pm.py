@@ -355,3 +355,37 @@ def test_positions_in_mpc(precision):
         want = x * box
     assert pos.dtype == want.dtype and np.array_equal(pos, want)
     assert pos.min() >= 0.0 and pos.max() < box
+
+
+@pytest.mark.parametrize("n_lo", [0, 4])
+def test_poisson_gauge_run_resumes_from_a_snapshot_with_its_history(n_lo):
+    # a Poisson-gauge snapshot between steps (particles, integrator state, Phi_old and the FP64
+    # island) restored into a fresh context with pm_set_state_gr continues as the original run;
+    # without the history pm_set_state refuses it, and a run resumed with a wrong (zero) history
+    # departs from the original
+    pm = lib()
+    cfg = pm.make_config(32, 64, 8000.0, 0.02, 1.0, 12, mode=1, n_lo=n_lo)
+    a = pm.PMRun(cfg)
+    a.ic(seed=4)
+    a.step(7)
+    x, p = (t.clone() for t in a.particles())
+    step, _, synced = a.state()
+    phi, island = a.gr_history()
+    a.step(5)
+    xa, pa = _host_particles(a)
+    b = pm.PMRun(cfg)
+    with pytest.raises(pm.PMError) as e:
+        pm.pm_set_state(b.ctx, x, p, step, synced)
+    assert e.value.status == 6
+    pm.pm_set_state_gr(b.ctx, x, p, step, synced, phi, island)
+    b.step(5)
+    xb, pb = _host_particles(b)
+    x0 = ticks_to_host(x).copy()
+    assert rel_l2(_disp(xb, 32) - _disp(x0, 32), _disp(xa, 32) - _disp(x0, 32)) < 1e-5
+    assert rel_l2(pb, pa) < 1e-5
+    z = pm.PMRun(cfg)
+    pm.pm_set_state_gr(z.ctx, x, p, step, synced, torch.zeros_like(phi),
+                       None if island is None else torch.zeros_like(island))
+    z.step(5)
+    _, pz = _host_particles(z)
+    assert rel_l2(pz, pa) > 1e-3
