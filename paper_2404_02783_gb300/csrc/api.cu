@@ -60,6 +60,10 @@ struct Layout {
 };
 
 constexpr int kMaxBins = 256;
+// Mean of the particle density in mesh-cell mass units (np^3 particles of mass (n / np)^3 on
+// n^3 cells), subtracted as the forward transform loads it: the operators drop the zero mode,
+// and the transform's FP32 rounding then scales with delta instead of with 1 + delta.
+constexpr double kDensityMean = 1.0;
 
 pm_status validate(const pm_config* c) {
     if (!c) return fail(PM_ERR_INVALID_ARG, "null config");
@@ -217,11 +221,12 @@ struct Phase {
     }
 };
 
-// Forward z and y passes of a real mesh of side n into spec.
+// Forward z and y passes of a real mesh of side n into spec, `sub` subtracted from every
+// value (kDensityMean for the particle density: its zero mode is dropped by every operator).
 template <typename T>
-pm_status forward_to_y(pm_ctx* c, const void* real, void* spec, int n) {
+pm_status forward_to_y(pm_ctx* c, const void* real, void* spec, int n, double sub = 0.0) {
     Phase ph(c, PM_PHASE_FFT_ZY_FWD);
-    PM_CK(forward_zy<T>((const T*)real, (cplx<T>*)spec, n, 1, c->st));
+    PM_CK(forward_zy<T>((const T*)real, (cplx<T>*)spec, n, 1, c->st, sub));
     return PM_OK;
 }
 
@@ -328,9 +333,9 @@ pm_status compute_forces_t(pm_ctx* c, double a) {
     if (fused_middle(c) || plane_middle(c)) {
         // the forward y pass runs inside the fused or whole-plane middle passes
         Phase ph(c, PM_PHASE_FFT_ZY_FWD);
-        PM_CK(z_r2c<T>((const T*)rho, s0, n, 1, c->st));
+        PM_CK(z_r2c<T>((const T*)rho, s0, n, 1, c->st, kDensityMean));
     } else {
-        PM_TRY(forward_to_y<T>(c, rho, s0, n));
+        PM_TRY(forward_to_y<T>(c, rho, s0, n, kDensityMean));
     }
     // the forward z pass has consumed rho: the fused update deposits the next density there, so
     // it is cleared, by the inverse z pass of the separate passes (beside the force rows it
@@ -491,7 +496,7 @@ pm_status power_t(pm_ctx* c, const void* field, const void* field2, int nbins, c
     if (!f1) PM_TRY(current_density(c, &f1));
     void* s0 = c->at(c->L.spec[0]);
     void* s1 = c->at(c->L.spec[1]);
-    PM_TRY(forward_to_y<T>(c, f1, s0, n));
+    PM_TRY(forward_to_y<T>(c, f1, s0, n, field ? 0.0 : kDensityMean));
     if (field2) PM_TRY(forward_to_y<T>(c, field2, s1, n));
     std::vector<int16_t> tab;
     PM_TRY(upload_bin_table(c, nbins, edges, tab));
@@ -631,7 +636,7 @@ pm_status bispectrum_t(pm_ctx* c, const void* field, int nbins, const double* ed
     // the data: forward transform of the field, masked spectra on the m grid, their inverse
     // transforms, the triple-product sums
     cplx<T>* s0 = (cplx<T>*)c->at(c->L.spec[0]);
-    PM_TRY(forward_to_y<T>(c, f1, s0, n));
+    PM_TRY(forward_to_y<T>(c, f1, s0, n, field ? 0.0 : kDensityMean));
     SpecOp fw;
     fw.kind = OP_FWD_STORE;
     fw.fwd = 1;
@@ -1068,7 +1073,7 @@ pm_status pm_potential(pm_ctx* c, void* phi) {
     op.coef = -1.5 * c->cfg.omega_m / ((double)n * n * n);
     if (c->fp64()) {
         double2* s0 = (double2*)c->at(c->L.spec[0]);
-        PM_TRY(forward_to_y<double>(c, rho, s0, n));
+        PM_TRY(forward_to_y<double>(c, rho, s0, n, kDensityMean));
         PM_CK(x_cols<double>(s0, nullptr, n / 2 + 1, n, op, c->st));
         PM_CK((y_rows<double, true>(s0, (int64_t)(n / 2 + 1) * n, n, c->st)));
         const double2* in[1] = {s0};
@@ -1076,7 +1081,7 @@ pm_status pm_potential(pm_ctx* c, void* phi) {
         PM_CK(z_c2r<double>(in, out, 1, n, 1, 0u, 0.0, c->st));
     } else {
         float2* s0 = (float2*)c->at(c->L.spec[0]);
-        PM_TRY(forward_to_y<float>(c, rho, s0, n));
+        PM_TRY(forward_to_y<float>(c, rho, s0, n, kDensityMean));
         PM_CK(x_cols<float>(s0, nullptr, n / 2 + 1, n, op, c->st));
         PM_CK((y_rows<float, true>(s0, (int64_t)(n / 2 + 1) * n, n, c->st)));
         const float2* in[1] = {s0};
@@ -1786,8 +1791,8 @@ pm_status batch_forces(pm_batch* b, cudaStream_t s, int r0, int c) {
     const bool plane = b->fft_form == 1 && (n == 64 || n == 128);
     // rho, consumed by the forward z pass, receives the update's deposit next: the inverse z pass
     // of the separate passes clears it beside its force rows, else a memset does
-    if (plane) PM_CK(z_r2c<float>(rho, s0, n, c, s));
-    else PM_CK(forward_zy<float>(rho, s0, n, c, s));
+    if (plane) PM_CK(z_r2c<float>(rho, s0, n, c, s, kDensityMean));
+    else PM_CK(forward_zy<float>(rho, s0, n, c, s, kDensityMean));
     if (plane) PM_CK(cudaMemsetAsync(rho, 0, sizeof(float) * c * n3, s));
     SpecOp op;
     op.kind = OP_NEWTON;

@@ -93,8 +93,13 @@ __device__ __forceinline__ size_t spec_row(int gl, int kz) {
 }
 
 // =============================================================== z: r2c
+// sub is subtracted from every input value as it is loaded: the mean of a density mesh (its
+// zero mode, which no operator of the path uses), so that the transform's rounding scales
+// with the fluctuations rather than with the mean (v - 1 is exact in floating point for v
+// in [0, 2^24] up to the rounding of v itself near 1).
 template <typename T, int LOGN>
-__global__ void __launch_bounds__(512, sizeof(T) == 4 ? 4 : 2) k_z_r2c(const T* __restrict__ in, cplx<T>* __restrict__ out) {
+__global__ void __launch_bounds__(512, sizeof(T) == 4 ? 4 : 2) k_z_r2c(const T* __restrict__ in, cplx<T>* __restrict__ out,
+                                                                       T sub) {
     typedef cplx<T> C;
     typedef Shape<T, LOGN> S;
     constexpr int N = S::N, M = S::M, Q = S::QM, YB = S::YB;
@@ -115,7 +120,11 @@ __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 4 : 2) k_z_r2c(const T* 
     const C* row = reinterpret_cast<const C*>(in + (g * N + y0 + b) * N);
     C v[1][8];
 #pragma unroll
-    for (int m = 0; m < 8; ++m) v[0][m] = row[t + m * Q];
+    for (int m = 0; m < 8; ++m) {
+        v[0][m] = row[t + m * Q];
+        v[0][m].x -= sub;
+        v[0][m].y -= sub;
+    }
     __syncthreads();
     RowEx<C, 1, false, LAY> ex{buf, YB, RS, b, 0};
     fft_regs<M, 1, false>(v, t, twM, ex);
@@ -971,12 +980,12 @@ __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) k_x_adj(const cpl
 
 // =============================================================== launchers
 template <typename T, int LOGN>
-cudaError_t z_r2c_n(const T* in, cplx<T>* out, int rows, cudaStream_t st) {
+cudaError_t z_r2c_n(const T* in, cplx<T>* out, int rows, cudaStream_t st, double sub = 0.0) {
     typedef Shape<T, LOGN> S;
     const size_t smem = sizeof(cplx<T>) * (S::M + ((S::M + 2) & ~1) + (size_t)S::YB * RowLayout<S::M, true>::RS);
     cudaError_t e = set_smem((const void*)k_z_r2c<T, LOGN>, smem);
     if (e != cudaSuccess) return e;
-    k_z_r2c<T, LOGN><<<dim3(S::N / S::YB, rows), S::YB * S::QM, smem, st>>>(in, out);
+    k_z_r2c<T, LOGN><<<dim3(S::N / S::YB, rows), S::YB * S::QM, smem, st>>>(in, out, (T)sub);
     return cudaGetLastError();
 }
 
@@ -1016,9 +1025,9 @@ cudaError_t y_grad3_n(const cplx<T>* A, const cplx<T>* B, cplx<T>* Ao, cplx<T>* 
 }
 
 template <typename T, int LOGN>
-cudaError_t forward_zy_n(const T* in, cplx<T>* spec, int batch, cudaStream_t st) {
+cudaError_t forward_zy_n(const T* in, cplx<T>* spec, int batch, cudaStream_t st, double sub) {
     constexpr int N = 1 << LOGN, M = N / 2;
-    cudaError_t e = z_r2c_n<T, LOGN>(in, spec, N * batch, st);
+    cudaError_t e = z_r2c_n<T, LOGN>(in, spec, N * batch, st, sub);
     if (e != cudaSuccess) return e;
     return y_rows_n<T, LOGN, false>(spec, spec, (int64_t)batch * (M + 1) * N, st);
 }
@@ -1165,8 +1174,8 @@ cudaError_t x_cols_kind(cplx<T>* data, cplx<T>* out2, int nplanes, const SpecOp&
     }
 
 template <typename T>
-cudaError_t z_r2c(const T* in, cplx<T>* out, int n, int batch, cudaStream_t st) {
-    PM_DISPATCH_LOGN(n, (z_r2c_n<T, LG>(in, out, n * batch, st)))
+cudaError_t z_r2c(const T* in, cplx<T>* out, int n, int batch, cudaStream_t st, double sub) {
+    PM_DISPATCH_LOGN(n, (z_r2c_n<T, LG>(in, out, n * batch, st, sub)))
 }
 
 template <typename T>
@@ -1228,8 +1237,8 @@ cudaError_t x_adj(const cplx<T>* V, cplx<T>* out, int n, double kf, double coef,
 }
 
 template <typename T>
-cudaError_t forward_zy(const T* in, cplx<T>* spec, int n, int batch, cudaStream_t st) {
-    PM_DISPATCH_LOGN(n, (forward_zy_n<T, LG>(in, spec, batch, st)))
+cudaError_t forward_zy(const T* in, cplx<T>* spec, int n, int batch, cudaStream_t st, double sub) {
+    PM_DISPATCH_LOGN(n, (forward_zy_n<T, LG>(in, spec, batch, st, sub)))
 }
 
 template <typename T>
@@ -1244,7 +1253,7 @@ cudaError_t x_cols(cplx<T>* data, cplx<T>* out2, int nplanes, int n, const SpecO
 }
 
 #define PM_INST(T)                                                                                     \
-    template cudaError_t z_r2c<T>(const T*, cplx<T>*, int, int, cudaStream_t);                         \
+    template cudaError_t z_r2c<T>(const T*, cplx<T>*, int, int, cudaStream_t, double);                 \
     template cudaError_t z_c2r<T>(const cplx<T>* const*, T* const*, int, int, int, unsigned, double,  \
                                   cudaStream_t, const double*);                                        \
     template cudaError_t y_rows<T, false>(cplx<T>*, int64_t, int, cudaStream_t);                      \
@@ -1252,7 +1261,7 @@ cudaError_t x_cols(cplx<T>* data, cplx<T>* out2, int nplanes, int n, const SpecO
     template cudaError_t y_rows_grad3<T>(cplx<T>*, cplx<T>*, cplx<T>*, int64_t, int, double,           \
                                          cudaStream_t, const double*, int64_t);                        \
     template cudaError_t x_cols<T>(cplx<T>*, cplx<T>*, int, int, const SpecOp&, cudaStream_t);      \
-    template cudaError_t forward_zy<T>(const T*, cplx<T>*, int, int, cudaStream_t);                     \
+    template cudaError_t forward_zy<T>(const T*, cplx<T>*, int, int, cudaStream_t, double);             \
     template cudaError_t x_adj<T>(const cplx<T>*, cplx<T>*, int, double, double, cudaStream_t, float*, \
                                   int64_t, const AdjGrOp*, bool);                                       \
     template cudaError_t inverse_yz_grad<T>(cplx<T>*, cplx<T>*, cplx<T>*, T* const*, int, int, double,   \

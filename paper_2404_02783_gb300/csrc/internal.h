@@ -67,9 +67,10 @@ int num_sms();
 cudaError_t div_mode_check(const double* a, const double* d, int64_t count, double* out, cudaStream_t st);
 
 // FFT passes.  n is the transform length (power of two, 16..1024); batch counts
-// independent 3D fields stored back to back.
+// independent 3D fields stored back to back.  The forward passes subtract `sub` from every
+// input value (a density's mean: only the zero mode changes).
 template <typename T>
-cudaError_t z_r2c(const T* in, cplx<T>* out, int n, int batch, cudaStream_t st);
+cudaError_t z_r2c(const T* in, cplx<T>* out, int n, int batch, cudaStream_t st, double sub = 0.0);
 // out_j = c2r(in_j [* -i kf kz when gradz_mask bit j is set]) for the ncomp fields
 template <typename T>
 cudaError_t z_c2r(const cplx<T>* const* in, T* const* out, int ncomp, int n, int batch,
@@ -130,7 +131,7 @@ cudaError_t fft_plane(cplx<T>* A, cplx<T>* GX, cplx<T>* GY, int nplanes, int n, 
 // Forward z (r2c) and y passes of `batch` real meshes into spec ([field][kz][kx][ky]
 // before the x pass).
 template <typename T>
-cudaError_t forward_zy(const T* in, cplx<T>* spec, int n, int batch, cudaStream_t st);
+cudaError_t forward_zy(const T* in, cplx<T>* spec, int n, int batch, cudaStream_t st, double sub = 0.0);
 // The three force meshes from phi and -i kx phi after the inverse x pass (A, B, full
 // layout; both overwritten): out[0] = c2r(IFFT_y(B)), out[1] = c2r(IFFT_y(-i ky A)),
 // out[2] = c2r(-i kz IFFT_y(A)); scratch holds one half spectrum per field.

@@ -7,6 +7,10 @@
   Eq. bispectre), the GPU's FP32 run against the oracle's FP64 run.
 * One step of the timed workload itself (512^3 particles on a 512^3 mesh, L = 5000 Mpc/h):
   the kick of sampled particles against an oracle force evaluation of the same positions.
+* The first two Poisson-gauge steps at the paired runs' size (128^3 particles on a 256^3 mesh,
+  L = 4000 Mpc/h, z = 100; Sec. 2), the second with the lagged constraint, and the first step
+  of the 64-realisation batch (64^3 particles on 128^3 meshes, boxes of 1, 2 and 4 Gpc/h) in the
+  launch shape its autotuner picks: sampled kicks against oracle force evaluations.
 
 Each B(k) triangle is a sum of products delta_1 delta_2 delta_3 over its configurations; its
 error is bounded against the same sum of |delta_1 delta_2 delta_3| (the scale any floating
@@ -19,7 +23,7 @@ import pytest
 import inputs
 from oracle import cic, gravity, ic, pm as opm, stats
 from oracle.cosmology import Cosmology
-from tests.gpu_util import bk_abs_scale, lib, to_dev, to_host, torch
+from tests.gpu_util import bk_abs_scale, lib, ticks_to_host, to_dev, to_host, torch
 
 pytestmark = pytest.mark.gpu
 
@@ -125,3 +129,90 @@ def test_one_step_kick_at_the_timed_size_matches_an_oracle_force_evaluation():
     # the FP32 force chain (deposit, five FFT passes, gather) against FP64: ~1e-6 of the largest kick
     assert np.linalg.norm(pg - want) < 1e-5 * np.linalg.norm(want)
     assert np.max(np.abs(pg - want)) < 1e-5 * np.max(np.abs(want))
+
+
+def _sampled(count, seed):
+    return np.concatenate([[0, count - 1], inputs.rng(seed).integers(0, count, size=62)])
+
+
+def _oracle_kick(ref, a, K, ids):
+    # K g(x) at the sampled particles, g = -grad phi of the oracle's own FP64 force chain (its
+    # potential_k keeps the Poisson-gauge history between calls)
+    phi_k = ref.potential_k(a)
+    g_mesh = gravity.gradient_force(phi_k, ref.n, ref.box)
+    xs = ref.x[:, ids]
+    return K * np.stack([cic.interpolate(g_mesh[j], xs) for j in range(3)])
+
+
+def _assert_kick(got, want):
+    assert np.max(np.abs(want)) > 0
+    assert np.linalg.norm(got - want) < 1e-5 * np.linalg.norm(want)
+    assert np.max(np.abs(got - want)) < 1e-5 * np.max(np.abs(want))
+
+
+@pytest.mark.slow
+def test_poisson_gauge_kicks_at_the_paired_runs_size_match_oracle_force_evaluations():
+    # the paired runs' launch path (128^3 particles on a 256^3 mesh: the tiled R = 2 update; the
+    # Poisson-gauge x pass at 256 with the FP64 island of the workloads): from seeded
+    # lattice-order positions at rest at z = 100, step 1 kicks by K(a_0, a_1/2) g(x_0) from the
+    # first force evaluation (no lag) and step 2 by K(a_1/2, a_3/2) g(x_1), whose constraint
+    # carries Phi' from the first; the oracle evaluates both in FP64 from the GPU's x_0 and x_1
+    pm = lib()
+    npart, n, box, steps, a_i = 128, 256, 4000.0, 100, 1.0 / 101.0
+    count = npart**3
+    x0 = inputs.lattice_order_ticks(71, npart, 1.5, n_mesh=n, tail_fraction=0.01)
+    run = pm.PMRun(pm.make_config(npart, n, box, a_i, 1.0, steps, mode=pm.PM_GR_POISSON, n_lo=pm.DEFAULT_N_LO))
+    pm.pm_set_particles(run.ctx, to_dev(x0), torch.zeros((3, count), dtype=torch.float32, device="cuda"))
+    ids = _sampled(count, 72)
+    idx = torch.from_numpy(ids).cuda()
+    run.step(1)
+    x, p = run.particles()
+    x1 = ticks_to_host(x).copy()
+    p1 = to_host(p[:, idx]).astype(np.float64)
+    run.step(1)
+    p2 = to_host(run.particles()[1][:, idx]).astype(np.float64)
+    del x, p, run
+    torch.cuda.empty_cache()
+
+    c = Cosmology()
+    a = a_i + (1.0 - a_i) * np.arange(3) / steps
+    ah = 0.5 * (a[:-1] + a[1:])
+    ref = opm.PMRun(c, n, box, a_i, 1.0, steps, x0, np.zeros((3, count)), mode=opm.GR_POISSON)
+    _assert_kick(p1, _oracle_kick(ref, a[0], c.kick_factor(a[0], ah[0]), ids))
+    ref.x = x1
+    _assert_kick(p2 - p1, _oracle_kick(ref, a[1], c.kick_factor(ah[0], ah[1]), ids))
+
+
+@pytest.mark.slow
+def test_batched_kicks_at_the_batch_size_match_oracle_force_evaluations():
+    # the batched workload (64 realisations of 64^3 particles on 128^3 meshes, boxes cycling
+    # 1000, 2000, 4000 Mpc/h, Zel'dovich ICs at z = 50, 50 steps) in the launch shape its
+    # autotuner picks, the step replayed from a CUDA graph: the first step kicks every
+    # realisation by K(a_0, a_1/2) g(x_0); the oracle evaluates g in FP64 from the batch's own
+    # x_0 at sampled particles of one realisation of each box
+    pm = lib()
+    B, npart, n, steps = 64, 64, 128, 50
+    count = npart**3
+    boxes = [(1000.0, 2000.0, 4000.0)[r % 3] for r in range(B)]
+    b = pm.PMBatch(pm.make_config(npart, n, 1000.0, A_I, A_F, steps), boxes=boxes)
+    b.autotune()
+    b.ic(list(range(1, B + 1)))
+    ids = _sampled(count, 73)
+    idx = torch.from_numpy(ids).cuda()
+    sample = [0, 31, 62]  # boxes 1000, 2000, 4000
+    before = {}
+    for r in sample:
+        x, p = b.particles(r)
+        before[r] = (ticks_to_host(x).copy(), to_host(p[:, idx]).astype(np.float64))
+    b.step(1, graph=True)
+    after = {r: to_host(b.particles(r)[1][:, idx]).astype(np.float64) for r in sample}
+    del b
+    torch.cuda.empty_cache()
+
+    c = Cosmology()
+    a1 = A_I + (A_F - A_I) / steps
+    K = c.kick_factor(A_I, 0.5 * (A_I + a1))
+    for r in sample:
+        x0, p0 = before[r]
+        ref = opm.PMRun(c, n, boxes[r], A_I, A_F, steps, x0, np.zeros((3, count)))
+        _assert_kick(after[r] - p0, _oracle_kick(ref, A_I, K, ids))

@@ -176,22 +176,24 @@ def test_poisson_gauge_run_matches_oracle(prec):
         xn, _ = out[(0, 0)]
         xi_g = min_image(positions_box_units(xg) - positions_box_units(xn))
         # xi is the difference of two runs, so FP32 rounding in either shows up relative to the
-        # difference: measured 6.2e-3 in FP32 on this 20 Gpc/h box (the same with and without the
-        # FP64 island), roundoff in FP64
-        assert rel_l2(xi_g, xi_o) < (1e-2 if prec == FP32 else 1e-9)
+        # difference: measured 1.0e-3 in FP32 on this 20 Gpc/h box (the same with and without the
+        # FP64 island; 6.2e-3 while the forward transform carried the density's mean), roundoff
+        # in FP64
+        assert rel_l2(xi_g, xi_o) < (3e-3 if prec == FP32 else 1e-9)
         d_g = min_image(positions_box_units(xg) - positions_box_units(x0))
         d_o = min_image(positions_box_units(ref_gr.x) - positions_box_units(x0))
         # FP32 stores rho ~ 1 + delta and resolves delta to ~6e-8; with delta ~ 1e-4 on these
         # 625 Mpc/h cells at z = 100 the FP32 forces, hence displacements, carry ~1e-3 errors
-        # (measured 7.7e-4)
-        assert rel_l2(d_g, d_o) < (2e-3 if prec == FP32 else 1e-11)
+        # (measured 4.2e-4)
+        assert rel_l2(d_g, d_o) < (1e-3 if prec == FP32 else 1e-11)
 
 
 @pytest.mark.slow
 def test_poisson_gauge_pair_at_the_horizon_scale_configuration():
     # the paired runs of the horizon-scale configuration at the same cell size on a 64^3 lattice:
     # 64^3 particles on a 128^3 mesh, L = 4000 Mpc/h, ZA at z = 100, 20 steps to z = 0; xi^GR of
-    # the FP32 runs within 1e-3 of the FP64 oracle's for n_lo = 0, 4 and 16 (measured 2.6e-4 each)
+    # the FP32 runs within 1e-4 of the FP64 oracle's for n_lo = 0, 4 and 16 (measured 1.3e-5
+    # each, displacements 4.9e-6)
     pm = lib()
     np_side, nmesh, box, a_i, steps = 64, 128, 4000.0, 1.0 / 101.0, 20
     c = Cosmology()
@@ -214,9 +216,9 @@ def test_poisson_gauge_pair_at_the_horizon_scale_configuration():
         gr.step(steps)
         xg, _ = _host_particles(gr)
         xi_g = min_image(positions_box_units(xg) - positions_box_units(xn))
-        assert rel_l2(xi_g, xi_o) < 1e-3
+        assert rel_l2(xi_g, xi_o) < 1e-4
         d_g = min_image(positions_box_units(xg) - positions_box_units(x0))
-        assert rel_l2(d_g, d_o) < 1e-4
+        assert rel_l2(d_g, d_o) < 2e-5
 
 
 @pytest.mark.parametrize("prec,np_side,nmesh", [(FP32, 32, 32), (FP32, 32, 64), (FP32, 64, 64), (FP32, 16, 64),
