@@ -31,7 +31,7 @@ def test_gradient_matches_fp64_oracle(np_side, nmesh):
     Lo, go = adjoint.loss_and_grad(c, np_side, nmesh, box, a_i, a_f, steps, w.astype(np.float64),
                                    target.astype(np.float64))
     assert L == pytest.approx(Lo, rel=1e-4)
-    assert rel_l2(to_host(g).astype(np.float64), go) < 1e-3
+    assert rel_l2(to_host(g).astype(np.float64), go) < 1e-4
 
 
 def test_checkpoint_interval_does_not_change_the_gradient():
@@ -117,7 +117,7 @@ def test_any_torch_loss_of_density_and_displacements_matches_fp64_oracle(np_side
     dk = np.fft.fftn(cic.density_contrast(u, nmesh))
     lam_delta = 2.0 * np.real(np.fft.ifftn(Wk * dk)) / nmesh**3
     go = adjoint.vjp(c, np_side, nmesh, box, a_i, a_f, steps, w64, lam_delta=lam_delta, lam_disp=gdisp)
-    assert rel_l2(g, go) < 1e-3
+    assert rel_l2(g, go) < 1e-5
     # the outputs themselves are the oracle's final density and displacements
     assert rel_l2(to_host(delta).astype(np.float64), cic.density_contrast(u, nmesh)) < 1e-4
     assert rel_l2(to_host(disp).astype(np.float64), adjoint.displacement(u, np_side, box)) < 1e-4
@@ -148,7 +148,7 @@ def test_a_loss_of_the_final_momenta_matches_fp64_oracle(np_side, nmesh):
         g = to_host(wv.grad).astype(np.float64)
         go = adjoint.vjp(c, np_side, nmesh, box, a_i, a_f, steps, w64, lam_delta=lam_delta if full else None,
                          lam_disp=gdisp if full else None, lam_mom=h)
-        assert rel_l2(g, go) < 1e-3
+        assert rel_l2(g, go) < 1e-5
         assert rel_l2(to_host(mom).astype(np.float64), p_o) < 1e-4
 
 
@@ -275,7 +275,7 @@ def test_poisson_gauge_gradient_matches_fp64_oracle(box, n_lo, vs_newton):
     # island, the carried spectrum in the transposed x pass) against the oracle's Poisson-gauge
     # vector-Jacobian product for a loss of the final density, displacements and momenta; the
     # Newtonian gradient of the same loss differs by more than vs_newton, so the lag is exercised
-    # (measured: 2.5e-7 - 8e-5 against the oracle, 4% and 55% from the Newtonian gradient)
+    # (measured: 3.1e-7 - 3.3e-7 against the oracle, 4% and 55% from the Newtonian gradient)
     pm = lib()
     nmesh, np_side, a_i, a_f, steps = 32, 16, 0.1, 0.5, 4
     c, w, run = _gr_case(pm, box, n_lo)
@@ -296,7 +296,7 @@ def test_poisson_gauge_gradient_matches_fp64_oracle(box, n_lo, vs_newton):
                      mode=adjoint.GR_POISSON)
     gn = adjoint.vjp(c, np_side, nmesh, box, a_i, a_f, steps, w64, lam_delta=lam_delta, lam_disp=gdisp, lam_mom=h,
                      mode=adjoint.NEWTON)
-    assert rel_l2(g, go) < 1e-3
+    assert rel_l2(g, go) < 1e-5
     assert rel_l2(gn, go) > vs_newton
     assert rel_l2(to_host(mom).astype(np.float64), p_o) < 1e-3
     assert rel_l2(to_host(disp).astype(np.float64), adjoint.displacement(u, np_side, box)) < 1e-3
@@ -319,7 +319,7 @@ def test_poisson_gauge_gradient_across_checkpoint_intervals_and_the_mse():
     Lo, go = adjoint.loss_and_grad(c, 16, 32, 20000.0, 0.1, 0.5, 8, w.astype(np.float64), target.astype(np.float64),
                                    mode=adjoint.GR_POISSON)
     assert L8 == pytest.approx(Lo, rel=1e-3)
-    assert rel_l2(to_host(g8).astype(np.float64), go) < 1e-2
+    assert rel_l2(to_host(g8).astype(np.float64), go) < 2e-4
 
 
 @pytest.mark.parametrize("mode", [0, 1])
@@ -374,7 +374,7 @@ def test_first_order_gradient_matches_fp64_oracle(mode, box, n_lo, a_i, a_f):
                      mode=om, gradient=adjoint.FD1)
     gs = adjoint.vjp(c, np_side, nmesh, box, a_i, a_f, steps, w64, lam_delta=lam_delta, lam_disp=gdisp, lam_mom=h,
                      mode=om, gradient=adjoint.SPECTRAL)
-    assert rel_l2(g, go) < 1e-3
+    assert rel_l2(g, go) < 1e-5
     assert rel_l2(gs, go) > 0.01  # the spectral gradient's chain would not pass
     assert rel_l2(to_host(mom).astype(np.float64), p_o) < 1e-3
     # the same gradient from one segment (no re-runs)

@@ -61,7 +61,9 @@ def test_combined_run_check_case_fp32_matches_fp64_oracle():
     ok = no > 0
     assert np.count_nonzero(ok) > 40
     np.testing.assert_allclose(kg[ok], ko[ok], rtol=1e-12)
-    assert np.max(np.abs(pg[ok] / po[ok] - 1.0)) < 1e-3
+    # the benchmark spec's bar is 1e-3; measured 4.5e-6 (the forward transform subtracts the density's
+    # mean, so its FP32 rounding scales with delta ~ 0.04 rather than with 1 + delta)
+    assert np.max(np.abs(pg[ok] / po[ok] - 1.0)) < 1e-4
 
     np.testing.assert_array_equal(cg, co)
     has = co > 0
@@ -69,14 +71,14 @@ def test_combined_run_check_case_fp32_matches_fp64_oracle():
     assert np.array_equal(np.isnan(bg), ~has)
     err = np.abs(bg[has] - bo[has])
     worst = float(np.max(err / scale[has]))
-    assert worst <= 1e-3, worst
+    assert worst <= 1e-4, worst  # measured 1.1e-6
     # and relative to B itself on the triangles whose sum does not cancel below 1% of its scale
     # (few here: at delta_rms ~ 0.04 per 78 Mpc/h cell the field is nearly Gaussian, so most
     # triangle sums cancel to well under 1% of their terms)
     big = np.abs(bo[has]) > 1e-2 * scale[has]
     assert np.count_nonzero(big) > 0
     rel = float(np.max(err[big] / np.abs(bo[has][big])))
-    assert rel < 1e-3, (rel, worst)
+    assert rel < 2e-4, (rel, worst)  # measured 2.5e-5
 
 
 def _mem_available_gb():

@@ -132,11 +132,12 @@ def test_full_run_power_spectrum(prec):
     ko, po, no = stats.power_spectrum(cic.density_contrast(ref.x, nmesh), box, edges)
     np.testing.assert_array_equal(ng, no)
     ok = no > 0
-    assert np.max(np.abs(pg[ok] / po[ok] - 1)) < (1e-3 if prec == FP32 else 1e-9)
+    # FP32 measured: P(k) 5.9e-6, positions within 3.1e-5 Mpc/h of the FP64 run's
+    assert np.max(np.abs(pg[ok] / po[ok] - 1)) < (1e-4 if prec == FP32 else 1e-9)
     assert np.max(np.abs(kg[ok] / ko[ok] - 1)) < 1e-12
     xg, pgm = _host_particles(run)
     assert np.max(np.abs(min_image(positions_box_units(xg) - positions_box_units(ref.x)))) * box < \
-        (0.05 if prec == FP32 else 1e-8)
+        (1e-3 if prec == FP32 else 1e-8)
     # momentum is conserved by the CIC + symmetric Green's function + odd gradient
     assert np.max(np.abs(pgm.sum(axis=1) - p0.sum(axis=1))) < (1e-4 if prec == FP32 else 1e-9) * np.abs(pgm).sum()
 
