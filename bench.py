@@ -85,11 +85,8 @@ def kernel_bytes(np_side, n, fp64, fused_fft=True):
         kb["fft_x_green"] = 4 * S            # read the z pass's spectrum, write the three y-inverted ones
         kb["fft_yz_inv"] = 3 * S + 3 * R     # the three z c2r
     if fused_update(np_side, n, fp64):
-        if fused_fft and fused_middle(n, fp64):
-            kb["deposit"] = R                # only the zeroing of rho remains in this phase
-        else:
-            kb["deposit"] = 0                # no launch: the inverse z pass clears rho ...
-            kb["fft_yz_inv"] += R            # ... beside the force rows it writes
+        kb["deposit"] = 0                    # no launch: the inverse z pass clears rho ...
+        kb["fft_yz_inv"] += R                # ... beside the force rows it writes
         kb["kick_drift"] += R                # the drifted positions are deposited in the same pass
     return kb
 

@@ -338,14 +338,8 @@ pm_status compute_forces_t(pm_ctx* c, double a) {
         PM_TRY(forward_to_y<T>(c, rho, s0, n, kDensityMean));
     }
     // the forward z pass has consumed rho: the fused update deposits the next density there, so
-    // it is cleared, by the inverse z pass of the separate passes (beside the force rows it
-    // writes) or else here
-    const bool clear_in_z = fused_update(c) && !fused_middle(c) && !plane_middle(c) &&
-                            c->cfg.gradient == PM_GRAD_SPECTRAL;
-    if (fused_update(c) && !clear_in_z) {
-        Phase ph(c, PM_PHASE_DEPOSIT);
-        PM_CK(cudaMemsetAsync(rho, 0, sizeof(T) * (size_t)n * n * n, c->st));
-    }
+    // the inverse z pass clears it beside the force rows it writes (every form of the passes)
+    T* clear = fused_update(c) ? (T*)rho : nullptr;
     c->rho_valid = false;
     SpecOp op;
     op.kf = c->kf;
@@ -377,7 +371,7 @@ pm_status compute_forces_t(pm_ctx* c, double a) {
         PM_CK((y_rows<T, true>(s0, (int64_t)(n / 2 + 1) * n, n, c->st)));
         const cplx<T>* in[1] = {s0};
         T* out[1] = {(T*)c->force(0)};
-        PM_CK(z_c2r<T>(in, out, 1, n, 1, 0u, 0.0, c->st));
+        PM_CK(z_c2r<T>(in, out, 1, n, 1, 0u, 0.0, c->st, nullptr, clear));
     } else if (plane_middle(c)) {
         {
             Phase ph(c, PM_PHASE_FFT_X_GREEN);
@@ -386,7 +380,7 @@ pm_status compute_forces_t(pm_ctx* c, double a) {
         Phase ph(c, PM_PHASE_FFT_YZ_INV);
         const cplx<T>* in[3] = {s1, s2, s0};  // -i k_j phi back along x and y, j = x, y, z
         T* out[3] = {(T*)c->force(0), (T*)c->force(1), (T*)c->force(2)};
-        PM_CK(z_c2r<T>(in, out, 3, n, 1, 0u, c->kf, c->st));
+        PM_CK(z_c2r<T>(in, out, 3, n, 1, 0u, c->kf, c->st, nullptr, clear));
     } else if (fused_middle(c)) {
         // z r2c above left the half spectrum in s0 before its forward y pass (see forward_to_y)
         {
@@ -396,7 +390,7 @@ pm_status compute_forces_t(pm_ctx* c, double a) {
         Phase ph(c, PM_PHASE_FFT_YZ_INV);
         const cplx<T>* in[3] = {s1, s2, s0};  // IFFT_y(-i kx phi), IFFT_y(-i ky phi), IFFT_y(phi) (-i kz)
         T* out[3] = {(T*)c->force(0), (T*)c->force(1), (T*)c->force(2)};
-        PM_CK(z_c2r<T>(in, out, 3, n, 1, 4u, c->kf, c->st));
+        PM_CK(z_c2r<T>(in, out, 3, n, 1, 4u, c->kf, c->st, nullptr, clear));
     } else {
         {
             Phase ph(c, PM_PHASE_FFT_X_GREEN);
@@ -404,7 +398,7 @@ pm_status compute_forces_t(pm_ctx* c, double a) {
         }
         Phase ph(c, PM_PHASE_FFT_YZ_INV);
         T* out[3] = {(T*)c->force(0), (T*)c->force(1), (T*)c->force(2)};
-        PM_CK(inverse_yz_grad<T>(s0, s1, s2, out, n, 1, c->kf, c->st, nullptr, clear_in_z ? (T*)rho : nullptr));
+        PM_CK(inverse_yz_grad<T>(s0, s1, s2, out, n, 1, c->kf, c->st, nullptr, clear));
     }
     if (c->cfg.mode == PM_GR_POISSON) {
         c->have_phi = true;
@@ -623,12 +617,17 @@ pm_status bispectrum_t(pm_ctx* c, const void* field, int nbins, const double* ed
     if (!f1) PM_TRY(current_density(c, &f1));
     std::vector<int16_t> tab;
     PM_TRY(upload_bin_table(c, nbins, edges, tab));
-    // units of up to eight triangles sharing (i, j) (see bk_units); never more units than triangles
+    // units (i, j-block of 4, l-block of 8) with at least one triangle i <= j <= l (see bk_units):
+    // every block from the one holding j = i on, and l-blocks from the one holding its first j;
+    // never more units than triangles
     std::vector<int4> units;
     units.reserve(B.ntri);
-    for (int i = 0, t = 0; i < nbins; ++i)
-        for (int j = i; j < nbins; t += nbins - j, ++j)
-            for (int lb = j / 8; 8 * lb < nbins; ++lb) units.push_back(make_int4(i, j, lb, t + std::max(j, 8 * lb) - j));
+    for (int i = 0, t = 0; i < nbins; ++i) {
+        const int Ti = t;  // index of triangle (i, i, i)
+        for (int j = i; j < nbins; ++j) t += nbins - j;
+        for (int jb = i / 4; 4 * jb < nbins; ++jb)
+            for (int lb = jb / 2; 8 * lb < nbins; ++lb) units.push_back(make_int4(i, jb, lb, Ti));
+    }
     int4* dunits = (int4*)(scratch + B.tri);
     PM_CK(cudaMemcpyAsync(dunits, units.data(), sizeof(int4) * units.size(), cudaMemcpyHostToDevice, c->st));
     const std::vector<double>* counts = nullptr;
@@ -1790,10 +1789,9 @@ pm_status batch_forces(pm_batch* b, cudaStream_t s, int r0, int c) {
     const double* kf = (const double*)b->at(b->KF) + r0;
     const bool plane = b->fft_form == 1 && (n == 64 || n == 128);
     // rho, consumed by the forward z pass, receives the update's deposit next: the inverse z pass
-    // of the separate passes clears it beside its force rows, else a memset does
+    // clears it beside its force rows
     if (plane) PM_CK(z_r2c<float>(rho, s0, n, c, s, kDensityMean));
     else PM_CK(forward_zy<float>(rho, s0, n, c, s, kDensityMean));
-    if (plane) PM_CK(cudaMemsetAsync(rho, 0, sizeof(float) * c * n3, s));
     SpecOp op;
     op.kind = OP_NEWTON;
     op.fwd = 1;
@@ -1820,7 +1818,7 @@ pm_status batch_forces(pm_batch* b, cudaStream_t s, int r0, int c) {
         // whole kz planes in shared memory: the three gradient spectra, then the z pass
         PM_CK(fft_plane<float>(s0, s1, s2, c * (M + 1), n, op, s));
         const float2* in[3] = {s1, s2, s0};
-        PM_CK(z_c2r<float>(in, out, 3, n, c, 0u, 0.0, s));
+        PM_CK(z_c2r<float>(in, out, 3, n, c, 0u, 0.0, s, nullptr, rho));
         return PM_OK;
     }
     PM_CK(x_cols<float>(s0, s1, c * (M + 1), n, op, s));

@@ -1180,12 +1180,13 @@ cudaError_t z_r2c(const T* in, cplx<T>* out, int n, int batch, cudaStream_t st, 
 
 template <typename T>
 cudaError_t z_c2r(const cplx<T>* const* in, T* const* out, int ncomp, int n, int batch, unsigned gradz_mask,
-                  double kf, cudaStream_t st, const double* kf_arr) {
+                  double kf, cudaStream_t st, const double* kf_arr, T* zero) {
     Ptr3<T> P;
     for (int j = 0; j < 3; ++j) {
         P.in[j] = in[j < ncomp ? j : 0];
         P.out[j] = out[j < ncomp ? j : 0];
     }
+    P.zero = zero;
     PM_DISPATCH_LOGN(n, (z_c2r_n<T, LG>(P, ncomp, n * batch, gradz_mask, kf, st, kf_arr)))
 }
 
@@ -1255,7 +1256,7 @@ cudaError_t x_cols(cplx<T>* data, cplx<T>* out2, int nplanes, int n, const SpecO
 #define PM_INST(T)                                                                                     \
     template cudaError_t z_r2c<T>(const T*, cplx<T>*, int, int, cudaStream_t, double);                 \
     template cudaError_t z_c2r<T>(const cplx<T>* const*, T* const*, int, int, int, unsigned, double,  \
-                                  cudaStream_t, const double*);                                        \
+                                  cudaStream_t, const double*, T*);                                    \
     template cudaError_t y_rows<T, false>(cplx<T>*, int64_t, int, cudaStream_t);                      \
     template cudaError_t y_rows<T, true>(cplx<T>*, int64_t, int, cudaStream_t);                       \
     template cudaError_t y_rows_grad3<T>(cplx<T>*, cplx<T>*, cplx<T>*, int64_t, int, double,           \

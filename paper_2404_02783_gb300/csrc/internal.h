@@ -71,10 +71,12 @@ cudaError_t div_mode_check(const double* a, const double* d, int64_t count, doub
 // input value (a density's mean: only the zero mode changes).
 template <typename T>
 cudaError_t z_r2c(const T* in, cplx<T>* out, int n, int batch, cudaStream_t st, double sub = 0.0);
-// out_j = c2r(in_j [* -i kf kz when gradz_mask bit j is set]) for the ncomp fields
+// out_j = c2r(in_j [* -i kf kz when gradz_mask bit j is set]) for the ncomp fields; zero (if
+// given, a mesh of the outputs' shape that the caller has finished with) is cleared beside them
 template <typename T>
 cudaError_t z_c2r(const cplx<T>* const* in, T* const* out, int ncomp, int n, int batch,
-                  unsigned gradz_mask, double kf, cudaStream_t st, const double* kf_arr = nullptr);
+                  unsigned gradz_mask, double kf, cudaStream_t st, const double* kf_arr = nullptr,
+                  T* zero = nullptr);
 template <typename T, bool INV>
 cudaError_t y_rows(cplx<T>* data, int64_t nrows, int n, cudaStream_t st);
 // A <- IFFT_y(A), B <- IFFT_y(B), C <- IFFT_y(-i ky A); kf_arr (optional) gives the kf of

@@ -105,18 +105,21 @@ cudaError_t bk_indicators(int n, double2* out, int m, int nbins, const int16_t* 
     return cudaGetLastError();
 }
 
-// Blocked form of the triangle sums: a unit is (i, j, l-block of 8) and covers the triangles
-// (i, j, l) with l in [max(j, 8 lb), min(nbins, 8 lb + 8)); per point it forms I_i I_j once and
-// multiplies it into the eight I_l (read as aligned vectors), so shared-memory traffic per
-// triangle is a fraction of one scalar load.  Rows of a staged point hold the nbins fields at
-// [0, nbp), nbp = nbins rounded up to 8 (zero padded).
-// unit = (i, j, lb, index of triangle (i, j, max(j, 8 lb)) in the i <= j <= l order).
+// Register-tiled triangle sums: a unit is (i, j-block of 4, l-block of 8) and covers the
+// triangles (i, j, l) with i <= j <= l among j in [4 jb, 4 jb + 4) and l in [8 lb, 8 lb + 8).
+// Per staged point a thread reads I_i, the four I_j and the eight I_l (aligned vectors), forms
+// the four products I_i I_j and multiplies them into the eight I_l: 36 arithmetic operations for
+// 1 + 4 / W + 8 / W shared-memory loads, so the loads no longer bound the sums.  Partial sums
+// run over a chunk of points in T and across chunks in FP64.  Rows of a staged point hold the
+// nbins fields at [0, nbp), nbp = nbins rounded up to 8 (zero padded), so the blocks never read
+// past a row.
+// unit = (i, jb, lb, index of triangle (i, i, i) in the i <= j <= l order).
 template <typename T> struct Vec4;
 template <> struct Vec4<float> { typedef float4 type; static constexpr int W = 4; };
 template <> struct Vec4<double> { typedef double2 type; static constexpr int W = 2; };
 
 template <typename T>
-__global__ void __launch_bounds__(256, 4) k_bk_units(const T* __restrict__ f, int64_t m3, int nbins, int nbp, int npts,
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_bk_units(const T* __restrict__ f, int64_t m3, int nbins, int nbp, int npts,
                                                   const int4* __restrict__ unit, int nunit, double* __restrict__ acc) {
     typedef typename Vec4<T>::type V;
     constexpr int W = Vec4<T>::W;
@@ -126,11 +129,12 @@ __global__ void __launch_bounds__(256, 4) k_bk_units(const T* __restrict__ f, in
     const int tid = threadIdx.x, nthr = blockDim.x;
     const int u = blockIdx.y * nthr + tid;
     const int4 my = (u < nunit) ? unit[u] : make_int4(0, 0, 0, -1);
-    const int i = my.x, j = my.y, l0 = 8 * my.z;
-    double sS[8];
+    const int i = my.x, j0 = 4 * my.y, l0 = 8 * my.z;
+    double sS[4][8];
 #pragma unroll
-    for (int q = 0; q < 8; ++q) sS[q] = 0.0;
-    // npts points per chunk: partial sums over a chunk in T, FP64 across chunks
+    for (int d = 0; d < 4; ++d)
+#pragma unroll
+        for (int q = 0; q < 8; ++q) sS[d][q] = 0.0;
     for (int64_t c0 = (int64_t)blockIdx.x * npts; c0 < m3; c0 += (int64_t)gridDim.x * npts) {
         __syncthreads();
         for (int e = tid; e < npts * stride; e += nthr) {
@@ -139,46 +143,68 @@ __global__ void __launch_bounds__(256, 4) k_bk_units(const T* __restrict__ f, in
         }
         __syncthreads();
         if (my.w < 0) continue;
-        T ps[8];
+        T ps[4][8];
 #pragma unroll
-        for (int q = 0; q < 8; ++q) ps[q] = T(0);
-#pragma unroll 4
+        for (int d = 0; d < 4; ++d)
+#pragma unroll
+            for (int q = 0; q < 8; ++q) ps[d][q] = T(0);
+#pragma unroll 2
         for (int pnt = 0; pnt < npts; ++pnt) {
             const T* row = s + pnt * stride;
-            const T a = row[i] * row[j];
-            const V* dl = reinterpret_cast<const V*>(row + l0);
+            const T fi = row[i];
+            T a[4], dl[8];
+#pragma unroll
+            for (int h = 0; h < 4 / W; ++h) {
+                const V v = reinterpret_cast<const V*>(row + j0)[h];
+                const T* vv = reinterpret_cast<const T*>(&v);
+#pragma unroll
+                for (int w = 0; w < W; ++w) a[h * W + w] = fi * vv[w];
+            }
 #pragma unroll
             for (int h = 0; h < 8 / W; ++h) {
-                const V d = dl[h];
-                const T* dv = reinterpret_cast<const T*>(&d);
+                const V v = reinterpret_cast<const V*>(row + l0)[h];
+                const T* vv = reinterpret_cast<const T*>(&v);
 #pragma unroll
-                for (int w = 0; w < W; ++w) ps[h * W + w] += a * dv[w];
+                for (int w = 0; w < W; ++w) dl[h * W + w] = vv[w];
             }
+#pragma unroll
+            for (int d = 0; d < 4; ++d)
+#pragma unroll
+                for (int q = 0; q < 8; ++q) ps[d][q] += a[d] * dl[q];
         }
 #pragma unroll
-        for (int q = 0; q < 8; ++q) sS[q] += (double)ps[q];
+        for (int d = 0; d < 4; ++d)
+#pragma unroll
+            for (int q = 0; q < 8; ++q) sS[d][q] += (double)ps[d][q];
     }
     if (my.w < 0) return;
-    const int lstart = max(j, l0), lend = min(nbins, l0 + 8);
 #pragma unroll
-    for (int q = 0; q < 8; ++q) {
-        const int l = l0 + q;
-        if (l < lstart || l >= lend) continue;
-        atomicAdd(&acc[my.w + (l - lstart)], sS[q]);
+    for (int d = 0; d < 4; ++d) {
+        const int j = j0 + d;
+        if (j < i || j >= nbins) continue;
+        // triangles (i, j', l) for i <= j' < j come first, nbins - j' of them for each j'
+        const int tij = my.w + (j - i) * nbins - ((j - i) * (i + j - 1)) / 2;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const int l = l0 + q;
+            if (l < j || l >= nbins) continue;
+            atomicAdd(&acc[tij + (l - j)], sS[d][q]);
+        }
     }
 }
 
 template <typename T>
 cudaError_t bk_units(const T* fields, int m, int nbins, const int4* unit, int nunit, double* acc, cudaStream_t st) {
-    const int nthr = 256;
+    // one thread per unit, at most 256 a CTA, whole warps
+    const int nthr = nunit >= 256 ? 256 : ((nunit + 31) & ~31);
     const int nbp = (nbins + 7) & ~7;
     const int64_t m3 = (int64_t)m * m * m;
-    // points per chunk: up to 256, the staged rows within 96 KB of shared memory
-    int npts = (int)((96 * 1024) / (sizeof(T) * nbp));
+    // points per chunk: up to 256, the staged rows within 48 KB of shared memory
+    int npts = (int)((48 * 1024) / (sizeof(T) * nbp));
     npts = npts > 256 ? 256 : (npts < 32 ? 32 : npts & ~31);
     const int gy = (nunit + nthr - 1) / nthr;
     int64_t gx = (m3 + npts - 1) / npts;
-    const int64_t cap = (152 * 8 + gy - 1) / gy;  // about eight CTAs per SM in all
+    const int64_t cap = (152 * 16 + gy - 1) / gy;  // about sixteen CTAs per SM in all
     if (gx > cap) gx = cap;
     const size_t smem = sizeof(T) * (size_t)npts * nbp;
     if (smem > 48 * 1024) {
