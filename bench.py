@@ -638,7 +638,17 @@ def estimators(pm, torch, args):
     gr.step(gsteps)
     e1.record(st)
     e1.synchronize()
-    out["gr_poisson_step"] = {"ms_per_step": round(e0.elapsed_time(e1) / gsteps, 4), "steps": gsteps,
+    ms_gr = e0.elapsed_time(e1) / gsteps
+    gr.ic(seed=3)
+    gr.step(gwarm)
+    pm.pm_profile(gr.ctx, True)
+    pm.pm_timings(gr.ctx)
+    gr.step(gsteps)
+    ph_gr = pm.pm_timings(gr.ctx)
+    pm.pm_profile(gr.ctx, False)
+    out["gr_poisson_step"] = {"ms_per_step": round(ms_gr, 4), "steps": gsteps,
+                              "phases_ms_per_launch": {k: round(v[0] / max(v[1], 1), 4) for k, v in ph_gr.items()
+                                                       if v[1]},
                               "what": f"{np_side}^3 particles, {n}^3 mesh, Poisson-gauge Green's function "
                                       "with Phi_old and the FP64 island |n| <= 4, otherwise as the headline"}
     del gr

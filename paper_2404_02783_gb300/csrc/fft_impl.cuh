@@ -330,6 +330,8 @@ __device__ __forceinline__ void cp_async16(void* smem_dst, const void* gmem_src)
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(gmem_src) : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+// A hint that brings the 128-byte line holding p into L2 (no register, no wait).
+__device__ __forceinline__ void prefetch_l2(const void* p) { asm volatile("prefetch.global.L2 [%0];\n" ::"l"(p)); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
 // Persistent: each CTA walks blocks blk = blockIdx.x, + gridDim.x, ... of CB columns of one
@@ -448,6 +450,19 @@ __global__ void __launch_bounds__(XShape<T, LOGN, KIND>::THREADS, XShape<T, LOGN
     double* acc2_row = (KIND == OP_BIN && cross && op.acc2) ? op.acc2 + (size_t)blockIdx.x * op.nbins : nullptr;
     auto issue = [&](int64_t blk) {
         const size_t pb = (size_t)(blk / NCG) * N * N + (size_t)(blk % NCG) * CB;
+        if constexpr (KIND == OP_GR) {
+            // the Poisson-gauge constraint reads this block's Phi_old after the forward
+            // transform: its lines are brought into L2 now, one block ahead, with the data
+            constexpr int LINES = CB * (int)sizeof(C) >= 128 ? CB * (int)sizeof(C) / 128 : 1;
+            constexpr int THREADS = XShape<T, LOGN, KIND>::THREADS;  // the launch's block size
+            const C* ph = reinterpret_cast<const C*>(op.phi_old) + pb;
+#pragma unroll
+            for (int q0 = 0; q0 < N * LINES; q0 += THREADS) {
+                const int q = q0 + tid;
+                if (q < N * LINES)
+                    prefetch_l2(reinterpret_cast<const char*>(ph + (size_t)(q / LINES) * N) + 128 * (q % LINES));
+            }
+        }
         for (int q = tid; q < N * CHUNKS_ROW; q += blockDim.x) {
             const int r = q / CHUNKS_ROW, h = q % CHUNKS_ROW;
             cp_async16(reinterpret_cast<char*>(stage + (size_t)r * CB) + 16 * h,
