@@ -539,6 +539,20 @@ __global__ void __launch_bounds__(XShape<T, LOGN, KIND>::THREADS, XShape<T, LOGN
         int run_bin = -1;
         T run_sum = T(0), run_sum2 = T(0);
         const T wyz = (KIND == OP_BIN) ? iw2[ny < 0 ? -ny : ny] * iw2[nz] * T((nz == 0 || nz == M) ? 1 : 2) : T(1);
+        // OP_BIN: the thread's modes kx = 8 t .. 8 t + 7 lie on one side of the Nyquist index, so
+        // |n|^2 is monotone over them, and a bin is a contiguous range of |n|^2: when the first
+        // and the last mode fall in the same bin (neither the zero mode nor beyond (n/2)^2), so
+        // do all eight, and two table lookups replace eight
+        int bin_all = -1;
+        if constexpr (KIND == OP_BIN) {
+            const int ia = 8 * t, ib = 8 * t + 7;
+            const int nxa = (ia < M) ? ia : ia - N, nxb = (ib < M) ? ib : ib - N;
+            const int n2a = nxa * nxa + ny * ny + nz * nz, n2b = nxb * nxb + ny * ny + nz * nz;
+            if (n2a > 0 && n2b > 0 && n2a <= M * M && n2b <= M * M) {
+                const int ba = op.bin_of[n2a], bb = op.bin_of[n2b];
+                if (ba == bb) bin_all = ba;
+            }
+        }
     #pragma unroll
         for (int m = 0; m < 8; ++m) {
             const int i = (KIND == OP_BIN) ? 8 * t + m : t + m * Q;
@@ -547,7 +561,7 @@ __global__ void __launch_bounds__(XShape<T, LOGN, KIND>::THREADS, XShape<T, LOGN
             const C vv = v[0][m];
             if constexpr (KIND == OP_BIN) {
                 if (n2 == 0 || n2 > M * M) continue;
-                const int bin = op.bin_of[n2];
+                const int bin = (bin_all >= 0) ? bin_all : op.bin_of[n2];
                 if (bin < 0) continue;
                 const C u = cross ? v[1][m] : vv;
                 // w |delta_n|^2 / W^2 (or the cross product), w = 1 on the kz = 0, n/2 planes, 2 elsewhere
