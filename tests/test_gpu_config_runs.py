@@ -5,8 +5,9 @@
   64 log bins on [k_f, k_Ny] and B(k) for every triangle of the 24 linear bins of width
   0.05/24 h/Mpc that lie below the 64^3 Nyquist frequency (Sec. 4.1 Eq. powerspectrum, Sec. 4.2
   Eq. bispectre), the GPU's FP32 run against the oracle's FP64 run.
-* One step of the timed workload itself (512^3 particles on a 512^3 mesh, L = 5000 Mpc/h):
-  the kick of sampled particles against an oracle force evaluation of the same positions.
+* One step of the timed workload itself (512^3 particles on a 512^3 mesh, L = 5000 Mpc/h), in FP32
+  and on the FP64 plain path: the kick of sampled particles against an oracle force evaluation of
+  the same positions.
 * The first two Poisson-gauge steps at the paired runs' size (128^3 particles on a 256^3 mesh,
   L = 4000 Mpc/h, z = 100; Sec. 2), the second with the lagged constraint, and the first step
   of the 64-realisation batch (64^3 particles on 128^3 meshes, boxes of 1, 2 and 4 Gpc/h) in the
@@ -94,19 +95,23 @@ def _mem_available_gb():
 
 
 @pytest.mark.slow
-def test_one_step_kick_at_the_timed_size_matches_an_oracle_force_evaluation():
-    # the timed workload's launch path (512^3 particles on 512^3 cells, FP32, row-sweep update):
-    # from seeded lattice-order positions at rest, one step kicks each particle by
-    # K(a_0, a_1/2) g(x_0); the oracle evaluates g = -grad phi by its own FP64 deposit, FFT,
-    # Green's function, gradient and CIC gather at 64 sampled particles
+@pytest.mark.parametrize("fp64", [False, True])
+def test_one_step_kick_at_the_timed_size_matches_an_oracle_force_evaluation(fp64):
+    # the timed workload's launch path (512^3 particles on 512^3 cells: FP32 ticks and the row-sweep
+    # update, or the FP64 plain path the metric sets beside it): from seeded lattice-order positions
+    # at rest, one step kicks each particle by K(a_0, a_1/2) g(x_0); the oracle evaluates
+    # g = -grad phi by its own FP64 deposit, FFT, Green's function, gradient and CIC gather at 64
+    # sampled particles
     if _mem_available_gb() < 64:
         pytest.skip("the FP64 oracle force of a 512^3 mesh needs about 30 GB of host memory")
     pm = lib()
     n, box, steps = 512, 5000.0, 100
-    x = inputs.lattice_order_ticks(61, n, 1.5, tail_fraction=0.01)
-    run = pm.PMRun(pm.make_config(n, n, box, A_I, A_F, steps))
+    ticks = inputs.lattice_order_ticks(61, n, 1.5, tail_fraction=0.01)
+    x = inputs.ticks_to_fractions(ticks) if fp64 else ticks
+    prec = pm.PM_FP64 if fp64 else pm.PM_FP32_FIXED
+    run = pm.PMRun(pm.make_config(n, n, box, A_I, A_F, steps, precision=prec))
     xd = to_dev(x)
-    pd = torch.zeros((3, n**3), dtype=torch.float32, device="cuda")
+    pd = torch.zeros((3, n**3), dtype=torch.float64 if fp64 else torch.float32, device="cuda")
     pm.pm_set_particles(run.ctx, xd, pd)
     run.step(1)
     _, p = run.particles()
@@ -128,9 +133,11 @@ def test_one_step_kick_at_the_timed_size_matches_an_oracle_force_evaluation():
     del g_mesh
     want = K * g
     assert np.max(np.abs(want)) > 0
-    # the FP32 force chain (deposit, five FFT passes, gather) against FP64: ~1e-6 of the largest kick
-    assert np.linalg.norm(pg - want) < 1e-5 * np.linalg.norm(want)
-    assert np.max(np.abs(pg - want)) < 1e-5 * np.max(np.abs(want))
+    # the FP32 force chain (deposit, five FFT passes, gather) against FP64: ~1e-6 of the largest
+    # kick; the FP64 chain: rounding of the FFTs and the per-mode divide
+    tol = 1e-10 if fp64 else 1e-5
+    assert np.linalg.norm(pg - want) < tol * np.linalg.norm(want)
+    assert np.max(np.abs(pg - want)) < tol * np.max(np.abs(want))
 
 
 def _sampled(count, seed):
