@@ -62,7 +62,7 @@ def test_combined_run_check_case_fp32_matches_fp64_oracle():
     ok = no > 0
     assert np.count_nonzero(ok) > 40
     np.testing.assert_allclose(kg[ok], ko[ok], rtol=1e-12)
-    # the benchmark spec's bar is 1e-3; measured 4.5e-6 (the forward transform subtracts the density's
+    # the required bar after a full run is 1e-3; measured 4.5e-6 (the forward transform subtracts the density's
     # mean, so its FP32 rounding scales with delta ~ 0.04 rather than with 1 + delta)
     assert np.max(np.abs(pg[ok] / po[ok] - 1.0)) < 1e-4
 
