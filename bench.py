@@ -372,6 +372,7 @@ def e2e(pm, torch, args, rank, world, n_jobs=2, form=0):
 def batched(pm, torch, args):
     """64 realisations x 64^3 particles on 128^3 meshes, boxes cycling {1000, 2000, 4000} Mpc/h,
     FP32: one graph-replayed batched run against the same realisations stepped one by one."""
+    import numpy as np
     B, np_side, n, grid_steps = args.batch, 64, 128, 50
     k = min(args.steps, grid_steps - 2)
     boxes = [(1000.0, 2000.0, 4000.0)[r % 3] for r in range(B)]
@@ -393,6 +394,23 @@ def batched(pm, torch, args):
     e1.record(st)
     e1.synchronize()
     t_batch = e0.elapsed_time(e1) * 1e-3
+    # the ensemble's purpose: the halo-proxy b1 of every realisation (top 5% of cells, 16 log bins,
+    # k < 0.05 h/Mpc) and its spread across the realisations of each box, after the timed steps
+    edges_b = pm.log_edges(16, 1.0, n / 2.0)
+    b.bias(edges_b, k_max=0.05)  # bin tables and mode counts of each box's geometry, untimed
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    b1 = b.bias(edges_b, k_max=0.05)[:, 0]
+    ms_bias = 1e3 * (time.perf_counter() - t0)
+    a_now = b.state()[1]
+    by_box = {}
+    for box in sorted(set(boxes)):
+        v = np.array([b1[r] for r in range(B) if boxes[r] == box])
+        by_box[f"{box:g}"] = {"n": int(v.size), "b1_mean": round(float(v.mean()), 4),
+                              "b1_std": round(float(v.std(ddof=1)), 4) if v.size > 1 else None}
+    bias = {"what": f"halo-proxy b1 (top 5% of cells, 16 log bins, k < 0.05 h/Mpc) of all {B} realisations "
+                    f"at a = {a_now:.3f} (pm_batch_bias: proxy selection, cross and auto spectra, host fit)",
+            "ms_all_realisations": round(ms_bias, 3), "by_box_mpc_h": by_box}
     del b
     torch.cuda.empty_cache()
     runs = {box: pm.PMRun(pm.make_config(np_side, n, box, A_INIT, A_FINAL, grid_steps)) for box in set(boxes)}
@@ -414,7 +432,7 @@ def batched(pm, torch, args):
                         "{1000, 2000, 4000} Mpc/h, FP32, one CUDA graph launch for all steps",
             "value": units / t_batch, "unit": UNIT, "ms_per_step": 1e3 * t_batch / k,
             "sequential_value": units / t_seq, "sequential_ms_per_step": 1e3 * t_seq / k,
-            "speedup_vs_sequential": t_seq / t_batch, "steps": k,
+            "speedup_vs_sequential": t_seq / t_batch, "steps": k, "bias": bias,
             "autotune": {"chunk": chunk, "fft_form": fft_form, "ms_per_step_at_tuning": round(tune_ms, 4),
                          "candidates": "middle FFT passes as separate launches (0) or on whole kz planes in "
                                        "shared memory (1), each with realisations per launch B, B/2, ..., 1"}}
