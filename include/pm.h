@@ -151,10 +151,11 @@ pm_status pm_step(pm_ctx* ctx, int n_steps);
 pm_status pm_particles(pm_ctx* ctx, void** x, void** p);
 
 /* Copy particles in (device-to-device, caller layout = context layout) and reset
- * the step counter to 0 with synchronised momenta at a_init.  FP64 positions must be
- * finite box fractions in [0, 1): otherwise PM_ERR_BOUNDS and nothing is copied (the
- * check runs on the device and synchronises the context stream; uint32 ticks are valid
- * by construction and are not checked). */
+ * the step counter to 0 with synchronised momenta at a_init.  x or p may be the context's
+ * own array (pm_particles), written by the caller beforehand: that array is not copied.
+ * FP64 positions must be finite box fractions in [0, 1): otherwise PM_ERR_BOUNDS and
+ * nothing is copied (the check runs on the device and synchronises the context stream;
+ * uint32 ticks are valid by construction and are not checked). */
 pm_status pm_set_particles(pm_ctx* ctx, const void* x, const void* p);
 
 /* Resume a run at a point of its a-grid (checkpoint / restart; the paper's runs write

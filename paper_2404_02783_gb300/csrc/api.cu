@@ -788,8 +788,9 @@ pm_status copy_state(pm_ctx* c, const void* x, const void* p, int step, bool syn
     PM_TRY(check_positions(c, x));
     if (c->adj) c->adj->recorded = false;
     const size_t bytes = 3 * (size_t)c->np3 * c->sT();
-    PM_CK(cudaMemcpyAsync(c->at(c->L.x), x, bytes, cudaMemcpyDeviceToDevice, c->st));
-    PM_CK(cudaMemcpyAsync(c->at(c->L.p), p, bytes, cudaMemcpyDeviceToDevice, c->st));
+    // the context's own arrays (pm_particles), already written by the caller, are not copied
+    if (x != c->at(c->L.x)) PM_CK(cudaMemcpyAsync(c->at(c->L.x), x, bytes, cudaMemcpyDeviceToDevice, c->st));
+    if (p != c->at(c->L.p)) PM_CK(cudaMemcpyAsync(c->at(c->L.p), p, bytes, cudaMemcpyDeviceToDevice, c->st));
     c->step = step;
     c->synced = synced;
     c->have_phi = false;

@@ -273,21 +273,31 @@ def test_first_order_gradient_is_refused_by_batches_and_the_fp64_gradient():
     assert e.value.status == 6
 
 
-def test_set_state_resumes_a_run_where_it_was_saved():
+@pytest.mark.parametrize("in_place", [False, True])
+def test_set_state_resumes_a_run_where_it_was_saved(in_place):
     # a snapshot (x, p, step, synchronised) taken between steps and restored into a fresh
     # context continues as the original run: the same integrator position and the same
-    # particles after the remaining steps (up to the summation order of the deposit atomics)
+    # particles after the remaining steps (up to the summation order of the deposit atomics);
+    # in_place: the snapshot is written into the context's own arrays (pm_particles) and
+    # pm_set_state, handed those arrays, copies nothing
     pm = lib()
     np_side = nmesh = 64
     box, steps, k = 1000.0, 40, 25
     runs = [pm.PMRun(pm.make_config(np_side, nmesh, box, 1.0 / 51.0, 1.0, steps)) for _ in range(2)]
     a, b = runs
+    b.ic(seed=10)  # other particles, overwritten by the snapshot
     a.ic(seed=9)
     a.step(k)
     st = a.state()
     assert st[0] == k and not st[2]
     x, p = (t.clone() for t in a.particles())
-    pm.pm_set_state(b.ctx, x, p, st[0], st[2])
+    if in_place:
+        xb0, pb0 = b.particles()
+        xb0.copy_(x)
+        pb0.copy_(p)
+        pm.pm_set_state(b.ctx, xb0, pb0, st[0], st[2])
+    else:
+        pm.pm_set_state(b.ctx, x, p, st[0], st[2])
     assert b.state() == st
     a.step(steps - k)
     b.step(steps - k)
