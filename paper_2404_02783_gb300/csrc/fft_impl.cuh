@@ -95,8 +95,8 @@ __device__ __forceinline__ size_t spec_row(int gl, int kz) {
 // =============================================================== z: r2c
 // sub is subtracted from every input value as it is loaded: the mean of a density mesh (its
 // zero mode, which no operator of the path uses), so that the transform's rounding scales
-// with the fluctuations rather than with the mean (v - 1 is exact in floating point for v
-// in [0, 2^24] up to the rounding of v itself near 1).
+// with the fluctuations rather than with the mean.  With sub = 1, v - 1 is exact for v in
+// [0.5, 2^24] and below 0.5 within half the spacing of the values near 1 (2^-25 in FP32).
 template <typename T, int LOGN>
 __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 4 : 2) k_z_r2c(const T* __restrict__ in, cplx<T>* __restrict__ out,
                                                                        T sub) {
