@@ -57,6 +57,19 @@ def test_tophat_window_is_fourier_transform_of_ball():
         assert Cosmology.tophat_window(k * R) == pytest.approx(3.0 * direct / R**3, rel=1e-9, abs=1e-12)
 
 
+def test_tophat_window_near_zero_against_extended_precision():
+    # the small-x branch (a series) against 3 (sin x - x cos x) / x^3 evaluated in 50-digit
+    # arithmetic, on both sides of the switch to the closed form; in FP64 the closed form
+    # loses digits to cancellation just above the switch (sin x - x cos x ~ x^3 / 3: about
+    # 3e-10 at x = 1e-3), the series is exact to rounding below it
+    mpmath = pytest.importorskip("mpmath")
+    mpmath.mp.dps = 50
+    for x, tol in ((1e-5, 1e-14), (5e-4, 1e-14), (9.99e-4, 1e-14), (1.001e-3, 1e-9), (3e-3, 1e-9)):
+        xm = mpmath.mpf(x)
+        exact = float(3 * (mpmath.sin(xm) - xm * mpmath.cos(xm)) / xm**3)
+        assert float(Cosmology.tophat_window(x)) == pytest.approx(exact, rel=0, abs=tol)
+
+
 def test_transfer_function_limits_and_bbks_shape():
     c = Cosmology()
     assert c.transfer_eh_nowiggle(1e-6) == pytest.approx(1.0, abs=1e-4)

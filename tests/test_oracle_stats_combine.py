@@ -85,12 +85,14 @@ def _brute_bispectrum(delta, box, edges, deconvolve=False):
     return S, C
 
 
-@pytest.mark.parametrize("deconvolve", [False, True])
-def test_bispectrum_against_brute_force_triplets(deconvolve):
-    # each mode divided by its own CIC window W(n) before the triplet product when deconvolving
+@pytest.mark.parametrize("deconvolve,top", [(False, 3.5), (True, 3.5), (False, 4.0)])
+def test_bispectrum_against_brute_force_triplets(deconvolve, top):
+    # each mode divided by its own CIC window W(n) before the triplet product when deconvolving;
+    # top = 4.0 closes the last bin at the 8^3 Nyquist frequency, so modes with a Nyquist
+    # component (|n_j| = 4, no distinct partner at -n) fall in it and must be left out
     n, box = 8, 300.0
     delta = inputs.lognormal_field(22, n, sigma=0.8)
-    edges = np.array([0.5, 1.5, 2.5, 3.5])
+    edges = np.array([0.5, 1.5, 2.5, top])
     tri, B, ntri = stats.bispectrum(delta, box, edges, deconvolve=deconvolve)
     S, C = _brute_bispectrum(delta, box, edges, deconvolve)
     for (i, j, l), bval, nt in zip(tri, B, ntri):
@@ -131,6 +133,26 @@ def test_bias_fit_recovers_exact_coefficients():
     _, pmm, _ = stats.power_spectrum(d, 1000.0, edges)
     (b,) = stats.fit_linear_bias(kk, phm / pmm, nm, 1.0)
     assert b == pytest.approx(2.7, rel=1e-12)
+
+
+def test_bias_fit_weights_modes_and_cuts_at_k_max():
+    # Eq. b1 fitted by least squares weighted with the mode counts on k < k_max: a constant
+    # fit is the mode-weighted mean of the ratios of the bins below k_max
+    k = np.array([0.01, 0.02, 0.04])
+    ratio = np.array([1.0, 3.0, 50.0])
+    w = np.array([3.0, 1.0, 100.0])
+    (b,) = stats.fit_linear_bias(k, ratio, w, 0.03)
+    assert b == pytest.approx((3.0 * 1.0 + 1.0 * 3.0) / 4.0, rel=1e-14)
+
+
+def test_halo_proxy_contrast_values():
+    # delta_h = n_h / mean(n_h) - 1 of the indicator of the selected cells: 1/f' - 1 on the
+    # selected cells (f' the selected fraction) and -1 elsewhere, zero mean
+    d = inputs.gaussian_field(24, 4)
+    dh = stats.halo_proxy_contrast(d, 0.05)  # ceil(3.2) = 4 of 64 cells
+    sel = stats.top_fraction_mask(d, 0.05)
+    assert np.all(dh[sel] == 15.0) and np.all(dh[~sel] == -1.0)
+    assert abs(dh.mean()) < 1e-15
 
 
 def test_top_fraction_mask_count_and_ties():
