@@ -38,6 +38,8 @@ def test_single_particle_weights():
             for iz, wz in w[2]:
                 expect[ix, iy, iz] = wx * wy * wz
     np.testing.assert_array_equal(rho, expect)
+    # a particle of mass m deposits m times the weights
+    np.testing.assert_array_equal(cic.deposit(x, n, mass=2.5), 2.5 * expect)
 
 
 def test_interpolation_is_transpose_of_deposit():
