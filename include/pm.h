@@ -83,6 +83,12 @@ enum { PM_FP32_FIXED = 0, PM_FP64 = 1 };
  * the difference across the cell over L/nmesh, weighted bilinearly on the other axes
  * (one inverse transform; the update gathers the potential's eight corners). */
 enum { PM_GRAD_SPECTRAL = 0, PM_GRAD_FD1 = 1 };
+/* Leapfrog factors: the FP64 integrals K = int da / (a^2 E), D = int da / (a^3 E), or the
+ * growth-matched factors that make every step exact for the linear growing mode (the force
+ * of step n taken at a_n, the momenta of its drift at a_{n+1/2}; FastPM, Feng et al. 2016):
+ * K = [a^2 E f D]_{a}^{b} / ((3/2) Om D(a_force)), D = [D]_{a_n}^{a_{n+1}} / (a^2 E f D)(a_{n+1/2}).
+ * The Poisson-gauge lag keeps the conformal time of the integral. */
+enum { PM_STEP_INTEGRALS = 0, PM_STEP_GROWTH = 1 };
 /* Initial-condition flags (pm_ic_zeldovich, pm_batch_ic). */
 enum { PM_IC_PAIRED = 1, PM_IC_FIXED = 2, PM_IC_2LPT = 4 };
 
@@ -104,6 +110,7 @@ typedef struct {
     int n_lo;          /* GR only: modes with |n|^2 <= n_lo^2 are solved and stored in FP64 */
     int gradient;      /* PM_GRAD_SPECTRAL (0) or PM_GRAD_FD1; pm_batch_* refuse FD1
                           (PM_ERR_INVALID_ARG) */
+    int stepping;      /* PM_STEP_INTEGRALS (0) or PM_STEP_GROWTH */
 } pm_config;
 
 typedef struct pm_ctx pm_ctx;   /* opaque host object owned by the library */

@@ -85,6 +85,22 @@ class Cosmology:
                                 epsabs=0.0, epsrel=1e-13, limit=200)
         return val
 
+    def growth_p(self, a):
+        """Momentum growth of the linear growing mode: p = a^3 E dx/da = a^2 E f D Psi for
+        x = q + D Psi (the Zel'dovich momenta of ``ic``)."""
+        return float(a)**2 * float(self.E(a)) * self.growth_f(a) * self.growth_D(a)
+
+    def kick_factor_growth(self, a0, a1, a_force):
+        """Kick factor that is exact for the linear growing mode (the growth-matched factors of
+        FastPM, Feng et al. 2016): the linear force at a_force is g = (3/2) Om D(a_force) Psi
+        and p must go from growth_p(a0) Psi to growth_p(a1) Psi."""
+        return (self.growth_p(a1) - self.growth_p(a0)) / (1.5 * self.omega_m * self.growth_D(a_force))
+
+    def drift_factor_growth(self, a0, a1, a_mom):
+        """Drift factor exact for the linear growing mode: x goes from D(a0) Psi to D(a1) Psi
+        with the momenta growth_p(a_mom) Psi held over the drift."""
+        return (self.growth_D(a1) - self.growth_D(a0)) / self.growth_p(a_mom)
+
     def delta_tau(self, a0, a1):
         """Conformal-time interval in Mpc/h: dtau = c da / (a^2 E)."""
         return C_LIGHT * self.kick_factor(a0, a1)

@@ -10,7 +10,10 @@ One force evaluation per step on a uniform a-grid a_n = a_i + n (a_f - a_i)/N_st
     closing   : p_N = p_{N-1/2} + K(a_{N-1/2}, a_N) g(x_N)     after the last step,
 
 with a_{n+1/2} the arithmetic midpoint, g = -grad(phi) interpolated with CIC, and
-K, D the FP64 integrals of ``cosmology``.  A force evaluation is: CIC deposit of
+K, D the FP64 integrals of ``cosmology`` (stepping = INTEGRALS) or the growth-matched
+factors that make every step exact for the linear growing mode (stepping = GROWTH:
+``cosmology.kick_factor_growth`` with the force taken at a_n, a_N for the closing kick, and
+``cosmology.drift_factor_growth`` with the momenta at a_{n+1/2}).  A force evaluation is: CIC deposit of
 the counting density, FFT, Green's function (Newtonian or the linearised
 Poisson-gauge constraint of ``gravity``), spectral gradient, inverse FFT, CIC
 interpolation.  With gradient = FD1 the potential itself is transformed back and
@@ -26,10 +29,13 @@ NEWTON = 0
 GR_POISSON = 1
 SPECTRAL = 0
 FD1 = 1
+INTEGRALS = 0
+GROWTH = 1
 
 
 class PMRun:
-    def __init__(self, cosmo, n_mesh, box, a_init, a_final, n_steps, x, p, mode=NEWTON, gradient=SPECTRAL):
+    def __init__(self, cosmo, n_mesh, box, a_init, a_final, n_steps, x, p, mode=NEWTON, gradient=SPECTRAL,
+                 stepping=INTEGRALS):
         self.cosmo = cosmo
         self.n = int(n_mesh)
         self.box = float(box)
@@ -40,6 +46,7 @@ class PMRun:
         self.fixed = self.x.dtype == np.uint32
         self.mode = mode
         self.gradient = gradient
+        self.stepping = stepping
         self.i = 0
         self.synced = True
         self.phi_old_k = None
@@ -86,14 +93,24 @@ class PMRun:
             ah = 0.5 * (a0 + a1)
             g = self.accel(a0)
             a_from = a0 if self.synced else 0.5 * (self.a_grid[self.i - 1] + a0)
-            self.p += self.cosmo.kick_factor(a_from, ah) * g
-            self._drift(self.cosmo.drift_factor(a0, a1))
+            self.p += self._kick(a_from, ah, a0) * g
+            self._drift(self._drift_fac(a0, a1, ah))
             self.i += 1
             self.synced = False
             if self.i == self.n_steps:
                 g = self.accel(a1)
-                self.p += self.cosmo.kick_factor(ah, a1) * g
+                self.p += self._kick(ah, a1, a1) * g
                 self.synced = True
+
+    def _kick(self, a0, a1, a_force):
+        if self.stepping == GROWTH:
+            return self.cosmo.kick_factor_growth(a0, a1, a_force)
+        return self.cosmo.kick_factor(a0, a1)
+
+    def _drift_fac(self, a0, a1, a_mom):
+        if self.stepping == GROWTH:
+            return self.cosmo.drift_factor_growth(a0, a1, a_mom)
+        return self.cosmo.drift_factor(a0, a1)
 
     def positions_mpc(self):
         """Positions in Mpc/h in [0, L)."""

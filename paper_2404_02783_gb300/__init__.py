@@ -22,6 +22,7 @@ PM_OK = 0
 PM_NEWTON, PM_GR_POISSON = 0, 1
 PM_FP32_FIXED, PM_FP64 = 0, 1
 PM_GRAD_SPECTRAL, PM_GRAD_FD1 = 0, 1
+PM_STEP_INTEGRALS, PM_STEP_GROWTH = 0, 1
 PM_IC_PAIRED, PM_IC_FIXED, PM_IC_2LPT = 1, 2, 4
 # FP64 island of the Poisson-gauge constraint used by the workloads: |n| <= DEFAULT_N_LO
 DEFAULT_N_LO = 4
@@ -49,13 +50,14 @@ class PMConfig(ctypes.Structure):
                 ("omega_m", ctypes.c_double), ("omega_b", ctypes.c_double), ("h", ctypes.c_double),
                 ("n_s", ctypes.c_double), ("sigma8", ctypes.c_double), ("a_init", ctypes.c_double),
                 ("a_final", ctypes.c_double), ("n_steps", ctypes.c_int), ("mode", ctypes.c_int),
-                ("precision", ctypes.c_int), ("n_lo", ctypes.c_int), ("gradient", ctypes.c_int)]
+                ("precision", ctypes.c_int), ("n_lo", ctypes.c_int), ("gradient", ctypes.c_int),
+                ("stepping", ctypes.c_int)]
 
 
 def make_config(np_side, nmesh, box, a_init, a_final, n_steps, mode=PM_NEWTON, precision=PM_FP32_FIXED,
-                omega_m=0.31, omega_b=0.049, h=0.67, n_s=0.965, sigma8=0.81, n_lo=0, gradient=0):
+                omega_m=0.31, omega_b=0.049, h=0.67, n_s=0.965, sigma8=0.81, n_lo=0, gradient=0, stepping=0):
     return PMConfig(np_side, nmesh, box, omega_m, omega_b, h, n_s, sigma8, a_init, a_final, n_steps, mode,
-                    precision, n_lo, gradient)
+                    precision, n_lo, gradient, stepping)
 
 
 _lib = None

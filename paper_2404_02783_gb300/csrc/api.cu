@@ -80,7 +80,20 @@ pm_status validate(const pm_config* c) {
     if (c->precision != PM_FP32_FIXED && c->precision != PM_FP64) return fail(PM_ERR_INVALID_ARG, "bad precision");
     if (c->n_lo < 0 || 2 * c->n_lo >= c->nmesh) return fail(PM_ERR_INVALID_ARG, "n_lo must be in [0, nmesh/2)");
     if (c->gradient != PM_GRAD_SPECTRAL && c->gradient != PM_GRAD_FD1) return fail(PM_ERR_INVALID_ARG, "bad gradient");
+    if (c->stepping != PM_STEP_INTEGRALS && c->stepping != PM_STEP_GROWTH)
+        return fail(PM_ERR_INVALID_ARG, "bad stepping");
     return PM_OK;
+}
+
+// Leapfrog factors of a run: the kick from a0 to a1 with the force taken at a_force, the
+// drift from a0 to a1 with the momenta held at a_mom (the FP64 integrals ignore both).
+double kick_factor(const pm_config& cfg, const pmhost::Cosmo& co, double a0, double a1, double a_force) {
+    return cfg.stepping == PM_STEP_GROWTH ? pmhost::kick_growth(co, a0, a1, a_force)
+                                          : pmhost::kick_integral(co, a0, a1);
+}
+double drift_factor(const pm_config& cfg, const pmhost::Cosmo& co, double a0, double a1, double a_mom) {
+    return cfg.stepping == PM_STEP_GROWTH ? pmhost::drift_growth(co, a0, a1, a_mom)
+                                          : pmhost::drift_integral(co, a0, a1);
 }
 
 Layout plan(const pm_config& c) {
@@ -942,12 +955,12 @@ pm_status pm_step(pm_ctx* c, int n_steps) {
         const double ah = 0.5 * (a0 + a1);
         PM_TRY(compute_forces(c, a0));
         const double a_from = c->synced ? a0 : 0.5 * (c->a_grid(c->step - 1) + a0);
-        PM_TRY(kick_drift(c, pmhost::kick_integral(c->cosmo, a_from, ah), pmhost::drift_integral(c->cosmo, a0, a1)));
+        PM_TRY(kick_drift(c, kick_factor(c->cfg, c->cosmo, a_from, ah, a0), drift_factor(c->cfg, c->cosmo, a0, a1, ah)));
         c->step += 1;
         c->synced = false;
         if (c->step == c->cfg.n_steps) {
             PM_TRY(compute_forces(c, a1));
-            PM_TRY(kick_drift(c, pmhost::kick_integral(c->cosmo, ah, a1), 0.0));
+            PM_TRY(kick_drift(c, kick_factor(c->cfg, c->cosmo, ah, a1, a1), 0.0));
             c->synced = true;
         }
     }
@@ -1372,10 +1385,11 @@ namespace {
 double kick_of_step(const pm_ctx* c, int s) {
     const double a0 = c->a_grid(s), a1 = c->a_grid(s + 1);
     const double a_from = (s == 0) ? a0 : 0.5 * (c->a_grid(s - 1) + a0);
-    return pmhost::kick_integral(c->cosmo, a_from, 0.5 * (a0 + a1));
+    return kick_factor(c->cfg, c->cosmo, a_from, 0.5 * (a0 + a1), a0);
 }
 double drift_of_step(const pm_ctx* c, int s) {
-    return pmhost::drift_integral(c->cosmo, c->a_grid(s), c->a_grid(s + 1));
+    const double a0 = c->a_grid(s), a1 = c->a_grid(s + 1);
+    return drift_factor(c->cfg, c->cosmo, a0, a1, 0.5 * (a0 + a1));
 }
 
 // Pieces of the reverse sweep shared by pm_adjoint_record, pm_adjoint_run and pm_loss_grad.
@@ -1482,7 +1496,8 @@ struct AdjSweep {
         return PM_OK;
     }
     double close_kick() const {
-        return pmhost::kick_integral(c->cosmo, 0.5 * (c->a_grid(steps - 1) + c->a_grid(steps)), c->a_grid(steps));
+        return kick_factor(c->cfg, c->cosmo, 0.5 * (c->a_grid(steps - 1) + c->a_grid(steps)), c->a_grid(steps),
+                           c->a_grid(steps));
     }
 
     // Reverse sweep from the adjoint positions lam_u (scratch lam_u) and, with mom, the adjoint
@@ -1855,12 +1870,12 @@ pm_status batch_forces_update(pm_batch* b, double kick, double drift, cudaStream
 pm_status batch_enqueue_step(pm_batch* b, cudaStream_t s) {
     const double a0 = b->a_grid(b->step), a1 = b->a_grid(b->step + 1), ah = 0.5 * (a0 + a1);
     const double a_from = b->synced ? a0 : 0.5 * (b->a_grid(b->step - 1) + a0);
-    PM_TRY(batch_forces_update(b, pmhost::kick_integral(b->cosmo, a_from, ah),
-                               pmhost::drift_integral(b->cosmo, a0, a1), s));
+    PM_TRY(batch_forces_update(b, kick_factor(b->cfg, b->cosmo, a_from, ah, a0),
+                               drift_factor(b->cfg, b->cosmo, a0, a1, ah), s));
     b->step += 1;
     b->synced = false;
     if (b->step == b->cfg.n_steps) {
-        PM_TRY(batch_forces_update(b, pmhost::kick_integral(b->cosmo, ah, a1), 0.0, s));
+        PM_TRY(batch_forces_update(b, kick_factor(b->cfg, b->cosmo, ah, a1, a1), 0.0, s));
         b->synced = true;
     }
     return PM_OK;

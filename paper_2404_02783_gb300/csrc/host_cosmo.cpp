@@ -124,6 +124,18 @@ double drift_integral(const Cosmo& c, double a0, double a1) {
     return integrate([&c](double a) { return 1.0 / (a * a * a * E(c, a)); }, a0, a1);
 }
 
+double growth_p(const Cosmo& c, double a) { return a * a * E(c, a) * growth_f(c, a) * growth_D(c, a); }
+
+// p goes from growth_p(a0) Psi to growth_p(a1) Psi under the kick K g with g = (3/2) Om D(a_force) Psi.
+double kick_growth(const Cosmo& c, double a0, double a1, double a_force) {
+    return (growth_p(c, a1) - growth_p(c, a0)) / (1.5 * c.omega_m * growth_D(c, a_force));
+}
+
+// x goes from D(a0) Psi to D(a1) Psi under the drift F p with p = growth_p(a_mom) Psi.
+double drift_growth(const Cosmo& c, double a0, double a1, double a_mom) {
+    return (growth_D(c, a1) - growth_D(c, a0)) / growth_p(c, a_mom);
+}
+
 double transfer_eh_nowiggle(const Cosmo& c, double k) {
     // Eisenstein & Hu (1998), Eqs. 26 and 28-31.
     const double omh2 = c.omega_m * c.h * c.h, obh2 = c.omega_b * c.h * c.h;

@@ -86,6 +86,23 @@ def test_batched_power_matches_oracle_and_single_runs():
         np.testing.assert_allclose(k[r][ok], ko[ok], rtol=1e-12)
 
 
+def test_growth_matched_stepping_in_a_batch_matches_single_runs():
+    pm = lib()
+    cfg = pm.make_config(NP, NMESH, BOXES[0], A_I, A_F, STEPS, stepping=pm.PM_STEP_GROWTH)
+    b = pm.PMBatch(cfg, boxes=BOXES)
+    b.ic(SEEDS)
+    b.step(STEPS, graph=True)
+    for r, (box, seed) in enumerate(zip(BOXES, SEEDS)):
+        run = pm.PMRun(pm.make_config(NP, NMESH, box, A_I, A_F, STEPS, stepping=pm.PM_STEP_GROWTH))
+        run.ic(seed=seed)
+        x0 = ticks_to_host(run.particles()[0]).copy()
+        run.step(STEPS)
+        xs, ps = ticks_to_host(run.particles()[0]).copy(), to_host(run.particles()[1]).astype(np.float64)
+        xb, pb = _batch_particles(b, r)
+        assert rel_l2(_disp(xb, x0), _disp(xs, x0)) < 1e-5
+        assert rel_l2(pb, ps) < 1e-5
+
+
 def test_batched_bias_matches_single_pipeline():
     pm = lib()
     b = pm.PMBatch(_cfg(pm), boxes=BOXES)

@@ -61,6 +61,53 @@ def test_zeldovich_plane_wave_and_second_order_convergence():
     assert np.max(np.abs(run.p[1])) < 1e-12 and np.max(np.abs(run.p[2])) < 1e-12
 
 
+def test_growth_matched_stepping_is_exact_for_the_linear_force():
+    # with the PM force replaced by the exact linear one, g = (3/2) Om d for the displacement
+    # d = D Psi (Poisson's equation for delta = -div d), the growth-matched kick and drift
+    # factors reproduce the Zel'dovich solution x = q + D Psi, p = a^2 E f D Psi at every step
+    # and after the closing kick, for any step count; the plain integrals do not
+    c = Cosmology()
+    n, box, a_i, a_f = 8, 100.0, 0.02, 1.0
+    q = np.stack([g.ravel() for g in np.meshgrid(*(np.arange(n) / n,) * 3, indexing="ij")])
+    psi = inputs.rng(31).normal(0.0, 2.0, size=(3, n**3))
+    mi = lambda d: d - np.rint(d)  # minimum image in box units
+    errs = {}
+    for stepping, ns in ((pm.GROWTH, 3), (pm.GROWTH, 7), (pm.INTEGRALS, 3)):
+        x0 = q + c.growth_D(a_i) * psi / box
+        run = pm.PMRun(c, n, box, a_i, a_f, ns, x0 - np.floor(x0), c.growth_p(a_i) * psi, stepping=stepping)
+        run.accel = lambda a, r=run: 1.5 * c.omega_m * mi(r.x - q) * box
+        run.step(ns)
+        d1, p1 = c.growth_D(a_f) * psi / box, c.growth_p(a_f) * psi
+        errs[(stepping, ns)] = max(np.max(np.abs(mi(run.x - q) - d1)) / np.max(np.abs(d1)),
+                                   np.max(np.abs(run.p - p1)) / np.max(np.abs(p1)))
+    assert errs[(pm.GROWTH, 3)] < 1e-12 and errs[(pm.GROWTH, 7)] < 1e-12
+    assert errs[(pm.INTEGRALS, 3)] > 1e-2
+
+
+def test_growth_matched_stepping_of_a_plane_wave():
+    # the mesh force of a plane wave before shell crossing is linear up to the mesh's own
+    # error: with growth-matched factors three steps land where 32 do (the mesh-limited
+    # answer), far closer than the plain integrals' three steps
+    def run(ns, stepping):
+        c = Cosmology()
+        n, box, a_i, a_f = 32, 100.0, 0.05, 0.5
+        k = 2 * np.pi / box
+        A = 0.5 / c.growth_D(a_f)
+        q = np.arange(n) / n
+        X, Y, Z = np.meshgrid(q, q, q, indexing="ij")
+        psi = np.zeros((3, n**3))
+        psi[0] = -(A / k) * np.sin(k * X.ravel() * box)
+        x0 = np.stack([X.ravel(), Y.ravel(), Z.ravel()]) + c.growth_D(a_i) * psi / box
+        r = pm.PMRun(c, n, box, a_i, a_f, ns, x0 - np.floor(x0), c.growth_p(a_i) * psi, stepping=stepping)
+        r.step(ns)
+        return r.x[0]
+    d = lambda u, v: np.max(np.abs((u - v) - np.rint(u - v)))
+    g3, g32 = run(3, pm.GROWTH), run(32, pm.GROWTH)
+    i3, i32 = run(3, pm.INTEGRALS), run(32, pm.INTEGRALS)
+    assert d(g32, i32) < 0.01 * 0.5 / (2 * np.pi)  # 32 steps: both close to the same answer
+    assert d(g3, g32) < 0.4 * d(i3, i32)
+
+
 def test_fixed_point_and_fp64_positions_agree():
     run_f, x_end, _ = _plane_wave_run(16, fixed=True)
     run_d, _, _ = _plane_wave_run(16, fixed=False)
