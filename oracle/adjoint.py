@@ -34,6 +34,7 @@ import numpy as np
 
 from . import cic, gravity, ic, philox
 from .cosmology import C_LIGHT
+from .pm import GROWTH, INTEGRALS
 
 NEWTON, GR_POISSON = 0, 1  # the force of the run, as in oracle.pm
 SPECTRAL, FD1 = 0, 1       # the gradient of the potential, as in oracle.pm
@@ -179,9 +180,10 @@ def _za_operator(w_or_s, n_p, box, cosmo, j):
     return np.fft.irfftn(1j * kf * Nj * dk * inv_k2, s=(n_p,) * 3, axes=(0, 1, 2))
 
 
-def forward(cosmo, n_p, n_mesh, box, a_i, a_f, n_steps, w, mode=NEWTON, gradient=SPECTRAL):
+def forward(cosmo, n_p, n_mesh, box, a_i, a_f, n_steps, w, mode=NEWTON, gradient=SPECTRAL, stepping=INTEGRALS):
     """ZA ICs from w and the KDK run (Newtonian or Poisson-gauge force, spectral or first-order
-    gradient); returns (u_final, p_final, ops, mass).  A kick op ("kick", K, u, info) keeps in
+    gradient, the kick and drift factors of ``pm.PMRun`` with the same stepping); returns
+    (u_final, p_final, ops, mass).  A kick op ("kick", K, u, info) keeps in
     info the force meshes "G" (spectral) or the potential mesh "phi" (first order), and for the
     Poisson gauge "gr" = (a, dtau)."""
     psi = ic.za_displacement(ic.linear_delta_k(cosmo, n_p, box, white_noise=w), n_p, box).reshape(3, -1)
@@ -211,22 +213,28 @@ def forward(cosmo, n_p, n_mesh, box, a_i, a_f, n_steps, w, mode=NEWTON, gradient
             g = -cic.interpolate_gradient(phi, uu, box)
         return ("kick", K, uu.copy(), info), g
 
+    def kick_fac(a, b, a_force):
+        return cosmo.kick_factor_growth(a, b, a_force) if stepping == GROWTH else cosmo.kick_factor(a, b)
+
+    def drift_fac(a, b, a_mom):
+        return cosmo.drift_factor_growth(a, b, a_mom) if stepping == GROWTH else cosmo.drift_factor(a, b)
+
     synced = True
     for s in range(n_steps):
         a0, a1 = grid[s], grid[s + 1]
         ah = 0.5 * (a0 + a1)
         a_from = a0 if synced else 0.5 * (grid[s - 1] + a0)
-        K = cosmo.kick_factor(a_from, ah)
+        K = kick_fac(a_from, ah, a0)
         op, g = kick(u, a0, K)
         ops.append(op)
         p = p + K * g
-        Dd = cosmo.drift_factor(a0, a1)
+        Dd = drift_fac(a0, a1, ah)
         ops.append(("drift", Dd))
         u = u + Dd * p / box
         u = u - np.floor(u)
         synced = False
         if s == n_steps - 1:
-            K = cosmo.kick_factor(ah, a1)
+            K = kick_fac(ah, a1, a1)
             op, g = kick(u, a1, K)
             ops.append(op)
             p = p + K * g
@@ -252,14 +260,14 @@ def displacement(u, n_p, box):
 
 
 def vjp(cosmo, n_p, n_mesh, box, a_i, a_f, n_steps, w, lam_delta=None, lam_disp=None, lam_mom=None, mode=NEWTON,
-        gradient=SPECTRAL):
+        gradient=SPECTRAL, stepping=INTEGRALS):
     """dL/dw for any loss L(delta_final, d_final, p_final) given its cotangents lam_delta =
     dL/d delta (n_mesh^3 mesh), lam_disp = dL/d d ((3, n_p^3), per Mpc/h) and lam_mom =
     dL/dp ((3, n_p^3), per Mpc/h of momentum, p after the closing half kick), by the reverse
     sweep of the recorded forward run.  Since d = (u - q) L (minimum image), dL/du = L
     lam_disp; the density adds m sum_c lam_delta(c) dW(u, c)/du; lam_mom is the adjoint
     momentum the sweep starts from (the closing kick is the first operation it reverses)."""
-    u, p, ops, mass = forward(cosmo, n_p, n_mesh, box, a_i, a_f, n_steps, w, mode, gradient)
+    u, p, ops, mass = forward(cosmo, n_p, n_mesh, box, a_i, a_f, n_steps, w, mode, gradient, stepping)
     lam_u = np.zeros_like(u)
     if lam_delta is not None:
         lam_u += mass * _grad_gather(np.asarray(lam_delta, dtype=np.float64), u, n_mesh)

@@ -123,6 +123,34 @@ def test_any_torch_loss_of_density_and_displacements_matches_fp64_oracle(np_side
     assert rel_l2(to_host(disp).astype(np.float64), adjoint.displacement(u, np_side, box)) < 1e-4
 
 
+def test_growth_matched_stepping_gradient_matches_fp64_oracle():
+    # PM_STEP_GROWTH: the reverse sweep takes the same growth-matched kick and drift factors as
+    # the forward run; a loss of the final density, displacements and momenta, checkpoints every
+    # 2 of 6 steps (the first segments re-run), against the oracle's vector-Jacobian product
+    pm = lib()
+    np_side, nmesh, box, a_i, a_f, steps = 16, 32, 1000.0, 0.05, 1.0, 6
+    c = Cosmology()
+    w = inputs.gaussian_field(33, np_side).astype(np.float32)
+    run = pm.PMRun(pm.make_config(np_side, nmesh, box, a_i, a_f, steps, stepping=pm.PM_STEP_GROWTH))
+    Wk = _spectral_weight(nmesh)
+    r = np.random.default_rng(15)
+    gdisp = r.standard_normal((3, np_side**3)) * 1e-3
+    h = r.standard_normal((3, np_side**3)) * 1e-2
+    wv = to_dev(w).requires_grad_(True)
+    delta, disp, mom = pm.run_fields(run, wv, checkpoint_every=2, momenta=True)
+    L = _torch_loss(delta, disp, to_dev(Wk), to_dev(gdisp), nmesh) + (to_dev(h) * mom.to(torch.float64)).sum()
+    L.backward()
+    g = to_host(wv.grad).astype(np.float64)
+    w64 = w.astype(np.float64)
+    u, p_o, _, _ = adjoint.forward(c, np_side, nmesh, box, a_i, a_f, steps, w64, stepping=1)
+    dk = np.fft.fftn(cic.density_contrast(u, nmesh))
+    lam_delta = 2.0 * np.real(np.fft.ifftn(Wk * dk)) / nmesh**3
+    go = adjoint.vjp(c, np_side, nmesh, box, a_i, a_f, steps, w64, lam_delta=lam_delta, lam_disp=gdisp, lam_mom=h,
+                     stepping=1)
+    assert rel_l2(g, go) < 1e-4
+    assert rel_l2(to_host(mom).astype(np.float64), p_o) < 1e-4
+
+
 @pytest.mark.parametrize("np_side,nmesh", [(16, 16), (32, 64)])
 def test_a_loss_of_the_final_momenta_matches_fp64_oracle(np_side, nmesh):
     # run_fields(momenta=True) also returns the synchronised final momenta; a loss with a term

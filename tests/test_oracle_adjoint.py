@@ -126,6 +126,46 @@ def test_forward_map_is_the_oracle_run(mode, gradient):
     np.testing.assert_allclose(run.p, p, rtol=0, atol=1e-12 * np.max(np.abs(p)))
 
 
+def test_growth_matched_stepping_forward_map_and_vector_jacobian_product():
+    # with the growth-matched kick and drift factors: the adjoint's forward map equals oracle.pm's
+    # run with the same factors, and its vector-Jacobian product for a loss of the final density,
+    # displacements and momenta matches central differences of that map
+    from oracle import pm as opm
+    c = Cosmology()
+    n_p, n_mesh, box, ai, af, steps = 8, 16, 1000.0, 0.05, 1.0, 4
+    w = inputs.gaussian_field(12, n_p)
+    u, p, _, _ = adjoint.forward(c, n_p, n_mesh, box, ai, af, steps, w, stepping=opm.GROWTH)
+    u0, p0 = _ics_of(c, n_p, box, ai, w)
+    run = opm.PMRun(c, n_mesh, box, ai, af, steps, u0, p0, stepping=opm.GROWTH)
+    run.step(steps)
+    d = run.x - u
+    assert np.max(np.abs(d - np.rint(d))) < 1e-13
+    np.testing.assert_allclose(run.p, p, rtol=0, atol=1e-12 * np.max(np.abs(p)))
+    r = np.random.default_rng(13)
+    f = np.fft.fftfreq(n_mesh, 1.0 / n_mesh)
+    Wk = 1.0 / (1.0 + f[:, None, None]**2 + f[None, :, None]**2 + f[None, None, :]**2)
+    gdisp = r.standard_normal((3, n_p**3)) * 1e-3
+    h = r.standard_normal((3, n_p**3)) * 1e-2
+
+    def L_of(ww):
+        uu, pp, _, _ = adjoint.forward(c, n_p, n_mesh, box, ai, af, steps, ww, stepping=opm.GROWTH)
+        dk = np.fft.fftn(cic.density_contrast(uu, n_mesh))
+        return float(np.sum(Wk * np.abs(dk)**2) / n_mesh**6 + np.sum(gdisp * adjoint.displacement(uu, n_p, box))
+                     + np.sum(h * pp))
+
+    dk = np.fft.fftn(cic.density_contrast(u, n_mesh))
+    lam_delta = 2.0 * np.real(np.fft.ifftn(Wk * dk)) / n_mesh**3
+    g = adjoint.vjp(c, n_p, n_mesh, box, ai, af, steps, w, lam_delta=lam_delta, lam_disp=gdisp, lam_mom=h,
+                    stepping=opm.GROWTH)
+    gi = adjoint.vjp(c, n_p, n_mesh, box, ai, af, steps, w, lam_delta=lam_delta, lam_disp=gdisp, lam_mom=h)
+    assert np.linalg.norm(g - gi) > 0.01 * np.linalg.norm(g)  # the factors matter for the gradient
+    eps = 1e-5
+    for _ in range(3):
+        v = r.standard_normal((n_p,) * 3)
+        fd = (L_of(w + eps * v) - L_of(w - eps * v)) / (2 * eps)
+        assert np.sum(g * v) == pytest.approx(fd, rel=1e-6)
+
+
 def test_poisson_gauge_vector_jacobian_product():
     # Poisson gauge at 20 Gpc/h (the lag term 3 calH / dtau is larger than k^2 on the low modes):
     # a loss of the final density, displacements and momenta; the reverse sweep with the carried
