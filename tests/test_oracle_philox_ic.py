@@ -142,6 +142,18 @@ def _bin_mean_linear_power(c, n, box, edges):
     return num / den
 
 
+def test_paired_phases_invert_the_linear_field():
+    # the pairing method (Sec. 4.2): the partner run starts from the same field with every phase
+    # shifted by pi, i.e. delta -> -delta (and the Zel'dovich displacements change sign)
+    c = Cosmology()
+    d = ic.linear_delta_k(c, 16, 500.0, seed=4)
+    dp = ic.linear_delta_k(c, 16, 500.0, seed=4, paired=True)
+    np.testing.assert_array_equal(dp, -d)
+    df = ic.linear_delta_k(c, 16, 500.0, seed=4, fixed_amplitude=True)
+    dfp = ic.linear_delta_k(c, 16, 500.0, seed=4, fixed_amplitude=True, paired=True)
+    np.testing.assert_array_equal(dfp, -df)
+
+
 def test_fixed_amplitude_ic_has_the_input_spectrum_exactly():
     # Fixed amplitudes (|g_n| = 1): the measured P(k) of the linear field equals the bin
     # mean of the input spectrum with no cosmic variance; Gaussian amplitudes scatter.

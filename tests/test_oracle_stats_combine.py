@@ -135,6 +135,15 @@ def test_bias_fit_recovers_exact_coefficients():
     assert b == pytest.approx(2.7, rel=1e-12)
 
 
+def test_cross_spectrum_is_the_real_part():
+    # Eq. powerspectrum for two fields: Re <delta_1 delta_2*>, so delta against -delta gives -P
+    d = inputs.gaussian_field(25, 16)
+    edges = stats.log_edges(6, 1.0, 8.0)
+    _, p, _ = stats.power_spectrum(d, 500.0, edges)
+    _, px, _ = stats.power_spectrum(d, 500.0, edges, delta2=-d)
+    np.testing.assert_allclose(px, -p, rtol=1e-14)
+
+
 def test_bias_fit_weights_modes_and_cuts_at_k_max():
     # Eq. b1 fitted by least squares weighted with the mode counts on k < k_max: a constant
     # fit is the mode-weighted mean of the ratios of the bins below k_max
@@ -192,3 +201,10 @@ def test_lagrangian_interpolation_reproduces_constant_and_linear():
     # FP64 form agrees with the tick form up to rounding
     outf = combine.interpolate_lagrangian(xi.astype(np.float64) * 2.0**-32, nc, nt)
     assert np.max(np.abs(outf * 2**32 - out.reshape(3, -1))) <= 0.5
+    # a target halfway between two coarse nodes gets their mean; on ticks a tie rounds half to
+    # even (the reading both sides share): 0 and 1 -> 0, 1 and 2 -> 2, -1 and 0 -> 0, 3 and 4 -> 4
+    for lo, hi, want in ((0, 1, 0), (1, 2, 2), (-1, 0, 0), (3, 4, 4), (5, 6, 6)):
+        v = np.where(np.arange(nc) % 2 == 0, lo, hi)
+        f = np.broadcast_to(v[:, None, None], (nc, nc, nc)).ravel()
+        t = combine.interpolate_lagrangian(np.stack([f, f, f]).astype(np.int32), nc, nt).reshape(3, nt, nt, nt)
+        assert t[0, 1, 0, 0] == want, (lo, hi, t[0, 1, 0, 0])
