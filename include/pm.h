@@ -47,7 +47,7 @@
  * the stateless operators) except pm_power, pm_bispectrum and pm_linear_bias, which
  * synchronise that stream before returning host results, and pm_adjoint_run /
  * pm_loss_grad, which also run on a second stream of the context's own and synchronise both.  Host-only calls
- * (pm_triangle_index, pm_b1_gr_theory, the *_size queries) touch no device.
+ * (pm_triangle_index, pm_b1_gr_theory, pm_step_factors, the *_size queries) touch no device.
  * Errors: every call returns a pm_status; pm_last_error() gives a static,
  * thread-local message for the last failure.  A CUDA error inside a call is
  * returned as PM_ERR_CUDA and leaves the context unusable (pm_destroy it).
@@ -301,6 +301,15 @@ pm_status pm_linear_bias(pm_ctx* ctx, const void* delta_h, const void* delta_m, 
  * the fitted b1^GR of the relativistic run minus that of the Newtonian run (the
  * Newtonian systematic).  Host only.  omega_m outside (0, 1] or a <= 0: PM_ERR_INVALID_ARG. */
 pm_status pm_b1_gr_theory(const pm_config* cfg, double a, double b1, double* b1_gr);
+
+/* The leapfrog factors pm_step uses for step s (0..n_steps-1) of a run started at a_init with
+ * synchronised momenta: kick = the kick of step s (from a_init for s = 0, else from the
+ * midpoint a_{s-1/2}, to a_{s+1/2}), drift = the drift from a_s to a_{s+1}, kick_close = the
+ * closing half kick from a_{N-1/2} to a_N; all in FP64 for cfg's background and stepping
+ * (PM_STEP_INTEGRALS or PM_STEP_GROWTH; the p update is p += kick * g with g = -grad phi, the
+ * position update x += drift * p).  Any output may be NULL.  Host only.  An invalid cfg or s
+ * outside 0..n_steps-1: PM_ERR_INVALID_ARG. */
+pm_status pm_step_factors(const pm_config* cfg, int s, double* kick, double* drift, double* kick_close);
 
 /* Device scratch bytes pm_bispectrum needs for grid m and nbins bins. */
 pm_status pm_bispectrum_scratch_size(const pm_ctx* ctx, int m, int nbins, size_t* bytes);

@@ -692,6 +692,25 @@ const char* pm_version(void) { return "pm-gb300 0.2 (sm_103a)"; }
 
 const char* pm_last_error(void) { return g_err.c_str(); }
 
+pm_status pm_step_factors(const pm_config* cfg, int s, double* kick, double* drift, double* kick_close) {
+    PM_TRY(validate(cfg));
+    if (s < 0 || s >= cfg->n_steps) return fail(PM_ERR_INVALID_ARG, "step outside 0..n_steps-1");
+    pmhost::Cosmo co;
+    co.omega_m = cfg->omega_m;
+    co.omega_b = cfg->omega_b;
+    co.h = cfg->h;
+    co.n_s = cfg->n_s;
+    co.sigma8 = cfg->sigma8;
+    auto grid = [cfg](int i) { return cfg->a_init + ((cfg->a_final - cfg->a_init) * i) / cfg->n_steps; };
+    const double a0 = grid(s), a1 = grid(s + 1), ah = 0.5 * (a0 + a1);
+    const double a_from = (s == 0) ? a0 : 0.5 * (grid(s - 1) + a0);
+    if (kick) *kick = kick_factor(*cfg, co, a_from, ah, a0);
+    if (drift) *drift = drift_factor(*cfg, co, a0, a1, ah);
+    const int N = cfg->n_steps;
+    if (kick_close) *kick_close = kick_factor(*cfg, co, 0.5 * (grid(N - 1) + grid(N)), grid(N), grid(N));
+    return PM_OK;
+}
+
 pm_status pm_b1_gr_theory(const pm_config* cfg, double a, double b1, double* b1_gr) {
     if (!cfg || !b1_gr) return fail(PM_ERR_INVALID_ARG, "null argument");
     if (!(cfg->omega_m > 0 && cfg->omega_m <= 1) || !(a > 0)) return fail(PM_ERR_INVALID_ARG, "bad omega_m or a");

@@ -5,6 +5,7 @@ import os
 import re
 import subprocess
 
+import numpy as np
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -141,3 +142,28 @@ def test_b1_gr_theory_matches_the_oracle(pm):
     assert pm.pm_b1_gr_theory(cfg, 0.7, 1.0) == 0.0
     with pytest.raises(pm.PMError):
         pm.pm_b1_gr_theory(cfg, -1.0, 2.0)
+
+
+@pytest.mark.parametrize("stepping", [0, 1])
+def test_step_factors_match_the_oracle(pm, stepping):
+    # host-only: the FP64 kick and drift factors pm_step uses (its own Gauss-Legendre quadrature
+    # or the growth-matched factors) against the oracle's (scipy quadrature, its growth ODE), for
+    # the first, a middle and the last step of a run from z = 50 and its closing half kick
+    from oracle import pm as opm
+    from oracle.cosmology import Cosmology
+    n, a_i, a_f = 20, 1.0 / 51.0, 1.0
+    cfg = pm.make_config(32, 64, 1000.0, a_i, a_f, n, stepping=stepping)
+    c = Cosmology()
+    ref = opm.PMRun(c, 64, 1000.0, a_i, a_f, n, np.zeros((3, 1)), np.zeros((3, 1)), stepping=stepping)
+    grid = ref.a_grid
+    for s in (0, 1, 9, n - 1):
+        a0, a1 = grid[s], grid[s + 1]
+        ah = 0.5 * (a0 + a1)
+        a_from = a0 if s == 0 else 0.5 * (grid[s - 1] + a0)
+        kick, drift, close = pm.pm_step_factors(cfg, s)
+        assert kick == pytest.approx(ref._kick(a_from, ah, a0), rel=1e-10)
+        assert drift == pytest.approx(ref._drift_fac(a0, a1, ah), rel=1e-10)
+        assert close == pytest.approx(ref._kick(0.5 * (grid[n - 1] + a_f), a_f, a_f), rel=1e-10)
+    for bad in (-1, n):
+        with pytest.raises(pm.PMError):
+            pm.pm_step_factors(cfg, bad)
