@@ -47,7 +47,8 @@
  * the stateless operators) except pm_power, pm_bispectrum and pm_linear_bias, which
  * synchronise that stream before returning host results, and pm_adjoint_run /
  * pm_loss_grad, which also run on a second stream of the context's own and synchronise both.  Host-only calls
- * (pm_triangle_index, pm_b1_gr_theory, pm_step_factors, the *_size queries) touch no device.
+ * (pm_triangle_index, pm_b1_gr_theory, pm_step_factors, pm_linear_power, the *_size queries)
+ * touch no device.
  * Errors: every call returns a pm_status; pm_last_error() gives a static,
  * thread-local message for the last failure.  A CUDA error inside a call is
  * returned as PM_ERR_CUDA and leaves the context unusable (pm_destroy it).
@@ -310,6 +311,15 @@ pm_status pm_b1_gr_theory(const pm_config* cfg, double a, double b1, double* b1_
  * position update x += drift * p).  Any output may be NULL.  Host only.  An invalid cfg or s
  * outside 0..n_steps-1: PM_ERR_INVALID_ARG. */
 pm_status pm_step_factors(const pm_config* cfg, int s, double* kick, double* drift, double* kick_close);
+
+/* The linear theory the initial conditions are drawn from (Sec. 3 setup): P_out[i] = P(k[i], a)
+ * in (Mpc/h)^3 for k[i] in h/Mpc (Eisenstein-Hu no-wiggle transfer function, n_s, sigma_8
+ * normalised with a real-space top hat of 8 Mpc/h at a = 1) times D(a)^2, and, if not NULL,
+ * D_out = D(a) (D(1) = 1) and f_out = dlnD/dlna for cfg's background (only its cosmological
+ * fields are read).  Host arrays of count >= 0 entries.  Host only.  omega_m outside (0, 1],
+ * a <= 0, a negative k or count < 0: PM_ERR_INVALID_ARG. */
+pm_status pm_linear_power(const pm_config* cfg, double a, const double* k, int64_t count, double* p_out, double* D_out,
+                          double* f_out);
 
 /* Device scratch bytes pm_bispectrum needs for grid m and nbins bins. */
 pm_status pm_bispectrum_scratch_size(const pm_ctx* ctx, int m, int nbins, size_t* bytes);

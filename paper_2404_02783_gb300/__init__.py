@@ -32,7 +32,7 @@ _STATUS = {0: "PM_OK", 1: "PM_ERR_INVALID_ARG", 2: "PM_ERR_CUDA", 3: "PM_ERR_WOR
 # every entry point declared in include/pm.h
 EXPORTS = ("pm_workspace_size", "pm_init", "pm_destroy", "pm_ic_zeldovich", "pm_step", "pm_particles",
            "pm_set_particles", "pm_set_state", "pm_state", "pm_set_fused_fft", "pm_autotune_fft", "pm_profile", "pm_timings", "pm_density", "pm_potential", "pm_displacement_correction", "pm_power", "pm_halo_proxy", "pm_linear_bias",
-           "pm_bispectrum_scratch_size", "pm_bispectrum", "pm_triangle_index", "pm_b1_gr_theory", "pm_step_factors", "pm_cic_deposit", "pm_cic_interp",
+           "pm_bispectrum_scratch_size", "pm_bispectrum", "pm_triangle_index", "pm_b1_gr_theory", "pm_step_factors", "pm_linear_power", "pm_cic_deposit", "pm_cic_interp",
            "pm_adjoint_scratch_size", "pm_adjoint_record", "pm_adjoint_run", "pm_loss_grad", "pm_displacement", "pm_positions", "pm_gr_history", "pm_set_state_gr", "pm_batch_workspace_size", "pm_batch_init", "pm_batch_destroy", "pm_batch_context", "pm_batch_ic",
            "pm_batch_step", "pm_batch_state", "pm_batch_power", "pm_batch_bias", "pm_batch_set_chunk", "pm_batch_autotune", "pm_batch_set_fft", "pm_batch_tuning",
            "pm_cell_sort_scratch_size", "pm_cell_sort", "pm_cell_sort_static", "pm_div_mode_check", "pm_fft_r2c", "pm_fft_c2r", "pm_version", "pm_last_error")
@@ -101,6 +101,7 @@ def lib():
         "pm_triangle_index": (i, i, i, i, ctypes.POINTER(i64)),
         "pm_b1_gr_theory": (cfgp, d, d, pd),
         "pm_step_factors": (cfgp, i, pd, pd, pd),
+        "pm_linear_power": (cfgp, d, pd, i64, pd, pd, pd),
         "pm_adjoint_scratch_size": (vp, i, ctypes.POINTER(sz)),
         "pm_loss_grad": (vp, vp, vp, i, vp, sz, pd, vp),
         "pm_adjoint_record": (vp, vp, i, vp, sz),
@@ -360,6 +361,16 @@ def pm_step_factors(cfg, s):
     k, dr, kc = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
     _check(lib().pm_step_factors(ctypes.byref(cfg), int(s), ctypes.byref(k), ctypes.byref(dr), ctypes.byref(kc)))
     return k.value, dr.value, kc.value
+
+
+def pm_linear_power(cfg, a, k):
+    """(P(k, a) [(Mpc/h)^3], D(a), f(a)) of the linear theory the ICs are drawn from (host only)."""
+    k = np.ascontiguousarray(k, dtype=np.float64)
+    p = np.empty_like(k)
+    D, f = ctypes.c_double(), ctypes.c_double()
+    _check(lib().pm_linear_power(ctypes.byref(cfg), float(a), _dptr(k), k.size, _dptr(p), ctypes.byref(D),
+                                 ctypes.byref(f)))
+    return p, D.value, f.value
 
 
 def bispectrum_configurations(nbins, k3_bin):

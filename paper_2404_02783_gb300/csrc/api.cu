@@ -711,6 +711,26 @@ pm_status pm_step_factors(const pm_config* cfg, int s, double* kick, double* dri
     return PM_OK;
 }
 
+pm_status pm_linear_power(const pm_config* cfg, double a, const double* k, int64_t count, double* p_out,
+                          double* D_out, double* f_out) {
+    if (!cfg || count < 0 || (count > 0 && (!k || !p_out))) return fail(PM_ERR_INVALID_ARG, "bad arguments");
+    if (!(cfg->omega_m > 0 && cfg->omega_m <= 1) || !(a > 0)) return fail(PM_ERR_INVALID_ARG, "bad omega_m or a");
+    for (int64_t i = 0; i < count; ++i)
+        if (!(k[i] >= 0)) return fail(PM_ERR_INVALID_ARG, "k must be non-negative");
+    pmhost::Cosmo co;
+    co.omega_m = cfg->omega_m;
+    co.omega_b = cfg->omega_b;
+    co.h = cfg->h;
+    co.n_s = cfg->n_s;
+    co.sigma8 = cfg->sigma8;
+    pmhost::normalise_sigma8(co);
+    const double D = pmhost::growth_D(co, a);
+    for (int64_t i = 0; i < count; ++i) p_out[i] = k[i] > 0 ? pmhost::power_linear(co, k[i]) * D * D : 0.0;
+    if (D_out) *D_out = D;
+    if (f_out) *f_out = pmhost::growth_f(co, a);
+    return PM_OK;
+}
+
 pm_status pm_b1_gr_theory(const pm_config* cfg, double a, double b1, double* b1_gr) {
     if (!cfg || !b1_gr) return fail(PM_ERR_INVALID_ARG, "null argument");
     if (!(cfg->omega_m > 0 && cfg->omega_m <= 1) || !(a > 0)) return fail(PM_ERR_INVALID_ARG, "bad omega_m or a");

@@ -144,6 +144,22 @@ def test_b1_gr_theory_matches_the_oracle(pm):
         pm.pm_b1_gr_theory(cfg, -1.0, 2.0)
 
 
+def test_linear_power_matches_the_oracle(pm):
+    # host-only: the library's Eisenstein-Hu no-wiggle spectrum, sigma_8 normalisation and growth
+    # (C++ quadrature) against the oracle's (scipy), which the ICs of both sides draw from
+    from oracle.cosmology import Cosmology
+    c = Cosmology()
+    cfg = pm.make_config(32, 64, 1000.0, 0.02, 1.0, 10)
+    k = np.geomspace(1e-4, 10.0, 23)
+    for a in (1.0, 0.5, 1.0 / 51.0):
+        p, D, f = pm.pm_linear_power(cfg, a, k)
+        np.testing.assert_allclose(p, c.power_linear(k, a), rtol=1e-9)
+        assert D == pytest.approx(c.growth_D(a), rel=1e-10) and f == pytest.approx(c.growth_f(a), rel=1e-10)
+    assert pm.pm_linear_power(cfg, 1.0, np.zeros(1))[0][0] == 0.0
+    with pytest.raises(pm.PMError):
+        pm.pm_linear_power(cfg, 1.0, np.array([-1.0]))
+
+
 @pytest.mark.parametrize("stepping", [0, 1])
 def test_step_factors_match_the_oracle(pm, stepping):
     # host-only: the FP64 kick and drift factors pm_step uses (its own Gauss-Legendre quadrature
