@@ -43,6 +43,7 @@ Planck 2018's measured r_drag within 3% and the baryon suppression alpha_Gamma
 (Eq. 31) to Sugiyama's (1995) independent fit within 1.5%, but L0 and C0
 (Eqs. 29-30) only through the BBKS shape within 8% (checked by eye), so a change
 of a few percent in one of their constants would pass.  Eq. bgr
-(``stats.b1_gr_theory``) is pinned only against the paper's Table 1 within its
-1.5-sigma errors, which do not tell its (3/2) Omega_m(z) term from Omega_m(z).
+(``stats.b1_gr_theory``) is pinned by its derivation from the gauge relations of
+linear theory (the Poisson-gauge shift of the comoving density and the counting
+volume of Eq. physical_density) and against the paper's Table 1.
 """

@@ -118,6 +118,35 @@ def test_sigma8_normalisation_and_growth_scaling():
     assert c.power_linear(0.05, a) / c.power_linear(0.05) == pytest.approx(c.growth_D(a)**2, rel=1e-12)
 
 
+def test_eq_bgr_from_the_gauge_relations_of_linear_theory():
+    # Eq. bgr derived, not restated: for the growing mode of pressureless matter + Lambda the
+    # comoving density delta_c grows as D on all scales, its velocity divergence in the Poisson
+    # (longitudinal) gauge is theta = -calH f delta_c, and k^2 Phi = -(3/2) calH^2 Om(a) delta_c.
+    # The Poisson-gauge density is delta_P = delta_c - 3 calH theta / k^2; halos with comoving bias
+    # b1 move with the matter, so they take the same gauge term; the counting densities are
+    # delta_P - 3 Phi (Eq. physical_density).  The coefficient of calH^2/k^2 in their ratio at
+    # k >> calH is b1^GR.
+    c = Cosmology()
+    for z, b1 in ((0.0, 2.0), (0.5, 3.0), (1.0, 1.5), (2.0, 4.5)):
+        a = 1.0 / (1.0 + z)
+        H, f, om = float(c.conformal_hubble(a)), c.growth_f(a), float(c.omega_m_a(a))
+        k = 1e4 * H
+        x = (H / k)**2
+        dc = 1.0
+        theta = -H * f * dc
+        phi = -1.5 * H * H * om * dc / k**2
+        d_m = dc - 3.0 * H * theta / k**2 - 3.0 * phi
+        d_h = b1 * dc - 3.0 * H * theta / k**2 - 3.0 * phi
+        slope = (d_h / d_m - b1) / x
+        assert slope == pytest.approx(b1_gr_theory(b1, f, om), rel=1e-6)
+    # the gauge term's sign: a superhorizon mode in matter domination (f = Om = 1) has the
+    # textbook Poisson-gauge density delta_P = -2 Phi
+    x = 1e8
+    d_p = 1.0 + 3.0 * x  # delta_c - 3 calH theta / k^2 with theta = -calH delta_c
+    phi = -1.5 * x
+    assert d_p / (-2.0 * phi) == pytest.approx(1.0, rel=1e-7)
+
+
 def test_paper_table1_gr_bias_consistent_with_eq_bgr():
     # Table 1 b1GR at z <= 0.5 lies within 1.5 sigma of Eq. bgr evaluated with the oracle's
     # f(z) and Omega_m(z) in the Sec. 3 cosmology (the paper reports agreement with theory).
